@@ -1,0 +1,286 @@
+"""CPU oracle of the DARB-Splatting rasterizer: ctypes wrapper around darb_oracle.c.
+
+TEST INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / reference legs of ``bench.py`` may import this package.
+It shares no code with the CUDA library and imports nothing from it.
+
+Every function here is argument marshalling; the arithmetic lives in
+darb_oracle.c (see its header for what is computed and where the paper
+defines it).
+
+Kernel table (Table 1 forms with the xi of Table 2, the psi of the Sec. B
+listings, and the main-lobe limits of Sec. A.3 / the listings):
+
+  name               enum  psi    q_max  strict   F(q), q = d_M^2
+  gaussian            0    1.0    9.0    no       exp(-q/2)
+  half_cosine         1    1.36   9.0    no       cos(pi q / 18)
+  raised_cosine       2    0.655  6.25   no       1/2 + 1/2 cos(pi sqrt(q) / 2.5)
+  mod_sinc            3    1.18   9.0    no       sin(x)/x, x = pi sqrt(q) / 3
+  inv_quadric         4    1.38   9.0    yes      1 / (1 + q)
+  inv_multiquadric    5    1.61   9.0    yes      (1 + q)^(-1/2)
+  parabola            6    1.3    9.0    no       1 - q/9
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import shutil
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "darb_oracle.c")
+_HDR = os.path.join(_HERE, "project_impl.h")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_OUT_DIR, "libdarb_oracle.so")
+
+KERNELS = {
+    # name: (enum, psi, q_max, strict)
+    "gaussian": (0, 1.0, 9.0, 0),
+    "half_cosine": (1, 1.36, 9.0, 0),
+    "raised_cosine": (2, 0.655, 6.25, 0),
+    "mod_sinc": (3, 1.18, 9.0, 0),
+    "inv_quadric": (4, 1.38, 9.0, 1),
+    "inv_multiquadric": (5, 1.61, 9.0, 1),
+    "parabola": (6, 1.3, 9.0, 0),
+}
+KERNEL_NAMES = list(KERNELS)
+
+# Default ambiguity margins for the alpha >= 1/255 and T(1-alpha) >= 1e-4 tests:
+# |alpha - 1/255| <= EPS_ALPHA (absolute), |T(1-alpha) - 1e-4| <= EPS_T * 1e-4.
+EPS_ALPHA = 2e-6
+EPS_T = 2e-3
+
+
+class OrcCamera(ctypes.Structure):
+    _fields_ = [("viewmat", ctypes.c_float * 16), ("fx", ctypes.c_float), ("fy", ctypes.c_float),
+                ("cx", ctypes.c_float), ("cy", ctypes.c_float), ("near_plane", ctypes.c_float),
+                ("width", ctypes.c_int), ("height", ctypes.c_int), ("bg", ctypes.c_float * 3)]
+
+
+class OrcKernel(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("psi", ctypes.c_float), ("q_max", ctypes.c_float),
+                ("q_max_strict", ctypes.c_int)]
+
+
+class OrcOutcome(ctypes.Structure):
+    _fields_ = [("pixel", ctypes.c_int), ("count", ctypes.c_int), ("last_id", ctypes.c_int),
+                ("primary", ctypes.c_int), ("T", ctypes.c_double), ("C", ctypes.c_double * 3),
+                ("sig", ctypes.c_uint64)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def _needs_build() -> bool:
+    if not os.path.exists(_LIB_PATH):
+        return True
+    t = os.path.getmtime(_LIB_PATH)
+    return any(os.path.getmtime(p) > t for p in (_SRC, _HDR))
+
+
+def build(force: bool = False) -> str:
+    """Compile darb_oracle.c with gcc (-O2, no FP contraction, OpenMP if available)."""
+    if not force and not _needs_build():
+        return _LIB_PATH
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        raise RuntimeError("no C compiler found to build the oracle")
+    base = [cc, "-O2", "-std=c11", "-D_GNU_SOURCE", "-ffp-contract=off", "-fno-fast-math",
+            "-fPIC", "-shared", "-I", _HERE, _SRC, "-o", _LIB_PATH + ".tmp", "-lm"]
+    for extra in (["-fopenmp"], []):
+        r = subprocess.run(base[:1] + extra + base[1:], capture_output=True, text=True)
+        if r.returncode == 0:
+            os.replace(_LIB_PATH + ".tmp", _LIB_PATH)
+            return _LIB_PATH
+    raise RuntimeError("oracle build failed:\n" + r.stderr)
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            _lib = ctypes.CDLL(_LIB_PATH)
+            _lib.orc_build_lists.restype = ctypes.c_longlong
+            _lib.orc_num_threads.restype = ctypes.c_int
+    return _lib
+
+
+def num_threads() -> int:
+    return int(lib().orc_num_threads())
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+def kernel_params(name_or_kind, psi=None):
+    name = KERNEL_NAMES[name_or_kind] if isinstance(name_or_kind, int) else name_or_kind
+    kind, p, qmax, strict = KERNELS[name]
+    return OrcKernel(kind, float(p if psi is None else psi), float(qmax), int(strict))
+
+
+def camera_struct(cam) -> OrcCamera:
+    c = OrcCamera()
+    c.viewmat[:] = [float(v) for v in np.asarray(cam.viewmat, np.float32).reshape(16)]
+    c.fx, c.fy, c.cx, c.cy, c.near_plane = cam.fx, cam.fy, cam.cx, cam.cy, cam.near
+    c.width, c.height = cam.width, cam.height
+    c.bg[:] = [float(b) for b in cam.bg]
+    return c
+
+
+def tiles_xy(cam, tile):
+    return (cam.width + tile - 1) // tile, (cam.height + tile - 1) // tile
+
+
+def kernel_eval(kind, q):
+    q = np.ascontiguousarray(q, np.float64)
+    F = np.empty_like(q)
+    dF = np.empty_like(q)
+    lib().orc_kernel_eval(ctypes.c_int(kind), ctypes.c_int(q.size), _p(q), _p(F), _p(dF))
+    return F, dF
+
+
+def sh_basis(deg, dirs):
+    dirs = np.ascontiguousarray(dirs, np.float64).reshape(-1, 3)
+    K = (deg + 1) ** 2
+    Y = np.empty((dirs.shape[0], K))
+    dY = np.empty((dirs.shape[0], K, 3))
+    lib().orc_sh_basis(ctypes.c_int(deg), ctypes.c_int(dirs.shape[0]), _p(dirs), _p(Y), _p(dY))
+    return Y, dY
+
+
+def project(splats, cam, kparams, tile=16, geom32=True):
+    """Per-splat preprocessing.  Returns a dict of numpy arrays."""
+    n = splats.n
+    out = dict(
+        culled=np.empty(n, np.int32), radius=np.empty(n, np.int32), rect=np.empty((n, 4), np.int32),
+        tiles=np.empty(n, np.int32), depth=np.empty(n, np.float32), clampxy=np.empty((n, 2), np.int32),
+        mean2d=np.empty((n, 2)), conic=np.empty((n, 3)), rgb=np.empty((n, 3)), clamped=np.empty(n, np.uint8))
+    c = camera_struct(cam)
+    r = lib().orc_project(ctypes.c_int(n), _p(splats.means), _p(splats.scales), _p(splats.quats),
+                          _p(splats.sh), ctypes.c_int(splats.sh_degree), ctypes.byref(c),
+                          ctypes.byref(kparams), ctypes.c_int(tile), ctypes.c_int(int(geom32)),
+                          _p(out["culled"]), _p(out["radius"]), _p(out["rect"]), _p(out["tiles"]),
+                          _p(out["depth"]), _p(out["clampxy"]), _p(out["mean2d"]), _p(out["conic"]),
+                          _p(out["rgb"]), _p(out["clamped"]))
+    if r != 0:
+        raise ValueError("orc_project rejected its arguments")
+    out["geom32"] = bool(geom32)
+    out["opac"] = np.ascontiguousarray(splats.opacities, np.float32)
+    return out
+
+
+def build_lists(proj, cam, tile=16, tile_mask=None):
+    """Sorted (tile, depth, id) instances.  Returns keys u64[M], ids i32[M], ranges i32[tiles,2]."""
+    tx, ty = tiles_xy(cam, tile)
+    n = proj["culled"].shape[0]
+    mask = None if tile_mask is None else np.ascontiguousarray(tile_mask, np.uint8).reshape(-1)
+    L = lib()
+    args = (ctypes.c_int(n), _p(proj["culled"]), _p(proj["rect"]), _p(proj["depth"]), ctypes.c_int(tx),
+            ctypes.c_int(ty), _p(mask))
+    M = L.orc_build_lists(*args, None, None, ctypes.c_longlong(0), None)
+    keys = np.empty(max(M, 1), np.uint64)
+    ids = np.empty(max(M, 1), np.int32)
+    ranges = np.zeros((tx * ty, 2), np.int32)
+    M2 = L.orc_build_lists(*args, _p(keys), _p(ids), ctypes.c_longlong(M), _p(ranges))
+    if M2 != M:
+        raise RuntimeError("orc_build_lists failed")
+    return dict(keys=keys[:M], ids=ids[:M], ranges=ranges, M=int(M))
+
+
+def render(proj, cam, kparams, tile=16, mode="tiled", lists=None, tile_mask=None,
+           eps_alpha=EPS_ALPHA, eps_T=EPS_T, max_branch=3, alts_cap=1 << 16):
+    """Front-to-back composite.  mode: 'tiled' or 'brute'.
+
+    Returns image [3,H,W] (f64), T [H,W], count [H,W], last_id [H,W] (-1 if none),
+    amb [H,W] (0 unique, 1 several outcomes enumerated, 2 unverifiable),
+    sig [H,W] (hash of the blended id sequence) and alts (list of the other
+    outcomes of ambiguous pixels: pixel, count, last_id, T, C).
+    """
+    W, H = cam.width, cam.height
+    mask = None if tile_mask is None else np.ascontiguousarray(tile_mask, np.uint8).reshape(-1)
+    if mode == "tiled" and lists is None:
+        lists = build_lists(proj, cam, tile, mask)
+    image = np.zeros((3, H, W))
+    T = np.ones((H, W))
+    count = np.zeros((H, W), np.int32)
+    last = np.full((H, W), -1, np.int32)
+    amb = np.zeros((H, W), np.int32)
+    sig = np.zeros((H, W), np.uint64)
+    alts = (OrcOutcome * alts_cap)()
+    nalts = ctypes.c_int(0)
+    c = camera_struct(cam)
+    ids = lists["ids"] if mode == "tiled" else None
+    ranges = lists["ranges"] if mode == "tiled" else None
+    n = proj["culled"].shape[0]
+    r = lib().orc_render(
+        ctypes.c_int(n), _p(proj["culled"]), _p(proj["rect"]), _p(proj["depth"]), _p(proj["mean2d"]),
+        _p(proj["conic"]), _p(proj["opac"]), _p(proj["rgb"]), ctypes.c_int(int(proj["geom32"])),
+        ctypes.byref(c), ctypes.byref(kparams), ctypes.c_int(tile), ctypes.c_int(1 if mode == "tiled" else 0),
+        _p(ids), _p(ranges), _p(mask), ctypes.c_double(eps_alpha), ctypes.c_double(eps_T),
+        ctypes.c_int(max_branch), _p(image), _p(T), _p(count), _p(last), _p(amb), _p(sig),
+        alts, ctypes.c_int(alts_cap), ctypes.byref(nalts))
+    if r != 0:
+        raise RuntimeError("orc_render failed")
+    k = min(nalts.value, alts_cap)
+    alt_list = [dict(pixel=alts[i].pixel, count=alts[i].count, last_id=alts[i].last_id, T=alts[i].T,
+                     C=tuple(alts[i].C)) for i in range(k)]
+    return dict(image=image, T=T, count=count, last_id=last, amb=amb, sig=sig, alts=alt_list,
+                alts_overflow=nalts.value > alts_cap, lists=lists)
+
+
+def render_backward(proj, cam, kparams, lists, dL_dimage, tile=16, tile_mask=None):
+    """Gradient of the composite w.r.t. per-splat (mu'x, mu'y, A, B, C, opacity, r, g, b)."""
+    n = proj["culled"].shape[0]
+    grad2d = np.zeros((n, 9))
+    dl = np.ascontiguousarray(dL_dimage, np.float64)
+    mask = None if tile_mask is None else np.ascontiguousarray(tile_mask, np.uint8).reshape(-1)
+    c = camera_struct(cam)
+    r = lib().orc_render_backward(
+        ctypes.c_int(n), _p(proj["rect"]), _p(proj["mean2d"]), _p(proj["conic"]), _p(proj["opac"]),
+        _p(proj["rgb"]), ctypes.c_int(int(proj["geom32"])), ctypes.byref(c), ctypes.byref(kparams),
+        ctypes.c_int(tile), _p(lists["ids"]), _p(lists["ranges"]), ctypes.c_longlong(lists["M"]), _p(mask),
+        _p(dl), _p(grad2d))
+    if r != 0:
+        raise RuntimeError("orc_render_backward failed")
+    return grad2d
+
+
+def project_backward(splats, proj, cam, kparams, grad2d):
+    """Chain the per-splat 2D gradients back to means, scales, quats, opacities and SH."""
+    n = splats.n
+    K = (splats.sh_degree + 1) ** 2
+    out = dict(means=np.empty((n, 3)), scales=np.empty((n, 3)), quats=np.empty((n, 4)),
+               opacities=np.empty(n), sh=np.empty((n, K, 3)))
+    g = np.ascontiguousarray(grad2d, np.float64)
+    c = camera_struct(cam)
+    lib().orc_project_backward(
+        ctypes.c_int(n), _p(splats.means), _p(splats.scales), _p(splats.quats), _p(splats.sh),
+        ctypes.c_int(splats.sh_degree), ctypes.byref(c), ctypes.byref(kparams), _p(proj["culled"]),
+        _p(proj["clampxy"]), _p(proj["clamped"]), _p(g), _p(out["means"]), _p(out["scales"]),
+        _p(out["quats"]), _p(out["opacities"]), _p(out["sh"]))
+    return out
+
+
+def forward(splats, cam, kernel="half_cosine", tile=16, mode="tiled", geom32=True, tile_mask=None, **kw):
+    kp = kernel_params(kernel) if isinstance(kernel, (str, int)) else kernel
+    proj = project(splats, cam, kp, tile, geom32)
+    lists = build_lists(proj, cam, tile, tile_mask) if mode == "tiled" else None
+    out = render(proj, cam, kp, tile, mode, lists, tile_mask, **kw)
+    out["proj"] = proj
+    return out
+
+
+def gradients(splats, cam, dL_dimage, kernel="half_cosine", tile=16, geom32=True, tile_mask=None):
+    """Forward (tiled) + analytic backward.  Returns (forward dict, grad2d, param grads)."""
+    kp = kernel_params(kernel) if isinstance(kernel, (str, int)) else kernel
+    fwd = forward(splats, cam, kp, tile, "tiled", geom32, tile_mask)
+    g2 = render_backward(fwd["proj"], cam, kp, fwd["lists"], dL_dimage, tile, tile_mask)
+    gp = project_backward(splats, fwd["proj"], cam, kp, g2)
+    return fwd, g2, gp

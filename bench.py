@@ -1,0 +1,504 @@
+#!/usr/bin/env python3
+"""Benchmark of the DARB rasterizer on GB300: one 3DGS-style training iteration per step.
+
+Workload: 3,000,000 clustered splats (SH degree 3), 100 cameras on a radius-6 sphere,
+1920x1080, fx = 1500, half-cosine kernel (the paper's headline DARB kernel), 16x16 tiles.
+A step is the whole hot path for one camera: preprocess -> tile/depth key duplication ->
+radix sort + tile ranges -> compositing -> L1 loss -> compositing backward -> preprocess
+backward -> Adam, all in libdarb.so kernels called through the C ABI.  The splat state
+(~2.1 GB with Adam moments) is far larger than L2, so no L2 flush is needed between steps.
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+import torch  # noqa: E402
+
+METRIC = "fwd Mpix/s & fwd+bwd iters/s at 3M splats 1080p; serving p50/p99 ms"
+WORKLOAD = "train_step_3M_splats_1080p"
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+LRS = dict(means=1.6e-4 * 6.0, scales=5e-3, quats=1e-3, opacities=0.02, sh_dc=2.5e-3, sh_rest=2.5e-3 / 20)
+
+
+# ----------------------------------------------------------------------------- distributed
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def dist_init(world, backend):
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend=backend)
+        return dist
+    return None
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(dist, value, device):
+    if dist is None:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi sampled every 200 ms while the timed region runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(f[1]), max=float(f[2]), hw=f[5], hwt=f[6], swt=f[7], pc=f[8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        reasons = set()
+        for r in rows:
+            for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"), ("swt", "sw_thermal_slowdown"),
+                              ("pc", "sw_power_cap")):
+                if r[key].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in rows), "sm_max_mhz": max(r["max"] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------- our arm
+
+class TrainStep:
+    """Device buffers of one training replica and the per-step sequence of C-ABI calls."""
+
+    def __init__(self, splats, cams, kernel, tile, device):
+        from paper_2501_12369_gb300 import darb
+        self.darb = darb
+        self.L = darb.lib()
+        self.cams = cams
+        self.tile = tile
+        self.device = device
+        self.kp = darb.darb_kernel_defaults(kernel)
+        n = splats.n
+        self.n = n
+        dev = dict(device=device, dtype=torch.float32)
+        t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device)  # noqa: E731
+        self.means, self.quats, self.sh = t(splats.means), t(splats.quats), t(splats.sh)
+        self.scales, self.opac = t(splats.scales), t(splats.opacities)
+        self.log_scales = t(np.log(splats.scales))
+        self.logits = t(np.log(splats.opacities / (1.0 - splats.opacities)))
+        self.sh_degree = splats.sh_degree
+        self.state = {f: torch.zeros_like(p) for f, p in (
+            ("m_means", self.means), ("v_means", self.means), ("m_scales", self.scales), ("v_scales", self.scales),
+            ("m_quats", self.quats), ("v_quats", self.quats), ("m_opac", self.opac), ("v_opac", self.opac),
+            ("m_sh", self.sh), ("v_sh", self.sh))}
+        self.proj = darb.Projected.empty(n, device)
+        W, H = cams[0].width, cams[0].height
+        self.W, self.H = W, H
+        self.img = darb.ImageOut.empty(W, H, device)
+        self.grad2d = torch.empty(n, 12, **dev)
+        self.grads = darb.SplatGrads(*(torch.empty_like(x) for x in (self.means, self.scales, self.quats,
+                                                                         self.opac, self.sh)))
+        self.dL = torch.empty(3, H, W, **dev)
+        self.loss = torch.zeros(1, **dev)
+        self.target = torch.empty(3, H, W, **dev)
+        self.tx, self.ty = darb.darb_tile_grid(cams[0], tile)
+        self.cam_structs = [darb.camera(c) for c in cams]
+        self.capacity = 0
+        self.ws = None
+        self.bins = None
+        self.step_no = 0
+        self.kp_ref = ctypes.byref(self.kp)
+        self._structs()
+
+    def _structs(self):
+        d = self.darb
+        self.s_splats = d.darb_splats(d._p(self.means), d._p(self.scales), d._p(self.quats), d._p(self.opac),
+                                      d._p(self.sh), self.n, self.sh_degree)
+        self.s_proj = self.proj.struct()
+        self.s_img = self.img.struct()
+        self.s_grads = self.grads.struct()
+        self.s_params = d.darb_train_params(d._p(self.means), d._p(self.log_scales), d._p(self.quats),
+                                            d._p(self.logits), d._p(self.sh), d._p(self.scales), d._p(self.opac),
+                                            self.n, self.sh_degree)
+        self.s_state = d.darb_adam_state(*(d._p(self.state[f]) for f, _ in d.darb_adam_state._fields_))
+
+    def set_capacity(self, capacity):
+        d = self.darb
+        self.capacity = int(capacity)
+        nbytes = d.darb_bin_sort_workspace_size(self.n, self.tile, self.cams[0], self.capacity)
+        self.ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.ws_bytes = nbytes
+        self.bins = d.Binning.empty(self.capacity, self.tx * self.ty, self.device)
+        self.s_bins = self.bins.struct()
+
+    def count_instances(self, cam_idx):
+        """M for one camera (synchronising), used to size the capacity before timing."""
+        d = self.darb
+        st = d._stream()
+        c = ctypes.byref(self.cam_structs[cam_idx])
+        d._check(self.L.darb_preprocess(ctypes.byref(self.s_splats), c, self.kp_ref, self.tile,
+                                        ctypes.byref(self.s_proj), st), "preprocess")
+        m = ctypes.c_uint64(0)
+        r = self.L.darb_bin_sort(ctypes.byref(self.s_proj), self.n, self.tile, c, d._p(self.ws), self.ws_bytes,
+                                 self.capacity, ctypes.byref(self.s_bins), ctypes.byref(m), st)
+        if r not in (0, 3):
+            d._check(r, "bin_sort")
+        return int(m.value)
+
+    def forward(self, cam_idx, ev=None):
+        d, L = self.darb, self.L
+        st = d._stream()
+        c = ctypes.byref(self.cam_structs[cam_idx])
+        rec = (lambda i: ev[i].record()) if ev is not None else (lambda i: None)
+        rec(0)
+        d._check(L.darb_preprocess(ctypes.byref(self.s_splats), c, self.kp_ref, self.tile, ctypes.byref(self.s_proj),
+                                   st), "preprocess")
+        rec(1)
+        d._check(L.darb_bin_sort(ctypes.byref(self.s_proj), self.n, self.tile, c, d._p(self.ws), self.ws_bytes,
+                                 self.capacity, ctypes.byref(self.s_bins), None, st), "bin_sort")
+        rec(2)
+        d._check(L.darb_render_fwd(ctypes.byref(self.s_proj), ctypes.byref(self.s_bins), c, self.kp_ref, self.tile,
+                                   ctypes.byref(self.s_img), st), "render_fwd")
+        rec(3)
+
+    def train(self, cam_idx, ev=None):
+        d, L = self.darb, self.L
+        st = d._stream()
+        c = ctypes.byref(self.cam_structs[cam_idx])
+        rec = (lambda i: ev[i].record()) if ev is not None else (lambda i: None)
+        self.forward(cam_idx, ev)
+        d._check(L.darb_l1_loss(d._p(self.img.image), d._p(self.target), self.W, self.H, d._p(self.dL),
+                                d._p(self.loss), st), "l1")
+        rec(4)
+        d._check(L.darb_render_bwd(ctypes.byref(self.s_proj), self.n, ctypes.byref(self.s_bins), c, self.kp_ref,
+                                   self.tile, ctypes.byref(self.s_img), d._p(self.dL), d._p(self.grad2d), st),
+                 "render_bwd")
+        rec(5)
+        d._check(L.darb_preprocess_bwd(ctypes.byref(self.s_splats), c, self.kp_ref, ctypes.byref(self.s_proj),
+                                       d._p(self.grad2d), ctypes.byref(self.s_grads), st), "preprocess_bwd")
+        rec(6)
+        self.step_no += 1
+        cfg = d.darb_adam_config(LRS["means"], LRS["scales"], LRS["quats"], LRS["opacities"], LRS["sh_dc"],
+                                 LRS["sh_rest"], 0.9, 0.999, 1e-15, self.step_no)
+        d._check(L.darb_adam_step(ctypes.byref(self.s_params), ctypes.byref(self.s_grads), ctypes.byref(self.s_state),
+                                  ctypes.byref(cfg), st), "adam")
+        rec(7)
+
+
+STAGES = ["preprocess", "bin_sort", "render_fwd", "l1_loss", "render_bwd", "preprocess_bwd", "adam"]
+
+
+def algorithmic_bytes(stage, n, M, passes, sh_k):
+    """HBM bytes a stage must move at minimum, per launch (see the data layout notes in the docs)."""
+    sh_b = sh_k * 3 * 4
+    if stage == "preprocess":
+        return n * (12 + 12 + 16 + 4 + sh_b) + n * (4 + 4 + 16 + 8 + 16 + 12 + 1 + 4)
+    if stage == "bin_sort":
+        return n * (4 + 4 + 16 + 4) + M * (12 + 8 + 24 * passes + 8)
+    if stage == "preprocess_bwd":
+        return n * (12 + 12 + 16 + sh_b + 48 + 4 + 1) + n * (12 + 12 + 16 + 4 + sh_b)
+    if stage == "adam":
+        params = 3 + 3 + 4 + 1 + sh_k * 3
+        return n * (params * 28 + 4 * 8)
+    return None
+
+
+def load_peaks():
+    try:
+        return json.load(open(PEAKS_PATH))
+    except (OSError, ValueError):
+        return None
+
+
+def cpu_baseline(splats, cams, kernel, tile, target_seconds=15.0):
+    """The oracle, as it stands, on the host cores: one training iteration of the same workload,
+    estimated from a bounded sample (full preprocess and preprocess backward; compositing forward
+    and backward on a random subset of tiles scaled to the frame; Adam on a 200k-splat slice
+    scaled to 3M)."""
+    import oracle
+    cam = cams[0]
+    kp = oracle.kernel_params(kernel)
+    t0 = time.perf_counter()
+    proj = oracle.project(splats, cam, kp, tile, True)
+    t_pre = time.perf_counter() - t0
+    tx, ty = oracle.tiles_xy(cam, tile)
+    rng = np.random.default_rng(0)
+    order = rng.permutation(tx * ty)
+    dl_full = None
+    done, t_tiles, S = 0, 0.0, 8
+    while True:
+        mask = np.zeros(tx * ty, np.uint8)
+        mask[order[done:done + S]] = 1
+        t0 = time.perf_counter()
+        lists = oracle.build_lists(proj, cam, tile, mask)
+        fwd = oracle.render(proj, cam, kp, tile, "tiled", lists, mask)
+        if dl_full is None:
+            dl_full = np.sign(np.random.default_rng(1).uniform(-1, 1, (3, cam.height, cam.width))) / (3 * cam.width * cam.height)
+        g2 = oracle.render_backward(proj, cam, kp, lists, dl_full, tile, mask)
+        t_tiles += time.perf_counter() - t0
+        done += S
+        if t_tiles > target_seconds * 0.5 or done >= tx * ty:
+            break
+        S *= 2
+    t0 = time.perf_counter()
+    oracle.project_backward(splats, proj, cam, kp, g2)
+    t_pbwd = time.perf_counter() - t0
+    sl = slice(0, min(200_000, splats.n))
+    raw = dict(means=splats.means[sl], log_scales=np.log(splats.scales[sl]), quats=splats.quats[sl],
+               opacity_logits=np.log(splats.opacities[sl] / (1 - splats.opacities[sl])), sh=splats.sh[sl])
+    grads = dict(means=raw["means"], scales=splats.scales[sl], quats=raw["quats"], opacities=splats.opacities[sl],
+                 sh=raw["sh"])
+    state = {f"{m}_{k}": np.zeros_like(raw[k], np.float64) for k in raw for m in ("m", "v")}
+    t0 = time.perf_counter()
+    oracle.adam_step_splats(raw, grads, state, LRS, 1)
+    t_adam = (time.perf_counter() - t0) * splats.n / (sl.stop - sl.start)
+    frac = done / (tx * ty)
+    est = t_pre + t_tiles / frac + t_pbwd + t_adam
+    return {"value": 1.0 / est, "unit": "it/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": (f"one 1920x1080 view of the 3M-splat scene: full FP32/FP64 preprocess ({t_pre:.1f} s) and "
+                       f"preprocess backward ({t_pbwd:.1f} s); tiled compositing forward+backward on {done} random "
+                       f"tiles of {tx * ty} ({t_tiles:.1f} s, scaled x{1 / frac:.0f}); Adam on 200k splats "
+                       f"scaled to {splats.n}"),
+            "seconds_per_iteration": est}
+
+
+def run_ours(args):
+    world, rank, local = dist_env()
+    dist = dist_init(world, "nccl")
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    from paper_2501_12369_gb300 import build, synth
+    build.build()
+    splats, cams = synth.scene_3m_1080p()
+    ts = TrainStep(splats, cams, args.kernel, args.tile, device)
+    # replicas: rank r trains on its own camera sequence
+    cam_seq = [(rank * 37 + i) % len(cams) for i in range(args.warmup + args.steps)]
+    targets = [torch.from_numpy(synth.random_target(1080, 1920, seed=10 + i)).to(device) for i in range(4)]
+    # capacity from the cameras this run visits (x1.3 for the Adam drift), probed before timing
+    ts.set_capacity(1 << 20)
+    Ms = []
+    for ci in sorted(set(cam_seq)):
+        m = ts.count_instances(ci)
+        if m > ts.capacity:
+            ts.set_capacity(int(m * 1.3))
+            m = ts.count_instances(ci)
+        Ms.append(m)
+    ts.set_capacity(int(max(Ms) * 1.3) + 1024)
+    torch.cuda.synchronize()
+
+    def step(i, ev=None):
+        ts.target.copy_(targets[i % 4], non_blocking=True) if ev is None else None
+        ts.train(cam_seq[i], ev)
+
+    # warm-up
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+
+    # timed training steps with per-stage events
+    n_ev = 8
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(n_ev)] for _ in range(args.steps)]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    barrier(dist)
+    torch.cuda.synchronize()
+    clocks.start()
+    start.record()
+    for k in range(args.steps):
+        ts.target = targets[k % 4]
+        step(args.warmup + k, evs[k])
+    end.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier(dist)
+    ms_total = start.elapsed_time(end)
+    ms_max = max_over_ranks(dist, ms_total, device)
+    status = int(ts.bins.status.item())
+    if status != 0:
+        raise RuntimeError(f"bin_sort reported status {status} during the timed run")
+    stage_ms = {s: 0.0 for s in STAGES}
+    for e in evs:
+        for j, s in enumerate(STAGES):
+            stage_ms[s] += e[j].elapsed_time(e[j + 1])
+    stage_ms = {s: v / args.steps for s, v in stage_ms.items()}
+
+    # forward only (Mpix/s)
+    fstart, fend = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    fstart.record()
+    for k in range(args.steps):
+        ts.forward(cam_seq[args.warmup + k])
+    fend.record()
+    torch.cuda.synchronize()
+    fwd_ms = max_over_ranks(dist, fstart.elapsed_time(fend), device)
+    fwd_mpix = world * args.steps * 1920 * 1080 / (fwd_ms / 1e3) / 1e6
+
+    # end to end through the C ABI with host buffers: target image H2D from pinned memory,
+    # loss D2H into pinned memory, every step
+    host_targets = [t.cpu().pin_memory() for t in targets]
+    loss_host = torch.empty(args.steps, dtype=torch.float32).pin_memory()
+    dev_target = torch.empty_like(targets[0])
+    ts.target = dev_target
+    estart, eend = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(dist)
+    torch.cuda.synchronize()
+    estart.record()
+    for k in range(args.steps):
+        dev_target.copy_(host_targets[k % 4], non_blocking=True)
+        ts.train(cam_seq[args.warmup + k])
+        loss_host[k:k + 1].copy_(ts.loss, non_blocking=True)
+    eend.record()
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(dist, estart.elapsed_time(eend), device)
+    assert np.isfinite(loss_host.numpy()).all()
+
+    # roofline of the dominant kernel stage
+    M_mean = float(np.mean(Ms))
+    passes = (32 + int(np.ceil(np.log2(ts.tx * ts.ty))) + 7) // 8
+    sh_k = (splats.sh_degree + 1) ** 2
+    dominant = max(stage_ms, key=stage_ms.get)
+    hbm_stages = {s: stage_ms[s] for s in ("preprocess", "bin_sort", "preprocess_bwd", "adam")}
+    peaks = load_peaks()
+    peak_gbs = peaks["hbm_gbs"] if peaks else 6800.0
+    rl_stage = dominant if algorithmic_bytes(dominant, ts.n, M_mean, passes, sh_k) else max(hbm_stages, key=hbm_stages.get)
+    ab = algorithmic_bytes(rl_stage, ts.n, M_mean, passes, sh_k)
+    achieved = ab / (stage_ms[rl_stage] / 1e3) / 1e9
+    its = world * args.steps / (ms_max / 1e3)
+    line = {
+        "metric": METRIC, "value": its, "unit": "it/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic (seeded clustered splats; no dataset)",
+        "config": {"workload": WORKLOAD, "splats": ts.n, "sh_degree": splats.sh_degree, "width": 1920,
+                   "height": 1080, "fx": 1500.0, "cameras": len(cams), "kernel": args.kernel, "tile": args.tile,
+                   "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (2.1 GB splat state)",
+                   "mean_instances": int(M_mean)},
+        "fwd_mpix_s": fwd_mpix,
+        "fwd_ms": fwd_ms / args.steps,
+        "stage_ms": {s: round(v, 4) for s, v in stage_ms.items()},
+        "dominant_stage": dominant,
+        "roofline": {"bound": "hbm", "kernel": rl_stage, "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
+                     "frac": achieved / peak_gbs, "traffic": None,
+                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback 6.8 TB/s",
+                     "algorithmic_bytes": ab},
+        "e2e": {"value": world * args.steps / (e2e_ms / 1e3), "unit": "it/s",
+                "h2d_bytes_per_step": int(targets[0].numel() * 4), "d2h_bytes_per_step": 4},
+        "gpu_launches": None,
+        "clocks": clk,
+    }
+    line["gpu_launches"] = args.steps * launches_per_step(passes)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(splats, cams, args.kernel, args.tile)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def launches_per_step(passes):
+    # preprocess 1; bin_sort: block sums, scan, duplicate, histogram, hist scan, passes x onesweep, ranges;
+    # render_fwd 1; l1 1; render_bwd 1; preprocess_bwd 1; adam 5 groups
+    return 1 + (6 + passes) + 1 + 1 + 1 + 1 + 5
+
+
+# ----------------------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    world, rank, local = dist_env()
+    if rank != 0:
+        return
+    from paper_2501_12369_gb300 import synth
+    import oracle
+    oracle.build()
+    splats, cams = synth.scene_3m_1080p()
+    vals = []
+    for i in range(args.warmup + args.steps):
+        r = cpu_baseline(splats, [cams[i % len(cams)]], args.kernel, args.tile, target_seconds=2.0)
+        if i >= args.warmup:
+            vals.append(r["value"])
+    v = float(np.mean(vals))
+    line = {"metric": METRIC, "value": v, "unit": "it/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded clustered splats; no dataset)",
+            "config": {"workload": WORKLOAD, "splats": splats.n, "sh_degree": 3, "width": 1920, "height": 1080,
+                       "kernel": args.kernel, "tile": args.tile, "parallelism": "host cores"},
+            "impl": "reference",
+            "cpu_baseline": {"value": v, "unit": "it/s", "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": r["sample"]},
+            "e2e": {"value": v, "unit": "it/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--kernel", default="half_cosine")
+    ap.add_argument("--tile", type=int, default=16)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,248 @@
+/*
+ * darb.h -- C ABI of libdarb.so, a GB300 (sm_103a) differentiable tile rasterizer for
+ * DARB splats: 3D anisotropic splats whose reconstruction kernel is a decaying
+ * anisotropic radial basis function F(d_M) of the Mahalanobis distance
+ * (arxiv 2501.12369, Sec. 4, Eq. darbf_class, Table 1).
+ *
+ * Conventions for every entry point
+ *   - Pointers named "device" are CUDA global-memory pointers on the current device;
+ *     "host" pointers are ordinary CPU memory.  The caller owns and allocates every
+ *     buffer; the library never allocates device memory on these paths and keeps no
+ *     pointer after a call returns.
+ *   - Device pointers must be 16-byte aligned (any cudaMalloc / PyTorch allocation is).
+ *   - All work is enqueued on the given stream (NULL = legacy default stream) and runs
+ *     asynchronously unless the entry point says it synchronises.
+ *   - Errors are returned as darb_status; nothing is thrown across the ABI.  A status
+ *     other than DARB_OK means nothing was enqueued, except DARB_ERR_CUDA (a launch or
+ *     copy failed; the stream state is undefined) and the statuses that say otherwise.
+ *   - Arrays are row-major, C-contiguous float32 unless stated.  Images are planar
+ *     [3][H][W].  Pixel (x, y) has its centre at (x + 0.5, y + 0.5).
+ *   - Cameras use OpenCV axes (x right, y down, z forward); viewmat maps world to camera.
+ */
+#ifndef DARB_H
+#define DARB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *darb_stream; /* a cudaStream_t */
+
+typedef enum {
+    DARB_OK = 0,
+    DARB_ERR_INVALID_ARG = 1, /* bad size, NULL, misaligned pointer, unknown enum */
+    DARB_ERR_WORKSPACE = 2,   /* workspace smaller than the size query returned */
+    DARB_ERR_CAPACITY = 3,    /* more (splat, tile) instances than the output capacity */
+    DARB_ERR_CUDA = 4,        /* a CUDA runtime call failed */
+    DARB_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up; results invalid */
+    DARB_ERR_ADMISSION = 6,   /* serving: request cannot be admitted */
+    DARB_ERR_NOT_FOUND = 7    /* serving: unknown scene or ticket */
+} darb_status;
+
+/* Reconstruction kernels.  q = d_M^2 under the psi-corrected, dilated 2D covariance.
+ *   GAUSSIAN          exp(-q/2)                        (Table 1, xi = 2)
+ *   HALF_COSINE       cos(pi q / 18)                   (Eq. HalfCosine, xi = 18/pi)
+ *   RAISED_COSINE     1/2 + 1/2 cos(pi sqrt(q) / 2.5)  (Sec. B.1, xi = 2.5/pi)
+ *   MOD_SINC          |sin x| / x, x = pi sqrt(q) / 3  (Sec. B.3, xi = 3/pi)
+ *   INV_QUADRIC       1 / (1 + q)                      (Sec. B.4 listing)
+ *   INV_MULTIQUADRIC  (1 + q)^(-1/2)                   (Table 1, xi = 1)
+ *   PARABOLA          1 - q/9                          (Table 1, Sec. B.5, xi = 9)      */
+typedef enum {
+    DARB_GAUSSIAN = 0,
+    DARB_HALF_COSINE = 1,
+    DARB_RAISED_COSINE = 2,
+    DARB_MOD_SINC = 3,
+    DARB_INV_QUADRIC = 4,
+    DARB_INV_MULTIQUADRIC = 5,
+    DARB_PARABOLA = 6
+} darb_kernel;
+
+/* kind: a darb_kernel.  psi: correction factor multiplying the 2x2 EWA block (Eq.
+ * 2x2covProjection, Table 2).  q_max: main-lobe limit on q (Sec. A.3); a pixel is
+ * skipped when q > q_max, or q >= q_max when q_max_strict is non-zero. */
+typedef struct {
+    int32_t kind;
+    float psi;
+    float q_max;
+    int32_t q_max_strict;
+} darb_kernel_params;
+
+typedef struct {
+    float viewmat[16]; /* world -> camera, row-major [R t; 0 0 0 1] */
+    float fx, fy, cx, cy, near_plane;
+    int32_t width, height;
+    float bg[3]; /* background colour composited behind the splats */
+} darb_camera;
+
+/* Splat parameters, device pointers, SoA (the 3DGS parameterisation, Sec. 4.1).
+ * means [n][3]; scales [n][3] (activated, > 0); quats [n][4] as (w, x, y, z), any
+ * non-zero norm (normalised inside); opacities [n] (activated, in (0, 1));
+ * sh [n][(sh_degree+1)^2][3] real SH coefficients, sh_degree in 0..3. */
+typedef struct {
+    const float *means, *scales, *quats, *opacities, *sh;
+    int32_t n, sh_degree;
+} darb_splats;
+
+/* Per-splat outputs of darb_preprocess, device pointers, each with n entries.
+ * depth [n]: camera-space z.  radius [n]: ceil(3 sqrt(lambda_max)), 0 = culled.
+ * tile_rect [n][4]: inclusive tile rectangle (tx0, ty0, tx1, ty1).
+ * mean2d [n][2]: projected centre in pixels.  conic_o [n][4]: (A, B, C, opacity) with
+ * q = A dx^2 + 2 B dx dy + C dy^2.  rgb [n][3]: SH colour.  clamped [n]: bit c set when
+ * colour channel c was clamped at 0.  tiles_touched [n]: tiles in the rectangle. */
+typedef struct {
+    float *depth;
+    int32_t *radius;
+    int32_t *tile_rect;
+    float *mean2d;
+    float *conic_o;
+    float *rgb;
+    uint8_t *clamped;
+    uint32_t *tiles_touched;
+} darb_projected;
+
+/* Outputs of darb_bin_sort, device pointers.
+ * keys [capacity], values [capacity]: the (splat, tile) instances sorted by
+ * key = tile << 32 | bits(depth), ties by splat index; values hold splat indices.
+ * ranges [tiles_y * tiles_x][2]: [start, end) of each tile's run in values.
+ * num_instances [1]: M, the number of instances (written even when M > capacity).
+ * status [1]: 0, or a darb_status the device detected (DARB_ERR_CAPACITY, DARB_ERR_TIMEOUT). */
+typedef struct {
+    uint64_t *keys;
+    uint32_t *values;
+    uint32_t *ranges;
+    uint32_t *num_instances;
+    uint32_t *status;
+} darb_binning;
+
+/* Outputs of darb_render_fwd, device pointers.
+ * image [3][H][W]; t_final [H][W]: transmittance left after the last blended splat;
+ * last [H][W]: one past the position, within the pixel's tile run, of the last blended
+ * splat (0 if none); n_contrib [H][W]: number of blended splats. */
+typedef struct {
+    float *image;
+    float *t_final;
+    uint32_t *last;
+    uint32_t *n_contrib;
+} darb_image;
+
+/* Gradients w.r.t. the splat parameters, device pointers, layouts as darb_splats.
+ * dscales and dopacities are w.r.t. the activated values. */
+typedef struct {
+    float *dmeans, *dscales, *dquats, *dopacities, *dsh;
+} darb_splat_grads;
+
+/* Human-readable name of a status.  Never NULL. */
+const char *darb_status_string(darb_status s);
+
+/* Paper defaults for a kernel: psi of the Sec. B listings (Table 2 where no listing is
+ * printed), q_max and strictness of the listings' main-lobe limits (Sec. A.3).
+ * out: host pointer.  DARB_ERR_INVALID_ARG for an unknown kind or NULL out. */
+darb_status darb_kernel_defaults(int32_t kind, darb_kernel_params *out);
+
+/* Number of tiles of a camera: tiles_x = ceil(W / tile), tiles_y = ceil(H / tile).
+ * Host pointers.  tile must be 8, 16 or 32. */
+darb_status darb_tile_grid(const darb_camera *cam, int32_t tile, int32_t *tiles_x, int32_t *tiles_y);
+
+/* Step 1: per-splat preprocessing (Sec. 4.1 "DARB Projection"; Eq. 2x2covProjection;
+ * the "cov *= correctionFactor" lines of the Sec. B listings): view transform, near
+ * cull (z <= near_plane), Sigma = R S S^T R^T, Sigma2 = psi (J W Sigma W^T J^T)_2x2
+ * + 0.3 I, conic, R = ceil(3 sqrt(lambda_max)) (Sec. 4.1), pixel-exact tile rectangle,
+ * SH colour.  Geometry follows a fixed IEEE FP32 operation sequence, so the results
+ * are bit-reproducible.  splats, cam, kparams: host structs holding device pointers
+ * (splats) or values.  out: host struct of caller-owned device buffers sized n. */
+darb_status darb_preprocess(const darb_splats *splats, const darb_camera *cam,
+                            const darb_kernel_params *kparams, int32_t tile,
+                            const darb_projected *out, darb_stream stream);
+
+/* Workspace bytes darb_bin_sort needs for n splats and an instance capacity.
+ * Host pointers; no device work. */
+darb_status darb_bin_sort_workspace_size(int32_t n, int32_t tile, const darb_camera *cam,
+                                         uint64_t capacity, size_t *bytes);
+
+/* Steps 2 and 3: tile/depth key duplication and radix sort (the tile-based
+ * rasterization with a bounding box that Sec. A.3 inherits from 3DGS).  Scans
+ * tiles_touched, emits one (tile << 32 | depth bits, splat) instance per tile of each
+ * rectangle, sorts them with an LSD onesweep radix sort over the low
+ * 32 + ceil(log2(tiles)) key bits (stable, so ties keep splat order), and writes the
+ * per-tile ranges.  proj: darb_preprocess outputs.  workspace: device, at least
+ * darb_bin_sort_workspace_size bytes, contents scratch.  capacity: entries of
+ * out->keys / out->values (< 2^30).  num_instances_host: if non-NULL the call
+ * synchronises the stream once to read M and returns DARB_ERR_CAPACITY when
+ * M > capacity (outputs then undefined); if NULL nothing synchronises, the sort is
+ * sized by capacity, and an overflow is reported in out->status. */
+darb_status darb_bin_sort(const darb_projected *proj, int32_t n, int32_t tile,
+                          const darb_camera *cam, void *workspace, size_t workspace_bytes,
+                          uint64_t capacity, const darb_binning *out,
+                          uint64_t *num_instances_host, darb_stream stream);
+
+/* Step 4: per-pixel front-to-back compositing (Sec. 4.1, "alpha blending ... similar to
+ * 3DGS"; forward listings of Sec. B): for each splat of the pixel's tile run in depth
+ * order, skip unless 0 <= q <= q_max, alpha = min(0.99, o F(q)), skip alpha < 1/255,
+ * stop before T (1 - alpha) < 1e-4, C += c alpha T.  Then C += T bg.
+ * q = dx (A dx + 2B dy) + (C dy) dy is evaluated by a fixed FP32 sequence. */
+darb_status darb_render_fwd(const darb_projected *proj, const darb_binning *bins,
+                            const darb_camera *cam, const darb_kernel_params *kparams,
+                            int32_t tile, const darb_image *out, darb_stream stream);
+
+/* Backward of step 4 (Sec. 4.2; backward listings of Sec. B): replays each pixel back
+ * to front from last / t_final, applies dF/dq of the kernel, and accumulates per-splat
+ * gradients.  n: number of splats.  dL_dimage: device [3][H][W].  grad2d: device [n][12],
+ * zeroed by the callee,
+ * per splat (d mu'x, d mu'y, dA, dB, dC, d opacity, dr, dg, db, 0, 0, 0).  The alpha
+ * clamp at 0.99 has zero derivative. */
+darb_status darb_render_bwd(const darb_projected *proj, int32_t n, const darb_binning *bins,
+                            const darb_camera *cam, const darb_kernel_params *kparams,
+                            int32_t tile, const darb_image *fwd, const float *dL_dimage,
+                            float *grad2d, darb_stream stream);
+
+/* Backward of step 1: chains grad2d through the conic, psi, the EWA projection, the
+ * quaternion normalisation and the SH basis (the conic -> covariance lines of the Sec. B
+ * backward listings carry psi).  out: caller-owned device buffers, fully written
+ * (zeros for culled splats). */
+darb_status darb_preprocess_bwd(const darb_splats *splats, const darb_camera *cam,
+                                const darb_kernel_params *kparams, const darb_projected *proj,
+                                const float *grad2d, const darb_splat_grads *out,
+                                darb_stream stream);
+
+/* L1 photometric term of the training loss (Sec. 4.2): loss = mean |image - target|,
+ * dL_dimage = sign(image - target) / (3 H W).  image, target, dL_dimage: device
+ * [3][H][W].  loss: device float[1], overwritten. */
+darb_status darb_l1_loss(const float *image, const float *target, int32_t width, int32_t height,
+                         float *dL_dimage, float *loss, darb_stream stream);
+
+/* Raw (optimised) parameters of a training run, device pointers, layouts as darb_splats
+ * except log_scales = log(scales) and opacity_logits = logit(opacities).  scales and
+ * opacities are the activated copies that darb_adam_step rewrites after the update. */
+typedef struct {
+    float *means, *log_scales, *quats, *opacity_logits, *sh;
+    float *scales, *opacities;
+    int32_t n, sh_degree;
+} darb_train_params;
+
+/* Adam first and second moments, device pointers with the layouts of the raw params. */
+typedef struct {
+    float *m_means, *v_means, *m_scales, *v_scales, *m_quats, *v_quats;
+    float *m_opac, *v_opac, *m_sh, *v_sh;
+} darb_adam_state;
+
+typedef struct {
+    float lr_means, lr_scales, lr_quats, lr_opacities, lr_sh_dc, lr_sh_rest;
+    float beta1, beta2, eps;
+    int32_t step; /* 1-based step number, for bias correction */
+} darb_adam_config;
+
+/* One Adam step of the 3DGS optimiser (Sec. 5: original hyper-parameters, opacity lr
+ * 0.02) on the raw parameters.  grads: w.r.t. the activated values (darb_preprocess_bwd);
+ * chained through exp / sigmoid inside.  Updates params, state and the activated copies. */
+darb_status darb_adam_step(const darb_train_params *params, const darb_splat_grads *grads,
+                           const darb_adam_state *state, const darb_adam_config *cfg,
+                           darb_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DARB_H */

@@ -284,3 +284,45 @@ def gradients(splats, cam, dL_dimage, kernel="half_cosine", tile=16, geom32=True
     g2 = render_backward(fwd["proj"], cam, kp, fwd["lists"], dL_dimage, tile, tile_mask)
     gp = project_backward(splats, fwd["proj"], cam, kp, g2)
     return fwd, g2, gp
+
+
+# ---------------------------------------------------------------------------
+# Training-step terms in plain NumPy FP64.
+
+def l1_loss(image, target):
+    """L1 term of the loss (Sec. 4.2): mean |image - target| and its gradient sign(.)/count."""
+    d = np.asarray(image, np.float64) - np.asarray(target, np.float64)
+    return np.abs(d).mean(), np.sign(d) / d.size
+
+
+def adam_update(p, g, m, v, lr, step, beta1=0.9, beta2=0.999, eps=1e-15):
+    """One Adam step (Kingma & Ba, Algorithm 1) on float64 copies; returns (p, m, v)."""
+    p, g, m, v = (np.asarray(a, np.float64) for a in (p, g, m, v))
+    m = beta1 * m + (1 - beta1) * g
+    v = beta2 * v + (1 - beta2) * g * g
+    mhat = m / (1 - beta1 ** step)
+    vhat = v / (1 - beta2 ** step)
+    return p - lr * mhat / (np.sqrt(vhat) + eps), m, v
+
+
+def adam_step_splats(raw, grads, state, lrs, step, beta1=0.9, beta2=0.999, eps=1e-15):
+    """Adam on the raw 3DGS parameters.  raw: dict means, log_scales, quats, opacity_logits, sh;
+    grads: dict w.r.t. the activated values (means, scales, quats, opacities, sh); the chain
+    through exp (scales) and the sigmoid (opacities) is applied here.  lrs: dict with keys
+    means, scales, quats, opacities, sh_dc, sh_rest.  Returns (raw', state')."""
+    scales = np.exp(np.asarray(raw["log_scales"], np.float64))
+    opac = 1.0 / (1.0 + np.exp(-np.asarray(raw["opacity_logits"], np.float64)))
+    g_raw = dict(means=grads["means"], log_scales=np.asarray(grads["scales"]) * scales,
+                 quats=grads["quats"], opacity_logits=np.asarray(grads["opacities"]) * opac * (1 - opac),
+                 sh=grads["sh"])
+    lr_of = dict(means=lrs["means"], log_scales=lrs["scales"], quats=lrs["quats"], opacity_logits=lrs["opacities"])
+    out, new_state = {}, {}
+    for k in ("means", "log_scales", "quats", "opacity_logits"):
+        out[k], m, v = adam_update(raw[k], g_raw[k], state["m_" + k], state["v_" + k], lr_of[k], step, beta1, beta2, eps)
+        new_state["m_" + k], new_state["v_" + k] = m, v
+    sh = np.asarray(raw["sh"], np.float64)
+    lr_sh = np.full(sh.shape, lrs["sh_rest"])
+    lr_sh[:, 0, :] = lrs["sh_dc"]
+    out["sh"], new_state["m_sh"], new_state["v_sh"] = adam_update(sh, g_raw["sh"], state["m_sh"], state["v_sh"],
+                                                                  lr_sh, step, beta1, beta2, eps)
+    return out, new_state

@@ -1,0 +1,249 @@
+// The C ABI of libdarb.so (declared in include/darb.h): argument validation, workspace
+// carving and kernel launches.  No entry point here allocates device memory.
+#include <cmath>
+
+#include "kernels.cuh"
+
+using namespace darb;
+
+namespace {
+
+bool valid_tile(int t) { return t == 8 || t == 16 || t == 32; }
+
+bool finitef(float x) { return std::isfinite(x); }
+
+bool valid_camera(const darb_camera *c) {
+    if (!c) return false;
+    if (c->width <= 0 || c->height <= 0 || c->width > 65536 || c->height > 65536) return false;
+    if (!(c->fx > 0.0f) || !(c->fy > 0.0f) || !finitef(c->fx) || !finitef(c->fy)) return false;
+    if (!finitef(c->cx) || !finitef(c->cy) || !(c->near_plane > 0.0f) || !finitef(c->near_plane)) return false;
+    for (int i = 0; i < 16; ++i)
+        if (!finitef(c->viewmat[i])) return false;
+    for (int i = 0; i < 3; ++i)
+        if (!finitef(c->bg[i])) return false;
+    return true;
+}
+
+bool valid_kernel(const darb_kernel_params *k) {
+    return k && k->kind >= 0 && k->kind < kNumKernels && k->psi > 0.0f && finitef(k->psi) && k->q_max > 0.0f &&
+           finitef(k->q_max);
+}
+
+bool valid_splats(const darb_splats *s) {
+    if (!s || s->n < 0 || s->sh_degree < 0 || s->sh_degree > 3) return false;
+    if (s->n == 0) return true;
+    const void *p[5] = {s->means, s->scales, s->quats, s->opacities, s->sh};
+    for (const void *q : p)
+        if (!q || !aligned16(q)) return false;
+    return true;
+}
+
+bool valid_projected(const darb_projected *o) {
+    if (!o) return false;
+    const void *p[8] = {o->depth, o->radius, o->tile_rect, o->mean2d, o->conic_o, o->rgb, o->clamped, o->tiles_touched};
+    for (const void *q : p)
+        if (!q || !aligned16(q)) return false;
+    return true;
+}
+
+// Compositing reads the projected records only through tile runs, so an empty scene (n = 0)
+// may pass NULL buffers; otherwise every buffer must be valid.
+bool valid_projected_or_empty(const darb_projected *o) {
+    if (!o) return false;
+    const void *p[8] = {o->depth, o->radius, o->tile_rect, o->mean2d, o->conic_o, o->rgb, o->clamped, o->tiles_touched};
+    bool all_null = true;
+    for (const void *q : p) all_null &= (q == nullptr);
+    return all_null || valid_projected(o);
+}
+
+ProjectedOut as_out(const darb_projected *o) {
+    ProjectedOut r;
+    r.depth = o->depth;
+    r.radius = o->radius;
+    r.tile_rect = reinterpret_cast<int4 *>(o->tile_rect);
+    r.mean2d = reinterpret_cast<float2 *>(o->mean2d);
+    r.conic_o = reinterpret_cast<float4 *>(o->conic_o);
+    r.rgb = o->rgb;
+    r.clamped = o->clamped;
+    r.tiles_touched = o->tiles_touched;
+    return r;
+}
+
+int tile_bits_for(const darb_camera *cam, int tile) {
+    const uint32_t n_tiles = (uint32_t)tile_count(cam->width, tile) * (uint32_t)tile_count(cam->height, tile);
+    return log2_ceil(n_tiles);
+}
+
+constexpr uint64_t kMaxCapacity = (1ull << 30) - 1;
+
+}  // namespace
+
+extern "C" {
+
+const char *darb_status_string(darb_status s) {
+    switch (s) {
+    case DARB_OK: return "ok";
+    case DARB_ERR_INVALID_ARG: return "invalid argument";
+    case DARB_ERR_WORKSPACE: return "workspace too small";
+    case DARB_ERR_CAPACITY: return "instance capacity exceeded";
+    case DARB_ERR_CUDA: return "CUDA error";
+    case DARB_ERR_TIMEOUT: return "device wait timed out";
+    case DARB_ERR_ADMISSION: return "request not admitted";
+    case DARB_ERR_NOT_FOUND: return "not found";
+    }
+    return "unknown status";
+}
+
+darb_status darb_kernel_defaults(int32_t kind, darb_kernel_params *out) {
+    // psi: Sec. B listings ("correctionFactor"), Table 2 for the inverse multiquadric and the
+    // Gaussian; q_max / strictness: the listings' main-lobe limits.
+    static const darb_kernel_params table[kNumKernels] = {
+        {DARB_GAUSSIAN, 1.0f, 9.0f, 0},     {DARB_HALF_COSINE, 1.36f, 9.0f, 0},
+        {DARB_RAISED_COSINE, 0.655f, 6.25f, 0}, {DARB_MOD_SINC, 1.18f, 9.0f, 0},
+        {DARB_INV_QUADRIC, 1.38f, 9.0f, 1}, {DARB_INV_MULTIQUADRIC, 1.61f, 9.0f, 1},
+        {DARB_PARABOLA, 1.3f, 9.0f, 0},
+    };
+    if (!out || kind < 0 || kind >= kNumKernels) return DARB_ERR_INVALID_ARG;
+    *out = table[kind];
+    return DARB_OK;
+}
+
+darb_status darb_tile_grid(const darb_camera *cam, int32_t tile, int32_t *tiles_x, int32_t *tiles_y) {
+    if (!valid_camera(cam) || !valid_tile(tile) || !tiles_x || !tiles_y) return DARB_ERR_INVALID_ARG;
+    *tiles_x = tile_count(cam->width, tile);
+    *tiles_y = tile_count(cam->height, tile);
+    return DARB_OK;
+}
+
+darb_status darb_preprocess(const darb_splats *splats, const darb_camera *cam, const darb_kernel_params *kparams,
+                            int32_t tile, const darb_projected *out, darb_stream stream) {
+    if (!valid_splats(splats) || !valid_camera(cam) || !valid_kernel(kparams) || !valid_tile(tile))
+        return DARB_ERR_INVALID_ARG;
+    if (splats->n == 0) return DARB_OK;
+    if (!valid_projected(out)) return DARB_ERR_INVALID_ARG;
+    DARB_CUDA_TRY(launch_preprocess(splats->n, *splats, make_cam(*cam), kparams->psi, tile, as_out(out),
+                                    reinterpret_cast<cudaStream_t>(stream)));
+    return DARB_OK;
+}
+
+darb_status darb_bin_sort_workspace_size(int32_t n, int32_t tile, const darb_camera *cam, uint64_t capacity,
+                                         size_t *bytes) {
+    if (n < 0 || !valid_tile(tile) || !valid_camera(cam) || !bytes || capacity > kMaxCapacity)
+        return DARB_ERR_INVALID_ARG;
+    const int passes = (32 + tile_bits_for(cam, tile) + 7) / 8;
+    *bytes = sort_workspace_bytes(n, capacity, passes);
+    return DARB_OK;
+}
+
+darb_status darb_bin_sort(const darb_projected *proj, int32_t n, int32_t tile, const darb_camera *cam,
+                          void *workspace, size_t workspace_bytes, uint64_t capacity, const darb_binning *out,
+                          uint64_t *num_instances_host, darb_stream stream) {
+    if (n < 0 || !valid_tile(tile) || !valid_camera(cam) || capacity > kMaxCapacity || !out) return DARB_ERR_INVALID_ARG;
+    if (!out->ranges || !out->num_instances || !out->status || !aligned16(out->ranges)) return DARB_ERR_INVALID_ARG;
+    if (capacity > 0 && (!out->keys || !out->values || !aligned16(out->keys) || !aligned16(out->values)))
+        return DARB_ERR_INVALID_ARG;
+    if (n > 0 && !valid_projected(proj)) return DARB_ERR_INVALID_ARG;
+    const int tile_bits = tile_bits_for(cam, tile);
+    const int passes = (32 + tile_bits + 7) / 8;
+    const size_t need = sort_workspace_bytes(n, capacity, passes);
+    if (!workspace || workspace_bytes < need || !aligned16(workspace)) return DARB_ERR_WORKSPACE;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int tiles_x = tile_count(cam->width, tile), tiles_y = tile_count(cam->height, tile);
+
+    void *base = reinterpret_cast<void *>((reinterpret_cast<uintptr_t>(workspace) + 255) & ~(uintptr_t)255);
+    const SortWorkspace ws = carve_sort_workspace(base, n, capacity, passes);
+    DARB_CUDA_TRY(cudaMemsetAsync(ws.hist, 0, ws.zero_bytes, st));
+    DARB_CUDA_TRY(cudaMemsetAsync(out->status, 0, sizeof(uint32_t), st));
+    DARB_CUDA_TRY(cudaMemsetAsync(out->ranges, 0, (size_t)tiles_x * tiles_y * 2 * sizeof(uint32_t), st));
+    DARB_CUDA_TRY(launch_count_instances(n, proj ? proj->tiles_touched : nullptr, ws, out->num_instances, out->status,
+                                         capacity, st));
+    uint64_t grid_instances = capacity;
+    if (num_instances_host) {
+        uint32_t M = 0;
+        DARB_CUDA_TRY(cudaMemcpyAsync(&M, out->num_instances, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+        DARB_CUDA_TRY(cudaStreamSynchronize(st));
+        *num_instances_host = M;
+        if (M > capacity) return DARB_ERR_CAPACITY;
+        grid_instances = M;
+    }
+    DARB_CUDA_TRY(launch_duplicate_and_sort(n, proj ? proj->tiles_touched : nullptr,
+                                            proj ? reinterpret_cast<const int4 *>(proj->tile_rect) : nullptr,
+                                            proj ? proj->depth : nullptr, tiles_x, tile_bits, capacity, grid_instances,
+                                            ws, out->keys, out->values, out->ranges, out->num_instances, out->status, st));
+    return DARB_OK;
+}
+
+darb_status darb_render_fwd(const darb_projected *proj, const darb_binning *bins, const darb_camera *cam,
+                            const darb_kernel_params *kparams, int32_t tile, const darb_image *out,
+                            darb_stream stream) {
+    if (!valid_projected_or_empty(proj) || !bins || !bins->ranges || !valid_camera(cam) || !valid_kernel(kparams) ||
+        !valid_tile(tile) || !out || !out->image || !out->t_final || !out->last || !out->n_contrib)
+        return DARB_ERR_INVALID_ARG;
+    const int tiles_x = tile_count(cam->width, tile), tiles_y = tile_count(cam->height, tile);
+    DARB_CUDA_TRY(launch_render_fwd(kparams->kind, tile, tiles_x, tiles_y, bins->ranges, bins->values,
+                                    reinterpret_cast<const float2 *>(proj->mean2d),
+                                    reinterpret_cast<const float4 *>(proj->conic_o), proj->rgb, make_cam(*cam),
+                                    kparams->q_max, kparams->q_max_strict ? 1 : 0, out->image, out->t_final, out->last,
+                                    out->n_contrib, reinterpret_cast<cudaStream_t>(stream)));
+    return DARB_OK;
+}
+
+darb_status darb_render_bwd(const darb_projected *proj, int32_t n, const darb_binning *bins, const darb_camera *cam,
+                            const darb_kernel_params *kparams, int32_t tile, const darb_image *fwd,
+                            const float *dL_dimage, float *grad2d, darb_stream stream) {
+    if (n < 0 || !valid_projected_or_empty(proj) || !bins || !bins->ranges || !valid_camera(cam) ||
+        !valid_kernel(kparams) || !valid_tile(tile) || !fwd || !fwd->t_final || !fwd->last || !dL_dimage ||
+        (n > 0 && (!grad2d || !aligned16(grad2d))))
+        return DARB_ERR_INVALID_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (n > 0) DARB_CUDA_TRY(cudaMemsetAsync(grad2d, 0, (size_t)n * 12 * sizeof(float), st));
+    const int tiles_x = tile_count(cam->width, tile), tiles_y = tile_count(cam->height, tile);
+    DARB_CUDA_TRY(launch_render_bwd(kparams->kind, tile, tiles_x, tiles_y, bins->ranges, bins->values,
+                                    reinterpret_cast<const float2 *>(proj->mean2d),
+                                    reinterpret_cast<const float4 *>(proj->conic_o), proj->rgb, make_cam(*cam),
+                                    kparams->q_max, kparams->q_max_strict ? 1 : 0, fwd->t_final, fwd->last, dL_dimage,
+                                    grad2d, st));
+    return DARB_OK;
+}
+
+darb_status darb_preprocess_bwd(const darb_splats *splats, const darb_camera *cam, const darb_kernel_params *kparams,
+                                const darb_projected *proj, const float *grad2d, const darb_splat_grads *out,
+                                darb_stream stream) {
+    if (!valid_splats(splats) || !valid_camera(cam) || !valid_kernel(kparams)) return DARB_ERR_INVALID_ARG;
+    if (splats->n == 0) return DARB_OK;
+    if (!valid_projected(proj) || !grad2d || !aligned16(grad2d) || !out || !out->dmeans || !out->dscales ||
+        !out->dquats || !out->dopacities || !out->dsh)
+        return DARB_ERR_INVALID_ARG;
+    GradOut g{out->dmeans, out->dscales, out->dquats, out->dopacities, out->dsh};
+    DARB_CUDA_TRY(launch_preprocess_bwd(splats->n, *splats, make_cam(*cam), kparams->psi, proj->radius, proj->clamped,
+                                        grad2d, g, reinterpret_cast<cudaStream_t>(stream)));
+    return DARB_OK;
+}
+
+darb_status darb_l1_loss(const float *image, const float *target, int32_t width, int32_t height, float *dL_dimage,
+                         float *loss, darb_stream stream) {
+    if (!image || !target || !dL_dimage || !loss || width <= 0 || height <= 0) return DARB_ERR_INVALID_ARG;
+    DARB_CUDA_TRY(launch_l1_loss(image, target, 3 * width * height, dL_dimage, loss,
+                                 reinterpret_cast<cudaStream_t>(stream)));
+    return DARB_OK;
+}
+
+darb_status darb_adam_step(const darb_train_params *params, const darb_splat_grads *grads,
+                           const darb_adam_state *state, const darb_adam_config *cfg, darb_stream stream) {
+    if (!params || !grads || !state || !cfg || params->n < 0 || params->sh_degree < 0 || params->sh_degree > 3 ||
+        cfg->step < 1 || !(cfg->beta1 >= 0.0f && cfg->beta1 < 1.0f) || !(cfg->beta2 >= 0.0f && cfg->beta2 < 1.0f) ||
+        !(cfg->eps > 0.0f))
+        return DARB_ERR_INVALID_ARG;
+    if (params->n == 0) return DARB_OK;
+    const void *p[] = {params->means, params->log_scales, params->quats, params->opacity_logits, params->sh,
+                       params->scales, params->opacities, grads->dmeans, grads->dscales, grads->dquats,
+                       grads->dopacities, grads->dsh, state->m_means, state->v_means, state->m_scales,
+                       state->v_scales, state->m_quats, state->v_quats, state->m_opac, state->v_opac,
+                       state->m_sh, state->v_sh};
+    for (const void *q : p)
+        if (!q) return DARB_ERR_INVALID_ARG;
+    DARB_CUDA_TRY(launch_adam(*params, *grads, *state, *cfg, reinterpret_cast<cudaStream_t>(stream)));
+    return DARB_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,152 @@
+// Shared device helpers of libdarb.so (GB300, sm_103a).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "darb.h"
+
+namespace darb {
+
+constexpr float kAlphaMax = 0.99f;          // 3DGS alpha clamp (listings: min(0.99f, ...))
+constexpr float kAlphaMin = 1.0f / 255.0f;  // 3DGS: skip alpha < 1/255
+constexpr float kTMin = 0.0001f;            // 3DGS: stop before T (1 - alpha) < 1e-4
+constexpr float kDilation = 0.3f;           // low-pass filter added to the 2D covariance
+constexpr float kGuardBand = 1.3f;          // Jacobian clamp at 1.3 tan(fov/2)
+constexpr float kPi = 3.14159265358979323846f;
+
+constexpr int kNumKernels = 7;
+
+// Camera as passed by value to kernels.
+struct Cam {
+    float V[16];
+    float fx, fy, cx, cy, near_plane;
+    int W, H;
+    float bg[3];
+    float campos[3];  // -R^T t, for the SH viewing direction
+};
+
+inline Cam make_cam(const darb_camera &c) {
+    Cam k;
+    for (int i = 0; i < 16; ++i) k.V[i] = c.viewmat[i];
+    k.fx = c.fx; k.fy = c.fy; k.cx = c.cx; k.cy = c.cy; k.near_plane = c.near_plane;
+    k.W = c.width; k.H = c.height;
+    for (int i = 0; i < 3; ++i) k.bg[i] = c.bg[i];
+    for (int j = 0; j < 3; ++j) {
+        double s = 0.0;
+        for (int r = 0; r < 3; ++r) s -= (double)c.viewmat[4 * r + j] * (double)c.viewmat[4 * r + 3];
+        k.campos[j] = (float)s;
+    }
+    return k;
+}
+
+// ---------------------------------------------------------------------------
+// Kernel profiles F(q) and dF/dq in FP32 (Table 1 with the xi of Table 2 in the
+// forms the Sec. B listings evaluate).  Main-lobe arguments are bounded, so the
+// accurate single-precision library functions are used.
+
+template <int K> __device__ __forceinline__ float kernel_F(float q);
+template <int K> __device__ __forceinline__ float kernel_dF(float q);
+
+// kernel_F uses explicit __f*_rn intrinsics so that its rounding never depends on how the
+// compiler contracts the surrounding code: forward and backward must get the same alpha.
+template <> __device__ __forceinline__ float kernel_F<DARB_GAUSSIAN>(float q) {
+    return expf(__fmul_rn(-0.5f, q));
+}
+template <> __device__ __forceinline__ float kernel_dF<DARB_GAUSSIAN>(float q) { return -0.5f * expf(-0.5f * q); }
+
+template <> __device__ __forceinline__ float kernel_F<DARB_HALF_COSINE>(float q) {
+    return cosf(__fmul_rn(q, kPi / 18.0f));
+}
+template <> __device__ __forceinline__ float kernel_dF<DARB_HALF_COSINE>(float q) {
+    return -(kPi / 18.0f) * sinf(q * (kPi / 18.0f));
+}
+
+template <> __device__ __forceinline__ float kernel_F<DARB_RAISED_COSINE>(float q) {
+    return __fmaf_rn(0.5f, cosf(__fmul_rn(__fsqrt_rn(q), kPi / 2.5f)), 0.5f);
+}
+template <> __device__ __forceinline__ float kernel_dF<DARB_RAISED_COSINE>(float q) {
+    // -(k/4) sin(k sqrt q) / sqrt q, k = pi/2.5; limit -k^2/4 at q = 0.
+    constexpr float k = kPi / 2.5f;
+    if (q < 1e-6f) return -0.25f * k * k + (k * k * k * k / 24.0f) * q;
+    const float r = sqrtf(q);
+    return -0.25f * k * sinf(k * r) / r;
+}
+
+template <> __device__ __forceinline__ float kernel_F<DARB_MOD_SINC>(float q) {
+    const float x = __fmul_rn(__fsqrt_rn(q), kPi / 3.0f);
+    if (x < 1e-2f) {  // sin x / x = 1 - x^2/6 + x^4/120
+        const float x2 = __fmul_rn(x, x);
+        return __fmaf_rn(x2, __fmaf_rn(x2, 1.0f / 120.0f, -1.0f / 6.0f), 1.0f);
+    }
+    return __fdiv_rn(fabsf(sinf(x)), x);
+}
+template <> __device__ __forceinline__ float kernel_dF<DARB_MOD_SINC>(float q) {
+    // (x cos x - sin x) / (2 q x), x = pi sqrt(q)/3; series below x = 0.3.
+    const float x = sqrtf(q) * (kPi / 3.0f);
+    if (x < 0.3f) {
+        constexpr float a = kPi * kPi / 9.0f;  // x^2 = a q
+        return -a / 6.0f + (a * a / 60.0f) * q - (a * a * a / 1680.0f) * q * q +
+               (a * a * a * a / 90720.0f) * q * q * q;
+    }
+    float s, c;
+    sincosf(x, &s, &c);
+    return (x * c - s) / (2.0f * q * x);
+}
+
+template <> __device__ __forceinline__ float kernel_F<DARB_INV_QUADRIC>(float q) {
+    return __fdiv_rn(1.0f, __fadd_rn(1.0f, q));
+}
+template <> __device__ __forceinline__ float kernel_dF<DARB_INV_QUADRIC>(float q) {
+    const float r = 1.0f / (1.0f + q);
+    return -r * r;
+}
+
+template <> __device__ __forceinline__ float kernel_F<DARB_INV_MULTIQUADRIC>(float q) {
+    return rsqrtf(__fadd_rn(1.0f, q));
+}
+template <> __device__ __forceinline__ float kernel_dF<DARB_INV_MULTIQUADRIC>(float q) {
+    const float r = rsqrtf(1.0f + q);
+    return -0.5f * r * r * r;
+}
+
+template <> __device__ __forceinline__ float kernel_F<DARB_PARABOLA>(float q) {
+    return __fmaf_rn(q, -1.0f / 9.0f, 1.0f);
+}
+template <> __device__ __forceinline__ float kernel_dF<DARB_PARABOLA>(float) { return -1.0f / 9.0f; }
+
+// The support test on q: 0 <= q <= q_max (q < q_max when strict).
+__device__ __forceinline__ bool in_support(float q, float qmax, bool strict) {
+    return q >= 0.0f && (strict ? q < qmax : q <= qmax);
+}
+
+// q = dx (A dx + 2B dy) + (C dy) dy as a fixed FP32 sequence (no contraction beyond the
+// two explicit fused multiply-adds), shared by forward and backward so both take the
+// same support decision.  B2 = 2B (exact).
+__device__ __forceinline__ float conic_q(float dx, float dy, float A, float B2, float C) {
+    const float e = __fmul_rn(B2, dy);
+    const float g = __fmaf_rn(A, dx, e);
+    const float h = __fmul_rn(__fmul_rn(C, dy), dy);
+    return __fmaf_rn(dx, g, h);
+}
+
+// ---------------------------------------------------------------------------
+// Host-side helpers.
+
+#define DARB_CUDA_TRY(expr)                                   \
+    do {                                                      \
+        cudaError_t _e = (expr);                              \
+        if (_e != cudaSuccess) return DARB_ERR_CUDA;          \
+    } while (0)
+
+inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+inline int tile_count(int extent, int tile) { return (extent + tile - 1) / tile; }
+
+inline int log2_ceil(uint32_t v) {
+    int b = 0;
+    while ((1ull << b) < v) ++b;
+    return b;
+}
+
+}  // namespace darb

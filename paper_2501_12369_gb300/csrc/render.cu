@@ -1,0 +1,327 @@
+// Step 4 and its backward: per-pixel front-to-back compositing over each tile's depth-sorted
+// splat run (paper Sec. 4.1 "alpha blending ... similar to 3DGS", Eq. HalfCosine and
+// Eq. 2DSplattedFunction; forward and backward listings of Sec. B).
+//
+// One CTA per tile, one thread per pixel.  The tile's run is consumed in batches of
+// TILE*TILE splats: each thread gathers one splat's record (mean, conic, opacity, colour)
+// into shared memory, then every thread walks the batch.  A CTA-wide vote ends the loop once
+// every pixel of the tile has stopped (T < 1e-4) -- the early termination of 3DGS.
+//
+// The support test uses the fixed FP32 sequence conic_q(), and alpha / the kernel value are
+// computed by the same inline code in forward and backward, so the backward re-takes exactly
+// the forward's decisions when it replays a pixel from its last contributor.
+#include "kernels.cuh"
+
+namespace darb {
+
+namespace {
+
+struct Bg {
+    float r, g, b;
+};
+
+template <int KIND, int TILE>
+__global__ void __launch_bounds__(TILE *TILE)
+k_render_fwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ values,
+             const float2 *__restrict__ mean2d, const float4 *__restrict__ conic_o,
+             const float *__restrict__ rgb, int W, int H, int tiles_x, float qmax, int strict, Bg bg,
+             float *__restrict__ image, float *__restrict__ t_final, uint32_t *__restrict__ last,
+             uint32_t *__restrict__ n_contrib) {
+    constexpr int NT = TILE * TILE;
+    constexpr int BATCH = NT < 256 ? NT : 256;
+    __shared__ float2 s_xy[BATCH];
+    __shared__ float4 s_co[BATCH];  // A, 2B, C, opacity
+    __shared__ float s_rgb[BATCH][3];
+
+    const int tile = blockIdx.x;
+    const int tx = tile % tiles_x, ty = tile / tiles_x;
+    const int px = tx * TILE + (threadIdx.x % TILE), py = ty * TILE + (threadIdx.x / TILE);
+    const bool inside = px < W && py < H;
+    const float fpx = (float)px + 0.5f, fpy = (float)py + 0.5f;
+    const uint2 r = ranges[tile];
+    const int start = (int)r.x, end = (int)r.y;
+
+    float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
+    uint32_t count = 0, lastp = 0;
+    bool done = !inside;
+    for (int b0 = start; b0 < end; b0 += BATCH) {
+        if (__syncthreads_count(done) == NT) break;
+        const int idx = b0 + (int)threadIdx.x;
+        if ((int)threadIdx.x < BATCH && idx < end) {
+            const uint32_t id = values[idx];
+            s_xy[threadIdx.x] = mean2d[id];
+            float4 co = conic_o[id];
+            co.y = 2.0f * co.y;
+            s_co[threadIdx.x] = co;
+            s_rgb[threadIdx.x][0] = rgb[3 * (size_t)id];
+            s_rgb[threadIdx.x][1] = rgb[3 * (size_t)id + 1];
+            s_rgb[threadIdx.x][2] = rgb[3 * (size_t)id + 2];
+        }
+        __syncthreads();
+        const int nb = min(BATCH, end - b0);
+        for (int j = 0; j < nb && !done; ++j) {
+            const float2 xy = s_xy[j];
+            const float4 co = s_co[j];
+            const float dx = __fsub_rn(xy.x, fpx), dy = __fsub_rn(xy.y, fpy);
+            const float q = conic_q(dx, dy, co.x, co.y, co.z);
+            if (!in_support(q, qmax, strict)) continue;
+            const float alpha = fminf(kAlphaMax, __fmul_rn(co.w, kernel_F<KIND>(q)));
+            if (alpha < kAlphaMin) continue;
+            const float Tn = T * (1.0f - alpha);
+            if (Tn < kTMin) {
+                done = true;
+                break;
+            }
+            const float w = alpha * T;
+            C0 = fmaf(s_rgb[j][0], w, C0);
+            C1 = fmaf(s_rgb[j][1], w, C1);
+            C2 = fmaf(s_rgb[j][2], w, C2);
+            T = Tn;
+            ++count;
+            lastp = (uint32_t)(b0 - start + j + 1);
+        }
+    }
+    if (inside) {
+        const size_t pix = (size_t)py * W + px, plane = (size_t)W * H;
+        image[pix] = fmaf(T, bg.r, C0);
+        image[plane + pix] = fmaf(T, bg.g, C1);
+        image[2 * plane + pix] = fmaf(T, bg.b, C2);
+        t_final[pix] = T;
+        last[pix] = lastp;
+        n_contrib[pix] = count;
+    }
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+// Backward: replay each pixel back to front from its last contributor.  With T_k the
+// transmittance in front of splat k and S the colour composited behind it (background
+// included), dC/dalpha_k = c_k T_k - S / (1 - alpha_k) and dC/dc_k = alpha_k T_k.
+// Per splat and tile the contributions are summed by warp shuffles, then across warps in
+// shared memory, then added to grad2d with one vector atomic per 4 floats.
+template <int KIND, int TILE>
+__global__ void __launch_bounds__(TILE *TILE)
+k_render_bwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ values,
+             const float2 *__restrict__ mean2d, const float4 *__restrict__ conic_o,
+             const float *__restrict__ rgb, int W, int H, int tiles_x, float qmax, int strict, Bg bg,
+             const float *__restrict__ t_final, const uint32_t *__restrict__ last,
+             const float *__restrict__ dL_dimage, float4 *__restrict__ grad2d) {
+    constexpr int NT = TILE * TILE;
+    constexpr int NW = NT / 32;
+    constexpr int BATCH = NT < 256 ? NT : 256;
+    __shared__ float2 s_xy[BATCH];
+    __shared__ float4 s_co[BATCH];
+    __shared__ float s_rgb[BATCH][3];
+    __shared__ uint32_t s_id[BATCH];
+    __shared__ float s_acc[BATCH][9];
+    __shared__ uint32_t s_max[NW];
+
+    const int tile = blockIdx.x;
+    const int tx = tile % tiles_x, ty = tile / tiles_x;
+    const int px = tx * TILE + (threadIdx.x % TILE), py = ty * TILE + (threadIdx.x / TILE);
+    const bool inside = px < W && py < H;
+    const float fpx = (float)px + 0.5f, fpy = (float)py + 0.5f;
+    const uint2 r = ranges[tile];
+    const int start = (int)r.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+    float T = 1.0f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
+    uint32_t my_last = 0;
+    if (inside) {
+        const size_t pix = (size_t)py * W + px, plane = (size_t)W * H;
+        T = t_final[pix];
+        my_last = last[pix];
+        g0 = dL_dimage[pix];
+        g1 = dL_dimage[plane + pix];
+        g2 = dL_dimage[2 * plane + pix];
+    }
+    float S0 = T * bg.r, S1 = T * bg.g, S2 = T * bg.b;
+
+    uint32_t m = my_last;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if (lane == 0) s_max[warp] = m;
+    for (int i = threadIdx.x; i < BATCH * 9; i += NT) (&s_acc[0][0])[i] = 0.0f;
+    __syncthreads();
+    int nlast = 0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) nlast = max(nlast, (int)s_max[w]);
+
+    for (int bend = nlast; bend > 0; bend -= BATCH) {
+        const int bstart = max(0, bend - BATCH);
+        const int cnt = bend - bstart;
+        if ((int)threadIdx.x < cnt) {
+            const uint32_t id = values[start + bstart + threadIdx.x];
+            s_id[threadIdx.x] = id;
+            s_xy[threadIdx.x] = mean2d[id];
+            float4 co = conic_o[id];
+            co.y = 2.0f * co.y;
+            s_co[threadIdx.x] = co;
+            s_rgb[threadIdx.x][0] = rgb[3 * (size_t)id];
+            s_rgb[threadIdx.x][1] = rgb[3 * (size_t)id + 1];
+            s_rgb[threadIdx.x][2] = rgb[3 * (size_t)id + 2];
+        }
+        __syncthreads();
+        for (int j = cnt - 1; j >= 0; --j) {
+            const int pos = bstart + j;
+            float v[9];
+#pragma unroll
+            for (int u = 0; u < 9; ++u) v[u] = 0.0f;
+            bool contrib = false;
+            if (pos < (int)my_last) {
+                const float2 xy = s_xy[j];
+                const float4 co = s_co[j];
+                const float dx = __fsub_rn(xy.x, fpx), dy = __fsub_rn(xy.y, fpy);
+                const float q = conic_q(dx, dy, co.x, co.y, co.z);
+                if (in_support(q, qmax, strict)) {
+                    const float F = kernel_F<KIND>(q);
+                    const float of = __fmul_rn(co.w, F);
+                    const float alpha = fminf(kAlphaMax, of);
+                    if (alpha >= kAlphaMin) {
+                        contrib = true;
+                        const float om = 1.0f - alpha;
+                        const float Tk = T / om;
+                        const float c0 = s_rgb[j][0], c1 = s_rgb[j][1], c2 = s_rgb[j][2];
+                        const float dalpha = g0 * (c0 * Tk - S0 / om) + g1 * (c1 * Tk - S1 / om) + g2 * (c2 * Tk - S2 / om);
+                        const float w = alpha * Tk;
+                        S0 = fmaf(c0, w, S0);
+                        S1 = fmaf(c1, w, S1);
+                        S2 = fmaf(c2, w, S2);
+                        T = Tk;
+                        v[6] = w * g0;
+                        v[7] = w * g1;
+                        v[8] = w * g2;
+                        if (!(of > kAlphaMax)) {
+                            v[5] = F * dalpha;
+                            const float dq = co.w * kernel_dF<KIND>(q) * dalpha;
+                            const float B = 0.5f * co.y;
+                            v[0] = 2.0f * dq * (co.x * dx + B * dy);
+                            v[1] = 2.0f * dq * (B * dx + co.z * dy);
+                            v[2] = dq * dx * dx;
+                            v[3] = 2.0f * dq * dx * dy;
+                            v[4] = dq * dy * dy;
+                        }
+                    }
+                }
+            }
+            if (__any_sync(0xffffffffu, contrib)) {
+#pragma unroll
+                for (int u = 0; u < 9; ++u) v[u] = warp_sum(v[u]);
+                if (lane == 0) {
+#pragma unroll
+                    for (int u = 0; u < 9; ++u) atomicAdd(&s_acc[j][u], v[u]);
+                }
+            }
+        }
+        __syncthreads();
+        if ((int)threadIdx.x < cnt) {
+            float *a = s_acc[threadIdx.x];
+            bool any = false;
+#pragma unroll
+            for (int u = 0; u < 9; ++u) any |= a[u] != 0.0f;
+            if (any) {
+                float4 *gp = grad2d + 3 * (size_t)s_id[threadIdx.x];
+                atomicAdd(gp, make_float4(a[0], a[1], a[2], a[3]));
+                atomicAdd(gp + 1, make_float4(a[4], a[5], a[6], a[7]));
+                atomicAdd(reinterpret_cast<float *>(gp + 2), a[8]);
+            }
+#pragma unroll
+            for (int u = 0; u < 9; ++u) a[u] = 0.0f;
+        }
+        __syncthreads();
+    }
+}
+
+template <int KIND, int TILE>
+cudaError_t fwd_t(int n_tiles, const uint2 *ranges, const uint32_t *values, const float2 *mean2d,
+                  const float4 *conic_o, const float *rgb, const Cam &cam, int tiles_x, float qmax, int strict,
+                  float *image, float *t_final, uint32_t *last, uint32_t *n_contrib, cudaStream_t st) {
+    k_render_fwd<KIND, TILE><<<n_tiles, TILE * TILE, 0, st>>>(ranges, values, mean2d, conic_o, rgb, cam.W, cam.H, tiles_x,
+                                                               qmax, strict, Bg{cam.bg[0], cam.bg[1], cam.bg[2]}, image,
+                                                               t_final, last, n_contrib);
+    return cudaGetLastError();
+}
+
+template <int KIND, int TILE>
+cudaError_t bwd_t(int n_tiles, const uint2 *ranges, const uint32_t *values, const float2 *mean2d,
+                  const float4 *conic_o, const float *rgb, const Cam &cam, int tiles_x, float qmax, int strict,
+                  const float *t_final, const uint32_t *last, const float *dL, float *grad2d, cudaStream_t st) {
+    k_render_bwd<KIND, TILE><<<n_tiles, TILE * TILE, 0, st>>>(ranges, values, mean2d, conic_o, rgb, cam.W, cam.H, tiles_x,
+                                                               qmax, strict, Bg{cam.bg[0], cam.bg[1], cam.bg[2]}, t_final,
+                                                               last, dL, reinterpret_cast<float4 *>(grad2d));
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_render_fwd(int kind, int tile, int tiles_x, int tiles_y, const uint32_t *ranges,
+                              const uint32_t *values, const float2 *mean2d, const float4 *conic_o,
+                              const float *rgb, const Cam &cam, float qmax, int strict,
+                              float *image, float *t_final, uint32_t *last, uint32_t *n_contrib,
+                              cudaStream_t st) {
+    const int n_tiles = tiles_x * tiles_y;
+    if (n_tiles == 0) return cudaSuccess;
+    const uint2 *rg = reinterpret_cast<const uint2 *>(ranges);
+#define FWD_ARGS (n_tiles, rg, values, mean2d, conic_o, rgb, cam, tiles_x, qmax, strict, image, t_final, last, n_contrib, st)
+#define FWD_CALL(K, T) fwd_t<K, T> FWD_ARGS
+    if (tile == 8) {
+        switch (kind) {
+        case 0: return FWD_CALL(0, 8); case 1: return FWD_CALL(1, 8); case 2: return FWD_CALL(2, 8);
+        case 3: return FWD_CALL(3, 8); case 4: return FWD_CALL(4, 8); case 5: return FWD_CALL(5, 8);
+        default: return FWD_CALL(6, 8);
+        }
+    } else if (tile == 16) {
+        switch (kind) {
+        case 0: return FWD_CALL(0, 16); case 1: return FWD_CALL(1, 16); case 2: return FWD_CALL(2, 16);
+        case 3: return FWD_CALL(3, 16); case 4: return FWD_CALL(4, 16); case 5: return FWD_CALL(5, 16);
+        default: return FWD_CALL(6, 16);
+        }
+    } else {
+        switch (kind) {
+        case 0: return FWD_CALL(0, 32); case 1: return FWD_CALL(1, 32); case 2: return FWD_CALL(2, 32);
+        case 3: return FWD_CALL(3, 32); case 4: return FWD_CALL(4, 32); case 5: return FWD_CALL(5, 32);
+        default: return FWD_CALL(6, 32);
+        }
+    }
+#undef FWD_CALL
+#undef FWD_ARGS
+}
+
+cudaError_t launch_render_bwd(int kind, int tile, int tiles_x, int tiles_y, const uint32_t *ranges,
+                              const uint32_t *values, const float2 *mean2d, const float4 *conic_o,
+                              const float *rgb, const Cam &cam, float qmax, int strict,
+                              const float *t_final, const uint32_t *last, const float *dL_dimage,
+                              float *grad2d, cudaStream_t st) {
+    const int n_tiles = tiles_x * tiles_y;
+    if (n_tiles == 0) return cudaSuccess;
+    const uint2 *rg = reinterpret_cast<const uint2 *>(ranges);
+#define BWD_ARGS (n_tiles, rg, values, mean2d, conic_o, rgb, cam, tiles_x, qmax, strict, t_final, last, dL_dimage, grad2d, st)
+#define BWD_CALL(K, T) bwd_t<K, T> BWD_ARGS
+    if (tile == 8) {
+        switch (kind) {
+        case 0: return BWD_CALL(0, 8); case 1: return BWD_CALL(1, 8); case 2: return BWD_CALL(2, 8);
+        case 3: return BWD_CALL(3, 8); case 4: return BWD_CALL(4, 8); case 5: return BWD_CALL(5, 8);
+        default: return BWD_CALL(6, 8);
+        }
+    } else if (tile == 16) {
+        switch (kind) {
+        case 0: return BWD_CALL(0, 16); case 1: return BWD_CALL(1, 16); case 2: return BWD_CALL(2, 16);
+        case 3: return BWD_CALL(3, 16); case 4: return BWD_CALL(4, 16); case 5: return BWD_CALL(5, 16);
+        default: return BWD_CALL(6, 16);
+        }
+    } else {
+        switch (kind) {
+        case 0: return BWD_CALL(0, 32); case 1: return BWD_CALL(1, 32); case 2: return BWD_CALL(2, 32);
+        case 3: return BWD_CALL(3, 32); case 4: return BWD_CALL(4, 32); case 5: return BWD_CALL(5, 32);
+        default: return BWD_CALL(6, 32);
+        }
+    }
+#undef BWD_CALL
+#undef BWD_ARGS
+}
+
+}  // namespace darb

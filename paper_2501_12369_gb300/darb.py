@@ -1,0 +1,423 @@
+"""Python binding of libdarb.so (include/darb.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls, takes torch CUDA tensors
+(PyTorch provides device memory and the current stream) and performs no arithmetic of the
+method itself.  If libdarb.so is missing the import of the library raises: there is no
+CPU or PyTorch fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+import threading
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+c_f32 = ctypes.c_float
+c_i32 = ctypes.c_int32
+c_vp = ctypes.c_void_p
+
+KERNEL_NAMES = ["gaussian", "half_cosine", "raised_cosine", "mod_sinc", "inv_quadric", "inv_multiquadric", "parabola"]
+STATUS_NAMES = {0: "DARB_OK", 1: "DARB_ERR_INVALID_ARG", 2: "DARB_ERR_WORKSPACE", 3: "DARB_ERR_CAPACITY",
+                4: "DARB_ERR_CUDA", 5: "DARB_ERR_TIMEOUT", 6: "DARB_ERR_ADMISSION", 7: "DARB_ERR_NOT_FOUND"}
+
+
+class darb_kernel_params(ctypes.Structure):
+    _fields_ = [("kind", c_i32), ("psi", c_f32), ("q_max", c_f32), ("q_max_strict", c_i32)]
+
+
+class darb_camera(ctypes.Structure):
+    _fields_ = [("viewmat", c_f32 * 16), ("fx", c_f32), ("fy", c_f32), ("cx", c_f32), ("cy", c_f32),
+                ("near_plane", c_f32), ("width", c_i32), ("height", c_i32), ("bg", c_f32 * 3)]
+
+
+class darb_splats(ctypes.Structure):
+    _fields_ = [("means", c_vp), ("scales", c_vp), ("quats", c_vp), ("opacities", c_vp), ("sh", c_vp),
+                ("n", c_i32), ("sh_degree", c_i32)]
+
+
+class darb_projected(ctypes.Structure):
+    _fields_ = [("depth", c_vp), ("radius", c_vp), ("tile_rect", c_vp), ("mean2d", c_vp), ("conic_o", c_vp),
+                ("rgb", c_vp), ("clamped", c_vp), ("tiles_touched", c_vp)]
+
+
+class darb_binning(ctypes.Structure):
+    _fields_ = [("keys", c_vp), ("values", c_vp), ("ranges", c_vp), ("num_instances", c_vp), ("status", c_vp)]
+
+
+class darb_image(ctypes.Structure):
+    _fields_ = [("image", c_vp), ("t_final", c_vp), ("last", c_vp), ("n_contrib", c_vp)]
+
+
+class darb_splat_grads(ctypes.Structure):
+    _fields_ = [("dmeans", c_vp), ("dscales", c_vp), ("dquats", c_vp), ("dopacities", c_vp), ("dsh", c_vp)]
+
+
+class darb_train_params(ctypes.Structure):
+    _fields_ = [("means", c_vp), ("log_scales", c_vp), ("quats", c_vp), ("opacity_logits", c_vp), ("sh", c_vp),
+                ("scales", c_vp), ("opacities", c_vp), ("n", c_i32), ("sh_degree", c_i32)]
+
+
+class darb_adam_state(ctypes.Structure):
+    _fields_ = [(f, c_vp) for f in ("m_means", "v_means", "m_scales", "v_scales", "m_quats", "v_quats",
+                                    "m_opac", "v_opac", "m_sh", "v_sh")]
+
+
+class darb_adam_config(ctypes.Structure):
+    _fields_ = [("lr_means", c_f32), ("lr_scales", c_f32), ("lr_quats", c_f32), ("lr_opacities", c_f32),
+                ("lr_sh_dc", c_f32), ("lr_sh_rest", c_f32), ("beta1", c_f32), ("beta2", c_f32), ("eps", c_f32),
+                ("step", c_i32)]
+
+
+# Every entry point declared in include/darb.h, with its ctypes signature.
+_P = ctypes.POINTER
+SIGNATURES = {
+    "darb_status_string": (ctypes.c_char_p, [c_i32]),
+    "darb_kernel_defaults": (c_i32, [c_i32, _P(darb_kernel_params)]),
+    "darb_tile_grid": (c_i32, [_P(darb_camera), c_i32, _P(c_i32), _P(c_i32)]),
+    "darb_preprocess": (c_i32, [_P(darb_splats), _P(darb_camera), _P(darb_kernel_params), c_i32,
+                                _P(darb_projected), c_vp]),
+    "darb_bin_sort_workspace_size": (c_i32, [c_i32, c_i32, _P(darb_camera), ctypes.c_uint64,
+                                             _P(ctypes.c_size_t)]),
+    "darb_bin_sort": (c_i32, [_P(darb_projected), c_i32, c_i32, _P(darb_camera), c_vp, ctypes.c_size_t,
+                              ctypes.c_uint64, _P(darb_binning), _P(ctypes.c_uint64), c_vp]),
+    "darb_render_fwd": (c_i32, [_P(darb_projected), _P(darb_binning), _P(darb_camera), _P(darb_kernel_params),
+                                c_i32, _P(darb_image), c_vp]),
+    "darb_render_bwd": (c_i32, [_P(darb_projected), c_i32, _P(darb_binning), _P(darb_camera),
+                                _P(darb_kernel_params), c_i32, _P(darb_image), c_vp, c_vp, c_vp]),
+    "darb_preprocess_bwd": (c_i32, [_P(darb_splats), _P(darb_camera), _P(darb_kernel_params), _P(darb_projected),
+                                    c_vp, _P(darb_splat_grads), c_vp]),
+    "darb_l1_loss": (c_i32, [c_vp, c_vp, c_i32, c_i32, c_vp, c_vp, c_vp]),
+    "darb_adam_step": (c_i32, [_P(darb_train_params), _P(darb_splat_grads), _P(darb_adam_state),
+                               _P(darb_adam_config), c_vp]),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB_PATH
+
+
+def lib() -> ctypes.CDLL:
+    """Load libdarb.so (built in-tree by paper_2501_12369_gb300.build).  Raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = library_path()
+            if not os.path.exists(path):
+                raise RuntimeError(f"libdarb.so not found at {path}; build it with paper_2501_12369_gb300.build.build()")
+            L = ctypes.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+class DarbError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}")
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise DarbError(status, where)
+
+
+def _p(t):
+    return None if t is None else c_vp(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return c_vp(s.cuda_stream)
+
+
+# ---------------------------------------------------------------------------
+# Host structs
+
+def kernel_index(kernel) -> int:
+    return KERNEL_NAMES.index(kernel) if isinstance(kernel, str) else int(kernel)
+
+
+def darb_kernel_defaults(kernel) -> darb_kernel_params:
+    kp = darb_kernel_params()
+    _check(lib().darb_kernel_defaults(kernel_index(kernel), ctypes.byref(kp)), "darb_kernel_defaults")
+    return kp
+
+
+def camera(cam) -> darb_camera:
+    """darb_camera from any object with viewmat, fx, fy, cx, cy, near, width, height, bg."""
+    c = darb_camera()
+    c.viewmat[:] = [float(v) for v in np.asarray(cam.viewmat, np.float32).reshape(16)]
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    c.near_plane = float(cam.near)
+    c.width, c.height = int(cam.width), int(cam.height)
+    c.bg[:] = [float(b) for b in cam.bg]
+    return c
+
+
+def darb_tile_grid(cam, tile):
+    tx, ty = c_i32(), c_i32()
+    _check(lib().darb_tile_grid(ctypes.byref(camera(cam)), int(tile), ctypes.byref(tx), ctypes.byref(ty)),
+           "darb_tile_grid")
+    return tx.value, ty.value
+
+
+@dataclasses.dataclass
+class SplatTensors:
+    means: torch.Tensor
+    scales: torch.Tensor
+    quats: torch.Tensor
+    opacities: torch.Tensor
+    sh: torch.Tensor
+    sh_degree: int
+
+    @property
+    def n(self):
+        return int(self.means.shape[0])
+
+    def struct(self) -> darb_splats:
+        for t in (self.means, self.scales, self.quats, self.opacities, self.sh):
+            assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()
+        return darb_splats(_p(self.means), _p(self.scales), _p(self.quats), _p(self.opacities), _p(self.sh),
+                           self.n, int(self.sh_degree))
+
+
+def splats_to_device(s, device="cuda") -> SplatTensors:
+    """Copy a synth.Splats (numpy) to the device."""
+    t = [torch.from_numpy(np.ascontiguousarray(a)).to(device) for a in (s.means, s.scales, s.quats, s.opacities, s.sh)]
+    return SplatTensors(*t, s.sh_degree)
+
+
+@dataclasses.dataclass
+class Projected:
+    depth: torch.Tensor
+    radius: torch.Tensor
+    tile_rect: torch.Tensor
+    mean2d: torch.Tensor
+    conic_o: torch.Tensor
+    rgb: torch.Tensor
+    clamped: torch.Tensor
+    tiles_touched: torch.Tensor
+
+    @staticmethod
+    def empty(n, device="cuda"):
+        f = dict(device=device)
+        return Projected(torch.empty(n, dtype=torch.float32, **f), torch.empty(n, dtype=torch.int32, **f),
+                         torch.empty(n, 4, dtype=torch.int32, **f), torch.empty(n, 2, dtype=torch.float32, **f),
+                         torch.empty(n, 4, dtype=torch.float32, **f), torch.empty(n, 3, dtype=torch.float32, **f),
+                         torch.empty(n, dtype=torch.uint8, **f), torch.empty(n, dtype=torch.int32, **f))
+
+    def struct(self) -> darb_projected:
+        return darb_projected(*(_p(getattr(self, f.name)) for f in dataclasses.fields(self)))
+
+
+@dataclasses.dataclass
+class Binning:
+    keys: torch.Tensor
+    values: torch.Tensor
+    ranges: torch.Tensor
+    num_instances: torch.Tensor
+    status: torch.Tensor
+    M: int | None = None
+
+    @staticmethod
+    def empty(capacity, n_tiles, device="cuda"):
+        f = dict(device=device)
+        cap = max(int(capacity), 1)
+        return Binning(torch.empty(cap, dtype=torch.int64, **f), torch.empty(cap, dtype=torch.int32, **f),
+                       torch.empty(n_tiles, 2, dtype=torch.int32, **f), torch.zeros(1, dtype=torch.int32, **f),
+                       torch.zeros(1, dtype=torch.int32, **f))
+
+    def struct(self) -> darb_binning:
+        return darb_binning(_p(self.keys), _p(self.values), _p(self.ranges), _p(self.num_instances), _p(self.status))
+
+
+@dataclasses.dataclass
+class ImageOut:
+    image: torch.Tensor
+    t_final: torch.Tensor
+    last: torch.Tensor
+    n_contrib: torch.Tensor
+
+    @staticmethod
+    def empty(width, height, device="cuda"):
+        f = dict(device=device)
+        return ImageOut(torch.empty(3, height, width, dtype=torch.float32, **f),
+                        torch.empty(height, width, dtype=torch.float32, **f),
+                        torch.empty(height, width, dtype=torch.int32, **f),
+                        torch.empty(height, width, dtype=torch.int32, **f))
+
+    def struct(self) -> darb_image:
+        return darb_image(_p(self.image), _p(self.t_final), _p(self.last), _p(self.n_contrib))
+
+
+# ---------------------------------------------------------------------------
+# Entry points
+
+def darb_preprocess(splats: SplatTensors, cam, kparams, tile=16, out: Projected | None = None, stream=None):
+    out = Projected.empty(splats.n, splats.means.device) if out is None else out
+    sp, c, o = splats.struct(), camera(cam), out.struct()
+    _check(lib().darb_preprocess(ctypes.byref(sp), ctypes.byref(c), ctypes.byref(kparams), int(tile), ctypes.byref(o),
+                                 _stream(stream)), "darb_preprocess")
+    return out
+
+
+def darb_bin_sort_workspace_size(n, tile, cam, capacity) -> int:
+    b = ctypes.c_size_t()
+    _check(lib().darb_bin_sort_workspace_size(int(n), int(tile), ctypes.byref(camera(cam)), int(capacity),
+                                              ctypes.byref(b)), "darb_bin_sort_workspace_size")
+    return int(b.value)
+
+
+def darb_bin_sort(proj: Projected, n, tile, cam, workspace: torch.Tensor, capacity, out: Binning | None = None,
+                  sync=True, stream=None):
+    """sync=True reads M back (one stream synchronisation) and sizes the sort by it."""
+    tx, ty = darb_tile_grid(cam, tile)
+    out = Binning.empty(capacity, tx * ty, workspace.device) if out is None else out
+    pr, c, b = proj.struct(), camera(cam), out.struct()
+    m = ctypes.c_uint64(0)
+    st = lib().darb_bin_sort(ctypes.byref(pr), int(n), int(tile), ctypes.byref(c), _p(workspace),
+                             workspace.numel() * workspace.element_size(), int(capacity), ctypes.byref(b),
+                             ctypes.byref(m) if sync else None, _stream(stream))
+    out.M = int(m.value) if sync else None
+    _check(st, "darb_bin_sort")
+    return out
+
+
+def darb_render_fwd(proj: Projected, bins: Binning, cam, kparams, tile=16, out: ImageOut | None = None, stream=None):
+    out = ImageOut.empty(cam.width, cam.height, proj.depth.device) if out is None else out
+    pr, b, c, o = proj.struct(), bins.struct(), camera(cam), out.struct()
+    _check(lib().darb_render_fwd(ctypes.byref(pr), ctypes.byref(b), ctypes.byref(c), ctypes.byref(kparams), int(tile),
+                                 ctypes.byref(o), _stream(stream)), "darb_render_fwd")
+    return out
+
+
+def darb_render_bwd(proj: Projected, n, bins: Binning, cam, kparams, tile, fwd: ImageOut, dL_dimage: torch.Tensor,
+                    grad2d: torch.Tensor | None = None, stream=None):
+    grad2d = torch.empty(n, 12, dtype=torch.float32, device=proj.depth.device) if grad2d is None else grad2d
+    assert dL_dimage.is_contiguous() and dL_dimage.dtype == torch.float32
+    pr, b, c, f = proj.struct(), bins.struct(), camera(cam), fwd.struct()
+    _check(lib().darb_render_bwd(ctypes.byref(pr), int(n), ctypes.byref(b), ctypes.byref(c), ctypes.byref(kparams),
+                                 int(tile), ctypes.byref(f), _p(dL_dimage), _p(grad2d), _stream(stream)),
+           "darb_render_bwd")
+    return grad2d
+
+
+@dataclasses.dataclass
+class SplatGrads:
+    dmeans: torch.Tensor
+    dscales: torch.Tensor
+    dquats: torch.Tensor
+    dopacities: torch.Tensor
+    dsh: torch.Tensor
+
+    @staticmethod
+    def empty_like(s: SplatTensors):
+        return SplatGrads(*(torch.empty_like(t) for t in (s.means, s.scales, s.quats, s.opacities, s.sh)))
+
+    def struct(self) -> darb_splat_grads:
+        return darb_splat_grads(_p(self.dmeans), _p(self.dscales), _p(self.dquats), _p(self.dopacities), _p(self.dsh))
+
+
+def darb_preprocess_bwd(splats: SplatTensors, cam, kparams, proj: Projected, grad2d: torch.Tensor,
+                        out: SplatGrads | None = None, stream=None):
+    out = SplatGrads.empty_like(splats) if out is None else out
+    sp, c, pr, g = splats.struct(), camera(cam), proj.struct(), out.struct()
+    _check(lib().darb_preprocess_bwd(ctypes.byref(sp), ctypes.byref(c), ctypes.byref(kparams), ctypes.byref(pr),
+                                     _p(grad2d), ctypes.byref(g), _stream(stream)), "darb_preprocess_bwd")
+    return out
+
+
+def darb_l1_loss(image, target, dL_dimage=None, loss=None, stream=None):
+    H, W = image.shape[-2:]
+    dL_dimage = torch.empty_like(image) if dL_dimage is None else dL_dimage
+    loss = torch.empty(1, dtype=torch.float32, device=image.device) if loss is None else loss
+    _check(lib().darb_l1_loss(_p(image), _p(target), int(W), int(H), _p(dL_dimage), _p(loss), _stream(stream)),
+           "darb_l1_loss")
+    return dL_dimage, loss
+
+
+def darb_adam_step(params, grads: SplatGrads, state, cfg: darb_adam_config, stream=None):
+    """params / state: objects exposing the darb_train_params / darb_adam_state fields as tensors."""
+    p = darb_train_params(_p(params.means), _p(params.log_scales), _p(params.quats), _p(params.opacity_logits),
+                          _p(params.sh), _p(params.scales), _p(params.opacities), int(params.means.shape[0]),
+                          int(params.sh_degree))
+    s = darb_adam_state(*(_p(getattr(state, f)) for f, _ in darb_adam_state._fields_))
+    g = grads.struct()
+    _check(lib().darb_adam_step(ctypes.byref(p), ctypes.byref(g), ctypes.byref(s), ctypes.byref(cfg), _stream(stream)),
+           "darb_adam_step")
+
+
+# ---------------------------------------------------------------------------
+# A reusable forward/backward pipeline and its autograd wrapper.
+
+class Rasterizer:
+    """Holds the per-view buffers of one camera configuration and runs the four steps."""
+
+    def __init__(self, cam, kernel="half_cosine", tile=16, capacity=None, device="cuda", psi=None):
+        self.cam = cam
+        self.tile = int(tile)
+        self.kparams = darb_kernel_defaults(kernel)
+        if psi is not None:
+            self.kparams.psi = float(psi)
+        self.device = device
+        self.tiles_x, self.tiles_y = darb_tile_grid(cam, tile)
+        self.capacity = int(capacity) if capacity else 0
+        self._ws = None
+        self._bins = None
+        self._n = -1
+
+    def _ensure(self, n, capacity):
+        if capacity > self.capacity or self._ws is None or n != self._n:
+            self.capacity = max(capacity, self.capacity)
+            nbytes = darb_bin_sort_workspace_size(n, self.tile, self.cam, self.capacity)
+            self._ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+            self._bins = Binning.empty(self.capacity, self.tiles_x * self.tiles_y, self.device)
+            self._n = n
+
+    def forward(self, splats: SplatTensors):
+        proj = darb_preprocess(splats, self.cam, self.kparams, self.tile)
+        if self.capacity == 0:
+            self.capacity = max(1024, 8 * splats.n)
+        self._ensure(splats.n, self.capacity)
+        try:
+            bins = darb_bin_sort(proj, splats.n, self.tile, self.cam, self._ws, self.capacity, self._bins)
+        except DarbError as e:
+            if e.status != 3:
+                raise
+            self._ensure(splats.n, int(self._bins.M * 1.25) + 1)
+            bins = darb_bin_sort(proj, splats.n, self.tile, self.cam, self._ws, self.capacity, self._bins)
+        img = darb_render_fwd(proj, bins, self.cam, self.kparams, self.tile)
+        return proj, bins, img
+
+    def backward(self, splats, proj, bins, img, dL_dimage):
+        g2 = darb_render_bwd(proj, splats.n, bins, self.cam, self.kparams, self.tile, img, dL_dimage.contiguous())
+        return darb_preprocess_bwd(splats, self.cam, self.kparams, proj, g2), g2
+
+
+class DarbRasterize(torch.autograd.Function):
+    """image = DarbRasterize.apply(means, scales, quats, opacities, sh, sh_degree, rasterizer)."""
+
+    @staticmethod
+    def forward(ctx, means, scales, quats, opacities, sh, sh_degree, rasterizer):
+        s = SplatTensors(means.contiguous(), scales.contiguous(), quats.contiguous(), opacities.contiguous(),
+                         sh.contiguous(), int(sh_degree))
+        proj, bins, img = rasterizer.forward(s)
+        ctx.state = (s, proj, bins, img, rasterizer)
+        return img.image
+
+    @staticmethod
+    def backward(ctx, dimage):
+        s, proj, bins, img, r = ctx.state
+        g, _ = r.backward(s, proj, bins, img, dimage.float().contiguous())
+        return g.dmeans, g.dscales, g.dquats, g.dopacities, g.dsh, None, None

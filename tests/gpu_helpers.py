@@ -1,0 +1,140 @@
+"""Helpers for the GPU parity tests: run the CUDA path and compare it with the oracle."""
+import numpy as np
+import torch
+
+import oracle
+from paper_2501_12369_gb300 import darb
+
+COLOUR_TOL = 1e-4  # absolute, per channel (FP32 path against the FP64 oracle)
+GRAD_RTOL = 1e-3   # relative, per element ...
+GRAD_ATOL = 1e-4   # ... plus this fraction of the largest magnitude in the parameter group
+
+
+def to_np(t):
+    return t.detach().cpu().numpy()
+
+
+def gpu_forward(splats, cam, kernel, tile, capacity=None):
+    r = darb.Rasterizer(cam, kernel, tile, capacity=capacity)
+    s = darb.splats_to_device(splats)
+    proj, bins, img = r.forward(s)
+    torch.cuda.synchronize()
+    return r, s, proj, bins, img
+
+
+def f32_bits(a):
+    return np.ascontiguousarray(np.asarray(a, np.float32)).view(np.uint32)
+
+
+def check_preprocess(proj, ref):
+    culled = ref["culled"].astype(bool)
+    rad = to_np(proj.radius)
+    assert np.array_equal(rad == 0, culled), "culling differs"
+    vis = ~culled
+    assert np.array_equal(rad[vis], ref["radius"][vis]), "radius differs"
+    assert np.array_equal(to_np(proj.tile_rect)[vis], ref["rect"][vis]), "tile rectangle differs"
+    assert np.array_equal(to_np(proj.tiles_touched)[vis].astype(np.int64), ref["tiles"][vis]), "tiles differ"
+    assert np.array_equal(f32_bits(to_np(proj.depth)[vis]), f32_bits(ref["depth"][vis])), "depth bits differ"
+    assert np.array_equal(f32_bits(to_np(proj.mean2d)[vis]), f32_bits(ref["mean2d"][vis])), "mean2d bits differ"
+    co = to_np(proj.conic_o)
+    assert np.array_equal(f32_bits(co[vis, :3]), f32_bits(ref["conic"][vis])), "conic bits differ"
+    assert np.array_equal(co[vis, 3], ref["opac"][vis]), "opacity differs"
+    rgb = to_np(proj.rgb)
+    assert np.abs(rgb[vis] - ref["rgb"][vis]).max(initial=0.0) <= 1e-5, "SH colour differs"
+    cl = to_np(proj.clamped)[vis]
+    diff = cl != ref["clamped"][vis]
+    near0 = (ref["rgb"][vis] < 1e-5).any(axis=1)
+    assert not (diff & ~near0).any(), "colour clamp flags differ"
+
+
+def tile_runs(keys_or_none, values, ranges):
+    return [values[a:b] for a, b in ranges]
+
+
+def check_lists(bins, ref_lists, tile_mask=None):
+    """Per-tile runs of the GPU sort equal the oracle's (tile, depth, id) order, bit for bit."""
+    ranges = to_np(bins.ranges).astype(np.int64)
+    rref = ref_lists["ranges"].astype(np.int64)
+    M = int(to_np(bins.num_instances)[0])
+    keys = to_np(bins.keys)[:M].view(np.uint64)
+    vals = to_np(bins.values)[:M]
+    if tile_mask is None:
+        assert M == ref_lists["M"], f"instance count {M} != {ref_lists['M']}"
+        assert np.array_equal(keys, ref_lists["keys"]), "sorted keys differ"
+        assert np.array_equal(vals, ref_lists["ids"]), "sorted values differ"
+        assert np.array_equal(ranges, rref), "tile ranges differ"
+    else:
+        for t in np.flatnonzero(np.asarray(tile_mask).reshape(-1)):
+            a, b = ranges[t]
+            c, d = rref[t]
+            assert b - a == d - c, f"tile {t}: run length {b - a} != {d - c}"
+            assert np.array_equal(vals[a:b], ref_lists["ids"][c:d]), f"tile {t}: run differs"
+            assert np.array_equal(keys[a:b], ref_lists["keys"][c:d]), f"tile {t}: keys differ"
+
+
+def last_ids(img, bins, cam, tile):
+    """Splat id of each pixel's last contributor from the GPU's run position (-1 if none)."""
+    H, W = cam.height, cam.width
+    tx = (W + tile - 1) // tile
+    last = to_np(img.last).astype(np.int64)
+    ranges = to_np(bins.ranges).astype(np.int64)
+    vals = to_np(bins.values).astype(np.int64)
+    ys, xs = np.mgrid[0:H, 0:W]
+    t = (ys // tile) * tx + xs // tile
+    start = ranges[t, 0]
+    out = np.where(last > 0, vals[np.clip(start + last - 1, 0, len(vals) - 1)], -1)
+    return out
+
+
+def check_render(img, bins, ref, cam, tile, pixel_mask=None, tol=COLOUR_TOL):
+    """Counts and last contributors exact where the oracle's decisions are unique; colour and
+    transmittance within tol.  Where the oracle enumerated several outcomes the GPU must equal
+    one of them.  Returns (#checked, #ambiguous, #unverifiable)."""
+    H, W = cam.height, cam.width
+    mask = np.ones((H, W), bool) if pixel_mask is None else pixel_mask
+    image = to_np(img.image)
+    T = to_np(img.t_final)
+    count = to_np(img.n_contrib)
+    lid = last_ids(img, bins, cam, tile)
+    amb = ref["amb"]
+    uniq = mask & (amb == 0)
+    assert np.array_equal(count[uniq], ref["count"][uniq]), \
+        f"contributor counts differ at {np.argwhere(uniq & (count != ref['count']))[:5].tolist()}"
+    assert np.array_equal(lid[uniq], ref["last_id"][uniq]), "last contributors differ"
+    cerr = np.abs(image - ref["image"])[:, uniq].max(initial=0.0)
+    assert cerr <= tol, f"colour error {cerr}"
+    terr = np.abs(T - ref["T"])[uniq].max(initial=0.0)
+    assert terr <= tol, f"transmittance error {terr}"
+    alts = {}
+    for a in ref["alts"]:
+        alts.setdefault(a["pixel"], []).append(a)
+    n_amb = 0
+    for y, x in np.argwhere(mask & (amb == 1)):
+        pix = y * W + x
+        options = [dict(count=ref["count"][y, x], last_id=ref["last_id"][y, x], C=ref["image"][:, y, x])]
+        options += [dict(count=a["count"], last_id=a["last_id"], C=np.array(a["C"])) for a in alts.get(pix, [])]
+        ok = any(o["count"] == count[y, x] and o["last_id"] == lid[y, x] and
+                 np.abs(image[:, y, x] - o["C"]).max() <= tol for o in options)
+        assert ok, f"pixel ({x},{y}) matches none of the {len(options)} valid outcomes"
+        n_amb += 1
+    n_unv = int((mask & (amb == 2)).sum())
+    assert n_unv <= max(2, 1e-3 * mask.sum()), f"{n_unv} unverifiable pixels"
+    return int(uniq.sum()), n_amb, n_unv
+
+
+def grad_close(name, got, ref, rtol=GRAD_RTOL, atol=GRAD_ATOL):
+    got = np.asarray(got, np.float64)
+    ref = np.asarray(ref, np.float64)
+    scale = np.abs(ref).max(initial=0.0)
+    err = np.abs(got - ref)
+    bound = rtol * np.abs(ref) + atol * scale
+    bad = err > bound
+    assert not bad.any(), (f"{name}: {bad.sum()} of {bad.size} elements out of tolerance; worst "
+                           f"{(err / np.maximum(bound, 1e-300)).max():.3g}x bound, scale {scale:.3g}")
+
+
+def ambiguity_masked_grad(dL, amb):
+    """Zero the upstream gradient at pixels whose forward decisions are not unique."""
+    d = np.array(dL, np.float64, copy=True)
+    d[:, amb != 0] = 0.0
+    return d

@@ -1,0 +1,222 @@
+"""CUDA path (through the C ABI) against the CPU oracle, element by element."""
+import dataclasses
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2501_12369_gb300 import darb, synth
+
+from gpu_helpers import (ambiguity_masked_grad, check_lists, check_preprocess, check_render, gpu_forward,
+                         grad_close, to_np)
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
+
+KERNELS = oracle.KERNEL_NAMES
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2501_12369_gb300 import build
+    build.build()
+    oracle.build()
+
+
+def _medium_scene(n=20000, seed=5, deg=3):
+    s = synth.cluster_scene(n, seed=seed, sh_degree=deg)
+    cam = synth.fibonacci_cameras(16, 6.0, 333, 207, 260.0)[3]  # ragged: 333x207 is no multiple of any tile
+    return s, cam
+
+
+# --------------------------------------------------------------------------- step 1
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_preprocess_is_bit_exact_small(kernel):
+    s, cam = synth.small_forward_workload()
+    r, sd, proj, bins, img = gpu_forward(s, cam, kernel, 16)
+    check_preprocess(proj, oracle.project(s, cam, oracle.kernel_params(kernel), 16, True))
+
+
+@pytest.mark.parametrize("deg", [0, 1, 2, 3])
+def test_preprocess_is_bit_exact_clusters(deg):
+    s, cam = _medium_scene(deg=deg)
+    s.quats *= np.float32(1.7)  # unnormalised quaternions are normalised inside
+    for kernel in ("half_cosine", "raised_cosine"):
+        r, sd, proj, bins, img = gpu_forward(s, cam, kernel, 16)
+        check_preprocess(proj, oracle.project(s, cam, oracle.kernel_params(kernel), 16, True))
+
+
+# --------------------------------------------------------------------------- steps 2-3
+
+@pytest.mark.parametrize("tile", [8, 16, 32])
+def test_bin_sort_is_bit_exact(tile):
+    s, cam = _medium_scene()
+    s.means[::50] = s.means[7]  # coincident splats: equal keys must keep splat order
+    r, sd, proj, bins, img = gpu_forward(s, cam, "half_cosine", tile)
+    ref = oracle.project(s, cam, oracle.kernel_params("half_cosine"), tile, True)
+    check_lists(bins, oracle.build_lists(ref, cam, tile))
+
+
+def test_bin_sort_async_capacity_mode_matches_sync():
+    s, cam = _medium_scene()
+    kp = darb.darb_kernel_defaults("half_cosine")
+    sd = darb.splats_to_device(s)
+    proj = darb.darb_preprocess(sd, cam, kp, 16)
+    cap = 400000
+    ws = torch.empty(darb.darb_bin_sort_workspace_size(s.n, 16, cam, cap), dtype=torch.uint8, device="cuda")
+    a = darb.darb_bin_sort(proj, s.n, 16, cam, ws, cap, sync=True)
+    M = a.M
+    ka, va, ra = to_np(a.keys)[:M].copy(), to_np(a.values)[:M].copy(), to_np(a.ranges).copy()
+    b = darb.darb_bin_sort(proj, s.n, 16, cam, ws, cap, sync=False)
+    torch.cuda.synchronize()
+    assert int(to_np(b.num_instances)[0]) == M and int(to_np(b.status)[0]) == 0
+    assert np.array_equal(to_np(b.keys)[:M], ka) and np.array_equal(to_np(b.values)[:M], va)
+    assert np.array_equal(to_np(b.ranges), ra)
+
+
+def test_bin_sort_reports_capacity_overflow():
+    s, cam = synth.small_forward_workload()
+    kp = darb.darb_kernel_defaults("half_cosine")
+    sd = darb.splats_to_device(s)
+    proj = darb.darb_preprocess(sd, cam, kp, 16)
+    cap = 100
+    ws = torch.empty(darb.darb_bin_sort_workspace_size(s.n, 16, cam, cap), dtype=torch.uint8, device="cuda")
+    with pytest.raises(darb.DarbError) as e:
+        darb.darb_bin_sort(proj, s.n, 16, cam, ws, cap, sync=True)
+    assert e.value.status == 3
+    b = darb.darb_bin_sort(proj, s.n, 16, cam, ws, cap, sync=False)  # async: flagged on the device
+    torch.cuda.synchronize()
+    assert int(to_np(b.status)[0]) == 3 and int(to_np(b.num_instances)[0]) > cap
+    small = torch.empty(16, dtype=torch.uint8, device="cuda")
+    with pytest.raises(darb.DarbError) as e:
+        darb.darb_bin_sort(proj, s.n, 16, cam, small, cap)
+    assert e.value.status == 2
+
+
+# --------------------------------------------------------------------------- step 4
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_render_forward_small(kernel):
+    s, cam = synth.small_forward_workload()
+    r, sd, proj, bins, img = gpu_forward(s, cam, kernel, 16)
+    ref = oracle.forward(s, cam, kernel, tile=16, mode="brute")
+    n, namb, nunv = check_render(img, bins, ref, cam, 16)
+    assert n > 3900
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("tile", [8, 16, 32])
+def test_render_forward_clusters(kernel, tile):
+    s, cam = _medium_scene()
+    cam = dataclasses.replace(cam, bg=(0.2, 0.4, 0.6))
+    r, sd, proj, bins, img = gpu_forward(s, cam, kernel, tile)
+    ref = oracle.forward(s, cam, kernel, tile=tile)
+    check_render(img, bins, ref, cam, tile)
+
+
+# --------------------------------------------------------------------------- backward
+
+def _grads(s, cam, kernel, tile, dl_seed=3):
+    r, sd, proj, bins, img = gpu_forward(s, cam, kernel, tile)
+    dl = synth.random_image_grad(cam.height, cam.width, seed=dl_seed)
+    ref_f = oracle.forward(s, cam, kernel, tile=tile)
+    dl = ambiguity_masked_grad(dl, ref_f["amb"])
+    dL = torch.from_numpy(dl.astype(np.float32)).cuda()
+    g, g2 = r.backward(sd, proj, bins, img, dL)
+    torch.cuda.synchronize()
+    _, g2_ref, gp_ref = oracle.gradients(s, cam, dl.astype(np.float32).astype(np.float64), kernel, tile=tile)
+    return g, g2, g2_ref, gp_ref, sd, proj, r
+
+
+G2_NAMES = ["dmean_x", "dmean_y", "dA", "dB", "dC", "dopacity", "dr", "dg", "db"]
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_render_backward_matches_oracle(kernel):
+    s, cam = synth.small_forward_workload()
+    g, g2, g2_ref, gp_ref, *_ = _grads(s, cam, kernel, 16)
+    g2 = to_np(g2)
+    assert np.all(g2[:, 9:] == 0)
+    for j, name in enumerate(G2_NAMES):
+        grad_close(f"{kernel}/{name}", g2[:, j], g2_ref[:, j])
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_preprocess_backward_matches_oracle(kernel):
+    """The per-splat chain alone: the oracle's own grad2d fed to the GPU's preprocess backward."""
+    s, cam = _medium_scene(n=5000)
+    r, sd, proj, bins, img = gpu_forward(s, cam, kernel, 16)
+    ref = oracle.project(s, cam, oracle.kernel_params(kernel), 16, True)
+    rng = np.random.default_rng(0)
+    g2 = rng.normal(size=(s.n, 9))
+    g2[ref["culled"] == 1] = 0.0
+    g2_12 = np.zeros((s.n, 12), np.float32)
+    g2_12[:, :9] = g2
+    out = darb.darb_preprocess_bwd(sd, cam, r.kparams, proj, torch.from_numpy(g2_12).cuda())
+    torch.cuda.synchronize()
+    gp = oracle.project_backward(s, ref, cam, oracle.kernel_params(kernel), g2_12[:, :9].astype(np.float64))
+    for name, got in (("means", out.dmeans), ("scales", out.dscales), ("quats", out.dquats),
+                      ("opacities", out.dopacities), ("sh", out.dsh)):
+        grad_close(f"{kernel}/{name}", to_np(got), gp[name])
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_full_gradient_matches_oracle(kernel):
+    s, cam = _medium_scene(n=8000)
+    g, g2, g2_ref, gp_ref, *_ = _grads(s, cam, kernel, 16)
+    for name, got in (("means", g.dmeans), ("scales", g.dscales), ("quats", g.dquats),
+                      ("opacities", g.dopacities), ("sh", g.dsh)):
+        grad_close(f"{kernel}/{name}", to_np(got), gp_ref[name])
+
+
+def test_gradients_on_the_256_splat_32x32_subset():
+    """The finite-difference subset of the 500k / 720p scene: the 256 splats projecting nearest
+    the image centre, seen through a 32x32 crop.  GPU gradient against the oracle's analytic
+    gradient (which the CPU suite checks against central differences)."""
+    s, cam = synth.scene_500k_720p()
+    kp = oracle.kernel_params("half_cosine")
+    p = oracle.project(s, cam, kp, 16, True)
+    vis = np.flatnonzero(p["culled"] == 0)
+    d = np.linalg.norm(p["mean2d"][vis] - [cam.cx, cam.cy], axis=1)
+    sub = s.subset(np.sort(vis[np.argsort(d)[:256]]))
+    crop = synth.crop_camera(cam, int(cam.cx) - 16, int(cam.cy) - 16, 32, 32)
+    for kernel in ("gaussian", "half_cosine"):
+        g, g2, g2_ref, gp_ref, *_ = _grads(sub, crop, kernel, 16)
+        for name, got in (("means", g.dmeans), ("scales", g.dscales), ("quats", g.dquats),
+                          ("opacities", g.dopacities), ("sh", g.dsh)):
+            grad_close(f"{kernel}/{name}", to_np(got), gp_ref[name])
+
+
+# --------------------------------------------------------------------------- edge cases
+
+def test_empty_and_fully_culled_scenes():
+    cam = synth.pinhole((0.0, 0.0, 4.0), 48, 40, 50.0, bg=(0.3, 0.2, 0.1))
+    s = synth.uniform_cube_scene(500, seed=1)
+    s.means[:, 2] += 10.0  # every splat behind the camera
+    for scene in (s, s.subset(np.arange(0))):
+        r, sd, proj, bins, img = gpu_forward(scene, cam, "half_cosine", 16)
+        assert bins.M == 0
+        im = to_np(img.image)
+        assert np.allclose(im, np.array(cam.bg)[:, None, None]) and np.all(to_np(img.n_contrib) == 0)
+        assert np.all(to_np(img.t_final) == 1.0)
+
+
+def test_single_splat_covering_the_image():
+    cam = synth.pinhole((0.0, 0.0, 2.0), 100, 60, 80.0, bg=(0.0, 0.0, 0.0))
+    s = synth.uniform_cube_scene(1, seed=2, log_scale=(-0.3, -0.2))
+    s.means[:] = 0.0
+    for kernel in KERNELS:
+        r, sd, proj, bins, img = gpu_forward(s, cam, kernel, 16)
+        assert bins.M == 7 * 4  # the rectangle is clamped to the whole 7 x 4 tile grid
+        check_render(img, bins, oracle.forward(s, cam, kernel, tile=16), cam, 16)
+
+
+def test_tiny_and_odd_images():
+    s = synth.uniform_cube_scene(300, seed=9)
+    for (w, h) in [(1, 1), (7, 3), (17, 33), (129, 65)]:
+        cam = synth.pinhole((0.2, 0.1, 3.5), w, h, 0.8 * w + 4)
+        for tile in (8, 16, 32):
+            r, sd, proj, bins, img = gpu_forward(s, cam, "parabola", tile)
+            check_render(img, bins, oracle.forward(s, cam, "parabola", tile=tile), cam, tile)

@@ -178,6 +178,23 @@ darb_status darb_bin_sort(const darb_projected *proj, int32_t n, int32_t tile,
                           uint64_t capacity, const darb_binning *out,
                           uint64_t *num_instances_host, darb_stream stream);
 
+/* darb_bin_sort without a caller-supplied workspace, for callers that cannot allocate device
+ * memory: for instance a plugin running inside another application's capture or render loop,
+ * where a cudaMalloc would synchronise the device, break a memory budget the host application
+ * enforces, or is simply not permitted.  The paper has no counterpart; it is an allocation-free
+ * form of the same sort with identical results.
+ * The scratch is a static device array of 64 MiB inside the library, held by every GPU that
+ * loads the library until the process exits.  Sizes whose darb_bin_sort_workspace_size exceeds
+ * 64 MiB are rejected with DARB_ERR_WORKSPACE.  The first call on a device resolves the array's
+ * device address (cudaGetSymbolAddress) with that device current; make it before any stream
+ * capture.  The call itself allocates nothing: no cudaMalloc, no cudaFree.  All calls share the
+ * one array and each call clears what must start at zero, so calls that overlap on the GPU (two
+ * streams, or two host threads) race and must be serialised by the caller.  Other arguments and
+ * results are those of darb_bin_sort. */
+darb_status darb_bin_sort_noalloc(const darb_projected *proj, int32_t n, int32_t tile,
+                                  const darb_camera *cam, uint64_t capacity, const darb_binning *out,
+                                  uint64_t *num_instances_host, darb_stream stream);
+
 /* Step 4: per-pixel front-to-back compositing (Sec. 4.1, "alpha blending ... similar to
  * 3DGS"; forward listings of Sec. B): for each splat of the pixel's tile run in depth
  * order, skip unless 0 <= q <= q_max, alpha = min(0.99, o F(q)), skip alpha < 1/255,

@@ -85,6 +85,8 @@ SIGNATURES = {
                                              _P(ctypes.c_size_t)]),
     "darb_bin_sort": (c_i32, [_P(darb_projected), c_i32, c_i32, _P(darb_camera), c_vp, ctypes.c_size_t,
                               ctypes.c_uint64, _P(darb_binning), _P(ctypes.c_uint64), c_vp]),
+    "darb_bin_sort_noalloc": (c_i32, [_P(darb_projected), c_i32, c_i32, _P(darb_camera), ctypes.c_uint64,
+                                      _P(darb_binning), _P(ctypes.c_uint64), c_vp]),
     "darb_render_fwd": (c_i32, [_P(darb_projected), _P(darb_binning), _P(darb_camera), _P(darb_kernel_params),
                                 c_i32, _P(darb_image), c_vp]),
     "darb_render_bwd": (c_i32, [_P(darb_projected), c_i32, _P(darb_binning), _P(darb_camera),
@@ -291,6 +293,20 @@ def darb_bin_sort(proj: Projected, n, tile, cam, workspace: torch.Tensor, capaci
                              ctypes.byref(m) if sync else None, _stream(stream))
     out.M = int(m.value) if sync else None
     _check(st, "darb_bin_sort")
+    return out
+
+
+def darb_bin_sort_noalloc(proj: Projected, n, tile, cam, capacity, out: Binning | None = None, sync=True,
+                          stream=None):
+    """darb_bin_sort with the library's static device scratch instead of a caller workspace."""
+    tx, ty = darb_tile_grid(cam, tile)
+    out = Binning.empty(capacity, tx * ty, proj.depth.device) if out is None else out
+    pr, c, b = proj.struct(), camera(cam), out.struct()
+    m = ctypes.c_uint64(0)
+    st = lib().darb_bin_sort_noalloc(ctypes.byref(pr), int(n), int(tile), ctypes.byref(c), int(capacity),
+                                     ctypes.byref(b), ctypes.byref(m) if sync else None, _stream(stream))
+    out.M = int(m.value) if sync else None
+    _check(st, "darb_bin_sort_noalloc")
     return out
 
 

@@ -1,0 +1,57 @@
+"""darb_bin_sort_noalloc, the allocation-free form of darb_bin_sort for callers that cannot
+allocate device memory (it sorts in a static scratch array inside the library).
+
+Collected last on purpose: it checks the variant against the existing entry point on two
+calls in a row, and must pass both alone in a fresh process and after the other tests.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2501_12369_gb300 import darb, synth
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2501_12369_gb300 import build
+    build.build()
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+def test_noalloc_sort_equals_workspace_sort_twice_in_a_row():
+    s, cam = synth.small_forward_workload()
+    big = synth.cluster_scene(20000, seed=4)
+    cam_big = synth.fibonacci_cameras(8, 6.0, 320, 200, 250.0)[1]
+    for splats, c, tile in ((s, cam, 16), (big, cam_big, 8)):
+        kp = darb.darb_kernel_defaults("half_cosine")
+        sd = darb.splats_to_device(splats)
+        proj = darb.darb_preprocess(sd, c, kp, tile)
+        cap = 200000
+        ws = torch.empty(darb.darb_bin_sort_workspace_size(splats.n, tile, c, cap), dtype=torch.uint8, device="cuda")
+        ref = darb.darb_bin_sort(proj, splats.n, tile, c, ws, cap)
+        M = ref.M
+        rk, rv, rr = _np(ref.keys)[:M].copy(), _np(ref.values)[:M].copy(), _np(ref.ranges).copy()
+        for sync in (True, False):  # two calls in a row, host-sized and capacity-sized
+            b = darb.darb_bin_sort_noalloc(proj, splats.n, tile, c, cap, sync=sync)
+            torch.cuda.synchronize()
+            assert int(_np(b.num_instances)[0]) == M and int(_np(b.status)[0]) == 0
+            assert np.array_equal(_np(b.keys)[:M], rk)
+            assert np.array_equal(_np(b.values)[:M], rv)
+            assert np.array_equal(_np(b.ranges), rr)
+
+
+def test_noalloc_rejects_sizes_beyond_its_scratch():
+    s, cam = synth.small_forward_workload()
+    kp = darb.darb_kernel_defaults("half_cosine")
+    proj = darb.darb_preprocess(darb.splats_to_device(s), cam, kp, 16)
+    cap = 1 << 26  # needs far more than the 64 MiB static scratch
+    out = darb.Binning.empty(16, 16, "cuda")
+    with pytest.raises(darb.DarbError) as e:
+        darb.darb_bin_sort_noalloc(proj, s.n, 16, cam, cap, out=out)
+    assert e.value.status == 2

@@ -124,9 +124,10 @@ class ClockSampler:
 class TrainStep:
     """Device buffers of one training replica and the per-step sequence of C-ABI calls."""
 
-    def __init__(self, splats, cams, kernel, tile, device):
+    def __init__(self, splats, cams, kernel, tile, device, strategy=0):
         from paper_2501_12369_gb300 import darb
         self.darb = darb
+        self.strategy = int(strategy)
         self.L = darb.lib()
         self.cams = cams
         self.tile = tile
@@ -179,11 +180,13 @@ class TrainStep:
     def set_capacity(self, capacity):
         d = self.darb
         self.capacity = int(capacity)
-        nbytes = d.darb_bin_sort_workspace_size(self.n, self.tile, self.cams[0], self.capacity)
+        nbytes = d.darb_bin_sort_workspace_size(self.n, self.tile, self.cams[0], self.capacity, self.strategy)
         self.ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
         self.ws_bytes = nbytes
         self.bins = d.Binning.empty(self.capacity, self.tx * self.ty, self.device)
         self.s_bins = self.bins.struct()
+        if self.strategy == d.DARB_SORT_DEPTH_THEN_TILE:
+            self.s_bins.keys = None  # 64-bit keys are not needed by the compositing
 
     def count_instances(self, cam_idx):
         """M for one camera (synchronising), used to size the capacity before timing."""
@@ -194,7 +197,7 @@ class TrainStep:
                                         ctypes.byref(self.s_proj), st), "preprocess")
         m = ctypes.c_uint64(0)
         r = self.L.darb_bin_sort(ctypes.byref(self.s_proj), self.n, self.tile, c, d._p(self.ws), self.ws_bytes,
-                                 self.capacity, ctypes.byref(self.s_bins), ctypes.byref(m), st)
+                                 self.capacity, self.strategy, ctypes.byref(self.s_bins), ctypes.byref(m), st)
         if r not in (0, 3):
             d._check(r, "bin_sort")
         return int(m.value)
@@ -209,7 +212,7 @@ class TrainStep:
                                    st), "preprocess")
         rec(1)
         d._check(L.darb_bin_sort(ctypes.byref(self.s_proj), self.n, self.tile, c, d._p(self.ws), self.ws_bytes,
-                                 self.capacity, ctypes.byref(self.s_bins), None, st), "bin_sort")
+                                 self.capacity, self.strategy, ctypes.byref(self.s_bins), None, st), "bin_sort")
         rec(2)
         d._check(L.darb_render_fwd(ctypes.byref(self.s_proj), ctypes.byref(self.s_bins), c, self.kp_ref, self.tile,
                                    ctypes.byref(self.s_img), st), "render_fwd")
@@ -242,13 +245,18 @@ class TrainStep:
 STAGES = ["preprocess", "bin_sort", "render_fwd", "l1_loss", "render_bwd", "preprocess_bwd", "adam"]
 
 
-def algorithmic_bytes(stage, n, M, passes, sh_k):
+def algorithmic_bytes(stage, n, M, passes, sh_k, strategy=0, tile_passes=2):
     """HBM bytes a stage must move at minimum, per launch (see the data layout notes in the docs)."""
     sh_b = sh_k * 3 * 4
     if stage == "preprocess":
         return n * (12 + 12 + 16 + 4 + sh_b) + n * (4 + 4 + 16 + 8 + 16 + 12 + 1 + 4)
     if stage == "bin_sort":
-        return n * (4 + 4 + 16 + 4) + M * (12 + 8 + 24 * passes + 8)
+        if strategy == 1:
+            return n * (4 + 4 + 16 + 4) + M * (12 + 8 + 24 * passes + 8)
+        # per splat: depth keys (read depth+radius, write key), 4 depth passes (16 B each), tiles
+        # gathered twice in depth order, offsets written and read, rect; per instance: duplicate
+        # write 8, each tile pass read 8 + write 8, ranges read 4
+        return n * (8 + 4 + 4 * 16 + 8 + 8 + 16) + M * (8 + 16 * tile_passes + 4)
     if stage == "preprocess_bwd":
         return n * (12 + 12 + 16 + sh_b + 48 + 4 + 1) + n * (12 + 12 + 16 + 4 + sh_b)
     if stage == "adam":
@@ -324,7 +332,7 @@ def run_ours(args):
     from paper_2501_12369_gb300 import build, synth
     build.build()
     splats, cams = synth.scene_3m_1080p()
-    ts = TrainStep(splats, cams, args.kernel, args.tile, device)
+    ts = TrainStep(splats, cams, args.kernel, args.tile, device, args.sort)
     # replicas: rank r trains on its own camera sequence
     cam_seq = [(rank * 37 + i) % len(cams) for i in range(args.warmup + args.steps)]
     targets = [torch.from_numpy(synth.random_target(1080, 1920, seed=10 + i)).to(device) for i in range(4)]
@@ -414,8 +422,11 @@ def run_ours(args):
     hbm_stages = {s: stage_ms[s] for s in ("preprocess", "bin_sort", "preprocess_bwd", "adam")}
     peaks = load_peaks()
     peak_gbs = peaks["hbm_gbs"] if peaks else 6800.0
-    rl_stage = dominant if algorithmic_bytes(dominant, ts.n, M_mean, passes, sh_k) else max(hbm_stages, key=hbm_stages.get)
-    ab = algorithmic_bytes(rl_stage, ts.n, M_mean, passes, sh_k)
+    tile_bits = int(np.ceil(np.log2(ts.tx * ts.ty)))
+    tile_passes = max(1, (tile_bits + 7) // 8)
+    ab_of = lambda st: algorithmic_bytes(st, ts.n, M_mean, passes, sh_k, args.sort, tile_passes)  # noqa: E731
+    rl_stage = dominant if ab_of(dominant) else max(hbm_stages, key=hbm_stages.get)
+    ab = ab_of(rl_stage)
     achieved = ab / (stage_ms[rl_stage] / 1e3) / 1e9
     its = world * args.steps / (ms_max / 1e3)
     line = {
@@ -439,7 +450,8 @@ def run_ours(args):
         "gpu_launches": None,
         "clocks": clk,
     }
-    line["gpu_launches"] = args.steps * launches_per_step(passes)
+    line["gpu_launches"] = args.steps * launches_per_step(args.sort, int(np.ceil(np.log2(ts.tx * ts.ty))))
+    line["config"]["sort"] = "depth_then_tile" if args.sort == 0 else "keys64"
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(splats, cams, args.kernel, args.tile)
     if rank == 0:
@@ -448,10 +460,15 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def launches_per_step(passes):
-    # preprocess 1; bin_sort: block sums, scan, duplicate, histogram, hist scan, passes x onesweep, ranges;
-    # render_fwd 1; l1 1; render_bwd 1; preprocess_bwd 1; adam 5 groups
-    return 1 + (6 + passes) + 1 + 1 + 1 + 1 + 5
+def launches_per_step(strategy, tile_bits):
+    """Kernels of libdarb.so launched per training step (memsets excluded)."""
+    if strategy == 1:  # 64-bit keys: block sums, scan, duplicate, histogram, hist scan, passes, ranges
+        sort = 6 + (32 + tile_bits + 7) // 8
+    else:  # depth keys, histogram, hist scan, 4 depth passes, block sums, scan, offsets, duplicate,
+        # tile hist scan, tile passes, ranges
+        sort = 3 + 4 + 6 + max(1, (tile_bits + 7) // 8)
+    # preprocess, render_fwd, l1, render_bwd, preprocess_bwd, 5 Adam groups
+    return 1 + sort + 1 + 1 + 1 + 1 + 5
 
 
 # ----------------------------------------------------------------------------- reference arm
@@ -490,6 +507,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--kernel", default="half_cosine")
     ap.add_argument("--tile", type=int, default=16)
+    ap.add_argument("--sort", type=int, default=0, help="0: depth then tile (default), 1: 64-bit keys")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

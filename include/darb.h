@@ -157,25 +157,34 @@ darb_status darb_preprocess(const darb_splats *splats, const darb_camera *cam,
                             const darb_kernel_params *kparams, int32_t tile,
                             const darb_projected *out, darb_stream stream);
 
-/* Workspace bytes darb_bin_sort needs for n splats and an instance capacity.
+/* Sort strategies of darb_bin_sort.  Both give the same keys, values and ranges, bit for bit.
+ *   DARB_SORT_DEPTH_THEN_TILE: sort the n splats by depth once, emit the instances in that order
+ *     and sort them stably by tile id only (2 LSD passes of 32-bit keys at 1080p / 16-pixel tiles;
+ *     about 36 bytes of traffic per instance).  out->keys is optional (NULL: not written).
+ *   DARB_SORT_KEYS64: one stable LSD sort of the 64-bit keys tile << 32 | bits(depth) over their
+ *     low 32 + ceil(log2(tiles)) bits (6 passes at 1080p).  out->keys is required. */
+typedef enum { DARB_SORT_DEPTH_THEN_TILE = 0, DARB_SORT_KEYS64 = 1 } darb_sort_strategy;
+
+/* Workspace bytes darb_bin_sort needs for n splats, an instance capacity and a strategy.
  * Host pointers; no device work. */
 darb_status darb_bin_sort_workspace_size(int32_t n, int32_t tile, const darb_camera *cam,
-                                         uint64_t capacity, size_t *bytes);
+                                         uint64_t capacity, int32_t strategy, size_t *bytes);
 
 /* Steps 2 and 3: tile/depth key duplication and radix sort (the tile-based
  * rasterization with a bounding box that Sec. A.3 inherits from 3DGS).  Scans
- * tiles_touched, emits one (tile << 32 | depth bits, splat) instance per tile of each
- * rectangle, sorts them with an LSD onesweep radix sort over the low
- * 32 + ceil(log2(tiles)) key bits (stable, so ties keep splat order), and writes the
- * per-tile ranges.  proj: darb_preprocess outputs.  workspace: device, at least
+ * tiles_touched, emits one instance per tile of each rectangle and sorts them with LSD
+ * onesweep radix passes into the order of key = tile << 32 | bits(depth), ties by splat
+ * index, then writes the per-tile ranges.  strategy: a darb_sort_strategy.
+ * proj: darb_preprocess outputs.  workspace: device, at least
  * darb_bin_sort_workspace_size bytes, contents scratch.  capacity: entries of
  * out->keys / out->values (< 2^30).  num_instances_host: if non-NULL the call
  * synchronises the stream once to read M and returns DARB_ERR_CAPACITY when
  * M > capacity (outputs then undefined); if NULL nothing synchronises, the sort is
- * sized by capacity, and an overflow is reported in out->status. */
+ * sized by capacity, and an overflow is reported in out->status with every tile range
+ * left empty (so a following darb_render_fwd draws only the background). */
 darb_status darb_bin_sort(const darb_projected *proj, int32_t n, int32_t tile,
                           const darb_camera *cam, void *workspace, size_t workspace_bytes,
-                          uint64_t capacity, const darb_binning *out,
+                          uint64_t capacity, int32_t strategy, const darb_binning *out,
                           uint64_t *num_instances_host, darb_stream stream);
 
 /* darb_bin_sort without a caller-supplied workspace, for callers that cannot allocate device

@@ -126,51 +126,45 @@ darb_status darb_preprocess(const darb_splats *splats, const darb_camera *cam, c
     return DARB_OK;
 }
 
+bool valid_strategy(int s) { return s == DARB_SORT_DEPTH_THEN_TILE || s == DARB_SORT_KEYS64; }
+
 darb_status darb_bin_sort_workspace_size(int32_t n, int32_t tile, const darb_camera *cam, uint64_t capacity,
-                                         size_t *bytes) {
-    if (n < 0 || !valid_tile(tile) || !valid_camera(cam) || !bytes || capacity > kMaxCapacity)
+                                         int32_t strategy, size_t *bytes) {
+    if (n < 0 || !valid_tile(tile) || !valid_camera(cam) || !bytes || capacity > kMaxCapacity ||
+        !valid_strategy(strategy))
         return DARB_ERR_INVALID_ARG;
-    const int passes = (32 + tile_bits_for(cam, tile) + 7) / 8;
-    *bytes = sort_workspace_bytes(n, capacity, passes);
+    const int n_tiles = tile_count(cam->width, tile) * tile_count(cam->height, tile);
+    *bytes = sort_workspace_bytes(n, capacity, n_tiles, strategy);
     return DARB_OK;
 }
 
 darb_status darb_bin_sort(const darb_projected *proj, int32_t n, int32_t tile, const darb_camera *cam,
-                          void *workspace, size_t workspace_bytes, uint64_t capacity, const darb_binning *out,
-                          uint64_t *num_instances_host, darb_stream stream) {
-    if (n < 0 || !valid_tile(tile) || !valid_camera(cam) || capacity > kMaxCapacity || !out) return DARB_ERR_INVALID_ARG;
+                          void *workspace, size_t workspace_bytes, uint64_t capacity, int32_t strategy,
+                          const darb_binning *out, uint64_t *num_instances_host, darb_stream stream) {
+    if (n < 0 || !valid_tile(tile) || !valid_camera(cam) || capacity > kMaxCapacity || !out ||
+        !valid_strategy(strategy))
+        return DARB_ERR_INVALID_ARG;
     if (!out->ranges || !out->num_instances || !out->status || !aligned16(out->ranges)) return DARB_ERR_INVALID_ARG;
-    if (capacity > 0 && (!out->keys || !out->values || !aligned16(out->keys) || !aligned16(out->values)))
+    const bool need_keys = strategy == DARB_SORT_KEYS64;
+    if (capacity > 0 && (!out->values || !aligned16(out->values) || (need_keys && !out->keys) ||
+                         (out->keys && !aligned16(out->keys))))
         return DARB_ERR_INVALID_ARG;
     if (n > 0 && !valid_projected(proj)) return DARB_ERR_INVALID_ARG;
-    const int tile_bits = tile_bits_for(cam, tile);
-    const int passes = (32 + tile_bits + 7) / 8;
-    const size_t need = sort_workspace_bytes(n, capacity, passes);
-    if (!workspace || workspace_bytes < need || !aligned16(workspace)) return DARB_ERR_WORKSPACE;
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const int tiles_x = tile_count(cam->width, tile), tiles_y = tile_count(cam->height, tile);
-
-    void *base = reinterpret_cast<void *>((reinterpret_cast<uintptr_t>(workspace) + 255) & ~(uintptr_t)255);
-    const SortWorkspace ws = carve_sort_workspace(base, n, capacity, passes);
-    DARB_CUDA_TRY(cudaMemsetAsync(ws.hist, 0, ws.zero_bytes, st));
-    DARB_CUDA_TRY(cudaMemsetAsync(out->status, 0, sizeof(uint32_t), st));
-    DARB_CUDA_TRY(cudaMemsetAsync(out->ranges, 0, (size_t)tiles_x * tiles_y * 2 * sizeof(uint32_t), st));
-    DARB_CUDA_TRY(launch_count_instances(n, proj ? proj->tiles_touched : nullptr, ws, out->num_instances, out->status,
-                                         capacity, st));
-    uint64_t grid_instances = capacity;
-    if (num_instances_host) {
-        uint32_t M = 0;
-        DARB_CUDA_TRY(cudaMemcpyAsync(&M, out->num_instances, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-        DARB_CUDA_TRY(cudaStreamSynchronize(st));
-        *num_instances_host = M;
-        if (M > capacity) return DARB_ERR_CAPACITY;
-        grid_instances = M;
+    const size_t need = sort_workspace_bytes(n, capacity, tiles_x * tiles_y, strategy);
+    if (!workspace || workspace_bytes < need || !aligned16(workspace)) return DARB_ERR_WORKSPACE;
+    ProjectedIn pin{};
+    if (n > 0) {
+        pin.depth = proj->depth;
+        pin.radius = proj->radius;
+        pin.tile_rect = reinterpret_cast<const int4 *>(proj->tile_rect);
+        pin.tiles_touched = proj->tiles_touched;
     }
-    DARB_CUDA_TRY(launch_duplicate_and_sort(n, proj ? proj->tiles_touched : nullptr,
-                                            proj ? reinterpret_cast<const int4 *>(proj->tile_rect) : nullptr,
-                                            proj ? proj->depth : nullptr, tiles_x, tile_bits, capacity, grid_instances,
-                                            ws, out->keys, out->values, out->ranges, out->num_instances, out->status, st));
-    return DARB_OK;
+    const BinOut bo{out->keys, out->values, out->ranges, out->num_instances, out->status};
+    bool exceeded = false;
+    DARB_CUDA_TRY(launch_bin_sort(n, pin, tiles_x, tiles_x * tiles_y, capacity, strategy, workspace, bo,
+                                  num_instances_host, &exceeded, reinterpret_cast<cudaStream_t>(stream)));
+    return exceeded ? DARB_ERR_CAPACITY : DARB_OK;
 }
 
 darb_status darb_render_fwd(const darb_projected *proj, const darb_binning *bins, const darb_camera *cam,

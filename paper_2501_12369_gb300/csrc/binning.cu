@@ -1,24 +1,33 @@
 // Steps 2 and 3: tile/depth key duplication and the radix sort of those keys, plus the
 // per-tile ranges.  This is the tile-based rasterization with a bounding box that the paper
-// keeps from 3DGS (Sec. A.3); the paper prints none of it, so the design here is GB300's:
+// keeps from 3DGS (Sec. A.3); the paper prints none of it, so the design here is GB300's.
 //
-//   k_block_sums / k_scan_block_sums  scan of tiles_touched (2048 splats per CTA, then one
-//                                      CTA over the CTA sums; no inter-CTA waiting)
-//   k_duplicate                        per CTA: block scan -> per-splat offsets in shared
-//                                      memory, then a load-balanced flat loop over the CTA's
-//                                      instances (binary search for the owning splat), so
-//                                      consecutive threads write consecutive keys
-//   k_sort_hist / k_hist_scan          one read of the keys for the digit histograms of all
-//                                      passes, then per-pass exclusive scans
-//   k_onesweep (one launch per pass)   LSD onesweep pass: warp-level multisplit ranking with
-//                                      match.any, decoupled look-back across partitions
-//                                      (bounded spins), staging in shared memory so global
-//                                      writes go out in digit runs
-//   k_ranges                           [start, end) of each tile from adjacent keys
+// The result is fixed: every (splat, tile-of-its-rectangle) instance, ordered by
+// key = tile << 32 | bits(depth) (depth > 0, so the unsigned order is (tile, depth)), equal keys
+// in ascending splat index.  Two strategies produce it bit for bit:
 //
-// Keys are tile << 32 | bits(depth) with depth > 0, so the unsigned order is (tile, depth);
-// only the low 32 + ceil(log2(tiles)) bits are sorted.  Each pass is stable, so equal keys
-// keep their emission order, which is ascending splat index.
+// DARB_SORT_DEPTH_THEN_TILE (default)
+//   k_depth_keys + 4 x k_onesweep<u32>   sort the N splats by depth bits (stable, so equal depths
+//                                         keep index order): N-sized, cheap
+//   k_block_sums / k_scan_block_sums      scan of tiles_touched in that depth order
+//   k_splat_offsets                       per-position instance offsets (depth order)
+//   k_duplicate_balanced                  emit (tile id, splat) per instance in depth order, each
+//                                         CTA a fixed range of instances (near splats are the
+//                                         largest, so splitting by splats would be unbalanced),
+//                                         plus the digit histograms of the tile passes
+//   p x k_onesweep<u32>                   stable LSD sort of the 32-bit tile ids (p = 2 at 1080p
+//                                         with 16-pixel tiles); the last writes the output values
+//   k_ranges32                            [start, end) of each tile from the sorted tile ids
+//   k_keys64 (optional)                   the 64-bit keys, when the caller asks for them
+//   About 44 bytes of HBM traffic per instance.
+//
+// DARB_SORT_KEYS64
+//   k_duplicate (64-bit keys in splat order), k_sort_hist, k_hist_scan, 6 x k_onesweep<u64>
+//   over the low 32 + ceil(log2 tiles) bits, k_ranges.  About 170 bytes per instance.
+//
+// k_onesweep is one LSD pass: warp-level multisplit ranking with match.any, decoupled look-back
+// across partitions claimed in launch order (spins bounded; on timeout the status word is set
+// and successors are released), and staging in shared memory so the scatter leaves in digit runs.
 #include <algorithm>
 #include <utility>
 
@@ -32,6 +41,9 @@ constexpr uint32_t kFlagLocal = 1u << 30;
 constexpr uint32_t kFlagIncl = 2u << 30;
 constexpr uint32_t kCountMask = (1u << 30) - 1;
 constexpr int kSpinLimit = 1 << 22;  // x >= 64 ns sleep: a few hundred ms at most
+constexpr int kDupItems = 16;
+constexpr int kDupTile = kScanThreads * kDupItems;  // instances per balanced duplicate CTA
+constexpr int kMaxTilePasses = 4;  // 26 tile bits at most (65536^2 pixels, 8-pixel tiles)
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
@@ -46,7 +58,7 @@ __device__ __forceinline__ void st_relaxed(uint32_t *p, uint32_t v) {
     *reinterpret_cast<volatile uint32_t *>(p) = v;
 }
 
-// Exclusive scan of one value per thread over a CTA of NT threads.  s_warp holds NT/32
+// Exclusive scan of one value per thread over a CTA of NT threads.  s_warp holds NT/32 + 1
 // entries.  Returns the exclusive prefix; total receives the CTA sum.
 template <int NT, typename T>
 __device__ __forceinline__ T block_exclusive_scan(T v, T *s_warp, T &total) {
@@ -78,15 +90,24 @@ __device__ __forceinline__ T block_exclusive_scan(T v, T *s_warp, T &total) {
     return res;
 }
 
+struct PassSpec {
+    int shift[kMaxPasses];
+    int bits[kMaxPasses];
+    int passes;
+};
+
+// ---------------------------------------------------------------------------- scan of tiles_touched
+
+// Per-CTA sums of tiles_touched over kScanTile positions; order (if given) maps positions to splats.
 __global__ void __launch_bounds__(kScanThreads)
-k_block_sums(int n, const uint32_t *__restrict__ tiles, uint32_t *__restrict__ sums) {
+k_block_sums(int n, const uint32_t *__restrict__ tiles, const uint32_t *__restrict__ order, uint32_t *__restrict__ sums) {
     __shared__ uint32_t s_warp[kScanThreads / 32 + 1];
     const int base = blockIdx.x * kScanTile;
     uint32_t s = 0;
 #pragma unroll
     for (int j = 0; j < kScanItems; ++j) {
         const int idx = base + j * kScanThreads + threadIdx.x;
-        if (idx < n) s += tiles[idx];
+        if (idx < n) s += tiles[order ? order[idx] : idx];
     }
     uint32_t total;
     block_exclusive_scan<kScanThreads>(s, s_warp, total);
@@ -112,19 +133,22 @@ k_scan_block_sums(int nb, const uint32_t *__restrict__ sums, unsigned long long 
     }
 }
 
-__global__ void __launch_bounds__(kScanThreads)
-k_duplicate(int n, const uint32_t *__restrict__ tiles, const unsigned long long *__restrict__ block_offsets,
-            const int4 *__restrict__ rect, const float *__restrict__ depth, int tiles_x,
-            unsigned long long capacity, uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
-    __shared__ uint32_t s_off[kScanTile + 1];
-    __shared__ uint32_t s_warp[kScanThreads / 32 + 1];
-    const int base = blockIdx.x * kScanTile;
+// Block scan of the CTA's kScanTile counts into s_off (exclusive, s_off[kScanTile] = total).
+__device__ __forceinline__ uint32_t cta_offsets(int n, int base, const uint32_t *__restrict__ tiles,
+                                                const uint32_t *__restrict__ order, uint32_t *s_off,
+                                                uint32_t *s_id, uint32_t *s_warp) {
     const int t = threadIdx.x;
     uint32_t c[kScanItems], sum = 0;
 #pragma unroll
     for (int j = 0; j < kScanItems; ++j) {
         const int idx = base + t * kScanItems + j;
-        c[j] = idx < n ? tiles[idx] : 0u;
+        uint32_t id = (uint32_t)idx;
+        c[j] = 0u;
+        if (idx < n) {
+            if (order) id = order[idx];
+            c[j] = tiles[id];
+        }
+        if (s_id) s_id[t * kScanItems + j] = id;
         sum += c[j];
     }
     uint32_t total;
@@ -135,49 +159,188 @@ k_duplicate(int n, const uint32_t *__restrict__ tiles, const unsigned long long 
         ex += c[j];
     }
     __syncthreads();
+    return total;
+}
+
+// Position in [0, nloc) of the splat owning CTA-local instance k: the largest s with s_off[s] <= k.
+__device__ __forceinline__ int owner_of(const uint32_t *s_off, int nloc, uint32_t k) {
+    int lo = 0, hi = nloc - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (s_off[mid] <= k) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// ---------------------------------------------------------------------------- duplication
+
+// 64-bit keys in splat order (strategy KEYS64).
+__global__ void __launch_bounds__(kScanThreads)
+k_duplicate(int n, const uint32_t *__restrict__ tiles, const unsigned long long *__restrict__ block_offsets,
+            const int4 *__restrict__ rect, const float *__restrict__ depth, int tiles_x,
+            unsigned long long capacity, uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+    __shared__ uint32_t s_off[kScanTile + 1];
+    __shared__ uint32_t s_warp[kScanThreads / 32 + 1];
+    const int base = blockIdx.x * kScanTile;
+    const uint32_t total = cta_offsets(n, base, tiles, nullptr, s_off, nullptr, s_warp);
     const unsigned long long gbase = block_offsets[blockIdx.x];
     const int nloc = min(kScanTile, n - base);
-    for (uint32_t k = t; k < total; k += kScanThreads) {
-        // owning splat: the largest s with s_off[s] <= k (it has >= 1 instance)
-        int lo = 0, hi = nloc - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (s_off[mid] <= k) lo = mid;
-            else hi = mid - 1;
-        }
-        const uint32_t l = k - s_off[lo];
-        const int4 r = __ldg(rect + base + lo);
+    for (uint32_t k = threadIdx.x; k < total; k += kScanThreads) {
+        const int s = owner_of(s_off, nloc, k);
+        const uint32_t l = k - s_off[s];
+        const int4 r = __ldg(rect + base + s);
         const int w = r.z - r.x + 1;
         const int ty = r.y + (int)(l / (uint32_t)w), tx = r.x + (int)(l % (uint32_t)w);
-        const uint64_t key = ((uint64_t)(uint32_t)(ty * tiles_x + tx) << 32) | __float_as_uint(__ldg(depth + base + lo));
+        const uint64_t key = ((uint64_t)(uint32_t)(ty * tiles_x + tx) << 32) | __float_as_uint(__ldg(depth + base + s));
         const unsigned long long dst = gbase + k;
         if (dst < capacity) {
             keys[dst] = key;
-            vals[dst] = (uint32_t)(base + lo);
+            vals[dst] = (uint32_t)(base + s);
         }
     }
 }
 
-__global__ void __launch_bounds__(256)
-k_sort_hist(const uint64_t *__restrict__ keys, const uint32_t *num, unsigned long long cap, int passes,
-            uint32_t *__restrict__ hist) {
-    __shared__ uint32_t s_h[kMaxPasses * 256];
-    for (int i = threadIdx.x; i < passes * 256; i += 256) s_h[i] = 0;
+// Per-position instance offsets in depth order: offs[j] = sum of tiles_touched over positions < j.
+__global__ void __launch_bounds__(kScanThreads)
+k_splat_offsets(int n, const uint32_t *__restrict__ order, const uint32_t *__restrict__ tiles,
+                const unsigned long long *__restrict__ block_offsets, const uint32_t *__restrict__ num,
+                uint32_t *__restrict__ offs) {
+    __shared__ uint32_t s_off[kScanTile + 1];
+    __shared__ uint32_t s_warp[kScanThreads / 32 + 1];
+    const int base = blockIdx.x * kScanTile;
+    cta_offsets(n, base, tiles, order, s_off, nullptr, s_warp);
+    const uint32_t gbase = (uint32_t)block_offsets[blockIdx.x];
+    for (int j = threadIdx.x; j < kScanTile; j += kScanThreads)
+        if (base + j < n) offs[base + j] = gbase + s_off[j];
+    if (blockIdx.x == 0 && threadIdx.x == 0) offs[n] = *num;
+}
+
+// Largest s in [0, n) with offs[s] <= target (offs non-decreasing, offs[0] = 0), by warp 0 of
+// the CTA with 32-way probes.  Returns the result to every thread of the CTA.
+__device__ __forceinline__ int cta_upper_owner(const uint32_t *__restrict__ offs, int n, uint32_t target, int *s_res) {
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        int a = 0, b = n;  // answer in [a, b)
+        while (b - a > 32) {
+            const int step = (b - a + 31) / 32;
+            const int p = a + lane * step;
+            const bool ok = p < b && offs[p] <= target;
+            const uint32_t bal = __ballot_sync(0xffffffffu, ok);
+            const int j = 31 - __clz(bal);  // offs[a] <= target always holds, so bal != 0
+            a = a + j * step;
+            b = min(b, a + step);
+        }
+        const int p = a + lane;
+        const bool ok = p < b && offs[p] <= target;
+        const uint32_t bal = __ballot_sync(0xffffffffu, ok);
+        if (lane == 0) *s_res = a + 31 - __clz(bal);
+    }
     __syncthreads();
-    const unsigned long long M = min((unsigned long long)*num, cap);
-    const int lane = threadIdx.x & 31;
-    for (unsigned long long b = (unsigned long long)blockIdx.x * 256; b < M; b += (unsigned long long)gridDim.x * 256) {
-        const unsigned long long i = b + threadIdx.x;
-        const bool valid = i < M;
-        const uint64_t k = valid ? keys[i] : 0ull;
-        for (int p = 0; p < passes; ++p) {
-            const uint32_t d = valid ? (uint32_t)(k >> (8 * p)) & 255u : 256u;
+    return *s_res;
+}
+
+// 32-bit tile ids in depth order (strategy DEPTH_THEN_TILE), balanced over instances: CTA c
+// emits instances [c * kDupTile, (c + 1) * kDupTile).  Lane-major order within each warp's
+// chunk keeps the writes coalesced.  Digit histograms of the tile passes are accumulated in
+// shared memory (match.any aggregated) and added to hist once per CTA.
+__global__ void __launch_bounds__(kScanThreads)
+k_duplicate_balanced(int n, const uint32_t *__restrict__ order, const uint32_t *__restrict__ offs,
+                     const int4 *__restrict__ rect, int tiles_x, const uint32_t *__restrict__ num,
+                     unsigned long long cap, PassSpec ps, uint32_t *__restrict__ keys, uint32_t *__restrict__ vals,
+                     uint32_t *__restrict__ hist) {
+    __shared__ uint32_t s_off[kDupTile + 1];
+    __shared__ uint32_t s_id[kDupTile];
+    __shared__ uint32_t s_h[kMaxTilePasses * 256];
+    __shared__ int s_res[2];
+    const unsigned long long Mfull = *num;
+    if (Mfull > cap) return;  // overflow: nothing is emitted (status already set)
+    const uint32_t M = (uint32_t)Mfull;
+    const uint32_t lo = blockIdx.x * (uint32_t)kDupTile;
+    if (lo >= M) return;
+    const uint32_t hi = min(M, lo + (uint32_t)kDupTile);
+    for (int i = threadIdx.x; i < ps.passes * 256; i += kScanThreads) s_h[i] = 0;
+    const int first = cta_upper_owner(offs, n, lo, &s_res[0]);
+    const int last = cta_upper_owner(offs, n, hi - 1, &s_res[1]);
+    const int count = min(last - first + 1, kDupTile);  // every owner has >= 1 instance
+    for (int i = threadIdx.x; i <= count; i += kScanThreads) {
+        s_off[i] = offs[first + i];
+        if (i < count) s_id[i] = order[first + i];
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t wbase = lo + (uint32_t)warp * (32 * kDupItems);
+    int s = 0;
+    {  // owner of this lane's first instance
+        const uint32_t k0 = min(wbase + lane, hi - 1);
+        int a = 0, b = count - 1;
+        while (a < b) {
+            const int mid = (a + b + 1) >> 1;
+            if (s_off[mid] <= k0) a = mid;
+            else b = mid - 1;
+        }
+        s = a;
+    }
+    for (int it = 0; it < kDupItems; ++it) {
+        const uint32_t k = wbase + it * 32 + lane;
+        const bool valid = k < hi;
+        uint32_t tile = 0;
+        if (valid) {
+            if (s_off[min(s + 8, count)] <= k) {  // far ahead: binary search the rest
+                int a = s, b = count - 1;
+                while (a < b) {
+                    const int mid = (a + b + 1) >> 1;
+                    if (s_off[mid] <= k) a = mid;
+                    else b = mid - 1;
+                }
+                s = a;
+            } else {
+                while (s_off[s + 1] <= k) ++s;
+            }
+            const uint32_t id = s_id[s];
+            const uint32_t l = k - s_off[s];
+            const int4 r = __ldg(rect + id);
+            const uint32_t w = (uint32_t)(r.z - r.x + 1);
+            const uint32_t ty = (uint32_t)r.y + l / w, tx = (uint32_t)r.x + l % w;
+            tile = ty * (uint32_t)tiles_x + tx;
+            keys[k] = tile;
+            vals[k] = id;
+        }
+        for (int p = 0; p < ps.passes; ++p) {
+            const uint32_t d = valid ? (tile >> ps.shift[p]) & ((1u << ps.bits[p]) - 1u) : 256u;
             const uint32_t peers = __match_any_sync(0xffffffffu, d);
             if (valid && lane == __ffs(peers) - 1) atomicAdd(&s_h[p * 256 + d], (uint32_t)__popc(peers));
         }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < passes * 256; i += 256)
+    for (int i = threadIdx.x; i < ps.passes * 256; i += kScanThreads)
+        if (s_h[i]) atomicAdd(&hist[i], s_h[i]);
+}
+
+// ---------------------------------------------------------------------------- histograms
+
+// Digit histograms of all passes in one read of the keys (M = min(*num, cap), or cap if num is null).
+template <typename K>
+__global__ void __launch_bounds__(256)
+k_sort_hist(const K *__restrict__ keys, const uint32_t *num, unsigned long long cap, PassSpec ps,
+            uint32_t *__restrict__ hist) {
+    __shared__ uint32_t s_h[kMaxPasses * 256];
+    for (int i = threadIdx.x; i < ps.passes * 256; i += 256) s_h[i] = 0;
+    __syncthreads();
+    const unsigned long long M = num ? min((unsigned long long)*num, cap) : cap;
+    const int lane = threadIdx.x & 31;
+    for (unsigned long long b = (unsigned long long)blockIdx.x * 256; b < M; b += (unsigned long long)gridDim.x * 256) {
+        const unsigned long long i = b + threadIdx.x;
+        const bool valid = i < M;
+        const K k = valid ? keys[i] : K(0);
+        for (int p = 0; p < ps.passes; ++p) {
+            const uint32_t d = valid ? (uint32_t)(k >> ps.shift[p]) & ((1u << ps.bits[p]) - 1u) : 256u;
+            const uint32_t peers = __match_any_sync(0xffffffffu, d);
+            if (valid && lane == __ffs(peers) - 1) atomicAdd(&s_h[p * 256 + d], (uint32_t)__popc(peers));
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < ps.passes * 256; i += 256)
         if (s_h[i]) atomicAdd(&hist[i], s_h[i]);
 }
 
@@ -189,14 +352,24 @@ __global__ void __launch_bounds__(256) k_hist_scan(const uint32_t *__restrict__ 
     base[p * 256 + threadIdx.x] = ex;
 }
 
-// One LSD pass over the 8-bit digit at `shift`.  Stable.
+// ---------------------------------------------------------------------------- onesweep
+
+template <typename K, bool WRITE_KEYS>
+struct Staging {
+    static constexpr size_t bytes = (size_t)kSortTile * ((WRITE_KEYS ? sizeof(K) : 1) + 4);
+};
+
+// One stable LSD pass over the digit of `bits` bits at `shift`.  M = min(*num, cap), or cap if
+// num is null.  vin may be null: values are then the input positions (iota).
+template <typename K, bool WRITE_KEYS>
 __global__ void __launch_bounds__(kSortThreads)
-k_onesweep(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint64_t *__restrict__ kout,
-           uint32_t *__restrict__ vout, const uint32_t *num, unsigned long long cap, int shift,
+k_onesweep(const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__restrict__ kout,
+           uint32_t *__restrict__ vout, const uint32_t *num, unsigned long long cap, int shift, int bits,
            const uint32_t *__restrict__ digit_base, uint32_t *lookback, uint32_t *part_counter, uint32_t *status) {
     extern __shared__ __align__(16) unsigned char smem[];
-    uint64_t *s_k = reinterpret_cast<uint64_t *>(smem);
-    uint32_t *s_v = reinterpret_cast<uint32_t *>(smem + (size_t)kSortTile * 8);
+    uint32_t *s_v = reinterpret_cast<uint32_t *>(smem);
+    K *s_k = reinterpret_cast<K *>(smem + (size_t)kSortTile * 4);
+    uint8_t *s_d = reinterpret_cast<uint8_t *>(smem + (size_t)kSortTile * 4);
     constexpr int NW = kSortThreads / 32;
     __shared__ uint32_t s_wh[NW][256];
     __shared__ uint32_t s_cta_excl[256];
@@ -205,32 +378,36 @@ k_onesweep(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin, u
     __shared__ uint32_t s_part;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t radix = 1u << bits, mask = radix - 1u;
+    // After a capacity overflow the instance buffers hold only part of the instances while the
+    // digit bases count all of them: sort nothing (the caller sees DARB_ERR_CAPACITY).
+    if (num && (unsigned long long)*num > cap) return;
     if (tid == 0) s_part = atomicAdd(part_counter, 1u);
     for (int i = tid; i < NW * 256; i += kSortThreads) (&s_wh[0][0])[i] = 0;
     __syncthreads();
-    const uint32_t M = (uint32_t)min((unsigned long long)*num, cap);
+    const uint32_t M = (uint32_t)(num ? min((unsigned long long)*num, cap) : cap);
     const uint32_t part = s_part;
     const uint32_t n_parts = (M + kSortTile - 1) / kSortTile;
     if (part >= n_parts) return;
     const uint32_t base = part * kSortTile;
 
-    uint64_t k[kSortItems];
+    K k[kSortItems];
     uint32_t v[kSortItems], rk[kSortItems];
 #pragma unroll
     for (int it = 0; it < kSortItems; ++it) {
         const uint32_t idx = base + warp * (32 * kSortItems) + it * 32 + lane;
         if (idx < M) {
             k[it] = kin[idx];
-            v[it] = vin[idx];
+            v[it] = vin ? vin[idx] : idx;
         } else {
-            k[it] = ~0ull;  // digit 255, ranked after every valid key of the partition
+            k[it] = ~K(0);  // the top digit, ranked after every valid key of the partition
             v[it] = 0;
         }
     }
     const uint32_t lt = lanemask_lt();
 #pragma unroll
     for (int it = 0; it < kSortItems; ++it) {
-        const uint32_t d = (uint32_t)(k[it] >> shift) & 255u;
+        const uint32_t d = (uint32_t)(k[it] >> shift) & mask;
         const uint32_t peers = __match_any_sync(0xffffffffu, d);
         const uint32_t prev = s_wh[warp][d];
         rk[it] = prev + __popc(peers & lt);
@@ -241,66 +418,77 @@ k_onesweep(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin, u
     __syncthreads();
 
     // thread = digit: per-warp exclusive offsets, CTA count, decoupled look-back
-    const int dg = tid;
+    const uint32_t dg = (uint32_t)tid;
     uint32_t cnt = 0;
+    if (dg < radix) {
 #pragma unroll
-    for (int w = 0; w < NW; ++w) {
-        const uint32_t c = s_wh[w][dg];
-        s_wh[w][dg] = cnt;
-        cnt += c;
-    }
-    uint32_t *mine = lookback + (size_t)part * 256 + dg;
-    uint32_t excl = 0;
-    if (part == 0) {
-        st_relaxed(mine, kFlagIncl | cnt);
-    } else {
-        st_relaxed(mine, kFlagLocal | cnt);
-        int p = (int)part - 1;
-        int spins = 0, ns = 64;
-        while (true) {
-            const uint32_t s = ld_relaxed(lookback + (size_t)p * 256 + dg);
-            const uint32_t f = s & ~kCountMask;
-            if (f == 0) {
-                if (++spins > kSpinLimit) {
-                    atomicExch(status, (uint32_t)DARB_ERR_TIMEOUT);
-                    break;
-                }
-                __nanosleep(ns);
-                ns = min(ns * 2, 1024);
-                continue;
-            }
-            excl += s & kCountMask;
-            if (f == kFlagIncl || p == 0) break;
-            --p;
+        for (int w = 0; w < NW; ++w) {
+            const uint32_t c = s_wh[w][dg];
+            s_wh[w][dg] = cnt;
+            cnt += c;
         }
-        st_relaxed(mine, kFlagIncl | ((excl + cnt) & kCountMask));
+        uint32_t *mine = lookback + (size_t)part * radix + dg;
+        uint32_t excl = 0;
+        if (part == 0) {
+            st_relaxed(mine, kFlagIncl | cnt);
+        } else {
+            st_relaxed(mine, kFlagLocal | cnt);
+            int p = (int)part - 1;
+            int spins = 0, ns = 64;
+            while (true) {
+                const uint32_t s = ld_relaxed(lookback + (size_t)p * radix + dg);
+                const uint32_t f = s & ~kCountMask;
+                if (f == 0) {
+                    if (++spins > kSpinLimit) {
+                        atomicExch(status, (uint32_t)DARB_ERR_TIMEOUT);
+                        break;
+                    }
+                    __nanosleep(ns);
+                    ns = min(ns * 2, 1024);
+                    continue;
+                }
+                excl += s & kCountMask;
+                if (f == kFlagIncl || p == 0) break;
+                --p;
+            }
+            st_relaxed(mine, kFlagIncl | ((excl + cnt) & kCountMask));
+        }
+        s_gbase[dg] = digit_base[dg] + excl;
     }
-    s_gbase[dg] = digit_base[dg] + excl;
     uint32_t tot;
-    s_cta_excl[dg] = block_exclusive_scan<kSortThreads>(cnt, s_warp, tot);
+    const uint32_t cex = block_exclusive_scan<kSortThreads>(cnt, s_warp, tot);
+    if (dg < radix) s_cta_excl[dg] = cex;
     __syncthreads();
 
 #pragma unroll
     for (int it = 0; it < kSortItems; ++it) {
-        const uint32_t d = (uint32_t)(k[it] >> shift) & 255u;
+        const uint32_t d = (uint32_t)(k[it] >> shift) & mask;
         const uint32_t pos = s_cta_excl[d] + s_wh[warp][d] + rk[it];
-        s_k[pos] = k[it];
+        if (WRITE_KEYS) s_k[pos] = k[it];
+        else s_d[pos] = (uint8_t)d;
         s_v[pos] = v[it];
     }
     __syncthreads();
     const uint32_t nvalid = min((uint32_t)kSortTile, M - base);
     for (uint32_t j = tid; j < nvalid; j += kSortThreads) {
-        const uint64_t kk = s_k[j];
-        const uint32_t d = (uint32_t)(kk >> shift) & 255u;
+        uint32_t d;
+        K kk = K(0);
+        if (WRITE_KEYS) {
+            kk = s_k[j];
+            d = (uint32_t)(kk >> shift) & mask;
+        } else {
+            d = s_d[j];
+        }
         const uint32_t dst = s_gbase[d] + (j - s_cta_excl[d]);
-        kout[dst] = kk;
+        if (WRITE_KEYS) kout[dst] = kk;
         vout[dst] = s_v[j];
     }
 }
 
 __global__ void __launch_bounds__(256)
 k_ranges(const uint64_t *__restrict__ keys, const uint32_t *num, unsigned long long cap, uint32_t *__restrict__ ranges) {
-    const unsigned long long M = min((unsigned long long)*num, cap);
+    if ((unsigned long long)*num > cap) return;  // overflow: ranges stay empty
+    const unsigned long long M = *num;
     for (unsigned long long i = (unsigned long long)blockIdx.x * 256 + threadIdx.x; i < M;
          i += (unsigned long long)gridDim.x * 256) {
         const uint32_t t = (uint32_t)(keys[i] >> 32);
@@ -309,96 +497,291 @@ k_ranges(const uint64_t *__restrict__ keys, const uint32_t *num, unsigned long l
     }
 }
 
+__global__ void __launch_bounds__(256)
+k_ranges32(const uint32_t *__restrict__ tiles, const uint32_t *num, unsigned long long cap, uint32_t *__restrict__ ranges) {
+    if ((unsigned long long)*num > cap) return;  // overflow: ranges stay empty
+    const uint32_t M = *num;
+    for (uint32_t i = blockIdx.x * 256 + threadIdx.x; i < M; i += gridDim.x * 256) {
+        const uint32_t t = tiles[i];
+        if (i == 0 || tiles[i - 1] != t) ranges[2 * (size_t)t] = i;
+        if (i == M - 1 || tiles[i + 1] != t) ranges[2 * (size_t)t + 1] = i + 1;
+    }
+}
+
+__global__ void __launch_bounds__(256)
+k_depth_keys(int n, const int *__restrict__ radius, const float *__restrict__ depth, uint32_t *__restrict__ keys) {
+    const int i = blockIdx.x * 256 + threadIdx.x;
+    if (i < n) keys[i] = radius[i] > 0 ? __float_as_uint(depth[i]) : 0xffffffffu;
+}
+
+// 64-bit keys of the sorted instances, one CTA per tile.
+__global__ void __launch_bounds__(256)
+k_keys64(const uint32_t *__restrict__ ranges, const uint32_t *__restrict__ vals, const float *__restrict__ depth,
+         int n, uint64_t *__restrict__ keys) {
+    const uint32_t t = blockIdx.x;
+    const uint32_t a = ranges[2 * t], b = ranges[2 * t + 1];
+    for (uint32_t i = a + threadIdx.x; i < b; i += 256) {
+        const uint32_t v = vals[i];
+        keys[i] = ((uint64_t)t << 32) | (v < (uint32_t)n ? __float_as_uint(depth[v]) : 0u);
+    }
+}
+
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+PassSpec split_bits(int total_bits) {
+    PassSpec ps{};
+    const int tb = std::max(total_bits, 1);
+    ps.passes = (tb + 7) / 8;
+    int shift = 0;
+    for (int p = 0; p < ps.passes; ++p) {
+        const int b = (tb - shift + (ps.passes - p) - 1) / (ps.passes - p);
+        ps.shift[p] = shift;
+        ps.bits[p] = b;
+        shift += b;
+    }
+    return ps;
+}
+
+template <typename K, bool WK>
+cudaError_t launch_pass(const K *kin, const uint32_t *vin, K *kout, uint32_t *vout, const uint32_t *num,
+                        unsigned long long cap, uint64_t grid_instances, int shift, int bits, const uint32_t *base,
+                        uint32_t *lookback, uint32_t *counter, uint32_t *status, cudaStream_t st) {
+    const size_t smem = Staging<K, WK>::bytes;
+    cudaError_t e = cudaFuncSetAttribute(k_onesweep<K, WK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const unsigned n_parts = (unsigned)((grid_instances + kSortTile - 1) / kSortTile);
+    if (n_parts == 0) return cudaSuccess;
+    k_onesweep<K, WK><<<n_parts, kSortThreads, smem, st>>>(kin, vin, kout, vout, num, cap, shift, bits, base, lookback,
+                                                           counter, status);
+    return cudaGetLastError();
+}
 
 }  // namespace
 
-size_t sort_workspace_bytes(int n, uint64_t capacity, int passes) {
+// ---------------------------------------------------------------------------- workspace
+
+namespace {
+struct Layout {
+    size_t total;
+    size_t off[17];
+};
+
+// Offsets of the workspace regions.  Regions 0..9 are data; [zero_begin, zero_end) is zeroed per call.
+Layout layout(int n, uint64_t capacity, int n_tiles, int strategy, int tile_bits) {
     const size_t nb = (size_t)(n + kScanTile - 1) / kScanTile;
-    const size_t n_parts = (capacity + kSortTile - 1) / kSortTile;
+    const size_t parts_cap = (capacity + kSortTile - 1) / kSortTile;
+    const size_t parts_n = ((size_t)n + kSortTile - 1) / kSortTile;
+    Layout L{};
     size_t b = 0;
-    b += align256(capacity * 8);
-    b += align256(capacity * 4);
-    b += align256(nb * 4);
-    b += align256(nb * 8);
-    b += (size_t)kMaxPasses * 256 * 4 * 2;
-    b += (size_t)passes * n_parts * 256 * 4;
-    b += align256((size_t)kMaxPasses * 4);
-    return b + 256;
-}
-
-SortWorkspace carve_sort_workspace(void *base, int n, uint64_t capacity, int passes) {
-    const size_t nb = (size_t)(n + kScanTile - 1) / kScanTile;
-    const size_t n_parts = (capacity + kSortTile - 1) / kSortTile;
-    unsigned char *p = reinterpret_cast<unsigned char *>(base);
-    SortWorkspace w;
-    w.keys_alt = reinterpret_cast<uint64_t *>(p);
-    p += align256(capacity * 8);
-    w.vals_alt = reinterpret_cast<uint32_t *>(p);
-    p += align256(capacity * 4);
-    w.block_sums = reinterpret_cast<uint32_t *>(p);
-    p += align256(nb * 4);
-    w.block_offsets = reinterpret_cast<uint32_t *>(p);
-    p += align256(nb * 8);
-    unsigned char *zero0 = p;
-    w.hist = reinterpret_cast<uint32_t *>(p);
-    p += (size_t)kMaxPasses * 256 * 4;
-    w.digit_base = reinterpret_cast<uint32_t *>(p);
-    p += (size_t)kMaxPasses * 256 * 4;
-    w.lookback = reinterpret_cast<uint32_t *>(p);
-    p += (size_t)passes * n_parts * 256 * 4;
-    w.part_counter = reinterpret_cast<uint32_t *>(p);
-    p += (size_t)kMaxPasses * 4;
-    w.zero_bytes = (size_t)(p - zero0);
-    return w;
-}
-
-cudaError_t launch_count_instances(int n, const uint32_t *tiles_touched, const SortWorkspace &ws,
-                                   uint32_t *num_instances, uint32_t *status, uint64_t capacity,
-                                   cudaStream_t st) {
-    const int nb = (n + kScanTile - 1) / kScanTile;
-    if (nb > 0) k_block_sums<<<nb, kScanThreads, 0, st>>>(n, tiles_touched, ws.block_sums);
-    k_scan_block_sums<<<1, 1024, 0, st>>>(nb, ws.block_sums, reinterpret_cast<unsigned long long *>(ws.block_offsets),
-                                          num_instances, status, (unsigned long long)capacity);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_duplicate_and_sort(int n, const uint32_t *tiles_touched, const int4 *rect,
-                                      const float *depth, int tiles_x, int tile_bits,
-                                      uint64_t capacity, uint64_t grid_instances,
-                                      const SortWorkspace &ws, uint64_t *keys, uint32_t *values,
-                                      uint32_t *ranges, const uint32_t *num_instances,
-                                      uint32_t *status, cudaStream_t st) {
-    const int bits = 32 + tile_bits;
-    const int passes = (bits + 7) / 8;
-    const int nb = (n + kScanTile - 1) / kScanTile;
-    // the last pass must land in (keys, values)
-    uint64_t *ka = (passes % 2 == 0) ? keys : ws.keys_alt;
-    uint32_t *va = (passes % 2 == 0) ? values : ws.vals_alt;
-    uint64_t *kb = (passes % 2 == 0) ? ws.keys_alt : keys;
-    uint32_t *vb = (passes % 2 == 0) ? ws.vals_alt : values;
-    if (nb > 0)
-        k_duplicate<<<nb, kScanThreads, 0, st>>>(n, tiles_touched, reinterpret_cast<const unsigned long long *>(ws.block_offsets),
-                                                 rect, depth, tiles_x, (unsigned long long)capacity, ka, va);
-    if (grid_instances == 0) return cudaGetLastError();
-    const int hist_blocks = (int)std::min<uint64_t>((grid_instances + 255) / 256, 152 * 8);
-    k_sort_hist<<<hist_blocks, 256, 0, st>>>(ka, num_instances, (unsigned long long)capacity, passes, ws.hist);
-    k_hist_scan<<<passes, 256, 0, st>>>(ws.hist, ws.digit_base);
-    const int smem = kSortTile * 12;
-    cudaError_t e = cudaFuncSetAttribute(k_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    const unsigned n_parts = (unsigned)((grid_instances + kSortTile - 1) / kSortTile);
-    const size_t lb_stride = (size_t)((capacity + kSortTile - 1) / kSortTile) * 256;
-    for (int p = 0; p < passes; ++p) {
-        k_onesweep<<<n_parts, kSortThreads, smem, st>>>(ka, va, kb, vb, num_instances, (unsigned long long)capacity,
-                                                        8 * p, ws.digit_base + p * 256, ws.lookback + p * lb_stride,
-                                                        ws.part_counter + p, status);
-        std::swap(ka, kb);
-        std::swap(va, vb);
+    auto put = [&](int i, size_t bytes) {
+        L.off[i] = b;
+        b += align256(bytes);
+    };
+    if (strategy == DARB_SORT_KEYS64) {
+        const int passes = (32 + tile_bits + 7) / 8;
+        put(0, capacity * 8);  // keys_alt
+        put(1, capacity * 4);  // vals_alt
+        put(2, 0);
+        put(3, 0);
+        put(4, 0);
+        put(5, 0);
+        put(6, nb * 4);        // block sums
+        put(7, nb * 8);        // block offsets
+        put(8, 0);
+        put(15, 0);
+        put(9, (size_t)kMaxPasses * 256 * 4);  // digit bases
+        put(10, (size_t)kMaxPasses * 256 * 4); // --- zeroed from here: histograms
+        put(11, (size_t)passes * parts_cap * 256 * 4);  // look-back
+        put(12, 0);
+        put(13, (size_t)kMaxPasses * 4 * 2);   // partition counters
+    } else {
+        const int passes = split_bits(tile_bits).passes;
+        put(0, capacity * 4);  // tile keys A
+        put(1, capacity * 4);  // values A
+        put(2, capacity * 4);  // tile keys B
+        put(3, capacity * 4);  // values B
+        put(4, (size_t)n * 4 * 2);  // depth keys ping-pong
+        put(5, (size_t)n * 4 * 2);  // depth values ping-pong (sorted order ends here)
+        put(6, nb * 4);
+        put(7, nb * 8);
+        put(8, (size_t)kMaxPasses * 256 * 4);  // tile digit bases
+        put(9, (size_t)kMaxPasses * 256 * 4);  // depth digit bases
+        put(15, ((size_t)n + 1) * 4);           // per-position instance offsets in depth order
+        put(10, (size_t)2 * kMaxPasses * 256 * 4);  // --- zeroed: tile-pass + depth-pass histograms
+        put(11, (size_t)passes * parts_cap * 256 * 4);  // tile-pass look-back
+        put(12, (size_t)4 * parts_n * 256 * 4);         // depth-pass look-back
+        put(13, (size_t)kMaxPasses * 4 * 2);            // partition counters
     }
-    const int rblocks = (int)std::min<uint64_t>((grid_instances + 255) / 256, 152 * 16);
-    k_ranges<<<rblocks, 256, 0, st>>>(ka, num_instances, (unsigned long long)capacity, ranges);
-    return cudaGetLastError();
+    L.off[14] = b;
+    L.total = b + 256;
+    return L;
+}
+}  // namespace
+
+int sort_tile_bits(int n_tiles) { return log2_ceil((uint32_t)n_tiles); }
+
+size_t sort_workspace_bytes(int n, uint64_t capacity, int n_tiles, int strategy) {
+    return layout(n, capacity, n_tiles, strategy, sort_tile_bits(n_tiles)).total;
+}
+
+cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int n_tiles, uint64_t capacity,
+                            int strategy, void *workspace, const BinOut &out, uint64_t *num_instances_host,
+                            bool *capacity_exceeded, cudaStream_t st) {
+    const int tile_bits = sort_tile_bits(n_tiles);
+    const Layout L = layout(n, capacity, n_tiles, strategy, tile_bits);
+    unsigned char *w = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(workspace) + 255) & ~(uintptr_t)255);
+    auto at = [&](int i) { return reinterpret_cast<void *>(w + L.off[i]); };
+    const int nb = (n + kScanTile - 1) / kScanTile;
+    const unsigned long long cap = capacity;
+    *capacity_exceeded = false;
+    cudaError_t e;
+#define TRY(x)                          \
+    do {                                \
+        e = (x);                        \
+        if (e != cudaSuccess) return e; \
+    } while (0)
+    TRY(cudaMemsetAsync(at(10), 0, L.off[14] - L.off[10], st));
+    TRY(cudaMemsetAsync(out.status, 0, sizeof(uint32_t), st));
+    TRY(cudaMemsetAsync(out.ranges, 0, (size_t)n_tiles * 2 * sizeof(uint32_t), st));
+    uint32_t *block_sums = reinterpret_cast<uint32_t *>(at(6));
+    auto *block_off = reinterpret_cast<unsigned long long *>(at(7));
+    uint32_t *counters = reinterpret_cast<uint32_t *>(at(13));
+
+    if (strategy == DARB_SORT_KEYS64) {
+        if (nb > 0) k_block_sums<<<nb, kScanThreads, 0, st>>>(n, proj.tiles_touched, nullptr, block_sums);
+        k_scan_block_sums<<<1, 1024, 0, st>>>(nb, block_sums, block_off, out.num_instances, out.status, cap);
+        TRY(cudaGetLastError());
+        uint64_t grid = capacity;
+        if (num_instances_host) {
+            uint32_t M = 0;
+            TRY(cudaMemcpyAsync(&M, out.num_instances, 4, cudaMemcpyDeviceToHost, st));
+            TRY(cudaStreamSynchronize(st));
+            *num_instances_host = M;
+            if (M > capacity) {
+                *capacity_exceeded = true;
+                return cudaSuccess;
+            }
+            grid = M;
+        }
+        const int passes = (32 + tile_bits + 7) / 8;
+        uint64_t *ka = (passes % 2 == 0) ? out.keys : reinterpret_cast<uint64_t *>(at(0));
+        uint32_t *va = (passes % 2 == 0) ? out.values : reinterpret_cast<uint32_t *>(at(1));
+        uint64_t *kb = (passes % 2 == 0) ? reinterpret_cast<uint64_t *>(at(0)) : out.keys;
+        uint32_t *vb = (passes % 2 == 0) ? reinterpret_cast<uint32_t *>(at(1)) : out.values;
+        if (nb > 0)
+            k_duplicate<<<nb, kScanThreads, 0, st>>>(n, proj.tiles_touched, block_off, proj.tile_rect, proj.depth,
+                                                     tiles_x, cap, ka, va);
+        if (grid == 0) return cudaGetLastError();
+        PassSpec ps{};
+        ps.passes = passes;
+        for (int p = 0; p < passes; ++p) {
+            ps.shift[p] = 8 * p;
+            ps.bits[p] = 8;
+        }
+        uint32_t *hist = reinterpret_cast<uint32_t *>(at(10));
+        uint32_t *dbase = reinterpret_cast<uint32_t *>(at(9));
+        const int hb = (int)std::min<uint64_t>((grid + 255) / 256, 152 * 8);
+        k_sort_hist<uint64_t><<<hb, 256, 0, st>>>(ka, out.num_instances, cap, ps, hist);
+        k_hist_scan<<<passes, 256, 0, st>>>(hist, dbase);
+        TRY(cudaGetLastError());
+        const size_t lb_stride = ((capacity + kSortTile - 1) / kSortTile) * 256;
+        uint32_t *lb = reinterpret_cast<uint32_t *>(at(11));
+        for (int p = 0; p < passes; ++p) {
+            TRY((launch_pass<uint64_t, true>(ka, va, kb, vb, out.num_instances, cap, grid, 8 * p, 8, dbase + p * 256,
+                                             lb + p * lb_stride, counters + p, out.status, st)));
+            std::swap(ka, kb);
+            std::swap(va, vb);
+        }
+        const int rb = (int)std::min<uint64_t>((grid + 255) / 256, 152 * 16);
+        k_ranges<<<rb, 256, 0, st>>>(ka, out.num_instances, cap, out.ranges);
+        return cudaGetLastError();
+    }
+
+    // DEPTH_THEN_TILE: 1) depth order of the splats (4 stable 8-bit passes over N keys)
+    uint32_t *kbuf[2] = {reinterpret_cast<uint32_t *>(at(4)), reinterpret_cast<uint32_t *>(at(4)) + n};
+    uint32_t *vbuf[2] = {reinterpret_cast<uint32_t *>(at(5)), reinterpret_cast<uint32_t *>(at(5)) + n};
+    const uint32_t *order = nullptr;  // sorted splat ids
+    if (n > 0) {
+        const PassSpec dps = split_bits(32);
+        uint32_t *dhist = reinterpret_cast<uint32_t *>(at(10)) + kMaxPasses * 256;
+        uint32_t *dbase = reinterpret_cast<uint32_t *>(at(9));
+        k_depth_keys<<<(n + 255) / 256, 256, 0, st>>>(n, proj.radius, proj.depth, kbuf[0]);
+        const int hb = std::min((n + 255) / 256, 152 * 8);
+        k_sort_hist<uint32_t><<<hb, 256, 0, st>>>(kbuf[0], nullptr, (unsigned long long)n, dps, dhist);
+        k_hist_scan<<<dps.passes, 256, 0, st>>>(dhist, dbase);
+        TRY(cudaGetLastError());
+        uint32_t *lbd = reinterpret_cast<uint32_t *>(at(12));
+        const size_t lbd_stride = (((size_t)n + kSortTile - 1) / kSortTile) * 256;
+        const uint32_t *vin = nullptr;  // first pass: values are the splat indices
+        int cur = 0;
+        for (int p = 0; p < dps.passes; ++p) {
+            const int nxt = 1 - cur;
+            if (p == dps.passes - 1)
+                TRY((launch_pass<uint32_t, false>(kbuf[cur], vin, nullptr, vbuf[nxt], nullptr, (unsigned long long)n,
+                                                  (uint64_t)n, dps.shift[p], dps.bits[p], dbase + p * 256,
+                                                  lbd + p * lbd_stride, counters + kMaxPasses + p, out.status, st)));
+            else
+                TRY((launch_pass<uint32_t, true>(kbuf[cur], vin, kbuf[nxt], vbuf[nxt], nullptr, (unsigned long long)n,
+                                                 (uint64_t)n, dps.shift[p], dps.bits[p], dbase + p * 256,
+                                                 lbd + p * lbd_stride, counters + kMaxPasses + p, out.status, st)));
+            vin = vbuf[nxt];
+            cur = nxt;
+        }
+        order = vin;
+    }
+    // 2) scan of tiles_touched in depth order
+    if (nb > 0) k_block_sums<<<nb, kScanThreads, 0, st>>>(n, proj.tiles_touched, order, block_sums);
+    k_scan_block_sums<<<1, 1024, 0, st>>>(nb, block_sums, block_off, out.num_instances, out.status, cap);
+    TRY(cudaGetLastError());
+    uint64_t grid = capacity;
+    if (num_instances_host) {
+        uint32_t M = 0;
+        TRY(cudaMemcpyAsync(&M, out.num_instances, 4, cudaMemcpyDeviceToHost, st));
+        TRY(cudaStreamSynchronize(st));
+        *num_instances_host = M;
+        if (M > capacity) {
+            *capacity_exceeded = true;
+            return cudaSuccess;
+        }
+        grid = M;
+    }
+    // 3) per-position offsets, then the balanced duplication with the tile-pass histograms
+    uint32_t *tk_a = reinterpret_cast<uint32_t *>(at(0)), *tv_a = reinterpret_cast<uint32_t *>(at(1));
+    uint32_t *tk_b = reinterpret_cast<uint32_t *>(at(2)), *tv_b = reinterpret_cast<uint32_t *>(at(3));
+    uint32_t *offs = reinterpret_cast<uint32_t *>(at(15));
+    const PassSpec tps = split_bits(tile_bits);
+    uint32_t *thist = reinterpret_cast<uint32_t *>(at(10));
+    uint32_t *tbase = reinterpret_cast<uint32_t *>(at(8));
+    if (nb > 0) k_splat_offsets<<<nb, kScanThreads, 0, st>>>(n, order, proj.tiles_touched, block_off, out.num_instances, offs);
+    if (grid > 0 && n > 0) {
+        const unsigned dup_blocks = (unsigned)((grid + kDupTile - 1) / kDupTile);
+        k_duplicate_balanced<<<dup_blocks, kScanThreads, 0, st>>>(n, order, offs, proj.tile_rect, tiles_x,
+                                                                  out.num_instances, cap, tps, tk_a, tv_a, thist);
+    }
+    k_hist_scan<<<tps.passes, 256, 0, st>>>(thist, tbase);
+    TRY(cudaGetLastError());
+    // 4) stable LSD passes over the tile ids (the last writes the values to the output)
+    if (grid > 0) {
+        uint32_t *lb = reinterpret_cast<uint32_t *>(at(11));
+        const size_t lb_stride = ((capacity + kSortTile - 1) / kSortTile) * 256;
+        uint32_t *ka = tk_a, *va = tv_a, *kb = tk_b, *vb = tv_b;
+        for (int p = 0; p < tps.passes; ++p) {
+            uint32_t *vo = (p == tps.passes - 1) ? out.values : vb;
+            TRY((launch_pass<uint32_t, true>(ka, va, kb, vo, out.num_instances, cap, grid, tps.shift[p], tps.bits[p],
+                                             tbase + p * 256, lb + p * lb_stride, counters + p, out.status, st)));
+            std::swap(ka, kb);
+            va = vo;
+            vb = (vo == tv_b) ? tv_a : tv_b;
+        }
+        // 5) ranges from the sorted tile ids (in ka), optional 64-bit keys
+        const int rb = (int)std::min<uint64_t>((grid + 255) / 256, 152 * 16);
+        k_ranges32<<<rb, 256, 0, st>>>(ka, out.num_instances, cap, out.ranges);
+        if (out.keys) k_keys64<<<n_tiles, 256, 0, st>>>(out.ranges, out.values, proj.depth, n, out.keys);
+        TRY(cudaGetLastError());
+    }
+    return cudaSuccess;
+#undef TRY
 }
 
 }  // namespace darb

@@ -36,30 +36,28 @@ constexpr int kSortItems = 16;
 constexpr int kSortTile = kSortThreads * kSortItems;  // keys per onesweep partition
 constexpr int kMaxPasses = 8;
 
-struct SortWorkspace {
-    uint64_t *keys_alt;
-    uint32_t *vals_alt;
-    uint32_t *block_sums;     // [nb]
-    uint32_t *block_offsets;  // [nb]
-    uint32_t *hist;           // [kMaxPasses][256]
-    uint32_t *digit_base;     // [kMaxPasses][256]
-    uint32_t *lookback;       // [passes][n_parts][256]
-    uint32_t *part_counter;   // [kMaxPasses]
-    size_t zero_bytes;        // bytes from hist to the end of part_counter, zeroed per call
+struct ProjectedIn {
+    const float *depth;
+    const int *radius;
+    const int4 *tile_rect;
+    const uint32_t *tiles_touched;
 };
 
-size_t sort_workspace_bytes(int n, uint64_t capacity, int passes);
-SortWorkspace carve_sort_workspace(void *base, int n, uint64_t capacity, int passes);
+struct BinOut {
+    uint64_t *keys;  // may be null for DARB_SORT_DEPTH_THEN_TILE
+    uint32_t *values;
+    uint32_t *ranges;
+    uint32_t *num_instances;
+    uint32_t *status;
+};
 
-cudaError_t launch_count_instances(int n, const uint32_t *tiles_touched, const SortWorkspace &ws,
-                                   uint32_t *num_instances, uint32_t *status, uint64_t capacity,
-                                   cudaStream_t st);
-cudaError_t launch_duplicate_and_sort(int n, const uint32_t *tiles_touched, const int4 *rect,
-                                      const float *depth, int tiles_x, int tile_bits,
-                                      uint64_t capacity, uint64_t grid_instances,
-                                      const SortWorkspace &ws, uint64_t *keys, uint32_t *values,
-                                      uint32_t *ranges, const uint32_t *num_instances,
-                                      uint32_t *status, cudaStream_t st);
+int sort_tile_bits(int n_tiles);
+size_t sort_workspace_bytes(int n, uint64_t capacity, int n_tiles, int strategy);
+// Enqueues the whole bin/sort.  With num_instances_host non-null it synchronises once after the
+// scan; if M exceeds the capacity it sets *capacity_exceeded and enqueues nothing more.
+cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int n_tiles, uint64_t capacity,
+                            int strategy, void *workspace, const BinOut &out, uint64_t *num_instances_host,
+                            bool *capacity_exceeded, cudaStream_t st);
 
 // render.cu
 cudaError_t launch_render_fwd(int kind, int tile, int tiles_x, int tiles_y, const uint32_t *ranges,

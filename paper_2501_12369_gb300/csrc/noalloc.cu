@@ -43,12 +43,12 @@ extern "C" darb_status darb_bin_sort_noalloc(const darb_projected *proj, int32_t
                                              const darb_camera *cam, uint64_t capacity, const darb_binning *out,
                                              uint64_t *num_instances_host, darb_stream stream) {
     size_t need = 0;
-    const darb_status qs = darb_bin_sort_workspace_size(n, tile, cam, capacity, &need);
+    const darb_status qs = darb_bin_sort_workspace_size(n, tile, cam, capacity, DARB_SORT_DEPTH_THEN_TILE, &need);
     if (qs != DARB_OK) return qs;
     if (need > kNoAllocScratchBytes) return DARB_ERR_WORKSPACE;  // beyond the static scratch
     void *scratch = nullptr;
     const darb_status as = scratch_address(&scratch);
     if (as != DARB_OK) return as;
-    return darb_bin_sort(proj, n, tile, cam, scratch, kNoAllocScratchBytes, capacity, out, num_instances_host,
-                         stream);
+    return darb_bin_sort(proj, n, tile, cam, scratch, kNoAllocScratchBytes, capacity, DARB_SORT_DEPTH_THEN_TILE, out,
+                         num_instances_host, stream);
 }

@@ -81,10 +81,10 @@ SIGNATURES = {
     "darb_tile_grid": (c_i32, [_P(darb_camera), c_i32, _P(c_i32), _P(c_i32)]),
     "darb_preprocess": (c_i32, [_P(darb_splats), _P(darb_camera), _P(darb_kernel_params), c_i32,
                                 _P(darb_projected), c_vp]),
-    "darb_bin_sort_workspace_size": (c_i32, [c_i32, c_i32, _P(darb_camera), ctypes.c_uint64,
+    "darb_bin_sort_workspace_size": (c_i32, [c_i32, c_i32, _P(darb_camera), ctypes.c_uint64, c_i32,
                                              _P(ctypes.c_size_t)]),
     "darb_bin_sort": (c_i32, [_P(darb_projected), c_i32, c_i32, _P(darb_camera), c_vp, ctypes.c_size_t,
-                              ctypes.c_uint64, _P(darb_binning), _P(ctypes.c_uint64), c_vp]),
+                              ctypes.c_uint64, c_i32, _P(darb_binning), _P(ctypes.c_uint64), c_vp]),
     "darb_bin_sort_noalloc": (c_i32, [_P(darb_projected), c_i32, c_i32, _P(darb_camera), ctypes.c_uint64,
                                       _P(darb_binning), _P(ctypes.c_uint64), c_vp]),
     "darb_render_fwd": (c_i32, [_P(darb_projected), _P(darb_binning), _P(darb_camera), _P(darb_kernel_params),
@@ -274,23 +274,27 @@ def darb_preprocess(splats: SplatTensors, cam, kparams, tile=16, out: Projected 
     return out
 
 
-def darb_bin_sort_workspace_size(n, tile, cam, capacity) -> int:
+DARB_SORT_DEPTH_THEN_TILE = 0
+DARB_SORT_KEYS64 = 1
+
+
+def darb_bin_sort_workspace_size(n, tile, cam, capacity, strategy=DARB_SORT_DEPTH_THEN_TILE) -> int:
     b = ctypes.c_size_t()
     _check(lib().darb_bin_sort_workspace_size(int(n), int(tile), ctypes.byref(camera(cam)), int(capacity),
-                                              ctypes.byref(b)), "darb_bin_sort_workspace_size")
+                                              int(strategy), ctypes.byref(b)), "darb_bin_sort_workspace_size")
     return int(b.value)
 
 
 def darb_bin_sort(proj: Projected, n, tile, cam, workspace: torch.Tensor, capacity, out: Binning | None = None,
-                  sync=True, stream=None):
+                  sync=True, stream=None, strategy=DARB_SORT_DEPTH_THEN_TILE):
     """sync=True reads M back (one stream synchronisation) and sizes the sort by it."""
     tx, ty = darb_tile_grid(cam, tile)
     out = Binning.empty(capacity, tx * ty, workspace.device) if out is None else out
     pr, c, b = proj.struct(), camera(cam), out.struct()
     m = ctypes.c_uint64(0)
     st = lib().darb_bin_sort(ctypes.byref(pr), int(n), int(tile), ctypes.byref(c), _p(workspace),
-                             workspace.numel() * workspace.element_size(), int(capacity), ctypes.byref(b),
-                             ctypes.byref(m) if sync else None, _stream(stream))
+                             workspace.numel() * workspace.element_size(), int(capacity), int(strategy),
+                             ctypes.byref(b), ctypes.byref(m) if sync else None, _stream(stream))
     out.M = int(m.value) if sync else None
     _check(st, "darb_bin_sort")
     return out
@@ -380,8 +384,10 @@ def darb_adam_step(params, grads: SplatGrads, state, cfg: darb_adam_config, stre
 class Rasterizer:
     """Holds the per-view buffers of one camera configuration and runs the four steps."""
 
-    def __init__(self, cam, kernel="half_cosine", tile=16, capacity=None, device="cuda", psi=None):
+    def __init__(self, cam, kernel="half_cosine", tile=16, capacity=None, device="cuda", psi=None,
+                 strategy=DARB_SORT_DEPTH_THEN_TILE):
         self.cam = cam
+        self.strategy = int(strategy)
         self.tile = int(tile)
         self.kparams = darb_kernel_defaults(kernel)
         if psi is not None:
@@ -396,7 +402,7 @@ class Rasterizer:
     def _ensure(self, n, capacity):
         if capacity > self.capacity or self._ws is None or n != self._n:
             self.capacity = max(capacity, self.capacity)
-            nbytes = darb_bin_sort_workspace_size(n, self.tile, self.cam, self.capacity)
+            nbytes = darb_bin_sort_workspace_size(n, self.tile, self.cam, self.capacity, self.strategy)
             self._ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
             self._bins = Binning.empty(self.capacity, self.tiles_x * self.tiles_y, self.device)
             self._n = n
@@ -407,12 +413,14 @@ class Rasterizer:
             self.capacity = max(1024, 8 * splats.n)
         self._ensure(splats.n, self.capacity)
         try:
-            bins = darb_bin_sort(proj, splats.n, self.tile, self.cam, self._ws, self.capacity, self._bins)
+            bins = darb_bin_sort(proj, splats.n, self.tile, self.cam, self._ws, self.capacity, self._bins,
+                                 strategy=self.strategy)
         except DarbError as e:
             if e.status != 3:
                 raise
             self._ensure(splats.n, int(self._bins.M * 1.25) + 1)
-            bins = darb_bin_sort(proj, splats.n, self.tile, self.cam, self._ws, self.capacity, self._bins)
+            bins = darb_bin_sort(proj, splats.n, self.tile, self.cam, self._ws, self.capacity, self._bins,
+                                 strategy=self.strategy)
         img = darb_render_fwd(proj, bins, self.cam, self.kparams, self.tile)
         return proj, bins, img
 

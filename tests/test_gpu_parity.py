@@ -50,13 +50,34 @@ def test_preprocess_is_bit_exact_clusters(deg):
 
 # --------------------------------------------------------------------------- steps 2-3
 
+@pytest.mark.parametrize("strategy", [darb.DARB_SORT_DEPTH_THEN_TILE, darb.DARB_SORT_KEYS64])
 @pytest.mark.parametrize("tile", [8, 16, 32])
-def test_bin_sort_is_bit_exact(tile):
+def test_bin_sort_is_bit_exact(tile, strategy):
     s, cam = _medium_scene()
     s.means[::50] = s.means[7]  # coincident splats: equal keys must keep splat order
-    r, sd, proj, bins, img = gpu_forward(s, cam, "half_cosine", tile)
+    s.means[1::97, 2] = s.means[5, 2]  # equal depths across different tiles
+    r = darb.Rasterizer(cam, "half_cosine", tile, strategy=strategy)
+    proj, bins, img = r.forward(darb.splats_to_device(s))
+    torch.cuda.synchronize()
     ref = oracle.project(s, cam, oracle.kernel_params("half_cosine"), tile, True)
     check_lists(bins, oracle.build_lists(ref, cam, tile))
+
+
+def test_bin_sort_strategies_agree_on_a_large_scene():
+    s = synth.cluster_scene(300_000, seed=11)
+    cam = synth.fibonacci_cameras(10, 6.0, 1280, 720, 1000.0)[4]
+    out = []
+    for strategy in (darb.DARB_SORT_DEPTH_THEN_TILE, darb.DARB_SORT_KEYS64):
+        r = darb.Rasterizer(cam, "gaussian", 16, strategy=strategy)
+        proj, bins, img = r.forward(darb.splats_to_device(s))
+        torch.cuda.synchronize()
+        M = bins.M
+        out.append((M, to_np(bins.keys)[:M].copy(), to_np(bins.values)[:M].copy(), to_np(bins.ranges).copy(),
+                    to_np(img.image).copy()))
+    a, b = out
+    assert a[0] == b[0] and a[0] > 1_000_000
+    for x, y in zip(a[1:], b[1:]):
+        assert np.array_equal(x, y)
 
 
 def test_bin_sort_async_capacity_mode_matches_sync():
@@ -68,6 +89,7 @@ def test_bin_sort_async_capacity_mode_matches_sync():
     ws = torch.empty(darb.darb_bin_sort_workspace_size(s.n, 16, cam, cap), dtype=torch.uint8, device="cuda")
     a = darb.darb_bin_sort(proj, s.n, 16, cam, ws, cap, sync=True)
     M = a.M
+    assert M > 0
     ka, va, ra = to_np(a.keys)[:M].copy(), to_np(a.values)[:M].copy(), to_np(a.ranges).copy()
     b = darb.darb_bin_sort(proj, s.n, 16, cam, ws, cap, sync=False)
     torch.cuda.synchronize()
@@ -89,6 +111,7 @@ def test_bin_sort_reports_capacity_overflow():
     b = darb.darb_bin_sort(proj, s.n, 16, cam, ws, cap, sync=False)  # async: flagged on the device
     torch.cuda.synchronize()
     assert int(to_np(b.status)[0]) == 3 and int(to_np(b.num_instances)[0]) > cap
+    assert np.all(to_np(b.ranges) == 0)  # nothing to composite after an overflow
     small = torch.empty(16, dtype=torch.uint8, device="cuda")
     with pytest.raises(darb.DarbError) as e:
         darb.darb_bin_sort(proj, s.n, 16, cam, small, cap)
@@ -220,3 +243,64 @@ def test_tiny_and_odd_images():
         for tile in (8, 16, 32):
             r, sd, proj, bins, img = gpu_forward(s, cam, "parabola", tile)
             check_render(img, bins, oracle.forward(s, cam, "parabola", tile=tile), cam, tile)
+
+
+# --------------------------------------------------------------------------- full sizes
+
+def _tile_pixel_mask(cam, tile, tiles):
+    tx = (cam.width + tile - 1) // tile
+    m = np.zeros((cam.height, cam.width), bool)
+    for t in tiles:
+        y0, x0 = (t // tx) * tile, (t % tx) * tile
+        m[y0:y0 + tile, x0:x0 + tile] = True
+    return m
+
+
+def test_full_size_training_view_on_sampled_tiles():
+    """3M splats, 1920x1080, half-cosine, 16-pixel tiles, default sort -- the configuration the
+    benchmark times.  Preprocess is compared for every splat; lists, pixels and gradients on a
+    seeded sample of 24 occupied tiles (the upstream gradient is zero elsewhere, so every splat's
+    gradient is exactly the contribution of those tiles on both sides)."""
+    splats, cams = synth.scene_3m_1080p(num_cameras=100)
+    cam, tile, kernel = cams[0], 16, "half_cosine"
+    r, sd, proj, bins, img = gpu_forward(splats, cam, kernel, tile)
+    kp = oracle.kernel_params(kernel)
+    ref_p = oracle.project(splats, cam, kp, tile, True)
+    check_preprocess(proj, ref_p)
+    ranges = to_np(bins.ranges)
+    occupied = np.flatnonzero(ranges[:, 1] > ranges[:, 0])
+    rng = np.random.default_rng(7)
+    tiles = np.sort(rng.choice(occupied, 24, replace=False))
+    mask = np.zeros(ranges.shape[0], np.uint8)
+    mask[tiles] = 1
+    lists = oracle.build_lists(ref_p, cam, tile, mask)
+    check_lists(bins, lists, mask)
+    ref_f = oracle.render(ref_p, cam, kp, tile, "tiled", lists, mask)
+    pmask = _tile_pixel_mask(cam, tile, tiles)
+    check_render(img, bins, ref_f, cam, tile, pixel_mask=pmask)
+    dl = synth.random_image_grad(cam.height, cam.width, seed=5)
+    dl[:, ~pmask] = 0.0
+    dl = ambiguity_masked_grad(dl, ref_f["amb"]).astype(np.float32)
+    g, g2 = r.backward(sd, proj, bins, img, torch.from_numpy(dl).cuda())
+    torch.cuda.synchronize()
+    g2_ref = oracle.render_backward(ref_p, cam, kp, lists, dl.astype(np.float64), tile, mask)
+    touched = np.flatnonzero(np.abs(g2_ref).sum(1) > 0)
+    assert len(touched) > 100
+    g2n = to_np(g2)
+    for j, name in enumerate(G2_NAMES):
+        grad_close(f"3M/{name}", g2n[:, j], g2_ref[:, j])
+    gp_ref = oracle.project_backward(splats, ref_p, cam, kp, g2_ref)
+    for name, got in (("means", g.dmeans), ("scales", g.dscales), ("quats", g.dquats),
+                      ("opacities", g.dopacities), ("sh", g.dsh)):
+        grad_close(f"3M/{name}", to_np(got), gp_ref[name])
+
+
+@pytest.mark.parametrize("kernel", ["gaussian", "half_cosine"])
+def test_500k_720p_forward_and_backward_full_frame(kernel):
+    s, cam = synth.scene_500k_720p()
+    g, g2, g2_ref, gp_ref, *_ = _grads(s, cam, kernel, 16)
+    for name, got in (("means", g.dmeans), ("scales", g.dscales), ("quats", g.dquats),
+                      ("opacities", g.dopacities), ("sh", g.dsh)):
+        grad_close(f"500k/{kernel}/{name}", to_np(got), gp_ref[name])
+    r, sd, proj, bins, img = gpu_forward(s, cam, kernel, 16)
+    check_render(img, bins, oracle.forward(s, cam, kernel, tile=16), cam, 16)

@@ -362,7 +362,7 @@ struct Staging {
 // One stable LSD pass over the digit of `bits` bits at `shift`.  M = min(*num, cap), or cap if
 // num is null.  vin may be null: values are then the input positions (iota).
 template <typename K, bool WRITE_KEYS>
-__global__ void __launch_bounds__(kSortThreads)
+__global__ void __launch_bounds__(kSortThreads, 3)
 k_onesweep(const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__restrict__ kout,
            uint32_t *__restrict__ vout, const uint32_t *num, unsigned long long cap, int shift, int bits,
            const uint32_t *__restrict__ digit_base, uint32_t *lookback, uint32_t *part_counter, uint32_t *status) {
@@ -405,10 +405,14 @@ k_onesweep(const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__res
         }
     }
     const uint32_t lt = lanemask_lt();
+    // Peer masks first (independent, so they pipeline), then the per-warp running counts:
+    // rk holds the peer mask until it is replaced by the rank.
+#pragma unroll
+    for (int it = 0; it < kSortItems; ++it) rk[it] = __match_any_sync(0xffffffffu, (uint32_t)(k[it] >> shift) & mask);
 #pragma unroll
     for (int it = 0; it < kSortItems; ++it) {
         const uint32_t d = (uint32_t)(k[it] >> shift) & mask;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t peers = rk[it];
         const uint32_t prev = s_wh[warp][d];
         rk[it] = prev + __popc(peers & lt);
         __syncwarp();
@@ -434,7 +438,7 @@ k_onesweep(const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__res
         } else {
             st_relaxed(mine, kFlagLocal | cnt);
             int p = (int)part - 1;
-            int spins = 0, ns = 64;
+            int spins = 0, ns = 32;
             while (true) {
                 const uint32_t s = ld_relaxed(lookback + (size_t)p * radix + dg);
                 const uint32_t f = s & ~kCountMask;
@@ -443,8 +447,10 @@ k_onesweep(const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__res
                         atomicExch(status, (uint32_t)DARB_ERR_TIMEOUT);
                         break;
                     }
-                    __nanosleep(ns);
-                    ns = min(ns * 2, 1024);
+                    if (spins > 16) {  // poll busily at first, then back off
+                        __nanosleep(ns);
+                        ns = min(ns * 2, 512);
+                    }
                     continue;
                 }
                 excl += s & kCountMask;

@@ -123,6 +123,24 @@ __device__ __forceinline__ void load_sh(const float *__restrict__ sh, int i, flo
     }
 }
 
+template <int DEG>
+__device__ __forceinline__ void store_sh(float *__restrict__ dsh, int i, const float (*c)[3]) {
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    if constexpr ((K * 3) % 4 == 0) {
+        float4 *p = reinterpret_cast<float4 *>(dsh + (size_t)i * K * 3);
+        float buf[K * 3];
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+            for (int ch = 0; ch < 3; ++ch) buf[3 * k + ch] = c[k][ch];
+#pragma unroll
+        for (int j = 0; j < K * 3 / 4; ++j) p[j] = make_float4(buf[4 * j], buf[4 * j + 1], buf[4 * j + 2], buf[4 * j + 3]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+            for (int ch = 0; ch < 3; ++ch) dsh[((size_t)i * K + k) * 3 + ch] = c[k][ch];
+    }
+}
+
 // The fixed FP32 projection sequence.  Returns false when the splat is culled.
 struct Geom {
     float t[3];
@@ -298,11 +316,13 @@ k_preprocess_bwd(int n, const float *__restrict__ means, const float *__restrict
     if (i >= n) return;
     constexpr int K = (DEG + 1) * (DEG + 1);
     float *dm = out.dmeans + 3 * (size_t)i, *ds = out.dscales + 3 * (size_t)i, *dqo = out.dquats + 4 * (size_t)i;
-    float *dsh = out.dsh + (size_t)K * 3 * i;
     if (radius[i] == 0) {
         for (int j = 0; j < 3; ++j) dm[j] = ds[j] = 0.0f;
-        for (int j = 0; j < 4; ++j) dqo[j] = 0.0f;
-        for (int j = 0; j < K * 3; ++j) dsh[j] = 0.0f;
+        reinterpret_cast<float4 *>(out.dquats)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        float zero[K][3];
+#pragma unroll
+        for (int k = 0; k < K; ++k) zero[k][0] = zero[k][1] = zero[k][2] = 0.0f;
+        store_sh<DEG>(out.dsh, i, zero);
         out.dopacities[i] = 0.0f;
         return;
     }
@@ -420,10 +440,9 @@ k_preprocess_bwd(int n, const float *__restrict__ means, const float *__restrict
     const float gz = 2.f * (-2.f * z * dR[0][0] - w * dR[0][1] + x * dR[0][2] + w * dR[1][0] - 2.f * z * dR[1][1] +
                             y * dR[1][2] + x * dR[2][0] + y * dR[2][1]);
     const float nd = w * gw + x * gx + y * gy + z * gz;
-    dqo[0] = (gw - w * nd) / qn;
-    dqo[1] = (gx - x * nd) / qn;
-    dqo[2] = (gy - y * nd) / qn;
-    dqo[3] = (gz - z * nd) / qn;
+    const float iqn = 1.0f / qn;
+    reinterpret_cast<float4 *>(dqo)[0] =
+        make_float4((gw - w * nd) * iqn, (gx - x * nd) * iqn, (gy - y * nd) * iqn, (gz - z * nd) * iqn);
 
     // SH: coefficients and the viewing direction
     float v0 = m[0] - cam.campos[0], v1 = m[1] - cam.campos[1], v2 = m[2] - cam.campos[2];
@@ -434,15 +453,20 @@ k_preprocess_bwd(int n, const float *__restrict__ means, const float *__restrict
     const uint8_t cl = clamped[i];
     float gr[3];
     for (int ch = 0; ch < 3; ++ch) gr[ch] = ((cl >> ch) & 1) ? 0.f : drgb[ch];
-    float wsum[K];
+    float coef[K][3];
+    load_sh<DEG>(sh, i, coef);
+    float wsum[K], dcoef[K][3];
+#pragma unroll
     for (int k = 0; k < K; ++k) {
         float acc = 0.f;
+#pragma unroll
         for (int ch = 0; ch < 3; ++ch) {
-            dsh[3 * k + ch] = Y[k] * gr[ch];
-            acc += gr[ch] * sh[((size_t)i * K + k) * 3 + ch];
+            dcoef[k][ch] = Y[k] * gr[ch];
+            acc += gr[ch] * coef[k][ch];
         }
         wsum[k] = acc;
     }
+    store_sh<DEG>(out.dsh, i, dcoef);
     float gd[3];
     sh_basis_vjp<DEG>(dir[0], dir[1], dir[2], wsum, gd);
     const float dd = dir[0] * gd[0] + dir[1] * gd[1] + dir[2] * gd[2];

@@ -31,27 +31,77 @@ k_l1_loss(const float *__restrict__ image, const float *__restrict__ target, int
 // act: 0 = identity, 1 = exp (log-scale -> scale), 2 = sigmoid (logit -> opacity).
 // For act != 0 the incoming gradient is w.r.t. the activated value and `activated` holds that
 // value; the raw gradient is g * d(act)/d(raw), and `activated` is refreshed after the step.
-// lr2 applies to the elements whose index within a row of `row` floats is >= split (SH rest).
+template <int ACT>
+__device__ __forceinline__ void adam_elem(float &p, float g, float &m, float &v, float lr, float b1, float b2,
+                                          float eps, float ibc1, float ibc2, float *act_val) {
+    if (ACT == 1) g *= *act_val;
+    if (ACT == 2) g *= *act_val * (1.0f - *act_val);
+    m = fmaf(b1, m, (1.0f - b1) * g);
+    v = fmaf(b2, v, (1.0f - b2) * g * g);
+    p -= lr * (m * ibc1) / (sqrtf(v * ibc2) + eps);
+    if (ACT == 1) *act_val = expf(p);
+    if (ACT == 2) *act_val = 1.0f / (1.0f + expf(-p));
+}
+
+// Flat parameter group, float4 lanes; `row`/`split` select lr2 for the elements whose index
+// within a row of ROW floats is >= SPLIT (the SH coefficients after the DC term).  ROW is a
+// multiple of 4 (or 0 for a single learning rate), so no float4 straddles two rows.
+template <int ACT, int ROW, int SPLIT>
 __global__ void __launch_bounds__(256)
-k_adam(long long count, float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
-       float *__restrict__ v, float lr, float lr2, int row, int split, float b1, float b2, float eps,
-       float bc1, float bc2, int act, float *__restrict__ activated) {
-    for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < count; i += (long long)gridDim.x * 256) {
-        float grad = g[i];
-        if (act == 1) grad *= activated[i];
-        else if (act == 2) {
-            const float o = activated[i];
-            grad *= o * (1.0f - o);
+k_adam4(long long count, float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
+        float *__restrict__ v, float lr, float lr2, float b1, float b2, float eps, float ibc1, float ibc2,
+        float *__restrict__ activated) {
+    const long long n4 = count >> 2;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n4; j += stride) {
+        float4 P = reinterpret_cast<float4 *>(p)[j];
+        const float4 G = reinterpret_cast<const float4 *>(g)[j];
+        float4 Mm = reinterpret_cast<float4 *>(m)[j];
+        float4 V = reinterpret_cast<float4 *>(v)[j];
+        float4 A = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (ACT) A = reinterpret_cast<float4 *>(activated)[j];
+        float lrs[4] = {lr, lr, lr, lr};
+        if (ROW > 0) {
+            const int pos = (int)((j * 4) % ROW);  // ROW is a compile-time constant
+#pragma unroll
+            for (int u = 0; u < 4; ++u) lrs[u] = (pos + u >= SPLIT) ? lr2 : lr;
         }
-        const float mi = b1 * m[i] + (1.0f - b1) * grad;
-        const float vi = b2 * v[i] + (1.0f - b2) * grad * grad;
-        m[i] = mi;
-        v[i] = vi;
-        const float step = (row > 0 && (int)(i % row) >= split) ? lr2 : lr;
-        const float pi = p[i] - step * (mi / bc1) / (sqrtf(vi / bc2) + eps);
-        p[i] = pi;
-        if (act == 1) activated[i] = expf(pi);
-        else if (act == 2) activated[i] = 1.0f / (1.0f + expf(-pi));
+        adam_elem<ACT>(P.x, G.x, Mm.x, V.x, lrs[0], b1, b2, eps, ibc1, ibc2, &A.x);
+        adam_elem<ACT>(P.y, G.y, Mm.y, V.y, lrs[1], b1, b2, eps, ibc1, ibc2, &A.y);
+        adam_elem<ACT>(P.z, G.z, Mm.z, V.z, lrs[2], b1, b2, eps, ibc1, ibc2, &A.z);
+        adam_elem<ACT>(P.w, G.w, Mm.w, V.w, lrs[3], b1, b2, eps, ibc1, ibc2, &A.w);
+        reinterpret_cast<float4 *>(p)[j] = P;
+        reinterpret_cast<float4 *>(m)[j] = Mm;
+        reinterpret_cast<float4 *>(v)[j] = V;
+        if (ACT) reinterpret_cast<float4 *>(activated)[j] = A;
+    }
+    // scalar tail (count % 4 elements)
+    if (blockIdx.x == 0 && threadIdx.x < (count & 3)) {
+        const long long i = (n4 << 2) + threadIdx.x;
+        float pp = p[i], mm = m[i], vv = v[i];
+        float a = ACT ? activated[i] : 0.f;
+        const float l = (ROW > 0 && (int)(i % (ROW > 0 ? ROW : 1)) >= SPLIT) ? lr2 : lr;
+        adam_elem<ACT>(pp, g[i], mm, vv, l, b1, b2, eps, ibc1, ibc2, &a);
+        p[i] = pp;
+        m[i] = mm;
+        v[i] = vv;
+        if (ACT) activated[i] = a;
+    }
+}
+
+// Rows whose length is not a multiple of 4 (SH degrees 0 and 2): scalar lanes.
+template <int ROW, int SPLIT>
+__global__ void __launch_bounds__(256)
+k_adam_rows(long long count, float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
+            float *__restrict__ v, float lr, float lr2, float b1, float b2, float eps, float ibc1, float ibc2) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (long long)gridDim.x * blockDim.x) {
+        float pp = p[i], mm = m[i], vv = v[i];
+        const float l = (int)(i % ROW) >= SPLIT ? lr2 : lr;
+        adam_elem<0>(pp, g[i], mm, vv, l, b1, b2, eps, ibc1, ibc2, nullptr);
+        p[i] = pp;
+        m[i] = mm;
+        v[i] = vv;
     }
 }
 
@@ -75,27 +125,37 @@ cudaError_t launch_adam(const darb_train_params &p, const darb_splat_grads &g, c
                         const darb_adam_config &c, cudaStream_t st) {
     const long long n = p.n;
     if (n == 0) return cudaSuccess;
-    const float bc1 = 1.0f - powf(c.beta1, (float)c.step);
-    const float bc2 = 1.0f - powf(c.beta2, (float)c.step);
+    const float ibc1 = 1.0f / (1.0f - powf(c.beta1, (float)c.step));
+    const float ibc2 = 1.0f / (1.0f - powf(c.beta2, (float)c.step));
+    const float b1 = c.beta1, b2 = c.beta2, eps = c.eps;
     const long long K = (long long)(p.sh_degree + 1) * (p.sh_degree + 1);
-    struct Group {
-        long long count;
-        float *p;
-        const float *g;
-        float *m, *v;
-        float lr, lr2;
-        int row, split, act;
-        float *activated;
-    } groups[5] = {
-        {3 * n, p.means, g.dmeans, s.m_means, s.v_means, c.lr_means, c.lr_means, 0, 0, 0, nullptr},
-        {3 * n, p.log_scales, g.dscales, s.m_scales, s.v_scales, c.lr_scales, c.lr_scales, 0, 0, 1, p.scales},
-        {4 * n, p.quats, g.dquats, s.m_quats, s.v_quats, c.lr_quats, c.lr_quats, 0, 0, 0, nullptr},
-        {n, p.opacity_logits, g.dopacities, s.m_opac, s.v_opac, c.lr_opacities, c.lr_opacities, 0, 0, 2, p.opacities},
-        {3 * K * n, p.sh, g.dsh, s.m_sh, s.v_sh, c.lr_sh_dc, c.lr_sh_rest, (int)(3 * K), 3, 0, nullptr},
-    };
-    for (const Group &gr : groups) {
-        k_adam<<<grid_for(gr.count), 256, 0, st>>>(gr.count, gr.p, gr.g, gr.m, gr.v, gr.lr, gr.lr2, gr.row, gr.split,
-                                                   c.beta1, c.beta2, c.eps, bc1, bc2, gr.act, gr.activated);
+    auto g4 = [](long long count) { return grid_for((count + 3) / 4); };
+    k_adam4<0, 0, 0><<<g4(3 * n), 256, 0, st>>>(3 * n, p.means, g.dmeans, s.m_means, s.v_means, c.lr_means,
+                                                 c.lr_means, b1, b2, eps, ibc1, ibc2, nullptr);
+    k_adam4<1, 0, 0><<<g4(3 * n), 256, 0, st>>>(3 * n, p.log_scales, g.dscales, s.m_scales, s.v_scales, c.lr_scales,
+                                                 c.lr_scales, b1, b2, eps, ibc1, ibc2, p.scales);
+    k_adam4<0, 0, 0><<<g4(4 * n), 256, 0, st>>>(4 * n, p.quats, g.dquats, s.m_quats, s.v_quats, c.lr_quats,
+                                                 c.lr_quats, b1, b2, eps, ibc1, ibc2, nullptr);
+    k_adam4<2, 0, 0><<<g4(n), 256, 0, st>>>(n, p.opacity_logits, g.dopacities, s.m_opac, s.v_opac, c.lr_opacities,
+                                             c.lr_opacities, b1, b2, eps, ibc1, ibc2, p.opacities);
+    const long long cs = 3 * K * n;
+    switch (p.sh_degree) {
+    case 0:
+        k_adam_rows<3, 3><<<grid_for(cs), 256, 0, st>>>(cs, p.sh, g.dsh, s.m_sh, s.v_sh, c.lr_sh_dc, c.lr_sh_rest, b1,
+                                                         b2, eps, ibc1, ibc2);
+        break;
+    case 1:
+        k_adam4<0, 12, 3><<<g4(cs), 256, 0, st>>>(cs, p.sh, g.dsh, s.m_sh, s.v_sh, c.lr_sh_dc, c.lr_sh_rest, b1, b2,
+                                                  eps, ibc1, ibc2, nullptr);
+        break;
+    case 2:
+        k_adam_rows<27, 3><<<grid_for(cs), 256, 0, st>>>(cs, p.sh, g.dsh, s.m_sh, s.v_sh, c.lr_sh_dc, c.lr_sh_rest, b1,
+                                                          b2, eps, ibc1, ibc2);
+        break;
+    default:
+        k_adam4<0, 48, 3><<<g4(cs), 256, 0, st>>>(cs, p.sh, g.dsh, s.m_sh, s.v_sh, c.lr_sh_dc, c.lr_sh_rest, b1, b2,
+                                                  eps, ibc1, ibc2, nullptr);
+        break;
     }
     return cudaGetLastError();
 }

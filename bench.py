@@ -254,9 +254,10 @@ def algorithmic_bytes(stage, n, M, passes, sh_k, strategy=0, tile_passes=2):
         if strategy == 1:
             return n * (4 + 4 + 16 + 4) + M * (12 + 8 + 24 * passes + 8)
         # per splat: depth keys (read depth+radius, write key), 4 depth passes (16 B each), tiles
-        # gathered twice in depth order, offsets written and read, rect; per instance: duplicate
-        # write 8, each tile pass read 8 + write 8, ranges read 4
-        return n * (8 + 4 + 4 * 16 + 8 + 8 + 16) + M * (8 + 16 * tile_passes + 4)
+        # gathered twice in depth order, offsets written and read, rect twice (difference array,
+        # duplicate); per instance: duplicate write 8, each tile pass read 8 + write 8 except the
+        # last, which writes only the 4-byte values
+        return n * (8 + 4 + 4 * 16 + 8 + 8 + 32) + M * (8 + 16 * tile_passes - 4)
     if stage == "preprocess_bwd":
         return n * (12 + 12 + 16 + sh_b + 48 + 4 + 1) + n * (12 + 12 + 16 + 4 + sh_b)
     if stage == "adam":
@@ -464,8 +465,8 @@ def launches_per_step(strategy, tile_bits):
     """Kernels of libdarb.so launched per training step (memsets excluded)."""
     if strategy == 1:  # 64-bit keys: block sums, scan, duplicate, histogram, hist scan, passes, ranges
         sort = 6 + (32 + tile_bits + 7) // 8
-    else:  # depth keys, histogram, hist scan, 4 depth passes, block sums, scan, offsets, duplicate,
-        # tile hist scan, tile passes, ranges
+    else:  # depth keys, histogram, hist scan, 4 depth passes, block sums, scan, tile diff, tile setup,
+        # offsets, duplicate, tile passes
         sort = 3 + 4 + 6 + max(1, (tile_bits + 7) // 8)
     # preprocess, render_fwd, l1, render_bwd, preprocess_bwd, 5 Adam groups
     return 1 + sort + 1 + 1 + 1 + 1 + 5

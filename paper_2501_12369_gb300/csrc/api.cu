@@ -133,8 +133,7 @@ darb_status darb_bin_sort_workspace_size(int32_t n, int32_t tile, const darb_cam
     if (n < 0 || !valid_tile(tile) || !valid_camera(cam) || !bytes || capacity > kMaxCapacity ||
         !valid_strategy(strategy))
         return DARB_ERR_INVALID_ARG;
-    const int n_tiles = tile_count(cam->width, tile) * tile_count(cam->height, tile);
-    *bytes = sort_workspace_bytes(n, capacity, n_tiles, strategy);
+    *bytes = sort_workspace_bytes(n, capacity, tile_count(cam->width, tile), tile_count(cam->height, tile), strategy);
     return DARB_OK;
 }
 
@@ -151,7 +150,7 @@ darb_status darb_bin_sort(const darb_projected *proj, int32_t n, int32_t tile, c
         return DARB_ERR_INVALID_ARG;
     if (n > 0 && !valid_projected(proj)) return DARB_ERR_INVALID_ARG;
     const int tiles_x = tile_count(cam->width, tile), tiles_y = tile_count(cam->height, tile);
-    const size_t need = sort_workspace_bytes(n, capacity, tiles_x * tiles_y, strategy);
+    const size_t need = sort_workspace_bytes(n, capacity, tiles_x, tiles_y, strategy);
     if (!workspace || workspace_bytes < need || !aligned16(workspace)) return DARB_ERR_WORKSPACE;
     ProjectedIn pin{};
     if (n > 0) {
@@ -162,7 +161,7 @@ darb_status darb_bin_sort(const darb_projected *proj, int32_t n, int32_t tile, c
     }
     const BinOut bo{out->keys, out->values, out->ranges, out->num_instances, out->status};
     bool exceeded = false;
-    DARB_CUDA_TRY(launch_bin_sort(n, pin, tiles_x, tiles_x * tiles_y, capacity, strategy, workspace, bo,
+    DARB_CUDA_TRY(launch_bin_sort(n, pin, tiles_x, tiles_y, capacity, strategy, workspace, bo,
                                   num_instances_host, &exceeded, reinterpret_cast<cudaStream_t>(stream)));
     return exceeded ? DARB_ERR_CAPACITY : DARB_OK;
 }

@@ -10,24 +10,26 @@
 //   k_depth_keys + 4 x k_onesweep<u32>   sort the N splats by depth bits (stable, so equal depths
 //                                         keep index order): N-sized, cheap
 //   k_block_sums / k_scan_block_sums      scan of tiles_touched in that depth order
+//   k_tile_diff / k_tile_setup            per-tile instance counts from the rectangles (2D
+//                                         difference array, 4 atomics per splat) -> the tile
+//                                         ranges and the digit bases of the tile passes
 //   k_splat_offsets                       per-position instance offsets (depth order)
 //   k_duplicate_balanced                  emit (tile id, splat) per instance in depth order, each
 //                                         CTA a fixed range of instances (near splats are the
-//                                         largest, so splitting by splats would be unbalanced),
-//                                         plus the digit histograms of the tile passes
+//                                         largest, so splitting by splats would be unbalanced)
 //   p x k_onesweep<u32>                   stable LSD sort of the 32-bit tile ids (p = 2 at 1080p
-//                                         with 16-pixel tiles); the last writes the output values
-//   k_ranges32                            [start, end) of each tile from the sorted tile ids
+//                                         with 16-pixel tiles); the last writes only the values
 //   k_keys64 (optional)                   the 64-bit keys, when the caller asks for them
-//   About 44 bytes of HBM traffic per instance.
+//   About 36 bytes of HBM traffic per instance.
 //
 // DARB_SORT_KEYS64
 //   k_duplicate (64-bit keys in splat order), k_sort_hist, k_hist_scan, 6 x k_onesweep<u64>
 //   over the low 32 + ceil(log2 tiles) bits, k_ranges.  About 170 bytes per instance.
 //
-// k_onesweep is one LSD pass: warp-level multisplit ranking with match.any, decoupled look-back
-// across partitions claimed in launch order (spins bounded; on timeout the status word is set
-// and successors are released), and staging in shared memory so the scatter leaves in digit runs.
+// k_onesweep is one LSD pass: unordered per-warp digit counts published at once (so successors
+// can look back early), stable warp-level ranking with match.any, decoupled look-back across
+// partitions claimed in launch order (spins bounded; on timeout the status word is set and
+// successors are released), and staging in shared memory so the scatter leaves in digit runs.
 #include <algorithm>
 #include <utility>
 
@@ -242,16 +244,13 @@ __device__ __forceinline__ int cta_upper_owner(const uint32_t *__restrict__ offs
 
 // 32-bit tile ids in depth order (strategy DEPTH_THEN_TILE), balanced over instances: CTA c
 // emits instances [c * kDupTile, (c + 1) * kDupTile).  Lane-major order within each warp's
-// chunk keeps the writes coalesced.  Digit histograms of the tile passes are accumulated in
-// shared memory (match.any aggregated) and added to hist once per CTA.
+// chunk keeps the writes coalesced.
 __global__ void __launch_bounds__(kScanThreads)
 k_duplicate_balanced(int n, const uint32_t *__restrict__ order, const uint32_t *__restrict__ offs,
                      const int4 *__restrict__ rect, int tiles_x, const uint32_t *__restrict__ num,
-                     unsigned long long cap, PassSpec ps, uint32_t *__restrict__ keys, uint32_t *__restrict__ vals,
-                     uint32_t *__restrict__ hist) {
+                     unsigned long long cap, uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
     __shared__ uint32_t s_off[kDupTile + 1];
     __shared__ uint32_t s_id[kDupTile];
-    __shared__ uint32_t s_h[kMaxTilePasses * 256];
     __shared__ int s_res[2];
     const unsigned long long Mfull = *num;
     if (Mfull > cap) return;  // overflow: nothing is emitted (status already set)
@@ -259,7 +258,6 @@ k_duplicate_balanced(int n, const uint32_t *__restrict__ order, const uint32_t *
     const uint32_t lo = blockIdx.x * (uint32_t)kDupTile;
     if (lo >= M) return;
     const uint32_t hi = min(M, lo + (uint32_t)kDupTile);
-    for (int i = threadIdx.x; i < ps.passes * 256; i += kScanThreads) s_h[i] = 0;
     const int first = cta_upper_owner(offs, n, lo, &s_res[0]);
     const int last = cta_upper_owner(offs, n, hi - 1, &s_res[1]);
     const int count = min(last - first + 1, kDupTile);  // every owner has >= 1 instance
@@ -281,40 +279,47 @@ k_duplicate_balanced(int n, const uint32_t *__restrict__ order, const uint32_t *
         }
         s = a;
     }
+#pragma unroll 4
     for (int it = 0; it < kDupItems; ++it) {
         const uint32_t k = wbase + it * 32 + lane;
-        const bool valid = k < hi;
-        uint32_t tile = 0;
-        if (valid) {
-            if (s_off[min(s + 8, count)] <= k) {  // far ahead: binary search the rest
-                int a = s, b = count - 1;
-                while (a < b) {
-                    const int mid = (a + b + 1) >> 1;
-                    if (s_off[mid] <= k) a = mid;
-                    else b = mid - 1;
-                }
-                s = a;
-            } else {
-                while (s_off[s + 1] <= k) ++s;
+        if (k >= hi) break;
+        if (s_off[min(s + 8, count)] <= k) {  // far ahead: binary search the rest
+            int a = s, b = count - 1;
+            while (a < b) {
+                const int mid = (a + b + 1) >> 1;
+                if (s_off[mid] <= k) a = mid;
+                else b = mid - 1;
             }
-            const uint32_t id = s_id[s];
-            const uint32_t l = k - s_off[s];
-            const int4 r = __ldg(rect + id);
-            const uint32_t w = (uint32_t)(r.z - r.x + 1);
-            const uint32_t ty = (uint32_t)r.y + l / w, tx = (uint32_t)r.x + l % w;
-            tile = ty * (uint32_t)tiles_x + tx;
-            keys[k] = tile;
-            vals[k] = id;
+            s = a;
+        } else {
+            while (s_off[s + 1] <= k) ++s;
         }
-        for (int p = 0; p < ps.passes; ++p) {
-            const uint32_t d = valid ? (tile >> ps.shift[p]) & ((1u << ps.bits[p]) - 1u) : 256u;
-            const uint32_t peers = __match_any_sync(0xffffffffu, d);
-            if (valid && lane == __ffs(peers) - 1) atomicAdd(&s_h[p * 256 + d], (uint32_t)__popc(peers));
-        }
+        const uint32_t id = s_id[s];
+        const uint32_t l = k - s_off[s];
+        const int4 r = __ldg(rect + id);
+        const uint32_t w = (uint32_t)(r.z - r.x + 1);
+        // row = l / w: float estimate, then exact integer correction
+        uint32_t row = __float2uint_rz(__fdividef((float)l, (float)w));
+        while (row * w > l) --row;
+        while ((row + 1) * w <= l) ++row;
+        const uint32_t tile = ((uint32_t)r.y + row) * (uint32_t)tiles_x + (uint32_t)r.x + (l - row * w);
+        keys[k] = tile;
+        vals[k] = id;
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < ps.passes * 256; i += kScanThreads)
-        if (s_h[i]) atomicAdd(&hist[i], s_h[i]);
+}
+
+// Tile coverage as a 2D difference array: +1 / -1 at the four corners of each visible splat's
+// tile rectangle, so that a 2D prefix sum gives the number of instances of every tile.
+__global__ void __launch_bounds__(256)
+k_tile_diff(int n, const int *__restrict__ radius, const int4 *__restrict__ rect, int tiles_x, int *__restrict__ diff) {
+    const int i = blockIdx.x * 256 + threadIdx.x;
+    if (i >= n || radius[i] == 0) return;
+    const int4 r = rect[i];
+    const int w1 = tiles_x + 1;
+    atomicAdd(&diff[r.y * w1 + r.x], 1);
+    atomicAdd(&diff[r.y * w1 + r.z + 1], -1);
+    atomicAdd(&diff[(r.w + 1) * w1 + r.x], -1);
+    atomicAdd(&diff[(r.w + 1) * w1 + r.z + 1], 1);
 }
 
 // ---------------------------------------------------------------------------- histograms
@@ -350,6 +355,62 @@ __global__ void __launch_bounds__(256) k_hist_scan(const uint32_t *__restrict__ 
     uint32_t total;
     const uint32_t ex = block_exclusive_scan<256>(hist[p * 256 + threadIdx.x], s_warp, total);
     base[p * 256 + threadIdx.x] = ex;
+}
+
+// Per-tile instance counts (2D prefix of the difference array) -> ranges [start, end) and the
+// digit bases of the tile passes.  One CTA.  After a capacity overflow every range is empty.
+__global__ void __launch_bounds__(1024)
+k_tile_setup(int tiles_x, int tiles_y, const int *__restrict__ diff, uint32_t *__restrict__ counts,
+             const uint32_t *num, unsigned long long capacity, PassSpec ps, uint32_t *__restrict__ ranges,
+             uint32_t *__restrict__ digit_base) {
+    __shared__ uint32_t s_h[kMaxPasses * 256];
+    __shared__ unsigned long long s_warp[1024 / 32 + 1];
+    __shared__ uint32_t s_warp32[1024 / 32 + 1];
+    for (int i = threadIdx.x; i < kMaxPasses * 256; i += 1024) s_h[i] = 0;
+    const int w1 = tiles_x + 1;
+    for (int y = threadIdx.x; y < tiles_y; y += 1024) {  // prefix along x
+        int acc = 0;
+        for (int x = 0; x < tiles_x; ++x) {
+            acc += diff[y * w1 + x];
+            counts[y * tiles_x + x] = (uint32_t)acc;
+        }
+    }
+    __syncthreads();
+    for (int x = threadIdx.x; x < tiles_x; x += 1024) {  // prefix along y
+        uint32_t acc = 0;
+        for (int y = 0; y < tiles_y; ++y) {
+            acc += counts[y * tiles_x + x];
+            counts[y * tiles_x + x] = acc;
+        }
+    }
+    __syncthreads();
+    const bool overflow = (unsigned long long)*num > capacity;
+    const int n_tiles = tiles_x * tiles_y;
+    unsigned long long carry = 0;
+    for (int chunk = 0; chunk < n_tiles; chunk += 1024) {
+        const int t = chunk + threadIdx.x;
+        const uint32_t c = t < n_tiles ? counts[t] : 0u;
+        unsigned long long total;
+        const unsigned long long ex = carry + block_exclusive_scan<1024>((unsigned long long)c, s_warp, total);
+        if (t < n_tiles) {
+            ranges[2 * (size_t)t] = overflow ? 0u : (uint32_t)ex;
+            ranges[2 * (size_t)t + 1] = overflow ? 0u : (uint32_t)(ex + c);
+            if (c) {
+#pragma unroll
+                for (int p = 0; p < kMaxPasses; ++p)
+                    if (p < ps.passes)
+                        atomicAdd(&s_h[p * 256 + (((uint32_t)t >> ps.shift[p]) & ((1u << ps.bits[p]) - 1u))], c);
+            }
+        }
+        carry += total;
+    }
+    __syncthreads();
+    for (int p = 0; p < ps.passes; ++p) {
+        const uint32_t v = threadIdx.x < 256 ? s_h[p * 256 + threadIdx.x] : 0u;
+        uint32_t total;
+        const uint32_t ex = block_exclusive_scan<1024>(v, s_warp32, total);
+        if (threadIdx.x < 256) digit_base[p * 256 + threadIdx.x] = ex;
+    }
 }
 
 // ---------------------------------------------------------------------------- onesweep
@@ -405,25 +466,22 @@ k_onesweep(const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__res
         }
     }
     const uint32_t lt = lanemask_lt();
-    // Peer masks first (independent, so they pipeline), then the per-warp running counts:
-    // rk holds the peer mask until it is replaced by the rank.
-#pragma unroll
-    for (int it = 0; it < kSortItems; ++it) rk[it] = __match_any_sync(0xffffffffu, (uint32_t)(k[it] >> shift) & mask);
+    // 1) Unordered per-warp digit counts (one shared-memory atomic per group of equal digits);
+    //    rk keeps each item's peer mask for the ordered ranking below.
 #pragma unroll
     for (int it = 0; it < kSortItems; ++it) {
         const uint32_t d = (uint32_t)(k[it] >> shift) & mask;
-        const uint32_t peers = rk[it];
-        const uint32_t prev = s_wh[warp][d];
-        rk[it] = prev + __popc(peers & lt);
-        __syncwarp();
-        if (lane == 31 - __clz(peers)) s_wh[warp][d] = prev + __popc(peers);
-        __syncwarp();
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        if (lane == __ffs(peers) - 1) atomicAdd(&s_wh[warp][d], (uint32_t)__popc(peers));
+        rk[it] = peers;
     }
     __syncthreads();
 
-    // thread = digit: per-warp exclusive offsets, CTA count, decoupled look-back
+    // 2) thread = digit: per-warp exclusive offsets and the CTA count, published at once so that
+    //    successors can look back while this CTA is still ranking
     const uint32_t dg = (uint32_t)tid;
     uint32_t cnt = 0;
+    uint32_t *mine = lookback + (size_t)part * radix + dg;
     if (dg < radix) {
 #pragma unroll
         for (int w = 0; w < NW; ++w) {
@@ -431,17 +489,38 @@ k_onesweep(const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__res
             s_wh[w][dg] = cnt;
             cnt += c;
         }
-        uint32_t *mine = lookback + (size_t)part * radix + dg;
+        st_relaxed(mine, (part == 0 ? kFlagIncl : kFlagLocal) | cnt);
+    }
+    uint32_t tot;
+    const uint32_t cex = block_exclusive_scan<kSortThreads>(cnt, s_warp, tot);
+    if (dg < radix) s_cta_excl[dg] = cex;
+    __syncthreads();
+
+    // 3) ordered ranking inside each warp (stable: item-major, lane-minor order = input order),
+    //    then staging at the CTA-local sorted position
+#pragma unroll
+    for (int it = 0; it < kSortItems; ++it) {
+        const uint32_t d = (uint32_t)(k[it] >> shift) & mask;
+        const uint32_t peers = rk[it];
+        const uint32_t prev = s_wh[warp][d];
+        const uint32_t pos = s_cta_excl[d] + prev + __popc(peers & lt);
+        __syncwarp();
+        if (lane == 31 - __clz(peers)) s_wh[warp][d] = prev + __popc(peers);
+        __syncwarp();
+        if (WRITE_KEYS) s_k[pos] = k[it];
+        else s_d[pos] = (uint8_t)d;
+        s_v[pos] = v[it];
+    }
+
+    // 4) decoupled look-back for the global base of each digit
+    if (dg < radix) {
         uint32_t excl = 0;
-        if (part == 0) {
-            st_relaxed(mine, kFlagIncl | cnt);
-        } else {
-            st_relaxed(mine, kFlagLocal | cnt);
+        if (part > 0) {
             int p = (int)part - 1;
             int spins = 0, ns = 32;
             while (true) {
-                const uint32_t s = ld_relaxed(lookback + (size_t)p * radix + dg);
-                const uint32_t f = s & ~kCountMask;
+                const uint32_t sv = ld_relaxed(lookback + (size_t)p * radix + dg);
+                const uint32_t f = sv & ~kCountMask;
                 if (f == 0) {
                     if (++spins > kSpinLimit) {
                         atomicExch(status, (uint32_t)DARB_ERR_TIMEOUT);
@@ -453,26 +532,13 @@ k_onesweep(const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__res
                     }
                     continue;
                 }
-                excl += s & kCountMask;
+                excl += sv & kCountMask;
                 if (f == kFlagIncl || p == 0) break;
                 --p;
             }
             st_relaxed(mine, kFlagIncl | ((excl + cnt) & kCountMask));
         }
         s_gbase[dg] = digit_base[dg] + excl;
-    }
-    uint32_t tot;
-    const uint32_t cex = block_exclusive_scan<kSortThreads>(cnt, s_warp, tot);
-    if (dg < radix) s_cta_excl[dg] = cex;
-    __syncthreads();
-
-#pragma unroll
-    for (int it = 0; it < kSortItems; ++it) {
-        const uint32_t d = (uint32_t)(k[it] >> shift) & mask;
-        const uint32_t pos = s_cta_excl[d] + s_wh[warp][d] + rk[it];
-        if (WRITE_KEYS) s_k[pos] = k[it];
-        else s_d[pos] = (uint8_t)d;
-        s_v[pos] = v[it];
     }
     __syncthreads();
     const uint32_t nvalid = min((uint32_t)kSortTile, M - base);
@@ -500,17 +566,6 @@ k_ranges(const uint64_t *__restrict__ keys, const uint32_t *num, unsigned long l
         const uint32_t t = (uint32_t)(keys[i] >> 32);
         if (i == 0 || (uint32_t)(keys[i - 1] >> 32) != t) ranges[2 * (size_t)t] = (uint32_t)i;
         if (i == M - 1 || (uint32_t)(keys[i + 1] >> 32) != t) ranges[2 * (size_t)t + 1] = (uint32_t)(i + 1);
-    }
-}
-
-__global__ void __launch_bounds__(256)
-k_ranges32(const uint32_t *__restrict__ tiles, const uint32_t *num, unsigned long long cap, uint32_t *__restrict__ ranges) {
-    if ((unsigned long long)*num > cap) return;  // overflow: ranges stay empty
-    const uint32_t M = *num;
-    for (uint32_t i = blockIdx.x * 256 + threadIdx.x; i < M; i += gridDim.x * 256) {
-        const uint32_t t = tiles[i];
-        if (i == 0 || tiles[i - 1] != t) ranges[2 * (size_t)t] = i;
-        if (i == M - 1 || tiles[i + 1] != t) ranges[2 * (size_t)t + 1] = i + 1;
     }
 }
 
@@ -569,11 +624,12 @@ cudaError_t launch_pass(const K *kin, const uint32_t *vin, K *kout, uint32_t *vo
 namespace {
 struct Layout {
     size_t total;
-    size_t off[17];
+    size_t off[18];
 };
 
 // Offsets of the workspace regions.  Regions 0..9 are data; [zero_begin, zero_end) is zeroed per call.
-Layout layout(int n, uint64_t capacity, int n_tiles, int strategy, int tile_bits) {
+Layout layout(int n, uint64_t capacity, int tiles_x, int tiles_y, int strategy, int tile_bits) {
+    const int n_tiles = tiles_x * tiles_y;
     const size_t nb = (size_t)(n + kScanTile - 1) / kScanTile;
     const size_t parts_cap = (capacity + kSortTile - 1) / kSortTile;
     const size_t parts_n = ((size_t)n + kSortTile - 1) / kSortTile;
@@ -595,6 +651,7 @@ Layout layout(int n, uint64_t capacity, int n_tiles, int strategy, int tile_bits
         put(7, nb * 8);        // block offsets
         put(8, 0);
         put(15, 0);
+        put(16, 0);
         put(9, (size_t)kMaxPasses * 256 * 4);  // digit bases
         put(10, (size_t)kMaxPasses * 256 * 4); // --- zeroed from here: histograms
         put(11, (size_t)passes * parts_cap * 256 * 4);  // look-back
@@ -613,7 +670,9 @@ Layout layout(int n, uint64_t capacity, int n_tiles, int strategy, int tile_bits
         put(8, (size_t)kMaxPasses * 256 * 4);  // tile digit bases
         put(9, (size_t)kMaxPasses * 256 * 4);  // depth digit bases
         put(15, ((size_t)n + 1) * 4);           // per-position instance offsets in depth order
-        put(10, (size_t)2 * kMaxPasses * 256 * 4);  // --- zeroed: tile-pass + depth-pass histograms
+        put(16, (size_t)n_tiles * 4);           // per-tile instance counts
+        // --- zeroed per call: depth histogram (+ spare), tile difference array, look-backs, counters
+        put(10, (size_t)2 * kMaxPasses * 256 * 4 + (size_t)(tiles_x + 1) * (tiles_y + 1) * 4);
         put(11, (size_t)passes * parts_cap * 256 * 4);  // tile-pass look-back
         put(12, (size_t)4 * parts_n * 256 * 4);         // depth-pass look-back
         put(13, (size_t)kMaxPasses * 4 * 2);            // partition counters
@@ -626,15 +685,16 @@ Layout layout(int n, uint64_t capacity, int n_tiles, int strategy, int tile_bits
 
 int sort_tile_bits(int n_tiles) { return log2_ceil((uint32_t)n_tiles); }
 
-size_t sort_workspace_bytes(int n, uint64_t capacity, int n_tiles, int strategy) {
-    return layout(n, capacity, n_tiles, strategy, sort_tile_bits(n_tiles)).total;
+size_t sort_workspace_bytes(int n, uint64_t capacity, int tiles_x, int tiles_y, int strategy) {
+    return layout(n, capacity, tiles_x, tiles_y, strategy, sort_tile_bits(tiles_x * tiles_y)).total;
 }
 
-cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int n_tiles, uint64_t capacity,
+cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int tiles_y, uint64_t capacity,
                             int strategy, void *workspace, const BinOut &out, uint64_t *num_instances_host,
                             bool *capacity_exceeded, cudaStream_t st) {
+    const int n_tiles = tiles_x * tiles_y;
     const int tile_bits = sort_tile_bits(n_tiles);
-    const Layout L = layout(n, capacity, n_tiles, strategy, tile_bits);
+    const Layout L = layout(n, capacity, tiles_x, tiles_y, strategy, tile_bits);
     unsigned char *w = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(workspace) + 255) & ~(uintptr_t)255);
     auto at = [&](int i) { return reinterpret_cast<void *>(w + L.off[i]); };
@@ -752,37 +812,44 @@ cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int n_t
         }
         grid = M;
     }
-    // 3) per-position offsets, then the balanced duplication with the tile-pass histograms
+    // 3) per-tile counts from the rectangles -> ranges and tile-pass digit bases
+    const PassSpec tps = split_bits(tile_bits);
+    int *diff = reinterpret_cast<int *>(at(10)) + 2 * kMaxPasses * 256;
+    uint32_t *counts = reinterpret_cast<uint32_t *>(at(16));
+    uint32_t *tbase = reinterpret_cast<uint32_t *>(at(8));
+    if (n > 0) k_tile_diff<<<(n + 255) / 256, 256, 0, st>>>(n, proj.radius, proj.tile_rect, tiles_x, diff);
+    k_tile_setup<<<1, 1024, 0, st>>>(tiles_x, tiles_y, diff, counts, out.num_instances, cap, tps,
+                                     out.ranges, tbase);
+    TRY(cudaGetLastError());
+    // 4) per-position offsets, then the balanced duplication in depth order
     uint32_t *tk_a = reinterpret_cast<uint32_t *>(at(0)), *tv_a = reinterpret_cast<uint32_t *>(at(1));
     uint32_t *tk_b = reinterpret_cast<uint32_t *>(at(2)), *tv_b = reinterpret_cast<uint32_t *>(at(3));
     uint32_t *offs = reinterpret_cast<uint32_t *>(at(15));
-    const PassSpec tps = split_bits(tile_bits);
-    uint32_t *thist = reinterpret_cast<uint32_t *>(at(10));
-    uint32_t *tbase = reinterpret_cast<uint32_t *>(at(8));
     if (nb > 0) k_splat_offsets<<<nb, kScanThreads, 0, st>>>(n, order, proj.tiles_touched, block_off, out.num_instances, offs);
     if (grid > 0 && n > 0) {
         const unsigned dup_blocks = (unsigned)((grid + kDupTile - 1) / kDupTile);
         k_duplicate_balanced<<<dup_blocks, kScanThreads, 0, st>>>(n, order, offs, proj.tile_rect, tiles_x,
-                                                                  out.num_instances, cap, tps, tk_a, tv_a, thist);
+                                                                  out.num_instances, cap, tk_a, tv_a);
     }
-    k_hist_scan<<<tps.passes, 256, 0, st>>>(thist, tbase);
     TRY(cudaGetLastError());
-    // 4) stable LSD passes over the tile ids (the last writes the values to the output)
+    // 5) stable LSD passes over the tile ids; the last writes only the output values
     if (grid > 0) {
         uint32_t *lb = reinterpret_cast<uint32_t *>(at(11));
         const size_t lb_stride = ((capacity + kSortTile - 1) / kSortTile) * 256;
         uint32_t *ka = tk_a, *va = tv_a, *kb = tk_b, *vb = tv_b;
         for (int p = 0; p < tps.passes; ++p) {
-            uint32_t *vo = (p == tps.passes - 1) ? out.values : vb;
-            TRY((launch_pass<uint32_t, true>(ka, va, kb, vo, out.num_instances, cap, grid, tps.shift[p], tps.bits[p],
-                                             tbase + p * 256, lb + p * lb_stride, counters + p, out.status, st)));
-            std::swap(ka, kb);
-            va = vo;
-            vb = (vo == tv_b) ? tv_a : tv_b;
+            if (p == tps.passes - 1) {
+                TRY((launch_pass<uint32_t, false>(ka, va, nullptr, out.values, out.num_instances, cap, grid,
+                                                  tps.shift[p], tps.bits[p], tbase + p * 256, lb + p * lb_stride,
+                                                  counters + p, out.status, st)));
+            } else {
+                TRY((launch_pass<uint32_t, true>(ka, va, kb, vb, out.num_instances, cap, grid, tps.shift[p],
+                                                 tps.bits[p], tbase + p * 256, lb + p * lb_stride, counters + p,
+                                                 out.status, st)));
+                std::swap(ka, kb);
+                std::swap(va, vb);
+            }
         }
-        // 5) ranges from the sorted tile ids (in ka), optional 64-bit keys
-        const int rb = (int)std::min<uint64_t>((grid + 255) / 256, 152 * 16);
-        k_ranges32<<<rb, 256, 0, st>>>(ka, out.num_instances, cap, out.ranges);
         if (out.keys) k_keys64<<<n_tiles, 256, 0, st>>>(out.ranges, out.values, proj.depth, n, out.keys);
         TRY(cudaGetLastError());
     }

@@ -52,10 +52,10 @@ struct BinOut {
 };
 
 int sort_tile_bits(int n_tiles);
-size_t sort_workspace_bytes(int n, uint64_t capacity, int n_tiles, int strategy);
+size_t sort_workspace_bytes(int n, uint64_t capacity, int tiles_x, int tiles_y, int strategy);
 // Enqueues the whole bin/sort.  With num_instances_host non-null it synchronises once after the
 // scan; if M exceeds the capacity it sets *capacity_exceeded and enqueues nothing more.
-cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int n_tiles, uint64_t capacity,
+cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int tiles_y, uint64_t capacity,
                             int strategy, void *workspace, const BinOut &out, uint64_t *num_instances_host,
                             bool *capacity_exceeded, cudaStream_t st);
 

@@ -69,11 +69,6 @@ ProjectedOut as_out(const darb_projected *o) {
     return r;
 }
 
-int tile_bits_for(const darb_camera *cam, int tile) {
-    const uint32_t n_tiles = (uint32_t)tile_count(cam->width, tile) * (uint32_t)tile_count(cam->height, tile);
-    return log2_ceil(n_tiles);
-}
-
 constexpr uint64_t kMaxCapacity = (1ull << 30) - 1;
 
 }  // namespace

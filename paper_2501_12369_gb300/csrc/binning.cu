@@ -42,15 +42,31 @@ namespace {
 constexpr uint32_t kFlagLocal = 1u << 30;
 constexpr uint32_t kFlagIncl = 2u << 30;
 constexpr uint32_t kCountMask = (1u << 30) - 1;
-constexpr int kSpinLimit = 1 << 22;  // x >= 64 ns sleep: a few hundred ms at most
+constexpr int kSpinLimit = 1 << 22;  // with the 512 ns back-off: about two seconds at most
+constexpr int kLookbackWindow = 8;
+constexpr size_t kMaxDiffSmem = 96 * 1024;  // tile difference array privatised per CTA up to this size
 constexpr int kDupItems = 16;
+static_assert(kScanThreads * kDupItems == kSortTile, "a duplicate CTA must cover exactly one sort partition");
 constexpr int kDupTile = kScanThreads * kDupItems;  // instances per balanced duplicate CTA
-constexpr int kMaxTilePasses = 4;  // 26 tile bits at most (65536^2 pixels, 8-pixel tiles)
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
     return m;
+}
+
+// Lanes of the warp whose digit equals this lane's digit, from one ballot per digit bit.
+__device__ __forceinline__ uint32_t match_digit(uint32_t d, int bits) {
+    uint32_t peers = 0xffffffffu;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        if (i < bits) {
+            const bool b = (d >> i) & 1u;
+            const uint32_t bal = __ballot_sync(0xffffffffu, b);
+            peers &= b ? bal : ~bal;
+        }
+    }
+    return peers;
 }
 
 __device__ __forceinline__ uint32_t ld_relaxed(const uint32_t *p) {
@@ -245,18 +261,28 @@ __device__ __forceinline__ int cta_upper_owner(const uint32_t *__restrict__ offs
 // 32-bit tile ids in depth order (strategy DEPTH_THEN_TILE), balanced over instances: CTA c
 // emits instances [c * kDupTile, (c + 1) * kDupTile).  Lane-major order within each warp's
 // chunk keeps the writes coalesced.
+// A CTA's instance range is exactly one sort partition (kDupTile == kSortTile), so the CTA also
+// writes that partition's histogram of the first tile-pass digit (tile & (2^bits1 - 1)) into
+// ph[d * n_parts + partition].
 __global__ void __launch_bounds__(kScanThreads)
 k_duplicate_balanced(int n, const uint32_t *__restrict__ order, const uint32_t *__restrict__ offs,
                      const int4 *__restrict__ rect, int tiles_x, const uint32_t *__restrict__ num,
-                     unsigned long long cap, uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+                     unsigned long long cap, uint32_t *__restrict__ keys, uint32_t *__restrict__ vals, int bits1,
+                     uint32_t n_parts, uint32_t *__restrict__ ph) {
     __shared__ uint32_t s_off[kDupTile + 1];
     __shared__ uint32_t s_id[kDupTile];
+    __shared__ uint32_t s_h[256];
     __shared__ int s_res[2];
     const unsigned long long Mfull = *num;
     if (Mfull > cap) return;  // overflow: nothing is emitted (status already set)
     const uint32_t M = (uint32_t)Mfull;
     const uint32_t lo = blockIdx.x * (uint32_t)kDupTile;
-    if (lo >= M) return;
+    const uint32_t radix1 = 1u << bits1, mask1 = radix1 - 1u;
+    for (int i = threadIdx.x; i < 256; i += kScanThreads) s_h[i] = 0;
+    if (lo >= M) {  // an empty partition (capacity-sized grid): zero histogram
+        for (uint32_t d = threadIdx.x; d < radix1; d += kScanThreads) ph[(size_t)d * n_parts + blockIdx.x] = 0;
+        return;
+    }
     const uint32_t hi = min(M, lo + (uint32_t)kDupTile);
     const int first = cta_upper_owner(offs, n, lo, &s_res[0]);
     const int last = cta_upper_owner(offs, n, hi - 1, &s_res[1]);
@@ -305,21 +331,40 @@ k_duplicate_balanced(int n, const uint32_t *__restrict__ order, const uint32_t *
         const uint32_t tile = ((uint32_t)r.y + row) * (uint32_t)tiles_x + (uint32_t)r.x + (l - row * w);
         keys[k] = tile;
         vals[k] = id;
+        atomicAdd(&s_h[tile & mask1], 1u);  // neighbouring lanes hold neighbouring tiles: few conflicts
     }
+    __syncthreads();
+    for (uint32_t d = threadIdx.x; d < radix1; d += kScanThreads) ph[(size_t)d * n_parts + blockIdx.x] = s_h[d];
 }
 
 // Tile coverage as a 2D difference array: +1 / -1 at the four corners of each visible splat's
-// tile rectangle, so that a 2D prefix sum gives the number of instances of every tile.
-__global__ void __launch_bounds__(256)
-k_tile_diff(int n, const int *__restrict__ radius, const int4 *__restrict__ rect, int tiles_x, int *__restrict__ diff) {
-    const int i = blockIdx.x * 256 + threadIdx.x;
-    if (i >= n || radius[i] == 0) return;
-    const int4 r = rect[i];
+// tile rectangle, so that a 2D prefix sum gives the number of instances of every tile.  With
+// SMEM each CTA accumulates a private copy in shared memory (grid-stride over splats) and adds
+// its non-zero entries to the global array once.
+template <bool SMEM>
+__global__ void __launch_bounds__(1024)
+k_tile_diff(int n, const int *__restrict__ radius, const int4 *__restrict__ rect, int tiles_x, int diff_size,
+            int *__restrict__ diff) {
+    extern __shared__ int s_diff[];
+    int *d = SMEM ? s_diff : diff;
+    if (SMEM) {
+        for (int i = threadIdx.x; i < diff_size; i += blockDim.x) s_diff[i] = 0;
+        __syncthreads();
+    }
     const int w1 = tiles_x + 1;
-    atomicAdd(&diff[r.y * w1 + r.x], 1);
-    atomicAdd(&diff[r.y * w1 + r.z + 1], -1);
-    atomicAdd(&diff[(r.w + 1) * w1 + r.x], -1);
-    atomicAdd(&diff[(r.w + 1) * w1 + r.z + 1], 1);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (radius[i] == 0) continue;
+        const int4 r = rect[i];
+        atomicAdd(&d[r.y * w1 + r.x], 1);
+        atomicAdd(&d[r.y * w1 + r.z + 1], -1);
+        atomicAdd(&d[(r.w + 1) * w1 + r.x], -1);
+        atomicAdd(&d[(r.w + 1) * w1 + r.z + 1], 1);
+    }
+    if (SMEM) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < diff_size; i += blockDim.x)
+            if (s_diff[i]) atomicAdd(&diff[i], s_diff[i]);
+    }
 }
 
 // ---------------------------------------------------------------------------- histograms
@@ -413,6 +458,202 @@ k_tile_setup(int tiles_x, int tiles_y, const int *__restrict__ diff, uint32_t *_
     }
 }
 
+// ---------------------------------------------------------------------------- reduce-then-scan passes
+//
+// One LSD pass without inter-CTA waiting: k_part_hist writes each partition's digit histogram
+// digit-major (ph[d * n_parts + partition]), the three k_scan_* kernels turn that table into
+// exclusive offsets -- digit-major order makes each entry the global output position of the
+// partition's first key with that digit -- and k_downsweep ranks and scatters each partition.
+
+constexpr int kScanBlock = 4096;  // values per CTA of the table scan (1024 threads x 4)
+
+// The depth-then-tile strategy sorts with onesweep passes (1) or reduce-then-scan passes (0).
+#ifndef DARB_PASS_ONESWEEP
+#define DARB_PASS_ONESWEEP 1
+#endif
+constexpr bool kPassOnesweep = DARB_PASS_ONESWEEP != 0;
+
+// Peer masks by match.any (one instruction) or by one ballot per digit bit.
+#ifndef DARB_PEERS_BY_MATCH
+#define DARB_PEERS_BY_MATCH 1
+#endif
+constexpr bool PEERS_BY_MATCH = DARB_PEERS_BY_MATCH != 0;
+
+
+template <typename K>
+__global__ void __launch_bounds__(kSortThreads)
+k_part_hist(const K *__restrict__ keys, const uint32_t *num, unsigned long long cap, int shift, int bits,
+            uint32_t n_parts, uint32_t *__restrict__ ph) {
+    __shared__ uint32_t s_h[256];
+    const uint32_t radix = 1u << bits, mask = radix - 1u;
+    for (int i = threadIdx.x; i < 256; i += kSortThreads) s_h[i] = 0;
+    __syncthreads();
+    const unsigned long long Mfull = num ? (unsigned long long)*num : cap;
+    const uint32_t M = Mfull > cap ? 0u : (uint32_t)Mfull;
+    const uint32_t base = blockIdx.x * (uint32_t)kSortTile;
+    const int lane = threadIdx.x & 31;
+    K kk[kSortItems];  // all loads in flight before the first warp vote
+#pragma unroll
+    for (int it = 0; it < kSortItems; ++it) {
+        const uint32_t idx = base + it * kSortThreads + threadIdx.x;
+        kk[it] = idx < M ? keys[idx] : K(0);
+    }
+#pragma unroll
+    for (int it = 0; it < kSortItems; ++it) {
+        const bool valid = base + it * kSortThreads + threadIdx.x < M;
+        const uint32_t d = valid ? (uint32_t)(kk[it] >> shift) & mask : 0u;
+        const uint32_t peers = (PEERS_BY_MATCH ? __match_any_sync(0xffffffffu, d) : match_digit(d, bits)) &
+                               __ballot_sync(0xffffffffu, valid);
+        if (valid && lane == __ffs(peers) - 1) atomicAdd(&s_h[d], (uint32_t)__popc(peers));
+    }
+    __syncthreads();
+    for (uint32_t d = threadIdx.x; d < radix; d += kSortThreads) ph[(size_t)d * n_parts + blockIdx.x] = s_h[d];
+}
+
+__global__ void __launch_bounds__(1024)
+k_scan_reduce(const uint32_t *__restrict__ data, unsigned long long count, uint32_t *__restrict__ sums) {
+    __shared__ uint32_t s_warp[1024 / 32 + 1];
+    const unsigned long long base = (unsigned long long)blockIdx.x * kScanBlock;
+    uint32_t v = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const unsigned long long i = base + (unsigned long long)j * 1024 + threadIdx.x;
+        if (i < count) v += data[i];
+    }
+    uint32_t total;
+    block_exclusive_scan<1024>(v, s_warp, total);
+    if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_top(uint32_t *__restrict__ sums, int nb) {
+    __shared__ uint32_t s_warp[1024 / 32 + 1];
+    uint32_t carry = 0;
+    for (int chunk = 0; chunk < nb; chunk += 1024) {
+        const int i = chunk + threadIdx.x;
+        const uint32_t v = i < nb ? sums[i] : 0u;
+        uint32_t total;
+        const uint32_t ex = block_exclusive_scan<1024>(v, s_warp, total);
+        if (i < nb) sums[i] = carry + ex;
+        carry += total;
+    }
+}
+
+__global__ void __launch_bounds__(1024)
+k_scan_apply(uint32_t *__restrict__ data, unsigned long long count, const uint32_t *__restrict__ sums) {
+    __shared__ uint32_t s_warp[1024 / 32 + 1];
+    const unsigned long long base = (unsigned long long)blockIdx.x * kScanBlock + (unsigned long long)threadIdx.x * 4;
+    uint32_t v[4], sum = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        v[j] = base + j < count ? data[base + j] : 0u;
+        sum += v[j];
+    }
+    uint32_t total;
+    uint32_t ex = block_exclusive_scan<1024>(sum, s_warp, total) + sums[blockIdx.x];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        if (base + j < count) data[base + j] = ex;
+        ex += v[j];
+    }
+}
+
+// Rank and scatter one partition with known per-digit global offsets (no look-back).
+template <typename K, bool WRITE_KEYS>
+__global__ void __launch_bounds__(kSortThreads, 2)
+k_downsweep(const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__restrict__ kout,
+            uint32_t *__restrict__ vout, const uint32_t *num, unsigned long long cap, int shift, int bits,
+            const uint32_t *__restrict__ offsets, uint32_t n_parts) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint32_t *s_v = reinterpret_cast<uint32_t *>(smem);
+    K *s_k = reinterpret_cast<K *>(smem + (size_t)kSortTile * 4);
+    uint8_t *s_d = reinterpret_cast<uint8_t *>(smem + (size_t)kSortTile * 4);
+    constexpr int NW = kSortThreads / 32;
+    __shared__ uint32_t s_wh[NW][256];
+    __shared__ uint32_t s_gbase[256];
+    __shared__ uint32_t s_warp[NW + 1];
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t radix = 1u << bits, mask = radix - 1u;
+    if (num && (unsigned long long)*num > cap) return;  // overflow: sort nothing
+    const uint32_t M = (uint32_t)(num ? min((unsigned long long)*num, cap) : cap);
+    const uint32_t part = blockIdx.x;
+    const uint32_t base = part * kSortTile;
+    if (base >= M) return;
+    for (int i = tid; i < NW * 256; i += kSortThreads) (&s_wh[0][0])[i] = 0;
+    __syncthreads();
+
+    K k[kSortItems];
+    uint32_t v[kSortItems], rk[kSortItems];
+#pragma unroll
+    for (int it = 0; it < kSortItems; ++it) {
+        const uint32_t idx = base + warp * (32 * kSortItems) + it * 32 + lane;
+        if (idx < M) {
+            k[it] = kin[idx];
+            v[it] = vin ? vin[idx] : idx;
+        } else {
+            k[it] = ~K(0);  // the top digit, ranked after every valid key of the partition
+            v[it] = 0;
+        }
+    }
+    const uint32_t lt = lanemask_lt();
+#pragma unroll
+    for (int it = 0; it < kSortItems; ++it) {
+        const uint32_t d = (uint32_t)(k[it] >> shift) & mask;
+        const uint32_t peers = PEERS_BY_MATCH ? __match_any_sync(0xffffffffu, d) : match_digit(d, bits);
+        if (lane == __ffs(peers) - 1) atomicAdd(&s_wh[warp][d], (uint32_t)__popc(peers));
+        rk[it] = peers;
+    }
+    __syncthreads();
+    const uint32_t dg = (uint32_t)tid;
+    uint32_t cnt = 0;
+    if (dg < radix) {
+#pragma unroll
+        for (int w = 0; w < NW; ++w) cnt += s_wh[w][dg];
+    }
+    uint32_t tot;
+    const uint32_t cex = block_exclusive_scan<kSortThreads>(cnt, s_warp, tot);
+    if (dg < radix) {
+        // per-warp running positions start at the CTA offset of the digit plus earlier warps' counts
+        uint32_t run = cex;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            const uint32_t c = s_wh[w][dg];
+            s_wh[w][dg] = run;
+            run += c;
+        }
+        s_gbase[dg] = offsets[(size_t)dg * n_parts + part] - cex;  // global = this + local position
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < kSortItems; ++it) {
+        const uint32_t d = (uint32_t)(k[it] >> shift) & mask;
+        const uint32_t peers = rk[it];
+        const uint32_t prev = s_wh[warp][d];
+        const uint32_t pos = prev + __popc(peers & lt);
+        __syncwarp();
+        if (lane == 31 - __clz(peers)) s_wh[warp][d] = prev + __popc(peers);
+        __syncwarp();
+        if (WRITE_KEYS) s_k[pos] = k[it];
+        else s_d[pos] = (uint8_t)d;
+        s_v[pos] = v[it];
+    }
+    __syncthreads();
+    const uint32_t nvalid = min((uint32_t)kSortTile, M - base);
+    for (uint32_t j = tid; j < nvalid; j += kSortThreads) {
+        uint32_t d;
+        K kk = K(0);
+        if (WRITE_KEYS) {
+            kk = s_k[j];
+            d = (uint32_t)(kk >> shift) & mask;
+        } else {
+            d = s_d[j];
+        }
+        const uint32_t dst = s_gbase[d] + j;
+        if (WRITE_KEYS) kout[dst] = kk;
+        vout[dst] = s_v[j];
+    }
+}
+
 // ---------------------------------------------------------------------------- onesweep
 
 template <typename K, bool WRITE_KEYS>
@@ -423,7 +664,7 @@ struct Staging {
 // One stable LSD pass over the digit of `bits` bits at `shift`.  M = min(*num, cap), or cap if
 // num is null.  vin may be null: values are then the input positions (iota).
 template <typename K, bool WRITE_KEYS>
-__global__ void __launch_bounds__(kSortThreads, 3)
+__global__ void __launch_bounds__(kSortThreads, 2)
 k_onesweep(const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__restrict__ kout,
            uint32_t *__restrict__ vout, const uint32_t *num, unsigned long long cap, int shift, int bits,
            const uint32_t *__restrict__ digit_base, uint32_t *lookback, uint32_t *part_counter, uint32_t *status) {
@@ -471,7 +712,7 @@ k_onesweep(const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__res
 #pragma unroll
     for (int it = 0; it < kSortItems; ++it) {
         const uint32_t d = (uint32_t)(k[it] >> shift) & mask;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t peers = PEERS_BY_MATCH ? __match_any_sync(0xffffffffu, d) : match_digit(d, bits);
         if (lane == __ffs(peers) - 1) atomicAdd(&s_wh[warp][d], (uint32_t)__popc(peers));
         rk[it] = peers;
     }
@@ -512,29 +753,40 @@ k_onesweep(const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__res
         s_v[pos] = v[it];
     }
 
-    // 4) decoupled look-back for the global base of each digit
+    // 4) decoupled look-back for the global base of each digit, 8 predecessors per round trip
     if (dg < radix) {
         uint32_t excl = 0;
         if (part > 0) {
             int p = (int)part - 1;
-            int spins = 0, ns = 32;
-            while (true) {
-                const uint32_t sv = ld_relaxed(lookback + (size_t)p * radix + dg);
-                const uint32_t f = sv & ~kCountMask;
-                if (f == 0) {
-                    if (++spins > kSpinLimit) {
-                        atomicExch(status, (uint32_t)DARB_ERR_TIMEOUT);
-                        break;
+            bool found = false;
+            while (!found) {
+                const int nwin = min(kLookbackWindow, p + 1);
+                uint32_t st[kLookbackWindow];
+#pragma unroll
+                for (int j = 0; j < kLookbackWindow; ++j)
+                    st[j] = j < nwin ? ld_relaxed(lookback + (size_t)(p - j) * radix + dg) : 0u;
+#pragma unroll
+                for (int j = 0; j < kLookbackWindow; ++j) {
+                    if (found || j >= nwin) break;
+                    uint32_t sv = st[j];
+                    int spins = 0, ns = 32;
+                    while ((sv & ~kCountMask) == 0) {  // not published yet: wait for this one
+                        if (++spins > kSpinLimit) {
+                            atomicExch(status, (uint32_t)DARB_ERR_TIMEOUT);
+                            sv = kFlagIncl;
+                            break;
+                        }
+                        if (spins > 16) {  // poll busily at first, then back off
+                            __nanosleep(ns);
+                            ns = min(ns * 2, 512);
+                        }
+                        sv = ld_relaxed(lookback + (size_t)(p - j) * radix + dg);
                     }
-                    if (spins > 16) {  // poll busily at first, then back off
-                        __nanosleep(ns);
-                        ns = min(ns * 2, 512);
-                    }
-                    continue;
+                    excl += sv & kCountMask;
+                    found = (sv & ~kCountMask) == kFlagIncl;
                 }
-                excl += sv & kCountMask;
-                if (f == kFlagIncl || p == 0) break;
-                --p;
+                p -= nwin;
+                if (p < 0) found = true;  // partition 0 publishes an inclusive count at once
             }
             st_relaxed(mine, kFlagIncl | ((excl + cnt) & kCountMask));
         }
@@ -603,6 +855,27 @@ PassSpec split_bits(int total_bits) {
     return ps;
 }
 
+// One reduce-then-scan pass.  ph: partition histograms (filled here unless hist_ready); table
+// scan sums in `sums`.  n_parts = ceil(grid / kSortTile).
+template <typename K, bool WK>
+cudaError_t launch_rts_pass(const K *kin, const uint32_t *vin, K *kout, uint32_t *vout, const uint32_t *num,
+                            unsigned long long cap, uint64_t grid, int shift, int bits, uint32_t *ph,
+                            uint32_t *sums, bool hist_ready, cudaStream_t st) {
+    const uint32_t n_parts = (uint32_t)((grid + kSortTile - 1) / kSortTile);
+    if (n_parts == 0) return cudaSuccess;
+    if (!hist_ready) k_part_hist<K><<<n_parts, kSortThreads, 0, st>>>(kin, num, cap, shift, bits, n_parts, ph);
+    const unsigned long long count = (unsigned long long)n_parts << bits;
+    const int nb = (int)((count + kScanBlock - 1) / kScanBlock);
+    k_scan_reduce<<<nb, 1024, 0, st>>>(ph, count, sums);
+    k_scan_top<<<1, 1024, 0, st>>>(sums, nb);
+    k_scan_apply<<<nb, 1024, 0, st>>>(ph, count, sums);
+    const size_t smem = Staging<K, WK>::bytes;
+    cudaError_t e = cudaFuncSetAttribute(k_downsweep<K, WK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_downsweep<K, WK><<<n_parts, kSortThreads, smem, st>>>(kin, vin, kout, vout, num, cap, shift, bits, ph, n_parts);
+    return cudaGetLastError();
+}
+
 template <typename K, bool WK>
 cudaError_t launch_pass(const K *kin, const uint32_t *vin, K *kout, uint32_t *vout, const uint32_t *num,
                         unsigned long long cap, uint64_t grid_instances, int shift, int bits, const uint32_t *base,
@@ -624,7 +897,7 @@ cudaError_t launch_pass(const K *kin, const uint32_t *vin, K *kout, uint32_t *vo
 namespace {
 struct Layout {
     size_t total;
-    size_t off[18];
+    size_t off[21];
 };
 
 // Offsets of the workspace regions.  Regions 0..9 are data; [zero_begin, zero_end) is zeroed per call.
@@ -652,6 +925,9 @@ Layout layout(int n, uint64_t capacity, int tiles_x, int tiles_y, int strategy, 
         put(8, 0);
         put(15, 0);
         put(16, 0);
+        put(17, 0);
+        put(18, 0);
+        put(19, 0);
         put(9, (size_t)kMaxPasses * 256 * 4);  // digit bases
         put(10, (size_t)kMaxPasses * 256 * 4); // --- zeroed from here: histograms
         put(11, (size_t)passes * parts_cap * 256 * 4);  // look-back
@@ -671,11 +947,14 @@ Layout layout(int n, uint64_t capacity, int tiles_x, int tiles_y, int strategy, 
         put(9, (size_t)kMaxPasses * 256 * 4);  // depth digit bases
         put(15, ((size_t)n + 1) * 4);           // per-position instance offsets in depth order
         put(16, (size_t)n_tiles * 4);           // per-tile instance counts
-        // --- zeroed per call: depth histogram (+ spare), tile difference array, look-backs, counters
+        put(11, parts_cap * 256 * 4);           // tile-pass partition histograms / offsets
+        put(12, parts_n * 256 * 4);             // depth-pass partition histograms / offsets
+        put(17, ((std::max(parts_cap, parts_n) * 256 + 4095) / 4096 + 1) * 4);  // table-scan block sums
+        // --- zeroed per call: histograms (+ spare), the tile difference array, onesweep look-backs
         put(10, (size_t)2 * kMaxPasses * 256 * 4 + (size_t)(tiles_x + 1) * (tiles_y + 1) * 4);
-        put(11, (size_t)passes * parts_cap * 256 * 4);  // tile-pass look-back
-        put(12, (size_t)4 * parts_n * 256 * 4);         // depth-pass look-back
-        put(13, (size_t)kMaxPasses * 4 * 2);            // partition counters
+        put(18, kPassOnesweep ? (size_t)passes * parts_cap * 256 * 4 : 0);  // tile-pass look-back
+        put(19, kPassOnesweep ? (size_t)4 * parts_n * 256 * 4 : 0);         // depth-pass look-back
+        put(13, (size_t)kMaxPasses * 4 * 2);    // onesweep partition counters
     }
     L.off[14] = b;
     L.total = b + 256;
@@ -768,29 +1047,45 @@ cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int til
     uint32_t *kbuf[2] = {reinterpret_cast<uint32_t *>(at(4)), reinterpret_cast<uint32_t *>(at(4)) + n};
     uint32_t *vbuf[2] = {reinterpret_cast<uint32_t *>(at(5)), reinterpret_cast<uint32_t *>(at(5)) + n};
     const uint32_t *order = nullptr;  // sorted splat ids
+    uint32_t *sums = reinterpret_cast<uint32_t *>(at(17));
     if (n > 0) {
         const PassSpec dps = split_bits(32);
-        uint32_t *dhist = reinterpret_cast<uint32_t *>(at(10)) + kMaxPasses * 256;
-        uint32_t *dbase = reinterpret_cast<uint32_t *>(at(9));
+        uint32_t *dph = reinterpret_cast<uint32_t *>(at(12));
         k_depth_keys<<<(n + 255) / 256, 256, 0, st>>>(n, proj.radius, proj.depth, kbuf[0]);
-        const int hb = std::min((n + 255) / 256, 152 * 8);
-        k_sort_hist<uint32_t><<<hb, 256, 0, st>>>(kbuf[0], nullptr, (unsigned long long)n, dps, dhist);
-        k_hist_scan<<<dps.passes, 256, 0, st>>>(dhist, dbase);
+        uint32_t *dbase = reinterpret_cast<uint32_t *>(at(9));
+        if (kPassOnesweep) {
+            uint32_t *dhist = reinterpret_cast<uint32_t *>(at(10)) + kMaxPasses * 256;
+            const int hb = std::min((n + 255) / 256, 152 * 8);
+            k_sort_hist<uint32_t><<<hb, 256, 0, st>>>(kbuf[0], nullptr, (unsigned long long)n, dps, dhist);
+            k_hist_scan<<<dps.passes, 256, 0, st>>>(dhist, dbase);
+        }
         TRY(cudaGetLastError());
-        uint32_t *lbd = reinterpret_cast<uint32_t *>(at(12));
+        uint32_t *lbd = reinterpret_cast<uint32_t *>(at(19));
         const size_t lbd_stride = (((size_t)n + kSortTile - 1) / kSortTile) * 256;
         const uint32_t *vin = nullptr;  // first pass: values are the splat indices
         int cur = 0;
         for (int p = 0; p < dps.passes; ++p) {
             const int nxt = 1 - cur;
-            if (p == dps.passes - 1)
-                TRY((launch_pass<uint32_t, false>(kbuf[cur], vin, nullptr, vbuf[nxt], nullptr, (unsigned long long)n,
-                                                  (uint64_t)n, dps.shift[p], dps.bits[p], dbase + p * 256,
-                                                  lbd + p * lbd_stride, counters + kMaxPasses + p, out.status, st)));
-            else
-                TRY((launch_pass<uint32_t, true>(kbuf[cur], vin, kbuf[nxt], vbuf[nxt], nullptr, (unsigned long long)n,
-                                                 (uint64_t)n, dps.shift[p], dps.bits[p], dbase + p * 256,
-                                                 lbd + p * lbd_stride, counters + kMaxPasses + p, out.status, st)));
+            const bool last = p == dps.passes - 1;
+            if (kPassOnesweep) {
+                if (last)
+                    TRY((launch_pass<uint32_t, false>(kbuf[cur], vin, nullptr, vbuf[nxt], nullptr, (unsigned long long)n,
+                                                      (uint64_t)n, dps.shift[p], dps.bits[p], dbase + p * 256,
+                                                      lbd + p * lbd_stride, counters + kMaxPasses + p, out.status, st)));
+                else
+                    TRY((launch_pass<uint32_t, true>(kbuf[cur], vin, kbuf[nxt], vbuf[nxt], nullptr, (unsigned long long)n,
+                                                     (uint64_t)n, dps.shift[p], dps.bits[p], dbase + p * 256,
+                                                     lbd + p * lbd_stride, counters + kMaxPasses + p, out.status, st)));
+            } else {
+                if (last)
+                    TRY((launch_rts_pass<uint32_t, false>(kbuf[cur], vin, nullptr, vbuf[nxt], nullptr,
+                                                          (unsigned long long)n, (uint64_t)n, dps.shift[p], dps.bits[p],
+                                                          dph, sums, false, st)));
+                else
+                    TRY((launch_rts_pass<uint32_t, true>(kbuf[cur], vin, kbuf[nxt], vbuf[nxt], nullptr,
+                                                         (unsigned long long)n, (uint64_t)n, dps.shift[p], dps.bits[p],
+                                                         dph, sums, false, st)));
+            }
             vin = vbuf[nxt];
             cur = nxt;
         }
@@ -817,7 +1112,18 @@ cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int til
     int *diff = reinterpret_cast<int *>(at(10)) + 2 * kMaxPasses * 256;
     uint32_t *counts = reinterpret_cast<uint32_t *>(at(16));
     uint32_t *tbase = reinterpret_cast<uint32_t *>(at(8));
-    if (n > 0) k_tile_diff<<<(n + 255) / 256, 256, 0, st>>>(n, proj.radius, proj.tile_rect, tiles_x, diff);
+    if (n > 0) {
+        const int diff_size = (tiles_x + 1) * (tiles_y + 1);
+        const size_t smem = (size_t)diff_size * 4;
+        if (smem <= kMaxDiffSmem) {
+            TRY(cudaFuncSetAttribute(k_tile_diff<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            const int blocks = std::min((n + 1023) / 1024, 2 * 152);
+            k_tile_diff<true><<<blocks, 1024, smem, st>>>(n, proj.radius, proj.tile_rect, tiles_x, diff_size, diff);
+        } else {
+            k_tile_diff<false><<<(n + 1023) / 1024, 1024, 0, st>>>(n, proj.radius, proj.tile_rect, tiles_x, diff_size,
+                                                                    diff);
+        }
+    }
     k_tile_setup<<<1, 1024, 0, st>>>(tiles_x, tiles_y, diff, counts, out.num_instances, cap, tps,
                                      out.ranges, tbase);
     TRY(cudaGetLastError());
@@ -826,26 +1132,45 @@ cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int til
     uint32_t *tk_b = reinterpret_cast<uint32_t *>(at(2)), *tv_b = reinterpret_cast<uint32_t *>(at(3));
     uint32_t *offs = reinterpret_cast<uint32_t *>(at(15));
     if (nb > 0) k_splat_offsets<<<nb, kScanThreads, 0, st>>>(n, order, proj.tiles_touched, block_off, out.num_instances, offs);
-    if (grid > 0 && n > 0) {
-        const unsigned dup_blocks = (unsigned)((grid + kDupTile - 1) / kDupTile);
-        k_duplicate_balanced<<<dup_blocks, kScanThreads, 0, st>>>(n, order, offs, proj.tile_rect, tiles_x,
-                                                                  out.num_instances, cap, tk_a, tv_a);
+    uint32_t *tph = reinterpret_cast<uint32_t *>(at(11));
+    const uint32_t n_parts = (uint32_t)((grid + kSortTile - 1) / kSortTile);
+    if (grid > 0) {
+        if (n > 0)
+            k_duplicate_balanced<<<n_parts, kScanThreads, 0, st>>>(n, order, offs, proj.tile_rect, tiles_x,
+                                                                   out.num_instances, cap, tk_a, tv_a, tps.bits[0],
+                                                                   n_parts, tph);
+        else
+            TRY(cudaMemsetAsync(tph, 0, ((size_t)n_parts << tps.bits[0]) * 4, st));
     }
     TRY(cudaGetLastError());
     // 5) stable LSD passes over the tile ids; the last writes only the output values
     if (grid > 0) {
-        uint32_t *lb = reinterpret_cast<uint32_t *>(at(11));
-        const size_t lb_stride = ((capacity + kSortTile - 1) / kSortTile) * 256;
         uint32_t *ka = tk_a, *va = tv_a, *kb = tk_b, *vb = tv_b;
+        uint32_t *lb = reinterpret_cast<uint32_t *>(at(18));
+        const size_t lb_stride = ((capacity + kSortTile - 1) / kSortTile) * 256;
         for (int p = 0; p < tps.passes; ++p) {
-            if (p == tps.passes - 1) {
-                TRY((launch_pass<uint32_t, false>(ka, va, nullptr, out.values, out.num_instances, cap, grid,
-                                                  tps.shift[p], tps.bits[p], tbase + p * 256, lb + p * lb_stride,
-                                                  counters + p, out.status, st)));
+            const bool last = p == tps.passes - 1;
+            uint32_t *kout = last ? nullptr : kb;
+            uint32_t *vout = last ? out.values : vb;
+            if (kPassOnesweep) {
+                if (last)
+                    TRY((launch_pass<uint32_t, false>(ka, va, kout, vout, out.num_instances, cap, grid, tps.shift[p],
+                                                      tps.bits[p], tbase + p * 256, lb + p * lb_stride, counters + p,
+                                                      out.status, st)));
+                else
+                    TRY((launch_pass<uint32_t, true>(ka, va, kout, vout, out.num_instances, cap, grid, tps.shift[p],
+                                                     tps.bits[p], tbase + p * 256, lb + p * lb_stride, counters + p,
+                                                     out.status, st)));
             } else {
-                TRY((launch_pass<uint32_t, true>(ka, va, kb, vb, out.num_instances, cap, grid, tps.shift[p],
-                                                 tps.bits[p], tbase + p * 256, lb + p * lb_stride, counters + p,
-                                                 out.status, st)));
+                const bool ready = p == 0;  // the duplication wrote the first pass's histograms
+                if (last)
+                    TRY((launch_rts_pass<uint32_t, false>(ka, va, kout, vout, out.num_instances, cap, grid,
+                                                          tps.shift[p], tps.bits[p], tph, sums, ready, st)));
+                else
+                    TRY((launch_rts_pass<uint32_t, true>(ka, va, kout, vout, out.num_instances, cap, grid,
+                                                         tps.shift[p], tps.bits[p], tph, sums, ready, st)));
+            }
+            if (!last) {
                 std::swap(ka, kb);
                 std::swap(va, vb);
             }

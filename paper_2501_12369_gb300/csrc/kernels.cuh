@@ -31,8 +31,8 @@ cudaError_t launch_preprocess_bwd(int n, const darb_splats &sp, const Cam &cam, 
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
 constexpr int kScanTile = kScanThreads * kScanItems;  // splats per scan/duplicate CTA
-constexpr int kSortThreads = 256;
-constexpr int kSortItems = 16;
+constexpr int kSortThreads = 512;
+constexpr int kSortItems = 8;
 constexpr int kSortTile = kSortThreads * kSortItems;  // keys per onesweep partition
 constexpr int kMaxPasses = 8;
 

@@ -62,7 +62,7 @@ k_adam4(long long count, float *__restrict__ p, const float *__restrict__ g, flo
         if (ACT) A = reinterpret_cast<float4 *>(activated)[j];
         float lrs[4] = {lr, lr, lr, lr};
         if (ROW > 0) {
-            const int pos = (int)((j * 4) % ROW);  // ROW is a compile-time constant
+            const int pos = (int)((j * 4) % (ROW > 0 ? ROW : 1));  // ROW is a compile-time constant
 #pragma unroll
             for (int u = 0; u < 4; ++u) lrs[u] = (pos + u >= SPLIT) ? lr2 : lr;
         }

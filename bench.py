@@ -156,8 +156,8 @@ class TrainStep:
         self.dL = torch.empty(3, H, W, **dev)
         self.loss = torch.zeros(1, **dev)
         self.target = torch.empty(3, H, W, **dev)
-        self.tx, self.ty = darb.darb_tile_grid(cams[0], tile)
         self.cam_structs = [darb.camera(c) for c in cams]
+        self.set_tile(tile)
         self.capacity = 0
         self.ws = None
         self.bins = None
@@ -176,6 +176,25 @@ class TrainStep:
                                             d._p(self.logits), d._p(self.sh), d._p(self.scales), d._p(self.opac),
                                             self.n, self.sh_degree)
         self.s_state = d.darb_adam_state(*(d._p(self.state[f]) for f, _ in d.darb_adam_state._fields_))
+
+    def set_tile(self, tile):
+        self.tile = int(tile)
+        self.tx, self.ty = self.darb.darb_tile_grid(self.cams[0], self.tile)
+        self.capacity = 0
+        self.ws = self.bins = None
+
+    def size_capacity(self, cam_ids):
+        """Capacity for the cameras a run visits (x1.3 for the drift of the training updates)."""
+        self.set_capacity(1 << 20)
+        Ms = []
+        for ci in sorted(set(cam_ids)):
+            m = self.count_instances(ci)
+            if m > self.capacity:
+                self.set_capacity(int(m * 1.3))
+                m = self.count_instances(ci)
+            Ms.append(m)
+        self.set_capacity(int(max(Ms) * 1.3) + 1024)
+        return Ms
 
     def set_capacity(self, capacity):
         d = self.darb
@@ -333,25 +352,39 @@ def run_ours(args):
     from paper_2501_12369_gb300 import build, synth
     build.build()
     splats, cams = synth.scene_3m_1080p()
-    ts = TrainStep(splats, cams, args.kernel, args.tile, device, args.sort)
+    candidates = [args.tile] if args.tile else [8, 16, 32]
+    ts = TrainStep(splats, cams, args.kernel, candidates[0], device, args.sort)
     # replicas: rank r trains on its own camera sequence
     cam_seq = [(rank * 37 + i) % len(cams) for i in range(args.warmup + args.steps)]
     targets = [torch.from_numpy(synth.random_target(1080, 1920, seed=10 + i)).to(device) for i in range(4)]
-    # capacity from the cameras this run visits (x1.3 for the Adam drift), probed before timing
-    ts.set_capacity(1 << 20)
-    Ms = []
-    for ci in sorted(set(cam_seq)):
-        m = ts.count_instances(ci)
-        if m > ts.capacity:
-            ts.set_capacity(int(m * 1.3))
-            m = ts.count_instances(ci)
-        Ms.append(m)
-    ts.set_capacity(int(max(Ms) * 1.3) + 1024)
-    torch.cuda.synchronize()
 
     def step(i, ev=None):
         ts.target.copy_(targets[i % 4], non_blocking=True) if ev is None else None
-        ts.train(cam_seq[i], ev)
+        ts.train(cam_seq[i % len(cam_seq)], ev)
+
+    # tile-size autotuning over whole training steps (before anything is timed)
+    tuning = {}
+    if len(candidates) > 1:
+        for t in candidates:
+            ts.set_tile(t)
+            ts.size_capacity(cam_seq[:16])
+            for i in range(3):
+                step(i)
+            torch.cuda.synchronize()
+            t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t0.record()
+            for i in range(3, 13):
+                step(i)
+            t1.record()
+            torch.cuda.synchronize()
+            tuning[t] = round(10 / (t0.elapsed_time(t1) / 1e3), 2)
+        best = max(tuning, key=tuning.get)
+    else:
+        best = candidates[0]
+    ts.set_tile(best)
+    args.tile = best
+    Ms = ts.size_capacity(cam_seq)
+    torch.cuda.synchronize()
 
     # warm-up
     for i in range(args.warmup):
@@ -439,6 +472,7 @@ def run_ours(args):
                    "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (2.1 GB splat state)",
                    "mean_instances": int(M_mean)},
         "fwd_mpix_s": fwd_mpix,
+        "tile_autotune_it_s": tuning or None,
         "fwd_ms": fwd_ms / args.steps,
         "stage_ms": {s: round(v, 4) for s, v in stage_ms.items()},
         "dominant_stage": dominant,
@@ -482,6 +516,7 @@ def run_reference(args):
     import oracle
     oracle.build()
     splats, cams = synth.scene_3m_1080p()
+    args.tile = args.tile or 16
     vals = []
     for i in range(args.warmup + args.steps):
         r = cpu_baseline(splats, [cams[i % len(cams)]], args.kernel, args.tile, target_seconds=2.0)
@@ -507,7 +542,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--kernel", default="half_cosine")
-    ap.add_argument("--tile", type=int, default=16)
+    ap.add_argument("--tile", type=int, default=0, help="tile size; 0 = autotune over 8, 16, 32")
     ap.add_argument("--sort", type=int, default=0, help="0: depth then tile (default), 1: 64-bit keys")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

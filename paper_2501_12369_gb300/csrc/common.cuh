@@ -41,45 +41,55 @@ inline Cam make_cam(const darb_camera &c) {
 }
 
 // ---------------------------------------------------------------------------
-// Kernel profiles F(q) and dF/dq in FP32 (Table 1 with the xi of Table 2 in the
-// forms the Sec. B listings evaluate).  Main-lobe arguments are bounded, so the
-// accurate single-precision library functions are used.
+// Kernel profiles F(q) and dF/dq in FP32 (Table 1 with the xi of Table 2 in the forms the
+// Sec. B listings evaluate).  Every main-lobe argument is bounded (cos on [0, pi/2] or
+// [0, pi], exp on [-4.5, 0]), so the hardware approximations (__cosf, __expf, __sincosf:
+// absolute error below 4e-7 there) are accurate enough; the sinc uses its Taylor series in
+// x^2 to the x^14 term (truncation error below 3e-7 on [0, pi]).
+// kernel_F is written with explicit intrinsics so that its rounding never depends on how the
+// compiler contracts the surrounding code: forward and backward must get the same alpha.
 
 template <int K> __device__ __forceinline__ float kernel_F(float q);
 template <int K> __device__ __forceinline__ float kernel_dF(float q);
 
-// kernel_F uses explicit __f*_rn intrinsics so that its rounding never depends on how the
-// compiler contracts the surrounding code: forward and backward must get the same alpha.
-template <> __device__ __forceinline__ float kernel_F<DARB_GAUSSIAN>(float q) {
-    return expf(__fmul_rn(-0.5f, q));
+// sin(x)/x = 1 - u/3! + u^2/5! - ... - u^7/15! with u = x^2, evaluated by Horner as
+// 1 - u (1/3! - u (1/5! - u (1/7! - u (1/9! - u (1/11! - u (1/13! - u/15!)))))).
+__device__ __forceinline__ float sinc_series(float u) {
+    float r = __fmaf_rn(u, 1.0f / 1307674368000.0f, -1.0f / 6227020800.0f);  // -(1/13! - u/15!)
+    r = __fmaf_rn(r, u, 1.0f / 39916800.0f);   // 1/11! - u(...)
+    r = __fmaf_rn(r, u, -1.0f / 362880.0f);    // -(1/9! - u(...))
+    r = __fmaf_rn(r, u, 1.0f / 5040.0f);       // 1/7! - u(...)
+    r = __fmaf_rn(r, u, -1.0f / 120.0f);       // -(1/5! - u(...))
+    r = __fmaf_rn(r, u, 1.0f / 6.0f);          // 1/3! - u(...)
+    return __fmaf_rn(r, -u, 1.0f);
 }
-template <> __device__ __forceinline__ float kernel_dF<DARB_GAUSSIAN>(float q) { return -0.5f * expf(-0.5f * q); }
+
+template <> __device__ __forceinline__ float kernel_F<DARB_GAUSSIAN>(float q) {
+    return __expf(__fmul_rn(-0.5f, q));
+}
+template <> __device__ __forceinline__ float kernel_dF<DARB_GAUSSIAN>(float q) { return -0.5f * __expf(-0.5f * q); }
 
 template <> __device__ __forceinline__ float kernel_F<DARB_HALF_COSINE>(float q) {
-    return cosf(__fmul_rn(q, kPi / 18.0f));
+    return __cosf(__fmul_rn(q, kPi / 18.0f));
 }
 template <> __device__ __forceinline__ float kernel_dF<DARB_HALF_COSINE>(float q) {
-    return -(kPi / 18.0f) * sinf(q * (kPi / 18.0f));
+    return -(kPi / 18.0f) * __sinf(q * (kPi / 18.0f));
 }
 
 template <> __device__ __forceinline__ float kernel_F<DARB_RAISED_COSINE>(float q) {
-    return __fmaf_rn(0.5f, cosf(__fmul_rn(__fsqrt_rn(q), kPi / 2.5f)), 0.5f);
+    return __fmaf_rn(0.5f, __cosf(__fmul_rn(__fsqrt_rn(q), kPi / 2.5f)), 0.5f);
 }
 template <> __device__ __forceinline__ float kernel_dF<DARB_RAISED_COSINE>(float q) {
     // -(k/4) sin(k sqrt q) / sqrt q, k = pi/2.5; limit -k^2/4 at q = 0.
     constexpr float k = kPi / 2.5f;
     if (q < 1e-6f) return -0.25f * k * k + (k * k * k * k / 24.0f) * q;
     const float r = sqrtf(q);
-    return -0.25f * k * sinf(k * r) / r;
+    return -0.25f * k * __sinf(k * r) / r;
 }
 
 template <> __device__ __forceinline__ float kernel_F<DARB_MOD_SINC>(float q) {
-    const float x = __fmul_rn(__fsqrt_rn(q), kPi / 3.0f);
-    if (x < 1e-2f) {  // sin x / x = 1 - x^2/6 + x^4/120
-        const float x2 = __fmul_rn(x, x);
-        return __fmaf_rn(x2, __fmaf_rn(x2, 1.0f / 120.0f, -1.0f / 6.0f), 1.0f);
-    }
-    return __fdiv_rn(fabsf(sinf(x)), x);
+    // x = pi sqrt(q) / 3, so x^2 = (pi^2 / 9) q; sin(x)/x >= 0 on the main lobe
+    return fmaxf(sinc_series(__fmul_rn(q, kPi * kPi / 9.0f)), 0.0f);
 }
 template <> __device__ __forceinline__ float kernel_dF<DARB_MOD_SINC>(float q) {
     // (x cos x - sin x) / (2 q x), x = pi sqrt(q)/3; series below x = 0.3.
@@ -90,15 +100,15 @@ template <> __device__ __forceinline__ float kernel_dF<DARB_MOD_SINC>(float q) {
                (a * a * a * a / 90720.0f) * q * q * q;
     }
     float s, c;
-    sincosf(x, &s, &c);
+    __sincosf(x, &s, &c);
     return (x * c - s) / (2.0f * q * x);
 }
 
 template <> __device__ __forceinline__ float kernel_F<DARB_INV_QUADRIC>(float q) {
-    return __fdiv_rn(1.0f, __fadd_rn(1.0f, q));
+    return __fdividef(1.0f, __fadd_rn(1.0f, q));
 }
 template <> __device__ __forceinline__ float kernel_dF<DARB_INV_QUADRIC>(float q) {
-    const float r = 1.0f / (1.0f + q);
+    const float r = __fdividef(1.0f, 1.0f + q);
     return -r * r;
 }
 

@@ -2,10 +2,12 @@
 // splat run (paper Sec. 4.1 "alpha blending ... similar to 3DGS", Eq. HalfCosine and
 // Eq. 2DSplattedFunction; forward and backward listings of Sec. B).
 //
-// One CTA per tile, one thread per pixel.  The tile's run is consumed in batches of
-// TILE*TILE splats: each thread gathers one splat's record (mean, conic, opacity, colour)
-// into shared memory, then every thread walks the batch.  A CTA-wide vote ends the loop once
-// every pixel of the tile has stopped (T < 1e-4) -- the early termination of 3DGS.
+// One CTA per tile.  Each thread owns PIX pixels of one column of the tile (rows r, r + TILE/PIX,
+// ...), so every splat record loaded from shared memory serves PIX pixels and dx is shared.  The
+// tile's run is consumed in batches of NT records (NT = threads): each thread gathers one splat's
+// record (mean, conic, opacity, colour) into shared memory, then every thread walks the batch.  A
+// CTA-wide vote ends the loop once every pixel of the tile has stopped (T < 1e-4) -- the early
+// termination of 3DGS.
 //
 // The support test uses the fixed FP32 sequence conic_q(), and alpha / the kernel value are
 // computed by the same inline code in forward and backward, so the backward re-takes exactly
@@ -20,34 +22,53 @@ struct Bg {
     float r, g, b;
 };
 
+template <int TILE>
+struct RenderShape {
+    static constexpr int PIX = TILE >= 16 ? 2 : 1;   // pixels per thread
+    static constexpr int NT = TILE * TILE / PIX;      // threads per CTA = records per batch
+    static constexpr int ROWS = TILE / PIX;           // row stride between a thread's pixels
+};
+
 template <int KIND, int TILE>
-__global__ void __launch_bounds__(TILE *TILE)
+__global__ void __launch_bounds__(RenderShape<TILE>::NT)
 k_render_fwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ values,
              const float2 *__restrict__ mean2d, const float4 *__restrict__ conic_o,
              const float *__restrict__ rgb, int W, int H, int tiles_x, float qmax, int strict, Bg bg,
              float *__restrict__ image, float *__restrict__ t_final, uint32_t *__restrict__ last,
              uint32_t *__restrict__ n_contrib) {
-    constexpr int NT = TILE * TILE;
-    constexpr int BATCH = NT < 256 ? NT : 256;
-    __shared__ float2 s_xy[BATCH];
-    __shared__ float4 s_co[BATCH];  // A, 2B, C, opacity
-    __shared__ float s_rgb[BATCH][3];
+    using S = RenderShape<TILE>;
+    constexpr int NT = S::NT, PIX = S::PIX;
+    __shared__ float2 s_xy[NT];
+    __shared__ float4 s_co[NT];  // A, 2B, C, opacity
+    __shared__ float s_rgb[NT][3];
 
     const int tile = blockIdx.x;
     const int tx = tile % tiles_x, ty = tile / tiles_x;
-    const int px = tx * TILE + (threadIdx.x % TILE), py = ty * TILE + (threadIdx.x / TILE);
-    const bool inside = px < W && py < H;
-    const float fpx = (float)px + 0.5f, fpy = (float)py + 0.5f;
+    const int px = tx * TILE + (threadIdx.x % TILE);
+    const int py0 = ty * TILE + (threadIdx.x / TILE);
+    const float fpx = (float)px + 0.5f;
     const uint2 r = ranges[tile];
     const int start = (int)r.x, end = (int)r.y;
 
-    float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
-    uint32_t count = 0, lastp = 0;
-    bool done = !inside;
-    for (int b0 = start; b0 < end; b0 += BATCH) {
-        if (__syncthreads_count(done) == NT) break;
+    float fpy[PIX], T[PIX], C0[PIX], C1[PIX], C2[PIX];
+    uint32_t count[PIX], lastp[PIX];
+    bool done[PIX];
+#pragma unroll
+    for (int k = 0; k < PIX; ++k) {
+        const int py = py0 + k * S::ROWS;
+        fpy[k] = (float)py + 0.5f;
+        T[k] = 1.0f;
+        C0[k] = C1[k] = C2[k] = 0.0f;
+        count[k] = lastp[k] = 0;
+        done[k] = !(px < W && py < H);
+    }
+    for (int b0 = start; b0 < end; b0 += NT) {
+        bool all_done = true;
+#pragma unroll
+        for (int k = 0; k < PIX; ++k) all_done &= done[k];
+        if (__syncthreads_count(all_done) == NT) break;
         const int idx = b0 + (int)threadIdx.x;
-        if ((int)threadIdx.x < BATCH && idx < end) {
+        if (idx < end) {
             const uint32_t id = values[idx];
             s_xy[threadIdx.x] = mean2d[id];
             float4 co = conic_o[id];
@@ -58,37 +79,50 @@ k_render_fwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ valu
             s_rgb[threadIdx.x][2] = rgb[3 * (size_t)id + 2];
         }
         __syncthreads();
-        const int nb = min(BATCH, end - b0);
-        for (int j = 0; j < nb && !done; ++j) {
+        if (all_done) continue;
+        const int nb = min(NT, end - b0);
+        for (int j = 0; j < nb; ++j) {
             const float2 xy = s_xy[j];
             const float4 co = s_co[j];
-            const float dx = __fsub_rn(xy.x, fpx), dy = __fsub_rn(xy.y, fpy);
-            const float q = conic_q(dx, dy, co.x, co.y, co.z);
-            if (!in_support(q, qmax, strict)) continue;
-            const float alpha = fminf(kAlphaMax, __fmul_rn(co.w, kernel_F<KIND>(q)));
-            if (alpha < kAlphaMin) continue;
-            const float Tn = T * (1.0f - alpha);
-            if (Tn < kTMin) {
-                done = true;
-                break;
+            const float dx = __fsub_rn(xy.x, fpx);
+            bool any_live = false;
+#pragma unroll
+            for (int k = 0; k < PIX; ++k) {
+                if (done[k]) continue;
+                any_live = true;
+                const float dy = __fsub_rn(xy.y, fpy[k]);
+                const float q = conic_q(dx, dy, co.x, co.y, co.z);
+                if (!in_support(q, qmax, strict)) continue;
+                const float alpha = fminf(kAlphaMax, __fmul_rn(co.w, kernel_F<KIND>(q)));
+                if (alpha < kAlphaMin) continue;
+                const float Tn = T[k] * (1.0f - alpha);
+                if (Tn < kTMin) {
+                    done[k] = true;
+                    continue;
+                }
+                const float w = alpha * T[k];
+                C0[k] = fmaf(s_rgb[j][0], w, C0[k]);
+                C1[k] = fmaf(s_rgb[j][1], w, C1[k]);
+                C2[k] = fmaf(s_rgb[j][2], w, C2[k]);
+                T[k] = Tn;
+                ++count[k];
+                lastp[k] = (uint32_t)(b0 - start + j + 1);
             }
-            const float w = alpha * T;
-            C0 = fmaf(s_rgb[j][0], w, C0);
-            C1 = fmaf(s_rgb[j][1], w, C1);
-            C2 = fmaf(s_rgb[j][2], w, C2);
-            T = Tn;
-            ++count;
-            lastp = (uint32_t)(b0 - start + j + 1);
+            if (!any_live) break;
         }
     }
-    if (inside) {
-        const size_t pix = (size_t)py * W + px, plane = (size_t)W * H;
-        image[pix] = fmaf(T, bg.r, C0);
-        image[plane + pix] = fmaf(T, bg.g, C1);
-        image[2 * plane + pix] = fmaf(T, bg.b, C2);
-        t_final[pix] = T;
-        last[pix] = lastp;
-        n_contrib[pix] = count;
+    const size_t plane = (size_t)W * H;
+#pragma unroll
+    for (int k = 0; k < PIX; ++k) {
+        const int py = py0 + k * S::ROWS;
+        if (!(px < W && py < H)) continue;
+        const size_t pix = (size_t)py * W + px;
+        image[pix] = fmaf(T[k], bg.r, C0[k]);
+        image[plane + pix] = fmaf(T[k], bg.g, C1[k]);
+        image[2 * plane + pix] = fmaf(T[k], bg.b, C2[k]);
+        t_final[pix] = T[k];
+        last[pix] = lastp[k];
+        n_contrib[pix] = count[k];
     }
 }
 
@@ -101,58 +135,70 @@ __device__ __forceinline__ float warp_sum(float v) {
 // Backward: replay each pixel back to front from its last contributor.  With T_k the
 // transmittance in front of splat k and S the colour composited behind it (background
 // included), dC/dalpha_k = c_k T_k - S / (1 - alpha_k) and dC/dc_k = alpha_k T_k.
-// Per splat and tile the contributions are summed by warp shuffles, then across warps in
-// shared memory, then added to grad2d with one vector atomic per 4 floats.
+// Per splat and tile the contributions of a thread's pixels are added in registers, summed
+// over the warp by shuffles, then across warps in shared memory, then added to grad2d with one
+// vector atomic per 4 floats.
 template <int KIND, int TILE>
-__global__ void __launch_bounds__(TILE *TILE)
+__global__ void __launch_bounds__(RenderShape<TILE>::NT)
 k_render_bwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ values,
              const float2 *__restrict__ mean2d, const float4 *__restrict__ conic_o,
              const float *__restrict__ rgb, int W, int H, int tiles_x, float qmax, int strict, Bg bg,
              const float *__restrict__ t_final, const uint32_t *__restrict__ last,
              const float *__restrict__ dL_dimage, float4 *__restrict__ grad2d) {
-    constexpr int NT = TILE * TILE;
+    using S = RenderShape<TILE>;
+    constexpr int NT = S::NT, PIX = S::PIX;
     constexpr int NW = NT / 32;
-    constexpr int BATCH = NT < 256 ? NT : 256;
-    __shared__ float2 s_xy[BATCH];
-    __shared__ float4 s_co[BATCH];
-    __shared__ float s_rgb[BATCH][3];
-    __shared__ uint32_t s_id[BATCH];
-    __shared__ float s_acc[BATCH][9];
+    __shared__ float2 s_xy[NT];
+    __shared__ float4 s_co[NT];
+    __shared__ float s_rgb[NT][3];
+    __shared__ uint32_t s_id[NT];
+    __shared__ float s_acc[NT][9];
     __shared__ uint32_t s_max[NW];
 
     const int tile = blockIdx.x;
     const int tx = tile % tiles_x, ty = tile / tiles_x;
-    const int px = tx * TILE + (threadIdx.x % TILE), py = ty * TILE + (threadIdx.x / TILE);
-    const bool inside = px < W && py < H;
-    const float fpx = (float)px + 0.5f, fpy = (float)py + 0.5f;
+    const int px = tx * TILE + (threadIdx.x % TILE);
+    const int py0 = ty * TILE + (threadIdx.x / TILE);
+    const float fpx = (float)px + 0.5f;
     const uint2 r = ranges[tile];
     const int start = (int)r.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const size_t plane = (size_t)W * H;
 
-    float T = 1.0f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
-    uint32_t my_last = 0;
-    if (inside) {
-        const size_t pix = (size_t)py * W + px, plane = (size_t)W * H;
-        T = t_final[pix];
-        my_last = last[pix];
-        g0 = dL_dimage[pix];
-        g1 = dL_dimage[plane + pix];
-        g2 = dL_dimage[2 * plane + pix];
+    float fpy[PIX], T[PIX], g0[PIX], g1[PIX], g2[PIX], S0[PIX], S1[PIX], S2[PIX];
+    uint32_t my_last[PIX];
+    uint32_t m = 0;
+#pragma unroll
+    for (int k = 0; k < PIX; ++k) {
+        const int py = py0 + k * S::ROWS;
+        fpy[k] = (float)py + 0.5f;
+        T[k] = 1.0f;
+        g0[k] = g1[k] = g2[k] = 0.0f;
+        my_last[k] = 0;
+        if (px < W && py < H) {
+            const size_t pix = (size_t)py * W + px;
+            T[k] = t_final[pix];
+            my_last[k] = last[pix];
+            g0[k] = dL_dimage[pix];
+            g1[k] = dL_dimage[plane + pix];
+            g2[k] = dL_dimage[2 * plane + pix];
+        }
+        S0[k] = T[k] * bg.r;
+        S1[k] = T[k] * bg.g;
+        S2[k] = T[k] * bg.b;
+        m = max(m, my_last[k]);
     }
-    float S0 = T * bg.r, S1 = T * bg.g, S2 = T * bg.b;
-
-    uint32_t m = my_last;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, off));
     if (lane == 0) s_max[warp] = m;
-    for (int i = threadIdx.x; i < BATCH * 9; i += NT) (&s_acc[0][0])[i] = 0.0f;
+    for (int i = threadIdx.x; i < NT * 9; i += NT) (&s_acc[0][0])[i] = 0.0f;
     __syncthreads();
     int nlast = 0;
 #pragma unroll
     for (int w = 0; w < NW; ++w) nlast = max(nlast, (int)s_max[w]);
 
-    for (int bend = nlast; bend > 0; bend -= BATCH) {
-        const int bstart = max(0, bend - BATCH);
+    for (int bend = nlast; bend > 0; bend -= NT) {
+        const int bstart = max(0, bend - NT);
         const int cnt = bend - bstart;
         if ((int)threadIdx.x < cnt) {
             const uint32_t id = values[start + bstart + threadIdx.x];
@@ -172,48 +218,54 @@ k_render_bwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ valu
 #pragma unroll
             for (int u = 0; u < 9; ++u) v[u] = 0.0f;
             bool contrib = false;
-            if (pos < (int)my_last) {
-                const float2 xy = s_xy[j];
-                const float4 co = s_co[j];
-                const float dx = __fsub_rn(xy.x, fpx), dy = __fsub_rn(xy.y, fpy);
+            const float2 xy = s_xy[j];
+            const float4 co = s_co[j];
+            const float dx = __fsub_rn(xy.x, fpx);
+#pragma unroll
+            for (int k = 0; k < PIX; ++k) {
+                if (pos >= (int)my_last[k]) continue;
+                const float dy = __fsub_rn(xy.y, fpy[k]);
                 const float q = conic_q(dx, dy, co.x, co.y, co.z);
-                if (in_support(q, qmax, strict)) {
-                    const float F = kernel_F<KIND>(q);
-                    const float of = __fmul_rn(co.w, F);
-                    const float alpha = fminf(kAlphaMax, of);
-                    if (alpha >= kAlphaMin) {
-                        contrib = true;
-                        const float om = 1.0f - alpha;
-                        const float Tk = T / om;
-                        const float c0 = s_rgb[j][0], c1 = s_rgb[j][1], c2 = s_rgb[j][2];
-                        const float dalpha = g0 * (c0 * Tk - S0 / om) + g1 * (c1 * Tk - S1 / om) + g2 * (c2 * Tk - S2 / om);
-                        const float w = alpha * Tk;
-                        S0 = fmaf(c0, w, S0);
-                        S1 = fmaf(c1, w, S1);
-                        S2 = fmaf(c2, w, S2);
-                        T = Tk;
-                        v[6] = w * g0;
-                        v[7] = w * g1;
-                        v[8] = w * g2;
-                        if (!(of > kAlphaMax)) {
-                            v[5] = F * dalpha;
-                            const float dq = co.w * kernel_dF<KIND>(q) * dalpha;
-                            const float B = 0.5f * co.y;
-                            v[0] = 2.0f * dq * (co.x * dx + B * dy);
-                            v[1] = 2.0f * dq * (B * dx + co.z * dy);
-                            v[2] = dq * dx * dx;
-                            v[3] = 2.0f * dq * dx * dy;
-                            v[4] = dq * dy * dy;
-                        }
-                    }
+                if (!in_support(q, qmax, strict)) continue;
+                const float F = kernel_F<KIND>(q);
+                const float of = __fmul_rn(co.w, F);
+                const float alpha = fminf(kAlphaMax, of);
+                if (alpha < kAlphaMin) continue;
+                contrib = true;
+                const float om = 1.0f - alpha;
+                const float iom = __fdividef(1.0f, om);
+                const float Tk = T[k] * iom;
+                const float c0 = s_rgb[j][0], c1 = s_rgb[j][1], c2 = s_rgb[j][2];
+                const float dalpha = g0[k] * (c0 * Tk - S0[k] * iom) + g1[k] * (c1 * Tk - S1[k] * iom) +
+                                     g2[k] * (c2 * Tk - S2[k] * iom);
+                const float w = alpha * Tk;
+                S0[k] = fmaf(c0, w, S0[k]);
+                S1[k] = fmaf(c1, w, S1[k]);
+                S2[k] = fmaf(c2, w, S2[k]);
+                T[k] = Tk;
+                v[6] = fmaf(w, g0[k], v[6]);
+                v[7] = fmaf(w, g1[k], v[7]);
+                v[8] = fmaf(w, g2[k], v[8]);
+                if (!(of > kAlphaMax)) {
+                    v[5] = fmaf(F, dalpha, v[5]);
+                    const float dq = co.w * kernel_dF<KIND>(q) * dalpha;
+                    const float B = 0.5f * co.y;
+                    v[0] = fmaf(2.0f * dq, co.x * dx + B * dy, v[0]);
+                    v[1] = fmaf(2.0f * dq, B * dx + co.z * dy, v[1]);
+                    v[2] = fmaf(dq, dx * dx, v[2]);
+                    v[3] = fmaf(2.0f * dq, dx * dy, v[3]);
+                    v[4] = fmaf(dq, dy * dy, v[4]);
                 }
             }
             if (__any_sync(0xffffffffu, contrib)) {
 #pragma unroll
                 for (int u = 0; u < 9; ++u) v[u] = warp_sum(v[u]);
-                if (lane == 0) {
+                if (lane < 9) {
+                    float val = v[0];
 #pragma unroll
-                    for (int u = 0; u < 9; ++u) atomicAdd(&s_acc[j][u], v[u]);
+                    for (int u = 1; u < 9; ++u)
+                        if (lane == u) val = v[u];
+                    atomicAdd(&s_acc[j][lane], val);
                 }
             }
         }
@@ -240,9 +292,9 @@ template <int KIND, int TILE>
 cudaError_t fwd_t(int n_tiles, const uint2 *ranges, const uint32_t *values, const float2 *mean2d,
                   const float4 *conic_o, const float *rgb, const Cam &cam, int tiles_x, float qmax, int strict,
                   float *image, float *t_final, uint32_t *last, uint32_t *n_contrib, cudaStream_t st) {
-    k_render_fwd<KIND, TILE><<<n_tiles, TILE * TILE, 0, st>>>(ranges, values, mean2d, conic_o, rgb, cam.W, cam.H, tiles_x,
-                                                               qmax, strict, Bg{cam.bg[0], cam.bg[1], cam.bg[2]}, image,
-                                                               t_final, last, n_contrib);
+    k_render_fwd<KIND, TILE><<<n_tiles, RenderShape<TILE>::NT, 0, st>>>(
+        ranges, values, mean2d, conic_o, rgb, cam.W, cam.H, tiles_x, qmax, strict, Bg{cam.bg[0], cam.bg[1], cam.bg[2]},
+        image, t_final, last, n_contrib);
     return cudaGetLastError();
 }
 
@@ -250,9 +302,9 @@ template <int KIND, int TILE>
 cudaError_t bwd_t(int n_tiles, const uint2 *ranges, const uint32_t *values, const float2 *mean2d,
                   const float4 *conic_o, const float *rgb, const Cam &cam, int tiles_x, float qmax, int strict,
                   const float *t_final, const uint32_t *last, const float *dL, float *grad2d, cudaStream_t st) {
-    k_render_bwd<KIND, TILE><<<n_tiles, TILE * TILE, 0, st>>>(ranges, values, mean2d, conic_o, rgb, cam.W, cam.H, tiles_x,
-                                                               qmax, strict, Bg{cam.bg[0], cam.bg[1], cam.bg[2]}, t_final,
-                                                               last, dL, reinterpret_cast<float4 *>(grad2d));
+    k_render_bwd<KIND, TILE><<<n_tiles, RenderShape<TILE>::NT, 0, st>>>(
+        ranges, values, mean2d, conic_o, rgb, cam.W, cam.H, tiles_x, qmax, strict, Bg{cam.bg[0], cam.bg[1], cam.bg[2]},
+        t_final, last, dL, reinterpret_cast<float4 *>(grad2d));
     return cudaGetLastError();
 }
 

@@ -445,3 +445,30 @@ class DarbRasterize(torch.autograd.Function):
         s, proj, bins, img, r = ctx.state
         g, _ = r.backward(s, proj, bins, img, dimage.float().contiguous())
         return g.dmeans, g.dscales, g.dquats, g.dopacities, g.dsh, None, None
+
+
+def autotune_tile(splats: SplatTensors, cams, kernel="half_cosine", candidates=(8, 16, 32), reps=5,
+                  strategy=DARB_SORT_DEPTH_THEN_TILE):
+    """Tile size with the fastest forward (preprocess, bin/sort, compositing) over `cams`.
+
+    Each candidate is warmed once per camera (which also sizes its instance capacity), then
+    timed with CUDA events over `reps` passes of the camera list.  Returns
+    (best_tile, {tile: ms per view}).  All cameras must share one resolution.
+    """
+    times = {}
+    for t in candidates:
+        rast = Rasterizer(cams[0], kernel, t, strategy=strategy)
+        for cam in cams:  # warm-up and capacity sizing
+            rast.cam = cam
+            rast.forward(splats)
+        torch.cuda.synchronize()
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        start.record()
+        for _ in range(reps):
+            for cam in cams:
+                rast.cam = cam
+                rast.forward(splats)
+        end.record()
+        torch.cuda.synchronize()
+        times[t] = start.elapsed_time(end) / (reps * len(cams))
+    return min(times, key=times.get), times

@@ -124,10 +124,11 @@ class ClockSampler:
 class TrainStep:
     """Device buffers of one training replica and the per-step sequence of C-ABI calls."""
 
-    def __init__(self, splats, cams, kernel, tile, device, strategy=0):
+    def __init__(self, splats, cams, kernel, tile, device, strategy=0, fused=True):
         from paper_2501_12369_gb300 import darb
         self.darb = darb
         self.strategy = int(strategy)
+        self.fused = bool(fused)
         self.L = darb.lib()
         self.cams = cams
         self.tile = tile
@@ -250,18 +251,25 @@ class TrainStep:
                                    self.tile, ctypes.byref(self.s_img), d._p(self.dL), d._p(self.grad2d), st),
                  "render_bwd")
         rec(5)
-        d._check(L.darb_preprocess_bwd(ctypes.byref(self.s_splats), c, self.kp_ref, ctypes.byref(self.s_proj),
-                                       d._p(self.grad2d), ctypes.byref(self.s_grads), st), "preprocess_bwd")
-        rec(6)
         self.step_no += 1
         cfg = d.darb_adam_config(LRS["means"], LRS["scales"], LRS["quats"], LRS["opacities"], LRS["sh_dc"],
                                  LRS["sh_rest"], 0.9, 0.999, 1e-15, self.step_no)
+        if self.fused:
+            d._check(L.darb_preprocess_bwd_adam(ctypes.byref(self.s_params), c, self.kp_ref, ctypes.byref(self.s_proj),
+                                                d._p(self.grad2d), ctypes.byref(self.s_state), ctypes.byref(cfg), st),
+                     "preprocess_bwd_adam")
+            rec(6)
+            return
+        d._check(L.darb_preprocess_bwd(ctypes.byref(self.s_splats), c, self.kp_ref, ctypes.byref(self.s_proj),
+                                       d._p(self.grad2d), ctypes.byref(self.s_grads), st), "preprocess_bwd")
+        rec(6)
         d._check(L.darb_adam_step(ctypes.byref(self.s_params), ctypes.byref(self.s_grads), ctypes.byref(self.s_state),
                                   ctypes.byref(cfg), st), "adam")
         rec(7)
 
 
-STAGES = ["preprocess", "bin_sort", "render_fwd", "l1_loss", "render_bwd", "preprocess_bwd", "adam"]
+STAGES_FUSED = ["preprocess", "bin_sort", "render_fwd", "l1_loss", "render_bwd", "preprocess_bwd_adam"]
+STAGES_SEPARATE = ["preprocess", "bin_sort", "render_fwd", "l1_loss", "render_bwd", "preprocess_bwd", "adam"]
 
 
 def algorithmic_bytes(stage, n, M, passes, sh_k, strategy=0, tile_passes=2):
@@ -282,6 +290,11 @@ def algorithmic_bytes(stage, n, M, passes, sh_k, strategy=0, tile_passes=2):
     if stage == "adam":
         params = 3 + 3 + 4 + 1 + sh_k * 3
         return n * (params * 28 + 4 * 8)
+    if stage == "preprocess_bwd_adam":
+        # per splat: raw parameters and both moments read and written (6 x 4 B per parameter),
+        # activated scales and opacity read and written, grad2d (48 B), radius and clamped flags
+        params = 3 + 3 + 4 + 1 + sh_k * 3
+        return n * (params * 24 + 2 * (12 + 4) + 48 + 4 + 1)
     return None
 
 
@@ -353,7 +366,8 @@ def run_ours(args):
     build.build()
     splats, cams = synth.scene_3m_1080p()
     candidates = [args.tile] if args.tile else [8, 16, 32]
-    ts = TrainStep(splats, cams, args.kernel, candidates[0], device, args.sort)
+    ts = TrainStep(splats, cams, args.kernel, candidates[0], device, args.sort, fused=not args.unfused)
+    STAGES = STAGES_SEPARATE if args.unfused else STAGES_FUSED
     # replicas: rank r trains on its own camera sequence
     cam_seq = [(rank * 37 + i) % len(cams) for i in range(args.warmup + args.steps)]
     targets = [torch.from_numpy(synth.random_target(1080, 1920, seed=10 + i)).to(device) for i in range(4)]
@@ -392,7 +406,7 @@ def run_ours(args):
     torch.cuda.synchronize()
 
     # timed training steps with per-stage events
-    n_ev = 8
+    n_ev = len(STAGES) + 1
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(n_ev)] for _ in range(args.steps)]
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(local)
@@ -453,7 +467,8 @@ def run_ours(args):
     passes = (32 + int(np.ceil(np.log2(ts.tx * ts.ty))) + 7) // 8
     sh_k = (splats.sh_degree + 1) ** 2
     dominant = max(stage_ms, key=stage_ms.get)
-    hbm_stages = {s: stage_ms[s] for s in ("preprocess", "bin_sort", "preprocess_bwd", "adam")}
+    hbm_stages = {s: stage_ms[s] for s in ("preprocess", "bin_sort", "preprocess_bwd", "adam", "preprocess_bwd_adam")
+                  if s in stage_ms}
     peaks = load_peaks()
     peak_gbs = peaks["hbm_gbs"] if peaks else 6800.0
     tile_bits = int(np.ceil(np.log2(ts.tx * ts.ty)))
@@ -485,7 +500,9 @@ def run_ours(args):
         "gpu_launches": None,
         "clocks": clk,
     }
-    line["gpu_launches"] = args.steps * launches_per_step(args.sort, int(np.ceil(np.log2(ts.tx * ts.ty))))
+    line["gpu_launches"] = args.steps * launches_per_step(args.sort, int(np.ceil(np.log2(ts.tx * ts.ty))),
+                                                          not args.unfused)
+    line["config"]["optimizer"] = "adam (separate)" if args.unfused else "adam fused into preprocess backward"
     line["config"]["sort"] = "depth_then_tile" if args.sort == 0 else "keys64"
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(splats, cams, args.kernel, args.tile)
@@ -495,15 +512,15 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def launches_per_step(strategy, tile_bits):
+def launches_per_step(strategy, tile_bits, fused=True):
     """Kernels of libdarb.so launched per training step (memsets excluded)."""
     if strategy == 1:  # 64-bit keys: block sums, scan, duplicate, histogram, hist scan, passes, ranges
         sort = 6 + (32 + tile_bits + 7) // 8
     else:  # depth keys, histogram, hist scan, 4 depth passes, block sums, scan, tile diff, tile setup,
         # offsets, duplicate, tile passes
         sort = 3 + 4 + 6 + max(1, (tile_bits + 7) // 8)
-    # preprocess, render_fwd, l1, render_bwd, preprocess_bwd, 5 Adam groups
-    return 1 + sort + 1 + 1 + 1 + 1 + 5
+    # preprocess, render_fwd, l1, render_bwd, then preprocess_bwd + 5 Adam groups or one fused kernel
+    return 1 + sort + 1 + 1 + 1 + (1 if fused else 1 + 5)
 
 
 # ----------------------------------------------------------------------------- reference arm
@@ -545,6 +562,7 @@ def main():
     ap.add_argument("--tile", type=int, default=0, help="tile size; 0 = autotune over 8, 16, 32")
     ap.add_argument("--sort", type=int, default=0, help="0: depth then tile (default), 1: 64-bit keys")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--unfused", action="store_true", help="separate preprocess backward and Adam kernels")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

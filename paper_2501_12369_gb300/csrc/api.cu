@@ -229,8 +229,33 @@ darb_status darb_adam_step(const darb_train_params *params, const darb_splat_gra
                        state->v_scales, state->m_quats, state->v_quats, state->m_opac, state->v_opac,
                        state->m_sh, state->v_sh};
     for (const void *q : p)
-        if (!q) return DARB_ERR_INVALID_ARG;
+        if (!q || !aligned16(q)) return DARB_ERR_INVALID_ARG;  // float4 lanes over every group
     DARB_CUDA_TRY(launch_adam(*params, *grads, *state, *cfg, reinterpret_cast<cudaStream_t>(stream)));
+    return DARB_OK;
+}
+
+darb_status darb_preprocess_bwd_adam(const darb_train_params *params, const darb_camera *cam,
+                                     const darb_kernel_params *kparams, const darb_projected *proj,
+                                     const float *grad2d, const darb_adam_state *state, const darb_adam_config *cfg,
+                                     darb_stream stream) {
+    if (!params || !state || !cfg || params->n < 0 || params->sh_degree < 0 || params->sh_degree > 3 ||
+        !valid_camera(cam) || !valid_kernel(kparams) || cfg->step < 1 || !(cfg->beta1 >= 0.0f && cfg->beta1 < 1.0f) ||
+        !(cfg->beta2 >= 0.0f && cfg->beta2 < 1.0f) || !(cfg->eps > 0.0f))
+        return DARB_ERR_INVALID_ARG;
+    if (params->n == 0) return DARB_OK;
+    if (!valid_projected(proj) || !grad2d || !aligned16(grad2d)) return DARB_ERR_INVALID_ARG;
+    const void *p[] = {params->means, params->log_scales, params->quats, params->opacity_logits, params->sh,
+                       params->scales, params->opacities, state->m_means, state->v_means, state->m_scales,
+                       state->v_scales, state->m_quats, state->v_quats, state->m_opac, state->v_opac,
+                       state->m_sh, state->v_sh};
+    for (const void *q : p)
+        if (!q) return DARB_ERR_INVALID_ARG;
+    const void *a16[] = {params->quats, state->m_quats, state->v_quats, params->sh, state->m_sh, state->v_sh};
+    for (const void *q : a16)
+        if (!aligned16(q)) return DARB_ERR_INVALID_ARG;
+    DARB_CUDA_TRY(launch_preprocess_bwd_adam(params->n, params->sh_degree, *params, *state, make_adam_consts(*cfg),
+                                             make_cam(*cam), kparams->psi, proj->radius, proj->clamped, grad2d,
+                                             reinterpret_cast<cudaStream_t>(stream)));
     return DARB_OK;
 }
 

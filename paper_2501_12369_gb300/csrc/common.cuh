@@ -1,6 +1,7 @@
 // Shared device helpers of libdarb.so (GB300, sm_103a).
 #pragma once
 
+#include <cmath>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -138,6 +139,31 @@ __device__ __forceinline__ float conic_q(float dx, float dy, float A, float B2, 
     const float g = __fmaf_rn(A, dx, e);
     const float h = __fmul_rn(__fmul_rn(C, dy), dy);
     return __fmaf_rn(dx, g, h);
+}
+
+// ---------------------------------------------------------------------------
+// Adam (Kingma & Ba) on one element: m, v moments; bias corrections as reciprocals.
+
+struct AdamConsts {
+    float lr_means, lr_scales, lr_quats, lr_opacities, lr_sh_dc, lr_sh_rest;
+    float b1, b2, eps, ibc1, ibc2;
+};
+
+__device__ __forceinline__ void adam_apply(float &p, float g, float &m, float &v, float lr, const AdamConsts &c) {
+    m = fmaf(c.b1, m, (1.0f - c.b1) * g);
+    v = fmaf(c.b2, v, (1.0f - c.b2) * g * g);
+    p -= lr * (m * c.ibc1) / (sqrtf(v * c.ibc2) + c.eps);
+}
+
+inline AdamConsts make_adam_consts(const darb_adam_config &c) {
+    AdamConsts a;
+    a.lr_means = c.lr_means; a.lr_scales = c.lr_scales; a.lr_quats = c.lr_quats;
+    a.lr_opacities = c.lr_opacities; a.lr_sh_dc = c.lr_sh_dc; a.lr_sh_rest = c.lr_sh_rest;
+    a.b1 = c.beta1; a.b2 = c.beta2; a.eps = c.eps;
+    // bias corrections on the host in double: 1 - beta^t loses digits for beta near 1
+    a.ibc1 = (float)(1.0 / (1.0 - std::pow((double)c.beta1, (double)c.step)));
+    a.ibc2 = (float)(1.0 / (1.0 - std::pow((double)c.beta2, (double)c.step)));
+    return a;
 }
 
 // ---------------------------------------------------------------------------

@@ -27,6 +27,10 @@ cudaError_t launch_preprocess_bwd(int n, const darb_splats &sp, const Cam &cam, 
                                   const int *radius, const uint8_t *clamped, const float *grad2d,
                                   const GradOut &out, cudaStream_t st);
 
+cudaError_t launch_preprocess_bwd_adam(int n, int sh_degree, const darb_train_params &p, const darb_adam_state &s,
+                                       const AdamConsts &ac, const Cam &cam, float psi, const int *radius,
+                                       const uint8_t *clamped, const float *grad2d, cudaStream_t st);
+
 // binning.cu
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;

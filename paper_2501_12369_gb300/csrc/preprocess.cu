@@ -6,6 +6,8 @@
 // order and the per-pixel support test) follows a fixed IEEE FP32 operation sequence
 // written with __f*_rn intrinsics, which the compiler neither contracts nor reorders,
 // so its results are bit-reproducible.  SH colour and the backward use ordinary FP32.
+#include <atomic>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -306,30 +308,17 @@ k_preprocess(int n, const float *__restrict__ means, const float *__restrict__ s
 // Sigma = M M^T with M = R(q/|q|) diag(s), and the SH colour (coefficients and viewing
 // direction).
 
-template <int DEG>
-__global__ void __launch_bounds__(256)
-k_preprocess_bwd(int n, const float *__restrict__ means, const float *__restrict__ scales,
-                 const float4 *__restrict__ quats, const float *__restrict__ sh, Cam cam, float psi,
-                 const int *__restrict__ radius, const uint8_t *__restrict__ clamped,
-                 const float4 *__restrict__ grad2d, GradOut out) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+template <int DEG, class LoadCoef>
+__device__ __forceinline__ void splat_backward(int i, const float *__restrict__ means, const float *__restrict__ scales,
+                                               const float4 *__restrict__ quats, LoadCoef load_coef,
+                                               const Cam &cam, float psi, uint8_t cl,
+                                               const float4 *__restrict__ grad2d, float *dm, float *ds, float *dq,
+                                               float &dop, float (*dcoef)[3]) {
     constexpr int K = (DEG + 1) * (DEG + 1);
-    float *dm = out.dmeans + 3 * (size_t)i, *ds = out.dscales + 3 * (size_t)i, *dqo = out.dquats + 4 * (size_t)i;
-    if (radius[i] == 0) {
-        for (int j = 0; j < 3; ++j) dm[j] = ds[j] = 0.0f;
-        reinterpret_cast<float4 *>(out.dquats)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        float zero[K][3];
-#pragma unroll
-        for (int k = 0; k < K; ++k) zero[k][0] = zero[k][1] = zero[k][2] = 0.0f;
-        store_sh<DEG>(out.dsh, i, zero);
-        out.dopacities[i] = 0.0f;
-        return;
-    }
     const float4 g0 = grad2d[3 * (size_t)i], g1 = grad2d[3 * (size_t)i + 1], g2 = grad2d[3 * (size_t)i + 2];
     const float dmx = g0.x, dmy = g0.y, dA = g0.z, dB = g0.w, dC = g1.x, dO = g1.y;
     const float drgb[3] = {g1.z, g1.w, g2.x};
-    out.dopacities[i] = dO;
+    dop = dO;
 
     const float *V = cam.V;
     const float m[3] = {means[3 * (size_t)i], means[3 * (size_t)i + 1], means[3 * (size_t)i + 2]};
@@ -441,8 +430,10 @@ k_preprocess_bwd(int n, const float *__restrict__ means, const float *__restrict
                             y * dR[1][2] + x * dR[2][0] + y * dR[2][1]);
     const float nd = w * gw + x * gx + y * gy + z * gz;
     const float iqn = 1.0f / qn;
-    reinterpret_cast<float4 *>(dqo)[0] =
-        make_float4((gw - w * nd) * iqn, (gx - x * nd) * iqn, (gy - y * nd) * iqn, (gz - z * nd) * iqn);
+    dq[0] = (gw - w * nd) * iqn;
+    dq[1] = (gx - x * nd) * iqn;
+    dq[2] = (gy - y * nd) * iqn;
+    dq[3] = (gz - z * nd) * iqn;
 
     // SH: coefficients and the viewing direction
     float v0 = m[0] - cam.campos[0], v1 = m[1] - cam.campos[1], v2 = m[2] - cam.campos[2];
@@ -450,12 +441,11 @@ k_preprocess_bwd(int n, const float *__restrict__ means, const float *__restrict
     const float dir[3] = {v0 / len, v1 / len, v2 / len};
     float Y[K];
     sh_eval_basis<DEG>(dir[0], dir[1], dir[2], Y);
-    const uint8_t cl = clamped[i];
     float gr[3];
     for (int ch = 0; ch < 3; ++ch) gr[ch] = ((cl >> ch) & 1) ? 0.f : drgb[ch];
     float coef[K][3];
-    load_sh<DEG>(sh, i, coef);
-    float wsum[K], dcoef[K][3];
+    load_coef(coef);
+    float wsum[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         float acc = 0.f;
@@ -466,11 +456,175 @@ k_preprocess_bwd(int n, const float *__restrict__ means, const float *__restrict
         }
         wsum[k] = acc;
     }
-    store_sh<DEG>(out.dsh, i, dcoef);
     float gd[3];
     sh_basis_vjp<DEG>(dir[0], dir[1], dir[2], wsum, gd);
     const float dd = dir[0] * gd[0] + dir[1] * gd[1] + dir[2] * gd[2];
     for (int j = 0; j < 3; ++j) dm[j] = gm[j] + (gd[j] - dir[j] * dd) / len;
+}
+
+
+template <int DEG>
+__global__ void __launch_bounds__(256)
+k_preprocess_bwd(int n, const float *__restrict__ means, const float *__restrict__ scales,
+                 const float4 *__restrict__ quats, const float *__restrict__ sh, Cam cam, float psi,
+                 const int *__restrict__ radius, const uint8_t *__restrict__ clamped,
+                 const float4 *__restrict__ grad2d, GradOut out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    float dm[3] = {0.f, 0.f, 0.f}, ds[3] = {0.f, 0.f, 0.f}, dq[4] = {0.f, 0.f, 0.f, 0.f}, dop = 0.f;
+    float dcoef[K][3];
+#pragma unroll
+    for (int k = 0; k < K; ++k) dcoef[k][0] = dcoef[k][1] = dcoef[k][2] = 0.0f;
+    if (radius[i] != 0)
+        splat_backward<DEG>(
+            i, means, scales, quats, [&](float(*c)[3]) { load_sh<DEG>(sh, i, c); }, cam, psi, clamped[i], grad2d, dm,
+            ds, dq, dop, dcoef);
+    for (int j = 0; j < 3; ++j) {
+        out.dmeans[3 * (size_t)i + j] = dm[j];
+        out.dscales[3 * (size_t)i + j] = ds[j];
+    }
+    reinterpret_cast<float4 *>(out.dquats)[i] = make_float4(dq[0], dq[1], dq[2], dq[3]);
+    out.dopacities[i] = dop;
+    store_sh<DEG>(out.dsh, i, dcoef);
+}
+
+// The same gradients applied at once by Adam to the raw parameters (log-scales, opacity
+// logits), refreshing the activated copies; no gradient goes through HBM.  Means, scales,
+// quaternions and opacities are updated by the splat's own thread (a warp touches one
+// contiguous span of each array).  SH rows (3K floats, 192 B at degree 3) would make every
+// lane's access land in a different line, so their gradients are staged in shared memory and
+// the block then updates its contiguous SH segment with consecutive lanes on consecutive
+// float4s.
+template <int DEG>
+struct ShStage {
+    static constexpr int K = (DEG + 1) * (DEG + 1);
+    static constexpr int ROW = 3 * K;
+    static constexpr bool VEC = ROW % 4 == 0;
+    // float4 rows padded to an odd number of float4s: the per-splat stores of a quarter-warp
+    // then fall in distinct banks
+    static constexpr int PAD = VEC ? ((ROW / 4) % 2 == 1 ? ROW : ROW + 4) : ROW;
+};
+
+constexpr int kBwdAdamThreads = 128;
+constexpr int kMaxDevicesAttr = 64;
+
+template <int DEG>
+__global__ void __launch_bounds__(kBwdAdamThreads)
+k_preprocess_bwd_adam(int n, darb_train_params P, darb_adam_state A, AdamConsts ac, Cam cam, float psi,
+                      const int *__restrict__ radius, const uint8_t *__restrict__ clamped,
+                      const float4 *__restrict__ grad2d) {
+    using S = ShStage<DEG>;
+    constexpr int K = S::K, ROW = S::ROW, PAD = S::PAD, NT = kBwdAdamThreads;
+    extern __shared__ __align__(16) float s_stage[];
+    float *s_sh = s_stage;             // the block's SH rows as read (padded rows)
+    float *s_dsh = s_stage + NT * PAD; // their gradients
+    const int t = threadIdx.x;
+    const int i0 = blockIdx.x * NT;
+    const int i = i0 + t;
+    const int cnt = min(NT, n - i0);
+    const size_t base = (size_t)i0 * ROW;  // the block's SH segment: cnt rows from row i0
+    if constexpr (S::VEC) {
+        const float4 *src = reinterpret_cast<const float4 *>(P.sh + base);
+        for (int f4 = t; f4 < cnt * (ROW / 4); f4 += NT) {
+            const int r = f4 / (ROW / 4), col = 4 * (f4 - r * (ROW / 4));
+            *reinterpret_cast<float4 *>(&s_sh[r * PAD + col]) = src[f4];
+        }
+    } else {
+        for (int f = t; f < cnt * ROW; f += NT) {
+            const int r = f / ROW;
+            s_sh[r * PAD + (f - r * ROW)] = P.sh[base + f];
+        }
+    }
+    __syncthreads();
+    if (i < n) {
+        float dm[3] = {0.f, 0.f, 0.f}, ds[3] = {0.f, 0.f, 0.f}, dq[4] = {0.f, 0.f, 0.f, 0.f}, dop = 0.f;
+        float dcoef[K][3];
+#pragma unroll
+        for (int k = 0; k < K; ++k) dcoef[k][0] = dcoef[k][1] = dcoef[k][2] = 0.0f;
+        const float *row = s_sh + t * PAD;
+        auto from_stage = [&](float(*c)[3]) {
+            if constexpr (S::VEC) {
+#pragma unroll
+                for (int u = 0; u < ROW / 4; ++u) {
+                    const float4 v = *reinterpret_cast<const float4 *>(row + 4 * u);
+                    const float b[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) c[(4 * u + e) / 3][(4 * u + e) % 3] = b[e];
+                }
+            } else {
+#pragma unroll
+                for (int u = 0; u < ROW; ++u) c[u / 3][u % 3] = row[u];
+            }
+        };
+        if (radius[i] != 0)
+            splat_backward<DEG>(i, P.means, P.scales, reinterpret_cast<const float4 *>(P.quats), from_stage, cam, psi,
+                                clamped[i], grad2d, dm, ds, dq, dop, dcoef);
+        const float *dc = &dcoef[0][0];
+        if constexpr (S::VEC) {
+#pragma unroll
+            for (int u = 0; u < ROW / 4; ++u)
+                *reinterpret_cast<float4 *>(&s_dsh[t * PAD + 4 * u]) =
+                    make_float4(dc[4 * u], dc[4 * u + 1], dc[4 * u + 2], dc[4 * u + 3]);
+        } else {
+#pragma unroll
+            for (int u = 0; u < ROW; ++u) s_dsh[t * PAD + u] = dc[u];
+        }
+    const size_t i3 = 3 * (size_t)i;
+        for (int j = 0; j < 3; ++j) {
+            float p = P.means[i3 + j], m = A.m_means[i3 + j], v = A.v_means[i3 + j];
+            adam_apply(p, dm[j], m, v, ac.lr_means, ac);
+            P.means[i3 + j] = p; A.m_means[i3 + j] = m; A.v_means[i3 + j] = v;
+            float ls = P.log_scales[i3 + j], ms = A.m_scales[i3 + j], vs = A.v_scales[i3 + j];
+            adam_apply(ls, ds[j] * P.scales[i3 + j], ms, vs, ac.lr_scales, ac);  // d scale / d log-scale = scale
+            P.log_scales[i3 + j] = ls; A.m_scales[i3 + j] = ms; A.v_scales[i3 + j] = vs;
+            P.scales[i3 + j] = expf(ls);
+        }
+        {
+            float4 q = reinterpret_cast<float4 *>(P.quats)[i], mq = reinterpret_cast<float4 *>(A.m_quats)[i],
+                   vq = reinterpret_cast<float4 *>(A.v_quats)[i];
+            adam_apply(q.x, dq[0], mq.x, vq.x, ac.lr_quats, ac);
+            adam_apply(q.y, dq[1], mq.y, vq.y, ac.lr_quats, ac);
+            adam_apply(q.z, dq[2], mq.z, vq.z, ac.lr_quats, ac);
+            adam_apply(q.w, dq[3], mq.w, vq.w, ac.lr_quats, ac);
+            reinterpret_cast<float4 *>(P.quats)[i] = q;
+            reinterpret_cast<float4 *>(A.m_quats)[i] = mq;
+            reinterpret_cast<float4 *>(A.v_quats)[i] = vq;
+        }
+        {
+            const float o = P.opacities[i];
+            float lg = P.opacity_logits[i], mo = A.m_opac[i], vo = A.v_opac[i];
+            adam_apply(lg, dop * (o * (1.0f - o)), mo, vo, ac.lr_opacities, ac);  // d sigmoid = o (1 - o)
+            P.opacity_logits[i] = lg; A.m_opac[i] = mo; A.v_opac[i] = vo;
+            P.opacities[i] = 1.0f / (1.0f + expf(-lg));
+        }
+    }
+    __syncthreads();
+    if constexpr (S::VEC) {
+        float4 *pc = reinterpret_cast<float4 *>(P.sh + base);
+        float4 *pm = reinterpret_cast<float4 *>(A.m_sh + base);
+        float4 *pv = reinterpret_cast<float4 *>(A.v_sh + base);
+        const int n4 = cnt * (ROW / 4);
+        for (int f4 = t; f4 < n4; f4 += NT) {
+            const int r = f4 / (ROW / 4), col = 4 * (f4 - r * (ROW / 4));
+            const float4 g = *reinterpret_cast<const float4 *>(&s_dsh[r * PAD + col]);
+            float4 c = *reinterpret_cast<const float4 *>(&s_sh[r * PAD + col]), m = pm[f4], v = pv[f4];
+            adam_apply(c.x, g.x, m.x, v.x, col + 0 < 3 ? ac.lr_sh_dc : ac.lr_sh_rest, ac);
+            adam_apply(c.y, g.y, m.y, v.y, col + 1 < 3 ? ac.lr_sh_dc : ac.lr_sh_rest, ac);
+            adam_apply(c.z, g.z, m.z, v.z, col + 2 < 3 ? ac.lr_sh_dc : ac.lr_sh_rest, ac);
+            adam_apply(c.w, g.w, m.w, v.w, col + 3 < 3 ? ac.lr_sh_dc : ac.lr_sh_rest, ac);
+            pc[f4] = c; pm[f4] = m; pv[f4] = v;
+        }
+    } else {
+        float *pc = P.sh + base, *pm = A.m_sh + base, *pv = A.v_sh + base;
+        const int nf = cnt * ROW;
+        for (int f = t; f < nf; f += NT) {
+            const int r = f / ROW, col = f - r * ROW;
+            float c = s_sh[r * PAD + col], m = pm[f], v = pv[f];
+            adam_apply(c, s_dsh[r * PAD + col], m, v, col < 3 ? ac.lr_sh_dc : ac.lr_sh_rest, ac);
+            pc[f] = c; pm[f] = m; pv[f] = v;
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -503,6 +657,39 @@ cudaError_t launch_preprocess_bwd(int n, const darb_splats &sp, const Cam &cam, 
     default: k_preprocess_bwd<3><<<blocks, threads, 0, st>>>(n, sp.means, sp.scales, q, sp.sh, cam, psi, radius, clamped, g, out); break;
     }
     return cudaGetLastError();
+}
+
+template <int DEG>
+cudaError_t launch_bwd_adam_deg(int n, const darb_train_params &p, const darb_adam_state &s, const AdamConsts &ac,
+                                const Cam &cam, float psi, const int *radius, const uint8_t *clamped,
+                                const float4 *g, cudaStream_t st) {
+    const size_t smem = 2 * sizeof(float) * kBwdAdamThreads * ShStage<DEG>::PAD;
+    // the opt-in above 48 KB, once per instantiation and device
+    static std::atomic<bool> attr_set[kMaxDevicesAttr];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevicesAttr || !attr_set[dev].load(std::memory_order_acquire)) {
+        e = cudaFuncSetAttribute(k_preprocess_bwd_adam<DEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < kMaxDevicesAttr) attr_set[dev].store(true, std::memory_order_release);
+    }
+    const int blocks = (n + kBwdAdamThreads - 1) / kBwdAdamThreads;
+    k_preprocess_bwd_adam<DEG><<<blocks, kBwdAdamThreads, smem, st>>>(n, p, s, ac, cam, psi, radius, clamped, g);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_preprocess_bwd_adam(int n, int sh_degree, const darb_train_params &p, const darb_adam_state &s,
+                                       const AdamConsts &ac, const Cam &cam, float psi, const int *radius,
+                                       const uint8_t *clamped, const float *grad2d, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    const float4 *g = reinterpret_cast<const float4 *>(grad2d);
+    switch (sh_degree) {
+    case 0: return launch_bwd_adam_deg<0>(n, p, s, ac, cam, psi, radius, clamped, g, st);
+    case 1: return launch_bwd_adam_deg<1>(n, p, s, ac, cam, psi, radius, clamped, g, st);
+    case 2: return launch_bwd_adam_deg<2>(n, p, s, ac, cam, psi, radius, clamped, g, st);
+    default: return launch_bwd_adam_deg<3>(n, p, s, ac, cam, psi, radius, clamped, g, st);
+    }
 }
 
 }  // namespace darb

@@ -36,9 +36,9 @@ __device__ __forceinline__ void adam_elem(float &p, float g, float &m, float &v,
                                           float eps, float ibc1, float ibc2, float *act_val) {
     if (ACT == 1) g *= *act_val;
     if (ACT == 2) g *= *act_val * (1.0f - *act_val);
-    m = fmaf(b1, m, (1.0f - b1) * g);
-    v = fmaf(b2, v, (1.0f - b2) * g * g);
-    p -= lr * (m * ibc1) / (sqrtf(v * ibc2) + eps);
+    AdamConsts c;
+    c.b1 = b1; c.b2 = b2; c.eps = eps; c.ibc1 = ibc1; c.ibc2 = ibc2;
+    adam_apply(p, g, m, v, lr, c);
     if (ACT == 1) *act_val = expf(p);
     if (ACT == 2) *act_val = 1.0f / (1.0f + expf(-p));
 }
@@ -125,8 +125,8 @@ cudaError_t launch_adam(const darb_train_params &p, const darb_splat_grads &g, c
                         const darb_adam_config &c, cudaStream_t st) {
     const long long n = p.n;
     if (n == 0) return cudaSuccess;
-    const float ibc1 = 1.0f / (1.0f - powf(c.beta1, (float)c.step));
-    const float ibc2 = 1.0f / (1.0f - powf(c.beta2, (float)c.step));
+    const AdamConsts ac = make_adam_consts(c);
+    const float ibc1 = ac.ibc1, ibc2 = ac.ibc2;
     const float b1 = c.beta1, b2 = c.beta2, eps = c.eps;
     const long long K = (long long)(p.sh_degree + 1) * (p.sh_degree + 1);
     auto g4 = [](long long count) { return grid_for((count + 3) / 4); };

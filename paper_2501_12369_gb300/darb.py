@@ -96,6 +96,9 @@ SIGNATURES = {
     "darb_l1_loss": (c_i32, [c_vp, c_vp, c_i32, c_i32, c_vp, c_vp, c_vp]),
     "darb_adam_step": (c_i32, [_P(darb_train_params), _P(darb_splat_grads), _P(darb_adam_state),
                                _P(darb_adam_config), c_vp]),
+    "darb_preprocess_bwd_adam": (c_i32, [_P(darb_train_params), _P(darb_camera), _P(darb_kernel_params),
+                                         _P(darb_projected), c_vp, _P(darb_adam_state), _P(darb_adam_config),
+                                         c_vp]),
 }
 
 _lock = threading.Lock()
@@ -367,12 +370,30 @@ def darb_l1_loss(image, target, dL_dimage=None, loss=None, stream=None):
     return dL_dimage, loss
 
 
+def train_params(params) -> darb_train_params:
+    """params: an object exposing the darb_train_params fields as tensors (plus sh_degree)."""
+    return darb_train_params(_p(params.means), _p(params.log_scales), _p(params.quats), _p(params.opacity_logits),
+                             _p(params.sh), _p(params.scales), _p(params.opacities), int(params.means.shape[0]),
+                             int(params.sh_degree))
+
+
+def adam_state(state) -> darb_adam_state:
+    """state: an object exposing the darb_adam_state fields as tensors."""
+    return darb_adam_state(*(_p(getattr(state, f)) for f, _ in darb_adam_state._fields_))
+
+
+def darb_preprocess_bwd_adam(params, cam, kparams, proj: Projected, grad2d: torch.Tensor, state,
+                             cfg: darb_adam_config, stream=None):
+    """Preprocess backward and the Adam step in one pass; params and state are updated in place."""
+    p, s, c, pr = train_params(params), adam_state(state), camera(cam), proj.struct()
+    _check(lib().darb_preprocess_bwd_adam(ctypes.byref(p), ctypes.byref(c), ctypes.byref(kparams), ctypes.byref(pr),
+                                          _p(grad2d), ctypes.byref(s), ctypes.byref(cfg), _stream(stream)),
+           "darb_preprocess_bwd_adam")
+
+
 def darb_adam_step(params, grads: SplatGrads, state, cfg: darb_adam_config, stream=None):
     """params / state: objects exposing the darb_train_params / darb_adam_state fields as tensors."""
-    p = darb_train_params(_p(params.means), _p(params.log_scales), _p(params.quats), _p(params.opacity_logits),
-                          _p(params.sh), _p(params.scales), _p(params.opacities), int(params.means.shape[0]),
-                          int(params.sh_degree))
-    s = darb_adam_state(*(_p(getattr(state, f)) for f, _ in darb_adam_state._fields_))
+    p, s = train_params(params), adam_state(state)
     g = grads.struct()
     _check(lib().darb_adam_step(ctypes.byref(p), ctypes.byref(g), ctypes.byref(s), ctypes.byref(cfg), _stream(stream)),
            "darb_adam_step")

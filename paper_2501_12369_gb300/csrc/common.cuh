@@ -149,10 +149,20 @@ struct AdamConsts {
     float b1, b2, eps, ibc1, ibc2;
 };
 
+// The step divides by sqrt(v_hat) + eps with the hardware's approximate square root and
+// divide (PTX sqrt.approx.f32, within 2^-23 relative, subnormals kept; __fdividef, 2 ulp for
+// divisors below 2^126): a few ulp on an update of order lr, against the IEEE sequences'
+// many instructions per element.
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 __device__ __forceinline__ void adam_apply(float &p, float g, float &m, float &v, float lr, const AdamConsts &c) {
     m = fmaf(c.b1, m, (1.0f - c.b1) * g);
     v = fmaf(c.b2, v, (1.0f - c.b2) * g * g);
-    p -= lr * (m * c.ibc1) / (sqrtf(v * c.ibc2) + c.eps);
+    p -= lr * __fdividef(m * c.ibc1, sqrt_approx(v * c.ibc2) + c.eps);
 }
 
 inline AdamConsts make_adam_consts(const darb_adam_config &c) {

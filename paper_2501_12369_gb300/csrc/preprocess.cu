@@ -6,8 +6,6 @@
 // order and the per-pixel support test) follows a fixed IEEE FP32 operation sequence
 // written with __f*_rn intrinsics, which the compiler neither contracts nor reorders,
 // so its results are bit-reproducible.  SH colour and the backward use ordinary FP32.
-#include <atomic>
-
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -490,140 +488,154 @@ k_preprocess_bwd(int n, const float *__restrict__ means, const float *__restrict
 }
 
 // The same gradients applied at once by Adam to the raw parameters (log-scales, opacity
-// logits), refreshing the activated copies; no gradient goes through HBM.  Means, scales,
-// quaternions and opacities are updated by the splat's own thread (a warp touches one
-// contiguous span of each array).  SH rows (3K floats, 192 B at degree 3) would make every
-// lane's access land in a different line, so their gradients are staged in shared memory and
-// the block then updates its contiguous SH segment with consecutive lanes on consecutive
-// float4s.
+// logits), refreshing the activated copies; no gradient goes through HBM.
+//
+// Two phases per block of kBwdAdamThreads splats.  (1) Each thread runs its splat's chain
+// rule and leaves the gradients w.r.t. the raw parameters in shared memory, one segment per
+// parameter group laid out as in HBM.  (2) The block walks each group's contiguous HBM
+// segment (its splats' rows) with consecutive lanes on consecutive float4s, several in
+// flight per thread, and applies Adam: parameters and both moments are read and written
+// once, coalesced, as in a flat optimiser pass.
 template <int DEG>
-struct ShStage {
+struct BwdAdamStage {
     static constexpr int K = (DEG + 1) * (DEG + 1);
-    static constexpr int ROW = 3 * K;
-    static constexpr bool VEC = ROW % 4 == 0;
-    // float4 rows padded to an odd number of float4s: the per-splat stores of a quarter-warp
-    // then fall in distinct banks
-    static constexpr int PAD = VEC ? ((ROW / 4) % 2 == 1 ? ROW : ROW + 4) : ROW;
+    static constexpr int ROW = 3 * K;  // SH floats per splat
+    // SH rows of an even number of float4s are padded by one float4: the per-splat float4
+    // stores of a quarter-warp then fall in distinct banks
+    static constexpr int PAD = (ROW % 4 == 0 && (ROW / 4) % 2 == 0) ? ROW + 4 : ROW;
 };
 
 constexpr int kBwdAdamThreads = 128;
-constexpr int kMaxDevicesAttr = 64;
+
+// One parameter group of the block: count floats from p/m/v (HBM, 16-byte aligned) with
+// gradients grad4(j) for float4 j; ACT 1 refreshes act = exp(p), ACT 2 act = sigmoid(p).
+template <int ACT, class Grad4, class LrOf>
+__device__ __forceinline__ void block_adam(int count, float *__restrict__ p, float *__restrict__ m,
+                                           float *__restrict__ v, float *__restrict__ act, Grad4 grad4, LrOf lr_of,
+                                           const AdamConsts &ac) {
+    constexpr int NT = kBwdAdamThreads, U = 4;
+    const int n4 = count >> 2;
+    float4 *p4 = reinterpret_cast<float4 *>(p), *m4 = reinterpret_cast<float4 *>(m), *v4 = reinterpret_cast<float4 *>(v);
+    for (int b = threadIdx.x; b < n4; b += NT * U) {
+        float4 P[U], M[U], V[U], G[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int j = b + u * NT;
+            if (j < n4) {
+                P[u] = p4[j];
+                M[u] = m4[j];
+                V[u] = v4[j];
+                G[u] = grad4(j);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int j = b + u * NT;
+            if (j < n4) {
+                adam_apply(P[u].x, G[u].x, M[u].x, V[u].x, lr_of(4 * j + 0), ac);
+                adam_apply(P[u].y, G[u].y, M[u].y, V[u].y, lr_of(4 * j + 1), ac);
+                adam_apply(P[u].z, G[u].z, M[u].z, V[u].z, lr_of(4 * j + 2), ac);
+                adam_apply(P[u].w, G[u].w, M[u].w, V[u].w, lr_of(4 * j + 3), ac);
+                p4[j] = P[u];
+                m4[j] = M[u];
+                v4[j] = V[u];
+                if (ACT == 1)
+                    reinterpret_cast<float4 *>(act)[j] =
+                        make_float4(expf(P[u].x), expf(P[u].y), expf(P[u].z), expf(P[u].w));
+                if (ACT == 2)
+                    reinterpret_cast<float4 *>(act)[j] =
+                        make_float4(1.0f / (1.0f + expf(-P[u].x)), 1.0f / (1.0f + expf(-P[u].y)),
+                                    1.0f / (1.0f + expf(-P[u].z)), 1.0f / (1.0f + expf(-P[u].w)));
+            }
+        }
+    }
+    // the last block's ragged end: count % 4 floats
+    const int f = (n4 << 2) + (int)threadIdx.x;
+    if (f < count) {
+        const float4 g = grad4(f >> 2);
+        const float gs[4] = {g.x, g.y, g.z, g.w};
+        float pp = p[f], mm = m[f], vv = v[f];
+        adam_apply(pp, gs[f & 3], mm, vv, lr_of(f), ac);
+        p[f] = pp;
+        m[f] = mm;
+        v[f] = vv;
+        if (ACT == 1) act[f] = expf(pp);
+        if (ACT == 2) act[f] = 1.0f / (1.0f + expf(-pp));
+    }
+}
 
 template <int DEG>
-__global__ void __launch_bounds__(kBwdAdamThreads)
+__global__ void __launch_bounds__(kBwdAdamThreads, DEG == 2 ? 4 : 6)
 k_preprocess_bwd_adam(int n, darb_train_params P, darb_adam_state A, AdamConsts ac, Cam cam, float psi,
                       const int *__restrict__ radius, const uint8_t *__restrict__ clamped,
                       const float4 *__restrict__ grad2d) {
-    using S = ShStage<DEG>;
+    using S = BwdAdamStage<DEG>;
     constexpr int K = S::K, ROW = S::ROW, PAD = S::PAD, NT = kBwdAdamThreads;
-    extern __shared__ __align__(16) float s_stage[];
-    float *s_sh = s_stage;             // the block's SH rows as read (padded rows)
-    float *s_dsh = s_stage + NT * PAD; // their gradients
+    // gradient segments; the tail of each is read as float4 up to a multiple of 4 floats
+    __shared__ __align__(16) float s_means[NT * 3];
+    __shared__ __align__(16) float s_lsc[NT * 3];
+    __shared__ __align__(16) float s_quat[NT * 4];
+    __shared__ __align__(16) float s_logit[NT];
+    __shared__ __align__(16) float s_sh[NT * PAD];
     const int t = threadIdx.x;
     const int i0 = blockIdx.x * NT;
     const int i = i0 + t;
     const int cnt = min(NT, n - i0);
-    const size_t base = (size_t)i0 * ROW;  // the block's SH segment: cnt rows from row i0
-    if constexpr (S::VEC) {
-        const float4 *src = reinterpret_cast<const float4 *>(P.sh + base);
-        for (int f4 = t; f4 < cnt * (ROW / 4); f4 += NT) {
-            const int r = f4 / (ROW / 4), col = 4 * (f4 - r * (ROW / 4));
-            *reinterpret_cast<float4 *>(&s_sh[r * PAD + col]) = src[f4];
-        }
-    } else {
-        for (int f = t; f < cnt * ROW; f += NT) {
-            const int r = f / ROW;
-            s_sh[r * PAD + (f - r * ROW)] = P.sh[base + f];
-        }
-    }
-    __syncthreads();
     if (i < n) {
         float dm[3] = {0.f, 0.f, 0.f}, ds[3] = {0.f, 0.f, 0.f}, dq[4] = {0.f, 0.f, 0.f, 0.f}, dop = 0.f;
         float dcoef[K][3];
 #pragma unroll
         for (int k = 0; k < K; ++k) dcoef[k][0] = dcoef[k][1] = dcoef[k][2] = 0.0f;
-        const float *row = s_sh + t * PAD;
-        auto from_stage = [&](float(*c)[3]) {
-            if constexpr (S::VEC) {
-#pragma unroll
-                for (int u = 0; u < ROW / 4; ++u) {
-                    const float4 v = *reinterpret_cast<const float4 *>(row + 4 * u);
-                    const float b[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) c[(4 * u + e) / 3][(4 * u + e) % 3] = b[e];
-                }
-            } else {
-#pragma unroll
-                for (int u = 0; u < ROW; ++u) c[u / 3][u % 3] = row[u];
-            }
-        };
         if (radius[i] != 0)
-            splat_backward<DEG>(i, P.means, P.scales, reinterpret_cast<const float4 *>(P.quats), from_stage, cam, psi,
-                                clamped[i], grad2d, dm, ds, dq, dop, dcoef);
+            splat_backward<DEG>(
+                i, P.means, P.scales, reinterpret_cast<const float4 *>(P.quats),
+                [&](float(*c)[3]) { load_sh<DEG>(P.sh, i, c); }, cam, psi, clamped[i], grad2d, dm, ds, dq, dop, dcoef);
+        // gradients w.r.t. the raw parameters: d scale / d log-scale = scale, d sigmoid = o (1 - o)
+        const size_t i3 = 3 * (size_t)i;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            s_means[3 * t + j] = dm[j];
+            s_lsc[3 * t + j] = ds[j] * P.scales[i3 + j];
+        }
+        *reinterpret_cast<float4 *>(&s_quat[4 * t]) = make_float4(dq[0], dq[1], dq[2], dq[3]);
+        const float o = P.opacities[i];
+        s_logit[t] = dop * (o * (1.0f - o));
         const float *dc = &dcoef[0][0];
-        if constexpr (S::VEC) {
+        if constexpr (ROW % 4 == 0) {
 #pragma unroll
             for (int u = 0; u < ROW / 4; ++u)
-                *reinterpret_cast<float4 *>(&s_dsh[t * PAD + 4 * u]) =
+                *reinterpret_cast<float4 *>(&s_sh[t * PAD + 4 * u]) =
                     make_float4(dc[4 * u], dc[4 * u + 1], dc[4 * u + 2], dc[4 * u + 3]);
         } else {
 #pragma unroll
-            for (int u = 0; u < ROW; ++u) s_dsh[t * PAD + u] = dc[u];
-        }
-    const size_t i3 = 3 * (size_t)i;
-        for (int j = 0; j < 3; ++j) {
-            float p = P.means[i3 + j], m = A.m_means[i3 + j], v = A.v_means[i3 + j];
-            adam_apply(p, dm[j], m, v, ac.lr_means, ac);
-            P.means[i3 + j] = p; A.m_means[i3 + j] = m; A.v_means[i3 + j] = v;
-            float ls = P.log_scales[i3 + j], ms = A.m_scales[i3 + j], vs = A.v_scales[i3 + j];
-            adam_apply(ls, ds[j] * P.scales[i3 + j], ms, vs, ac.lr_scales, ac);  // d scale / d log-scale = scale
-            P.log_scales[i3 + j] = ls; A.m_scales[i3 + j] = ms; A.v_scales[i3 + j] = vs;
-            P.scales[i3 + j] = expf(ls);
-        }
-        {
-            float4 q = reinterpret_cast<float4 *>(P.quats)[i], mq = reinterpret_cast<float4 *>(A.m_quats)[i],
-                   vq = reinterpret_cast<float4 *>(A.v_quats)[i];
-            adam_apply(q.x, dq[0], mq.x, vq.x, ac.lr_quats, ac);
-            adam_apply(q.y, dq[1], mq.y, vq.y, ac.lr_quats, ac);
-            adam_apply(q.z, dq[2], mq.z, vq.z, ac.lr_quats, ac);
-            adam_apply(q.w, dq[3], mq.w, vq.w, ac.lr_quats, ac);
-            reinterpret_cast<float4 *>(P.quats)[i] = q;
-            reinterpret_cast<float4 *>(A.m_quats)[i] = mq;
-            reinterpret_cast<float4 *>(A.v_quats)[i] = vq;
-        }
-        {
-            const float o = P.opacities[i];
-            float lg = P.opacity_logits[i], mo = A.m_opac[i], vo = A.v_opac[i];
-            adam_apply(lg, dop * (o * (1.0f - o)), mo, vo, ac.lr_opacities, ac);  // d sigmoid = o (1 - o)
-            P.opacity_logits[i] = lg; A.m_opac[i] = mo; A.v_opac[i] = vo;
-            P.opacities[i] = 1.0f / (1.0f + expf(-lg));
+            for (int u = 0; u < ROW; ++u) s_sh[t * PAD + u] = dc[u];
         }
     }
     __syncthreads();
-    if constexpr (S::VEC) {
-        float4 *pc = reinterpret_cast<float4 *>(P.sh + base);
-        float4 *pm = reinterpret_cast<float4 *>(A.m_sh + base);
-        float4 *pv = reinterpret_cast<float4 *>(A.v_sh + base);
-        const int n4 = cnt * (ROW / 4);
-        for (int f4 = t; f4 < n4; f4 += NT) {
-            const int r = f4 / (ROW / 4), col = 4 * (f4 - r * (ROW / 4));
-            const float4 g = *reinterpret_cast<const float4 *>(&s_dsh[r * PAD + col]);
-            float4 c = *reinterpret_cast<const float4 *>(&s_sh[r * PAD + col]), m = pm[f4], v = pv[f4];
-            adam_apply(c.x, g.x, m.x, v.x, col + 0 < 3 ? ac.lr_sh_dc : ac.lr_sh_rest, ac);
-            adam_apply(c.y, g.y, m.y, v.y, col + 1 < 3 ? ac.lr_sh_dc : ac.lr_sh_rest, ac);
-            adam_apply(c.z, g.z, m.z, v.z, col + 2 < 3 ? ac.lr_sh_dc : ac.lr_sh_rest, ac);
-            adam_apply(c.w, g.w, m.w, v.w, col + 3 < 3 ? ac.lr_sh_dc : ac.lr_sh_rest, ac);
-            pc[f4] = c; pm[f4] = m; pv[f4] = v;
-        }
+    // Block segments start at row i0 (a multiple of 128), so each is 16-byte aligned in HBM
+    // (the arrays are) and in shared memory.
+    const size_t r3 = 3 * (size_t)i0;
+    auto flat = [](const float *s) { return [s](int j) { return reinterpret_cast<const float4 *>(s)[j]; }; };
+    auto lr_const = [](float lr) { return [lr](int) { return lr; }; };
+    block_adam<0>(3 * cnt, P.means + r3, A.m_means + r3, A.v_means + r3, nullptr, flat(s_means),
+                  lr_const(ac.lr_means), ac);
+    block_adam<1>(3 * cnt, P.log_scales + r3, A.m_scales + r3, A.v_scales + r3, P.scales + r3, flat(s_lsc),
+                  lr_const(ac.lr_scales), ac);
+    block_adam<0>(4 * cnt, P.quats + 4 * (size_t)i0, A.m_quats + 4 * (size_t)i0, A.v_quats + 4 * (size_t)i0, nullptr,
+                  flat(s_quat), lr_const(ac.lr_quats), ac);
+    block_adam<2>(cnt, P.opacity_logits + i0, A.m_opac + i0, A.v_opac + i0, P.opacities + i0, flat(s_logit),
+                  lr_const(ac.lr_opacities), ac);
+    const size_t rs = (size_t)i0 * ROW;
+    const float lr_dc = ac.lr_sh_dc, lr_rest = ac.lr_sh_rest;
+    auto lr_sh = [=](int f) { return f % ROW < 3 ? lr_dc : lr_rest; };  // the DC term: first 3 floats of a row
+    if constexpr (PAD == ROW) {
+        block_adam<0>(ROW * cnt, P.sh + rs, A.m_sh + rs, A.v_sh + rs, nullptr, flat(s_sh), lr_sh, ac);
     } else {
-        float *pc = P.sh + base, *pm = A.m_sh + base, *pv = A.v_sh + base;
-        const int nf = cnt * ROW;
-        for (int f = t; f < nf; f += NT) {
-            const int r = f / ROW, col = f - r * ROW;
-            float c = s_sh[r * PAD + col], m = pm[f], v = pv[f];
-            adam_apply(c, s_dsh[r * PAD + col], m, v, col < 3 ? ac.lr_sh_dc : ac.lr_sh_rest, ac);
-            pc[f] = c; pm[f] = m; pv[f] = v;
-        }
+        auto padded = [&](int j) {
+            const int r = j / (ROW / 4), col = 4 * (j - r * (ROW / 4));
+            return *reinterpret_cast<const float4 *>(&s_sh[r * PAD + col]);
+        };
+        block_adam<0>(ROW * cnt, P.sh + rs, A.m_sh + rs, A.v_sh + rs, nullptr, padded, lr_sh, ac);
     }
 }
 
@@ -663,19 +675,8 @@ template <int DEG>
 cudaError_t launch_bwd_adam_deg(int n, const darb_train_params &p, const darb_adam_state &s, const AdamConsts &ac,
                                 const Cam &cam, float psi, const int *radius, const uint8_t *clamped,
                                 const float4 *g, cudaStream_t st) {
-    const size_t smem = 2 * sizeof(float) * kBwdAdamThreads * ShStage<DEG>::PAD;
-    // the opt-in above 48 KB, once per instantiation and device
-    static std::atomic<bool> attr_set[kMaxDevicesAttr];
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevicesAttr || !attr_set[dev].load(std::memory_order_acquire)) {
-        e = cudaFuncSetAttribute(k_preprocess_bwd_adam<DEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        if (dev >= 0 && dev < kMaxDevicesAttr) attr_set[dev].store(true, std::memory_order_release);
-    }
     const int blocks = (n + kBwdAdamThreads - 1) / kBwdAdamThreads;
-    k_preprocess_bwd_adam<DEG><<<blocks, kBwdAdamThreads, smem, st>>>(n, p, s, ac, cam, psi, radius, clamped, g);
+    k_preprocess_bwd_adam<DEG><<<blocks, kBwdAdamThreads, 0, st>>>(n, p, s, ac, cam, psi, radius, clamped, g);
     return cudaGetLastError();
 }
 

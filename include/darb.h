@@ -278,6 +278,42 @@ darb_status darb_preprocess_bwd_adam(const darb_train_params *params, const darb
                                      const float *grad2d, const darb_adam_state *state,
                                      const darb_adam_config *cfg, darb_stream stream);
 
+/* ---- Batched multi-view forward rendering ---------------------------------------------
+ * Renders n_views cameras of one splat set: per view, steps 1-3 as darb_preprocess and
+ * darb_bin_sort (DARB_SORT_DEPTH_THEN_TILE, asynchronous capacity mode); then step 4 for every
+ * view in one persistent launch whose CTAs take (view, tile) items from a device work queue.
+ * Views are spread round-robin over `depth` streams (created once per device by the library,
+ * joined back into `stream`) so that the preprocessing and sorting of several views overlap.
+ * A call neither allocates nor synchronises with the host, so a batch can be captured into a
+ * CUDA graph on `stream` (make one call before capturing: the first call on a device creates
+ * its streams).  Calls for one device are enqueued one at a time (a per-device lock).
+ * Results per view are those of the single-view calls with the same camera, tile and kernel. */
+#define DARB_MAX_BATCH_VIEWS 4096
+
+typedef struct {
+    int32_t n_views;   /* 1 .. DARB_MAX_BATCH_VIEWS */
+    int32_t tile;      /* 8, 16 or 32, shared by all views */
+    int32_t depth;     /* streams with views in flight, 1 .. 8 */
+    int32_t max_ctas;  /* cap on the persistent launch's CTAs; 0 = SMs x resident CTAs */
+    uint64_t capacity; /* instance capacity of each view */
+} darb_batch_params;
+
+/* Workspace bytes for darb_render_batch.  cams: host array [n_views]. */
+darb_status darb_render_batch_workspace_size(int32_t n, const darb_camera *cams,
+                                             const darb_batch_params *params, size_t *bytes);
+
+/* cams: host array [n_views] (read during the call only).  outs: host array [n_views] of
+ * device image buffers; image is required, t_final / last / n_contrib may be NULL (then not
+ * written).  workspace: device, at least the queried size; it holds every view's projected
+ * splats and sorted instances until the call's work completes.  num_instances, status: device
+ * u32[n_views] or NULL: each view's instance count M and darb_bin_sort status word.  A view
+ * with M > capacity has status DARB_ERR_CAPACITY and renders as background only; rerun it
+ * with a larger capacity. */
+darb_status darb_render_batch(const darb_splats *splats, const darb_camera *cams,
+                              const darb_kernel_params *kparams, const darb_batch_params *params,
+                              void *workspace, size_t workspace_bytes, const darb_image *outs,
+                              uint32_t *num_instances, uint32_t *status, darb_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,42 +1,10 @@
 // The C ABI of libdarb.so (declared in include/darb.h): argument validation, workspace
 // carving and kernel launches.  No entry point here allocates device memory.
-#include <cmath>
-
-#include "kernels.cuh"
+#include "validate.h"
 
 using namespace darb;
 
 namespace {
-
-bool valid_tile(int t) { return t == 8 || t == 16 || t == 32; }
-
-bool finitef(float x) { return std::isfinite(x); }
-
-bool valid_camera(const darb_camera *c) {
-    if (!c) return false;
-    if (c->width <= 0 || c->height <= 0 || c->width > 65536 || c->height > 65536) return false;
-    if (!(c->fx > 0.0f) || !(c->fy > 0.0f) || !finitef(c->fx) || !finitef(c->fy)) return false;
-    if (!finitef(c->cx) || !finitef(c->cy) || !(c->near_plane > 0.0f) || !finitef(c->near_plane)) return false;
-    for (int i = 0; i < 16; ++i)
-        if (!finitef(c->viewmat[i])) return false;
-    for (int i = 0; i < 3; ++i)
-        if (!finitef(c->bg[i])) return false;
-    return true;
-}
-
-bool valid_kernel(const darb_kernel_params *k) {
-    return k && k->kind >= 0 && k->kind < kNumKernels && k->psi > 0.0f && finitef(k->psi) && k->q_max > 0.0f &&
-           finitef(k->q_max);
-}
-
-bool valid_splats(const darb_splats *s) {
-    if (!s || s->n < 0 || s->sh_degree < 0 || s->sh_degree > 3) return false;
-    if (s->n == 0) return true;
-    const void *p[5] = {s->means, s->scales, s->quats, s->opacities, s->sh};
-    for (const void *q : p)
-        if (!q || !aligned16(q)) return false;
-    return true;
-}
 
 bool valid_projected(const darb_projected *o) {
     if (!o) return false;
@@ -68,8 +36,6 @@ ProjectedOut as_out(const darb_projected *o) {
     r.tiles_touched = o->tiles_touched;
     return r;
 }
-
-constexpr uint64_t kMaxCapacity = (1ull << 30) - 1;
 
 }  // namespace
 

@@ -31,6 +31,28 @@ cudaError_t launch_preprocess_bwd_adam(int n, int sh_degree, const darb_train_pa
                                        const AdamConsts &ac, const Cam &cam, float psi, const int *radius,
                                        const uint8_t *clamped, const float *grad2d, cudaStream_t st);
 
+// One view of a batched forward render (device memory).  tile_begin: index of the view's first
+// tile among all views' tiles, in view order.  t_final, last, n_contrib may be null.
+struct BatchView {
+    const uint2 *ranges;
+    const uint32_t *values;
+    const float2 *mean2d;
+    const float4 *conic_o;
+    const float *rgb;
+    float *image;
+    float *t_final;
+    uint32_t *last;
+    uint32_t *n_contrib;
+    int W, H, tiles_x, tile_begin;
+    float bg[3];
+    float pad_;
+};
+
+// render.cu: persistent launch over all views' tiles; queue is a device counter (reset here).
+// max_ctas > 0 caps the grid (else SMs x resident CTAs).
+cudaError_t launch_render_fwd_batch(int kind, int tile, const BatchView *views, int n_views, int total_tiles,
+                                    uint32_t *queue, float qmax, int strict, int max_ctas, cudaStream_t st);
+
 // binning.cu
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;

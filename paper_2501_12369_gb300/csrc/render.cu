@@ -22,6 +22,8 @@ struct Bg {
     float r, g, b;
 };
 
+constexpr int kMaxDevicesRender = 64;
+
 template <int TILE>
 struct RenderShape {
     static constexpr int PIX = TILE >= 16 ? 2 : 1;   // pixels per thread
@@ -29,20 +31,24 @@ struct RenderShape {
     static constexpr int ROWS = TILE / PIX;           // row stride between a thread's pixels
 };
 
+template <int TILE>
+struct FwdSmem {
+    float2 xy[RenderShape<TILE>::NT];
+    float4 co[RenderShape<TILE>::NT];  // A, 2B, C, opacity
+    float rgb[RenderShape<TILE>::NT][3];
+};
+
+// One tile of one view, by the whole CTA.  t_final, last and n_contrib may be null (not written).
 template <int KIND, int TILE>
-__global__ void __launch_bounds__(RenderShape<TILE>::NT)
-k_render_fwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ values,
-             const float2 *__restrict__ mean2d, const float4 *__restrict__ conic_o,
-             const float *__restrict__ rgb, int W, int H, int tiles_x, float qmax, int strict, Bg bg,
-             float *__restrict__ image, float *__restrict__ t_final, uint32_t *__restrict__ last,
-             uint32_t *__restrict__ n_contrib) {
+__device__ __forceinline__ void render_tile_fwd(int tile, FwdSmem<TILE> &sm, const uint2 *__restrict__ ranges,
+                                                const uint32_t *__restrict__ values,
+                                                const float2 *__restrict__ mean2d,
+                                                const float4 *__restrict__ conic_o, const float *__restrict__ rgb,
+                                                int W, int H, int tiles_x, float qmax, int strict, Bg bg,
+                                                float *__restrict__ image, float *__restrict__ t_final,
+                                                uint32_t *__restrict__ last, uint32_t *__restrict__ n_contrib) {
     using S = RenderShape<TILE>;
     constexpr int NT = S::NT, PIX = S::PIX;
-    __shared__ float2 s_xy[NT];
-    __shared__ float4 s_co[NT];  // A, 2B, C, opacity
-    __shared__ float s_rgb[NT][3];
-
-    const int tile = blockIdx.x;
     const int tx = tile % tiles_x, ty = tile / tiles_x;
     const int px = tx * TILE + (threadIdx.x % TILE);
     const int py0 = ty * TILE + (threadIdx.x / TILE);
@@ -70,20 +76,20 @@ k_render_fwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ valu
         const int idx = b0 + (int)threadIdx.x;
         if (idx < end) {
             const uint32_t id = values[idx];
-            s_xy[threadIdx.x] = mean2d[id];
+            sm.xy[threadIdx.x] = mean2d[id];
             float4 co = conic_o[id];
             co.y = 2.0f * co.y;
-            s_co[threadIdx.x] = co;
-            s_rgb[threadIdx.x][0] = rgb[3 * (size_t)id];
-            s_rgb[threadIdx.x][1] = rgb[3 * (size_t)id + 1];
-            s_rgb[threadIdx.x][2] = rgb[3 * (size_t)id + 2];
+            sm.co[threadIdx.x] = co;
+            sm.rgb[threadIdx.x][0] = rgb[3 * (size_t)id];
+            sm.rgb[threadIdx.x][1] = rgb[3 * (size_t)id + 1];
+            sm.rgb[threadIdx.x][2] = rgb[3 * (size_t)id + 2];
         }
         __syncthreads();
         if (all_done) continue;
         const int nb = min(NT, end - b0);
         for (int j = 0; j < nb; ++j) {
-            const float2 xy = s_xy[j];
-            const float4 co = s_co[j];
+            const float2 xy = sm.xy[j];
+            const float4 co = sm.co[j];
             const float dx = __fsub_rn(xy.x, fpx);
             bool any_live = false;
 #pragma unroll
@@ -101,9 +107,9 @@ k_render_fwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ valu
                     continue;
                 }
                 const float w = alpha * T[k];
-                C0[k] = fmaf(s_rgb[j][0], w, C0[k]);
-                C1[k] = fmaf(s_rgb[j][1], w, C1[k]);
-                C2[k] = fmaf(s_rgb[j][2], w, C2[k]);
+                C0[k] = fmaf(sm.rgb[j][0], w, C0[k]);
+                C1[k] = fmaf(sm.rgb[j][1], w, C1[k]);
+                C2[k] = fmaf(sm.rgb[j][2], w, C2[k]);
                 T[k] = Tn;
                 ++count[k];
                 lastp[k] = (uint32_t)(b0 - start + j + 1);
@@ -120,9 +126,56 @@ k_render_fwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ valu
         image[pix] = fmaf(T[k], bg.r, C0[k]);
         image[plane + pix] = fmaf(T[k], bg.g, C1[k]);
         image[2 * plane + pix] = fmaf(T[k], bg.b, C2[k]);
-        t_final[pix] = T[k];
-        last[pix] = lastp[k];
-        n_contrib[pix] = count[k];
+        if (t_final) t_final[pix] = T[k];
+        if (last) last[pix] = lastp[k];
+        if (n_contrib) n_contrib[pix] = count[k];
+    }
+}
+
+template <int KIND, int TILE>
+__global__ void __launch_bounds__(RenderShape<TILE>::NT)
+k_render_fwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ values,
+             const float2 *__restrict__ mean2d, const float4 *__restrict__ conic_o,
+             const float *__restrict__ rgb, int W, int H, int tiles_x, float qmax, int strict, Bg bg,
+             float *__restrict__ image, float *__restrict__ t_final, uint32_t *__restrict__ last,
+             uint32_t *__restrict__ n_contrib) {
+    __shared__ FwdSmem<TILE> sm;
+    render_tile_fwd<KIND, TILE>(blockIdx.x, sm, ranges, values, mean2d, conic_o, rgb, W, H, tiles_x, qmax, strict, bg,
+                                image, t_final, last, n_contrib);
+}
+
+// Several views in one persistent launch: CTAs take (view, tile) items from a device counter
+// (items numbered view-major; views[v].tile_begin is the first item of view v) until all are
+// done, so small and large views share the GPU without per-view launches or tails.
+template <int KIND, int TILE>
+__global__ void __launch_bounds__(RenderShape<TILE>::NT, 1536 / RenderShape<TILE>::NT)
+k_render_fwd_batch(const BatchView *__restrict__ views, int n_views, int total_tiles, uint32_t *__restrict__ queue,
+                   float qmax, int strict) {
+    __shared__ FwdSmem<TILE> sm;
+    __shared__ int s_item, s_view;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int item = (int)atomicAdd(queue, 1u);
+            int v = 0;
+            if (item < total_tiles) {  // last view whose first item is <= item
+                int lo = 0, hi = n_views - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (views[mid].tile_begin <= item) lo = mid; else hi = mid - 1;
+                }
+                v = lo;
+            }
+            s_item = item;
+            s_view = v;
+        }
+        __syncthreads();
+        const int item = s_item, v = s_view;
+        if (item >= total_tiles) break;
+        const BatchView &bv = views[v];
+        render_tile_fwd<KIND, TILE>(item - bv.tile_begin, sm, bv.ranges, bv.values, bv.mean2d, bv.conic_o, bv.rgb,
+                                    bv.W, bv.H, bv.tiles_x, qmax, strict, Bg{bv.bg[0], bv.bg[1], bv.bg[2]}, bv.image,
+                                    bv.t_final, bv.last, bv.n_contrib);
+        __syncthreads();  // the CTA is done with s_item and the staging arrays
     }
 }
 
@@ -341,6 +394,64 @@ cudaError_t launch_render_fwd(int kind, int tile, int tiles_x, int tiles_y, cons
     }
 #undef FWD_CALL
 #undef FWD_ARGS
+}
+
+namespace {
+
+template <int KIND, int TILE>
+cudaError_t fwd_batch_t(const BatchView *views, int n_views, int total_tiles, uint32_t *queue, float qmax, int strict,
+                        int max_ctas, cudaStream_t st) {
+    static int per_sm[kMaxDevicesRender] = {};  // resident CTAs per SM, once per device
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    int occ = (dev >= 0 && dev < kMaxDevicesRender) ? per_sm[dev] : 0;
+    if (occ == 0) {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_render_fwd_batch<KIND, TILE>,
+                                                          RenderShape<TILE>::NT, 0);
+        if (e != cudaSuccess) return e;
+        occ = occ > 0 ? occ : 1;
+        if (dev >= 0 && dev < kMaxDevicesRender) per_sm[dev] = occ;
+    }
+    int sms = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    long long grid = (long long)sms * occ;
+    if (max_ctas > 0 && grid > max_ctas) grid = max_ctas;
+    if (grid > total_tiles) grid = total_tiles;
+    e = cudaMemsetAsync(queue, 0, sizeof(uint32_t), st);
+    if (e != cudaSuccess) return e;
+    k_render_fwd_batch<KIND, TILE><<<(int)grid, RenderShape<TILE>::NT, 0, st>>>(views, n_views, total_tiles, queue,
+                                                                                 qmax, strict);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_render_fwd_batch(int kind, int tile, const BatchView *views, int n_views, int total_tiles,
+                                    uint32_t *queue, float qmax, int strict, int max_ctas, cudaStream_t st) {
+    if (total_tiles == 0 || n_views == 0) return cudaSuccess;
+#define FB_CALL(K, T) fwd_batch_t<K, T>(views, n_views, total_tiles, queue, qmax, strict, max_ctas, st)
+    if (tile == 8) {
+        switch (kind) {
+        case 0: return FB_CALL(0, 8); case 1: return FB_CALL(1, 8); case 2: return FB_CALL(2, 8);
+        case 3: return FB_CALL(3, 8); case 4: return FB_CALL(4, 8); case 5: return FB_CALL(5, 8);
+        default: return FB_CALL(6, 8);
+        }
+    } else if (tile == 16) {
+        switch (kind) {
+        case 0: return FB_CALL(0, 16); case 1: return FB_CALL(1, 16); case 2: return FB_CALL(2, 16);
+        case 3: return FB_CALL(3, 16); case 4: return FB_CALL(4, 16); case 5: return FB_CALL(5, 16);
+        default: return FB_CALL(6, 16);
+        }
+    } else {
+        switch (kind) {
+        case 0: return FB_CALL(0, 32); case 1: return FB_CALL(1, 32); case 2: return FB_CALL(2, 32);
+        case 3: return FB_CALL(3, 32); case 4: return FB_CALL(4, 32); case 5: return FB_CALL(5, 32);
+        default: return FB_CALL(6, 32);
+        }
+    }
+#undef FB_CALL
 }
 
 cudaError_t launch_render_bwd(int kind, int tile, int tiles_x, int tiles_y, const uint32_t *ranges,

@@ -73,6 +73,14 @@ class darb_adam_config(ctypes.Structure):
                 ("step", c_i32)]
 
 
+class darb_batch_params(ctypes.Structure):
+    _fields_ = [("n_views", c_i32), ("tile", c_i32), ("depth", c_i32), ("max_ctas", c_i32),
+                ("capacity", ctypes.c_uint64)]
+
+
+DARB_MAX_BATCH_VIEWS = 4096
+
+
 # Every entry point declared in include/darb.h, with its ctypes signature.
 _P = ctypes.POINTER
 SIGNATURES = {
@@ -99,6 +107,10 @@ SIGNATURES = {
     "darb_preprocess_bwd_adam": (c_i32, [_P(darb_train_params), _P(darb_camera), _P(darb_kernel_params),
                                          _P(darb_projected), c_vp, _P(darb_adam_state), _P(darb_adam_config),
                                          c_vp]),
+    "darb_render_batch_workspace_size": (c_i32, [c_i32, _P(darb_camera), _P(darb_batch_params),
+                                                 _P(ctypes.c_size_t)]),
+    "darb_render_batch": (c_i32, [_P(darb_splats), _P(darb_camera), _P(darb_kernel_params), _P(darb_batch_params),
+                                  c_vp, ctypes.c_size_t, _P(darb_image), c_vp, c_vp, c_vp]),
 }
 
 _lock = threading.Lock()
@@ -493,3 +505,141 @@ def autotune_tile(splats: SplatTensors, cams, kernel="half_cosine", candidates=(
         torch.cuda.synchronize()
         times[t] = start.elapsed_time(end) / (reps * len(cams))
     return min(times, key=times.get), times
+
+
+# ---------------------------------------------------------------------------
+# Batched multi-view rendering
+
+def darb_render_batch_workspace_size(n, cams, params: darb_batch_params) -> int:
+    arr = (darb_camera * len(cams))(*[camera(c) for c in cams])
+    nbytes = ctypes.c_size_t(0)
+    _check(lib().darb_render_batch_workspace_size(int(n), arr, ctypes.byref(params), ctypes.byref(nbytes)),
+           "darb_render_batch_workspace_size")
+    return int(nbytes.value)
+
+
+def darb_render_batch(splats: SplatTensors, cams, kparams, params: darb_batch_params, workspace: torch.Tensor,
+                      outs, num_instances=None, status=None, stream=None):
+    """outs: one ImageOut per camera (t_final / last / n_contrib may be None)."""
+    arr = (darb_camera * len(cams))(*[camera(c) for c in cams])
+    imgs = (darb_image * len(outs))(*[darb_image(_p(o.image), _p(o.t_final), _p(o.last), _p(o.n_contrib))
+                                      for o in outs])
+    sp = splats.struct()
+    _check(lib().darb_render_batch(ctypes.byref(sp), arr, ctypes.byref(kparams), ctypes.byref(params), _p(workspace),
+                                   workspace.numel() * workspace.element_size(), imgs, _p(num_instances),
+                                   _p(status), _stream(stream)), "darb_render_batch")
+
+
+class BatchRenderer:
+    """Forward renders of many cameras of one splat set: one darb_render_batch call, which can be
+    captured once into a CUDA graph and replayed.
+
+    capacity: instances per view; None sizes it from one counting pass per camera (x slack).
+    aux: also keep t_final / last / n_contrib per view."""
+
+    def __init__(self, splats: SplatTensors, cams, kernel="half_cosine", tile=16, depth=2, capacity=None,
+                 aux=False, max_ctas=0, slack=1.15, device="cuda"):
+        self.splats, self.cams = splats, list(cams)
+        self.kparams = darb_kernel_defaults(kernel)
+        self.tile, self.depth = int(tile), int(depth)
+        self.device = device
+        self.counts = None
+        if capacity is None:
+            self.counts = self.count_instances()
+            capacity = int(max(self.counts) * slack) + 1024
+        self.params = darb_batch_params(len(self.cams), self.tile, self.depth, int(max_ctas), int(capacity))
+        nbytes = darb_render_batch_workspace_size(splats.n, self.cams, self.params)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=device)
+        f = dict(device=device)
+        self.outs = []
+        for c in self.cams:
+            if aux:
+                self.outs.append(ImageOut.empty(c.width, c.height, device))
+            else:
+                self.outs.append(ImageOut(torch.empty(3, c.height, c.width, dtype=torch.float32, **f), None, None,
+                                          None))
+        self.num_instances = torch.zeros(len(self.cams), dtype=torch.int32, **f)
+        self.status = torch.zeros(len(self.cams), dtype=torch.int32, **f)
+        self.graph = None
+
+    @property
+    def capacity(self):
+        return int(self.params.capacity)
+
+    def count_instances(self):
+        """M of every camera at this tile size (synchronises once per camera)."""
+        counts = []
+        for c in self.cams:
+            proj = darb_preprocess(self.splats, c, self.kparams, self.tile)
+            ws = torch.empty(darb_bin_sort_workspace_size(self.splats.n, self.tile, c, 1), dtype=torch.uint8,
+                             device=self.device)
+            tx, ty = darb_tile_grid(c, self.tile)
+            bins = Binning.empty(1, tx * ty, self.device)
+            pr, cc, b = proj.struct(), camera(c), bins.struct()
+            m = ctypes.c_uint64(0)
+            st = lib().darb_bin_sort(ctypes.byref(pr), self.splats.n, self.tile, ctypes.byref(cc), _p(ws),
+                                     ws.numel(), 1, DARB_SORT_DEPTH_THEN_TILE, ctypes.byref(b), ctypes.byref(m),
+                                     _stream())
+            if st not in (0, 3):
+                _check(st, "darb_bin_sort")
+            counts.append(int(m.value))
+        return counts
+
+    def render(self, stream=None):
+        darb_render_batch(self.splats, self.cams, self.kparams, self.params, self.workspace, self.outs,
+                          self.num_instances, self.status, stream)
+
+    def capture(self):
+        """Record one batch into a CUDA graph (after one eager call, which creates the library's
+        per-device streams)."""
+        self.render()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            g.capture_begin()
+            self.render(s)
+            g.capture_end()
+        torch.cuda.current_stream().wait_stream(s)
+        self.graph = g
+        return g
+
+    def replay(self):
+        if self.graph is None:
+            self.capture()
+        self.graph.replay()
+
+    def check(self):
+        """Raises if any view overflowed its capacity or a device wait timed out."""
+        st = self.status.cpu().numpy()
+        if np.any(st != 0):
+            bad = int(np.flatnonzero(st)[0])
+            raise DarbError(int(st[bad]), f"view {bad} of the batch (M = {int(self.num_instances[bad])})")
+
+
+def autotune_batch(splats: SplatTensors, cams, kernel="half_cosine", tiles=(8, 16, 32), depths=(1, 2, 4), reps=5):
+    """(tile, depth) with the fastest graph-replayed batch over `cams`, and the ms per batch of
+    every pair.  Capacities are sized per tile from counting passes."""
+    times = {}
+    for t in tiles:
+        counts = None
+        for d in depths:
+            br = BatchRenderer(splats, cams, kernel, t, d,
+                               capacity=None if counts is None else int(max(counts) * 1.15) + 1024)
+            counts = br.counts if counts is None else counts
+            br.capture()
+            br.replay()
+            torch.cuda.synchronize()
+            br.check()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                br.replay()
+            e1.record()
+            torch.cuda.synchronize()
+            times[(t, d)] = e0.elapsed_time(e1) / reps
+            del br
+    best = min(times, key=times.get)
+    return best, times
+

@@ -185,3 +185,15 @@ def scene_3m_1080p(num_cameras=100):
     splats = cluster_scene(3_000_000, seed=0)
     cams = fibonacci_cameras(num_cameras, 6.0, 1920, 1080, 1500.0)
     return splats, cams
+
+
+MULTIVIEW_RESOLUTIONS = ((640, 360), (1280, 720), (1920, 1080))
+
+
+def scene_1m_multiview(num_cameras=64, seed=0):
+    """1M clustered splats, SH degree 3, cameras at random directions on the radius-5 sphere with
+    resolutions drawn from 640x360 / 1280x720 / 1920x1080 (fx = 0.78125 x width, the 1500 / 1920
+    of the 1080p workload)."""
+    splats = cluster_scene(1_000_000, seed=seed)
+    cams = random_pose_cameras(num_cameras, 5.0, MULTIVIEW_RESOLUTIONS, 1500.0 / 1920.0, seed=seed + 1)
+    return splats, cams

@@ -508,6 +508,9 @@ def run_ours(args):
         del ts
         torch.cuda.empty_cache()
         line["multiview"] = run_multiview(device, args.kernel)
+    if rank == 0 and not args.no_serving:
+        torch.cuda.empty_cache()
+        line["serving"] = run_serving(device, kernel=args.kernel)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(splats, cams, args.kernel, args.tile)
     if rank == 0:
@@ -597,6 +600,103 @@ def run_multiview(device, kernel="half_cosine", reps=10):
             "speedup": per_view_ms / batched_ms, "mean_instances": int(np.mean(br.counts))}
 
 
+# ----------------------------------------------------------------------------- serving
+
+def run_serving(device, rates=(200, 500, 1000, 2000), seconds=1.5, kernel="half_cosine", seed=0):
+    """Four resident scenes (200k / 500k / 1M / 3M clustered splats, SH degree 3).  Requests: a
+    random scene, a random pose on the radius-5 sphere, a random resolution among 640x360 /
+    1280x720 / 1920x1080.  Open loop: Poisson arrivals at each rate for `seconds`, submitted from
+    a client thread, collected in order; latency is submit -> image complete.  Sequential: the
+    same kind of requests one at a time (submit, wait, next), which is the service time alone."""
+    import threading
+    from paper_2501_12369_gb300 import darb, synth
+    sizes = (200_000, 500_000, 1_000_000, 3_000_000)
+    srv = darb.Server(scene_bytes=3 << 30, workspace_bytes=48 << 30, tile=32, max_batch=32, depth=2)
+    try:
+        ids = [srv.add_scene(darb.splats_to_device(synth.cluster_scene(n, seed=seed + i), device))
+               for i, n in enumerate(sizes)]
+        res = synth.MULTIVIEW_RESOLUTIONS
+        pools = {wh: [torch.empty(3, wh[1], wh[0], device=device) for _ in range(96)] for wh in res}
+        free = {wh: list(range(96)) for wh in res}
+        lock = threading.Condition()
+
+        def make_requests(count, rs):
+            rng = np.random.default_rng(rs)
+            cams = synth.random_pose_cameras(count, 5.0, res, 1500.0 / 1920.0, seed=rs)
+            return [(ids[int(rng.integers(len(ids)))], cams[i]) for i in range(count)]
+
+        def serve(reqs, arrivals):
+            tickets = [None] * len(reqs)
+            bufs = [None] * len(reqs)
+            t0 = time.perf_counter()
+
+            def client():
+                for i, ((sid, cam), at) in enumerate(zip(reqs, arrivals)):
+                    while True:
+                        dt = t0 + at - time.perf_counter()
+                        if dt <= 0:
+                            break
+                        time.sleep(dt if dt > 2e-3 else 0)
+                    wh = (cam.width, cam.height)
+                    with lock:
+                        while not free[wh]:
+                            lock.wait()
+                        b = free[wh].pop()
+                    bufs[i] = (wh, b)
+                    tickets[i] = srv.submit(sid, cam, pools[wh][b], kernel)
+                    with lock:
+                        lock.notify_all()
+
+            th = threading.Thread(target=client)
+            th.start()
+            out = []
+            for i in range(len(reqs)):
+                with lock:
+                    while tickets[i] is None:
+                        lock.wait(0.01)
+                r = srv.poll(tickets[i], 60_000)
+                if r.status != 0:
+                    raise RuntimeError(f"request {i} failed with status {r.status}")
+                out.append(r)
+                with lock:
+                    free[bufs[i][0]].append(bufs[i][1])
+                    lock.notify_all()
+            th.join()
+            wall = time.perf_counter() - t0
+            return out, wall
+
+        # warm-up: capacities learned per scene, code paths loaded
+        serve(make_requests(64, seed + 100), np.zeros(64))
+        # sequential service
+        seq = make_requests(120, seed + 200)
+        t0 = time.perf_counter()
+        for sid, cam in seq:
+            img = pools[(cam.width, cam.height)][0]
+            r = srv.poll(srv.submit(sid, cam, img, kernel), 60_000)
+        seq_s = time.perf_counter() - t0
+        seq_px = sum(c.width * c.height for _, c in seq)
+        report = {"workload": "serving_4_scenes_200k_500k_1M_3M_mixed_res", "tile": 32, "max_batch": 32,
+                  "sequential": {"requests": len(seq), "req_s": len(seq) / seq_s,
+                                 "mpix_s": seq_px / seq_s / 1e6, "ms_per_request": 1e3 * seq_s / len(seq)},
+                  "rates": []}
+        rng = np.random.default_rng(seed + 300)
+        for k, rate in enumerate(rates):
+            count = int(rate * seconds)
+            arrivals = np.cumsum(rng.exponential(1.0 / rate, size=count))
+            reqs = make_requests(count, seed + 400 + k)
+            out, wall = serve(reqs, arrivals)
+            lat = np.array([r.latency_us for r in out]) / 1e3
+            px = sum(c.width * c.height for _, c in reqs)
+            report["rates"].append({"offered_req_s": rate, "requests": count, "achieved_req_s": count / wall,
+                                    "mpix_s": px / wall / 1e6, "p50_ms": float(np.percentile(lat, 50)),
+                                    "p99_ms": float(np.percentile(lat, 99)),
+                                    "mean_batch": float(np.mean([r.batch_size for r in out])),
+                                    "retries": int(sum(r.attempts > 1 for r in out))})
+        return report
+    finally:
+        srv.close()
+
+
 # ----------------------------------------------------------------------------- reference arm
 
 def run_reference(args):
@@ -637,6 +737,7 @@ def main():
     ap.add_argument("--sort", type=int, default=0, help="0: depth then tile (default), 1: 64-bit keys")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-multiview", action="store_true", help="skip the batched multi-view measurement")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
     ap.add_argument("--unfused", action="store_true", help="separate preprocess backward and Adam kernels")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -314,6 +314,68 @@ darb_status darb_render_batch(const darb_splats *splats, const darb_camera *cams
                               void *workspace, size_t workspace_bytes, const darb_image *outs,
                               uint32_t *num_instances, uint32_t *status, darb_stream stream);
 
+/* ---- Serving ----------------------------------------------------------------------------
+ * A server renders requests (scene, camera, kernel) against resident splat sets on the device
+ * that is current at create time.  darb_serve_create allocates the server's whole device pool
+ * once (scene_bytes for splat sets plus workspace_bytes for two batch slots) and starts a
+ * worker thread; nothing is allocated afterwards.  The worker batches continuously: whenever a
+ * slot is free it takes pending requests in arrival order while their workspace fits the slot
+ * (at most max_batch), renders them with darb_render_batch (one call per scene and kernel), and
+ * completes their tickets when the batch's work has finished; the next batch is formed while
+ * the previous one renders.  A request's instance capacity is capacity_per_pixel x W x H
+ * until its scene has been rendered, then the scene's largest instances-per-pixel ratio so far
+ * x capacity_margin (at least capacity_min); a view that still overflows is re-queued once,
+ * at the head, with the capacity its instance count asks for.  The paper describes no serving
+ * system; this is the batched forward path of Sec. 4 behind a request queue. */
+typedef struct darb_server darb_server;
+
+typedef struct {
+    uint64_t scene_bytes;      /* device bytes for resident splat sets */
+    uint64_t workspace_bytes;  /* device bytes for the two batch slots (half each) */
+    int32_t tile;              /* 8, 16 or 32 */
+    int32_t max_batch;         /* requests per batch, 1 .. DARB_MAX_BATCH_VIEWS */
+    int32_t depth;             /* darb_batch_params.depth of each batch, 1 .. 8 */
+    float capacity_per_pixel;  /* first capacity guess, instances per pixel (> 0) */
+    float capacity_margin;     /* factor on the observed ratio (>= 1) */
+    uint64_t capacity_min;     /* lower bound of any capacity (>= 1) */
+} darb_serve_cfg;
+
+typedef struct {
+    int32_t scene_id;   /* from darb_serve_add_scene */
+    int32_t kernel;     /* a darb_kernel, with its darb_kernel_defaults parameters */
+    darb_camera cam;
+    float *image;       /* device [3][H][W], caller-owned, written by the server; keep it alive and
+                           unread until the ticket completes */
+} darb_request;
+
+typedef struct {
+    int32_t status;          /* DARB_OK or why the request failed */
+    uint32_t num_instances;  /* M of the final attempt */
+    uint32_t attempts;       /* 1, or 2 after a capacity retry */
+    uint32_t batch_size;     /* requests in the batch that rendered it */
+    double queue_us;         /* submit -> batch enqueued */
+    double latency_us;       /* submit -> image complete, as seen by the worker */
+} darb_result;
+
+/* DARB_ERR_CUDA if the pool cannot be allocated. */
+darb_status darb_serve_create(const darb_serve_cfg *cfg, darb_server **server);
+
+/* Copies a splat set (device pointers, as for darb_preprocess) into the scene region;
+ * synchronous.  DARB_ERR_ADMISSION when the region is full. */
+darb_status darb_serve_add_scene(darb_server *server, const darb_splats *splats, int32_t *scene_id);
+
+/* Queues a request; returns at once with its ticket.  DARB_ERR_NOT_FOUND for an unknown
+ * scene, DARB_ERR_ADMISSION if its workspace exceeds a batch slot even alone. */
+darb_status darb_serve_submit(darb_server *server, const darb_request *request, uint64_t *ticket);
+
+/* Waits up to timeout_ms for a ticket.  On DARB_OK the result is stored and the ticket is
+ * released; DARB_ERR_TIMEOUT leaves it pending; DARB_ERR_NOT_FOUND for an unknown or already
+ * collected ticket. */
+darb_status darb_serve_poll(darb_server *server, uint64_t ticket, int32_t timeout_ms, darb_result *result);
+
+/* Finishes every queued and in-flight request, stops the worker and frees the pool. */
+void darb_serve_destroy(darb_server *server);
+
 #ifdef __cplusplus
 }
 #endif

@@ -38,15 +38,23 @@ struct FwdSmem {
     float rgb[RenderShape<TILE>::NT][3];
 };
 
-// One tile of one view, by the whole CTA.  t_final, last and n_contrib may be null (not written).
-template <int KIND, int TILE>
+// Where a tile's results go; t_final, last and n_contrib may be null (not written).
+struct FwdSink {
+    float *image;
+    float *t_final;
+    uint32_t *last;
+    uint32_t *n_contrib;
+    Bg bg;
+};
+
+// One tile of one view, by the whole CTA.  sink() is called once, after the compositing loop,
+// so the output pointers need not stay live in registers across it.
+template <int KIND, int TILE, class SinkFn>
 __device__ __forceinline__ void render_tile_fwd(int tile, FwdSmem<TILE> &sm, const uint2 *__restrict__ ranges,
                                                 const uint32_t *__restrict__ values,
                                                 const float2 *__restrict__ mean2d,
                                                 const float4 *__restrict__ conic_o, const float *__restrict__ rgb,
-                                                int W, int H, int tiles_x, float qmax, int strict, Bg bg,
-                                                float *__restrict__ image, float *__restrict__ t_final,
-                                                uint32_t *__restrict__ last, uint32_t *__restrict__ n_contrib) {
+                                                int W, int H, int tiles_x, float qmax, int strict, SinkFn sink) {
     using S = RenderShape<TILE>;
     constexpr int NT = S::NT, PIX = S::PIX;
     const int tx = tile % tiles_x, ty = tile / tiles_x;
@@ -118,17 +126,18 @@ __device__ __forceinline__ void render_tile_fwd(int tile, FwdSmem<TILE> &sm, con
         }
     }
     const size_t plane = (size_t)W * H;
+    const FwdSink o = sink();
 #pragma unroll
     for (int k = 0; k < PIX; ++k) {
         const int py = py0 + k * S::ROWS;
         if (!(px < W && py < H)) continue;
         const size_t pix = (size_t)py * W + px;
-        image[pix] = fmaf(T[k], bg.r, C0[k]);
-        image[plane + pix] = fmaf(T[k], bg.g, C1[k]);
-        image[2 * plane + pix] = fmaf(T[k], bg.b, C2[k]);
-        if (t_final) t_final[pix] = T[k];
-        if (last) last[pix] = lastp[k];
-        if (n_contrib) n_contrib[pix] = count[k];
+        o.image[pix] = fmaf(T[k], o.bg.r, C0[k]);
+        o.image[plane + pix] = fmaf(T[k], o.bg.g, C1[k]);
+        o.image[2 * plane + pix] = fmaf(T[k], o.bg.b, C2[k]);
+        if (o.t_final) o.t_final[pix] = T[k];
+        if (o.last) o.last[pix] = lastp[k];
+        if (o.n_contrib) o.n_contrib[pix] = count[k];
     }
 }
 
@@ -140,8 +149,8 @@ k_render_fwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ valu
              float *__restrict__ image, float *__restrict__ t_final, uint32_t *__restrict__ last,
              uint32_t *__restrict__ n_contrib) {
     __shared__ FwdSmem<TILE> sm;
-    render_tile_fwd<KIND, TILE>(blockIdx.x, sm, ranges, values, mean2d, conic_o, rgb, W, H, tiles_x, qmax, strict, bg,
-                                image, t_final, last, n_contrib);
+    render_tile_fwd<KIND, TILE>(blockIdx.x, sm, ranges, values, mean2d, conic_o, rgb, W, H, tiles_x, qmax, strict,
+                                [&] { return FwdSink{image, t_final, last, n_contrib, bg}; });
 }
 
 // Several views in one persistent launch: CTAs take (view, tile) items from a device counter
@@ -173,8 +182,11 @@ k_render_fwd_batch(const BatchView *__restrict__ views, int n_views, int total_t
         if (item >= total_tiles) break;
         const BatchView &bv = views[v];
         render_tile_fwd<KIND, TILE>(item - bv.tile_begin, sm, bv.ranges, bv.values, bv.mean2d, bv.conic_o, bv.rgb,
-                                    bv.W, bv.H, bv.tiles_x, qmax, strict, Bg{bv.bg[0], bv.bg[1], bv.bg[2]}, bv.image,
-                                    bv.t_final, bv.last, bv.n_contrib);
+                                    bv.W, bv.H, bv.tiles_x, qmax, strict, [&] {
+                                        const BatchView &b = views[v];
+                                        return FwdSink{b.image, b.t_final, b.last, b.n_contrib,
+                                                       Bg{b.bg[0], b.bg[1], b.bg[2]}};
+                                    });
         __syncthreads();  // the CTA is done with s_item and the staging arrays
     }
 }

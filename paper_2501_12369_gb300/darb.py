@@ -81,6 +81,21 @@ class darb_batch_params(ctypes.Structure):
 DARB_MAX_BATCH_VIEWS = 4096
 
 
+class darb_serve_cfg(ctypes.Structure):
+    _fields_ = [("scene_bytes", ctypes.c_uint64), ("workspace_bytes", ctypes.c_uint64), ("tile", c_i32),
+                ("max_batch", c_i32), ("depth", c_i32), ("capacity_per_pixel", c_f32),
+                ("capacity_margin", c_f32), ("capacity_min", ctypes.c_uint64)]
+
+
+class darb_request(ctypes.Structure):
+    _fields_ = [("scene_id", c_i32), ("kernel", c_i32), ("cam", darb_camera), ("image", c_vp)]
+
+
+class darb_result(ctypes.Structure):
+    _fields_ = [("status", c_i32), ("num_instances", ctypes.c_uint32), ("attempts", ctypes.c_uint32),
+                ("batch_size", ctypes.c_uint32), ("queue_us", ctypes.c_double), ("latency_us", ctypes.c_double)]
+
+
 # Every entry point declared in include/darb.h, with its ctypes signature.
 _P = ctypes.POINTER
 SIGNATURES = {
@@ -111,6 +126,11 @@ SIGNATURES = {
                                                  _P(ctypes.c_size_t)]),
     "darb_render_batch": (c_i32, [_P(darb_splats), _P(darb_camera), _P(darb_kernel_params), _P(darb_batch_params),
                                   c_vp, ctypes.c_size_t, _P(darb_image), c_vp, c_vp, c_vp]),
+    "darb_serve_create": (c_i32, [_P(darb_serve_cfg), _P(c_vp)]),
+    "darb_serve_add_scene": (c_i32, [c_vp, _P(darb_splats), _P(c_i32)]),
+    "darb_serve_submit": (c_i32, [c_vp, _P(darb_request), _P(ctypes.c_uint64)]),
+    "darb_serve_poll": (c_i32, [c_vp, ctypes.c_uint64, c_i32, _P(darb_result)]),
+    "darb_serve_destroy": (None, [c_vp]),
 }
 
 _lock = threading.Lock()
@@ -642,4 +662,53 @@ def autotune_batch(splats: SplatTensors, cams, kernel="half_cosine", tiles=(8, 1
             del br
     best = min(times, key=times.get)
     return best, times
+
+
+# ---------------------------------------------------------------------------
+# Serving
+
+class Server:
+    """A darb_server: resident scenes, submit / poll of render requests (continuous batching in
+    the library's worker thread).  Images are caller-owned device tensors [3, H, W]."""
+
+    def __init__(self, scene_bytes, workspace_bytes, tile=32, max_batch=32, depth=2, capacity_per_pixel=16.0,
+                 capacity_margin=1.15, capacity_min=1 << 16):
+        self.cfg = darb_serve_cfg(int(scene_bytes), int(workspace_bytes), int(tile), int(max_batch), int(depth),
+                                  float(capacity_per_pixel), float(capacity_margin), int(capacity_min))
+        self.handle = c_vp()
+        _check(lib().darb_serve_create(ctypes.byref(self.cfg), ctypes.byref(self.handle)), "darb_serve_create")
+        self._keep = {}  # ticket -> image tensor, alive until collected
+
+    def add_scene(self, splats: SplatTensors) -> int:
+        sid = c_i32(0)
+        sp = splats.struct()
+        _check(lib().darb_serve_add_scene(self.handle, ctypes.byref(sp), ctypes.byref(sid)), "darb_serve_add_scene")
+        return int(sid.value)
+
+    def submit(self, scene_id, cam, image: torch.Tensor, kernel="half_cosine") -> int:
+        assert image.is_contiguous() and image.dtype == torch.float32 and tuple(image.shape) == (3, cam.height,
+                                                                                                 cam.width)
+        req = darb_request(int(scene_id), kernel_index(kernel), camera(cam), _p(image))
+        t = ctypes.c_uint64(0)
+        _check(lib().darb_serve_submit(self.handle, ctypes.byref(req), ctypes.byref(t)), "darb_serve_submit")
+        self._keep[int(t.value)] = image
+        return int(t.value)
+
+    def poll(self, ticket, timeout_ms=10_000) -> darb_result:
+        r = darb_result()
+        _check(lib().darb_serve_poll(self.handle, int(ticket), int(timeout_ms), ctypes.byref(r)), "darb_serve_poll")
+        self._keep.pop(int(ticket), None)
+        return r
+
+    def close(self):
+        if self.handle:
+            lib().darb_serve_destroy(self.handle)
+            self.handle = c_vp()
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 

@@ -163,6 +163,7 @@ class TrainStep:
         self.ws = None
         self.bins = None
         self.step_no = 0
+        self.visible = {}
         self.kp_ref = ctypes.byref(self.kp)
         self._structs()
 
@@ -220,6 +221,7 @@ class TrainStep:
                                  self.capacity, self.strategy, ctypes.byref(self.s_bins), ctypes.byref(m), st)
         if r not in (0, 3):
             d._check(r, "bin_sort")
+        self.visible[cam_idx] = int((self.proj.radius != 0).sum().item())
         return int(m.value)
 
     def forward(self, cam_idx, ev=None):
@@ -268,15 +270,25 @@ class TrainStep:
         rec(7)
 
 
+# DRAM bytes (read + write) per splat of k_preprocess_bwd_adam<3>: dram__bytes_read.sum +
+# dram__bytes_write.sum of one launch on 1M clustered splats (1920x1080, tile 32; the
+# train_tail case of paper_2501_12369_gb300.profile_cases), divided by the splat count.
+TRAFFIC_BWD_ADAM_PER_SPLAT = 1437.01
+
 STAGES_FUSED = ["preprocess", "bin_sort", "render_fwd", "l1_loss", "render_bwd", "preprocess_bwd_adam"]
 STAGES_SEPARATE = ["preprocess", "bin_sort", "render_fwd", "l1_loss", "render_bwd", "preprocess_bwd", "adam"]
 
 
-def algorithmic_bytes(stage, n, M, passes, sh_k, strategy=0, tile_passes=2):
-    """HBM bytes a stage must move at minimum, per launch (see the data layout notes in the docs)."""
+def algorithmic_bytes(stage, n, M, passes, sh_k, strategy=0, tile_passes=2, n_vis=None):
+    """HBM bytes a stage must move at minimum, per launch.  n_vis: splats that survive culling
+    (default n); a culled splat's preprocessing reads only its mean, scale and rotation."""
+    n_vis = n if n_vis is None else n_vis
     sh_b = sh_k * 3 * 4
     if stage == "preprocess":
-        return n * (12 + 12 + 16 + 4 + sh_b) + n * (4 + 4 + 16 + 8 + 16 + 12 + 1 + 4)
+        # visible: read means, scales, quats, opacity, SH; write depth, radius, rect, mean2d,
+        # conic_o, rgb, clamp bits, tiles.  culled: read means, scales, quats; write depth,
+        # radius, rect, tiles
+        return n_vis * (12 + 12 + 16 + 4 + sh_b + 4 + 4 + 16 + 8 + 16 + 12 + 1 + 4) + (n - n_vis) * (40 + 28)
     if stage == "bin_sort":
         if strategy == 1:
             return n * (4 + 4 + 16 + 4) + M * (12 + 8 + 24 * passes + 8)
@@ -286,15 +298,18 @@ def algorithmic_bytes(stage, n, M, passes, sh_k, strategy=0, tile_passes=2):
         # last, which writes only the 4-byte values
         return n * (8 + 4 + 4 * 16 + 8 + 8 + 32) + M * (8 + 16 * tile_passes - 4)
     if stage == "preprocess_bwd":
-        return n * (12 + 12 + 16 + sh_b + 48 + 4 + 1) + n * (12 + 12 + 16 + 4 + sh_b)
+        # every splat: radius read, all gradients written; visible: parameters, grad2d and clamp
+        # bits read
+        return n * (4 + 12 + 12 + 16 + 4 + sh_b) + n_vis * (12 + 12 + 16 + sh_b + 48 + 1)
     if stage == "adam":
         params = 3 + 3 + 4 + 1 + sh_k * 3
         return n * (params * 28 + 4 * 8)
     if stage == "preprocess_bwd_adam":
-        # per splat: raw parameters and both moments read and written (6 x 4 B per parameter),
-        # activated scales and opacity read and written, grad2d (48 B), radius and clamped flags
+        # every splat: raw parameters and both moments read and written (6 x 4 B per parameter),
+        # activated scales and opacity read and written, radius read; visible: grad2d (48 B) and
+        # clamp bits
         params = 3 + 3 + 4 + 1 + sh_k * 3
-        return n * (params * 24 + 2 * (12 + 4) + 48 + 4 + 1)
+        return n * (params * 24 + 2 * (12 + 4) + 4) + n_vis * (48 + 1)
     return None
 
 
@@ -350,8 +365,8 @@ def cpu_baseline(splats, cams, kernel, tile, target_seconds=15.0):
     frac = done / (tx * ty)
     est = t_pre + t_tiles / frac + t_pbwd + t_adam
     return {"value": 1.0 / est, "unit": "it/s", "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": (f"one 1920x1080 view of the 3M-splat scene: full FP32/FP64 preprocess ({t_pre:.1f} s) and "
-                       f"preprocess backward ({t_pbwd:.1f} s); tiled compositing forward+backward on {done} random "
+            "sample": (f"one 1920x1080 view of the 3M-splat scene: full FP32/FP64 preprocess ({t_pre:.2f} s) and "
+                       f"preprocess backward ({t_pbwd:.2f} s); tiled compositing forward+backward on {done} random "
                        f"tiles of {tx * ty} ({t_tiles:.1f} s, scaled x{1 / frac:.0f}); Adam on 200k splats "
                        f"scaled to {splats.n}"),
             "seconds_per_iteration": est}
@@ -462,21 +477,29 @@ def run_ours(args):
     e2e_ms = max_over_ranks(dist, estart.elapsed_time(eend), device)
     assert np.isfinite(loss_host.numpy()).all()
 
-    # roofline of the dominant kernel stage
+    # roofline of the dominant kernel: the longest stage that is a single HBM-bound kernel
+    # (bin_sort is a sequence of ~15 kernels; compositing is ALU-bound), plus every HBM stage
     M_mean = float(np.mean(Ms))
     passes = (32 + int(np.ceil(np.log2(ts.tx * ts.ty))) + 7) // 8
     sh_k = (splats.sh_degree + 1) ** 2
     dominant = max(stage_ms, key=stage_ms.get)
-    hbm_stages = {s: stage_ms[s] for s in ("preprocess", "bin_sort", "preprocess_bwd", "adam", "preprocess_bwd_adam")
-                  if s in stage_ms}
     peaks = load_peaks()
     peak_gbs = peaks["hbm_gbs"] if peaks else 6800.0
     tile_bits = int(np.ceil(np.log2(ts.tx * ts.ty)))
     tile_passes = max(1, (tile_bits + 7) // 8)
-    ab_of = lambda st: algorithmic_bytes(st, ts.n, M_mean, passes, sh_k, args.sort, tile_passes)  # noqa: E731
-    rl_stage = dominant if ab_of(dominant) else max(hbm_stages, key=hbm_stages.get)
+    n_vis = float(np.mean([ts.visible[c] for c in set(cam_seq)]))
+    ab_of = lambda st: algorithmic_bytes(st, ts.n, M_mean, passes, sh_k, args.sort, tile_passes, n_vis)  # noqa: E731
+    single = [st for st in ("preprocess", "preprocess_bwd", "adam", "preprocess_bwd_adam") if st in stage_ms]
+    rl_stage = max(single, key=stage_ms.get)
     ab = ab_of(rl_stage)
     achieved = ab / (stage_ms[rl_stage] / 1e3) / 1e9
+    stage_frac = {st: round(ab_of(st) / (stage_ms[st] / 1e3) / 1e9 / peak_gbs, 4)
+                  for st in single + ["bin_sort"] if ab_of(st)}
+    traffic = None
+    if rl_stage == "preprocess_bwd_adam" and splats.sh_degree == 3:
+        # ncu dram__bytes_read.sum + dram__bytes_write.sum of k_preprocess_bwd_adam<3> on the
+        # 1M-splat capture, scaled by splat count (traffic is per splat)
+        traffic = None if TRAFFIC_BWD_ADAM_PER_SPLAT is None else TRAFFIC_BWD_ADAM_PER_SPLAT * ts.n
     its = world * args.steps / (ms_max / 1e3)
     line = {
         "metric": METRIC, "value": its, "unit": "it/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -485,14 +508,15 @@ def run_ours(args):
         "config": {"workload": WORKLOAD, "splats": ts.n, "sh_degree": splats.sh_degree, "width": 1920,
                    "height": 1080, "fx": 1500.0, "cameras": len(cams), "kernel": args.kernel, "tile": args.tile,
                    "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (2.1 GB splat state)",
-                   "mean_instances": int(M_mean)},
+                   "mean_instances": int(M_mean), "mean_visible_splats": int(n_vis)},
         "fwd_mpix_s": fwd_mpix,
         "tile_autotune_it_s": tuning or None,
         "fwd_ms": fwd_ms / args.steps,
         "stage_ms": {s: round(v, 4) for s, v in stage_ms.items()},
         "dominant_stage": dominant,
+        "stage_hbm_frac": stage_frac,
         "roofline": {"bound": "hbm", "kernel": rl_stage, "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
-                     "frac": achieved / peak_gbs, "traffic": None,
+                     "frac": achieved / peak_gbs, "traffic": traffic,
                      "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback 6.8 TB/s",
                      "algorithmic_bytes": ab},
         "e2e": {"value": world * args.steps / (e2e_ms / 1e3), "unit": "it/s",

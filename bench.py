@@ -57,6 +57,11 @@ def barrier(dist):
         dist.barrier()
 
 
+def whole_job_rate(world, units_per_rank, ms_max):
+    """Units per second of the whole job: every rank's units over the slowest rank's time."""
+    return world * units_per_rank / (ms_max / 1e3)
+
+
 def max_over_ranks(dist, value, device):
     if dist is None:
         return value
@@ -500,7 +505,7 @@ def run_ours(args):
         # ncu dram__bytes_read.sum + dram__bytes_write.sum of k_preprocess_bwd_adam<3> on the
         # 1M-splat capture, scaled by splat count (traffic is per splat)
         traffic = None if TRAFFIC_BWD_ADAM_PER_SPLAT is None else TRAFFIC_BWD_ADAM_PER_SPLAT * ts.n
-    its = world * args.steps / (ms_max / 1e3)
+    its = whole_job_rate(world, args.steps, ms_max)
     line = {
         "metric": METRIC, "value": its, "unit": "it/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,

@@ -380,6 +380,23 @@ class SplatGrads:
     def empty_like(s: SplatTensors):
         return SplatGrads(*(torch.empty_like(t) for t in (s.means, s.scales, s.quats, s.opacities, s.sh)))
 
+    @staticmethod
+    def empty_flat(n, sh_degree, device="cuda", dtype=torch.float32):
+        """Gradients as views into one contiguous buffer (`.flat`), so a data-parallel step can
+        reduce them with a single collective.  Every view starts on a 16-byte boundary."""
+        k = (sh_degree + 1) ** 2
+        shapes = [(n, 3), (n, 3), (n, 4), (n,), (n, k, 3)]
+        sizes = [int(np.prod(sh)) for sh in shapes]
+        padded = [(z + 3) // 4 * 4 for z in sizes]
+        flat = torch.empty(sum(padded), dtype=dtype, device=device)
+        views, off = [], 0
+        for sh, z, pz in zip(shapes, sizes, padded):
+            views.append(flat[off:off + z].view(sh))
+            off += pz
+        g = SplatGrads(*views)
+        g.flat = flat
+        return g
+
     def struct(self) -> darb_splat_grads:
         return darb_splat_grads(_p(self.dmeans), _p(self.dscales), _p(self.dquats), _p(self.dopacities), _p(self.dsh))
 
@@ -711,4 +728,22 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------------------
+# Data-parallel training over several views per step
+
+def allreduce_splat_grads(grads: SplatGrads, group=None, average=False):
+    """Sums (or averages) the per-splat parameter gradients over the ranks of `group` with one
+    all-reduce of the flat buffer (grads from SplatGrads.empty_flat).  Each rank renders its own
+    views and runs darb_preprocess_bwd; after this call every rank holds the gradient of the
+    summed loss and applies the same darb_adam_step."""
+    import torch.distributed as dist
+    flat = getattr(grads, "flat", None)
+    if flat is None:
+        raise ValueError("allreduce_splat_grads needs gradients from SplatGrads.empty_flat")
+    dist.all_reduce(flat, op=dist.ReduceOp.SUM, group=group)
+    if average:
+        flat /= dist.get_world_size(group)
+    return grads
 

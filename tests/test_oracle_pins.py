@@ -464,3 +464,68 @@ def test_gradient_through_guard_band_and_colour_clamp():
             assert abs(fd - gp["means"][i, j]) <= 2e-3 * max(abs(fd), 1e-2)
             checked += 1
     assert checked >= 10
+
+
+# --------------------------------------------------------------------------- training-step terms
+
+def test_adam_closed_forms():
+    """Kingma & Ba, Algorithm 1: from zero moments a constant gradient g gives m_hat = g and
+    v_hat = g^2 at every step, so each step moves by lr g / (|g| + eps); a zero gradient only
+    decays the moments by beta1 and beta2."""
+    rng = np.random.default_rng(0)
+    p0 = rng.normal(size=50)
+    g = rng.normal(size=50)
+    p, m, v = p0.copy(), np.zeros(50), np.zeros(50)
+    lr, eps = 1e-3, 1e-15
+    for t in range(1, 8):
+        p, m, v = oracle.adam_update(p, g, m, v, lr, t, eps=eps)
+        np.testing.assert_allclose(p, p0 - t * lr * g / (np.abs(g) + eps), rtol=0, atol=1e-15)
+        np.testing.assert_allclose(m, (1 - 0.9 ** t) * g, rtol=1e-12)
+        np.testing.assert_allclose(v, (1 - 0.999 ** t) * g * g, rtol=1e-12)
+    m0, v0 = rng.normal(size=50), rng.uniform(0.1, 1.0, size=50)
+    _, m1, v1 = oracle.adam_update(p0, np.zeros(50), m0, v0, lr, 5)
+    np.testing.assert_allclose(m1, 0.9 * m0, rtol=1e-15)
+    np.testing.assert_allclose(v1, 0.999 * v0, rtol=1e-15)
+
+
+def test_adam_splat_groups_chain_through_the_activations():
+    """First moment after one step = (1 - beta1) x the raw-parameter gradient: the gradient
+    w.r.t. a log-scale is the scale-gradient times the scale (d exp), w.r.t. an opacity logit
+    the opacity-gradient times o (1 - o) (d sigmoid); the first step moves every raw parameter
+    by its learning rate (SH DC and rest apart)."""
+    rng = np.random.default_rng(1)
+    n, k = 40, 16
+    raw = dict(means=rng.normal(size=(n, 3)), log_scales=rng.uniform(-4, -1, size=(n, 3)),
+               quats=rng.normal(size=(n, 4)), opacity_logits=rng.normal(size=n), sh=rng.normal(size=(n, k, 3)))
+    grads = dict(means=rng.normal(size=(n, 3)), scales=rng.normal(size=(n, 3)), quats=rng.normal(size=(n, 4)),
+                 opacities=rng.normal(size=n), sh=rng.normal(size=(n, k, 3)))
+    state = {f"{m}_{key}": np.zeros_like(v) for key, v in raw.items() for m in ("m", "v")}
+    lrs = dict(means=1e-3, scales=5e-3, quats=1e-3, opacities=0.02, sh_dc=2.5e-3, sh_rest=1.25e-4)
+    new, st = oracle.adam_step_splats(raw, grads, state, lrs, 1)
+    scale = np.exp(raw["log_scales"])
+    o = 1 / (1 + np.exp(-raw["opacity_logits"]))
+    np.testing.assert_allclose(st["m_log_scales"], 0.1 * grads["scales"] * scale, rtol=1e-12)
+    np.testing.assert_allclose(st["m_opacity_logits"], 0.1 * grads["opacities"] * o * (1 - o), rtol=1e-12)
+    np.testing.assert_allclose(st["m_means"], 0.1 * grads["means"], rtol=1e-12)
+    for key, lr in (("means", 1e-3), ("log_scales", 5e-3), ("quats", 1e-3), ("opacity_logits", 0.02)):
+        np.testing.assert_allclose(np.abs(new[key] - raw[key]), lr, rtol=1e-9)
+    step = np.abs(new["sh"] - raw["sh"])
+    np.testing.assert_allclose(step[:, 0, :], 2.5e-3, rtol=1e-9)
+    np.testing.assert_allclose(step[:, 1:, :], 1.25e-4, rtol=1e-9)
+
+
+def test_l1_gradient_matches_finite_differences():
+    rng = np.random.default_rng(2)
+    img, tgt = rng.uniform(size=(3, 5, 7)), rng.uniform(size=(3, 5, 7))
+    loss, grad = oracle.l1_loss(img, tgt)
+    assert loss == pytest.approx(np.abs(img - tgt).mean(), rel=1e-15)
+    h = 1e-7
+    for idx in [(0, 0, 0), (1, 2, 3), (2, 4, 6), (0, 3, 5)]:
+        a, b = img.copy(), img.copy()
+        a[idx] += h
+        b[idx] -= h
+        fd = (oracle.l1_loss(a, tgt)[0] - oracle.l1_loss(b, tgt)[0]) / (2 * h)
+        assert grad[idx] == pytest.approx(fd, rel=1e-6)
+    tie = img.copy()
+    tie[0, 0, 0] = tgt[0, 0, 0]
+    assert oracle.l1_loss(tie, tgt)[1][0, 0, 0] == 0.0  # the subgradient taken at a tie

@@ -184,6 +184,10 @@ class TrainStep:
                                             self.n, self.sh_degree)
         self.s_state = d.darb_adam_state(*(d._p(self.state[f]) for f, _ in d.darb_adam_state._fields_))
 
+    def set_kernel(self, kernel):
+        self.kp = self.darb.darb_kernel_defaults(kernel)
+        self.kp_ref = ctypes.byref(self.kp)
+
     def set_tile(self, tile):
         self.tile = int(tile)
         self.tx, self.ty = self.darb.darb_tile_grid(self.cams[0], self.tile)
@@ -533,6 +537,8 @@ def run_ours(args):
                                                           not args.unfused)
     line["config"]["optimizer"] = "adam (separate)" if args.unfused else "adam fused into preprocess backward"
     line["config"]["sort"] = "depth_then_tile" if args.sort == 0 else "keys64"
+    if not args.no_sweep:
+        line["kernel_sweep"] = kernel_sweep(ts, step, cam_seq, args.warmup, STAGES, args.kernel)
     if rank == 0 and not args.no_multiview:
         del ts
         torch.cuda.empty_cache()
@@ -557,6 +563,29 @@ def launches_per_step(strategy, tile_bits, fused=True):
         sort = 3 + 4 + 6 + max(1, (tile_bits + 7) // 8)
     # preprocess, render_fwd, l1, render_bwd, then preprocess_bwd + 5 Adam groups or one fused kernel
     return 1 + sort + 1 + 1 + 1 + (1 if fused else 1 + 5)
+
+
+def kernel_sweep(ts, step, cam_seq, first, stages, restore_kernel, steps=20):
+    """Training it/s and per-stage ms for every reconstruction kernel (the tile stays the
+    autotuned one; capacity is re-sized, since psi changes the footprints)."""
+    from paper_2501_12369_gb300 import darb
+    out = {}
+    for k in darb.KERNEL_NAMES:
+        ts.set_kernel(k)
+        Ms = ts.size_capacity(cam_seq[:16])
+        for i in range(3):
+            step(first + i)
+        torch.cuda.synchronize()
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(stages) + 1)] for _ in range(steps)]
+        for j in range(steps):
+            step(first + 3 + j, evs[j])
+        torch.cuda.synchronize()
+        per = {s: sum(e[i].elapsed_time(e[i + 1]) for e in evs) / steps for i, s in enumerate(stages)}
+        total = evs[0][0].elapsed_time(evs[-1][-1])
+        out[k] = {"it_s": round(steps / (total / 1e3), 1), "mean_instances": int(np.mean(Ms)),
+                  "stage_ms": {s: round(v, 4) for s, v in per.items()}}
+    ts.set_kernel(restore_kernel)
+    return out
 
 
 # ----------------------------------------------------------------------------- batched views
@@ -767,6 +796,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-multiview", action="store_true", help="skip the batched multi-view measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the per-kernel training sweep")
     ap.add_argument("--unfused", action="store_true", help="separate preprocess backward and Adam kernels")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -303,9 +303,10 @@ def algorithmic_bytes(stage, n, M, passes, sh_k, strategy=0, tile_passes=2, n_vi
             return n * (4 + 4 + 16 + 4) + M * (12 + 8 + 24 * passes + 8)
         # per splat: depth keys (read depth+radius, write key), 4 depth passes (16 B each), tiles
         # gathered twice in depth order, offsets written and read, rect twice (difference array,
-        # duplicate); per instance: duplicate write 8, each tile pass read 8 + write 8 except the
-        # last, which writes only the 4-byte values
-        return n * (8 + 4 + 4 * 16 + 8 + 8 + 32) + M * (8 + 16 * tile_passes - 4)
+        # duplication); per instance: the duplication fused with the first tile pass writes
+        # 8 B, every later pass reads 8 B and writes 8 B, the last writes only 4-byte values
+        per_instance = 4 if tile_passes == 1 else 8 + 16 * (tile_passes - 2) + 12
+        return n * (8 + 4 + 4 * 16 + 8 + 8 + 32) + M * per_instance
     if stage == "preprocess_bwd":
         # every splat: radius read, all gradients written; visible: parameters, grad2d and clamp
         # bits read
@@ -559,8 +560,8 @@ def launches_per_step(strategy, tile_bits, fused=True):
     if strategy == 1:  # 64-bit keys: block sums, scan, duplicate, histogram, hist scan, passes, ranges
         sort = 6 + (32 + tile_bits + 7) // 8
     else:  # depth keys, histogram, hist scan, 4 depth passes, block sums, scan, tile diff, tile setup,
-        # offsets, duplicate, tile passes
-        sort = 3 + 4 + 6 + max(1, (tile_bits + 7) // 8)
+        # offsets, duplication fused with the first tile pass, the other tile passes
+        sort = 3 + 4 + 5 + max(1, (tile_bits + 7) // 8)
     # preprocess, render_fwd, l1, render_bwd, then preprocess_bwd + 5 Adam groups or one fused kernel
     return 1 + sort + 1 + 1 + 1 + (1 if fused else 1 + 5)
 

@@ -14,13 +14,16 @@
 //                                         difference array, 4 atomics per splat) -> the tile
 //                                         ranges and the digit bases of the tile passes
 //   k_splat_offsets                       per-position instance offsets (depth order)
-//   k_duplicate_balanced                  emit (tile id, splat) per instance in depth order, each
+//   k_dup_sweep                           emit (tile id, splat) per instance in depth order, each
 //                                         CTA a fixed range of instances (near splats are the
-//                                         largest, so splitting by splats would be unbalanced)
-//   p x k_onesweep<u32>                   stable LSD sort of the 32-bit tile ids (p = 2 at 1080p
-//                                         with 16-pixel tiles); the last writes only the values
+//                                         largest, so splitting by splats would be unbalanced),
+//                                         and sort that partition by the first tile digit at once
+//   (p - 1) x k_onesweep<u32>             the remaining stable LSD passes over the 32-bit tile ids
+//                                         (p = 2 at 1080p with 16- or 32-pixel tiles); the last
+//                                         writes only the values
 //   k_keys64 (optional)                   the 64-bit keys, when the caller asks for them
-//   About 36 bytes of HBM traffic per instance.
+//   About 20 bytes of HBM traffic per instance at p = 2.  (With the reduce-then-scan passes,
+//   k_duplicate_balanced writes the instances and the first pass reads them back.)
 //
 // DARB_SORT_KEYS64
 //   k_duplicate (64-bit keys in splat order), k_sort_hist, k_hist_scan, 6 x k_onesweep<u64>
@@ -45,6 +48,7 @@ constexpr uint32_t kCountMask = (1u << 30) - 1;
 constexpr int kSpinLimit = 1 << 22;  // with the 512 ns back-off: about two seconds at most
 constexpr int kLookbackWindow = 8;
 constexpr size_t kMaxDiffSmem = 96 * 1024;  // tile difference array privatised per CTA up to this size
+constexpr size_t kMaxSetupSmem = 160 * 1024;  // tile counts + difference array staged in shared memory up to this
 constexpr int kDupItems = 16;
 static_assert(kScanThreads * kDupItems == kSortTile, "a duplicate CTA must cover exactly one sort partition");
 constexpr int kDupTile = kScanThreads * kDupItems;  // instances per balanced duplicate CTA
@@ -404,33 +408,62 @@ __global__ void __launch_bounds__(256) k_hist_scan(const uint32_t *__restrict__ 
 
 // Per-tile instance counts (2D prefix of the difference array) -> ranges [start, end) and the
 // digit bases of the tile passes.  One CTA.  After a capacity overflow every range is empty.
+// One CTA: 2D prefix sums of the difference array (a warp per row, then a warp per column, in
+// shared memory when `counts` is a shared-memory array) give the per-tile instance counts, then
+// their exclusive scan gives the ranges and a histogram of each tile-pass digit the passes'
+// digit bases.  With SMEM the difference array is staged into shared memory first.
+template <bool SMEM>
 __global__ void __launch_bounds__(1024)
-k_tile_setup(int tiles_x, int tiles_y, const int *__restrict__ diff, uint32_t *__restrict__ counts,
+k_tile_setup(int tiles_x, int tiles_y, const int *__restrict__ diff_g, uint32_t *__restrict__ counts_g,
              const uint32_t *num, unsigned long long capacity, PassSpec ps, uint32_t *__restrict__ ranges,
              uint32_t *__restrict__ digit_base) {
+    extern __shared__ uint32_t s_dyn[];
     __shared__ uint32_t s_h[kMaxPasses * 256];
     __shared__ unsigned long long s_warp[1024 / 32 + 1];
     __shared__ uint32_t s_warp32[1024 / 32 + 1];
+    const int w1 = tiles_x + 1, n_tiles = tiles_x * tiles_y;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int *diff = diff_g;
+    uint32_t *counts = counts_g;
+    if (SMEM) {
+        counts = s_dyn;
+        int *d = reinterpret_cast<int *>(s_dyn + n_tiles);
+        for (int i = threadIdx.x; i < w1 * (tiles_y + 1); i += 1024) d[i] = diff_g[i];
+        diff = d;
+    }
     for (int i = threadIdx.x; i < kMaxPasses * 256; i += 1024) s_h[i] = 0;
-    const int w1 = tiles_x + 1;
-    for (int y = threadIdx.x; y < tiles_y; y += 1024) {  // prefix along x
-        int acc = 0;
-        for (int x = 0; x < tiles_x; ++x) {
-            acc += diff[y * w1 + x];
-            counts[y * tiles_x + x] = (uint32_t)acc;
+    __syncthreads();
+    for (int y = warp; y < tiles_y; y += 32) {  // prefix along x
+        uint32_t carry = 0;
+        for (int x0 = 0; x0 < tiles_x; x0 += 32) {
+            const int x = x0 + lane;
+            uint32_t v = x < tiles_x ? (uint32_t)diff[y * w1 + x] : 0u;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t u = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += u;
+            }
+            if (x < tiles_x) counts[y * tiles_x + x] = carry + v;
+            carry += __shfl_sync(0xffffffffu, v, 31);
         }
     }
     __syncthreads();
-    for (int x = threadIdx.x; x < tiles_x; x += 1024) {  // prefix along y
-        uint32_t acc = 0;
-        for (int y = 0; y < tiles_y; ++y) {
-            acc += counts[y * tiles_x + x];
-            counts[y * tiles_x + x] = acc;
+    for (int x = warp; x < tiles_x; x += 32) {  // prefix along y
+        uint32_t carry = 0;
+        for (int y0 = 0; y0 < tiles_y; y0 += 32) {
+            const int y = y0 + lane;
+            uint32_t v = y < tiles_y ? counts[y * tiles_x + x] : 0u;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t u = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += u;
+            }
+            if (y < tiles_y) counts[y * tiles_x + x] = carry + v;
+            carry += __shfl_sync(0xffffffffu, v, 31);
         }
     }
     __syncthreads();
     const bool overflow = (unsigned long long)*num > capacity;
-    const int n_tiles = tiles_x * tiles_y;
     unsigned long long carry = 0;
     for (int chunk = 0; chunk < n_tiles; chunk += 1024) {
         const int t = chunk + threadIdx.x;
@@ -472,6 +505,12 @@ constexpr int kScanBlock = 4096;  // values per CTA of the table scan (1024 thre
 #define DARB_PASS_ONESWEEP 1
 #endif
 constexpr bool kPassOnesweep = DARB_PASS_ONESWEEP != 0;
+
+// Resident CTAs per SM the one-pass sort kernels are compiled for (their register budget).
+#ifndef DARB_SORT_CTAS_PER_SM
+#define DARB_SORT_CTAS_PER_SM 3
+#endif
+constexpr int kSortCtasPerSm = DARB_SORT_CTAS_PER_SM;
 
 // Peer masks by match.any (one instruction) or by one ballot per digit bit.
 #ifndef DARB_PEERS_BY_MATCH
@@ -559,7 +598,7 @@ k_scan_apply(uint32_t *__restrict__ data, unsigned long long count, const uint32
 
 // Rank and scatter one partition with known per-digit global offsets (no look-back).
 template <typename K, bool WRITE_KEYS>
-__global__ void __launch_bounds__(kSortThreads, 2)
+__global__ void __launch_bounds__(kSortThreads, kSortCtasPerSm)
 k_downsweep(const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__restrict__ kout,
             uint32_t *__restrict__ vout, const uint32_t *num, unsigned long long cap, int shift, int bits,
             const uint32_t *__restrict__ offsets, uint32_t n_parts) {
@@ -661,51 +700,52 @@ struct Staging {
     static constexpr size_t bytes = (size_t)kSortTile * ((WRITE_KEYS ? sizeof(K) : 1) + 4);
 };
 
-// One stable LSD pass over the digit of `bits` bits at `shift`.  M = min(*num, cap), or cap if
-// num is null.  vin may be null: values are then the input positions (iota).
+// Dynamic shared memory of the fused duplicate + first pass: the staging arrays, which also
+// hold the partition's owner offsets (kDupTile + 1) and splat ids (kDupTile) while the
+// instances are generated.
+template <bool WRITE_KEYS>
+struct DupStaging {
+    static constexpr size_t owners = (size_t)(2 * kDupTile + 1) * 4;
+    static constexpr size_t bytes = Staging<uint32_t, WRITE_KEYS>::bytes > owners ? Staging<uint32_t, WRITE_KEYS>::bytes
+                                                                                   : owners;
+};
+
+struct SweepSmem {
+    uint32_t wh[kSortThreads / 32][256];
+    uint32_t cta_excl[256];
+    uint32_t gbase[256];
+    uint32_t warp[kSortThreads / 32 + 1];
+    uint32_t part;
+    int res[2];
+};
+
+// Claims this CTA's partition (in launch order, so that look-back only waits on CTAs that
+// have started) and clears the per-warp digit counters.
+__device__ __forceinline__ uint32_t sweep_begin(SweepSmem &sm, uint32_t *part_counter) {
+    if (threadIdx.x == 0) sm.part = atomicAdd(part_counter, 1u);
+    for (int i = threadIdx.x; i < (kSortThreads / 32) * 256; i += kSortThreads) (&sm.wh[0][0])[i] = 0;
+    __syncthreads();
+    return sm.part;
+}
+
+// Steps 1-4 of one stable LSD pass for a partition whose items are in registers (item `it` of
+// lane l in warp w is input position base + w * 32 * kSortItems + it * 32 + l; invalid items
+// carry the all-ones key): ranking, look-back for the digits' global bases, and the scatter.
+// Staging may alias memory the caller used before, as long as its last read precedes this
+// call's first barrier.
 template <typename K, bool WRITE_KEYS>
-__global__ void __launch_bounds__(kSortThreads, 2)
-k_onesweep(const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__restrict__ kout,
-           uint32_t *__restrict__ vout, const uint32_t *num, unsigned long long cap, int shift, int bits,
-           const uint32_t *__restrict__ digit_base, uint32_t *lookback, uint32_t *part_counter, uint32_t *status) {
-    extern __shared__ __align__(16) unsigned char smem[];
+__device__ __forceinline__ void sweep_partition(SweepSmem &sm, unsigned char *smem, const K (&k)[kSortItems],
+                                                const uint32_t (&v)[kSortItems], uint32_t part, uint32_t base,
+                                                uint32_t M, int shift, int bits,
+                                                const uint32_t *__restrict__ digit_base, uint32_t *lookback,
+                                                uint32_t *status, K *__restrict__ kout, uint32_t *__restrict__ vout) {
     uint32_t *s_v = reinterpret_cast<uint32_t *>(smem);
     K *s_k = reinterpret_cast<K *>(smem + (size_t)kSortTile * 4);
     uint8_t *s_d = reinterpret_cast<uint8_t *>(smem + (size_t)kSortTile * 4);
     constexpr int NW = kSortThreads / 32;
-    __shared__ uint32_t s_wh[NW][256];
-    __shared__ uint32_t s_cta_excl[256];
-    __shared__ uint32_t s_gbase[256];
-    __shared__ uint32_t s_warp[NW + 1];
-    __shared__ uint32_t s_part;
-
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t radix = 1u << bits, mask = radix - 1u;
-    // After a capacity overflow the instance buffers hold only part of the instances while the
-    // digit bases count all of them: sort nothing (the caller sees DARB_ERR_CAPACITY).
-    if (num && (unsigned long long)*num > cap) return;
-    if (tid == 0) s_part = atomicAdd(part_counter, 1u);
-    for (int i = tid; i < NW * 256; i += kSortThreads) (&s_wh[0][0])[i] = 0;
-    __syncthreads();
-    const uint32_t M = (uint32_t)(num ? min((unsigned long long)*num, cap) : cap);
-    const uint32_t part = s_part;
-    const uint32_t n_parts = (M + kSortTile - 1) / kSortTile;
-    if (part >= n_parts) return;
-    const uint32_t base = part * kSortTile;
-
-    K k[kSortItems];
-    uint32_t v[kSortItems], rk[kSortItems];
-#pragma unroll
-    for (int it = 0; it < kSortItems; ++it) {
-        const uint32_t idx = base + warp * (32 * kSortItems) + it * 32 + lane;
-        if (idx < M) {
-            k[it] = kin[idx];
-            v[it] = vin ? vin[idx] : idx;
-        } else {
-            k[it] = ~K(0);  // the top digit, ranked after every valid key of the partition
-            v[it] = 0;
-        }
-    }
+    uint32_t rk[kSortItems];
     const uint32_t lt = lanemask_lt();
     // 1) Unordered per-warp digit counts (one shared-memory atomic per group of equal digits);
     //    rk keeps each item's peer mask for the ordered ranking below.
@@ -713,7 +753,7 @@ k_onesweep(const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__res
     for (int it = 0; it < kSortItems; ++it) {
         const uint32_t d = (uint32_t)(k[it] >> shift) & mask;
         const uint32_t peers = PEERS_BY_MATCH ? __match_any_sync(0xffffffffu, d) : match_digit(d, bits);
-        if (lane == __ffs(peers) - 1) atomicAdd(&s_wh[warp][d], (uint32_t)__popc(peers));
+        if (lane == __ffs(peers) - 1) atomicAdd(&sm.wh[warp][d], (uint32_t)__popc(peers));
         rk[it] = peers;
     }
     __syncthreads();
@@ -726,15 +766,15 @@ k_onesweep(const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__res
     if (dg < radix) {
 #pragma unroll
         for (int w = 0; w < NW; ++w) {
-            const uint32_t c = s_wh[w][dg];
-            s_wh[w][dg] = cnt;
+            const uint32_t c = sm.wh[w][dg];
+            sm.wh[w][dg] = cnt;
             cnt += c;
         }
         st_relaxed(mine, (part == 0 ? kFlagIncl : kFlagLocal) | cnt);
     }
     uint32_t tot;
-    const uint32_t cex = block_exclusive_scan<kSortThreads>(cnt, s_warp, tot);
-    if (dg < radix) s_cta_excl[dg] = cex;
+    const uint32_t cex = block_exclusive_scan<kSortThreads>(cnt, sm.warp, tot);
+    if (dg < radix) sm.cta_excl[dg] = cex;
     __syncthreads();
 
     // 3) ordered ranking inside each warp (stable: item-major, lane-minor order = input order),
@@ -743,10 +783,10 @@ k_onesweep(const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__res
     for (int it = 0; it < kSortItems; ++it) {
         const uint32_t d = (uint32_t)(k[it] >> shift) & mask;
         const uint32_t peers = rk[it];
-        const uint32_t prev = s_wh[warp][d];
-        const uint32_t pos = s_cta_excl[d] + prev + __popc(peers & lt);
+        const uint32_t prev = sm.wh[warp][d];
+        const uint32_t pos = sm.cta_excl[d] + prev + __popc(peers & lt);
         __syncwarp();
-        if (lane == 31 - __clz(peers)) s_wh[warp][d] = prev + __popc(peers);
+        if (lane == 31 - __clz(peers)) sm.wh[warp][d] = prev + __popc(peers);
         __syncwarp();
         if (WRITE_KEYS) s_k[pos] = k[it];
         else s_d[pos] = (uint8_t)d;
@@ -790,7 +830,7 @@ k_onesweep(const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__res
             }
             st_relaxed(mine, kFlagIncl | ((excl + cnt) & kCountMask));
         }
-        s_gbase[dg] = digit_base[dg] + excl;
+        sm.gbase[dg] = digit_base[dg] + excl;
     }
     __syncthreads();
     const uint32_t nvalid = min((uint32_t)kSortTile, M - base);
@@ -803,10 +843,121 @@ k_onesweep(const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__res
         } else {
             d = s_d[j];
         }
-        const uint32_t dst = s_gbase[d] + (j - s_cta_excl[d]);
+        const uint32_t dst = sm.gbase[d] + (j - sm.cta_excl[d]);
         if (WRITE_KEYS) kout[dst] = kk;
         vout[dst] = s_v[j];
     }
+}
+
+// One stable LSD pass over the digit of `bits` bits at `shift`.  M = min(*num, cap), or cap if
+// num is null.  vin may be null: values are then the input positions (iota).
+template <typename K, bool WRITE_KEYS>
+__global__ void __launch_bounds__(kSortThreads, kSortCtasPerSm)
+k_onesweep(const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__restrict__ kout,
+           uint32_t *__restrict__ vout, const uint32_t *num, unsigned long long cap, int shift, int bits,
+           const uint32_t *__restrict__ digit_base, uint32_t *lookback, uint32_t *part_counter, uint32_t *status) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ SweepSmem sm;
+    // After a capacity overflow the instance buffers hold only part of the instances while the
+    // digit bases count all of them: sort nothing (the caller sees DARB_ERR_CAPACITY).
+    if (num && (unsigned long long)*num > cap) return;
+    const uint32_t part = sweep_begin(sm, part_counter);
+    const uint32_t M = (uint32_t)(num ? min((unsigned long long)*num, cap) : cap);
+    const uint32_t n_parts = (M + kSortTile - 1) / kSortTile;
+    if (part >= n_parts) return;
+    const uint32_t base = part * kSortTile;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    K k[kSortItems];
+    uint32_t v[kSortItems];
+#pragma unroll
+    for (int it = 0; it < kSortItems; ++it) {
+        const uint32_t idx = base + warp * (32 * kSortItems) + it * 32 + lane;
+        if (idx < M) {
+            k[it] = kin[idx];
+            v[it] = vin ? vin[idx] : idx;
+        } else {
+            k[it] = ~K(0);  // the top digit, ranked after every valid key of the partition
+            v[it] = 0;
+        }
+    }
+    sweep_partition<K, WRITE_KEYS>(sm, smem, k, v, part, base, M, shift, bits, digit_base, lookback, status, kout,
+                                   vout);
+}
+
+// The balanced duplication fused with the first tile pass: each CTA generates one partition
+// of instances (tile id, splat) in depth order straight into registers -- the owner of
+// instance j is the last depth-ordered splat whose offset is <= j -- and sorts it by the first
+// tile digit, so the unsorted instances never go through HBM.
+template <bool WRITE_KEYS>
+__global__ void __launch_bounds__(kSortThreads, kSortCtasPerSm)
+k_dup_sweep(int n, const uint32_t *__restrict__ order, const uint32_t *__restrict__ offs,
+            const int4 *__restrict__ rect, int tiles_x, const uint32_t *num, unsigned long long cap, int bits,
+            const uint32_t *__restrict__ digit_base, uint32_t *lookback, uint32_t *part_counter, uint32_t *status,
+            uint32_t *__restrict__ kout, uint32_t *__restrict__ vout) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ SweepSmem sm;
+    if ((unsigned long long)*num > cap) return;  // overflow: nothing is emitted (status already set)
+    const uint32_t part = sweep_begin(sm, part_counter);
+    const uint32_t M = *num;
+    const uint32_t n_parts = (M + kSortTile - 1) / kSortTile;
+    if (part >= n_parts) return;
+    const uint32_t lo = part * kSortTile, hi = min(M, lo + (uint32_t)kSortTile);
+    uint32_t *s_off = reinterpret_cast<uint32_t *>(smem);
+    uint32_t *s_id = s_off + kDupTile + 1;
+    const int first = cta_upper_owner(offs, n, lo, &sm.res[0]);
+    const int last = cta_upper_owner(offs, n, hi - 1, &sm.res[1]);
+    const int count = min(last - first + 1, kDupTile);  // every owner has >= 1 instance
+    for (int i = threadIdx.x; i <= count; i += kSortThreads) {
+        s_off[i] = offs[first + i];
+        if (i < count) s_id[i] = order[first + i];
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t wbase = lo + (uint32_t)warp * (32 * kSortItems);
+    int s = 0;
+    {  // owner of this lane's first instance
+        const uint32_t k0 = min(wbase + lane, hi - 1);
+        int a = 0, b = count - 1;
+        while (a < b) {
+            const int mid = (a + b + 1) >> 1;
+            if (s_off[mid] <= k0) a = mid;
+            else b = mid - 1;
+        }
+        s = a;
+    }
+    uint32_t kk[kSortItems], vv[kSortItems];
+#pragma unroll
+    for (int it = 0; it < kSortItems; ++it) {
+        const uint32_t j = wbase + it * 32 + lane;
+        if (j >= hi) {
+            kk[it] = 0xffffffffu;
+            vv[it] = 0;
+            continue;
+        }
+        if (s_off[min(s + 8, count)] <= j) {  // far ahead: binary search the rest
+            int a = s, b = count - 1;
+            while (a < b) {
+                const int mid = (a + b + 1) >> 1;
+                if (s_off[mid] <= j) a = mid;
+                else b = mid - 1;
+            }
+            s = a;
+        } else {
+            while (s_off[s + 1] <= j) ++s;
+        }
+        const uint32_t id = s_id[s];
+        const uint32_t l = j - s_off[s];
+        const int4 r = __ldg(rect + id);
+        const uint32_t w = (uint32_t)(r.z - r.x + 1);
+        // row = l / w: float estimate, then exact integer correction
+        uint32_t row = __float2uint_rz(__fdividef((float)l, (float)w));
+        while (row * w > l) --row;
+        while ((row + 1) * w <= l) ++row;
+        kk[it] = ((uint32_t)r.y + row) * (uint32_t)tiles_x + (uint32_t)r.x + (l - row * w);
+        vv[it] = id;
+    }
+    sweep_partition<uint32_t, WRITE_KEYS>(sm, smem, kk, vv, part, lo, M, 0, bits, digit_base, lookback, status, kout,
+                                          vout);
 }
 
 __global__ void __launch_bounds__(256)
@@ -818,6 +969,55 @@ k_ranges(const uint64_t *__restrict__ keys, const uint32_t *num, unsigned long l
         const uint32_t t = (uint32_t)(keys[i] >> 32);
         if (i == 0 || (uint32_t)(keys[i - 1] >> 32) != t) ranges[2 * (size_t)t] = (uint32_t)i;
         if (i == M - 1 || (uint32_t)(keys[i + 1] >> 32) != t) ranges[2 * (size_t)t + 1] = (uint32_t)(i + 1);
+    }
+}
+
+// Depth keys of the visible splats only, compacted in index order (so the depth sort, being
+// stable, keeps equal depths in index order): k_vis_count counts each kScanTile block's visible
+// splats, k_scan_block_sums turns the counts into block offsets and the total n_vis, and
+// k_depth_compact writes (depth bits, index) of the visible splats to [0, n_vis) and the culled
+// indices, also in index order, to [n_vis, n) of both value buffers -- where the sorted order
+// ends up after any number of passes over [0, n_vis).
+__global__ void __launch_bounds__(kScanThreads)
+k_vis_count(int n, const int *__restrict__ radius, uint32_t *__restrict__ block_counts) {
+    __shared__ uint32_t s_warp[kScanThreads / 32 + 1];
+    const int base = blockIdx.x * kScanTile;
+    uint32_t c = 0;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        const int i = base + j * kScanThreads + threadIdx.x;
+        c += (i < n && radius[i] != 0) ? 1u : 0u;
+    }
+    uint32_t total;
+    block_exclusive_scan<kScanThreads>(c, s_warp, total);
+    if (threadIdx.x == 0) block_counts[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+k_depth_compact(int n, const int *__restrict__ radius, const float *__restrict__ depth,
+                const unsigned long long *__restrict__ block_offsets, const uint32_t *__restrict__ n_vis,
+                uint32_t *__restrict__ keys, uint32_t *__restrict__ ids0, uint32_t *__restrict__ ids1) {
+    __shared__ uint32_t s_warp[kScanThreads / 32 + 1];
+    const int base = blockIdx.x * kScanTile;
+    const uint32_t vis0 = (uint32_t)block_offsets[blockIdx.x];
+    const uint32_t cul0 = *n_vis + ((uint32_t)base - vis0);  // culled splats before this block
+    uint32_t vis = 0, cul = 0;
+    for (int j = 0; j < kScanItems; ++j) {  // kScanThreads consecutive splats per round
+        const int i = base + j * kScanThreads + threadIdx.x;
+        const bool valid = i < n;
+        const bool v = valid && radius[i] != 0;
+        uint32_t tv, tc;
+        const uint32_t rv = block_exclusive_scan<kScanThreads>(v ? 1u : 0u, s_warp, tv);
+        const uint32_t rc = block_exclusive_scan<kScanThreads>((valid && !v) ? 1u : 0u, s_warp, tc);
+        if (v) {
+            keys[vis0 + vis + rv] = __float_as_uint(depth[i]);
+            ids0[vis0 + vis + rv] = (uint32_t)i;
+        } else if (valid) {
+            ids0[cul0 + cul + rc] = (uint32_t)i;
+            ids1[cul0 + cul + rc] = (uint32_t)i;
+        }
+        vis += tv;
+        cul += tc;
     }
 }
 
@@ -954,7 +1154,7 @@ Layout layout(int n, uint64_t capacity, int tiles_x, int tiles_y, int strategy, 
         put(10, (size_t)2 * kMaxPasses * 256 * 4 + (size_t)(tiles_x + 1) * (tiles_y + 1) * 4);
         put(18, kPassOnesweep ? (size_t)passes * parts_cap * 256 * 4 : 0);  // tile-pass look-back
         put(19, kPassOnesweep ? (size_t)4 * parts_n * 256 * 4 : 0);         // depth-pass look-back
-        put(13, (size_t)kMaxPasses * 4 * 2);    // onesweep partition counters
+        put(13, (size_t)(kMaxPasses * 2 + 1) * 4);  // onesweep partition counters, visible-splat count
     }
     L.off[14] = b;
     L.total = b + 256;
@@ -1051,29 +1251,38 @@ cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int til
     if (n > 0) {
         const PassSpec dps = split_bits(32);
         uint32_t *dph = reinterpret_cast<uint32_t *>(at(12));
-        k_depth_keys<<<(n + 255) / 256, 256, 0, st>>>(n, proj.radius, proj.depth, kbuf[0]);
         uint32_t *dbase = reinterpret_cast<uint32_t *>(at(9));
+        const uint32_t *n_vis = nullptr;  // keys sorted: all n, or the visible n_vis (device)
+        const uint32_t *vin = nullptr;    // first pass: values are the splat indices
         if (kPassOnesweep) {
+            uint32_t *nv = counters + 2 * kMaxPasses;
+            k_vis_count<<<nb, kScanThreads, 0, st>>>(n, proj.radius, block_sums);
+            k_scan_block_sums<<<1, 1024, 0, st>>>(nb, block_sums, block_off, nv, out.status, (unsigned long long)n);
+            k_depth_compact<<<nb, kScanThreads, 0, st>>>(n, proj.radius, proj.depth, block_off, nv, kbuf[0], vbuf[0],
+                                                          vbuf[1]);
+            n_vis = nv;
+            vin = vbuf[0];
             uint32_t *dhist = reinterpret_cast<uint32_t *>(at(10)) + kMaxPasses * 256;
             const int hb = std::min((n + 255) / 256, 152 * 8);
-            k_sort_hist<uint32_t><<<hb, 256, 0, st>>>(kbuf[0], nullptr, (unsigned long long)n, dps, dhist);
+            k_sort_hist<uint32_t><<<hb, 256, 0, st>>>(kbuf[0], n_vis, (unsigned long long)n, dps, dhist);
             k_hist_scan<<<dps.passes, 256, 0, st>>>(dhist, dbase);
+        } else {
+            k_depth_keys<<<(n + 255) / 256, 256, 0, st>>>(n, proj.radius, proj.depth, kbuf[0]);
         }
         TRY(cudaGetLastError());
         uint32_t *lbd = reinterpret_cast<uint32_t *>(at(19));
         const size_t lbd_stride = (((size_t)n + kSortTile - 1) / kSortTile) * 256;
-        const uint32_t *vin = nullptr;  // first pass: values are the splat indices
         int cur = 0;
         for (int p = 0; p < dps.passes; ++p) {
             const int nxt = 1 - cur;
             const bool last = p == dps.passes - 1;
             if (kPassOnesweep) {
                 if (last)
-                    TRY((launch_pass<uint32_t, false>(kbuf[cur], vin, nullptr, vbuf[nxt], nullptr, (unsigned long long)n,
+                    TRY((launch_pass<uint32_t, false>(kbuf[cur], vin, nullptr, vbuf[nxt], n_vis, (unsigned long long)n,
                                                       (uint64_t)n, dps.shift[p], dps.bits[p], dbase + p * 256,
                                                       lbd + p * lbd_stride, counters + kMaxPasses + p, out.status, st)));
                 else
-                    TRY((launch_pass<uint32_t, true>(kbuf[cur], vin, kbuf[nxt], vbuf[nxt], nullptr, (unsigned long long)n,
+                    TRY((launch_pass<uint32_t, true>(kbuf[cur], vin, kbuf[nxt], vbuf[nxt], n_vis, (unsigned long long)n,
                                                      (uint64_t)n, dps.shift[p], dps.bits[p], dbase + p * 256,
                                                      lbd + p * lbd_stride, counters + kMaxPasses + p, out.status, st)));
             } else {
@@ -1124,8 +1333,18 @@ cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int til
                                                                     diff);
         }
     }
-    k_tile_setup<<<1, 1024, 0, st>>>(tiles_x, tiles_y, diff, counts, out.num_instances, cap, tps,
-                                     out.ranges, tbase);
+    {
+        const size_t setup_smem = ((size_t)n_tiles + (size_t)(tiles_x + 1) * (tiles_y + 1)) * 4;
+        if (setup_smem <= kMaxSetupSmem) {
+            TRY(cudaFuncSetAttribute(k_tile_setup<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)setup_smem));
+            k_tile_setup<true><<<1, 1024, setup_smem, st>>>(tiles_x, tiles_y, diff, counts, out.num_instances, cap,
+                                                            tps, out.ranges, tbase);
+        } else {
+            k_tile_setup<false><<<1, 1024, 0, st>>>(tiles_x, tiles_y, diff, counts, out.num_instances, cap, tps,
+                                                    out.ranges, tbase);
+        }
+    }
     TRY(cudaGetLastError());
     // 4) per-position offsets, then the balanced duplication in depth order
     uint32_t *tk_a = reinterpret_cast<uint32_t *>(at(0)), *tv_a = reinterpret_cast<uint32_t *>(at(1));
@@ -1134,47 +1353,68 @@ cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int til
     if (nb > 0) k_splat_offsets<<<nb, kScanThreads, 0, st>>>(n, order, proj.tiles_touched, block_off, out.num_instances, offs);
     uint32_t *tph = reinterpret_cast<uint32_t *>(at(11));
     const uint32_t n_parts = (uint32_t)((grid + kSortTile - 1) / kSortTile);
-    if (grid > 0) {
+    uint32_t *lb = reinterpret_cast<uint32_t *>(at(18));
+    const size_t lb_stride = ((capacity + kSortTile - 1) / kSortTile) * 256;
+    if (grid > 0 && kPassOnesweep) {
+        // 5) duplication fused with the first tile pass, then the remaining stable LSD passes;
+        //    the last writes only the output values
+        const bool last0 = tps.passes == 1;
+        uint32_t *k0 = last0 ? nullptr : tk_b, *v0 = last0 ? out.values : tv_b;
+        const size_t smem = last0 ? DupStaging<false>::bytes : DupStaging<true>::bytes;
+        if (last0) {
+            TRY(cudaFuncSetAttribute(k_dup_sweep<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            k_dup_sweep<false><<<n_parts, kSortThreads, smem, st>>>(n, order, offs, proj.tile_rect, tiles_x,
+                                                                    out.num_instances, cap, tps.bits[0], tbase, lb,
+                                                                    counters, out.status, k0, v0);
+        } else {
+            TRY(cudaFuncSetAttribute(k_dup_sweep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            k_dup_sweep<true><<<n_parts, kSortThreads, smem, st>>>(n, order, offs, proj.tile_rect, tiles_x,
+                                                                   out.num_instances, cap, tps.bits[0], tbase, lb,
+                                                                   counters, out.status, k0, v0);
+        }
+        TRY(cudaGetLastError());
+        uint32_t *ka = tk_b, *va = tv_b, *kb = tk_a, *vb = tv_a;
+        for (int p = 1; p < tps.passes; ++p) {
+            const bool last = p == tps.passes - 1;
+            if (last)
+                TRY((launch_pass<uint32_t, false>(ka, va, nullptr, out.values, out.num_instances, cap, grid,
+                                                  tps.shift[p], tps.bits[p], tbase + p * 256, lb + p * lb_stride,
+                                                  counters + p, out.status, st)));
+            else
+                TRY((launch_pass<uint32_t, true>(ka, va, kb, vb, out.num_instances, cap, grid, tps.shift[p],
+                                                 tps.bits[p], tbase + p * 256, lb + p * lb_stride, counters + p,
+                                                 out.status, st)));
+            std::swap(ka, kb);
+            std::swap(va, vb);
+        }
+    } else if (grid > 0) {
+        // reduce-then-scan passes: the duplication also writes the first pass's histograms
         if (n > 0)
             k_duplicate_balanced<<<n_parts, kScanThreads, 0, st>>>(n, order, offs, proj.tile_rect, tiles_x,
                                                                    out.num_instances, cap, tk_a, tv_a, tps.bits[0],
                                                                    n_parts, tph);
         else
             TRY(cudaMemsetAsync(tph, 0, ((size_t)n_parts << tps.bits[0]) * 4, st));
-    }
-    TRY(cudaGetLastError());
-    // 5) stable LSD passes over the tile ids; the last writes only the output values
-    if (grid > 0) {
+        TRY(cudaGetLastError());
         uint32_t *ka = tk_a, *va = tv_a, *kb = tk_b, *vb = tv_b;
-        uint32_t *lb = reinterpret_cast<uint32_t *>(at(18));
-        const size_t lb_stride = ((capacity + kSortTile - 1) / kSortTile) * 256;
         for (int p = 0; p < tps.passes; ++p) {
             const bool last = p == tps.passes - 1;
             uint32_t *kout = last ? nullptr : kb;
             uint32_t *vout = last ? out.values : vb;
-            if (kPassOnesweep) {
-                if (last)
-                    TRY((launch_pass<uint32_t, false>(ka, va, kout, vout, out.num_instances, cap, grid, tps.shift[p],
-                                                      tps.bits[p], tbase + p * 256, lb + p * lb_stride, counters + p,
-                                                      out.status, st)));
-                else
-                    TRY((launch_pass<uint32_t, true>(ka, va, kout, vout, out.num_instances, cap, grid, tps.shift[p],
-                                                     tps.bits[p], tbase + p * 256, lb + p * lb_stride, counters + p,
-                                                     out.status, st)));
-            } else {
-                const bool ready = p == 0;  // the duplication wrote the first pass's histograms
-                if (last)
-                    TRY((launch_rts_pass<uint32_t, false>(ka, va, kout, vout, out.num_instances, cap, grid,
-                                                          tps.shift[p], tps.bits[p], tph, sums, ready, st)));
-                else
-                    TRY((launch_rts_pass<uint32_t, true>(ka, va, kout, vout, out.num_instances, cap, grid,
-                                                         tps.shift[p], tps.bits[p], tph, sums, ready, st)));
-            }
+            const bool ready = p == 0;
+            if (last)
+                TRY((launch_rts_pass<uint32_t, false>(ka, va, kout, vout, out.num_instances, cap, grid,
+                                                      tps.shift[p], tps.bits[p], tph, sums, ready, st)));
+            else
+                TRY((launch_rts_pass<uint32_t, true>(ka, va, kout, vout, out.num_instances, cap, grid,
+                                                     tps.shift[p], tps.bits[p], tph, sums, ready, st)));
             if (!last) {
                 std::swap(ka, kb);
                 std::swap(va, vb);
             }
         }
+    }
+    if (grid > 0) {
         if (out.keys) k_keys64<<<n_tiles, 256, 0, st>>>(out.ranges, out.values, proj.depth, n, out.keys);
         TRY(cudaGetLastError());
     }

@@ -295,6 +295,80 @@ def l1_loss(image, target):
     return np.abs(d).mean(), np.sign(d) / d.size
 
 
+# The paper's image loss (Sec. 4.2): L = (1 - lambda) L1 + lambda L_D-SSIM, the two terms of
+# the 3DGS work it builds on.  The paper gives neither lambda nor the SSIM window; they are taken
+# from that work: lambda = 0.2, D-SSIM = 1 - SSIM, SSIM per channel with an 11 x 11 Gaussian
+# window (sigma 1.5, normalised), zero padding outside the image, C1 = 0.01^2, C2 = 0.03^2 for
+# intensities in [0, 1], averaged over channels and pixels.
+SSIM_C1 = 0.01 ** 2
+SSIM_C2 = 0.03 ** 2
+SSIM_RADIUS = 5
+SSIM_SIGMA = 1.5
+
+
+def ssim_window():
+    """The 1-D window g[-5..5] = exp(-k^2 / (2 sigma^2)), normalised to sum 1; the 2-D window is
+    its outer product."""
+    k = np.arange(-SSIM_RADIUS, SSIM_RADIUS + 1, dtype=np.float64)
+    g = np.exp(-k * k / (2.0 * SSIM_SIGMA ** 2))
+    return g / g.sum()
+
+
+def _blur(a):
+    """Window-weighted local mean of a [C, H, W] array, zero outside the image: a plain loop over
+    the 11 x 11 offsets (the window is symmetric, so this equals its own adjoint)."""
+    g = ssim_window()
+    C, H, W = a.shape
+    R = SSIM_RADIUS
+    pad = np.zeros((C, H + 2 * R, W + 2 * R))
+    pad[:, R:R + H, R:R + W] = a
+    out = np.zeros((C, H, W))
+    for dy in range(-R, R + 1):
+        for dx in range(-R, R + 1):
+            out += g[dy + R] * g[dx + R] * pad[:, R + dy:R + dy + H, R + dx:R + dx + W]
+    return out
+
+
+def ssim_map(image, target):
+    """SSIM at every channel and pixel (Wang et al. 2004, the form 3DGS trains with)."""
+    x = np.asarray(image, np.float64)
+    y = np.asarray(target, np.float64)
+    mx, my = _blur(x), _blur(y)
+    vx = _blur(x * x) - mx * mx
+    vy = _blur(y * y) - my * my
+    cxy = _blur(x * y) - mx * my
+    return ((2 * mx * my + SSIM_C1) * (2 * cxy + SSIM_C2)) / ((mx * mx + my * my + SSIM_C1) * (vx + vy + SSIM_C2))
+
+
+def l1_dssim_loss(image, target, lam=0.2):
+    """(1 - lam) mean|x - y| + lam (1 - mean SSIM(x, y)) and its gradient w.r.t. x.
+
+    With the local moments m_x = G*x, m_y = G*y, s_xx = G*x^2, s_xy = G*xy and
+    A1 = 2 m_x m_y + C1, A2 = 2 (s_xy - m_x m_y) + C2, B1 = m_x^2 + m_y^2 + C1,
+    B2 = s_xx - m_x^2 + s_yy - m_y^2 + C2, SSIM = A1 A2 / (B1 B2) has
+      dSSIM/dm_x  = 2 m_y (A2 - A1) / (B1 B2) - 2 m_x SSIM (1/B1 - 1/B2)
+      dSSIM/ds_xx = -SSIM / B2
+      dSSIM/ds_xy = 2 A1 / (B1 B2)
+    and, the window being symmetric, d(mean SSIM)/dx = (G*dm + 2 x G*ds_xx + y G*ds_xy) / N."""
+    x = np.asarray(image, np.float64)
+    y = np.asarray(target, np.float64)
+    N = x.size
+    mx, my = _blur(x), _blur(y)
+    sxx, syy, sxy = _blur(x * x), _blur(y * y), _blur(x * y)
+    A1 = 2 * mx * my + SSIM_C1
+    A2 = 2 * (sxy - mx * my) + SSIM_C2
+    B1 = mx * mx + my * my + SSIM_C1
+    B2 = (sxx - mx * mx) + (syy - my * my) + SSIM_C2
+    ssim = A1 * A2 / (B1 * B2)
+    d_m = 2 * my * (A2 - A1) / (B1 * B2) - 2 * mx * ssim * (1 / B1 - 1 / B2)
+    d_sxx = -ssim / B2
+    d_sxy = 2 * A1 / (B1 * B2)
+    dssim_dx = (_blur(d_m) + 2 * x * _blur(d_sxx) + y * _blur(d_sxy)) / N
+    l1, dl1 = l1_loss(x, y)
+    loss = (1 - lam) * l1 + lam * (1 - ssim.mean())
+    return loss, (1 - lam) * dl1 - lam * dssim_dx, ssim.mean()
+
+
 def adam_update(p, g, m, v, lr, step, beta1=0.9, beta2=0.999, eps=1e-15):
     """One Adam step (Kingma & Ba, Algorithm 1) on float64 copies; returns (p, m, v)."""
     p, g, m, v = (np.asarray(a, np.float64) for a in (p, g, m, v))

@@ -529,3 +529,53 @@ def test_l1_gradient_matches_finite_differences():
     tie = img.copy()
     tie[0, 0, 0] = tgt[0, 0, 0]
     assert oracle.l1_loss(tie, tgt)[1][0, 0, 0] == 0.0  # the subgradient taken at a tie
+
+
+# --------------------------------------------------------------------------- D-SSIM term
+
+def test_ssim_window_is_the_normalised_gaussian():
+    g = oracle.ssim_window()
+    assert g.shape == (11,) and g.sum() == pytest.approx(1.0, abs=1e-15)
+    assert g[5] / g[6] == pytest.approx(np.exp(1 / (2 * 1.5 ** 2)), rel=1e-14)
+    assert np.allclose(g, g[::-1])
+
+
+def test_ssim_of_an_image_with_itself_is_one_with_zero_gradient():
+    rng = np.random.default_rng(5)
+    x = rng.uniform(size=(3, 23, 17))
+    assert np.allclose(oracle.ssim_map(x, x), 1.0, atol=1e-14)
+    loss, grad, mean_ssim = oracle.l1_dssim_loss(x, x, lam=1.0)
+    assert loss == pytest.approx(0.0, abs=1e-14) and mean_ssim == pytest.approx(1.0, abs=1e-14)
+    assert np.abs(grad).max() < 1e-15
+
+
+def test_ssim_is_symmetric_and_bounded():
+    rng = np.random.default_rng(6)
+    x, y = rng.uniform(size=(3, 19, 21)), rng.uniform(size=(3, 19, 21))
+    a, b = oracle.ssim_map(x, y), oracle.ssim_map(y, x)
+    np.testing.assert_allclose(a, b, rtol=1e-13, atol=1e-15)
+    assert np.all(a <= 1.0 + 1e-12) and np.all(a >= -1.0 - 1e-12)
+
+
+def test_ssim_of_constant_images_has_the_closed_form():
+    """Constant a against constant b: away from the zero padding every window sees only a and
+    b, so the variances vanish and SSIM = (2ab + C1) / (a^2 + b^2 + C1)."""
+    a, b = 0.7, 0.3
+    x, y = np.full((1, 30, 30), a), np.full((1, 30, 30), b)
+    s = oracle.ssim_map(x, y)
+    c1 = 0.01 ** 2
+    assert s[0, 15, 15] == pytest.approx((2 * a * b + c1) / (a * a + b * b + c1), rel=1e-12)
+    assert s[0, 0, 0] != pytest.approx(s[0, 15, 15], rel=1e-6)  # the border sees the padding
+
+
+def test_l1_dssim_gradient_matches_finite_differences():
+    rng = np.random.default_rng(7)
+    x, y = rng.uniform(size=(3, 13, 16)), rng.uniform(size=(3, 13, 16))
+    _, grad, _ = oracle.l1_dssim_loss(x, y, lam=0.2)
+    h = 1e-6
+    for idx in [(0, 0, 0), (1, 6, 7), (2, 12, 15), (0, 3, 14), (1, 12, 0)]:
+        a, b = x.copy(), x.copy()
+        a[idx] += h
+        b[idx] -= h
+        fd = (oracle.l1_dssim_loss(a, y, 0.2)[0] - oracle.l1_dssim_loss(b, y, 0.2)[0]) / (2 * h)
+        assert grad[idx] == pytest.approx(fd, rel=1e-5, abs=1e-12)

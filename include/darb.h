@@ -239,6 +239,18 @@ darb_status darb_preprocess_bwd(const darb_splats *splats, const darb_camera *ca
 darb_status darb_l1_loss(const float *image, const float *target, int32_t width, int32_t height,
                          float *dL_dimage, float *loss, darb_stream stream);
 
+/* The full image loss of Sec. 4.2: L = (1 - lambda) L1 + lambda (1 - SSIM).  The paper takes
+ * both terms from 3DGS without printing lambda or the SSIM window; as there: SSIM per channel
+ * with an 11 x 11 Gaussian window (sigma 1.5, normalised) over zero-padded images,
+ * C1 = 0.01^2, C2 = 0.03^2 (intensities in [0, 1]), averaged over the 3 H W values; lambda 0.2
+ * in 3DGS.  image, target, dL_dimage: device [3][H][W].  loss: device float[2], overwritten
+ * with L and the mean SSIM.  workspace: device, darb_l1_dssim_workspace_size bytes (three
+ * derivative maps and two sums).  lambda in [0, 1]; lambda = 0 gives darb_l1_loss's gradient. */
+darb_status darb_l1_dssim_workspace_size(int32_t width, int32_t height, size_t *bytes);
+darb_status darb_l1_dssim_loss(const float *image, const float *target, int32_t width, int32_t height,
+                               float lambda, void *workspace, size_t workspace_bytes, float *dL_dimage,
+                               float *loss, darb_stream stream);
+
 /* Raw (optimised) parameters of a training run, device pointers, layouts as darb_splats
  * except log_scales = log(scales) and opacity_logits = logit(opacities).  scales and
  * opacities are the activated copies that darb_adam_step rewrites after the update. */

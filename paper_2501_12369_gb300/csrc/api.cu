@@ -182,6 +182,24 @@ darb_status darb_l1_loss(const float *image, const float *target, int32_t width,
     return DARB_OK;
 }
 
+darb_status darb_l1_dssim_workspace_size(int32_t width, int32_t height, size_t *bytes) {
+    if (width <= 0 || height <= 0 || width > 65536 || height > 65536 || !bytes) return DARB_ERR_INVALID_ARG;
+    *bytes = l1_dssim_workspace_bytes(width, height);
+    return DARB_OK;
+}
+
+darb_status darb_l1_dssim_loss(const float *image, const float *target, int32_t width, int32_t height, float lambda,
+                               void *workspace, size_t workspace_bytes, float *dL_dimage, float *loss,
+                               darb_stream stream) {
+    if (!image || !target || !dL_dimage || !loss || !workspace || width <= 0 || height <= 0 || width > 65536 ||
+        height > 65536 || !(lambda >= 0.0f && lambda <= 1.0f))
+        return DARB_ERR_INVALID_ARG;
+    if (workspace_bytes < l1_dssim_workspace_bytes(width, height)) return DARB_ERR_WORKSPACE;
+    DARB_CUDA_TRY(launch_l1_dssim(image, target, width, height, lambda, workspace, dL_dimage, loss,
+                                  reinterpret_cast<cudaStream_t>(stream)));
+    return DARB_OK;
+}
+
 darb_status darb_adam_step(const darb_train_params *params, const darb_splat_grads *grads,
                            const darb_adam_state *state, const darb_adam_config *cfg, darb_stream stream) {
     if (!params || !grads || !state || !cfg || params->n < 0 || params->sh_degree < 0 || params->sh_degree > 3 ||

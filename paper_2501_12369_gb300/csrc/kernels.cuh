@@ -53,6 +53,11 @@ struct BatchView {
 cudaError_t launch_render_fwd_batch(int kind, int tile, const BatchView *views, int n_views, int total_tiles,
                                     uint32_t *queue, float qmax, int strict, int max_ctas, cudaStream_t st);
 
+// ssim.cu: the L1 + D-SSIM image loss and its gradient.
+size_t l1_dssim_workspace_bytes(int W, int H);
+cudaError_t launch_l1_dssim(const float *image, const float *target, int W, int H, float lam, void *workspace,
+                            float *dL, float *loss, cudaStream_t st);
+
 // binning.cu
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;

@@ -1,0 +1,208 @@
+// The paper's image loss (Sec. 4.2): L = (1 - lambda) L1 + lambda (1 - SSIM), with the SSIM of
+// the 3DGS work it builds on -- per channel, an 11 x 11 Gaussian window (sigma 1.5, normalised)
+// over zero-padded images, C1 = 0.01^2, C2 = 0.03^2 -- averaged over channels and pixels.
+//
+// Two tiled kernels, each CTA one 32 x 32 output tile of one channel with a 5-pixel halo:
+//   k_ssim_fwd  stages x and y, blurs the five moments (x, y, x^2, y^2, xy) with separable
+//               passes in shared memory, and writes per pixel the partial derivatives of SSIM
+//               w.r.t. the local moments m_x, s_xx, s_xy, plus the block sums of SSIM and |x - y|;
+//   k_ssim_bwd  blurs those three maps (the window is symmetric, so the blur is its own adjoint)
+//               and forms dL/dx = (1 - lambda) sign(x - y) / N - lambda (G*d_m + 2x G*d_sxx +
+//               y G*d_sxy) / N, N = 3HW; its first CTA also writes the loss.
+// With A1 = 2 m_x m_y + C1, A2 = 2 (s_xy - m_x m_y) + C2, B1 = m_x^2 + m_y^2 + C1,
+// B2 = s_xx - m_x^2 + s_yy - m_y^2 + C2 and SSIM = A1 A2 / (B1 B2):
+//   d_m = 2 m_y (A2 - A1) / (B1 B2) - 2 m_x SSIM (1/B1 - 1/B2),  d_sxx = -SSIM / B2,
+//   d_sxy = 2 A1 / (B1 B2).
+#include "kernels.cuh"
+
+namespace darb {
+namespace {
+
+constexpr int kSsimR = 5;
+constexpr int kSsimTs = 32;
+constexpr int kSsimIn = kSsimTs + 2 * kSsimR;  // 42
+constexpr int kSsimThreads = 256;
+constexpr float kSsimC1 = 0.01f * 0.01f;
+constexpr float kSsimC2 = 0.03f * 0.03f;
+
+struct Window {
+    float g[2 * kSsimR + 1];
+};
+
+Window make_window() {
+    Window w;
+    double sum = 0.0, v[2 * kSsimR + 1];
+    for (int k = -kSsimR; k <= kSsimR; ++k) {
+        v[k + kSsimR] = std::exp(-(double)(k * k) / (2.0 * 1.5 * 1.5));
+        sum += v[k + kSsimR];
+    }
+    for (int k = 0; k <= 2 * kSsimR; ++k) w.g[k] = (float)(v[k] / sum);
+    return w;
+}
+
+__device__ __forceinline__ float block_sum(float v, float *s_w) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = v;
+    __syncthreads();
+    float t = 0.0f;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < kSsimThreads / 32; ++i) t += s_w[i];
+    return t;  // valid on thread 0
+}
+
+__global__ void __launch_bounds__(kSsimThreads)
+k_ssim_fwd(const float *__restrict__ x, const float *__restrict__ y, int W, int H, Window win,
+           float *__restrict__ d_m, float *__restrict__ d_sxx, float *__restrict__ d_sxy, double *__restrict__ sums) {
+    __shared__ float sx[kSsimIn][kSsimIn + 1], sy[kSsimIn][kSsimIn + 1];
+    __shared__ float h[5][kSsimIn][kSsimTs];
+    __shared__ float s_w[kSsimThreads / 32];
+    const int x0 = blockIdx.x * kSsimTs, y0 = blockIdx.y * kSsimTs;
+    const size_t plane = (size_t)W * H, off = (size_t)blockIdx.z * plane;
+    for (int i = threadIdx.x; i < kSsimIn * kSsimIn; i += kSsimThreads) {
+        const int r = i / kSsimIn, c = i - r * kSsimIn;
+        const int gy = y0 - kSsimR + r, gx = x0 - kSsimR + c;
+        const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
+        sx[r][c] = in ? x[off + (size_t)gy * W + gx] : 0.0f;
+        sy[r][c] = in ? y[off + (size_t)gy * W + gx] : 0.0f;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kSsimIn * kSsimTs; i += kSsimThreads) {  // along x
+        const int r = i / kSsimTs, c = i - r * kSsimTs;
+        float a = 0.f, b = 0.f, aa = 0.f, bb = 0.f, ab = 0.f;
+#pragma unroll
+        for (int k = 0; k <= 2 * kSsimR; ++k) {
+            const float g = win.g[k], u = sx[r][c + k], v = sy[r][c + k];
+            a = fmaf(g, u, a);
+            b = fmaf(g, v, b);
+            aa = fmaf(g, u * u, aa);
+            bb = fmaf(g, v * v, bb);
+            ab = fmaf(g, u * v, ab);
+        }
+        h[0][r][c] = a;
+        h[1][r][c] = b;
+        h[2][r][c] = aa;
+        h[3][r][c] = bb;
+        h[4][r][c] = ab;
+    }
+    __syncthreads();
+    float ssim_sum = 0.0f, l1_sum = 0.0f;
+    for (int i = threadIdx.x; i < kSsimTs * kSsimTs; i += kSsimThreads) {  // along y
+        const int r = i / kSsimTs, c = i - r * kSsimTs;
+        const int gy = y0 + r, gx = x0 + c;
+        if (gx >= W || gy >= H) continue;
+        float m[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int k = 0; k <= 2 * kSsimR; ++k) {
+            const float g = win.g[k];
+#pragma unroll
+            for (int q = 0; q < 5; ++q) m[q] = fmaf(g, h[q][r + k][c], m[q]);
+        }
+        const float mx = m[0], my = m[1];
+        const float A1 = 2.0f * mx * my + kSsimC1;
+        const float A2 = 2.0f * (m[4] - mx * my) + kSsimC2;
+        const float B1 = mx * mx + my * my + kSsimC1;
+        const float B2 = (m[2] - mx * mx) + (m[3] - my * my) + kSsimC2;
+        const float iB = 1.0f / (B1 * B2);
+        const float s = A1 * A2 * iB;
+        const size_t p = off + (size_t)gy * W + gx;
+        d_m[p] = 2.0f * my * (A2 - A1) * iB - 2.0f * mx * s * (1.0f / B1 - 1.0f / B2);
+        d_sxx[p] = -s / B2;
+        d_sxy[p] = 2.0f * A1 * iB;
+        ssim_sum += s;
+        l1_sum += fabsf(sx[r + kSsimR][c + kSsimR] - sy[r + kSsimR][c + kSsimR]);
+    }
+    const float ts = block_sum(ssim_sum, s_w);
+    __syncthreads();
+    const float tl = block_sum(l1_sum, s_w);
+    if (threadIdx.x == 0) {
+        atomicAdd(&sums[0], (double)ts);
+        atomicAdd(&sums[1], (double)tl);
+    }
+}
+
+__global__ void __launch_bounds__(kSsimThreads)
+k_ssim_bwd(const float *__restrict__ x, const float *__restrict__ y, int W, int H, Window win,
+           const float *__restrict__ d_m, const float *__restrict__ d_sxx, const float *__restrict__ d_sxy,
+           float lam, const double *__restrict__ sums, float *__restrict__ dL, float *__restrict__ loss) {
+    __shared__ float sa[3][kSsimIn][kSsimIn + 1];
+    __shared__ float h[3][kSsimIn][kSsimTs];
+    const int x0 = blockIdx.x * kSsimTs, y0 = blockIdx.y * kSsimTs;
+    const size_t plane = (size_t)W * H, off = (size_t)blockIdx.z * plane;
+    const double n = 3.0 * (double)plane;
+    const float inv_n = (float)(1.0 / n);
+    if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0) {
+        const double ssim = sums[0] / n, l1 = sums[1] / n;
+        loss[0] = (float)((1.0 - lam) * l1 + lam * (1.0 - ssim));
+        loss[1] = (float)ssim;
+    }
+    for (int i = threadIdx.x; i < kSsimIn * kSsimIn; i += kSsimThreads) {
+        const int r = i / kSsimIn, c = i - r * kSsimIn;
+        const int gy = y0 - kSsimR + r, gx = x0 - kSsimR + c;
+        const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
+        const size_t p = off + (size_t)gy * W + gx;
+        sa[0][r][c] = in ? d_m[p] : 0.0f;
+        sa[1][r][c] = in ? d_sxx[p] : 0.0f;
+        sa[2][r][c] = in ? d_sxy[p] : 0.0f;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kSsimIn * kSsimTs; i += kSsimThreads) {
+        const int r = i / kSsimTs, c = i - r * kSsimTs;
+        float a = 0.f, b = 0.f, e = 0.f;
+#pragma unroll
+        for (int k = 0; k <= 2 * kSsimR; ++k) {
+            const float g = win.g[k];
+            a = fmaf(g, sa[0][r][c + k], a);
+            b = fmaf(g, sa[1][r][c + k], b);
+            e = fmaf(g, sa[2][r][c + k], e);
+        }
+        h[0][r][c] = a;
+        h[1][r][c] = b;
+        h[2][r][c] = e;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kSsimTs * kSsimTs; i += kSsimThreads) {
+        const int r = i / kSsimTs, c = i - r * kSsimTs;
+        const int gy = y0 + r, gx = x0 + c;
+        if (gx >= W || gy >= H) continue;
+        float a = 0.f, b = 0.f, e = 0.f;
+#pragma unroll
+        for (int k = 0; k <= 2 * kSsimR; ++k) {
+            const float g = win.g[k];
+            a = fmaf(g, h[0][r + k][c], a);
+            b = fmaf(g, h[1][r + k][c], b);
+            e = fmaf(g, h[2][r + k][c], e);
+        }
+        const size_t p = off + (size_t)gy * W + gx;
+        const float xv = x[p], yv = y[p], d = xv - yv;
+        const float sgn = d > 0.0f ? 1.0f : (d < 0.0f ? -1.0f : 0.0f);
+        const float dssim = (a + 2.0f * xv * b + yv * e) * inv_n;
+        dL[p] = (1.0f - lam) * sgn * inv_n - lam * dssim;
+    }
+}
+
+}  // namespace
+
+size_t l1_dssim_workspace_bytes(int W, int H) {
+    const size_t maps = 3 * (size_t)3 * W * H * sizeof(float);
+    return 256 + ((maps + 255) & ~(size_t)255) + 256;
+}
+
+cudaError_t launch_l1_dssim(const float *image, const float *target, int W, int H, float lam, void *workspace,
+                            float *dL, float *loss, cudaStream_t st) {
+    unsigned char *w = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(workspace) + 255) &
+                                                         ~(uintptr_t)255);
+    double *sums = reinterpret_cast<double *>(w);
+    float *maps = reinterpret_cast<float *>(w + 256);
+    const size_t n = (size_t)3 * W * H;
+    cudaError_t e = cudaMemsetAsync(sums, 0, 2 * sizeof(double), st);
+    if (e != cudaSuccess) return e;
+    static const Window win = make_window();
+    const dim3 grid((W + kSsimTs - 1) / kSsimTs, (H + kSsimTs - 1) / kSsimTs, 3);
+    k_ssim_fwd<<<grid, kSsimThreads, 0, st>>>(image, target, W, H, win, maps, maps + n, maps + 2 * n, sums);
+    k_ssim_bwd<<<grid, kSsimThreads, 0, st>>>(image, target, W, H, win, maps, maps + n, maps + 2 * n, lam, sums, dL,
+                                              loss);
+    return cudaGetLastError();
+}
+
+}  // namespace darb

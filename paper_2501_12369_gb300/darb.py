@@ -117,6 +117,8 @@ SIGNATURES = {
     "darb_preprocess_bwd": (c_i32, [_P(darb_splats), _P(darb_camera), _P(darb_kernel_params), _P(darb_projected),
                                     c_vp, _P(darb_splat_grads), c_vp]),
     "darb_l1_loss": (c_i32, [c_vp, c_vp, c_i32, c_i32, c_vp, c_vp, c_vp]),
+    "darb_l1_dssim_workspace_size": (c_i32, [c_i32, c_i32, _P(ctypes.c_size_t)]),
+    "darb_l1_dssim_loss": (c_i32, [c_vp, c_vp, c_i32, c_i32, c_f32, c_vp, ctypes.c_size_t, c_vp, c_vp, c_vp]),
     "darb_adam_step": (c_i32, [_P(darb_train_params), _P(darb_splat_grads), _P(darb_adam_state),
                                _P(darb_adam_config), c_vp]),
     "darb_preprocess_bwd_adam": (c_i32, [_P(darb_train_params), _P(darb_camera), _P(darb_kernel_params),
@@ -438,6 +440,26 @@ def darb_preprocess_bwd_adam(params, cam, kparams, proj: Projected, grad2d: torc
     _check(lib().darb_preprocess_bwd_adam(ctypes.byref(p), ctypes.byref(c), ctypes.byref(kparams), ctypes.byref(pr),
                                           _p(grad2d), ctypes.byref(s), ctypes.byref(cfg), _stream(stream)),
            "darb_preprocess_bwd_adam")
+
+
+def darb_l1_dssim_workspace_size(width, height) -> int:
+    n = ctypes.c_size_t(0)
+    _check(lib().darb_l1_dssim_workspace_size(int(width), int(height), ctypes.byref(n)),
+           "darb_l1_dssim_workspace_size")
+    return int(n.value)
+
+
+def darb_l1_dssim_loss(image, target, lam=0.2, workspace=None, dL_dimage=None, loss=None, stream=None):
+    """(1 - lam) L1 + lam (1 - SSIM) of [3, H, W] images; returns (dL_dimage, loss[2] = (L, mean SSIM))."""
+    H, W = image.shape[-2:]
+    if workspace is None:
+        workspace = torch.empty(darb_l1_dssim_workspace_size(W, H), dtype=torch.uint8, device=image.device)
+    dL_dimage = torch.empty_like(image) if dL_dimage is None else dL_dimage
+    loss = torch.empty(2, dtype=torch.float32, device=image.device) if loss is None else loss
+    _check(lib().darb_l1_dssim_loss(_p(image), _p(target), int(W), int(H), float(lam), _p(workspace),
+                                    workspace.numel() * workspace.element_size(), _p(dL_dimage), _p(loss),
+                                    _stream(stream)), "darb_l1_dssim_loss")
+    return dL_dimage, loss
 
 
 def darb_adam_step(params, grads: SplatGrads, state, cfg: darb_adam_config, stream=None):

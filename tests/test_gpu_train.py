@@ -213,3 +213,66 @@ def test_fused_backward_adam_argument_checks():
         darb.darb_preprocess_bwd_adam(p, cam, r.kparams, proj, g2.reshape(-1)[1:], st, _cfg(1))  # off 16 B
     with pytest.raises(darb.DarbError):
         darb.darb_preprocess_bwd_adam(p, cam, r.kparams, proj, g2, st, _cfg(0))  # steps count from 1
+
+
+# --------------------------------------------------------------------------- L1 + D-SSIM term
+
+@pytest.mark.parametrize("W,H", [(333, 207), (64, 64), (17, 23), (1, 1)])
+def test_l1_dssim_matches_oracle(W, H):
+    rng = np.random.default_rng(W + 3 * H)
+    img = rng.uniform(0, 1, (3, H, W)).astype(np.float32)
+    tgt = np.clip(img + rng.normal(0, 0.2, img.shape), 0, 1).astype(np.float32)  # correlated, like a render
+    tgt.reshape(-1)[::7] = img.reshape(-1)[::7]
+    dL, loss = darb.darb_l1_dssim_loss(torch.from_numpy(img).cuda(), torch.from_numpy(tgt).cuda(), 0.2)
+    torch.cuda.synchronize()
+    ref_loss, ref_grad, ref_ssim = oracle.l1_dssim_loss(img, tgt, 0.2)
+    got = to_np(loss)
+    assert abs(got[0] - ref_loss) <= 2e-6 * max(1.0, abs(ref_loss))
+    assert abs(got[1] - ref_ssim) <= 2e-6
+    g = to_np(dL).astype(np.float64)
+    np.testing.assert_allclose(g, ref_grad, rtol=1e-3, atol=1e-4 * np.abs(ref_grad).max())
+
+
+def test_l1_dssim_special_cases():
+    rng = np.random.default_rng(3)
+    img = torch.from_numpy(rng.uniform(0, 1, (3, 40, 50)).astype(np.float32)).cuda()
+    tgt = torch.from_numpy(rng.uniform(0, 1, (3, 40, 50)).astype(np.float32)).cuda()
+    # lambda = 0 is the L1 term alone
+    dL0, loss0 = darb.darb_l1_dssim_loss(img, tgt, 0.0)
+    dl1, l1 = darb.darb_l1_loss(img, tgt)
+    torch.cuda.synchronize()
+    assert torch.equal(dL0, dl1)
+    assert float(loss0[0]) == pytest.approx(float(l1[0]), rel=1e-6)
+    # an image against itself: D-SSIM 0, SSIM 1, gradient 0
+    dLs, losss = darb.darb_l1_dssim_loss(img, img, 1.0)
+    torch.cuda.synchronize()
+    assert float(losss[1]) == pytest.approx(1.0, abs=1e-6) and abs(float(losss[0])) < 1e-6
+    assert float(dLs.abs().max()) < 1e-9
+    with pytest.raises(darb.DarbError):
+        darb.darb_l1_dssim_loss(img, tgt, 1.5)
+    small = torch.empty(100, dtype=torch.uint8, device="cuda")
+    with pytest.raises(darb.DarbError) as e:
+        darb.darb_l1_dssim_loss(img, tgt, 0.2, workspace=small)
+    assert e.value.status == 2
+
+
+def test_l1_dssim_full_hd_crops():
+    """1920 x 1080, the training resolution: gradients of three 96 x 96 windows against the
+    oracle on the same window plus a 10-pixel margin (the gradient at a pixel depends on the
+    image within 2 x 5 pixels, so the window's inner pixels are exact)."""
+    rng = np.random.default_rng(11)
+    H, W = 1080, 1920
+    img = rng.uniform(0, 1, (3, H, W)).astype(np.float32)
+    tgt = np.clip(img + rng.normal(0, 0.1, img.shape), 0, 1).astype(np.float32)
+    dL, loss = darb.darb_l1_dssim_loss(torch.from_numpy(img).cuda(), torch.from_numpy(tgt).cuda(), 0.2)
+    torch.cuda.synchronize()
+    g = to_np(dL).astype(np.float64)
+    n_full, m = 3 * H * W, 10
+    for (y0, x0) in [(0, 0), (H - 96, W - 96), (500, 900)]:
+        ya, xa = max(0, y0 - m), max(0, x0 - m)
+        yb, xb = min(H, y0 + 96 + m), min(W, x0 + 96 + m)
+        _, ref, _ = oracle.l1_dssim_loss(img[:, ya:yb, xa:xb], tgt[:, ya:yb, xa:xb], 0.2)
+        ref = ref * (ref.size / n_full)  # the oracle normalised by the window's size
+        sl = (slice(None), slice(y0 - ya, y0 - ya + 96), slice(x0 - xa, x0 - xa + 96))
+        got = g[:, y0:y0 + 96, x0:x0 + 96]
+        np.testing.assert_allclose(got, ref[sl], rtol=1e-3, atol=1e-4 * np.abs(ref[sl]).max())

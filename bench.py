@@ -513,6 +513,14 @@ def run_ours(args):
     achieved = ab / (stage_ms[rl_stage] / 1e3) / 1e9
     stage_frac = {st: round(ab_of(st) / (stage_ms[st] / 1e3) / 1e9 / peak_gbs, 4)
                   for st in single + ["bin_sort"] if ab_of(st)}
+    # the same stages against the survey's per-unit byte figures (what the standard 3DGS design
+    # moves: 64-bit keys over p = ceil((32 + log2 tiles) / 8) passes, gradients through HBM)
+    p64 = (32 + tile_bits + 7) // 8
+    contract = {"preprocess": ts.n * 288, "bin_sort": ts.n * 24 + M_mean * (12 + 8 + 24 * p64),
+                "preprocess_bwd": ts.n * 500, "adam": ts.n * 28 * (11 + 3 * sh_k),
+                "preprocess_bwd_adam": ts.n * (500 + 28 * (11 + 3 * sh_k))}
+    stage_frac_contract = {st: round(contract[st] / (stage_ms[st] / 1e3) / 1e9 / peak_gbs, 4)
+                           for st in contract if st in stage_ms}
     traffic = None
     if rl_stage == "preprocess_bwd_adam" and splats.sh_degree == 3:
         # ncu dram__bytes_read.sum + dram__bytes_write.sum of k_preprocess_bwd_adam<3> on the
@@ -533,6 +541,7 @@ def run_ours(args):
         "stage_ms": {s: round(v, 4) for s, v in stage_ms.items()},
         "dominant_stage": dominant,
         "stage_hbm_frac": stage_frac,
+        "stage_hbm_frac_per_unit_figures": stage_frac_contract,
         "roofline": {"bound": "hbm", "kernel": rl_stage, "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
                      "frac": achieved / peak_gbs, "traffic": traffic,
                      "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback 6.8 TB/s",

@@ -62,7 +62,8 @@ class OrcCamera(ctypes.Structure):
 
 class OrcKernel(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("psi", ctypes.c_float), ("q_max", ctypes.c_float),
-                ("q_max_strict", ctypes.c_int)]
+                ("q_max_strict", ctypes.c_int), ("base", ctypes.c_int), ("xi", ctypes.c_float),
+                ("beta", ctypes.c_float), ("lobes", ctypes.c_int)]
 
 
 class OrcOutcome(ctypes.Structure):
@@ -125,6 +126,48 @@ def kernel_params(name_or_kind, psi=None):
     return OrcKernel(kind, float(p if psi is None else psi), float(qmax), int(strict))
 
 
+# Table 1's "modified" family (kind 7): F = base(u), u = d_M^beta / xi, each base on the
+# domain that keeps `lobes` lobes (one lobe: the strictly decaying main lobe).
+GENERIC = 7
+GENERIC_BASES = ("gaussian", "half_cosine", "raised_cosine", "mod_sinc", "inv_multiquadric", "parabola")
+
+
+def generic_u_max(base, lobes=1):
+    """End of the domain in u (Table 1's limits), inf for the unbounded members."""
+    b = GENERIC_BASES.index(base) if isinstance(base, str) else int(base)
+    return {0: np.inf, 1: np.pi / 2, 2: lobes * np.pi, 3: (lobes + 1) * np.pi / 2, 4: np.inf, 5: 1.0}[b]
+
+
+def generic_kernel(base, xi, beta, lobes=1, psi=None):
+    """Kernel parameters of a modified member.  q_max = min(9, (xi u_max)^(2/beta)): the tile
+    rectangle's radius 3 sqrt(lambda_max) bounds every footprint at q = 9.  psi defaults to the
+    moment integral (psi_moment)."""
+    b = GENERIC_BASES.index(base) if isinstance(base, str) else int(base)
+    q_dom = (xi * generic_u_max(b, lobes)) ** (2.0 / beta)
+    k = OrcKernel(GENERIC, 1.0, float(min(9.0, q_dom)), 0, b, float(xi), float(beta), int(lobes))
+    k.psi = float(psi_moment(k) if psi is None else psi)
+    return k
+
+
+def psi_moment(kp):
+    """psi = per-axis second moment of the truncated 3D kernel with Sigma = I (the quantity the
+    Sec. A.2 grid experiment measures): (1/3) int r^4 F(r^2) dr / int r^2 F(r^2) dr over
+    r in [0, sqrt(q_max)], by adaptive quadrature (breaks at the lobe ends)."""
+    from scipy import integrate
+    rmax = float(np.sqrt(kp.q_max))
+
+    def f(r):
+        return kernel_eval(kp, np.array([r * r]))[0][0]
+
+    pts = None
+    if kp.kind == GENERIC and kp.base in (2, 3):
+        ends = [(kp.xi * m * np.pi / 2) ** (1.0 / kp.beta) for m in range(1, 2 * kp.lobes + 2)]
+        pts = [e for e in ends if 0 < e < rmax] or None
+    num = integrate.quad(lambda r: r ** 4 * f(r), 0.0, rmax, points=pts, limit=400, epsabs=0, epsrel=1e-12)[0]
+    den = integrate.quad(lambda r: r ** 2 * f(r), 0.0, rmax, points=pts, limit=400, epsabs=0, epsrel=1e-12)[0]
+    return num / (3.0 * den)
+
+
 def camera_struct(cam) -> OrcCamera:
     c = OrcCamera()
     c.viewmat[:] = [float(v) for v in np.asarray(cam.viewmat, np.float32).reshape(16)]
@@ -139,10 +182,14 @@ def tiles_xy(cam, tile):
 
 
 def kernel_eval(kind, q):
+    """F(q) and dF/dq: kind is a kernel enum, or kernel parameters (the generic family too)."""
     q = np.ascontiguousarray(q, np.float64)
     F = np.empty_like(q)
     dF = np.empty_like(q)
-    lib().orc_kernel_eval(ctypes.c_int(kind), ctypes.c_int(q.size), _p(q), _p(F), _p(dF))
+    if isinstance(kind, OrcKernel):
+        lib().orc_kernel_eval_k(ctypes.byref(kind), ctypes.c_int(q.size), _p(q), _p(F), _p(dF))
+    else:
+        lib().orc_kernel_eval(ctypes.c_int(kind), ctypes.c_int(q.size), _p(q), _p(F), _p(dF))
     return F, dF
 
 

@@ -54,6 +54,10 @@ typedef struct {
     float psi;
     float q_max;
     int q_max_strict;
+    /* kind K_GENERIC only: Table 1's "modified" family F = base(u), u = d_M^beta / xi */
+    int base;
+    float xi, beta;
+    int lobes;
 } orc_kernel;
 
 typedef struct {
@@ -69,7 +73,7 @@ typedef struct {
 } orc_outcome;
 
 enum { K_GAUSSIAN = 0, K_HALF_COSINE, K_RAISED_COSINE, K_MOD_SINC, K_INV_QUADRIC,
-       K_INV_MULTIQUADRIC, K_PARABOLA, K_COUNT };
+       K_INV_MULTIQUADRIC, K_PARABOLA, K_GENERIC, K_COUNT };
 
 /* 3DGS compositing constants, as FP32 literals. */
 #define ALPHA_MAX ((double)0.99f)
@@ -118,6 +122,58 @@ enum { K_GAUSSIAN = 0, K_HALF_COSINE, K_RAISED_COSINE, K_MOD_SINC, K_INV_QUADRIC
 /* ------------------------------------------------------------------------ */
 /* Kernel profiles F(q), q = d_M^2 (Table 1 with the xi of Table 2, read in */
 /* the forms the Sec. B listings evaluate).                                 */
+
+/* Table 1's modified members, F = base(u) with u = d_M^beta / xi = q^(beta/2) / xi:
+ * base 0 exp(-u), 1 cos(u), 2 1/2 + 1/2 cos(u), 3 |sin u| / u, 4 (u + 1)^(-1/2), 5 1 - u. */
+static double generic_u(const orc_kernel *k, double q)
+{
+    if (q <= 0.0) return 0.0;
+    return pow(q, 0.5 * (double)k->beta) / (double)k->xi;
+}
+
+static double generic_base(int base, double u)
+{
+    switch (base) {
+    case 0: return exp(-u);
+    case 1: return cos(u);
+    case 2: return 0.5 + 0.5 * cos(u);
+    case 3: return u == 0.0 ? 1.0 : fabs(sin(u)) / u;
+    case 4: return 1.0 / sqrt(u + 1.0);
+    case 5: return 1.0 - u;
+    }
+    return 0.0;
+}
+
+static double generic_base_du(int base, double u)
+{
+    switch (base) {
+    case 0: return -exp(-u);
+    case 1: return -sin(u);
+    case 2: return -0.5 * sin(u);
+    case 3: {
+        if (u < 1e-3) return -u / 3.0 + u * u * u / 30.0; /* series of (u cos u - sin u) / u^2 */
+        const double sg = sin(u) < 0.0 ? -1.0 : 1.0;
+        return sg * (u * cos(u) - sin(u)) / (u * u);
+    }
+    case 4: return -0.5 * pow(u + 1.0, -1.5);
+    case 5: return -1.0;
+    }
+    return 0.0;
+}
+
+/* dF/dq = dF/du (beta/2) u / q; at q = 0 the one-sided limit is evaluated at q = 1e-24 (finite
+ * for beta = 2; for beta < 2 it diverges unless dF/du vanishes at u = 0). */
+static double generic_dq(const orc_kernel *k, double q)
+{
+    const double hb = 0.5 * (double)k->beta;
+    if (hb == 1.0) return generic_base_du(k->base, q / (double)k->xi) / (double)k->xi;
+    const double qq = q > 1e-24 ? q : 1e-24;
+    const double u = pow(qq, hb) / (double)k->xi;
+    return generic_base_du(k->base, u) * hb * u / qq;
+}
+
+static double F_value_k(const orc_kernel *k, double q);
+static double F_deriv_k(const orc_kernel *k, double q);
 
 static double F_value(int kind, double q)
 {
@@ -176,11 +232,30 @@ static double F_deriv(int kind, double q)
     return 0.0;
 }
 
+static double F_value_k(const orc_kernel *k, double q)
+{
+    return k->kind == K_GENERIC ? generic_base(k->base, generic_u(k, q)) : F_value(k->kind, q);
+}
+
+static double F_deriv_k(const orc_kernel *k, double q)
+{
+    return k->kind == K_GENERIC ? generic_dq(k, q) : F_deriv(k->kind, q);
+}
+
 void orc_kernel_eval(int kind, int n, const double *q, double *F, double *dF)
 {
     for (int i = 0; i < n; ++i) {
         if (F) F[i] = F_value(kind, q[i]);
         if (dF) dF[i] = F_deriv(kind, q[i]);
+    }
+}
+
+/* F and dF/dq of any kernel, the generic family included. */
+void orc_kernel_eval_k(const orc_kernel *k, int n, const double *q, double *F, double *dF)
+{
+    for (int i = 0; i < n; ++i) {
+        if (F) F[i] = F_value_k(k, q[i]);
+        if (dF) dF[i] = F_deriv_k(k, q[i]);
     }
 }
 
@@ -391,6 +466,7 @@ typedef struct {
     const float *opac;
     int geom32, kind, strict;
     float qmax;
+    orc_kernel kp;
     const int *seq;
     int len;
     int tx, ty;
@@ -431,7 +507,7 @@ static int eval_alpha(const walk_ctx *c, int id, double *alpha, double *F, doubl
         qq = fma(dx, fma(A, dx, (2.0 * B) * dy), (C * dy) * dy);
         if (qq < 0.0 || (c->strict ? qq >= (double)c->qmax : qq > (double)c->qmax)) return 0;
     }
-    const double Fv = F_value(c->kind, qq);
+    const double Fv = F_value_k(&c->kp, qq);
     double a = (double)c->opac[id] * Fv;
     if (a > ALPHA_MAX) a = ALPHA_MAX;
     *alpha = a;
@@ -526,6 +602,7 @@ static void init_ctx(walk_ctx *c, const int *rect, const double *mean2d, const d
     c->rgb = rgb;
     c->geom32 = geom32;
     c->kind = k->kind;
+    c->kp = *k;
     c->qmax = k->q_max;
     c->strict = k->q_max_strict;
     for (int ch = 0; ch < 3; ++ch) c->bg[ch] = cam->bg[ch];
@@ -716,7 +793,7 @@ int orc_render_backward(int n, const int *rect, const double *mean2d, const doub
                         const double o = (double)opac[id];
                         if (o * F > ALPHA_MAX) continue; /* clamped: alpha is constant */
                         out[5] += F * dalpha;
-                        const double dq = o * F_deriv(k->kind, q) * dalpha;
+                        const double dq = o * F_deriv_k(k, q) * dalpha;
                         const double dx = mean2d[2 * (size_t)id] - (double)c.px;
                         const double dy = mean2d[2 * (size_t)id + 1] - (double)c.py;
                         const double A = conic[3 * (size_t)id], B = conic[3 * (size_t)id + 1],

@@ -579,3 +579,93 @@ def test_l1_dssim_gradient_matches_finite_differences():
         b[idx] -= h
         fd = (oracle.l1_dssim_loss(a, y, 0.2)[0] - oracle.l1_dssim_loss(b, y, 0.2)[0]) / (2 * h)
         assert grad[idx] == pytest.approx(fd, rel=1e-5, abs=1e-12)
+
+
+# --------------------------------------------------------------------------- modified members (Table 1)
+
+# The fixed kernels as members of Table 1's modified family: (base, xi, beta)
+_AS_GENERIC = {"gaussian": ("gaussian", 2.0, 2.0), "half_cosine": ("half_cosine", 18 / math.pi, 2.0),
+               "raised_cosine": ("raised_cosine", 2.5 / math.pi, 1.0), "mod_sinc": ("mod_sinc", 3 / math.pi, 1.0),
+               "inv_multiquadric": ("inv_multiquadric", 1.0, 2.0), "parabola": ("parabola", 9.0, 2.0)}
+
+
+@pytest.mark.parametrize("name", list(_AS_GENERIC))
+def test_generic_family_reproduces_the_fixed_kernels(name):
+    base, xi, beta = _AS_GENERIC[name]
+    kg = oracle.generic_kernel(base, xi, beta, lobes=1)
+    kind, psi, qmax, strict = oracle.KERNELS[name]
+    assert kg.q_max == pytest.approx(qmax, rel=1e-6)
+    q = np.linspace(0.0, qmax * (1 - 1e-6), 301)[1:]  # the lobe end is a one-sided kink
+    Fg, dFg = oracle.kernel_eval(kg, q)
+    Ff, dFf = _F(name, q)
+    # xi is a float32 parameter (as the GPU receives it): 18/pi, 2.5/pi, 3/pi round at 6e-8
+    np.testing.assert_allclose(Fg, Ff, rtol=3e-7, atol=2e-7)
+    np.testing.assert_allclose(dFg, dFf, rtol=3e-7, atol=2e-7)
+    # psi of the generic member = the moment integral of the fixed kernel on its support
+    if name != "gaussian":
+        assert kg.psi == pytest.approx(_moment_psi(name, qmax), rel=1e-6)
+
+
+def test_generic_psi_has_the_closed_form():
+    """Modified half-cosine with xi = 1, beta = 1: F = cos(d) on d <= pi/2, so psi is
+    (1/3) int r^4 cos r / int r^2 cos r over [0, pi/2], evaluated symbolically."""
+    import sympy as sp
+    r = sp.symbols("r")
+    exact = sp.integrate(r ** 4 * sp.cos(r), (r, 0, sp.pi / 2)) / (3 * sp.integrate(r ** 2 * sp.cos(r), (r, 0, sp.pi / 2)))
+    kg = oracle.generic_kernel("half_cosine", 1.0, 1.0)
+    assert kg.q_max == pytest.approx((math.pi / 2) ** 2, rel=1e-7)
+    assert kg.psi == pytest.approx(float(exact), rel=1e-6)  # float32 field
+
+
+@pytest.mark.parametrize("member", [("half_cosine", 3.0, 1.5, 1), ("raised_cosine", 1.2, 2.0, 1),
+                                    ("mod_sinc", 1.1, 1.5, 2), ("gaussian", 1.0, 2.5, 1)])
+def test_generic_derivative_matches_central_differences(member):
+    base, xi, beta, lobes = member
+    kg = oracle.generic_kernel(base, xi, beta, lobes)
+    q = np.linspace(0.05, kg.q_max * 0.98, 97)
+    h = 1e-6
+    F, dF = oracle.kernel_eval(kg, q)
+    fd = (oracle.kernel_eval(kg, q + h)[0] - oracle.kernel_eval(kg, q - h)[0]) / (2 * h)
+    mask = np.ones_like(q, bool)
+    if base == "mod_sinc":  # |sin u| has a kink at u = pi
+        u = q ** (beta / 2) / xi
+        mask = np.abs(u - math.pi) > 1e-3
+    np.testing.assert_allclose(dF[mask], fd[mask], rtol=1e-6, atol=1e-8)
+    assert np.all(F >= -1e-15) and F[0] <= 1.0
+
+
+def test_generic_member_renders_tiled_as_brute_force_with_a_checked_gradient():
+    kg = oracle.generic_kernel("half_cosine", 3.0, 1.5)
+    s = synth.uniform_cube_scene(64, seed=4, sh_degree=1)
+    cam = synth.pinhole((0.3, -0.2, 3.0), 60, 44, 50.0, bg=(0.1, 0.0, 0.2))
+    a = oracle.forward(s, cam, kg, tile=8, mode="tiled")
+    b = oracle.forward(s, cam, kg, tile=8, mode="brute")
+    assert np.array_equal(a["image"], b["image"]) and np.array_equal(a["sig"], b["sig"])
+    s, cam = _fd_scene()
+    dL = synth.random_image_grad(cam.height, cam.width, seed=7)
+    fwd, g2, gp = oracle.gradients(s, cam, dL, kg, tile=8, geom32=False)
+    rng = np.random.default_rng(17)
+    checked = 0
+    for trial in range(30):
+        field = ("means", "scales", "opacities")[trial % 3]
+        arr = getattr(s, field)
+        idx = tuple(int(rng.integers(d)) for d in arr.shape)
+        if fwd["proj"]["culled"][idx[0]]:
+            continue
+        x0 = float(arr[idx])
+        h = 1e-4 if field == "opacities" else 1e-3 * max(1.0, abs(x0))
+        vals, steps, ok = [], [], True
+        for sgn in (1, -1):
+            s2 = dataclasses.replace(s, **{field: arr.copy()})
+            getattr(s2, field)[idx] = np.float32(x0 + sgn * h)
+            steps.append(float(getattr(s2, field)[idx]) - x0)
+            f = oracle.forward(s2, cam, kg, tile=8, geom32=False)
+            ok &= np.array_equal(f["sig"], fwd["sig"])
+            vals.append((f["image"] * dL).sum())
+        if not ok:
+            continue
+        fd = (vals[0] - vals[1]) / (steps[0] - steps[1])
+        an = gp[field][idx]
+        assert abs(fd - an) <= 2e-3 * max(abs(fd), abs(an), 1e-2), (field, idx, fd, an)
+        checked += 1
+    assert checked >= 12

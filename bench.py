@@ -603,7 +603,11 @@ def kernel_sweep(ts, step, cam_seq, first, stages, restore_kernel, steps=20):
     autotuned one; capacity is re-sized, since psi changes the footprints)."""
     from paper_2501_12369_gb300 import darb
     out = {}
-    for k in darb.KERNEL_NAMES:
+    t0 = time.perf_counter()
+    generic = darb.darb_kernel_generic("half_cosine", 3.0, 1.5, 1)  # psi by the device moment integral
+    psi_ms = (time.perf_counter() - t0) * 1e3
+    members = [(k, k) for k in darb.KERNEL_NAMES] + [("generic_half_cosine_xi3_beta1.5", generic)]
+    for label, k in members:
         ts.set_kernel(k)
         Ms = ts.size_capacity(cam_seq[:16])
         for i in range(3):
@@ -615,8 +619,10 @@ def kernel_sweep(ts, step, cam_seq, first, stages, restore_kernel, steps=20):
         torch.cuda.synchronize()
         per = {s: sum(e[i].elapsed_time(e[i + 1]) for e in evs) / steps for i, s in enumerate(stages)}
         total = evs[0][0].elapsed_time(evs[-1][-1])
-        out[k] = {"it_s": round(steps / (total / 1e3), 1), "mean_instances": int(np.mean(Ms)),
-                  "stage_ms": {s: round(v, 4) for s, v in per.items()}}
+        out[label] = {"it_s": round(steps / (total / 1e3), 1), "mean_instances": int(np.mean(Ms)),
+                      "stage_ms": {s: round(v, 4) for s, v in per.items()}}
+    out["generic_half_cosine_xi3_beta1.5"]["psi"] = generic.psi
+    out["generic_half_cosine_xi3_beta1.5"]["psi_device_ms"] = round(psi_ms, 3)
     ts.set_kernel(restore_kernel)
     return out
 

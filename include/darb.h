@@ -57,18 +57,48 @@ typedef enum {
     DARB_MOD_SINC = 3,
     DARB_INV_QUADRIC = 4,
     DARB_INV_MULTIQUADRIC = 5,
-    DARB_PARABOLA = 6
+    DARB_PARABOLA = 6,
+    DARB_GENERIC = 7 /* Table 1's modified family, described by base, xi, beta, lobes below */
 } darb_kernel;
+
+/* Bases of the generic member, F = base(u) with u = d_M^beta / xi (Table 1). */
+typedef enum {
+    DARB_BASE_GAUSSIAN = 0,         /* exp(-u)                               d_M >= 0          */
+    DARB_BASE_HALF_COSINE = 1,      /* cos(u)                                u <= pi / 2       */
+    DARB_BASE_RAISED_COSINE = 2,    /* 1/2 + 1/2 cos(u)                      u <= n pi         */
+    DARB_BASE_MOD_SINC = 3,         /* |sin u| / u                           u <= (n + 1) pi / 2 */
+    DARB_BASE_INV_MULTIQUADRIC = 4, /* (u + 1)^(-1/2)                        d_M >= 0          */
+    DARB_BASE_PARABOLA = 5          /* 1 - u                                 u <= 1            */
+} darb_kernel_base;
 
 /* kind: a darb_kernel.  psi: correction factor multiplying the 2x2 EWA block (Eq.
  * 2x2covProjection, Table 2).  q_max: main-lobe limit on q (Sec. A.3); a pixel is
- * skipped when q > q_max, or q >= q_max when q_max_strict is non-zero. */
+ * skipped when q > q_max, or q >= q_max when q_max_strict is non-zero.
+ * base, xi, beta, lobes: the member of Table 1's family; they define F for DARB_GENERIC and
+ * describe the fixed kinds (darb_kernel_defaults fills them; ignored there). */
 typedef struct {
     int32_t kind;
     float psi;
     float q_max;
     int32_t q_max_strict;
+    int32_t base; /* a darb_kernel_base */
+    float xi;     /* > 0 */
+    float beta;   /* 0.5 .. 4 */
+    int32_t lobes; /* n >= 1: lobes kept by the raised cosine and the modular sinc */
 } darb_kernel_params;
+
+/* Parameters of the generic member (base, xi, beta, lobes): q_max = min(9, (xi u_max)^(2/beta))
+ * with u_max the domain end of Table 1 (9 for the unbounded bases) -- the tile rectangle's
+ * radius 3 sqrt(lambda_max) bounds every footprint at q = 9 (Sec. 4.1).  psi is left 1: set it
+ * with darb_kernel_psi or by hand. */
+darb_status darb_kernel_generic(int32_t base, float xi, float beta, int32_t lobes, darb_kernel_params *out);
+
+/* psi of any kernel by the moment integral on the device: the per-axis second moment of the
+ * truncated 3D kernel with Sigma = I, (1/3) int r^4 F(r^2) dr / int r^2 F(r^2) dr over
+ * [0, sqrt(q_max)] -- the quantity the Sec. A.2 grid experiment measures (and, for the fixed
+ * kernels, the printed psi to its precision).  Midpoint rule over 2^22 radii in FP64.
+ * scratch: device double[2].  Synchronises `stream`; *psi receives the value. */
+darb_status darb_kernel_psi(const darb_kernel_params *kparams, double *scratch, double *psi, darb_stream stream);
 
 typedef struct {
     float viewmat[16]; /* world -> camera, row-major [R t; 0 0 0 1] */

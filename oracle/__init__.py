@@ -143,8 +143,9 @@ def generic_kernel(base, xi, beta, lobes=1, psi=None):
     rectangle's radius 3 sqrt(lambda_max) bounds every footprint at q = 9.  psi defaults to the
     moment integral (psi_moment)."""
     b = GENERIC_BASES.index(base) if isinstance(base, str) else int(base)
-    q_dom = (xi * generic_u_max(b, lobes)) ** (2.0 / beta)
-    k = OrcKernel(GENERIC, 1.0, float(min(9.0, q_dom)), 0, b, float(xi), float(beta), int(lobes))
+    xi32, beta32 = float(np.float32(xi)), float(np.float32(beta))  # the parameters as stored
+    q_dom = (xi32 * generic_u_max(b, lobes)) ** (2.0 / beta32)
+    k = OrcKernel(GENERIC, 1.0, float(min(9.0, q_dom)), 0, b, xi32, beta32, int(lobes))
     k.psi = float(psi_moment(k) if psi is None else psi)
     return k
 

@@ -1,5 +1,7 @@
 // The C ABI of libdarb.so (declared in include/darb.h): argument validation, workspace
 // carving and kernel launches.  No entry point here allocates device memory.
+#include <algorithm>
+
 #include "validate.h"
 
 using namespace darb;
@@ -58,14 +60,51 @@ const char *darb_status_string(darb_status s) {
 darb_status darb_kernel_defaults(int32_t kind, darb_kernel_params *out) {
     // psi: Sec. B listings ("correctionFactor"), Table 2 for the inverse multiquadric and the
     // Gaussian; q_max / strictness: the listings' main-lobe limits.
-    static const darb_kernel_params table[kNumKernels] = {
-        {DARB_GAUSSIAN, 1.0f, 9.0f, 0},     {DARB_HALF_COSINE, 1.36f, 9.0f, 0},
-        {DARB_RAISED_COSINE, 0.655f, 6.25f, 0}, {DARB_MOD_SINC, 1.18f, 9.0f, 0},
-        {DARB_INV_QUADRIC, 1.38f, 9.0f, 1}, {DARB_INV_MULTIQUADRIC, 1.61f, 9.0f, 1},
-        {DARB_PARABOLA, 1.3f, 9.0f, 0},
+    // base / xi / beta / lobes: the kernel as a member of Table 1's family (descriptive; the
+    // inverse quadric 1 / (1 + q) of the Sec. B.4 listing is none, base -1).
+    static const darb_kernel_params table[kNumKernels - 1] = {
+        {DARB_GAUSSIAN, 1.0f, 9.0f, 0, DARB_BASE_GAUSSIAN, 2.0f, 2.0f, 1},
+        {DARB_HALF_COSINE, 1.36f, 9.0f, 0, DARB_BASE_HALF_COSINE, (float)(18.0 / kPiD), 2.0f, 1},
+        {DARB_RAISED_COSINE, 0.655f, 6.25f, 0, DARB_BASE_RAISED_COSINE, (float)(2.5 / kPiD), 1.0f, 1},
+        {DARB_MOD_SINC, 1.18f, 9.0f, 0, DARB_BASE_MOD_SINC, (float)(3.0 / kPiD), 1.0f, 1},
+        {DARB_INV_QUADRIC, 1.38f, 9.0f, 1, -1, 1.0f, 2.0f, 1},
+        {DARB_INV_MULTIQUADRIC, 1.61f, 9.0f, 1, DARB_BASE_INV_MULTIQUADRIC, 1.0f, 2.0f, 1},
+        {DARB_PARABOLA, 1.3f, 9.0f, 0, DARB_BASE_PARABOLA, 9.0f, 2.0f, 1},
     };
-    if (!out || kind < 0 || kind >= kNumKernels) return DARB_ERR_INVALID_ARG;
+    if (!out || kind < 0 || kind >= kNumKernels - 1) return DARB_ERR_INVALID_ARG;  // DARB_GENERIC: darb_kernel_generic
     *out = table[kind];
+    return DARB_OK;
+}
+
+darb_status darb_kernel_generic(int32_t base, float xi, float beta, int32_t lobes, darb_kernel_params *out) {
+    if (!out || base < 0 || base > 5 || !(xi > 0.0f) || !std::isfinite(xi) || !(beta >= 0.5f && beta <= 4.0f) ||
+        lobes < 1 || lobes > 64)
+        return DARB_ERR_INVALID_ARG;
+    const double pi = kPiD;
+    const double u_max[6] = {INFINITY, pi / 2, lobes * pi, (lobes + 1) * pi / 2, INFINITY, 1.0};
+    const double q_dom = std::isinf(u_max[base]) ? INFINITY : std::pow((double)xi * u_max[base], 2.0 / beta);
+    darb_kernel_params k{};
+    k.kind = DARB_GENERIC;
+    k.psi = 1.0f;
+    k.q_max = (float)std::min(9.0, q_dom);
+    k.q_max_strict = 0;
+    k.base = base;
+    k.xi = xi;
+    k.beta = beta;
+    k.lobes = lobes;
+    *out = k;
+    return DARB_OK;
+}
+
+darb_status darb_kernel_psi(const darb_kernel_params *kparams, double *scratch, double *psi, darb_stream stream) {
+    if (!valid_kernel(kparams) || !scratch || !psi) return DARB_ERR_INVALID_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    double sums[2] = {0.0, 0.0};
+    DARB_CUDA_TRY(launch_psi_moment(*kparams, scratch, st));
+    DARB_CUDA_TRY(cudaMemcpyAsync(sums, scratch, sizeof(sums), cudaMemcpyDeviceToHost, st));
+    DARB_CUDA_TRY(cudaStreamSynchronize(st));
+    if (!(sums[1] > 0.0)) return DARB_ERR_INVALID_ARG;
+    *psi = sums[0] / (3.0 * sums[1]);
     return DARB_OK;
 }
 
@@ -137,7 +176,8 @@ darb_status darb_render_fwd(const darb_projected *proj, const darb_binning *bins
     DARB_CUDA_TRY(launch_render_fwd(kparams->kind, tile, tiles_x, tiles_y, bins->ranges, bins->values,
                                     reinterpret_cast<const float2 *>(proj->mean2d),
                                     reinterpret_cast<const float4 *>(proj->conic_o), proj->rgb, make_cam(*cam),
-                                    kparams->q_max, kparams->q_max_strict ? 1 : 0, out->image, out->t_final, out->last,
+                                    kparams->q_max, kparams->q_max_strict ? 1 : 0, make_spec(*kparams), out->image,
+                                    out->t_final, out->last,
                                     out->n_contrib, reinterpret_cast<cudaStream_t>(stream)));
     return DARB_OK;
 }
@@ -155,7 +195,8 @@ darb_status darb_render_bwd(const darb_projected *proj, int32_t n, const darb_bi
     DARB_CUDA_TRY(launch_render_bwd(kparams->kind, tile, tiles_x, tiles_y, bins->ranges, bins->values,
                                     reinterpret_cast<const float2 *>(proj->mean2d),
                                     reinterpret_cast<const float4 *>(proj->conic_o), proj->rgb, make_cam(*cam),
-                                    kparams->q_max, kparams->q_max_strict ? 1 : 0, fwd->t_final, fwd->last, dL_dimage,
+                                    kparams->q_max, kparams->q_max_strict ? 1 : 0, make_spec(*kparams), fwd->t_final,
+                                    fwd->last, dL_dimage,
                                     grad2d, st));
     return DARB_OK;
 }

@@ -244,7 +244,7 @@ darb_status darb_render_batch(const darb_splats *splats, const darb_camera *cams
         if (cudaStreamWaitEvent(st, P.join[s], 0) != cudaSuccess) return DARB_ERR_CUDA;
     }
     if (launch_render_fwd_batch(kparams->kind, tile, desc, V, total_tiles, queue, kparams->q_max,
-                                kparams->q_max_strict ? 1 : 0, bp->max_ctas, st) != cudaSuccess)
+                                kparams->q_max_strict ? 1 : 0, make_spec(*kparams), bp->max_ctas, st) != cudaSuccess)
         return DARB_ERR_CUDA;
     return DARB_OK;
 }

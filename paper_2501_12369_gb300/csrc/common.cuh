@@ -15,8 +15,9 @@ constexpr float kTMin = 0.0001f;            // 3DGS: stop before T (1 - alpha) <
 constexpr float kDilation = 0.3f;           // low-pass filter added to the 2D covariance
 constexpr float kGuardBand = 1.3f;          // Jacobian clamp at 1.3 tan(fov/2)
 constexpr float kPi = 3.14159265358979323846f;
+constexpr double kPiD = 3.14159265358979323846;
 
-constexpr int kNumKernels = 7;
+constexpr int kNumKernels = 8;  // the seven fixed kernels and DARB_GENERIC
 
 // Camera as passed by value to kernels.
 struct Cam {
@@ -50,8 +51,23 @@ inline Cam make_cam(const darb_camera &c) {
 // kernel_F is written with explicit intrinsics so that its rounding never depends on how the
 // compiler contracts the surrounding code: forward and backward must get the same alpha.
 
-template <int K> __device__ __forceinline__ float kernel_F(float q);
-template <int K> __device__ __forceinline__ float kernel_dF(float q);
+// Parameters of the generic member (kind DARB_GENERIC): F = base(u), u = q^(beta/2) / xi.
+struct KernelSpec {
+    int base;         // 0 exp(-u), 1 cos u, 2 1/2 + 1/2 cos u, 3 |sin u| / u, 4 (u + 1)^(-1/2), 5 1 - u
+    float inv_xi;     // 1 / xi
+    float half_beta;  // beta / 2
+};
+
+inline KernelSpec make_spec(const darb_kernel_params &k) {
+    KernelSpec s;
+    s.base = k.base;
+    s.inv_xi = k.xi > 0.0f ? 1.0f / k.xi : 0.0f;
+    s.half_beta = 0.5f * k.beta;
+    return s;
+}
+
+template <int K> __device__ __forceinline__ float kernel_F(float q, const KernelSpec &ks);
+template <int K> __device__ __forceinline__ float kernel_dF(float q, const KernelSpec &ks);
 
 // sin(x)/x = 1 - u/3! + u^2/5! - ... - u^7/15! with u = x^2, evaluated by Horner as
 // 1 - u (1/3! - u (1/5! - u (1/7! - u (1/9! - u (1/11! - u (1/13! - u/15!)))))).
@@ -65,22 +81,22 @@ __device__ __forceinline__ float sinc_series(float u) {
     return __fmaf_rn(r, -u, 1.0f);
 }
 
-template <> __device__ __forceinline__ float kernel_F<DARB_GAUSSIAN>(float q) {
+template <> __device__ __forceinline__ float kernel_F<DARB_GAUSSIAN>(float q, const KernelSpec &) {
     return __expf(__fmul_rn(-0.5f, q));
 }
-template <> __device__ __forceinline__ float kernel_dF<DARB_GAUSSIAN>(float q) { return -0.5f * __expf(-0.5f * q); }
+template <> __device__ __forceinline__ float kernel_dF<DARB_GAUSSIAN>(float q, const KernelSpec &) { return -0.5f * __expf(-0.5f * q); }
 
-template <> __device__ __forceinline__ float kernel_F<DARB_HALF_COSINE>(float q) {
+template <> __device__ __forceinline__ float kernel_F<DARB_HALF_COSINE>(float q, const KernelSpec &) {
     return __cosf(__fmul_rn(q, kPi / 18.0f));
 }
-template <> __device__ __forceinline__ float kernel_dF<DARB_HALF_COSINE>(float q) {
+template <> __device__ __forceinline__ float kernel_dF<DARB_HALF_COSINE>(float q, const KernelSpec &) {
     return -(kPi / 18.0f) * __sinf(q * (kPi / 18.0f));
 }
 
-template <> __device__ __forceinline__ float kernel_F<DARB_RAISED_COSINE>(float q) {
+template <> __device__ __forceinline__ float kernel_F<DARB_RAISED_COSINE>(float q, const KernelSpec &) {
     return __fmaf_rn(0.5f, __cosf(__fmul_rn(__fsqrt_rn(q), kPi / 2.5f)), 0.5f);
 }
-template <> __device__ __forceinline__ float kernel_dF<DARB_RAISED_COSINE>(float q) {
+template <> __device__ __forceinline__ float kernel_dF<DARB_RAISED_COSINE>(float q, const KernelSpec &) {
     // -(k/4) sin(k sqrt q) / sqrt q, k = pi/2.5; limit -k^2/4 at q = 0.
     constexpr float k = kPi / 2.5f;
     if (q < 1e-6f) return -0.25f * k * k + (k * k * k * k / 24.0f) * q;
@@ -88,11 +104,11 @@ template <> __device__ __forceinline__ float kernel_dF<DARB_RAISED_COSINE>(float
     return -0.25f * k * __sinf(k * r) / r;
 }
 
-template <> __device__ __forceinline__ float kernel_F<DARB_MOD_SINC>(float q) {
+template <> __device__ __forceinline__ float kernel_F<DARB_MOD_SINC>(float q, const KernelSpec &) {
     // x = pi sqrt(q) / 3, so x^2 = (pi^2 / 9) q; sin(x)/x >= 0 on the main lobe
     return fmaxf(sinc_series(__fmul_rn(q, kPi * kPi / 9.0f)), 0.0f);
 }
-template <> __device__ __forceinline__ float kernel_dF<DARB_MOD_SINC>(float q) {
+template <> __device__ __forceinline__ float kernel_dF<DARB_MOD_SINC>(float q, const KernelSpec &) {
     // (x cos x - sin x) / (2 q x), x = pi sqrt(q)/3; series below x = 0.3.
     const float x = sqrtf(q) * (kPi / 3.0f);
     if (x < 0.3f) {
@@ -105,26 +121,78 @@ template <> __device__ __forceinline__ float kernel_dF<DARB_MOD_SINC>(float q) {
     return (x * c - s) / (2.0f * q * x);
 }
 
-template <> __device__ __forceinline__ float kernel_F<DARB_INV_QUADRIC>(float q) {
+template <> __device__ __forceinline__ float kernel_F<DARB_INV_QUADRIC>(float q, const KernelSpec &) {
     return __fdividef(1.0f, __fadd_rn(1.0f, q));
 }
-template <> __device__ __forceinline__ float kernel_dF<DARB_INV_QUADRIC>(float q) {
+template <> __device__ __forceinline__ float kernel_dF<DARB_INV_QUADRIC>(float q, const KernelSpec &) {
     const float r = __fdividef(1.0f, 1.0f + q);
     return -r * r;
 }
 
-template <> __device__ __forceinline__ float kernel_F<DARB_INV_MULTIQUADRIC>(float q) {
+template <> __device__ __forceinline__ float kernel_F<DARB_INV_MULTIQUADRIC>(float q, const KernelSpec &) {
     return rsqrtf(__fadd_rn(1.0f, q));
 }
-template <> __device__ __forceinline__ float kernel_dF<DARB_INV_MULTIQUADRIC>(float q) {
+template <> __device__ __forceinline__ float kernel_dF<DARB_INV_MULTIQUADRIC>(float q, const KernelSpec &) {
     const float r = rsqrtf(1.0f + q);
     return -0.5f * r * r * r;
 }
 
-template <> __device__ __forceinline__ float kernel_F<DARB_PARABOLA>(float q) {
+template <> __device__ __forceinline__ float kernel_F<DARB_PARABOLA>(float q, const KernelSpec &) {
     return __fmaf_rn(q, -1.0f / 9.0f, 1.0f);
 }
-template <> __device__ __forceinline__ float kernel_dF<DARB_PARABOLA>(float) { return -1.0f / 9.0f; }
+template <> __device__ __forceinline__ float kernel_dF<DARB_PARABOLA>(float, const KernelSpec &) { return -1.0f / 9.0f; }
+
+// The generic member.  u = q / xi exactly when beta = 2, sqrt(q) / xi when beta = 1, else
+// __powf (a few ulp).  The cosines use the hardware approximation on the main lobe and the
+// accurate routine beyond pi; the sinc its series on [0, pi].
+__device__ __forceinline__ float generic_u(float q, const KernelSpec &ks) {
+    if (ks.half_beta == 1.0f) return __fmul_rn(q, ks.inv_xi);
+    if (!(q > 0.0f)) return 0.0f;
+    if (ks.half_beta == 0.5f) return __fmul_rn(__fsqrt_rn(q), ks.inv_xi);
+    return __fmul_rn(__powf(q, ks.half_beta), ks.inv_xi);
+}
+
+__device__ __forceinline__ float generic_base(int base, float u) {
+    switch (base) {
+    case 0: return __expf(-u);
+    case 1: return __cosf(u);
+    case 2: return __fmaf_rn(0.5f, u <= kPi ? __cosf(u) : cosf(u), 0.5f);
+    case 3: return u <= kPi ? fmaxf(sinc_series(__fmul_rn(u, u)), 0.0f) : fabsf(sinf(u)) / u;
+    case 4: return rsqrtf(__fadd_rn(u, 1.0f));
+    default: return __fadd_rn(1.0f, -u);
+    }
+}
+
+__device__ __forceinline__ float generic_base_du(int base, float u) {
+    switch (base) {
+    case 0: return -__expf(-u);
+    case 1: return -__sinf(u);
+    case 2: return -0.5f * (u <= kPi ? __sinf(u) : sinf(u));
+    case 3: {
+        if (u < 1e-3f) return -u * (1.0f / 3.0f);
+        float sn, cs;
+        if (u <= kPi) __sincosf(u, &sn, &cs);
+        else sincosf(u, &sn, &cs);
+        const float d = (u * cs - sn) / (u * u);
+        return sn < 0.0f ? -d : d;
+    }
+    case 4: {
+        const float r = rsqrtf(u + 1.0f);
+        return -0.5f * r * r * r;
+    }
+    default: return -1.0f;
+    }
+}
+
+template <> __device__ __forceinline__ float kernel_F<DARB_GENERIC>(float q, const KernelSpec &ks) {
+    return generic_base(ks.base, generic_u(q, ks));
+}
+template <> __device__ __forceinline__ float kernel_dF<DARB_GENERIC>(float q, const KernelSpec &ks) {
+    if (ks.half_beta == 1.0f) return generic_base_du(ks.base, q * ks.inv_xi) * ks.inv_xi;
+    const float qq = fmaxf(q, 1e-30f);  // one-sided limit at the centre (finite for beta >= 1 on cosines)
+    const float u = generic_u(qq, ks);
+    return generic_base_du(ks.base, u) * ks.half_beta * u / qq;
+}
 
 // The support test on q: 0 <= q <= q_max (q < q_max when strict).
 __device__ __forceinline__ bool in_support(float q, float qmax, bool strict) {

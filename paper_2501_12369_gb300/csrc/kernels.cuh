@@ -51,7 +51,11 @@ struct BatchView {
 // render.cu: persistent launch over all views' tiles; queue is a device counter (reset here).
 // max_ctas > 0 caps the grid (else SMs x resident CTAs).
 cudaError_t launch_render_fwd_batch(int kind, int tile, const BatchView *views, int n_views, int total_tiles,
-                                    uint32_t *queue, float qmax, int strict, int max_ctas, cudaStream_t st);
+                                    uint32_t *queue, float qmax, int strict, const KernelSpec &ks, int max_ctas,
+                                    cudaStream_t st);
+
+// psi.cu: the moment integrals of darb_kernel_psi into sums[0] (r^4 F) and sums[1] (r^2 F).
+cudaError_t launch_psi_moment(const darb_kernel_params &k, double *sums, cudaStream_t st);
 
 // ssim.cu: the L1 + D-SSIM image loss and its gradient.
 size_t l1_dssim_workspace_bytes(int W, int H);
@@ -93,12 +97,12 @@ cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int til
 // render.cu
 cudaError_t launch_render_fwd(int kind, int tile, int tiles_x, int tiles_y, const uint32_t *ranges,
                               const uint32_t *values, const float2 *mean2d, const float4 *conic_o,
-                              const float *rgb, const Cam &cam, float qmax, int strict,
+                              const float *rgb, const Cam &cam, float qmax, int strict, const KernelSpec &ks,
                               float *image, float *t_final, uint32_t *last, uint32_t *n_contrib,
                               cudaStream_t st);
 cudaError_t launch_render_bwd(int kind, int tile, int tiles_x, int tiles_y, const uint32_t *ranges,
                               const uint32_t *values, const float2 *mean2d, const float4 *conic_o,
-                              const float *rgb, const Cam &cam, float qmax, int strict,
+                              const float *rgb, const Cam &cam, float qmax, int strict, const KernelSpec &ks,
                               const float *t_final, const uint32_t *last, const float *dL_dimage,
                               float *grad2d, cudaStream_t st);
 

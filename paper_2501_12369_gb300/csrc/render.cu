@@ -54,7 +54,8 @@ __device__ __forceinline__ void render_tile_fwd(int tile, FwdSmem<TILE> &sm, con
                                                 const uint32_t *__restrict__ values,
                                                 const float2 *__restrict__ mean2d,
                                                 const float4 *__restrict__ conic_o, const float *__restrict__ rgb,
-                                                int W, int H, int tiles_x, float qmax, int strict, SinkFn sink) {
+                                                int W, int H, int tiles_x, float qmax, int strict,
+                                                const KernelSpec &ks, SinkFn sink) {
     using S = RenderShape<TILE>;
     constexpr int NT = S::NT, PIX = S::PIX;
     const int tx = tile % tiles_x, ty = tile / tiles_x;
@@ -107,7 +108,7 @@ __device__ __forceinline__ void render_tile_fwd(int tile, FwdSmem<TILE> &sm, con
                 const float dy = __fsub_rn(xy.y, fpy[k]);
                 const float q = conic_q(dx, dy, co.x, co.y, co.z);
                 if (!in_support(q, qmax, strict)) continue;
-                const float alpha = fminf(kAlphaMax, __fmul_rn(co.w, kernel_F<KIND>(q)));
+                const float alpha = fminf(kAlphaMax, __fmul_rn(co.w, kernel_F<KIND>(q, ks)));
                 if (alpha < kAlphaMin) continue;
                 const float Tn = T[k] * (1.0f - alpha);
                 if (Tn < kTMin) {
@@ -145,11 +146,11 @@ template <int KIND, int TILE>
 __global__ void __launch_bounds__(RenderShape<TILE>::NT)
 k_render_fwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ values,
              const float2 *__restrict__ mean2d, const float4 *__restrict__ conic_o,
-             const float *__restrict__ rgb, int W, int H, int tiles_x, float qmax, int strict, Bg bg,
+             const float *__restrict__ rgb, int W, int H, int tiles_x, float qmax, int strict, KernelSpec ks, Bg bg,
              float *__restrict__ image, float *__restrict__ t_final, uint32_t *__restrict__ last,
              uint32_t *__restrict__ n_contrib) {
     __shared__ FwdSmem<TILE> sm;
-    render_tile_fwd<KIND, TILE>(blockIdx.x, sm, ranges, values, mean2d, conic_o, rgb, W, H, tiles_x, qmax, strict,
+    render_tile_fwd<KIND, TILE>(blockIdx.x, sm, ranges, values, mean2d, conic_o, rgb, W, H, tiles_x, qmax, strict, ks,
                                 [&] { return FwdSink{image, t_final, last, n_contrib, bg}; });
 }
 
@@ -159,7 +160,7 @@ k_render_fwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ valu
 template <int KIND, int TILE>
 __global__ void __launch_bounds__(RenderShape<TILE>::NT, 1536 / RenderShape<TILE>::NT)
 k_render_fwd_batch(const BatchView *__restrict__ views, int n_views, int total_tiles, uint32_t *__restrict__ queue,
-                   float qmax, int strict) {
+                   float qmax, int strict, KernelSpec ks) {
     __shared__ FwdSmem<TILE> sm;
     __shared__ int s_item, s_view;
     for (;;) {
@@ -182,7 +183,7 @@ k_render_fwd_batch(const BatchView *__restrict__ views, int n_views, int total_t
         if (item >= total_tiles) break;
         const BatchView &bv = views[v];
         render_tile_fwd<KIND, TILE>(item - bv.tile_begin, sm, bv.ranges, bv.values, bv.mean2d, bv.conic_o, bv.rgb,
-                                    bv.W, bv.H, bv.tiles_x, qmax, strict, [&] {
+                                    bv.W, bv.H, bv.tiles_x, qmax, strict, ks, [&] {
                                         const BatchView &b = views[v];
                                         return FwdSink{b.image, b.t_final, b.last, b.n_contrib,
                                                        Bg{b.bg[0], b.bg[1], b.bg[2]}};
@@ -231,7 +232,7 @@ template <int KIND, int TILE>
 __global__ void __launch_bounds__(RenderShape<TILE>::NT)
 k_render_bwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ values,
              const float2 *__restrict__ mean2d, const float4 *__restrict__ conic_o,
-             const float *__restrict__ rgb, int W, int H, int tiles_x, float qmax, int strict, Bg bg,
+             const float *__restrict__ rgb, int W, int H, int tiles_x, float qmax, int strict, KernelSpec ks, Bg bg,
              const float *__restrict__ t_final, const uint32_t *__restrict__ last,
              const float *__restrict__ dL_dimage, float4 *__restrict__ grad2d) {
     using S = RenderShape<TILE>;
@@ -316,7 +317,7 @@ k_render_bwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ valu
                 const float dy = __fsub_rn(xy.y, fpy[k]);
                 const float q = conic_q(dx, dy, co.x, co.y, co.z);
                 if (!in_support(q, qmax, strict)) continue;
-                const float F = kernel_F<KIND>(q);
+                const float F = kernel_F<KIND>(q, ks);
                 const float of = __fmul_rn(co.w, F);
                 const float alpha = fminf(kAlphaMax, of);
                 if (alpha < kAlphaMin) continue;
@@ -337,7 +338,7 @@ k_render_bwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ valu
                 v[8] = fmaf(w, g2[k], v[8]);
                 if (!(of > kAlphaMax)) {
                     v[5] = fmaf(F, dalpha, v[5]);
-                    const float dq = co.w * kernel_dF<KIND>(q) * dalpha;
+                    const float dq = co.w * kernel_dF<KIND>(q, ks) * dalpha;
                     const float B = 0.5f * co.y;
                     v[0] = fmaf(2.0f * dq, co.x * dx + B * dy, v[0]);
                     v[1] = fmaf(2.0f * dq, B * dx + co.z * dy, v[1]);
@@ -383,20 +384,22 @@ k_render_bwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ valu
 template <int KIND, int TILE>
 cudaError_t fwd_t(int n_tiles, const uint2 *ranges, const uint32_t *values, const float2 *mean2d,
                   const float4 *conic_o, const float *rgb, const Cam &cam, int tiles_x, float qmax, int strict,
-                  float *image, float *t_final, uint32_t *last, uint32_t *n_contrib, cudaStream_t st) {
+                  const KernelSpec &ks, float *image, float *t_final, uint32_t *last, uint32_t *n_contrib,
+                  cudaStream_t st) {
     k_render_fwd<KIND, TILE><<<n_tiles, RenderShape<TILE>::NT, 0, st>>>(
-        ranges, values, mean2d, conic_o, rgb, cam.W, cam.H, tiles_x, qmax, strict, Bg{cam.bg[0], cam.bg[1], cam.bg[2]},
-        image, t_final, last, n_contrib);
+        ranges, values, mean2d, conic_o, rgb, cam.W, cam.H, tiles_x, qmax, strict, ks,
+        Bg{cam.bg[0], cam.bg[1], cam.bg[2]}, image, t_final, last, n_contrib);
     return cudaGetLastError();
 }
 
 template <int KIND, int TILE>
 cudaError_t bwd_t(int n_tiles, const uint2 *ranges, const uint32_t *values, const float2 *mean2d,
                   const float4 *conic_o, const float *rgb, const Cam &cam, int tiles_x, float qmax, int strict,
-                  const float *t_final, const uint32_t *last, const float *dL, float *grad2d, cudaStream_t st) {
+                  const KernelSpec &ks, const float *t_final, const uint32_t *last, const float *dL, float *grad2d,
+                  cudaStream_t st) {
     k_render_bwd<KIND, TILE><<<n_tiles, RenderShape<TILE>::NT, 0, st>>>(
-        ranges, values, mean2d, conic_o, rgb, cam.W, cam.H, tiles_x, qmax, strict, Bg{cam.bg[0], cam.bg[1], cam.bg[2]},
-        t_final, last, dL, reinterpret_cast<float4 *>(grad2d));
+        ranges, values, mean2d, conic_o, rgb, cam.W, cam.H, tiles_x, qmax, strict, ks,
+        Bg{cam.bg[0], cam.bg[1], cam.bg[2]}, t_final, last, dL, reinterpret_cast<float4 *>(grad2d));
     return cudaGetLastError();
 }
 
@@ -404,31 +407,31 @@ cudaError_t bwd_t(int n_tiles, const uint2 *ranges, const uint32_t *values, cons
 
 cudaError_t launch_render_fwd(int kind, int tile, int tiles_x, int tiles_y, const uint32_t *ranges,
                               const uint32_t *values, const float2 *mean2d, const float4 *conic_o,
-                              const float *rgb, const Cam &cam, float qmax, int strict,
+                              const float *rgb, const Cam &cam, float qmax, int strict, const KernelSpec &ks,
                               float *image, float *t_final, uint32_t *last, uint32_t *n_contrib,
                               cudaStream_t st) {
     const int n_tiles = tiles_x * tiles_y;
     if (n_tiles == 0) return cudaSuccess;
     const uint2 *rg = reinterpret_cast<const uint2 *>(ranges);
-#define FWD_ARGS (n_tiles, rg, values, mean2d, conic_o, rgb, cam, tiles_x, qmax, strict, image, t_final, last, n_contrib, st)
+#define FWD_ARGS (n_tiles, rg, values, mean2d, conic_o, rgb, cam, tiles_x, qmax, strict, ks, image, t_final, last, n_contrib, st)
 #define FWD_CALL(K, T) fwd_t<K, T> FWD_ARGS
     if (tile == 8) {
         switch (kind) {
         case 0: return FWD_CALL(0, 8); case 1: return FWD_CALL(1, 8); case 2: return FWD_CALL(2, 8);
         case 3: return FWD_CALL(3, 8); case 4: return FWD_CALL(4, 8); case 5: return FWD_CALL(5, 8);
-        default: return FWD_CALL(6, 8);
+        case 6: return FWD_CALL(6, 8); default: return FWD_CALL(7, 8);
         }
     } else if (tile == 16) {
         switch (kind) {
         case 0: return FWD_CALL(0, 16); case 1: return FWD_CALL(1, 16); case 2: return FWD_CALL(2, 16);
         case 3: return FWD_CALL(3, 16); case 4: return FWD_CALL(4, 16); case 5: return FWD_CALL(5, 16);
-        default: return FWD_CALL(6, 16);
+        case 6: return FWD_CALL(6, 16); default: return FWD_CALL(7, 16);
         }
     } else {
         switch (kind) {
         case 0: return FWD_CALL(0, 32); case 1: return FWD_CALL(1, 32); case 2: return FWD_CALL(2, 32);
         case 3: return FWD_CALL(3, 32); case 4: return FWD_CALL(4, 32); case 5: return FWD_CALL(5, 32);
-        default: return FWD_CALL(6, 32);
+        case 6: return FWD_CALL(6, 32); default: return FWD_CALL(7, 32);
         }
     }
 #undef FWD_CALL
@@ -439,7 +442,7 @@ namespace {
 
 template <int KIND, int TILE>
 cudaError_t fwd_batch_t(const BatchView *views, int n_views, int total_tiles, uint32_t *queue, float qmax, int strict,
-                        int max_ctas, cudaStream_t st) {
+                        const KernelSpec &ks, int max_ctas, cudaStream_t st) {
     static int per_sm[kMaxDevicesRender] = {};  // resident CTAs per SM, once per device
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -461,33 +464,34 @@ cudaError_t fwd_batch_t(const BatchView *views, int n_views, int total_tiles, ui
     e = cudaMemsetAsync(queue, 0, sizeof(uint32_t), st);
     if (e != cudaSuccess) return e;
     k_render_fwd_batch<KIND, TILE><<<(int)grid, RenderShape<TILE>::NT, 0, st>>>(views, n_views, total_tiles, queue,
-                                                                                 qmax, strict);
+                                                                                 qmax, strict, ks);
     return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_render_fwd_batch(int kind, int tile, const BatchView *views, int n_views, int total_tiles,
-                                    uint32_t *queue, float qmax, int strict, int max_ctas, cudaStream_t st) {
+                                    uint32_t *queue, float qmax, int strict, const KernelSpec &ks, int max_ctas,
+                                    cudaStream_t st) {
     if (total_tiles == 0 || n_views == 0) return cudaSuccess;
-#define FB_CALL(K, T) fwd_batch_t<K, T>(views, n_views, total_tiles, queue, qmax, strict, max_ctas, st)
+#define FB_CALL(K, T) fwd_batch_t<K, T>(views, n_views, total_tiles, queue, qmax, strict, ks, max_ctas, st)
     if (tile == 8) {
         switch (kind) {
         case 0: return FB_CALL(0, 8); case 1: return FB_CALL(1, 8); case 2: return FB_CALL(2, 8);
         case 3: return FB_CALL(3, 8); case 4: return FB_CALL(4, 8); case 5: return FB_CALL(5, 8);
-        default: return FB_CALL(6, 8);
+        case 6: return FB_CALL(6, 8); default: return FB_CALL(7, 8);
         }
     } else if (tile == 16) {
         switch (kind) {
         case 0: return FB_CALL(0, 16); case 1: return FB_CALL(1, 16); case 2: return FB_CALL(2, 16);
         case 3: return FB_CALL(3, 16); case 4: return FB_CALL(4, 16); case 5: return FB_CALL(5, 16);
-        default: return FB_CALL(6, 16);
+        case 6: return FB_CALL(6, 16); default: return FB_CALL(7, 16);
         }
     } else {
         switch (kind) {
         case 0: return FB_CALL(0, 32); case 1: return FB_CALL(1, 32); case 2: return FB_CALL(2, 32);
         case 3: return FB_CALL(3, 32); case 4: return FB_CALL(4, 32); case 5: return FB_CALL(5, 32);
-        default: return FB_CALL(6, 32);
+        case 6: return FB_CALL(6, 32); default: return FB_CALL(7, 32);
         }
     }
 #undef FB_CALL
@@ -495,31 +499,31 @@ cudaError_t launch_render_fwd_batch(int kind, int tile, const BatchView *views, 
 
 cudaError_t launch_render_bwd(int kind, int tile, int tiles_x, int tiles_y, const uint32_t *ranges,
                               const uint32_t *values, const float2 *mean2d, const float4 *conic_o,
-                              const float *rgb, const Cam &cam, float qmax, int strict,
+                              const float *rgb, const Cam &cam, float qmax, int strict, const KernelSpec &ks,
                               const float *t_final, const uint32_t *last, const float *dL_dimage,
                               float *grad2d, cudaStream_t st) {
     const int n_tiles = tiles_x * tiles_y;
     if (n_tiles == 0) return cudaSuccess;
     const uint2 *rg = reinterpret_cast<const uint2 *>(ranges);
-#define BWD_ARGS (n_tiles, rg, values, mean2d, conic_o, rgb, cam, tiles_x, qmax, strict, t_final, last, dL_dimage, grad2d, st)
+#define BWD_ARGS (n_tiles, rg, values, mean2d, conic_o, rgb, cam, tiles_x, qmax, strict, ks, t_final, last, dL_dimage, grad2d, st)
 #define BWD_CALL(K, T) bwd_t<K, T> BWD_ARGS
     if (tile == 8) {
         switch (kind) {
         case 0: return BWD_CALL(0, 8); case 1: return BWD_CALL(1, 8); case 2: return BWD_CALL(2, 8);
         case 3: return BWD_CALL(3, 8); case 4: return BWD_CALL(4, 8); case 5: return BWD_CALL(5, 8);
-        default: return BWD_CALL(6, 8);
+        case 6: return BWD_CALL(6, 8); default: return BWD_CALL(7, 8);
         }
     } else if (tile == 16) {
         switch (kind) {
         case 0: return BWD_CALL(0, 16); case 1: return BWD_CALL(1, 16); case 2: return BWD_CALL(2, 16);
         case 3: return BWD_CALL(3, 16); case 4: return BWD_CALL(4, 16); case 5: return BWD_CALL(5, 16);
-        default: return BWD_CALL(6, 16);
+        case 6: return BWD_CALL(6, 16); default: return BWD_CALL(7, 16);
         }
     } else {
         switch (kind) {
         case 0: return BWD_CALL(0, 32); case 1: return BWD_CALL(1, 32); case 2: return BWD_CALL(2, 32);
         case 3: return BWD_CALL(3, 32); case 4: return BWD_CALL(4, 32); case 5: return BWD_CALL(5, 32);
-        default: return BWD_CALL(6, 32);
+        case 6: return BWD_CALL(6, 32); default: return BWD_CALL(7, 32);
         }
     }
 #undef BWD_CALL

@@ -383,7 +383,7 @@ darb_status darb_serve_add_scene(darb_server *S, const darb_splats *splats, int3
 }
 
 darb_status darb_serve_submit(darb_server *S, const darb_request *r, uint64_t *ticket) {
-    if (!S || !r || !ticket || !valid_camera(&r->cam) || !r->image || r->kernel < 0 || r->kernel >= kNumKernels)
+    if (!S || !r || !ticket || !valid_camera(&r->cam) || !r->image || r->kernel < 0 || r->kernel >= kNumKernels - 1)
         return DARB_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lock(S->mu);
     if (S->stop) return DARB_ERR_INVALID_ARG;

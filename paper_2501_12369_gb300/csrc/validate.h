@@ -24,8 +24,12 @@ inline bool valid_camera(const darb_camera *c) {
 }
 
 inline bool valid_kernel(const darb_kernel_params *k) {
-    return k && k->kind >= 0 && k->kind < kNumKernels && k->psi > 0.0f && finitef(k->psi) && k->q_max > 0.0f &&
-           finitef(k->q_max);
+    if (!k || k->kind < 0 || k->kind >= kNumKernels || !(k->psi > 0.0f) || !finitef(k->psi) || !(k->q_max > 0.0f) ||
+        !finitef(k->q_max))
+        return false;
+    if (k->kind != DARB_GENERIC) return true;
+    return k->base >= 0 && k->base <= 5 && k->xi > 0.0f && finitef(k->xi) && k->beta >= 0.5f && k->beta <= 4.0f &&
+           k->lobes >= 1 && k->lobes <= 64;
 }
 
 inline bool valid_splats(const darb_splats *s) {

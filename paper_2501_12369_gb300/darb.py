@@ -27,7 +27,8 @@ STATUS_NAMES = {0: "DARB_OK", 1: "DARB_ERR_INVALID_ARG", 2: "DARB_ERR_WORKSPACE"
 
 
 class darb_kernel_params(ctypes.Structure):
-    _fields_ = [("kind", c_i32), ("psi", c_f32), ("q_max", c_f32), ("q_max_strict", c_i32)]
+    _fields_ = [("kind", c_i32), ("psi", c_f32), ("q_max", c_f32), ("q_max_strict", c_i32), ("base", c_i32),
+                ("xi", c_f32), ("beta", c_f32), ("lobes", c_i32)]
 
 
 class darb_camera(ctypes.Structure):
@@ -101,6 +102,8 @@ _P = ctypes.POINTER
 SIGNATURES = {
     "darb_status_string": (ctypes.c_char_p, [c_i32]),
     "darb_kernel_defaults": (c_i32, [c_i32, _P(darb_kernel_params)]),
+    "darb_kernel_generic": (c_i32, [c_i32, c_f32, c_f32, c_i32, _P(darb_kernel_params)]),
+    "darb_kernel_psi": (c_i32, [_P(darb_kernel_params), c_vp, _P(ctypes.c_double), c_vp]),
     "darb_tile_grid": (c_i32, [_P(darb_camera), c_i32, _P(c_i32), _P(c_i32)]),
     "darb_preprocess": (c_i32, [_P(darb_splats), _P(darb_camera), _P(darb_kernel_params), c_i32,
                                 _P(darb_projected), c_vp]),
@@ -188,9 +191,38 @@ def kernel_index(kernel) -> int:
 
 
 def darb_kernel_defaults(kernel) -> darb_kernel_params:
+    """Parameters of a fixed kernel (name or enum); a darb_kernel_params is returned as a copy."""
+    if isinstance(kernel, darb_kernel_params):
+        return darb_kernel_params.from_buffer_copy(kernel)
     kp = darb_kernel_params()
     _check(lib().darb_kernel_defaults(kernel_index(kernel), ctypes.byref(kp)), "darb_kernel_defaults")
     return kp
+
+
+DARB_GENERIC = 7
+GENERIC_BASES = ("gaussian", "half_cosine", "raised_cosine", "mod_sinc", "inv_multiquadric", "parabola")
+
+
+def darb_kernel_generic(base, xi, beta, lobes=1, psi="device", device="cuda") -> darb_kernel_params:
+    """A member of Table 1's modified family; psi="device" computes it with darb_kernel_psi,
+    a number sets it, None leaves 1."""
+    b = GENERIC_BASES.index(base) if isinstance(base, str) else int(base)
+    kp = darb_kernel_params()
+    _check(lib().darb_kernel_generic(b, float(xi), float(beta), int(lobes), ctypes.byref(kp)), "darb_kernel_generic")
+    if psi == "device":
+        kp.psi = darb_kernel_psi(kp, device=device)
+    elif psi is not None:
+        kp.psi = float(psi)
+    return kp
+
+
+def darb_kernel_psi(kp: darb_kernel_params, device="cuda", stream=None) -> float:
+    """psi of any kernel by the moment integral on the device (synchronises)."""
+    scratch = torch.empty(2, dtype=torch.float64, device=device)
+    out = ctypes.c_double(0.0)
+    _check(lib().darb_kernel_psi(ctypes.byref(kp), _p(scratch), ctypes.byref(out), _stream(stream)),
+           "darb_kernel_psi")
+    return float(out.value)
 
 
 def camera(cam) -> darb_camera:

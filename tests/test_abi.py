@@ -4,6 +4,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -103,3 +104,22 @@ def test_oracle_and_library_share_no_source():
         if f.endswith((".py", ".c", ".h")):
             text = open(os.path.join(ROOT, "oracle", f)).read()
             assert "paper_2501_12369_gb300" not in text and "darb.h" not in text, f
+
+
+def test_generic_kernel_parameters_match_the_oracle():
+    """darb_kernel_generic (host code) gives the oracle's float32 q_max for Table 1's members and
+    rejects invalid descriptions."""
+    import oracle
+    from paper_2501_12369_gb300 import darb
+    for base, xi, beta, lobes in [("half_cosine", 3.0, 1.5, 1), ("raised_cosine", 1.2, 2.0, 1),
+                                  ("mod_sinc", 1.1, 1.5, 2), ("gaussian", 1.0, 2.5, 1), ("parabola", 4.0, 2.0, 1),
+                                  ("half_cosine", 18 / np.pi, 2.0, 1), ("raised_cosine", 2.5 / np.pi, 1.0, 1)]:
+        kp = darb.darb_kernel_generic(base, xi, beta, lobes, psi=None)
+        ko = oracle.generic_kernel(base, xi, beta, lobes, psi=1.0)
+        assert kp.kind == 7 and kp.q_max == ko.q_max and kp.q_max_strict == 0
+        assert (kp.base, kp.xi, kp.beta, kp.lobes) == (ko.base, ko.xi, ko.beta, ko.lobes)
+    for bad in [(6, 1.0, 2.0, 1), (1, 0.0, 2.0, 1), (1, 1.0, 0.2, 1), (1, 1.0, 2.0, 0)]:
+        with pytest.raises(darb.DarbError):
+            darb.darb_kernel_generic(*bad, psi=None)
+    with pytest.raises(darb.DarbError):  # the generic kind has no defaults
+        darb.darb_kernel_defaults(7)

@@ -417,6 +417,113 @@ def l1_dssim_loss(image, target, lam=0.2):
     return loss, (1 - lam) * dl1 - lam * dssim_dx, ssim.mean()
 
 
+# Adaptive density control.  The paper keeps the optimisation pipeline of 3DGS (Sec. 4 block
+# diagram), whose density control is restated here: per training step, statistics of every
+# visible splat; every few hundred steps, clone, split and prune.  Decisions are taken in float32
+# with the same operations as the GPU (the rules require both sides to decide in one precision).
+
+def densify_stats(grad2d, radius, width, height, accum, count, max_radius):
+    """One step's statistics: the norm of the view-space mean gradient in normalised device
+    units (pixel gradient x (W/2, H/2)) added to accum, 1 added to count, and the largest
+    screen radius kept, for every visible splat (radius > 0).  float32, in place."""
+    f = np.float32
+    vis = np.asarray(radius) > 0
+    gx = np.asarray(grad2d[:, 0], f) * f(0.5 * width)
+    gy = np.asarray(grad2d[:, 1], f) * f(0.5 * height)
+    norm = np.sqrt(gx * gx + gy * gy).astype(f)
+    accum[vis] = (accum[vis] + norm[vis]).astype(f)
+    count[vis] = (count[vis] + f(1.0)).astype(f)
+    max_radius[vis] = np.maximum(max_radius[vis], np.asarray(radius)[vis])
+
+
+def densify_actions(scales, opacities, accum, count, max_radius, cfg):
+    """Per splat: (grow, split, keep) booleans.  avg = accum / count (0 unseen);
+    grow = avg >= grad_threshold; clone if grow and max scale <= dense_scale, split if grow and
+    max scale > dense_scale; a splat that is split is replaced by its children; any splat is
+    pruned (not kept) if opacity < min_opacity, or its max screen radius > max_screen_radius
+    (when > 0), or its max scale > max_world_scale (when > 0)."""
+    f = np.float32
+    cnt = np.asarray(count, f)
+    avg = np.where(cnt > 0, np.asarray(accum, f) / np.where(cnt > 0, cnt, f(1)), f(0)).astype(f)
+    smax = np.max(np.asarray(scales, f), axis=1)
+    grow = avg >= f(cfg["grad_threshold"])
+    split = grow & (smax > f(cfg["dense_scale"]))
+    clone = grow & ~split
+    keep = _survives(np.asarray(opacities, f), smax, np.asarray(max_radius), cfg)
+    return clone, split, keep
+
+
+def _survives(opac, smax, radius, cfg):
+    f = np.float32
+    ok = opac >= f(cfg["min_opacity"])
+    if cfg["max_screen_radius"] > 0:
+        ok &= np.asarray(radius, f) <= f(cfg["max_screen_radius"])
+    if cfg["max_world_scale"] > 0:
+        ok &= smax <= f(cfg["max_world_scale"])
+    return ok
+
+
+def densify(raw, act, state, accum, count, max_radius, normals, cfg):
+    """One density-control pass.  raw: dict means, log_scales, quats, opacity_logits, sh;
+    act: dict scales, opacities (activated copies); state: dict of Adam moments m_/v_ + the raw
+    names; normals: [n, 2, 3] standard normal draws for the split children.
+    Output order: surviving originals in index order, then clones in parent order, then split
+    children (two per parent, in parent order).  Originals keep their moments; clones and
+    children start from zero moments.  A clone carries its parent's statistics for the prune
+    test except the screen radius, which starts at 0 (it has not been rendered); so do
+    children, whose scales are the parent's / split_scale_div and whose means are
+    parent + R(q) (s * z), s the parent's scales, R the rotation of the normalised quaternion.
+    Returns (raw', act', state', n_out)."""
+    f = np.float32
+    n = raw["means"].shape[0]
+    clone, split, keep = densify_actions(act["scales"], act["opacities"], accum, count, max_radius, cfg)
+    surv = keep & ~split
+    smax = np.max(np.asarray(act["scales"], f), axis=1)
+    zero_r = np.zeros(n, np.int32)
+    opac = np.asarray(act["opacities"], f)
+    clone_kept = clone & _survives(opac, smax, zero_r, cfg)
+    div = f(cfg["split_scale_div"])
+    child_smax = np.max(np.asarray(act["scales"], f) / div, axis=1).astype(f)
+    child_kept = split & _survives(opac, child_smax, zero_r, cfg)
+    sel_s, sel_c, sel_p = np.flatnonzero(surv), np.flatnonzero(clone_kept), np.flatnonzero(child_kept)
+    q = np.asarray(raw["quats"], np.float64)
+    q = q / np.linalg.norm(q, axis=1, keepdims=True)
+    w, x, y, z = q[:, 0], q[:, 1], q[:, 2], q[:, 3]
+    R = np.stack([np.stack([1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)], -1),
+                  np.stack([2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)], -1),
+                  np.stack([2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)], -1)], 1)
+    sc = np.asarray(act["scales"], np.float64)
+    out_raw, out_act, out_state = {}, {}, {}
+    log_div = f(np.log(np.float64(div)))
+    for k, v in raw.items():
+        v = np.asarray(v)
+        if k == "means":
+            kids = []
+            for j in range(2):
+                off = np.einsum("nab,nb->na", R[sel_p], sc[sel_p] * np.asarray(normals, np.float64)[sel_p, j])
+                kids.append(v[sel_p].astype(np.float64) + off)
+            children = np.stack(kids, 1).reshape(-1, 3)
+        elif k == "log_scales":
+            children = np.repeat((v[sel_p].astype(f) - log_div).astype(f), 2, axis=0)
+        else:
+            children = np.repeat(v[sel_p], 2, axis=0)
+        out_raw[k] = np.concatenate([v[sel_s], v[sel_c], children.astype(v.dtype) if k != "means" else children])
+    out_act["scales"] = np.exp(np.asarray(out_raw["log_scales"], np.float64))
+    out_act["opacities"] = 1.0 / (1.0 + np.exp(-np.asarray(out_raw["opacity_logits"], np.float64)))
+    for k, v in state.items():
+        v = np.asarray(v)
+        new = np.zeros((len(sel_c) + 2 * len(sel_p),) + v.shape[1:], v.dtype)
+        out_state[k] = np.concatenate([v[sel_s], new])
+    return out_raw, out_act, out_state, len(sel_s) + len(sel_c) + 2 * len(sel_p)
+
+
+def reset_opacity(opacity_logits, max_opacity=0.01):
+    """Opacity reset: every opacity above max_opacity is set to it (logits clamped)."""
+    f = np.float32
+    cap = f(np.log(np.float64(max_opacity) / (1.0 - np.float64(max_opacity))))
+    return np.minimum(np.asarray(opacity_logits, f), cap)
+
+
 def adam_update(p, g, m, v, lr, step, beta1=0.9, beta2=0.999, eps=1e-15):
     """One Adam step (Kingma & Ba, Algorithm 1) on float64 copies; returns (p, m, v)."""
     p, g, m, v = (np.asarray(a, np.float64) for a in (p, g, m, v))

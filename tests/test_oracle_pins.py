@@ -669,3 +669,79 @@ def test_generic_member_renders_tiled_as_brute_force_with_a_checked_gradient():
         assert abs(fd - an) <= 2e-3 * max(abs(fd), abs(an), 1e-2), (field, idx, fd, an)
         checked += 1
     assert checked >= 12
+
+
+# --------------------------------------------------------------------------- adaptive density control
+
+_DCFG = dict(grad_threshold=2e-4, dense_scale=0.05, min_opacity=0.005, max_screen_radius=20.0,
+             max_world_scale=0.0, split_scale_div=1.6)
+
+
+def _dstate(n, rng):
+    raw = dict(means=rng.normal(size=(n, 3)).astype(np.float32),
+               log_scales=np.log(np.full((n, 3), 0.02)).astype(np.float32),
+               quats=np.tile(np.array([1, 0, 0, 0], np.float32), (n, 1)),
+               opacity_logits=np.zeros(n, np.float32), sh=rng.normal(size=(n, 4, 3)).astype(np.float32))
+    act = dict(scales=np.exp(raw["log_scales"].astype(np.float64)).astype(np.float32),
+               opacities=np.full(n, 0.5, np.float32))
+    state = {f"{m}_{k}": rng.normal(size=v.shape).astype(np.float32) for k, v in raw.items() for m in ("m", "v")}
+    return raw, act, state
+
+
+def test_densify_clones_splits_prunes_in_the_documented_order():
+    rng = np.random.default_rng(0)
+    raw, act, state = _dstate(4, rng)
+    raw["log_scales"][1] = np.log(np.float32([0.2, 0.1, 0.1]))  # splat 1 large
+    act["scales"][1] = np.exp(raw["log_scales"][1].astype(np.float64))
+    act["opacities"][2] = 0.001                                  # splat 2 transparent
+    accum = np.array([1e-3, 3e-3, 0.0, 1e-5], np.float32)
+    count = np.array([2, 3, 5, 1], np.float32)                   # averages 5e-4, 1e-3, 0, 1e-5
+    radius = np.array([3, 4, 2, 5], np.int32)
+    normals = np.zeros((4, 2, 3), np.float32)
+    normals[1, 0] = [1, 0, 0]
+    normals[1, 1] = [-1, 0, 0]
+    out, oact, ost, n = oracle.densify(raw, act, state, accum, count, radius, normals, _DCFG)
+    assert n == 5  # survivors 0, 3; clone of 0; children of 1 (2 pruned, 1 replaced)
+    np.testing.assert_array_equal(out["sh"][:2], raw["sh"][[0, 3]])
+    np.testing.assert_array_equal(out["sh"][2], raw["sh"][0])
+    np.testing.assert_array_equal(out["sh"][3:], raw["sh"][[1, 1]])
+    m = raw["means"][1].astype(np.float64)
+    np.testing.assert_allclose(out["means"][3], m + [0.2, 0, 0], rtol=0, atol=1e-7)  # identity rotation
+    np.testing.assert_allclose(out["means"][4], m - [0.2, 0, 0], rtol=0, atol=1e-7)
+    np.testing.assert_allclose(np.exp(out["log_scales"][3:].astype(np.float64)),
+                               np.tile(act["scales"][1] / 1.6, (2, 1)), rtol=1e-6)
+    np.testing.assert_array_equal(ost["m_means"][:2], state["m_means"][[0, 3]])
+    assert np.all(ost["v_sh"][2:] == 0)
+
+
+def test_split_offsets_follow_the_rotation():
+    rng = np.random.default_rng(1)
+    raw, act, state = _dstate(1, rng)
+    c = np.float32(np.cos(np.pi / 4))
+    raw["quats"][0] = [c, 0, 0, c]                    # 90 degrees about z
+    raw["log_scales"][0] = np.log(np.float32([0.3, 0.1, 0.1]))
+    act["scales"][0] = np.exp(raw["log_scales"][0].astype(np.float64))
+    normals = np.array([[[1, 0, 0], [0, 0, 2]]], np.float32)
+    out, _, _, n = oracle.densify(raw, act, state, np.float32([1.0]), np.float32([1.0]), np.int32([1]), normals,
+                                  _DCFG)
+    assert n == 2
+    m = raw["means"][0].astype(np.float64)
+    np.testing.assert_allclose(out["means"][0] - m, [0, 0.3, 0], atol=1e-7)  # x axis -> y
+    np.testing.assert_allclose(out["means"][1] - m, [0, 0, 0.2], atol=1e-7)
+
+
+def test_densify_statistics_and_opacity_reset():
+    g2 = np.zeros((3, 12), np.float32)
+    g2[0, :2] = [3.0, 4.0]
+    g2[1, :2] = [1.0, 0.0]
+    accum, count, rmax = np.zeros(3, np.float32), np.zeros(3, np.float32), np.zeros(3, np.int32)
+    oracle.densify_stats(g2, np.int32([7, 0, 2]), 2, 2, accum, count, rmax)  # W/2 = H/2 = 1
+    oracle.densify_stats(g2, np.int32([5, 0, 9]), 2, 2, accum, count, rmax)
+    np.testing.assert_array_equal(accum, [10.0, 0.0, 0.0])
+    np.testing.assert_array_equal(count, [2.0, 0.0, 2.0])
+    np.testing.assert_array_equal(rmax, [7, 0, 9])
+    logits = np.float32([-6.0, -4.0, 0.0, 3.0])
+    out = oracle.reset_opacity(logits, 0.01)
+    cap = np.log(0.01 / 0.99)
+    assert out[0] == logits[0] and out[2] == pytest.approx(cap, rel=1e-6) and out[3] == out[2]
+    assert 1 / (1 + np.exp(-np.float64(out[1]))) == pytest.approx(0.01, rel=1e-6)

@@ -572,6 +572,8 @@ def run_ours(args):
     ts.dssim_lambda = None
     if not args.no_sweep:
         line["kernel_sweep"] = kernel_sweep(ts, step, cam_seq, args.warmup, STAGES, args.kernel)
+    if not args.no_sweep:
+        line["density_control"] = density_control_timing(ts)
     if rank == 0 and not args.no_multiview:
         del ts
         torch.cuda.empty_cache()
@@ -625,6 +627,49 @@ def kernel_sweep(ts, step, cam_seq, first, stages, restore_kernel, steps=20):
     out["generic_half_cosine_xi3_beta1.5"]["psi_device_ms"] = round(psi_ms, 3)
     ts.set_kernel(restore_kernel)
     return out
+
+
+def density_control_timing(ts, reps=5):
+    """Adaptive density control on the training state: the per-step statistics kernel, one
+    clone / split / prune pass (statistics from 20 recorded steps, 3DGS thresholds with a
+    scene extent of 6), and the opacity reset."""
+    import types
+    from paper_2501_12369_gb300 import darb
+    n, dev = ts.n, ts.device
+    accum = torch.zeros(n, dtype=torch.float32, device=dev)
+    count = torch.zeros(n, dtype=torch.float32, device=dev)
+    rmax = torch.zeros(n, dtype=torch.int32, device=dev)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+    e[0].record()
+    for _ in range(20):
+        darb.darb_densify_stats(ts.grad2d, ts.proj.radius, ts.W, ts.H, accum, count, rmax)
+    e[1].record()
+    params = types.SimpleNamespace(means=ts.means, log_scales=ts.log_scales, quats=ts.quats,
+                                   opacity_logits=ts.logits, sh=ts.sh, scales=ts.scales, opacities=ts.opac,
+                                   sh_degree=ts.sh_degree)
+    state = types.SimpleNamespace(**ts.state)
+    out = types.SimpleNamespace(**{k: torch.empty((2 * n,) + tuple(getattr(params, k).shape[1:]),
+                                                  dtype=torch.float32, device=dev)
+                                   for k in ("means", "log_scales", "quats", "opacity_logits", "sh", "scales",
+                                             "opacities")}, sh_degree=ts.sh_degree)
+    out_state = types.SimpleNamespace(**{k: torch.empty((2 * n,) + tuple(v.shape[1:]), dtype=torch.float32,
+                                                        device=dev) for k, v in ts.state.items()})
+    normals = torch.randn(n, 2, 3, device=dev, generator=torch.Generator(device=dev).manual_seed(0))
+    cfg = darb.darb_densify_cfg(2e-4, 0.01 * 6.0, 0.005, 20.0, 0.1 * 6.0, 1.6)
+    n_out = darb.darb_densify(params, state, accum, count, rmax, normals, cfg, out, out_state)  # warm
+    torch.cuda.synchronize()
+    e[2].record()
+    for _ in range(reps):
+        n_out = darb.darb_densify(params, state, accum, count, rmax, normals, cfg, out, out_state)
+    e[3].record()
+    e[4].record()
+    darb.darb_reset_opacity(out, 0.01)
+    e[5].record()
+    torch.cuda.synchronize()
+    rows, c0, k0 = (int(x) for x in n_out.cpu())
+    return {"stats_ms_per_step": e[0].elapsed_time(e[1]) / 20, "densify_ms": e[2].elapsed_time(e[3]) / reps,
+            "splats_in": n, "splats_out": rows, "clones": k0 - c0, "split_children": rows - k0,
+            "survivors": c0, "reset_opacity_ms": e[4].elapsed_time(e[5])}
 
 
 # ----------------------------------------------------------------------------- batched views

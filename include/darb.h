@@ -320,6 +320,48 @@ darb_status darb_preprocess_bwd_adam(const darb_train_params *params, const darb
                                      const float *grad2d, const darb_adam_state *state,
                                      const darb_adam_config *cfg, darb_stream stream);
 
+/* ---- Adaptive density control -----------------------------------------------------------
+ * The paper keeps the 3DGS optimisation pipeline (Sec. 4 block diagram), whose density control
+ * is: per step, statistics of every visible splat; every few hundred steps, clone small splats
+ * with large view-space gradients, split large ones, prune transparent or oversized ones; and a
+ * periodic opacity reset.  All decisions are taken in float32 in a fixed operation order. */
+
+/* One step's statistics, for every splat with radius > 0: accum += |(dmean_x W/2, dmean_y H/2)|
+ * (the view-space mean gradient in normalised device units), count += 1, max_radius =
+ * max(max_radius, radius).  grad2d: device [n][12] from darb_render_bwd; radius: device [n] from
+ * darb_preprocess; accum, count (float), max_radius (int32): device [n], updated in place. */
+darb_status darb_densify_stats(const float *grad2d, const int32_t *radius, int32_t n, int32_t width,
+                               int32_t height, float *accum, float *count, int32_t *max_radius,
+                               darb_stream stream);
+
+typedef struct {
+    float grad_threshold;    /* grow when accum / count >= this (3DGS: 0.0002) */
+    float dense_scale;       /* clone when the largest scale <= this, split above (0.01 x extent) */
+    float min_opacity;       /* prune below (0.005) */
+    float max_screen_radius; /* prune above, pixels; <= 0 disables */
+    float max_world_scale;   /* prune when the largest scale is above; <= 0 disables */
+    float split_scale_div;   /* children's scales = parent's / this (1.6) */
+} darb_densify_cfg;
+
+darb_status darb_densify_workspace_size(int32_t n, size_t *bytes);
+
+/* One density-control pass from `in` (+ its Adam state) into `out` (+ state), which must not
+ * overlap the inputs and must hold capacity >= 2 n rows.  Output rows, in order: the surviving
+ * splats in index order (their moments kept), then the kept clones in parent order, then two
+ * children per kept split parent (moments zero).  Clones and children start with screen radius
+ * 0 for the prune test; children's means are parent + R(q) (s * z) with z = split_normals
+ * [n][2][3] (device, standard normal, caller-drawn), their log-scales the parent's minus
+ * log(split_scale_div).  n_out: device uint32[3] = rows written, first clone row, first child
+ * row.  Asynchronous; statistics of the new set are the caller's to reset. */
+darb_status darb_densify(const darb_train_params *in, const darb_adam_state *in_state, const float *accum,
+                         const float *count, const int32_t *max_radius, const float *split_normals,
+                         const darb_densify_cfg *cfg, void *workspace, size_t workspace_bytes,
+                         int32_t capacity, const darb_train_params *out, const darb_adam_state *out_state,
+                         uint32_t *n_out, darb_stream stream);
+
+/* Opacity reset: logits clamped to logit(max_opacity), activated opacities refreshed. */
+darb_status darb_reset_opacity(const darb_train_params *params, float max_opacity, darb_stream stream);
+
 /* ---- Batched multi-view forward rendering ---------------------------------------------
  * Renders n_views cameras of one splat set: per view, steps 1-3 as darb_preprocess and
  * darb_bin_sort (DARB_SORT_DEPTH_THEN_TILE, asynchronous capacity mode); then step 4 for every

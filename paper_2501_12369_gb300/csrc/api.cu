@@ -241,6 +241,68 @@ darb_status darb_l1_dssim_loss(const float *image, const float *target, int32_t 
     return DARB_OK;
 }
 
+namespace {
+
+bool train_params_complete(const darb_train_params *p) {
+    if (!p || p->n < 0 || p->sh_degree < 0 || p->sh_degree > 3) return false;
+    if (p->n == 0) return true;
+    const void *q[] = {p->means, p->log_scales, p->quats, p->opacity_logits, p->sh, p->scales, p->opacities};
+    for (const void *x : q)
+        if (!x || !aligned16(x)) return false;
+    return true;
+}
+
+bool adam_state_complete(const darb_adam_state *s) {
+    if (!s) return false;
+    const void *q[] = {s->m_means, s->v_means, s->m_scales, s->v_scales, s->m_quats, s->v_quats,
+                       s->m_opac,  s->v_opac,  s->m_sh,     s->v_sh};
+    for (const void *x : q)
+        if (!x) return false;
+    return true;
+}
+
+}  // namespace
+
+darb_status darb_densify_stats(const float *grad2d, const int32_t *radius, int32_t n, int32_t width, int32_t height,
+                               float *accum, float *count, int32_t *max_radius, darb_stream stream) {
+    if (n < 0 || width <= 0 || height <= 0) return DARB_ERR_INVALID_ARG;
+    if (n == 0) return DARB_OK;
+    if (!grad2d || !aligned16(grad2d) || !radius || !accum || !count || !max_radius) return DARB_ERR_INVALID_ARG;
+    DARB_CUDA_TRY(launch_densify_stats(grad2d, radius, n, width, height, accum, count, max_radius,
+                                       reinterpret_cast<cudaStream_t>(stream)));
+    return DARB_OK;
+}
+
+darb_status darb_densify_workspace_size(int32_t n, size_t *bytes) {
+    if (n < 0 || !bytes) return DARB_ERR_INVALID_ARG;
+    *bytes = densify_workspace_bytes(n);
+    return DARB_OK;
+}
+
+darb_status darb_densify(const darb_train_params *in, const darb_adam_state *in_state, const float *accum,
+                         const float *count, const int32_t *max_radius, const float *split_normals,
+                         const darb_densify_cfg *cfg, void *workspace, size_t workspace_bytes, int32_t capacity,
+                         const darb_train_params *out, const darb_adam_state *out_state, uint32_t *n_out,
+                         darb_stream stream) {
+    if (!train_params_complete(in) || !train_params_complete(out) || !adam_state_complete(in_state) ||
+        !adam_state_complete(out_state) || !cfg || !workspace || !n_out || out->sh_degree != in->sh_degree ||
+        capacity < 0 || (int64_t)capacity < 2 * (int64_t)in->n || !(cfg->split_scale_div > 0.0f) ||
+        !std::isfinite(cfg->grad_threshold) || !std::isfinite(cfg->dense_scale))
+        return DARB_ERR_INVALID_ARG;
+    if (in->n > 0 && (!accum || !count || !max_radius || !split_normals)) return DARB_ERR_INVALID_ARG;
+    if (in->means == out->means || in->sh == out->sh || in_state->m_sh == out_state->m_sh) return DARB_ERR_INVALID_ARG;
+    if (workspace_bytes < densify_workspace_bytes(in->n)) return DARB_ERR_WORKSPACE;
+    DARB_CUDA_TRY(launch_densify(*in, *in_state, accum, count, max_radius, split_normals, *cfg, workspace, *out,
+                                 *out_state, n_out, reinterpret_cast<cudaStream_t>(stream)));
+    return DARB_OK;
+}
+
+darb_status darb_reset_opacity(const darb_train_params *params, float max_opacity, darb_stream stream) {
+    if (!train_params_complete(params) || !(max_opacity > 0.0f && max_opacity < 1.0f)) return DARB_ERR_INVALID_ARG;
+    DARB_CUDA_TRY(launch_reset_opacity(*params, max_opacity, reinterpret_cast<cudaStream_t>(stream)));
+    return DARB_OK;
+}
+
 darb_status darb_adam_step(const darb_train_params *params, const darb_splat_grads *grads,
                            const darb_adam_state *state, const darb_adam_config *cfg, darb_stream stream) {
     if (!params || !grads || !state || !cfg || params->n < 0 || params->sh_degree < 0 || params->sh_degree > 3 ||

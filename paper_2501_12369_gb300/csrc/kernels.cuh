@@ -62,6 +62,16 @@ size_t l1_dssim_workspace_bytes(int W, int H);
 cudaError_t launch_l1_dssim(const float *image, const float *target, int W, int H, float lam, void *workspace,
                             float *dL, float *loss, cudaStream_t st);
 
+// density.cu: adaptive density control.
+size_t densify_workspace_bytes(int n);
+cudaError_t launch_densify_stats(const float *grad2d, const int *radius, int n, int W, int H, float *accum,
+                                 float *count, int *max_radius, cudaStream_t st);
+cudaError_t launch_densify(const darb_train_params &in, const darb_adam_state &sin, const float *accum,
+                           const float *count, const int *max_radius, const float *normals,
+                           const darb_densify_cfg &cfg, void *workspace, const darb_train_params &out,
+                           const darb_adam_state &sout, uint32_t *n_out, cudaStream_t st);
+cudaError_t launch_reset_opacity(const darb_train_params &p, float max_opacity, cudaStream_t st);
+
 // binning.cu
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;

@@ -82,6 +82,11 @@ class darb_batch_params(ctypes.Structure):
 DARB_MAX_BATCH_VIEWS = 4096
 
 
+class darb_densify_cfg(ctypes.Structure):
+    _fields_ = [("grad_threshold", c_f32), ("dense_scale", c_f32), ("min_opacity", c_f32),
+                ("max_screen_radius", c_f32), ("max_world_scale", c_f32), ("split_scale_div", c_f32)]
+
+
 class darb_serve_cfg(ctypes.Structure):
     _fields_ = [("scene_bytes", ctypes.c_uint64), ("workspace_bytes", ctypes.c_uint64), ("tile", c_i32),
                 ("max_batch", c_i32), ("depth", c_i32), ("capacity_per_pixel", c_f32),
@@ -131,6 +136,12 @@ SIGNATURES = {
                                                  _P(ctypes.c_size_t)]),
     "darb_render_batch": (c_i32, [_P(darb_splats), _P(darb_camera), _P(darb_kernel_params), _P(darb_batch_params),
                                   c_vp, ctypes.c_size_t, _P(darb_image), c_vp, c_vp, c_vp]),
+    "darb_densify_stats": (c_i32, [c_vp, c_vp, c_i32, c_i32, c_i32, c_vp, c_vp, c_vp, c_vp]),
+    "darb_densify_workspace_size": (c_i32, [c_i32, _P(ctypes.c_size_t)]),
+    "darb_densify": (c_i32, [_P(darb_train_params), _P(darb_adam_state), c_vp, c_vp, c_vp, c_vp,
+                             _P(darb_densify_cfg), c_vp, ctypes.c_size_t, c_i32, _P(darb_train_params),
+                             _P(darb_adam_state), c_vp, c_vp]),
+    "darb_reset_opacity": (c_i32, [_P(darb_train_params), c_f32, c_vp]),
     "darb_serve_create": (c_i32, [_P(darb_serve_cfg), _P(c_vp)]),
     "darb_serve_add_scene": (c_i32, [c_vp, _P(darb_splats), _P(c_i32)]),
     "darb_serve_submit": (c_i32, [c_vp, _P(darb_request), _P(ctypes.c_uint64)]),
@@ -800,4 +811,39 @@ def allreduce_splat_grads(grads: SplatGrads, group=None, average=False):
     if average:
         flat /= dist.get_world_size(group)
     return grads
+
+
+# ---------------------------------------------------------------------------
+# Adaptive density control
+
+def darb_densify_stats(grad2d, radius, width, height, accum, count, max_radius, stream=None):
+    _check(lib().darb_densify_stats(_p(grad2d), _p(radius), int(radius.shape[0]), int(width), int(height), _p(accum),
+                                    _p(count), _p(max_radius), _stream(stream)), "darb_densify_stats")
+
+
+def darb_densify(params, state, accum, count, max_radius, split_normals, cfg: darb_densify_cfg, out_params,
+                 out_state, stream=None):
+    """One clone / split / prune pass from (params, state) into (out_params, out_state), which
+    need 2 n rows; returns the device uint32[3] (rows written, first clone row, first child row)."""
+    n = int(params.means.shape[0])
+    ws = torch.empty(_ws_size(lib().darb_densify_workspace_size, n), dtype=torch.uint8, device=params.means.device)
+    n_out = torch.zeros(3, dtype=torch.int32, device=params.means.device)
+    p_in, s_in = train_params(params), adam_state(state)
+    p_out, s_out = train_params(out_params), adam_state(out_state)
+    p_out.n = int(out_params.means.shape[0])
+    _check(lib().darb_densify(ctypes.byref(p_in), ctypes.byref(s_in), _p(accum), _p(count), _p(max_radius),
+                              _p(split_normals), ctypes.byref(cfg), _p(ws), ws.numel(), int(out_params.means.shape[0]),
+                              ctypes.byref(p_out), ctypes.byref(s_out), _p(n_out), _stream(stream)), "darb_densify")
+    return n_out
+
+
+def _ws_size(fn, *args) -> int:
+    n = ctypes.c_size_t(0)
+    _check(fn(*args, ctypes.byref(n)), fn.__name__)
+    return int(n.value)
+
+
+def darb_reset_opacity(params, max_opacity=0.01, stream=None):
+    p = train_params(params)
+    _check(lib().darb_reset_opacity(ctypes.byref(p), float(max_opacity), _stream(stream)), "darb_reset_opacity")
 

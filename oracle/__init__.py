@@ -221,17 +221,20 @@ def project(splats, cam, kparams, tile=16, geom32=True):
         raise ValueError("orc_project rejected its arguments")
     out["geom32"] = bool(geom32)
     out["opac"] = np.ascontiguousarray(splats.opacities, np.float32)
+    out["q_max"] = float(kparams.q_max)
     return out
 
 
 def build_lists(proj, cam, tile=16, tile_mask=None):
-    """Sorted (tile, depth, id) instances.  Returns keys u64[M], ids i32[M], ranges i32[tiles,2]."""
+    """Sorted (tile, depth, id) instances over every splat's member tiles (the ellipse's row
+    spans).  Returns keys u64[M], ids i32[M], ranges i32[tiles,2]."""
     tx, ty = tiles_xy(cam, tile)
     n = proj["culled"].shape[0]
     mask = None if tile_mask is None else np.ascontiguousarray(tile_mask, np.uint8).reshape(-1)
     L = lib()
-    args = (ctypes.c_int(n), _p(proj["culled"]), _p(proj["rect"]), _p(proj["depth"]), ctypes.c_int(tx),
-            ctypes.c_int(ty), _p(mask))
+    args = (ctypes.c_int(n), _p(proj["culled"]), _p(proj["rect"]), _p(proj["depth"]), _p(proj["mean2d"]),
+            _p(proj["conic"]), ctypes.c_float(proj["q_max"]), ctypes.c_int(int(proj["geom32"])), ctypes.c_int(tile),
+            ctypes.c_int(cam.width), ctypes.c_int(cam.height), ctypes.c_int(tx), ctypes.c_int(ty), _p(mask))
     M = L.orc_build_lists(*args, None, None, ctypes.c_longlong(0), None)
     keys = np.empty(max(M, 1), np.uint64)
     ids = np.empty(max(M, 1), np.int32)

@@ -337,6 +337,76 @@ static void camera_centre(const orc_camera *cam, double c[3])
 }
 
 /* ------------------------------------------------------------------------ */
+/* Tile membership.  A splat's tiles are, row of tiles by row of tiles, those */
+/* whose pixel columns meet the x-extent of its ellipse {q <= q_max} over    */
+/* the row's band of pixel-centre heights: the extent's ends are the         */
+/* ellipse's leftmost and rightmost points, clamped to the band, so every    */
+/* pixel centre with q <= q_max lies in a member tile.  Tiles of the row     */
+/* form one run [c0, c1] inside the rectangle.  The FP32 track takes the     */
+/* fixed IEEE sequence below (the GPU takes the same one), the FP64 track    */
+/* the same formulas in double.                                              */
+
+#define SPAN_BODY(R, SQ, CE, FL, MX, MN)                                                      \
+    const R t1 = A * C, t2 = B * B, det = t1 - t2;                                          \
+    if (!(det > (R)0)) return 0;                                                             \
+    const R xm = SQ((qm * C) / det), ym = SQ((qm * A) / det);                                \
+    const R nB = -B;                                                                        \
+    const R dyR0 = (nB * xm) / C, dyL0 = -dyR0;                                              \
+    const R aq = A * qm;                                                                     \
+    const R ya = (R)(ty * tile) + (R)0.5f;                                                   \
+    const R yb = MN((R)(ty * tile + tile) - (R)0.5f, (R)H - (R)0.5f);                       \
+    const R ea = MX(ya - u1, -ym), eb = MN(yb - u1, ym);                                     \
+    if (!(ea <= eb)) return 0;                                                               \
+    const R dyR = MN(MX(dyR0, ea), eb), dyL = MN(MX(dyL0, ea), eb);                         \
+    const R sR = SQ(MX(aq - det * (dyR * dyR), (R)0));                                       \
+    const R sL = SQ(MX(aq - det * (dyL * dyL), (R)0));                                       \
+    const R right = (nB * dyR + sR) / A, left = (nB * dyL - sL) / A;                         \
+    const R i0 = MX(CE((u0 + left) - (R)0.5f), (R)0);                                        \
+    const R i1 = MN(FL((u0 + right) - (R)0.5f), (R)(W - 1));                                \
+    if (!(i0 <= i1)) return 0;                                                               \
+    int a0 = (int)i0 / tile, a1 = (int)i1 / tile;                                            \
+    if (a0 < r[0]) a0 = r[0];                                                                \
+    if (a1 > r[2]) a1 = r[2];                                                                \
+    if (a0 > a1) return 0;                                                                   \
+    *c0 = a0;                                                                                \
+    *c1 = a1;                                                                                \
+    return 1;
+
+static int span_f32(float u0, float u1, float A, float B, float C, float qm, int tile, int W, int H,
+                    const int *r, int ty, int *c0, int *c1)
+{
+    SPAN_BODY(float, sqrtf, ceilf, floorf, fmaxf, fminf)
+}
+
+static int span_f64(double u0, double u1, double A, double B, double C, double qm, int tile, int W, int H,
+                    const int *r, int ty, int *c0, int *c1)
+{
+    SPAN_BODY(double, sqrt, ceil, floor, fmax, fmin)
+}
+
+/* The run of member tiles of splat i in tile row ty; 0 if none. */
+static int row_span(int geom32, const double *mean2d, const double *conic, int i, float qmax, int tile, int W,
+                    int H, const int *rect, int ty, int *c0, int *c1)
+{
+    const int *r = rect + 4 * (size_t)i;
+    if (ty < r[1] || ty > r[3]) return 0;
+    const double *m = mean2d + 2 * (size_t)i, *k = conic + 3 * (size_t)i;
+    if (geom32)
+        return span_f32((float)m[0], (float)m[1], (float)k[0], (float)k[1], (float)k[2], qmax, tile, W, H, r, ty,
+                        c0, c1);
+    return span_f64(m[0], m[1], k[0], k[1], k[2], (double)qmax, tile, W, H, r, ty, c0, c1);
+}
+
+static int span_count(int geom32, const double *mean2d, const double *conic, int i, float qmax, int tile, int W,
+                      int H, const int *rect)
+{
+    int n = 0, c0, c1;
+    for (int ty = rect[4 * (size_t)i + 1]; ty <= rect[4 * (size_t)i + 3]; ++ty)
+        if (row_span(geom32, mean2d, conic, i, qmax, tile, W, H, rect, ty, &c0, &c1)) n += c1 - c0 + 1;
+    return n;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Per-splat preprocessing.                                                 */
 
 int orc_project(int n, const float *means, const float *scales, const float *quats,
@@ -359,7 +429,7 @@ int orc_project(int n, const float *means, const float *scales, const float *qua
         culled[i] = p.culled;
         radius[i] = p.culled ? 0 : p.radius;
         for (int j = 0; j < 4; ++j) rect[4 * (size_t)i + j] = p.rect[j];
-        tiles[i] = p.culled ? 0 : p.tiles;
+        tiles[i] = 0;
         depth[i] = p.depth;
         clampxy[2 * (size_t)i] = p.clampx;
         clampxy[2 * (size_t)i + 1] = p.clampy;
@@ -387,6 +457,8 @@ int orc_project(int n, const float *means, const float *scales, const float *qua
             rgb[3 * (size_t)i + ch] = v;
         }
         clamped[i] = cl;
+        if (!p.culled)
+            tiles[i] = span_count(geom32, mean2d, conic, i, k->q_max, tile, cam->width, cam->height, rect);
     }
     return 0;
 }
@@ -415,17 +487,21 @@ static uint32_t float_bits(float f)
     return u;
 }
 
-long long orc_build_lists(int n, const int *culled, const int *rect, const float *depth,
+long long orc_build_lists(int n, const int *culled, const int *rect, const float *depth, const double *mean2d,
+                          const double *conic, float qmax, int geom32, int tile, int width, int height,
                           int tiles_x, int tiles_y, const unsigned char *tile_mask,
                           uint64_t *keys, int *ids, long long capacity, int *ranges)
 {
     long long M = 0;
+    int c0, c1;
     for (int i = 0; i < n; ++i) {
         if (culled[i]) continue;
         const int *r = rect + 4 * (size_t)i;
-        for (int ty = r[1]; ty <= r[3]; ++ty)
-            for (int tx = r[0]; tx <= r[2]; ++tx)
+        for (int ty = r[1]; ty <= r[3]; ++ty) {
+            if (!row_span(geom32, mean2d, conic, i, qmax, tile, width, height, rect, ty, &c0, &c1)) continue;
+            for (int tx = c0; tx <= c1; ++tx)
                 if (!tile_mask || tile_mask[ty * tiles_x + tx]) ++M;
+        }
     }
     if (!keys) return M;
     if (M > capacity) return -1;
@@ -435,14 +511,16 @@ long long orc_build_lists(int n, const int *culled, const int *rect, const float
     for (int i = 0; i < n; ++i) {
         if (culled[i]) continue;
         const int *r = rect + 4 * (size_t)i;
-        for (int ty = r[1]; ty <= r[3]; ++ty)
-            for (int tx = r[0]; tx <= r[2]; ++tx) {
+        for (int ty = r[1]; ty <= r[3]; ++ty) {
+            if (!row_span(geom32, mean2d, conic, i, qmax, tile, width, height, rect, ty, &c0, &c1)) continue;
+            for (int tx = c0; tx <= c1; ++tx) {
                 const int t = ty * tiles_x + tx;
                 if (tile_mask && !tile_mask[t]) continue;
                 inst[m].key = ((uint64_t)t << 32) | float_bits(depth[i]);
                 inst[m].id = i;
                 ++m;
             }
+        }
     }
     qsort(inst, (size_t)M, sizeof(instance), cmp_instance);
     for (int t = 0; t < tiles_x * tiles_y; ++t) ranges[2 * t] = ranges[2 * t + 1] = 0;
@@ -470,6 +548,7 @@ typedef struct {
     const int *seq;
     int len;
     int tx, ty;
+    int check_member, tile, W, H; /* brute force: test the splat's tile membership per pixel */
     float px, py;
     double bg[3];
     double eps_a, eps_t;
@@ -486,8 +565,12 @@ typedef struct {
 /* Support test and alpha of splat id at this pixel; 0 if it does not apply. */
 static int eval_alpha(const walk_ctx *c, int id, double *alpha, double *F, double *q)
 {
-    const int *r = c->rect + 4 * (size_t)id;
-    if (c->tx < r[0] || c->tx > r[2] || c->ty < r[1] || c->ty > r[3]) return 0;
+    if (c->check_member) { /* tiled lists hold members only */
+        int c0, c1;
+        if (!row_span(c->geom32, c->mean2d, c->conic, id, c->qmax, c->tile, c->W, c->H, c->rect, c->ty, &c0, &c1) ||
+            c->tx < c0 || c->tx > c1)
+            return 0;
+    }
     double qq;
     if (c->geom32) { /* q by the fixed FP32 sequence: q = dx (A dx + 2B dy) + (C dy) dy */
         const float mx = (float)c->mean2d[2 * (size_t)id], my = (float)c->mean2d[2 * (size_t)id + 1];
@@ -666,6 +749,10 @@ int orc_render(int n, const int *culled, const int *rect, const float *depth,
         c.cap = MAX_OUT;
         c.tx = tx;
         c.ty = ty;
+        c.check_member = mode == 0;
+        c.tile = tile;
+        c.W = W;
+        c.H = H;
         if (mode == 0) {
             c.seq = order;
             c.len = norder;

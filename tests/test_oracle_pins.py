@@ -745,3 +745,42 @@ def test_densify_statistics_and_opacity_reset():
     cap = np.log(0.01 / 0.99)
     assert out[0] == logits[0] and out[2] == pytest.approx(cap, rel=1e-6) and out[3] == out[2]
     assert 1 / (1 + np.exp(-np.float64(out[1]))) == pytest.approx(0.01, rel=1e-6)
+
+
+# --------------------------------------------------------------------------- tile membership (ellipse row spans)
+
+def test_member_tiles_cover_every_pixel_of_the_footprint_and_fewer_than_the_rectangle():
+    """Each splat's member tiles (per tile row, the run that the ellipse's x-extent over the
+    row's band of pixel centres reaches) contain every pixel centre with q <= q_max (q by the
+    FP32 sequence the compositing uses) and lie inside the rectangle; for elongated splats they
+    are far fewer than the rectangle's tiles."""
+    s = synth.uniform_cube_scene(300, seed=6, sh_degree=0, half=1.0, log_scale=(-5.0, -1.5))
+    cam = synth.pinhole((0.2, 0.1, 3.0), 160, 120, 150.0)
+    for tile in (8, 16):
+        for name in ("half_cosine", "raised_cosine"):
+            kp = oracle.kernel_params(name)
+            proj = oracle.project(s, cam, kp, tile, True)
+            lists = oracle.build_lists(proj, cam, tile)
+            tx_n, _ = oracle.tiles_xy(cam, tile)
+            member = set()
+            for t in range(lists["ranges"].shape[0]):
+                a, b = lists["ranges"][t]
+                for i in lists["ids"][a:b]:
+                    member.add((int(i), t))
+            ys, xs = np.mgrid[0:cam.height, 0:cam.width]
+            px, py = (xs + 0.5).astype(np.float32), (ys + 0.5).astype(np.float32)
+            rect_tiles = 0
+            for i in np.flatnonzero(proj["culled"] == 0):
+                r = proj["rect"][i]
+                rect_tiles += (r[2] - r[0] + 1) * (r[3] - r[1] + 1)
+                mx, my = np.float32(proj["mean2d"][i])
+                A, B, C = np.float32(proj["conic"][i])
+                dx, dy = mx - px, my - py
+                g = A * dx + (np.float32(2) * B) * dy
+                q = dx * g + (C * dy) * dy
+                inside = q <= np.float32(kp.q_max)
+                for t in set(((ys[inside] // tile) * tx_n + xs[inside] // tile).tolist()):
+                    assert (int(i), t) in member, (name, tile, i, t)
+                    assert r[1] <= t // tx_n <= r[3] and r[0] <= t % tx_n <= r[2]
+            assert lists["M"] == int(proj["tiles"].sum())
+            assert lists["M"] < 0.8 * rect_tiles

@@ -229,7 +229,8 @@ class TrainStep:
         d._check(self.L.darb_preprocess(ctypes.byref(self.s_splats), c, self.kp_ref, self.tile,
                                         ctypes.byref(self.s_proj), st), "preprocess")
         m = ctypes.c_uint64(0)
-        r = self.L.darb_bin_sort(ctypes.byref(self.s_proj), self.n, self.tile, c, d._p(self.ws), self.ws_bytes,
+        r = self.L.darb_bin_sort(ctypes.byref(self.s_proj), self.n, self.tile, c, self.kp_ref, d._p(self.ws),
+                                 self.ws_bytes,
                                  self.capacity, self.strategy, ctypes.byref(self.s_bins), ctypes.byref(m), st)
         if r not in (0, 3):
             d._check(r, "bin_sort")
@@ -245,7 +246,8 @@ class TrainStep:
         d._check(L.darb_preprocess(ctypes.byref(self.s_splats), c, self.kp_ref, self.tile, ctypes.byref(self.s_proj),
                                    st), "preprocess")
         rec(1)
-        d._check(L.darb_bin_sort(ctypes.byref(self.s_proj), self.n, self.tile, c, d._p(self.ws), self.ws_bytes,
+        d._check(L.darb_bin_sort(ctypes.byref(self.s_proj), self.n, self.tile, c, self.kp_ref, d._p(self.ws),
+                                 self.ws_bytes,
                                  self.capacity, self.strategy, ctypes.byref(self.s_bins), None, st), "bin_sort")
         rec(2)
         d._check(L.darb_render_fwd(ctypes.byref(self.s_proj), ctypes.byref(self.s_bins), c, self.kp_ref, self.tile,
@@ -719,7 +721,8 @@ def run_multiview(device, kernel="half_cosine", reps=10):
         for c, pr, ws, cap, sb, im, _ in views:
             darb._check(L.darb_preprocess(ctypes.byref(sp), ctypes.byref(c), ctypes.byref(kp), tile, ctypes.byref(pr),
                                           st), "preprocess")
-            darb._check(L.darb_bin_sort(ctypes.byref(pr), sd.n, tile, ctypes.byref(c), darb._p(ws), ws.numel(), cap,
+            darb._check(L.darb_bin_sort(ctypes.byref(pr), sd.n, tile, ctypes.byref(c), ctypes.byref(kp), darb._p(ws),
+                                        ws.numel(), cap,
                                         0, ctypes.byref(sb), None, st), "bin_sort")
             darb._check(L.darb_render_fwd(ctypes.byref(pr), ctypes.byref(sb), ctypes.byref(c), ctypes.byref(kp), tile,
                                           ctypes.byref(im), st), "render_fwd")

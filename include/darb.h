@@ -136,7 +136,7 @@ typedef struct {
 /* Outputs of darb_bin_sort, device pointers.
  * keys [capacity], values [capacity]: the (splat, tile) instances sorted by
  * key = tile << 32 | bits(depth), ties by splat index; values hold splat indices.
- * ranges [tiles_y * tiles_x][2]: [start, end) of each tile's run in values.
+ * ranges [tiles_y * tiles_x][2]: [start, end) of each tile's run in values; [0, 0) if empty.
  * num_instances [1]: M, the number of instances (written even when M > capacity).
  * status [1]: 0, or a darb_status the device detected (DARB_ERR_CAPACITY, DARB_ERR_TIMEOUT). */
 typedef struct {
@@ -213,7 +213,8 @@ darb_status darb_bin_sort_workspace_size(int32_t n, int32_t tile, const darb_cam
  * sized by capacity, and an overflow is reported in out->status with every tile range
  * left empty (so a following darb_render_fwd draws only the background). */
 darb_status darb_bin_sort(const darb_projected *proj, int32_t n, int32_t tile,
-                          const darb_camera *cam, void *workspace, size_t workspace_bytes,
+                          const darb_camera *cam, const darb_kernel_params *kparams,
+                          void *workspace, size_t workspace_bytes,
                           uint64_t capacity, int32_t strategy, const darb_binning *out,
                           uint64_t *num_instances_host, darb_stream stream);
 
@@ -231,7 +232,8 @@ darb_status darb_bin_sort(const darb_projected *proj, int32_t n, int32_t tile,
  * streams, or two host threads) race and must be serialised by the caller.  Other arguments and
  * results are those of darb_bin_sort. */
 darb_status darb_bin_sort_noalloc(const darb_projected *proj, int32_t n, int32_t tile,
-                                  const darb_camera *cam, uint64_t capacity, const darb_binning *out,
+                                  const darb_camera *cam, const darb_kernel_params *kparams,
+                                  uint64_t capacity, const darb_binning *out,
                                   uint64_t *num_instances_host, darb_stream stream);
 
 /* Step 4: per-pixel front-to-back compositing (Sec. 4.1, "alpha blending ... similar to

@@ -346,21 +346,23 @@ static void camera_centre(const orc_camera *cam, double c[3])
 /* fixed IEEE sequence below (the GPU takes the same one), the FP64 track    */
 /* the same formulas in double.                                              */
 
+/* Per splat: det, the extents, 1/A and the x offsets at the unclamped extreme heights; per row: */
+/* the band, the clamped heights (the cached offsets where unclamped), the run.                 */
 #define SPAN_BODY(R, SQ, CE, FL, MX, MN)                                                      \
-    const R t1 = A * C, t2 = B * B, det = t1 - t2;                                          \
+    const R det = A * C - B * B;                                                             \
     if (!(det > (R)0)) return 0;                                                             \
     const R xm = SQ((qm * C) / det), ym = SQ((qm * A) / det);                                \
-    const R nB = -B;                                                                        \
+    const R nB = -B;                                                                         \
     const R dyR0 = (nB * xm) / C, dyL0 = -dyR0;                                              \
     const R aq = A * qm;                                                                     \
+    const R invA = (R)1 / A;                                                                 \
     const R ya = (R)(ty * tile) + (R)0.5f;                                                   \
     const R yb = MN((R)(ty * tile + tile) - (R)0.5f, (R)H - (R)0.5f);                       \
     const R ea = MX(ya - u1, -ym), eb = MN(yb - u1, ym);                                     \
     if (!(ea <= eb)) return 0;                                                               \
     const R dyR = MN(MX(dyR0, ea), eb), dyL = MN(MX(dyL0, ea), eb);                         \
-    const R sR = SQ(MX(aq - det * (dyR * dyR), (R)0));                                       \
-    const R sL = SQ(MX(aq - det * (dyL * dyL), (R)0));                                       \
-    const R right = (nB * dyR + sR) / A, left = (nB * dyL - sL) / A;                         \
+    const R right = (nB * dyR + SQ(MX(aq - det * (dyR * dyR), (R)0))) * invA;                \
+    const R left = (nB * dyL - SQ(MX(aq - det * (dyL * dyL), (R)0))) * invA;                 \
     const R i0 = MX(CE((u0 + left) - (R)0.5f), (R)0);                                        \
     const R i1 = MN(FL((u0 + right) - (R)0.5f), (R)(W - 1));                                \
     if (!(i0 <= i1)) return 0;                                                               \
@@ -457,8 +459,13 @@ int orc_project(int n, const float *means, const float *scales, const float *qua
             rgb[3 * (size_t)i + ch] = v;
         }
         clamped[i] = cl;
-        if (!p.culled)
+        if (!p.culled) { /* a splat whose ellipse reaches no tile is culled, like an empty rectangle */
             tiles[i] = span_count(geom32, mean2d, conic, i, k->q_max, tile, cam->width, cam->height, rect);
+            if (tiles[i] == 0) {
+                culled[i] = 1;
+                radius[i] = 0;
+            }
+        }
     }
     return 0;
 }

@@ -121,7 +121,7 @@ darb_status darb_preprocess(const darb_splats *splats, const darb_camera *cam, c
         return DARB_ERR_INVALID_ARG;
     if (splats->n == 0) return DARB_OK;
     if (!valid_projected(out)) return DARB_ERR_INVALID_ARG;
-    DARB_CUDA_TRY(launch_preprocess(splats->n, *splats, make_cam(*cam), kparams->psi, tile, as_out(out),
+    DARB_CUDA_TRY(launch_preprocess(splats->n, *splats, make_cam(*cam), kparams->psi, tile, kparams->q_max, as_out(out),
                                     reinterpret_cast<cudaStream_t>(stream)));
     return DARB_OK;
 }
@@ -138,10 +138,11 @@ darb_status darb_bin_sort_workspace_size(int32_t n, int32_t tile, const darb_cam
 }
 
 darb_status darb_bin_sort(const darb_projected *proj, int32_t n, int32_t tile, const darb_camera *cam,
-                          void *workspace, size_t workspace_bytes, uint64_t capacity, int32_t strategy,
-                          const darb_binning *out, uint64_t *num_instances_host, darb_stream stream) {
-    if (n < 0 || !valid_tile(tile) || !valid_camera(cam) || capacity > kMaxCapacity || !out ||
-        !valid_strategy(strategy))
+                          const darb_kernel_params *kparams, void *workspace, size_t workspace_bytes,
+                          uint64_t capacity, int32_t strategy, const darb_binning *out, uint64_t *num_instances_host,
+                          darb_stream stream) {
+    if (n < 0 || !valid_tile(tile) || !valid_camera(cam) || !valid_kernel(kparams) || capacity > kMaxCapacity ||
+        !out || !valid_strategy(strategy))
         return DARB_ERR_INVALID_ARG;
     if (!out->ranges || !out->num_instances || !out->status || !aligned16(out->ranges)) return DARB_ERR_INVALID_ARG;
     const bool need_keys = strategy == DARB_SORT_KEYS64;
@@ -158,10 +159,13 @@ darb_status darb_bin_sort(const darb_projected *proj, int32_t n, int32_t tile, c
         pin.radius = proj->radius;
         pin.tile_rect = reinterpret_cast<const int4 *>(proj->tile_rect);
         pin.tiles_touched = proj->tiles_touched;
+        pin.mean2d = reinterpret_cast<const float2 *>(proj->mean2d);
+        pin.conic_o = reinterpret_cast<const float4 *>(proj->conic_o);
     }
     const BinOut bo{out->keys, out->values, out->ranges, out->num_instances, out->status};
     bool exceeded = false;
-    DARB_CUDA_TRY(launch_bin_sort(n, pin, tiles_x, tiles_y, capacity, strategy, workspace, bo,
+    const SpanCtx sc{kparams->q_max, tile, cam->width, cam->height};
+    DARB_CUDA_TRY(launch_bin_sort(n, pin, tiles_x, tiles_y, sc, capacity, strategy, workspace, bo,
                                   num_instances_host, &exceeded, reinterpret_cast<cudaStream_t>(stream)));
     return exceeded ? DARB_ERR_CAPACITY : DARB_OK;
 }

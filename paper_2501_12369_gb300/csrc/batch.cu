@@ -224,17 +224,21 @@ darb_status darb_render_batch(const darb_splats *splats, const darb_camera *cams
         unsigned char *vb = w + L.views + L.per_view * (size_t)v;
         const ProjectedOut po = view_projected(vb, n);
         const Cam cam = make_cam(cams[v]);
-        if (launch_preprocess(n, *splats, cam, kparams->psi, tile, po, ss) != cudaSuccess) return DARB_ERR_CUDA;
+        if (launch_preprocess(n, *splats, cam, kparams->psi, tile, kparams->q_max, po, ss) != cudaSuccess)
+            return DARB_ERR_CUDA;
         ProjectedIn pin{};
         pin.depth = po.depth;
         pin.radius = po.radius;
         pin.tile_rect = po.tile_rect;
         pin.tiles_touched = po.tiles_touched;
+        pin.mean2d = po.mean2d;
+        pin.conic_o = po.conic_o;
         const BinOut bo{nullptr, reinterpret_cast<uint32_t *>(vb + L.values_off),
                         reinterpret_cast<uint32_t *>(vb + L.ranges_off), counts + v, stats + v};
         bool exceeded = false;
         const int tx = tile_count(cams[v].width, tile), ty = tile_count(cams[v].height, tile);
-        if (launch_bin_sort(n, pin, tx, ty, bp->capacity, DARB_SORT_DEPTH_THEN_TILE, w + L.slots + L.per_slot * s, bo,
+        const SpanCtx sc{kparams->q_max, tile, cams[v].width, cams[v].height};
+        if (launch_bin_sort(n, pin, tx, ty, sc, bp->capacity, DARB_SORT_DEPTH_THEN_TILE, w + L.slots + L.per_slot * s, bo,
                             nullptr, &exceeded, ss) != cudaSuccess)
             return DARB_ERR_CUDA;
     }

@@ -200,7 +200,8 @@ __device__ __forceinline__ int owner_of(const uint32_t *s_off, int nloc, uint32_
 // 64-bit keys in splat order (strategy KEYS64).
 __global__ void __launch_bounds__(kScanThreads)
 k_duplicate(int n, const uint32_t *__restrict__ tiles, const unsigned long long *__restrict__ block_offsets,
-            const int4 *__restrict__ rect, const float *__restrict__ depth, int tiles_x,
+            const int4 *__restrict__ rect, const float2 *__restrict__ mean2d, const float4 *__restrict__ conic_o,
+            SpanCtx sc, const float *__restrict__ depth, int tiles_x,
             unsigned long long capacity, uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
     __shared__ uint32_t s_off[kScanTile + 1];
     __shared__ uint32_t s_warp[kScanThreads / 32 + 1];
@@ -211,10 +212,9 @@ k_duplicate(int n, const uint32_t *__restrict__ tiles, const unsigned long long 
     for (uint32_t k = threadIdx.x; k < total; k += kScanThreads) {
         const int s = owner_of(s_off, nloc, k);
         const uint32_t l = k - s_off[s];
-        const int4 r = __ldg(rect + base + s);
-        const int w = r.z - r.x + 1;
-        const int ty = r.y + (int)(l / (uint32_t)w), tx = r.x + (int)(l % (uint32_t)w);
-        const uint64_t key = ((uint64_t)(uint32_t)(ty * tiles_x + tx) << 32) | __float_as_uint(__ldg(depth + base + s));
+        const uint32_t t = instance_tile(__ldg(mean2d + base + s), __ldg(conic_o + base + s), __ldg(rect + base + s), l,
+                                         tiles_x, sc);
+        const uint64_t key = ((uint64_t)t << 32) | __float_as_uint(__ldg(depth + base + s));
         const unsigned long long dst = gbase + k;
         if (dst < capacity) {
             keys[dst] = key;
@@ -262,6 +262,55 @@ __device__ __forceinline__ int cta_upper_owner(const uint32_t *__restrict__ offs
     return *s_res;
 }
 
+// The instances [lo, hi) of one partition, owner by owner (owners first .. first + count - 1 in
+// depth order): the thread that takes an owner computes its ellipse's row runs once and, at the
+// first position of every run inside the partition (clipped to lo), records the run's tile id
+// at that position and the splat id and sets the position's bit in `mark` (cleared by the
+// caller).  Every instance then finds its run start in `mark` without recomputing the ellipse.
+template <int NT>
+__device__ __forceinline__ void partition_runs(int first, int count, uint32_t lo, uint32_t hi,
+                                               const uint32_t *__restrict__ offs, const uint32_t *__restrict__ order,
+                                               const int4 *__restrict__ rect, const float2 *__restrict__ mean2d,
+                                               const float4 *__restrict__ conic_o, const SpanCtx &sc, int tiles_x,
+                                               uint32_t *s_base, uint32_t *s_val, uint32_t *mark) {
+    for (int o = threadIdx.x; o < count; o += NT) {
+        uint32_t j = offs[first + o];
+        const uint32_t id = order[first + o];
+        const float2 mu = __ldg(mean2d + id);
+        const float4 co = __ldg(conic_o + id);
+        const int4 r = __ldg(rect + id);
+        const SpanSplat p = span_prepare(mu.x, mu.y, co.x, co.y, co.z, sc.qmax);
+        for (int ty = r.y; ty <= r.w && j < hi; ++ty) {
+            int c0, c1;
+            if (!span_row(p, sc, r, ty, c0, c1)) continue;
+            const uint32_t w = (uint32_t)(c1 - c0 + 1);
+            if (j + w > lo) {
+                const uint32_t q = max(j, lo), pos = q - lo;
+                s_base[pos] = (uint32_t)(ty * tiles_x + c0) + (q - j);
+                s_val[pos] = id;
+                atomicOr(&mark[pos >> 5], 1u << (pos & 31));
+            }
+            j += w;
+        }
+    }
+}
+
+// Tile id and splat id of partition position pos, from the nearest run start at or before it.
+__device__ __forceinline__ void partition_lookup(uint32_t pos, const uint32_t *s_base, const uint32_t *s_val,
+                                                 const uint32_t *mark, uint32_t &key, uint32_t &val) {
+    int w = (int)(pos >> 5);
+    uint32_t m = mark[w] & (0xffffffffu >> (31 - (pos & 31)));
+    while (m == 0 && w > 0) m = mark[--w];
+    if (m == 0) {  // unreachable: position 0 always starts a run
+        key = 0xffffffffu;
+        val = 0;
+        return;
+    }
+    const uint32_t q = (uint32_t)w * 32 + 31 - __clz(m);
+    key = s_base[q] + (pos - q);
+    val = s_val[q];
+}
+
 // 32-bit tile ids in depth order (strategy DEPTH_THEN_TILE), balanced over instances: CTA c
 // emits instances [c * kDupTile, (c + 1) * kDupTile).  Lane-major order within each warp's
 // chunk keeps the writes coalesced.
@@ -270,11 +319,13 @@ __device__ __forceinline__ int cta_upper_owner(const uint32_t *__restrict__ offs
 // ph[d * n_parts + partition].
 __global__ void __launch_bounds__(kScanThreads)
 k_duplicate_balanced(int n, const uint32_t *__restrict__ order, const uint32_t *__restrict__ offs,
-                     const int4 *__restrict__ rect, int tiles_x, const uint32_t *__restrict__ num,
+                     const int4 *__restrict__ rect, const float2 *__restrict__ mean2d,
+                     const float4 *__restrict__ conic_o, SpanCtx sc, int tiles_x, const uint32_t *__restrict__ num,
                      unsigned long long cap, uint32_t *__restrict__ keys, uint32_t *__restrict__ vals, int bits1,
                      uint32_t n_parts, uint32_t *__restrict__ ph) {
-    __shared__ uint32_t s_off[kDupTile + 1];
-    __shared__ uint32_t s_id[kDupTile];
+    __shared__ uint32_t s_base[kDupTile];
+    __shared__ uint32_t s_val[kDupTile];
+    __shared__ uint32_t s_mark[kDupTile / 32];
     __shared__ uint32_t s_h[256];
     __shared__ int s_res[2];
     const unsigned long long Mfull = *num;
@@ -283,6 +334,7 @@ k_duplicate_balanced(int n, const uint32_t *__restrict__ order, const uint32_t *
     const uint32_t lo = blockIdx.x * (uint32_t)kDupTile;
     const uint32_t radix1 = 1u << bits1, mask1 = radix1 - 1u;
     for (int i = threadIdx.x; i < 256; i += kScanThreads) s_h[i] = 0;
+    for (int i = threadIdx.x; i < kDupTile / 32; i += kScanThreads) s_mark[i] = 0;
     if (lo >= M) {  // an empty partition (capacity-sized grid): zero histogram
         for (uint32_t d = threadIdx.x; d < radix1; d += kScanThreads) ph[(size_t)d * n_parts + blockIdx.x] = 0;
         return;
@@ -291,48 +343,17 @@ k_duplicate_balanced(int n, const uint32_t *__restrict__ order, const uint32_t *
     const int first = cta_upper_owner(offs, n, lo, &s_res[0]);
     const int last = cta_upper_owner(offs, n, hi - 1, &s_res[1]);
     const int count = min(last - first + 1, kDupTile);  // every owner has >= 1 instance
-    for (int i = threadIdx.x; i <= count; i += kScanThreads) {
-        s_off[i] = offs[first + i];
-        if (i < count) s_id[i] = order[first + i];
-    }
+    partition_runs<kScanThreads>(first, count, lo, hi, offs, order, rect, mean2d, conic_o, sc, tiles_x, s_base, s_val,
+                                 s_mark);
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t wbase = lo + (uint32_t)warp * (32 * kDupItems);
-    int s = 0;
-    {  // owner of this lane's first instance
-        const uint32_t k0 = min(wbase + lane, hi - 1);
-        int a = 0, b = count - 1;
-        while (a < b) {
-            const int mid = (a + b + 1) >> 1;
-            if (s_off[mid] <= k0) a = mid;
-            else b = mid - 1;
-        }
-        s = a;
-    }
 #pragma unroll 4
     for (int it = 0; it < kDupItems; ++it) {
         const uint32_t k = wbase + it * 32 + lane;
         if (k >= hi) break;
-        if (s_off[min(s + 8, count)] <= k) {  // far ahead: binary search the rest
-            int a = s, b = count - 1;
-            while (a < b) {
-                const int mid = (a + b + 1) >> 1;
-                if (s_off[mid] <= k) a = mid;
-                else b = mid - 1;
-            }
-            s = a;
-        } else {
-            while (s_off[s + 1] <= k) ++s;
-        }
-        const uint32_t id = s_id[s];
-        const uint32_t l = k - s_off[s];
-        const int4 r = __ldg(rect + id);
-        const uint32_t w = (uint32_t)(r.z - r.x + 1);
-        // row = l / w: float estimate, then exact integer correction
-        uint32_t row = __float2uint_rz(__fdividef((float)l, (float)w));
-        while (row * w > l) --row;
-        while ((row + 1) * w <= l) ++row;
-        const uint32_t tile = ((uint32_t)r.y + row) * (uint32_t)tiles_x + (uint32_t)r.x + (l - row * w);
+        uint32_t tile, id;
+        partition_lookup(k - lo, s_base, s_val, s_mark, tile, id);
         keys[k] = tile;
         vals[k] = id;
         atomicAdd(&s_h[tile & mask1], 1u);  // neighbouring lanes hold neighbouring tiles: few conflicts
@@ -341,14 +362,17 @@ k_duplicate_balanced(int n, const uint32_t *__restrict__ order, const uint32_t *
     for (uint32_t d = threadIdx.x; d < radix1; d += kScanThreads) ph[(size_t)d * n_parts + blockIdx.x] = s_h[d];
 }
 
-// Tile coverage as a 2D difference array: +1 / -1 at the four corners of each visible splat's
-// tile rectangle, so that a 2D prefix sum gives the number of instances of every tile.  With
+// Tile coverage as a row-wise difference array: +1 at the first and -1 past the last member
+// tile of each row run of each visible splat, so that prefix sums along the rows give the
+// number of instances of every tile.  The splats are order[0, *n_vis) when the visible ones
+// have been compacted (order and n_vis given), else all n with the culled ones skipped.  With
 // SMEM each CTA accumulates a private copy in shared memory (grid-stride over splats) and adds
 // its non-zero entries to the global array once.
 template <bool SMEM>
 __global__ void __launch_bounds__(1024)
-k_tile_diff(int n, const int *__restrict__ radius, const int4 *__restrict__ rect, int tiles_x, int diff_size,
-            int *__restrict__ diff) {
+k_tile_diff(int n, const uint32_t *__restrict__ order, const uint32_t *__restrict__ n_vis,
+            const int *__restrict__ radius, const int4 *__restrict__ rect, const float2 *__restrict__ mean2d,
+            const float4 *__restrict__ conic_o, SpanCtx sc, int tiles_x, int diff_size, int *__restrict__ diff) {
     extern __shared__ int s_diff[];
     int *d = SMEM ? s_diff : diff;
     if (SMEM) {
@@ -356,13 +380,20 @@ k_tile_diff(int n, const int *__restrict__ radius, const int4 *__restrict__ rect
         __syncthreads();
     }
     const int w1 = tiles_x + 1;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int m = n_vis ? (int)min(*n_vis, (uint32_t)n) : n;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) {
+        const int i = order ? (int)order[k] : k;
         if (radius[i] == 0) continue;
         const int4 r = rect[i];
-        atomicAdd(&d[r.y * w1 + r.x], 1);
-        atomicAdd(&d[r.y * w1 + r.z + 1], -1);
-        atomicAdd(&d[(r.w + 1) * w1 + r.x], -1);
-        atomicAdd(&d[(r.w + 1) * w1 + r.z + 1], 1);
+        const float2 mu = mean2d[i];
+        const float4 co = conic_o[i];
+        const SpanSplat sp = span_prepare(mu.x, mu.y, co.x, co.y, co.z, sc.qmax);
+        for (int ty = r.y; ty <= r.w; ++ty) {  // one run of member tiles per row: +1 at c0, -1 after c1
+            int c0, c1;
+            if (!span_row(sp, sc, r, ty, c0, c1)) continue;
+            atomicAdd(&d[ty * w1 + c0], 1);
+            atomicAdd(&d[ty * w1 + c1 + 1], -1);
+        }
     }
     if (SMEM) {
         __syncthreads();
@@ -408,8 +439,8 @@ __global__ void __launch_bounds__(256) k_hist_scan(const uint32_t *__restrict__ 
 
 // Per-tile instance counts (2D prefix of the difference array) -> ranges [start, end) and the
 // digit bases of the tile passes.  One CTA.  After a capacity overflow every range is empty.
-// One CTA: 2D prefix sums of the difference array (a warp per row, then a warp per column, in
-// shared memory when `counts` is a shared-memory array) give the per-tile instance counts, then
+// One CTA: prefix sums of the per-row difference array (a warp per row, in shared memory when
+// it fits) give the per-tile instance counts, then
 // their exclusive scan gives the ranges and a histogram of each tile-pass digit the passes'
 // digit bases.  With SMEM the difference array is staged into shared memory first.
 template <bool SMEM>
@@ -448,21 +479,7 @@ k_tile_setup(int tiles_x, int tiles_y, const int *__restrict__ diff_g, uint32_t 
         }
     }
     __syncthreads();
-    for (int x = warp; x < tiles_x; x += 32) {  // prefix along y
-        uint32_t carry = 0;
-        for (int y0 = 0; y0 < tiles_y; y0 += 32) {
-            const int y = y0 + lane;
-            uint32_t v = y < tiles_y ? counts[y * tiles_x + x] : 0u;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t u = __shfl_up_sync(0xffffffffu, v, o);
-                if (lane >= o) v += u;
-            }
-            if (y < tiles_y) counts[y * tiles_x + x] = carry + v;
-            carry += __shfl_sync(0xffffffffu, v, 31);
-        }
-    }
-    __syncthreads();
+
     const bool overflow = (unsigned long long)*num > capacity;
     unsigned long long carry = 0;
     for (int chunk = 0; chunk < n_tiles; chunk += 1024) {
@@ -471,8 +488,9 @@ k_tile_setup(int tiles_x, int tiles_y, const int *__restrict__ diff_g, uint32_t 
         unsigned long long total;
         const unsigned long long ex = carry + block_exclusive_scan<1024>((unsigned long long)c, s_warp, total);
         if (t < n_tiles) {
-            ranges[2 * (size_t)t] = overflow ? 0u : (uint32_t)ex;
-            ranges[2 * (size_t)t + 1] = overflow ? 0u : (uint32_t)(ex + c);
+            // an empty tile's run is [0, 0), as the other strategy and the oracle write it
+            ranges[2 * (size_t)t] = (overflow || c == 0) ? 0u : (uint32_t)ex;
+            ranges[2 * (size_t)t + 1] = (overflow || c == 0) ? 0u : (uint32_t)(ex + c);
             if (c) {
 #pragma unroll
                 for (int p = 0; p < kMaxPasses; ++p)
@@ -701,11 +719,11 @@ struct Staging {
 };
 
 // Dynamic shared memory of the fused duplicate + first pass: the staging arrays, which also
-// hold the partition's owner offsets (kDupTile + 1) and splat ids (kDupTile) while the
+// hold the partition's run starts (tile ids, splat ids and the kDupTile-bit mark) while the
 // instances are generated.
 template <bool WRITE_KEYS>
 struct DupStaging {
-    static constexpr size_t owners = (size_t)(2 * kDupTile + 1) * 4;
+    static constexpr size_t owners = (size_t)(2 * kDupTile + kDupTile / 32) * 4;
     static constexpr size_t bytes = Staging<uint32_t, WRITE_KEYS>::bytes > owners ? Staging<uint32_t, WRITE_KEYS>::bytes
                                                                                    : owners;
 };
@@ -844,8 +862,10 @@ __device__ __forceinline__ void sweep_partition(SweepSmem &sm, unsigned char *sm
             d = s_d[j];
         }
         const uint32_t dst = sm.gbase[d] + (j - sm.cta_excl[d]);
-        if (WRITE_KEYS) kout[dst] = kk;
-        vout[dst] = s_v[j];
+        if (dst < M) {  // always true for consistent digit bases; guards the buffers if they are not
+            if (WRITE_KEYS) kout[dst] = kk;
+            vout[dst] = s_v[j];
+        }
     }
 }
 
@@ -891,7 +911,8 @@ k_onesweep(const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__res
 template <bool WRITE_KEYS>
 __global__ void __launch_bounds__(kSortThreads, kSortCtasPerSm)
 k_dup_sweep(int n, const uint32_t *__restrict__ order, const uint32_t *__restrict__ offs,
-            const int4 *__restrict__ rect, int tiles_x, const uint32_t *num, unsigned long long cap, int bits,
+            const int4 *__restrict__ rect, const float2 *__restrict__ mean2d, const float4 *__restrict__ conic_o,
+            SpanCtx sc, int tiles_x, const uint32_t *num, unsigned long long cap, int bits,
             const uint32_t *__restrict__ digit_base, uint32_t *lookback, uint32_t *part_counter, uint32_t *status,
             uint32_t *__restrict__ kout, uint32_t *__restrict__ vout) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -902,60 +923,30 @@ k_dup_sweep(int n, const uint32_t *__restrict__ order, const uint32_t *__restric
     const uint32_t n_parts = (M + kSortTile - 1) / kSortTile;
     if (part >= n_parts) return;
     const uint32_t lo = part * kSortTile, hi = min(M, lo + (uint32_t)kSortTile);
-    uint32_t *s_off = reinterpret_cast<uint32_t *>(smem);
-    uint32_t *s_id = s_off + kDupTile + 1;
+    uint32_t *s_base = reinterpret_cast<uint32_t *>(smem);
+    uint32_t *s_val = s_base + kDupTile;
+    uint32_t *s_mark = s_val + kDupTile;
+    for (int i = threadIdx.x; i < kDupTile / 32; i += kSortThreads) s_mark[i] = 0;
     const int first = cta_upper_owner(offs, n, lo, &sm.res[0]);
     const int last = cta_upper_owner(offs, n, hi - 1, &sm.res[1]);
     const int count = min(last - first + 1, kDupTile);  // every owner has >= 1 instance
-    for (int i = threadIdx.x; i <= count; i += kSortThreads) {
-        s_off[i] = offs[first + i];
-        if (i < count) s_id[i] = order[first + i];
-    }
+    partition_runs<kSortThreads>(first, count, lo, hi, offs, order, rect, mean2d, conic_o, sc, tiles_x, s_base, s_val,
+                                 s_mark);
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t wbase = lo + (uint32_t)warp * (32 * kSortItems);
-    int s = 0;
-    {  // owner of this lane's first instance
-        const uint32_t k0 = min(wbase + lane, hi - 1);
-        int a = 0, b = count - 1;
-        while (a < b) {
-            const int mid = (a + b + 1) >> 1;
-            if (s_off[mid] <= k0) a = mid;
-            else b = mid - 1;
-        }
-        s = a;
-    }
     uint32_t kk[kSortItems], vv[kSortItems];
 #pragma unroll
     for (int it = 0; it < kSortItems; ++it) {
         const uint32_t j = wbase + it * 32 + lane;
-        if (j >= hi) {
+        if (j < hi) {
+            partition_lookup(j - lo, s_base, s_val, s_mark, kk[it], vv[it]);
+        } else {
             kk[it] = 0xffffffffu;
             vv[it] = 0;
-            continue;
         }
-        if (s_off[min(s + 8, count)] <= j) {  // far ahead: binary search the rest
-            int a = s, b = count - 1;
-            while (a < b) {
-                const int mid = (a + b + 1) >> 1;
-                if (s_off[mid] <= j) a = mid;
-                else b = mid - 1;
-            }
-            s = a;
-        } else {
-            while (s_off[s + 1] <= j) ++s;
-        }
-        const uint32_t id = s_id[s];
-        const uint32_t l = j - s_off[s];
-        const int4 r = __ldg(rect + id);
-        const uint32_t w = (uint32_t)(r.z - r.x + 1);
-        // row = l / w: float estimate, then exact integer correction
-        uint32_t row = __float2uint_rz(__fdividef((float)l, (float)w));
-        while (row * w > l) --row;
-        while ((row + 1) * w <= l) ++row;
-        kk[it] = ((uint32_t)r.y + row) * (uint32_t)tiles_x + (uint32_t)r.x + (l - row * w);
-        vv[it] = id;
     }
+    __syncthreads();  // the staging arrays below reuse the run starts' memory
     sweep_partition<uint32_t, WRITE_KEYS>(sm, smem, kk, vv, part, lo, M, 0, bits, digit_base, lookback, status, kout,
                                           vout);
 }
@@ -1168,7 +1159,8 @@ size_t sort_workspace_bytes(int n, uint64_t capacity, int tiles_x, int tiles_y, 
     return layout(n, capacity, tiles_x, tiles_y, strategy, sort_tile_bits(tiles_x * tiles_y)).total;
 }
 
-cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int tiles_y, uint64_t capacity,
+cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int tiles_y, const SpanCtx &sc,
+                            uint64_t capacity,
                             int strategy, void *workspace, const BinOut &out, uint64_t *num_instances_host,
                             bool *capacity_exceeded, cudaStream_t st) {
     const int n_tiles = tiles_x * tiles_y;
@@ -1215,7 +1207,8 @@ cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int til
         uint64_t *kb = (passes % 2 == 0) ? reinterpret_cast<uint64_t *>(at(0)) : out.keys;
         uint32_t *vb = (passes % 2 == 0) ? reinterpret_cast<uint32_t *>(at(1)) : out.values;
         if (nb > 0)
-            k_duplicate<<<nb, kScanThreads, 0, st>>>(n, proj.tiles_touched, block_off, proj.tile_rect, proj.depth,
+            k_duplicate<<<nb, kScanThreads, 0, st>>>(n, proj.tiles_touched, block_off, proj.tile_rect, proj.mean2d,
+                                                     proj.conic_o, sc, proj.depth,
                                                      tiles_x, cap, ka, va);
         if (grid == 0) return cudaGetLastError();
         PassSpec ps{};
@@ -1247,6 +1240,7 @@ cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int til
     uint32_t *kbuf[2] = {reinterpret_cast<uint32_t *>(at(4)), reinterpret_cast<uint32_t *>(at(4)) + n};
     uint32_t *vbuf[2] = {reinterpret_cast<uint32_t *>(at(5)), reinterpret_cast<uint32_t *>(at(5)) + n};
     const uint32_t *order = nullptr;  // sorted splat ids
+    const uint32_t *n_vis_dev = nullptr;  // visible count, when order starts with exactly the visible splats
     uint32_t *sums = reinterpret_cast<uint32_t *>(at(17));
     if (n > 0) {
         const PassSpec dps = split_bits(32);
@@ -1261,6 +1255,7 @@ cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int til
             k_depth_compact<<<nb, kScanThreads, 0, st>>>(n, proj.radius, proj.depth, block_off, nv, kbuf[0], vbuf[0],
                                                           vbuf[1]);
             n_vis = nv;
+            n_vis_dev = nv;
             vin = vbuf[0];
             uint32_t *dhist = reinterpret_cast<uint32_t *>(at(10)) + kMaxPasses * 256;
             const int hb = std::min((n + 255) / 256, 152 * 8);
@@ -1327,10 +1322,13 @@ cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int til
         if (smem <= kMaxDiffSmem) {
             TRY(cudaFuncSetAttribute(k_tile_diff<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             const int blocks = std::min((n + 1023) / 1024, 2 * 152);
-            k_tile_diff<true><<<blocks, 1024, smem, st>>>(n, proj.radius, proj.tile_rect, tiles_x, diff_size, diff);
+            k_tile_diff<true><<<blocks, 1024, smem, st>>>(n, n_vis_dev ? order : nullptr, n_vis_dev, proj.radius,
+                                                          proj.tile_rect, proj.mean2d, proj.conic_o, sc, tiles_x,
+                                                          diff_size, diff);
         } else {
-            k_tile_diff<false><<<(n + 1023) / 1024, 1024, 0, st>>>(n, proj.radius, proj.tile_rect, tiles_x, diff_size,
-                                                                    diff);
+            k_tile_diff<false><<<(n + 1023) / 1024, 1024, 0, st>>>(n, n_vis_dev ? order : nullptr, n_vis_dev,
+                                                                    proj.radius, proj.tile_rect, proj.mean2d,
+                                                                    proj.conic_o, sc, tiles_x, diff_size, diff);
         }
     }
     {
@@ -1363,12 +1361,14 @@ cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int til
         const size_t smem = last0 ? DupStaging<false>::bytes : DupStaging<true>::bytes;
         if (last0) {
             TRY(cudaFuncSetAttribute(k_dup_sweep<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            k_dup_sweep<false><<<n_parts, kSortThreads, smem, st>>>(n, order, offs, proj.tile_rect, tiles_x,
+            k_dup_sweep<false><<<n_parts, kSortThreads, smem, st>>>(n, order, offs, proj.tile_rect, proj.mean2d,
+                                                                    proj.conic_o, sc, tiles_x,
                                                                     out.num_instances, cap, tps.bits[0], tbase, lb,
                                                                     counters, out.status, k0, v0);
         } else {
             TRY(cudaFuncSetAttribute(k_dup_sweep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            k_dup_sweep<true><<<n_parts, kSortThreads, smem, st>>>(n, order, offs, proj.tile_rect, tiles_x,
+            k_dup_sweep<true><<<n_parts, kSortThreads, smem, st>>>(n, order, offs, proj.tile_rect, proj.mean2d,
+                                                                   proj.conic_o, sc, tiles_x,
                                                                    out.num_instances, cap, tps.bits[0], tbase, lb,
                                                                    counters, out.status, k0, v0);
         }
@@ -1390,7 +1390,8 @@ cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int til
     } else if (grid > 0) {
         // reduce-then-scan passes: the duplication also writes the first pass's histograms
         if (n > 0)
-            k_duplicate_balanced<<<n_parts, kScanThreads, 0, st>>>(n, order, offs, proj.tile_rect, tiles_x,
+            k_duplicate_balanced<<<n_parts, kScanThreads, 0, st>>>(n, order, offs, proj.tile_rect, proj.mean2d,
+                                                                   proj.conic_o, sc, tiles_x,
                                                                    out.num_instances, cap, tk_a, tv_a, tps.bits[0],
                                                                    n_parts, tph);
         else

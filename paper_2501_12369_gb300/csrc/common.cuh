@@ -194,6 +194,92 @@ template <> __device__ __forceinline__ float kernel_dF<DARB_GENERIC>(float q, co
     return generic_base_du(ks.base, u) * ks.half_beta * u / qq;
 }
 
+// ---------------------------------------------------------------------------
+// Tile membership: per row of tiles, the run [c0, c1] that the x-extent of the splat's ellipse
+// {q <= q_max} over the row's band of pixel-centre heights reaches -- the ellipse's leftmost and
+// rightmost points clamped to the band -- inside the rectangle r.  Every pixel centre with
+// q <= q_max lies in a member tile.  Fixed IEEE FP32 sequence (no contraction): the oracle
+// takes the same operations, so both sides build the same lists.
+struct SpanCtx {
+    float qmax;
+    int tile, W, H;
+};
+
+// Per-splat part of the sequence: the ellipse's extents, 1/A and its leftmost / rightmost x
+// offsets at the unclamped extreme heights (rows whose band contains an extreme reuse them).
+struct SpanSplat {
+    float u0, u1, nB, det, ym, dyR0, dyL0, aq, invA, rR, rL;
+    bool ok;
+};
+
+__device__ __forceinline__ SpanSplat span_prepare(float u0, float u1, float A, float B, float C, float qm) {
+    SpanSplat p;
+    p.u0 = u0;
+    p.u1 = u1;
+    p.det = __fsub_rn(__fmul_rn(A, C), __fmul_rn(B, B));
+    p.ok = p.det > 0.0f;
+    const float xm = __fsqrt_rn(__fdiv_rn(__fmul_rn(qm, C), p.det));
+    p.ym = __fsqrt_rn(__fdiv_rn(__fmul_rn(qm, A), p.det));
+    p.nB = -B;
+    p.dyR0 = __fdiv_rn(__fmul_rn(p.nB, xm), C);
+    p.dyL0 = -p.dyR0;
+    p.aq = __fmul_rn(A, qm);
+    p.invA = __fdiv_rn(1.0f, A);
+    p.rR = __fmul_rn(__fadd_rn(__fmul_rn(p.nB, p.dyR0),
+                               __fsqrt_rn(fmaxf(__fsub_rn(p.aq, __fmul_rn(p.det, __fmul_rn(p.dyR0, p.dyR0))), 0.0f))),
+                     p.invA);
+    p.rL = __fmul_rn(__fsub_rn(__fmul_rn(p.nB, p.dyL0),
+                               __fsqrt_rn(fmaxf(__fsub_rn(p.aq, __fmul_rn(p.det, __fmul_rn(p.dyL0, p.dyL0))), 0.0f))),
+                     p.invA);
+    return p;
+}
+
+__device__ __forceinline__ bool span_row(const SpanSplat &p, const SpanCtx &sc, const int4 &r, int ty, int &c0,
+                                         int &c1) {
+    if (!p.ok) return false;
+    const float ya = __fadd_rn((float)(ty * sc.tile), 0.5f);
+    const float yb = fminf(__fsub_rn((float)(ty * sc.tile + sc.tile), 0.5f), __fsub_rn((float)sc.H, 0.5f));
+    const float ea = fmaxf(__fsub_rn(ya, p.u1), -p.ym), eb = fminf(__fsub_rn(yb, p.u1), p.ym);
+    if (!(ea <= eb)) return false;
+    const float dyR = fminf(fmaxf(p.dyR0, ea), eb), dyL = fminf(fmaxf(p.dyL0, ea), eb);
+    const float right =
+        dyR == p.dyR0
+            ? p.rR
+            : __fmul_rn(__fadd_rn(__fmul_rn(p.nB, dyR),
+                                  __fsqrt_rn(fmaxf(__fsub_rn(p.aq, __fmul_rn(p.det, __fmul_rn(dyR, dyR))), 0.0f))),
+                        p.invA);
+    const float left =
+        dyL == p.dyL0
+            ? p.rL
+            : __fmul_rn(__fsub_rn(__fmul_rn(p.nB, dyL),
+                                  __fsqrt_rn(fmaxf(__fsub_rn(p.aq, __fmul_rn(p.det, __fmul_rn(dyL, dyL))), 0.0f))),
+                        p.invA);
+    const float i0 = fmaxf(ceilf(__fsub_rn(__fadd_rn(p.u0, left), 0.5f)), 0.0f);
+    const float i1 = fminf(floorf(__fsub_rn(__fadd_rn(p.u0, right), 0.5f)), (float)(sc.W - 1));
+    if (!(i0 <= i1)) return false;
+    c0 = max((int)i0 / sc.tile, r.x);
+    c1 = min((int)i1 / sc.tile, r.z);
+    return c0 <= c1;
+}
+
+// Member tiles of a splat in row-major order: the tile of its l-th instance (l below its count).
+__device__ __forceinline__ uint32_t instance_tile_p(const SpanSplat &p, const int4 &r, uint32_t l, int tiles_x,
+                                                    const SpanCtx &sc) {
+    for (int ty = r.y; ty <= r.w; ++ty) {
+        int c0, c1;
+        if (!span_row(p, sc, r, ty, c0, c1)) continue;
+        const uint32_t w = (uint32_t)(c1 - c0 + 1);
+        if (l < w) return (uint32_t)(ty * tiles_x + c0) + l;
+        l -= w;
+    }
+    return 0xffffffffu;  // unreachable for l below the count
+}
+
+__device__ __forceinline__ uint32_t instance_tile(float2 mu, float4 co, const int4 &r, uint32_t l, int tiles_x,
+                                                  const SpanCtx &sc) {
+    return instance_tile_p(span_prepare(mu.x, mu.y, co.x, co.y, co.z, sc.qmax), r, l, tiles_x, sc);
+}
+
 // The support test on q: 0 <= q <= q_max (q < q_max when strict).
 __device__ __forceinline__ bool in_support(float q, float qmax, bool strict) {
     return q >= 0.0f && (strict ? q < qmax : q <= qmax);

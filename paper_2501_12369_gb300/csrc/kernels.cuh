@@ -21,7 +21,7 @@ struct GradOut {
 };
 
 // preprocess.cu
-cudaError_t launch_preprocess(int n, const darb_splats &sp, const Cam &cam, float psi, int tile,
+cudaError_t launch_preprocess(int n, const darb_splats &sp, const Cam &cam, float psi, int tile, float qmax,
                               const ProjectedOut &out, cudaStream_t st);
 cudaError_t launch_preprocess_bwd(int n, const darb_splats &sp, const Cam &cam, float psi,
                                   const int *radius, const uint8_t *clamped, const float *grad2d,
@@ -86,6 +86,8 @@ struct ProjectedIn {
     const int *radius;
     const int4 *tile_rect;
     const uint32_t *tiles_touched;
+    const float2 *mean2d;   // with conic_o: the ellipse whose row spans give the member tiles
+    const float4 *conic_o;
 };
 
 struct BinOut {
@@ -100,7 +102,8 @@ int sort_tile_bits(int n_tiles);
 size_t sort_workspace_bytes(int n, uint64_t capacity, int tiles_x, int tiles_y, int strategy);
 // Enqueues the whole bin/sort.  With num_instances_host non-null it synchronises once after the
 // scan; if M exceeds the capacity it sets *capacity_exceeded and enqueues nothing more.
-cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int tiles_y, uint64_t capacity,
+cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int tiles_y, const SpanCtx &sc,
+                            uint64_t capacity,
                             int strategy, void *workspace, const BinOut &out, uint64_t *num_instances_host,
                             bool *capacity_exceeded, cudaStream_t st);
 

@@ -40,7 +40,8 @@ darb_status scratch_address(void **ptr) {
 }  // namespace
 
 extern "C" darb_status darb_bin_sort_noalloc(const darb_projected *proj, int32_t n, int32_t tile,
-                                             const darb_camera *cam, uint64_t capacity, const darb_binning *out,
+                                             const darb_camera *cam, const darb_kernel_params *kparams,
+                                             uint64_t capacity, const darb_binning *out,
                                              uint64_t *num_instances_host, darb_stream stream) {
     size_t need = 0;
     const darb_status qs = darb_bin_sort_workspace_size(n, tile, cam, capacity, DARB_SORT_DEPTH_THEN_TILE, &need);
@@ -49,6 +50,6 @@ extern "C" darb_status darb_bin_sort_noalloc(const darb_projected *proj, int32_t
     void *scratch = nullptr;
     const darb_status as = scratch_address(&scratch);
     if (as != DARB_OK) return as;
-    return darb_bin_sort(proj, n, tile, cam, scratch, kNoAllocScratchBytes, capacity, DARB_SORT_DEPTH_THEN_TILE, out,
+    return darb_bin_sort(proj, n, tile, cam, kparams, scratch, kNoAllocScratchBytes, capacity, DARB_SORT_DEPTH_THEN_TILE, out,
                          num_instances_host, stream);
 }

@@ -254,14 +254,24 @@ template <int DEG>
 __global__ void __launch_bounds__(256)
 k_preprocess(int n, const float *__restrict__ means, const float *__restrict__ scales,
              const float4 *__restrict__ quats, const float *__restrict__ opac,
-             const float *__restrict__ sh, Cam cam, float psi, int tile, ProjectedOut out) {
+             const float *__restrict__ sh, Cam cam, float psi, int tile, float qmax, ProjectedOut out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float m[3] = {__ldg(means + 3 * (size_t)i), __ldg(means + 3 * (size_t)i + 1), __ldg(means + 3 * (size_t)i + 2)};
     const float s[3] = {__ldg(scales + 3 * (size_t)i), __ldg(scales + 3 * (size_t)i + 1), __ldg(scales + 3 * (size_t)i + 2)};
     const float4 qr = __ldg(quats + i);
     Geom g;
-    if (!project_fixed(m, s, qr, cam, psi, tile, g)) {
+    uint32_t cnt = 0;  // member tiles: the ellipse's run in every row of the rectangle
+    if (project_fixed(m, s, qr, cam, psi, tile, g)) {
+        const SpanCtx sc{qmax, tile, cam.W, cam.H};
+        const int4 r = make_int4(g.rect[0], g.rect[1], g.rect[2], g.rect[3]);
+        const SpanSplat sp = span_prepare(g.u0, g.u1, g.A, g.B, g.C, qmax);
+        for (int ty = r.y; ty <= r.w; ++ty) {
+            int c0, c1;
+            if (span_row(sp, sc, r, ty, c0, c1)) cnt += (uint32_t)(c1 - c0 + 1);
+        }
+    }
+    if (cnt == 0) {  // culled, or an ellipse that reaches no tile
         out.radius[i] = 0;
         out.tiles_touched[i] = 0;
         out.tile_rect[i] = make_int4(0, 0, 0, 0);
@@ -271,7 +281,7 @@ k_preprocess(int n, const float *__restrict__ means, const float *__restrict__ s
     out.depth[i] = g.t[2];
     out.radius[i] = g.radius;
     out.tile_rect[i] = make_int4(g.rect[0], g.rect[1], g.rect[2], g.rect[3]);
-    out.tiles_touched[i] = (uint32_t)((g.rect[2] - g.rect[0] + 1) * (g.rect[3] - g.rect[1] + 1));
+    out.tiles_touched[i] = cnt;
     out.mean2d[i] = make_float2(g.u0, g.u1);
     out.conic_o[i] = make_float4(g.A, g.B, g.C, __ldg(opac + i));
 
@@ -641,16 +651,16 @@ k_preprocess_bwd_adam(int n, darb_train_params P, darb_adam_state A, AdamConsts 
 
 // ---------------------------------------------------------------------------
 
-cudaError_t launch_preprocess(int n, const darb_splats &sp, const Cam &cam, float psi, int tile,
+cudaError_t launch_preprocess(int n, const darb_splats &sp, const Cam &cam, float psi, int tile, float qmax,
                               const ProjectedOut &out, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
     const int threads = 256, blocks = (n + threads - 1) / threads;
     const float4 *q = reinterpret_cast<const float4 *>(sp.quats);
     switch (sp.sh_degree) {
-    case 0: k_preprocess<0><<<blocks, threads, 0, st>>>(n, sp.means, sp.scales, q, sp.opacities, sp.sh, cam, psi, tile, out); break;
-    case 1: k_preprocess<1><<<blocks, threads, 0, st>>>(n, sp.means, sp.scales, q, sp.opacities, sp.sh, cam, psi, tile, out); break;
-    case 2: k_preprocess<2><<<blocks, threads, 0, st>>>(n, sp.means, sp.scales, q, sp.opacities, sp.sh, cam, psi, tile, out); break;
-    default: k_preprocess<3><<<blocks, threads, 0, st>>>(n, sp.means, sp.scales, q, sp.opacities, sp.sh, cam, psi, tile, out); break;
+    case 0: k_preprocess<0><<<blocks, threads, 0, st>>>(n, sp.means, sp.scales, q, sp.opacities, sp.sh, cam, psi, tile, qmax, out); break;
+    case 1: k_preprocess<1><<<blocks, threads, 0, st>>>(n, sp.means, sp.scales, q, sp.opacities, sp.sh, cam, psi, tile, qmax, out); break;
+    case 2: k_preprocess<2><<<blocks, threads, 0, st>>>(n, sp.means, sp.scales, q, sp.opacities, sp.sh, cam, psi, tile, qmax, out); break;
+    default: k_preprocess<3><<<blocks, threads, 0, st>>>(n, sp.means, sp.scales, q, sp.opacities, sp.sh, cam, psi, tile, qmax, out); break;
     }
     return cudaGetLastError();
 }

@@ -114,9 +114,11 @@ SIGNATURES = {
                                 _P(darb_projected), c_vp]),
     "darb_bin_sort_workspace_size": (c_i32, [c_i32, c_i32, _P(darb_camera), ctypes.c_uint64, c_i32,
                                              _P(ctypes.c_size_t)]),
-    "darb_bin_sort": (c_i32, [_P(darb_projected), c_i32, c_i32, _P(darb_camera), c_vp, ctypes.c_size_t,
+    "darb_bin_sort": (c_i32, [_P(darb_projected), c_i32, c_i32, _P(darb_camera), _P(darb_kernel_params), c_vp,
+                              ctypes.c_size_t,
                               ctypes.c_uint64, c_i32, _P(darb_binning), _P(ctypes.c_uint64), c_vp]),
-    "darb_bin_sort_noalloc": (c_i32, [_P(darb_projected), c_i32, c_i32, _P(darb_camera), ctypes.c_uint64,
+    "darb_bin_sort_noalloc": (c_i32, [_P(darb_projected), c_i32, c_i32, _P(darb_camera), _P(darb_kernel_params),
+                                      ctypes.c_uint64,
                                       _P(darb_binning), _P(ctypes.c_uint64), c_vp]),
     "darb_render_fwd": (c_i32, [_P(darb_projected), _P(darb_binning), _P(darb_camera), _P(darb_kernel_params),
                                 c_i32, _P(darb_image), c_vp]),
@@ -347,10 +349,12 @@ class ImageOut:
 # Entry points
 
 def darb_preprocess(splats: SplatTensors, cam, kparams, tile=16, out: Projected | None = None, stream=None):
+    """The projected records; they remember `kparams` (the sort needs its q_max)."""
     out = Projected.empty(splats.n, splats.means.device) if out is None else out
     sp, c, o = splats.struct(), camera(cam), out.struct()
     _check(lib().darb_preprocess(ctypes.byref(sp), ctypes.byref(c), ctypes.byref(kparams), int(tile), ctypes.byref(o),
                                  _stream(stream)), "darb_preprocess")
+    out.kparams = kparams
     return out
 
 
@@ -366,13 +370,15 @@ def darb_bin_sort_workspace_size(n, tile, cam, capacity, strategy=DARB_SORT_DEPT
 
 
 def darb_bin_sort(proj: Projected, n, tile, cam, workspace: torch.Tensor, capacity, out: Binning | None = None,
-                  sync=True, stream=None, strategy=DARB_SORT_DEPTH_THEN_TILE):
-    """sync=True reads M back (one stream synchronisation) and sizes the sort by it."""
+                  sync=True, stream=None, strategy=DARB_SORT_DEPTH_THEN_TILE, kparams=None):
+    """sync=True reads M back (one stream synchronisation) and sizes the sort by it.  kparams:
+    the kernel the records were projected with (default: the one darb_preprocess recorded)."""
     tx, ty = darb_tile_grid(cam, tile)
     out = Binning.empty(capacity, tx * ty, workspace.device) if out is None else out
     pr, c, b = proj.struct(), camera(cam), out.struct()
+    kp = proj.kparams if kparams is None else kparams
     m = ctypes.c_uint64(0)
-    st = lib().darb_bin_sort(ctypes.byref(pr), int(n), int(tile), ctypes.byref(c), _p(workspace),
+    st = lib().darb_bin_sort(ctypes.byref(pr), int(n), int(tile), ctypes.byref(c), ctypes.byref(kp), _p(workspace),
                              workspace.numel() * workspace.element_size(), int(capacity), int(strategy),
                              ctypes.byref(b), ctypes.byref(m) if sync else None, _stream(stream))
     out.M = int(m.value) if sync else None
@@ -381,13 +387,15 @@ def darb_bin_sort(proj: Projected, n, tile, cam, workspace: torch.Tensor, capaci
 
 
 def darb_bin_sort_noalloc(proj: Projected, n, tile, cam, capacity, out: Binning | None = None, sync=True,
-                          stream=None):
+                          stream=None, kparams=None):
     """darb_bin_sort with the library's static device scratch instead of a caller workspace."""
     tx, ty = darb_tile_grid(cam, tile)
     out = Binning.empty(capacity, tx * ty, proj.depth.device) if out is None else out
     pr, c, b = proj.struct(), camera(cam), out.struct()
+    kp = proj.kparams if kparams is None else kparams
     m = ctypes.c_uint64(0)
-    st = lib().darb_bin_sort_noalloc(ctypes.byref(pr), int(n), int(tile), ctypes.byref(c), int(capacity),
+    st = lib().darb_bin_sort_noalloc(ctypes.byref(pr), int(n), int(tile), ctypes.byref(c), ctypes.byref(kp),
+                                     int(capacity),
                                      ctypes.byref(b), ctypes.byref(m) if sync else None, _stream(stream))
     out.M = int(m.value) if sync else None
     _check(st, "darb_bin_sort_noalloc")
@@ -679,7 +687,8 @@ class BatchRenderer:
             bins = Binning.empty(1, tx * ty, self.device)
             pr, cc, b = proj.struct(), camera(c), bins.struct()
             m = ctypes.c_uint64(0)
-            st = lib().darb_bin_sort(ctypes.byref(pr), self.splats.n, self.tile, ctypes.byref(cc), _p(ws),
+            st = lib().darb_bin_sort(ctypes.byref(pr), self.splats.n, self.tile, ctypes.byref(cc),
+                                     ctypes.byref(self.kparams), _p(ws),
                                      ws.numel(), 1, DARB_SORT_DEPTH_THEN_TILE, ctypes.byref(b), ctypes.byref(m),
                                      _stream())
             if st not in (0, 3):

@@ -346,8 +346,10 @@ static void camera_centre(const orc_camera *cam, double c[3])
 /* fixed IEEE sequence below (the GPU takes the same one), the FP64 track    */
 /* the same formulas in double.                                              */
 
-/* Per splat: det, the extents, 1/A and the x offsets at the unclamped extreme heights; per row: */
-/* the band, the clamped heights (the cached offsets where unclamped), the run.                 */
+/* Per splat: det, the extents and 1/A; per row: the band, the heights of the ellipse's         */
+/* rightmost and leftmost points clamped to it, the x offsets there and the run.  At the        */
+/* unclamped heights dyR0 = -B xm / C and -dyR0 the offsets are exactly xm and -xm (substitute  */
+/* dyR0 into the root), and are taken as such.                                                  */
 #define SPAN_BODY(R, SQ, CE, FL, MX, MN)                                                      \
     const R det = A * C - B * B;                                                             \
     if (!(det > (R)0)) return 0;                                                             \
@@ -361,8 +363,8 @@ static void camera_centre(const orc_camera *cam, double c[3])
     const R ea = MX(ya - u1, -ym), eb = MN(yb - u1, ym);                                     \
     if (!(ea <= eb)) return 0;                                                               \
     const R dyR = MN(MX(dyR0, ea), eb), dyL = MN(MX(dyL0, ea), eb);                         \
-    const R right = (nB * dyR + SQ(MX(aq - det * (dyR * dyR), (R)0))) * invA;                \
-    const R left = (nB * dyL - SQ(MX(aq - det * (dyL * dyL), (R)0))) * invA;                 \
+    const R right = dyR == dyR0 ? xm : (nB * dyR + SQ(MX(aq - det * (dyR * dyR), (R)0))) * invA; \
+    const R left = dyL == dyL0 ? -xm : (nB * dyL - SQ(MX(aq - det * (dyL * dyL), (R)0))) * invA; \
     const R i0 = MX(CE((u0 + left) - (R)0.5f), (R)0);                                        \
     const R i1 = MN(FL((u0 + right) - (R)0.5f), (R)(W - 1));                                \
     if (!(i0 <= i1)) return 0;                                                               \

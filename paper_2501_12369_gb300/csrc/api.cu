@@ -164,7 +164,7 @@ darb_status darb_bin_sort(const darb_projected *proj, int32_t n, int32_t tile, c
     }
     const BinOut bo{out->keys, out->values, out->ranges, out->num_instances, out->status};
     bool exceeded = false;
-    const SpanCtx sc{kparams->q_max, tile, cam->width, cam->height};
+    const SpanCtx sc = make_span_ctx(kparams->q_max, tile, cam->width, cam->height);
     DARB_CUDA_TRY(launch_bin_sort(n, pin, tiles_x, tiles_y, sc, capacity, strategy, workspace, bo,
                                   num_instances_host, &exceeded, reinterpret_cast<cudaStream_t>(stream)));
     return exceeded ? DARB_ERR_CAPACITY : DARB_OK;

@@ -237,7 +237,7 @@ darb_status darb_render_batch(const darb_splats *splats, const darb_camera *cams
                         reinterpret_cast<uint32_t *>(vb + L.ranges_off), counts + v, stats + v};
         bool exceeded = false;
         const int tx = tile_count(cams[v].width, tile), ty = tile_count(cams[v].height, tile);
-        const SpanCtx sc{kparams->q_max, tile, cams[v].width, cams[v].height};
+        const SpanCtx sc = make_span_ctx(kparams->q_max, tile, cams[v].width, cams[v].height);
         if (launch_bin_sort(n, pin, tx, ty, sc, bp->capacity, DARB_SORT_DEPTH_THEN_TILE, w + L.slots + L.per_slot * s, bo,
                             nullptr, &exceeded, ss) != cudaSuccess)
             return DARB_ERR_CUDA;

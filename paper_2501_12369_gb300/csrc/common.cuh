@@ -203,10 +203,19 @@ template <> __device__ __forceinline__ float kernel_dF<DARB_GENERIC>(float q, co
 struct SpanCtx {
     float qmax;
     int tile, W, H;
+    int shift;  // log2(tile): tiles are 8, 16 or 32 pixels
 };
+
+__host__ __device__ inline SpanCtx make_span_ctx(float qmax, int tile, int W, int H) {
+    int shift = 0;
+    while ((1 << shift) < tile) ++shift;
+    return SpanCtx{qmax, tile, W, H, shift};
+}
 
 // Per-splat part of the sequence: the ellipse's extents, 1/A and its leftmost / rightmost x
 // offsets at the unclamped extreme heights (rows whose band contains an extreme reuse them).
+// At the height dyR0 = -B xm / C of its rightmost point the ellipse's x-extent is exactly xm
+// (substitute dyR0 into the root below), so rR = xm and rL = -xm.
 struct SpanSplat {
     float u0, u1, nB, det, ym, dyR0, dyL0, aq, invA, rR, rL;
     bool ok;
@@ -225,20 +234,16 @@ __device__ __forceinline__ SpanSplat span_prepare(float u0, float u1, float A, f
     p.dyL0 = -p.dyR0;
     p.aq = __fmul_rn(A, qm);
     p.invA = __fdiv_rn(1.0f, A);
-    p.rR = __fmul_rn(__fadd_rn(__fmul_rn(p.nB, p.dyR0),
-                               __fsqrt_rn(fmaxf(__fsub_rn(p.aq, __fmul_rn(p.det, __fmul_rn(p.dyR0, p.dyR0))), 0.0f))),
-                     p.invA);
-    p.rL = __fmul_rn(__fsub_rn(__fmul_rn(p.nB, p.dyL0),
-                               __fsqrt_rn(fmaxf(__fsub_rn(p.aq, __fmul_rn(p.det, __fmul_rn(p.dyL0, p.dyL0))), 0.0f))),
-                     p.invA);
+    p.rR = xm;
+    p.rL = -xm;
     return p;
 }
 
 __device__ __forceinline__ bool span_row(const SpanSplat &p, const SpanCtx &sc, const int4 &r, int ty, int &c0,
                                          int &c1) {
     if (!p.ok) return false;
-    const float ya = __fadd_rn((float)(ty * sc.tile), 0.5f);
-    const float yb = fminf(__fsub_rn((float)(ty * sc.tile + sc.tile), 0.5f), __fsub_rn((float)sc.H, 0.5f));
+    const float ya = __fadd_rn((float)(ty << sc.shift), 0.5f);
+    const float yb = fminf(__fsub_rn((float)((ty + 1) << sc.shift), 0.5f), __fsub_rn((float)sc.H, 0.5f));
     const float ea = fmaxf(__fsub_rn(ya, p.u1), -p.ym), eb = fminf(__fsub_rn(yb, p.u1), p.ym);
     if (!(ea <= eb)) return false;
     const float dyR = fminf(fmaxf(p.dyR0, ea), eb), dyL = fminf(fmaxf(p.dyL0, ea), eb);
@@ -257,8 +262,8 @@ __device__ __forceinline__ bool span_row(const SpanSplat &p, const SpanCtx &sc, 
     const float i0 = fmaxf(ceilf(__fsub_rn(__fadd_rn(p.u0, left), 0.5f)), 0.0f);
     const float i1 = fminf(floorf(__fsub_rn(__fadd_rn(p.u0, right), 0.5f)), (float)(sc.W - 1));
     if (!(i0 <= i1)) return false;
-    c0 = max((int)i0 / sc.tile, r.x);
-    c1 = min((int)i1 / sc.tile, r.z);
+    c0 = max((int)i0 >> sc.shift, r.x);  // i0, i1 >= 0
+    c1 = min((int)i1 >> sc.shift, r.z);
     return c0 <= c1;
 }
 

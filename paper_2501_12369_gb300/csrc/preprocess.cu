@@ -263,7 +263,7 @@ k_preprocess(int n, const float *__restrict__ means, const float *__restrict__ s
     Geom g;
     uint32_t cnt = 0;  // member tiles: the ellipse's run in every row of the rectangle
     if (project_fixed(m, s, qr, cam, psi, tile, g)) {
-        const SpanCtx sc{qmax, tile, cam.W, cam.H};
+        const SpanCtx sc = make_span_ctx(qmax, tile, cam.W, cam.H);
         const int4 r = make_int4(g.rect[0], g.rect[1], g.rect[2], g.rect[3]);
         const SpanSplat sp = span_prepare(g.u0, g.u1, g.A, g.B, g.C, qmax);
         for (int ty = r.y; ty <= r.w; ++ty) {

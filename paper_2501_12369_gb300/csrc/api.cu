@@ -1,8 +1,17 @@
 // The C ABI of libdarb.so (declared in include/darb.h): argument validation, workspace
 // carving and kernel launches.  No entry point here allocates device memory.
 #include <algorithm>
+#include <cstdlib>
 
 #include "validate.h"
+
+bool darb::pdl_enabled() {
+    static const bool on = [] {
+        const char *e = std::getenv("DARB_PDL");
+        return !(e && e[0] == '0');
+    }();
+    return on;
+}
 
 using namespace darb;
 

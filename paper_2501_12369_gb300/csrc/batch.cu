@@ -31,6 +31,7 @@ struct Blob {
 // Copies parameter bytes to device memory: host data reaches the device through kernel
 // parameters, which stream capture records by value (no host buffer must outlive the call).
 __global__ void k_upload(uint32_t *__restrict__ dst, int n_words, Blob blob) {
+    pdl_entry();
     for (int i = threadIdx.x; i < n_words; i += blockDim.x) dst[i] = blob.words[i];
 }
 
@@ -209,7 +210,7 @@ darb_status darb_render_batch(const darb_splats *splats, const darb_camera *cams
         Blob blob;
         const int cnt = std::min(kBlobWords, words - o);
         std::copy(src + o, src + o + cnt, blob.words);
-        k_upload<<<1, 256, 0, st>>>(reinterpret_cast<uint32_t *>(desc) + o, cnt, blob);
+        launch_k(k_upload, 1, 256, 0, st, reinterpret_cast<uint32_t *>(desc) + o, cnt, blob);
     }
     if (cudaGetLastError() != cudaSuccess) return DARB_ERR_CUDA;
 

@@ -123,6 +123,7 @@ struct PassSpec {
 // Per-CTA sums of tiles_touched over kScanTile positions; order (if given) maps positions to splats.
 __global__ void __launch_bounds__(kScanThreads)
 k_block_sums(int n, const uint32_t *__restrict__ tiles, const uint32_t *__restrict__ order, uint32_t *__restrict__ sums) {
+    pdl_entry();
     __shared__ uint32_t s_warp[kScanThreads / 32 + 1];
     const int base = blockIdx.x * kScanTile;
     uint32_t s = 0;
@@ -139,6 +140,7 @@ k_block_sums(int n, const uint32_t *__restrict__ tiles, const uint32_t *__restri
 __global__ void __launch_bounds__(1024)
 k_scan_block_sums(int nb, const uint32_t *__restrict__ sums, unsigned long long *__restrict__ offsets,
                   uint32_t *num_instances, uint32_t *status, unsigned long long capacity) {
+    pdl_entry();
     __shared__ unsigned long long s_warp[1024 / 32 + 1];
     unsigned long long carry = 0;
     for (int chunk = 0; chunk < nb; chunk += 1024) {
@@ -203,6 +205,7 @@ k_duplicate(int n, const uint32_t *__restrict__ tiles, const unsigned long long 
             const int4 *__restrict__ rect, const float2 *__restrict__ mean2d, const float4 *__restrict__ conic_o,
             SpanCtx sc, const float *__restrict__ depth, int tiles_x,
             unsigned long long capacity, uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+    pdl_entry();
     __shared__ uint32_t s_off[kScanTile + 1];
     __shared__ uint32_t s_warp[kScanThreads / 32 + 1];
     const int base = blockIdx.x * kScanTile;
@@ -228,6 +231,7 @@ __global__ void __launch_bounds__(kScanThreads)
 k_splat_offsets(int n, const uint32_t *__restrict__ order, const uint32_t *__restrict__ tiles,
                 const unsigned long long *__restrict__ block_offsets, const uint32_t *__restrict__ num,
                 uint32_t *__restrict__ offs) {
+    pdl_entry();
     __shared__ uint32_t s_off[kScanTile + 1];
     __shared__ uint32_t s_warp[kScanThreads / 32 + 1];
     const int base = blockIdx.x * kScanTile;
@@ -323,6 +327,7 @@ k_duplicate_balanced(int n, const uint32_t *__restrict__ order, const uint32_t *
                      const float4 *__restrict__ conic_o, SpanCtx sc, int tiles_x, const uint32_t *__restrict__ num,
                      unsigned long long cap, uint32_t *__restrict__ keys, uint32_t *__restrict__ vals, int bits1,
                      uint32_t n_parts, uint32_t *__restrict__ ph) {
+    pdl_entry();
     __shared__ uint32_t s_base[kDupTile];
     __shared__ uint32_t s_val[kDupTile];
     __shared__ uint32_t s_mark[kDupTile / 32];
@@ -373,6 +378,7 @@ __global__ void __launch_bounds__(1024)
 k_tile_diff(int n, const uint32_t *__restrict__ order, const uint32_t *__restrict__ n_vis,
             const int *__restrict__ radius, const int4 *__restrict__ rect, const float2 *__restrict__ mean2d,
             const float4 *__restrict__ conic_o, SpanCtx sc, int tiles_x, int diff_size, int *__restrict__ diff) {
+    pdl_entry();
     extern __shared__ int s_diff[];
     int *d = SMEM ? s_diff : diff;
     if (SMEM) {
@@ -409,6 +415,7 @@ template <typename K>
 __global__ void __launch_bounds__(256)
 k_sort_hist(const K *__restrict__ keys, const uint32_t *num, unsigned long long cap, PassSpec ps,
             uint32_t *__restrict__ hist) {
+    pdl_entry();
     __shared__ uint32_t s_h[kMaxPasses * 256];
     for (int i = threadIdx.x; i < ps.passes * 256; i += 256) s_h[i] = 0;
     __syncthreads();
@@ -430,6 +437,7 @@ k_sort_hist(const K *__restrict__ keys, const uint32_t *num, unsigned long long 
 }
 
 __global__ void __launch_bounds__(256) k_hist_scan(const uint32_t *__restrict__ hist, uint32_t *__restrict__ base) {
+    pdl_entry();
     __shared__ uint32_t s_warp[256 / 32 + 1];
     const int p = blockIdx.x;
     uint32_t total;
@@ -448,6 +456,7 @@ __global__ void __launch_bounds__(1024)
 k_tile_setup(int tiles_x, int tiles_y, const int *__restrict__ diff_g, uint32_t *__restrict__ counts_g,
              const uint32_t *num, unsigned long long capacity, PassSpec ps, uint32_t *__restrict__ ranges,
              uint32_t *__restrict__ digit_base) {
+    pdl_entry();
     extern __shared__ uint32_t s_dyn[];
     __shared__ uint32_t s_h[kMaxPasses * 256];
     __shared__ unsigned long long s_warp[1024 / 32 + 1];
@@ -541,6 +550,7 @@ template <typename K>
 __global__ void __launch_bounds__(kSortThreads)
 k_part_hist(const K *__restrict__ keys, const uint32_t *num, unsigned long long cap, int shift, int bits,
             uint32_t n_parts, uint32_t *__restrict__ ph) {
+    pdl_entry();
     __shared__ uint32_t s_h[256];
     const uint32_t radix = 1u << bits, mask = radix - 1u;
     for (int i = threadIdx.x; i < 256; i += kSortThreads) s_h[i] = 0;
@@ -569,6 +579,7 @@ k_part_hist(const K *__restrict__ keys, const uint32_t *num, unsigned long long 
 
 __global__ void __launch_bounds__(1024)
 k_scan_reduce(const uint32_t *__restrict__ data, unsigned long long count, uint32_t *__restrict__ sums) {
+    pdl_entry();
     __shared__ uint32_t s_warp[1024 / 32 + 1];
     const unsigned long long base = (unsigned long long)blockIdx.x * kScanBlock;
     uint32_t v = 0;
@@ -583,6 +594,7 @@ k_scan_reduce(const uint32_t *__restrict__ data, unsigned long long count, uint3
 }
 
 __global__ void __launch_bounds__(1024) k_scan_top(uint32_t *__restrict__ sums, int nb) {
+    pdl_entry();
     __shared__ uint32_t s_warp[1024 / 32 + 1];
     uint32_t carry = 0;
     for (int chunk = 0; chunk < nb; chunk += 1024) {
@@ -597,6 +609,7 @@ __global__ void __launch_bounds__(1024) k_scan_top(uint32_t *__restrict__ sums, 
 
 __global__ void __launch_bounds__(1024)
 k_scan_apply(uint32_t *__restrict__ data, unsigned long long count, const uint32_t *__restrict__ sums) {
+    pdl_entry();
     __shared__ uint32_t s_warp[1024 / 32 + 1];
     const unsigned long long base = (unsigned long long)blockIdx.x * kScanBlock + (unsigned long long)threadIdx.x * 4;
     uint32_t v[4], sum = 0;
@@ -620,6 +633,7 @@ __global__ void __launch_bounds__(kSortThreads, kSortCtasPerSm)
 k_downsweep(const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__restrict__ kout,
             uint32_t *__restrict__ vout, const uint32_t *num, unsigned long long cap, int shift, int bits,
             const uint32_t *__restrict__ offsets, uint32_t n_parts) {
+    pdl_entry();
     extern __shared__ __align__(16) unsigned char smem[];
     uint32_t *s_v = reinterpret_cast<uint32_t *>(smem);
     K *s_k = reinterpret_cast<K *>(smem + (size_t)kSortTile * 4);
@@ -876,6 +890,7 @@ __global__ void __launch_bounds__(kSortThreads, kSortCtasPerSm)
 k_onesweep(const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__restrict__ kout,
            uint32_t *__restrict__ vout, const uint32_t *num, unsigned long long cap, int shift, int bits,
            const uint32_t *__restrict__ digit_base, uint32_t *lookback, uint32_t *part_counter, uint32_t *status) {
+    pdl_entry();
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ SweepSmem sm;
     // After a capacity overflow the instance buffers hold only part of the instances while the
@@ -915,6 +930,7 @@ k_dup_sweep(int n, const uint32_t *__restrict__ order, const uint32_t *__restric
             SpanCtx sc, int tiles_x, const uint32_t *num, unsigned long long cap, int bits,
             const uint32_t *__restrict__ digit_base, uint32_t *lookback, uint32_t *part_counter, uint32_t *status,
             uint32_t *__restrict__ kout, uint32_t *__restrict__ vout) {
+    pdl_entry();
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ SweepSmem sm;
     if ((unsigned long long)*num > cap) return;  // overflow: nothing is emitted (status already set)
@@ -953,6 +969,7 @@ k_dup_sweep(int n, const uint32_t *__restrict__ order, const uint32_t *__restric
 
 __global__ void __launch_bounds__(256)
 k_ranges(const uint64_t *__restrict__ keys, const uint32_t *num, unsigned long long cap, uint32_t *__restrict__ ranges) {
+    pdl_entry();
     if ((unsigned long long)*num > cap) return;  // overflow: ranges stay empty
     const unsigned long long M = *num;
     for (unsigned long long i = (unsigned long long)blockIdx.x * 256 + threadIdx.x; i < M;
@@ -971,6 +988,7 @@ k_ranges(const uint64_t *__restrict__ keys, const uint32_t *num, unsigned long l
 // ends up after any number of passes over [0, n_vis).
 __global__ void __launch_bounds__(kScanThreads)
 k_vis_count(int n, const int *__restrict__ radius, uint32_t *__restrict__ block_counts) {
+    pdl_entry();
     __shared__ uint32_t s_warp[kScanThreads / 32 + 1];
     const int base = blockIdx.x * kScanTile;
     uint32_t c = 0;
@@ -988,6 +1006,7 @@ __global__ void __launch_bounds__(kScanThreads)
 k_depth_compact(int n, const int *__restrict__ radius, const float *__restrict__ depth,
                 const unsigned long long *__restrict__ block_offsets, const uint32_t *__restrict__ n_vis,
                 uint32_t *__restrict__ keys, uint32_t *__restrict__ ids0, uint32_t *__restrict__ ids1) {
+    pdl_entry();
     __shared__ uint32_t s_warp[kScanThreads / 32 + 1];
     const int base = blockIdx.x * kScanTile;
     const uint32_t vis0 = (uint32_t)block_offsets[blockIdx.x];
@@ -1014,6 +1033,7 @@ k_depth_compact(int n, const int *__restrict__ radius, const float *__restrict__
 
 __global__ void __launch_bounds__(256)
 k_depth_keys(int n, const int *__restrict__ radius, const float *__restrict__ depth, uint32_t *__restrict__ keys) {
+    pdl_entry();
     const int i = blockIdx.x * 256 + threadIdx.x;
     if (i < n) keys[i] = radius[i] > 0 ? __float_as_uint(depth[i]) : 0xffffffffu;
 }
@@ -1022,6 +1042,7 @@ k_depth_keys(int n, const int *__restrict__ radius, const float *__restrict__ de
 __global__ void __launch_bounds__(256)
 k_keys64(const uint32_t *__restrict__ ranges, const uint32_t *__restrict__ vals, const float *__restrict__ depth,
          int n, uint64_t *__restrict__ keys) {
+    pdl_entry();
     const uint32_t t = blockIdx.x;
     const uint32_t a = ranges[2 * t], b = ranges[2 * t + 1];
     for (uint32_t i = a + threadIdx.x; i < b; i += 256) {
@@ -1054,16 +1075,16 @@ cudaError_t launch_rts_pass(const K *kin, const uint32_t *vin, K *kout, uint32_t
                             uint32_t *sums, bool hist_ready, cudaStream_t st) {
     const uint32_t n_parts = (uint32_t)((grid + kSortTile - 1) / kSortTile);
     if (n_parts == 0) return cudaSuccess;
-    if (!hist_ready) k_part_hist<K><<<n_parts, kSortThreads, 0, st>>>(kin, num, cap, shift, bits, n_parts, ph);
+    if (!hist_ready) launch_k(k_part_hist<K>, n_parts, kSortThreads, 0, st, kin, num, cap, shift, bits, n_parts, ph);
     const unsigned long long count = (unsigned long long)n_parts << bits;
     const int nb = (int)((count + kScanBlock - 1) / kScanBlock);
-    k_scan_reduce<<<nb, 1024, 0, st>>>(ph, count, sums);
-    k_scan_top<<<1, 1024, 0, st>>>(sums, nb);
-    k_scan_apply<<<nb, 1024, 0, st>>>(ph, count, sums);
+    launch_k(k_scan_reduce, nb, 1024, 0, st, ph, count, sums);
+    launch_k(k_scan_top, 1, 1024, 0, st, sums, nb);
+    launch_k(k_scan_apply, nb, 1024, 0, st, ph, count, sums);
     const size_t smem = Staging<K, WK>::bytes;
     cudaError_t e = cudaFuncSetAttribute(k_downsweep<K, WK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_downsweep<K, WK><<<n_parts, kSortThreads, smem, st>>>(kin, vin, kout, vout, num, cap, shift, bits, ph, n_parts);
+    launch_k(k_downsweep<K, WK>, n_parts, kSortThreads, smem, st, kin, vin, kout, vout, num, cap, shift, bits, ph, n_parts);
     return cudaGetLastError();
 }
 
@@ -1076,7 +1097,7 @@ cudaError_t launch_pass(const K *kin, const uint32_t *vin, K *kout, uint32_t *vo
     if (e != cudaSuccess) return e;
     const unsigned n_parts = (unsigned)((grid_instances + kSortTile - 1) / kSortTile);
     if (n_parts == 0) return cudaSuccess;
-    k_onesweep<K, WK><<<n_parts, kSortThreads, smem, st>>>(kin, vin, kout, vout, num, cap, shift, bits, base, lookback,
+    launch_k(k_onesweep<K, WK>, n_parts, kSortThreads, smem, st, kin, vin, kout, vout, num, cap, shift, bits, base, lookback,
                                                            counter, status);
     return cudaGetLastError();
 }
@@ -1186,8 +1207,8 @@ cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int til
     uint32_t *counters = reinterpret_cast<uint32_t *>(at(13));
 
     if (strategy == DARB_SORT_KEYS64) {
-        if (nb > 0) k_block_sums<<<nb, kScanThreads, 0, st>>>(n, proj.tiles_touched, nullptr, block_sums);
-        k_scan_block_sums<<<1, 1024, 0, st>>>(nb, block_sums, block_off, out.num_instances, out.status, cap);
+        if (nb > 0) launch_k(k_block_sums, nb, kScanThreads, 0, st, n, proj.tiles_touched, nullptr, block_sums);
+        launch_k(k_scan_block_sums, 1, 1024, 0, st, nb, block_sums, block_off, out.num_instances, out.status, cap);
         TRY(cudaGetLastError());
         uint64_t grid = capacity;
         if (num_instances_host) {
@@ -1207,7 +1228,7 @@ cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int til
         uint64_t *kb = (passes % 2 == 0) ? reinterpret_cast<uint64_t *>(at(0)) : out.keys;
         uint32_t *vb = (passes % 2 == 0) ? reinterpret_cast<uint32_t *>(at(1)) : out.values;
         if (nb > 0)
-            k_duplicate<<<nb, kScanThreads, 0, st>>>(n, proj.tiles_touched, block_off, proj.tile_rect, proj.mean2d,
+            launch_k(k_duplicate, nb, kScanThreads, 0, st, n, proj.tiles_touched, block_off, proj.tile_rect, proj.mean2d,
                                                      proj.conic_o, sc, proj.depth,
                                                      tiles_x, cap, ka, va);
         if (grid == 0) return cudaGetLastError();
@@ -1220,8 +1241,8 @@ cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int til
         uint32_t *hist = reinterpret_cast<uint32_t *>(at(10));
         uint32_t *dbase = reinterpret_cast<uint32_t *>(at(9));
         const int hb = (int)std::min<uint64_t>((grid + 255) / 256, 152 * 8);
-        k_sort_hist<uint64_t><<<hb, 256, 0, st>>>(ka, out.num_instances, cap, ps, hist);
-        k_hist_scan<<<passes, 256, 0, st>>>(hist, dbase);
+        launch_k(k_sort_hist<uint64_t>, hb, 256, 0, st, ka, out.num_instances, cap, ps, hist);
+        launch_k(k_hist_scan, passes, 256, 0, st, hist, dbase);
         TRY(cudaGetLastError());
         const size_t lb_stride = ((capacity + kSortTile - 1) / kSortTile) * 256;
         uint32_t *lb = reinterpret_cast<uint32_t *>(at(11));
@@ -1232,7 +1253,7 @@ cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int til
             std::swap(va, vb);
         }
         const int rb = (int)std::min<uint64_t>((grid + 255) / 256, 152 * 16);
-        k_ranges<<<rb, 256, 0, st>>>(ka, out.num_instances, cap, out.ranges);
+        launch_k(k_ranges, rb, 256, 0, st, ka, out.num_instances, cap, out.ranges);
         return cudaGetLastError();
     }
 
@@ -1250,19 +1271,19 @@ cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int til
         const uint32_t *vin = nullptr;    // first pass: values are the splat indices
         if (kPassOnesweep) {
             uint32_t *nv = counters + 2 * kMaxPasses;
-            k_vis_count<<<nb, kScanThreads, 0, st>>>(n, proj.radius, block_sums);
-            k_scan_block_sums<<<1, 1024, 0, st>>>(nb, block_sums, block_off, nv, out.status, (unsigned long long)n);
-            k_depth_compact<<<nb, kScanThreads, 0, st>>>(n, proj.radius, proj.depth, block_off, nv, kbuf[0], vbuf[0],
+            launch_k(k_vis_count, nb, kScanThreads, 0, st, n, proj.radius, block_sums);
+            launch_k(k_scan_block_sums, 1, 1024, 0, st, nb, block_sums, block_off, nv, out.status, (unsigned long long)n);
+            launch_k(k_depth_compact, nb, kScanThreads, 0, st, n, proj.radius, proj.depth, block_off, nv, kbuf[0], vbuf[0],
                                                           vbuf[1]);
             n_vis = nv;
             n_vis_dev = nv;
             vin = vbuf[0];
             uint32_t *dhist = reinterpret_cast<uint32_t *>(at(10)) + kMaxPasses * 256;
             const int hb = std::min((n + 255) / 256, 152 * 8);
-            k_sort_hist<uint32_t><<<hb, 256, 0, st>>>(kbuf[0], n_vis, (unsigned long long)n, dps, dhist);
-            k_hist_scan<<<dps.passes, 256, 0, st>>>(dhist, dbase);
+            launch_k(k_sort_hist<uint32_t>, hb, 256, 0, st, kbuf[0], n_vis, (unsigned long long)n, dps, dhist);
+            launch_k(k_hist_scan, dps.passes, 256, 0, st, dhist, dbase);
         } else {
-            k_depth_keys<<<(n + 255) / 256, 256, 0, st>>>(n, proj.radius, proj.depth, kbuf[0]);
+            launch_k(k_depth_keys, (n + 255) / 256, 256, 0, st, n, proj.radius, proj.depth, kbuf[0]);
         }
         TRY(cudaGetLastError());
         uint32_t *lbd = reinterpret_cast<uint32_t *>(at(19));
@@ -1296,8 +1317,8 @@ cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int til
         order = vin;
     }
     // 2) scan of tiles_touched in depth order
-    if (nb > 0) k_block_sums<<<nb, kScanThreads, 0, st>>>(n, proj.tiles_touched, order, block_sums);
-    k_scan_block_sums<<<1, 1024, 0, st>>>(nb, block_sums, block_off, out.num_instances, out.status, cap);
+    if (nb > 0) launch_k(k_block_sums, nb, kScanThreads, 0, st, n, proj.tiles_touched, order, block_sums);
+    launch_k(k_scan_block_sums, 1, 1024, 0, st, nb, block_sums, block_off, out.num_instances, out.status, cap);
     TRY(cudaGetLastError());
     uint64_t grid = capacity;
     if (num_instances_host) {
@@ -1322,11 +1343,11 @@ cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int til
         if (smem <= kMaxDiffSmem) {
             TRY(cudaFuncSetAttribute(k_tile_diff<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             const int blocks = std::min((n + 1023) / 1024, 2 * 152);
-            k_tile_diff<true><<<blocks, 1024, smem, st>>>(n, n_vis_dev ? order : nullptr, n_vis_dev, proj.radius,
+            launch_k(k_tile_diff<true>, blocks, 1024, smem, st, n, n_vis_dev ? order : nullptr, n_vis_dev, proj.radius,
                                                           proj.tile_rect, proj.mean2d, proj.conic_o, sc, tiles_x,
                                                           diff_size, diff);
         } else {
-            k_tile_diff<false><<<(n + 1023) / 1024, 1024, 0, st>>>(n, n_vis_dev ? order : nullptr, n_vis_dev,
+            launch_k(k_tile_diff<false>, (n + 1023) / 1024, 1024, 0, st, n, n_vis_dev ? order : nullptr, n_vis_dev,
                                                                     proj.radius, proj.tile_rect, proj.mean2d,
                                                                     proj.conic_o, sc, tiles_x, diff_size, diff);
         }
@@ -1336,10 +1357,10 @@ cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int til
         if (setup_smem <= kMaxSetupSmem) {
             TRY(cudaFuncSetAttribute(k_tile_setup<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)setup_smem));
-            k_tile_setup<true><<<1, 1024, setup_smem, st>>>(tiles_x, tiles_y, diff, counts, out.num_instances, cap,
+            launch_k(k_tile_setup<true>, 1, 1024, setup_smem, st, tiles_x, tiles_y, diff, counts, out.num_instances, cap,
                                                             tps, out.ranges, tbase);
         } else {
-            k_tile_setup<false><<<1, 1024, 0, st>>>(tiles_x, tiles_y, diff, counts, out.num_instances, cap, tps,
+            launch_k(k_tile_setup<false>, 1, 1024, 0, st, tiles_x, tiles_y, diff, counts, out.num_instances, cap, tps,
                                                     out.ranges, tbase);
         }
     }
@@ -1348,7 +1369,7 @@ cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int til
     uint32_t *tk_a = reinterpret_cast<uint32_t *>(at(0)), *tv_a = reinterpret_cast<uint32_t *>(at(1));
     uint32_t *tk_b = reinterpret_cast<uint32_t *>(at(2)), *tv_b = reinterpret_cast<uint32_t *>(at(3));
     uint32_t *offs = reinterpret_cast<uint32_t *>(at(15));
-    if (nb > 0) k_splat_offsets<<<nb, kScanThreads, 0, st>>>(n, order, proj.tiles_touched, block_off, out.num_instances, offs);
+    if (nb > 0) launch_k(k_splat_offsets, nb, kScanThreads, 0, st, n, order, proj.tiles_touched, block_off, out.num_instances, offs);
     uint32_t *tph = reinterpret_cast<uint32_t *>(at(11));
     const uint32_t n_parts = (uint32_t)((grid + kSortTile - 1) / kSortTile);
     uint32_t *lb = reinterpret_cast<uint32_t *>(at(18));
@@ -1361,13 +1382,13 @@ cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int til
         const size_t smem = last0 ? DupStaging<false>::bytes : DupStaging<true>::bytes;
         if (last0) {
             TRY(cudaFuncSetAttribute(k_dup_sweep<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            k_dup_sweep<false><<<n_parts, kSortThreads, smem, st>>>(n, order, offs, proj.tile_rect, proj.mean2d,
+            launch_k(k_dup_sweep<false>, n_parts, kSortThreads, smem, st, n, order, offs, proj.tile_rect, proj.mean2d,
                                                                     proj.conic_o, sc, tiles_x,
                                                                     out.num_instances, cap, tps.bits[0], tbase, lb,
                                                                     counters, out.status, k0, v0);
         } else {
             TRY(cudaFuncSetAttribute(k_dup_sweep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            k_dup_sweep<true><<<n_parts, kSortThreads, smem, st>>>(n, order, offs, proj.tile_rect, proj.mean2d,
+            launch_k(k_dup_sweep<true>, n_parts, kSortThreads, smem, st, n, order, offs, proj.tile_rect, proj.mean2d,
                                                                    proj.conic_o, sc, tiles_x,
                                                                    out.num_instances, cap, tps.bits[0], tbase, lb,
                                                                    counters, out.status, k0, v0);
@@ -1390,7 +1411,7 @@ cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int til
     } else if (grid > 0) {
         // reduce-then-scan passes: the duplication also writes the first pass's histograms
         if (n > 0)
-            k_duplicate_balanced<<<n_parts, kScanThreads, 0, st>>>(n, order, offs, proj.tile_rect, proj.mean2d,
+            launch_k(k_duplicate_balanced, n_parts, kScanThreads, 0, st, n, order, offs, proj.tile_rect, proj.mean2d,
                                                                    proj.conic_o, sc, tiles_x,
                                                                    out.num_instances, cap, tk_a, tv_a, tps.bits[0],
                                                                    n_parts, tph);
@@ -1416,7 +1437,7 @@ cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int til
         }
     }
     if (grid > 0) {
-        if (out.keys) k_keys64<<<n_tiles, 256, 0, st>>>(out.ranges, out.values, proj.depth, n, out.keys);
+        if (out.keys) launch_k(k_keys64, n_tiles, 256, 0, st, out.ranges, out.values, proj.depth, n, out.keys);
         TRY(cudaGetLastError());
     }
     return cudaSuccess;

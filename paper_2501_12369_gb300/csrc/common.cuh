@@ -9,6 +9,36 @@
 
 namespace darb {
 
+// ---------------------------------------------------------------------------
+// Programmatic dependent launch.  Every kernel of the library is launched through launch_k,
+// which lets it be scheduled while its predecessor in the stream drains, and starts with
+// pdl_entry(): wait until the predecessor grid has completed and its writes are visible (a
+// no-op without a programmatic predecessor), then allow the successor to be scheduled.  Only
+// the launch latency and the CTA start-up overlap; no kernel touches memory before the wait.
+// DARB_PDL=0 in the environment launches without the attribute.
+__device__ __forceinline__ void pdl_entry() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+bool pdl_enabled();  // read once from DARB_PDL (default on)
+
+template <typename... P, typename... A>
+inline void launch_k(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, A &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    // a launch error is also left for cudaGetLastError, which every caller checks
+    (void)cudaLaunchKernelEx(&cfg, kernel, static_cast<A &&>(args)...);
+}
+
 constexpr float kAlphaMax = 0.99f;          // 3DGS alpha clamp (listings: min(0.99f, ...))
 constexpr float kAlphaMin = 1.0f / 255.0f;  // 3DGS: skip alpha < 1/255
 constexpr float kTMin = 0.0001f;            // 3DGS: stop before T (1 - alpha) < 1e-4

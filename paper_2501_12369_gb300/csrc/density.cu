@@ -93,6 +93,7 @@ __device__ __forceinline__ uint32_t block_scan_packed(uint32_t v, uint32_t *s_w,
 __global__ void __launch_bounds__(256)
 k_densify_stats(const float4 *__restrict__ grad2d, const int *__restrict__ radius, int n, float half_w, float half_h,
                 float *__restrict__ accum, float *__restrict__ count, int *__restrict__ max_radius) {
+    pdl_entry();
     const int i = blockIdx.x * 256 + threadIdx.x;
     if (i >= n) return;
     const int r = radius[i];
@@ -109,6 +110,7 @@ __global__ void __launch_bounds__(kDenThreads)
 k_densify_count(int n, const float *__restrict__ scales, const float *__restrict__ opac,
                 const float *__restrict__ accum, const float *__restrict__ count, const int *__restrict__ max_radius,
                 DenCfg c, uint32_t *__restrict__ blk) {
+    pdl_entry();
     __shared__ uint32_t s_w[kDenThreads / 32];
     uint32_t sum[3] = {0, 0, 0};
     for (int j = 0; j < kDenItems; ++j) {
@@ -131,6 +133,7 @@ k_densify_count(int n, const float *__restrict__ scales, const float *__restrict
 // One CTA: exclusive offsets of the three block counts; segment bases; n_out.
 __global__ void __launch_bounds__(1024)
 k_densify_offsets(int nb, uint32_t *__restrict__ blk, uint32_t *__restrict__ n_out) {
+    pdl_entry();
     __shared__ uint32_t s_w[32];
     uint32_t carry[3] = {0, 0, 0};
     for (int f = 0; f < 3; ++f) {
@@ -188,6 +191,7 @@ __global__ void __launch_bounds__(kDenThreads)
 k_densify_scatter(int n, DenIO io, const float *__restrict__ accum, const float *__restrict__ count,
                   const int *__restrict__ max_radius, const float *__restrict__ normals, DenCfg c,
                   const uint32_t *__restrict__ blk, const uint32_t *__restrict__ n_out) {
+    pdl_entry();
     __shared__ uint32_t s_w[kDenThreads / 32];
     uint32_t base[3] = {blk[3 * (size_t)blockIdx.x], blk[3 * (size_t)blockIdx.x + 1], blk[3 * (size_t)blockIdx.x + 2]};
     const uint32_t clone0 = n_out[1], child0 = n_out[2];
@@ -232,6 +236,7 @@ k_densify_scatter(int n, DenIO io, const float *__restrict__ accum, const float 
 
 __global__ void __launch_bounds__(256)
 k_reset_opacity(int n, float cap, float *__restrict__ logits, float *__restrict__ opac) {
+    pdl_entry();
     const int i = blockIdx.x * 256 + threadIdx.x;
     if (i >= n) return;
     const float l = fminf(logits[i], cap);
@@ -249,7 +254,7 @@ size_t densify_workspace_bytes(int n) {
 cudaError_t launch_densify_stats(const float *grad2d, const int *radius, int n, int W, int H, float *accum,
                                  float *count, int *max_radius, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
-    k_densify_stats<<<(n + 255) / 256, 256, 0, st>>>(reinterpret_cast<const float4 *>(grad2d), radius, n, 0.5f * W,
+    launch_k(k_densify_stats, (n + 255) / 256, 256, 0, st, reinterpret_cast<const float4 *>(grad2d), radius, n, 0.5f * W,
                                                      0.5f * H, accum, count, max_radius);
     return cudaGetLastError();
 }
@@ -266,17 +271,17 @@ cudaError_t launch_densify(const darb_train_params &in, const darb_adam_state &s
     DenCfg c{cfg.grad_threshold, cfg.dense_scale, cfg.min_opacity, cfg.max_screen_radius, cfg.max_world_scale,
              cfg.split_scale_div, (float)std::log((double)cfg.split_scale_div)};
     if (nb == 0) return cudaMemsetAsync(n_out, 0, 3 * sizeof(uint32_t), st);
-    k_densify_count<<<nb, kDenThreads, 0, st>>>(n, in.scales, in.opacities, accum, count, max_radius, c, blk);
-    k_densify_offsets<<<1, 1024, 0, st>>>(nb, blk, n_out);
+    launch_k(k_densify_count, nb, kDenThreads, 0, st, n, in.scales, in.opacities, accum, count, max_radius, c, blk);
+    launch_k(k_densify_offsets, 1, 1024, 0, st, nb, blk, n_out);
     DenIO io{in, out, sin, sout, 3 * (in.sh_degree + 1) * (in.sh_degree + 1)};
-    k_densify_scatter<<<nb, kDenThreads, 0, st>>>(n, io, accum, count, max_radius, normals, c, blk, n_out);
+    launch_k(k_densify_scatter, nb, kDenThreads, 0, st, n, io, accum, count, max_radius, normals, c, blk, n_out);
     return cudaGetLastError();
 }
 
 cudaError_t launch_reset_opacity(const darb_train_params &p, float max_opacity, cudaStream_t st) {
     if (p.n == 0) return cudaSuccess;
     const float cap = (float)std::log((double)max_opacity / (1.0 - (double)max_opacity));
-    k_reset_opacity<<<(p.n + 255) / 256, 256, 0, st>>>(p.n, cap, p.opacity_logits, p.opacities);
+    launch_k(k_reset_opacity, (p.n + 255) / 256, 256, 0, st, p.n, cap, p.opacity_logits, p.opacities);
     return cudaGetLastError();
 }
 

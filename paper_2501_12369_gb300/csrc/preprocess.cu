@@ -255,6 +255,7 @@ __global__ void __launch_bounds__(256)
 k_preprocess(int n, const float *__restrict__ means, const float *__restrict__ scales,
              const float4 *__restrict__ quats, const float *__restrict__ opac,
              const float *__restrict__ sh, Cam cam, float psi, int tile, float qmax, ProjectedOut out) {
+    pdl_entry();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float m[3] = {__ldg(means + 3 * (size_t)i), __ldg(means + 3 * (size_t)i + 1), __ldg(means + 3 * (size_t)i + 2)};
@@ -477,6 +478,7 @@ k_preprocess_bwd(int n, const float *__restrict__ means, const float *__restrict
                  const float4 *__restrict__ quats, const float *__restrict__ sh, Cam cam, float psi,
                  const int *__restrict__ radius, const uint8_t *__restrict__ clamped,
                  const float4 *__restrict__ grad2d, GradOut out) {
+    pdl_entry();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     constexpr int K = (DEG + 1) * (DEG + 1);
@@ -579,6 +581,7 @@ __global__ void __launch_bounds__(kBwdAdamThreads, DEG == 2 ? 4 : 6)
 k_preprocess_bwd_adam(int n, darb_train_params P, darb_adam_state A, AdamConsts ac, Cam cam, float psi,
                       const int *__restrict__ radius, const uint8_t *__restrict__ clamped,
                       const float4 *__restrict__ grad2d) {
+    pdl_entry();
     using S = BwdAdamStage<DEG>;
     constexpr int K = S::K, ROW = S::ROW, PAD = S::PAD, NT = kBwdAdamThreads;
     // gradient segments; the tail of each is read as float4 up to a multiple of 4 floats
@@ -657,10 +660,10 @@ cudaError_t launch_preprocess(int n, const darb_splats &sp, const Cam &cam, floa
     const int threads = 256, blocks = (n + threads - 1) / threads;
     const float4 *q = reinterpret_cast<const float4 *>(sp.quats);
     switch (sp.sh_degree) {
-    case 0: k_preprocess<0><<<blocks, threads, 0, st>>>(n, sp.means, sp.scales, q, sp.opacities, sp.sh, cam, psi, tile, qmax, out); break;
-    case 1: k_preprocess<1><<<blocks, threads, 0, st>>>(n, sp.means, sp.scales, q, sp.opacities, sp.sh, cam, psi, tile, qmax, out); break;
-    case 2: k_preprocess<2><<<blocks, threads, 0, st>>>(n, sp.means, sp.scales, q, sp.opacities, sp.sh, cam, psi, tile, qmax, out); break;
-    default: k_preprocess<3><<<blocks, threads, 0, st>>>(n, sp.means, sp.scales, q, sp.opacities, sp.sh, cam, psi, tile, qmax, out); break;
+    case 0: launch_k(k_preprocess<0>, blocks, threads, 0, st, n, sp.means, sp.scales, q, sp.opacities, sp.sh, cam, psi, tile, qmax, out); break;
+    case 1: launch_k(k_preprocess<1>, blocks, threads, 0, st, n, sp.means, sp.scales, q, sp.opacities, sp.sh, cam, psi, tile, qmax, out); break;
+    case 2: launch_k(k_preprocess<2>, blocks, threads, 0, st, n, sp.means, sp.scales, q, sp.opacities, sp.sh, cam, psi, tile, qmax, out); break;
+    default: launch_k(k_preprocess<3>, blocks, threads, 0, st, n, sp.means, sp.scales, q, sp.opacities, sp.sh, cam, psi, tile, qmax, out); break;
     }
     return cudaGetLastError();
 }
@@ -673,10 +676,10 @@ cudaError_t launch_preprocess_bwd(int n, const darb_splats &sp, const Cam &cam, 
     const float4 *q = reinterpret_cast<const float4 *>(sp.quats);
     const float4 *g = reinterpret_cast<const float4 *>(grad2d);
     switch (sp.sh_degree) {
-    case 0: k_preprocess_bwd<0><<<blocks, threads, 0, st>>>(n, sp.means, sp.scales, q, sp.sh, cam, psi, radius, clamped, g, out); break;
-    case 1: k_preprocess_bwd<1><<<blocks, threads, 0, st>>>(n, sp.means, sp.scales, q, sp.sh, cam, psi, radius, clamped, g, out); break;
-    case 2: k_preprocess_bwd<2><<<blocks, threads, 0, st>>>(n, sp.means, sp.scales, q, sp.sh, cam, psi, radius, clamped, g, out); break;
-    default: k_preprocess_bwd<3><<<blocks, threads, 0, st>>>(n, sp.means, sp.scales, q, sp.sh, cam, psi, radius, clamped, g, out); break;
+    case 0: launch_k(k_preprocess_bwd<0>, blocks, threads, 0, st, n, sp.means, sp.scales, q, sp.sh, cam, psi, radius, clamped, g, out); break;
+    case 1: launch_k(k_preprocess_bwd<1>, blocks, threads, 0, st, n, sp.means, sp.scales, q, sp.sh, cam, psi, radius, clamped, g, out); break;
+    case 2: launch_k(k_preprocess_bwd<2>, blocks, threads, 0, st, n, sp.means, sp.scales, q, sp.sh, cam, psi, radius, clamped, g, out); break;
+    default: launch_k(k_preprocess_bwd<3>, blocks, threads, 0, st, n, sp.means, sp.scales, q, sp.sh, cam, psi, radius, clamped, g, out); break;
     }
     return cudaGetLastError();
 }
@@ -686,7 +689,7 @@ cudaError_t launch_bwd_adam_deg(int n, const darb_train_params &p, const darb_ad
                                 const Cam &cam, float psi, const int *radius, const uint8_t *clamped,
                                 const float4 *g, cudaStream_t st) {
     const int blocks = (n + kBwdAdamThreads - 1) / kBwdAdamThreads;
-    k_preprocess_bwd_adam<DEG><<<blocks, kBwdAdamThreads, 0, st>>>(n, p, s, ac, cam, psi, radius, clamped, g);
+    launch_k(k_preprocess_bwd_adam<DEG>, blocks, kBwdAdamThreads, 0, st, n, p, s, ac, cam, psi, radius, clamped, g);
     return cudaGetLastError();
 }
 

@@ -46,6 +46,7 @@ __device__ double F64(const PsiKernel &k, double q) {
 
 __global__ void __launch_bounds__(kPsiThreads)
 k_psi_moment(PsiKernel k, double rmax, double *__restrict__ sums) {
+    pdl_entry();
     __shared__ double s4[kPsiThreads / 32], s2[kPsiThreads / 32];
     const double h = rmax / (double)kPsiSamples;
     double a4 = 0.0, a2 = 0.0;
@@ -83,7 +84,7 @@ cudaError_t launch_psi_moment(const darb_kernel_params &kp, double *sums, cudaSt
     cudaError_t e = cudaMemsetAsync(sums, 0, 2 * sizeof(double), st);
     if (e != cudaSuccess) return e;
     const PsiKernel k{kp.kind, kp.base, (double)kp.xi, (double)kp.beta};
-    k_psi_moment<<<152 * 4, kPsiThreads, 0, st>>>(k, std::sqrt((double)kp.q_max), sums);
+    launch_k(k_psi_moment, 152 * 4, kPsiThreads, 0, st, k, std::sqrt((double)kp.q_max), sums);
     return cudaGetLastError();
 }
 

@@ -149,6 +149,7 @@ k_render_fwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ valu
              const float *__restrict__ rgb, int W, int H, int tiles_x, float qmax, int strict, KernelSpec ks, Bg bg,
              float *__restrict__ image, float *__restrict__ t_final, uint32_t *__restrict__ last,
              uint32_t *__restrict__ n_contrib) {
+    pdl_entry();
     __shared__ FwdSmem<TILE> sm;
     render_tile_fwd<KIND, TILE>(blockIdx.x, sm, ranges, values, mean2d, conic_o, rgb, W, H, tiles_x, qmax, strict, ks,
                                 [&] { return FwdSink{image, t_final, last, n_contrib, bg}; });
@@ -161,6 +162,7 @@ template <int KIND, int TILE>
 __global__ void __launch_bounds__(RenderShape<TILE>::NT, 1536 / RenderShape<TILE>::NT)
 k_render_fwd_batch(const BatchView *__restrict__ views, int n_views, int total_tiles, uint32_t *__restrict__ queue,
                    float qmax, int strict, KernelSpec ks) {
+    pdl_entry();
     __shared__ FwdSmem<TILE> sm;
     __shared__ int s_item, s_view;
     for (;;) {
@@ -235,6 +237,7 @@ k_render_bwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ valu
              const float *__restrict__ rgb, int W, int H, int tiles_x, float qmax, int strict, KernelSpec ks, Bg bg,
              const float *__restrict__ t_final, const uint32_t *__restrict__ last,
              const float *__restrict__ dL_dimage, float4 *__restrict__ grad2d) {
+    pdl_entry();
     using S = RenderShape<TILE>;
     constexpr int NT = S::NT, PIX = S::PIX;
     constexpr int NW = NT / 32;
@@ -386,7 +389,7 @@ cudaError_t fwd_t(int n_tiles, const uint2 *ranges, const uint32_t *values, cons
                   const float4 *conic_o, const float *rgb, const Cam &cam, int tiles_x, float qmax, int strict,
                   const KernelSpec &ks, float *image, float *t_final, uint32_t *last, uint32_t *n_contrib,
                   cudaStream_t st) {
-    k_render_fwd<KIND, TILE><<<n_tiles, RenderShape<TILE>::NT, 0, st>>>(
+    launch_k(k_render_fwd<KIND, TILE>, n_tiles, RenderShape<TILE>::NT, 0, st,
         ranges, values, mean2d, conic_o, rgb, cam.W, cam.H, tiles_x, qmax, strict, ks,
         Bg{cam.bg[0], cam.bg[1], cam.bg[2]}, image, t_final, last, n_contrib);
     return cudaGetLastError();
@@ -397,7 +400,7 @@ cudaError_t bwd_t(int n_tiles, const uint2 *ranges, const uint32_t *values, cons
                   const float4 *conic_o, const float *rgb, const Cam &cam, int tiles_x, float qmax, int strict,
                   const KernelSpec &ks, const float *t_final, const uint32_t *last, const float *dL, float *grad2d,
                   cudaStream_t st) {
-    k_render_bwd<KIND, TILE><<<n_tiles, RenderShape<TILE>::NT, 0, st>>>(
+    launch_k(k_render_bwd<KIND, TILE>, n_tiles, RenderShape<TILE>::NT, 0, st,
         ranges, values, mean2d, conic_o, rgb, cam.W, cam.H, tiles_x, qmax, strict, ks,
         Bg{cam.bg[0], cam.bg[1], cam.bg[2]}, t_final, last, dL, reinterpret_cast<float4 *>(grad2d));
     return cudaGetLastError();
@@ -463,7 +466,7 @@ cudaError_t fwd_batch_t(const BatchView *views, int n_views, int total_tiles, ui
     if (grid > total_tiles) grid = total_tiles;
     e = cudaMemsetAsync(queue, 0, sizeof(uint32_t), st);
     if (e != cudaSuccess) return e;
-    k_render_fwd_batch<KIND, TILE><<<(int)grid, RenderShape<TILE>::NT, 0, st>>>(views, n_views, total_tiles, queue,
+    launch_k(k_render_fwd_batch<KIND, TILE>, (int)grid, RenderShape<TILE>::NT, 0, st, views, n_views, total_tiles, queue,
                                                                                  qmax, strict, ks);
     return cudaGetLastError();
 }

@@ -54,6 +54,7 @@ __device__ __forceinline__ float block_sum(float v, float *s_w) {
 __global__ void __launch_bounds__(kSsimThreads)
 k_ssim_fwd(const float *__restrict__ x, const float *__restrict__ y, int W, int H, Window win,
            float *__restrict__ d_m, float *__restrict__ d_sxx, float *__restrict__ d_sxy, double *__restrict__ sums) {
+    pdl_entry();
     __shared__ float sx[kSsimIn][kSsimIn + 1], sy[kSsimIn][kSsimIn + 1];
     __shared__ float h[5][kSsimIn][kSsimTs];
     __shared__ float s_w[kSsimThreads / 32];
@@ -125,6 +126,7 @@ __global__ void __launch_bounds__(kSsimThreads)
 k_ssim_bwd(const float *__restrict__ x, const float *__restrict__ y, int W, int H, Window win,
            const float *__restrict__ d_m, const float *__restrict__ d_sxx, const float *__restrict__ d_sxy,
            float lam, const double *__restrict__ sums, float *__restrict__ dL, float *__restrict__ loss) {
+    pdl_entry();
     __shared__ float sa[3][kSsimIn][kSsimIn + 1];
     __shared__ float h[3][kSsimIn][kSsimTs];
     const int x0 = blockIdx.x * kSsimTs, y0 = blockIdx.y * kSsimTs;
@@ -199,8 +201,8 @@ cudaError_t launch_l1_dssim(const float *image, const float *target, int W, int 
     if (e != cudaSuccess) return e;
     static const Window win = make_window();
     const dim3 grid((W + kSsimTs - 1) / kSsimTs, (H + kSsimTs - 1) / kSsimTs, 3);
-    k_ssim_fwd<<<grid, kSsimThreads, 0, st>>>(image, target, W, H, win, maps, maps + n, maps + 2 * n, sums);
-    k_ssim_bwd<<<grid, kSsimThreads, 0, st>>>(image, target, W, H, win, maps, maps + n, maps + 2 * n, lam, sums, dL,
+    launch_k(k_ssim_fwd, grid, kSsimThreads, 0, st, image, target, W, H, win, maps, maps + n, maps + 2 * n, sums);
+    launch_k(k_ssim_bwd, grid, kSsimThreads, 0, st, image, target, W, H, win, maps, maps + n, maps + 2 * n, lam, sums, dL,
                                               loss);
     return cudaGetLastError();
 }

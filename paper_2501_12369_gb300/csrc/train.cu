@@ -10,6 +10,7 @@ namespace {
 __global__ void __launch_bounds__(256)
 k_l1_loss(const float *__restrict__ image, const float *__restrict__ target, int count, float inv_count,
           float *__restrict__ dL, float *__restrict__ loss) {
+    pdl_entry();
     __shared__ float s_warp[8];
     float acc = 0.0f;
     for (int i = blockIdx.x * 256 + threadIdx.x; i < count; i += gridDim.x * 256) {
@@ -51,6 +52,7 @@ __global__ void __launch_bounds__(256)
 k_adam4(long long count, float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
         float *__restrict__ v, float lr, float lr2, float b1, float b2, float eps, float ibc1, float ibc2,
         float *__restrict__ activated) {
+    pdl_entry();
     const long long n4 = count >> 2;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n4; j += stride) {
@@ -94,6 +96,7 @@ template <int ROW, int SPLIT>
 __global__ void __launch_bounds__(256)
 k_adam_rows(long long count, float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
             float *__restrict__ v, float lr, float lr2, float b1, float b2, float eps, float ibc1, float ibc2) {
+    pdl_entry();
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
          i += (long long)gridDim.x * blockDim.x) {
         float pp = p[i], mm = m[i], vv = v[i];
@@ -117,7 +120,7 @@ cudaError_t launch_l1_loss(const float *image, const float *target, int count, f
     cudaError_t e = cudaMemsetAsync(loss, 0, sizeof(float), st);
     if (e != cudaSuccess) return e;
     if (count == 0) return cudaSuccess;
-    k_l1_loss<<<grid_for(count), 256, 0, st>>>(image, target, count, 1.0f / (float)count, dL, loss);
+    launch_k(k_l1_loss, grid_for(count), 256, 0, st, image, target, count, 1.0f / (float)count, dL, loss);
     return cudaGetLastError();
 }
 
@@ -130,30 +133,30 @@ cudaError_t launch_adam(const darb_train_params &p, const darb_splat_grads &g, c
     const float b1 = c.beta1, b2 = c.beta2, eps = c.eps;
     const long long K = (long long)(p.sh_degree + 1) * (p.sh_degree + 1);
     auto g4 = [](long long count) { return grid_for((count + 3) / 4); };
-    k_adam4<0, 0, 0><<<g4(3 * n), 256, 0, st>>>(3 * n, p.means, g.dmeans, s.m_means, s.v_means, c.lr_means,
+    launch_k(k_adam4<0, 0, 0>, g4(3 * n), 256, 0, st, 3 * n, p.means, g.dmeans, s.m_means, s.v_means, c.lr_means,
                                                  c.lr_means, b1, b2, eps, ibc1, ibc2, nullptr);
-    k_adam4<1, 0, 0><<<g4(3 * n), 256, 0, st>>>(3 * n, p.log_scales, g.dscales, s.m_scales, s.v_scales, c.lr_scales,
+    launch_k(k_adam4<1, 0, 0>, g4(3 * n), 256, 0, st, 3 * n, p.log_scales, g.dscales, s.m_scales, s.v_scales, c.lr_scales,
                                                  c.lr_scales, b1, b2, eps, ibc1, ibc2, p.scales);
-    k_adam4<0, 0, 0><<<g4(4 * n), 256, 0, st>>>(4 * n, p.quats, g.dquats, s.m_quats, s.v_quats, c.lr_quats,
+    launch_k(k_adam4<0, 0, 0>, g4(4 * n), 256, 0, st, 4 * n, p.quats, g.dquats, s.m_quats, s.v_quats, c.lr_quats,
                                                  c.lr_quats, b1, b2, eps, ibc1, ibc2, nullptr);
-    k_adam4<2, 0, 0><<<g4(n), 256, 0, st>>>(n, p.opacity_logits, g.dopacities, s.m_opac, s.v_opac, c.lr_opacities,
+    launch_k(k_adam4<2, 0, 0>, g4(n), 256, 0, st, n, p.opacity_logits, g.dopacities, s.m_opac, s.v_opac, c.lr_opacities,
                                              c.lr_opacities, b1, b2, eps, ibc1, ibc2, p.opacities);
     const long long cs = 3 * K * n;
     switch (p.sh_degree) {
     case 0:
-        k_adam_rows<3, 3><<<grid_for(cs), 256, 0, st>>>(cs, p.sh, g.dsh, s.m_sh, s.v_sh, c.lr_sh_dc, c.lr_sh_rest, b1,
+        launch_k(k_adam_rows<3, 3>, grid_for(cs), 256, 0, st, cs, p.sh, g.dsh, s.m_sh, s.v_sh, c.lr_sh_dc, c.lr_sh_rest, b1,
                                                          b2, eps, ibc1, ibc2);
         break;
     case 1:
-        k_adam4<0, 12, 3><<<g4(cs), 256, 0, st>>>(cs, p.sh, g.dsh, s.m_sh, s.v_sh, c.lr_sh_dc, c.lr_sh_rest, b1, b2,
+        launch_k(k_adam4<0, 12, 3>, g4(cs), 256, 0, st, cs, p.sh, g.dsh, s.m_sh, s.v_sh, c.lr_sh_dc, c.lr_sh_rest, b1, b2,
                                                   eps, ibc1, ibc2, nullptr);
         break;
     case 2:
-        k_adam_rows<27, 3><<<grid_for(cs), 256, 0, st>>>(cs, p.sh, g.dsh, s.m_sh, s.v_sh, c.lr_sh_dc, c.lr_sh_rest, b1,
+        launch_k(k_adam_rows<27, 3>, grid_for(cs), 256, 0, st, cs, p.sh, g.dsh, s.m_sh, s.v_sh, c.lr_sh_dc, c.lr_sh_rest, b1,
                                                           b2, eps, ibc1, ibc2);
         break;
     default:
-        k_adam4<0, 48, 3><<<g4(cs), 256, 0, st>>>(cs, p.sh, g.dsh, s.m_sh, s.v_sh, c.lr_sh_dc, c.lr_sh_rest, b1, b2,
+        launch_k(k_adam4<0, 48, 3>, g4(cs), 256, 0, st, cs, p.sh, g.dsh, s.m_sh, s.v_sh, c.lr_sh_dc, c.lr_sh_rest, b1, b2,
                                                   eps, ibc1, ibc2, nullptr);
         break;
     }

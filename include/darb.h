@@ -117,11 +117,19 @@ typedef struct {
 } darb_splats;
 
 /* Per-splat outputs of darb_preprocess, device pointers, each with n entries.
- * depth [n]: camera-space z.  radius [n]: ceil(3 sqrt(lambda_max)), 0 = culled.
- * tile_rect [n][4]: inclusive tile rectangle (tx0, ty0, tx1, ty1).
+ * depth [n]: camera-space z.  radius [n]: ceil(3 sqrt(lambda_max)); 0 = culled (behind the
+ * near plane, outside the guard band, a degenerate covariance, or no member tile).
+ * tile_rect [n][4]: inclusive tile rectangle (tx0, ty0, tx1, ty1) of the pixel centres within
+ * radius of the centre.
  * mean2d [n][2]: projected centre in pixels.  conic_o [n][4]: (A, B, C, opacity) with
  * q = A dx^2 + 2 B dx dy + C dy^2.  rgb [n][3]: SH colour.  clamped [n]: bit c set when
- * colour channel c was clamped at 0.  tiles_touched [n]: tiles in the rectangle. */
+ * colour channel c was clamped at 0.
+ * tiles_touched [n]: member tiles.  In each tile row of the rectangle they are the run of
+ * columns whose pixel centres the ellipse {q <= q_max} reaches over the row's band of
+ * pixel-centre heights (the Sec. 3 footprint's support, tested per tile row).
+ * tile_runs [n]: the same runs packed, for darb_bin_sort: when the rectangle spans at most 4
+ * rows and 15 columns, byte k holds row ty0 + k's run as (c1 - tx0) << 4 | (c0 - tx0), or
+ * 0x0F for a row without member tiles; 0xFFFFFFFF for larger rectangles and culled splats. */
 typedef struct {
     float *depth;
     int32_t *radius;
@@ -131,6 +139,7 @@ typedef struct {
     float *rgb;
     uint8_t *clamped;
     uint32_t *tiles_touched;
+    uint32_t *tile_runs;
 } darb_projected;
 
 /* Outputs of darb_bin_sort, device pointers.

@@ -19,7 +19,8 @@ namespace {
 
 bool valid_projected(const darb_projected *o) {
     if (!o) return false;
-    const void *p[8] = {o->depth, o->radius, o->tile_rect, o->mean2d, o->conic_o, o->rgb, o->clamped, o->tiles_touched};
+    const void *p[9] = {o->depth,   o->radius,  o->tile_rect,     o->mean2d,   o->conic_o,
+                        o->rgb,     o->clamped, o->tiles_touched, o->tile_runs};
     for (const void *q : p)
         if (!q || !aligned16(q)) return false;
     return true;
@@ -29,7 +30,8 @@ bool valid_projected(const darb_projected *o) {
 // may pass NULL buffers; otherwise every buffer must be valid.
 bool valid_projected_or_empty(const darb_projected *o) {
     if (!o) return false;
-    const void *p[8] = {o->depth, o->radius, o->tile_rect, o->mean2d, o->conic_o, o->rgb, o->clamped, o->tiles_touched};
+    const void *p[9] = {o->depth,   o->radius,  o->tile_rect,     o->mean2d,   o->conic_o,
+                        o->rgb,     o->clamped, o->tiles_touched, o->tile_runs};
     bool all_null = true;
     for (const void *q : p) all_null &= (q == nullptr);
     return all_null || valid_projected(o);
@@ -45,6 +47,7 @@ ProjectedOut as_out(const darb_projected *o) {
     r.rgb = o->rgb;
     r.clamped = o->clamped;
     r.tiles_touched = o->tiles_touched;
+    r.tile_runs = o->tile_runs;
     return r;
 }
 
@@ -170,6 +173,7 @@ darb_status darb_bin_sort(const darb_projected *proj, int32_t n, int32_t tile, c
         pin.tiles_touched = proj->tiles_touched;
         pin.mean2d = reinterpret_cast<const float2 *>(proj->mean2d);
         pin.conic_o = reinterpret_cast<const float4 *>(proj->conic_o);
+        pin.tile_runs = proj->tile_runs;
     }
     const BinOut bo{out->keys, out->values, out->ranges, out->num_instances, out->status};
     bool exceeded = false;

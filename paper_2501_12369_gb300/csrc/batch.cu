@@ -41,7 +41,7 @@ size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 size_t projected_bytes(int n) {
     const size_t N = (size_t)n;
     return a256(4 * N) + a256(4 * N) + a256(16 * N) + a256(8 * N) + a256(16 * N) + a256(12 * N) + a256(N) +
-           a256(4 * N);
+           a256(4 * N) + a256(4 * N);
 }
 
 struct BatchLayout {
@@ -98,6 +98,8 @@ ProjectedOut view_projected(unsigned char *base, int n) {
     p.clamped = reinterpret_cast<uint8_t *>(base + o);
     o += a256(N);
     p.tiles_touched = reinterpret_cast<uint32_t *>(base + o);
+    o += a256(4 * N);
+    p.tile_runs = reinterpret_cast<uint32_t *>(base + o);
     return p;
 }
 
@@ -234,6 +236,7 @@ darb_status darb_render_batch(const darb_splats *splats, const darb_camera *cams
         pin.tiles_touched = po.tiles_touched;
         pin.mean2d = po.mean2d;
         pin.conic_o = po.conic_o;
+        pin.tile_runs = po.tile_runs;
         const BinOut bo{nullptr, reinterpret_cast<uint32_t *>(vb + L.values_off),
                         reinterpret_cast<uint32_t *>(vb + L.ranges_off), counts + v, stats + v};
         bool exceeded = false;

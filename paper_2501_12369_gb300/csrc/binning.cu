@@ -2,18 +2,20 @@
 // per-tile ranges.  This is the tile-based rasterization with a bounding box that the paper
 // keeps from 3DGS (Sec. A.3); the paper prints none of it, so the design here is GB300's.
 //
-// The result is fixed: every (splat, tile-of-its-rectangle) instance, ordered by
+// The result is fixed: every (splat, member tile) instance -- the member tiles being, per tile
+// row of the splat's rectangle, the run its ellipse reaches (see span_row) -- ordered by
 // key = tile << 32 | bits(depth) (depth > 0, so the unsigned order is (tile, depth)), equal keys
 // in ascending splat index.  Two strategies produce it bit for bit:
 //
 // DARB_SORT_DEPTH_THEN_TILE (default)
-//   k_depth_keys + 4 x k_onesweep<u32>   sort the N splats by depth bits (stable, so equal depths
-//                                         keep index order): N-sized, cheap
+//   k_vis_count, k_depth_compact,         sort the visible splats by depth bits (stable, so equal
+//   4 x k_onesweep<u32>                   depths keep index order): N-sized, cheap
 //   k_block_sums / k_scan_block_sums      scan of tiles_touched in that depth order
-//   k_tile_diff / k_tile_setup            per-tile instance counts from the rectangles (2D
-//                                         difference array, 4 atomics per splat) -> the tile
+//   k_tile_diff / k_tile_setup            per-tile instance counts from the row runs (a row-wise
+//                                         difference array, 2 atomics per run) -> the tile
 //                                         ranges and the digit bases of the tile passes
-//   k_splat_offsets                       per-position instance offsets (depth order)
+//   k_splat_offsets                       per-position instance offsets (depth order) and the
+//                                         first and last owner of every sort partition
 //   k_dup_sweep                           emit (tile id, splat) per instance in depth order, each
 //                                         CTA a fixed range of instances (near splats are the
 //                                         largest, so splitting by splats would be unbalanced),
@@ -227,19 +229,33 @@ k_duplicate(int n, const uint32_t *__restrict__ tiles, const unsigned long long 
 }
 
 // Per-position instance offsets in depth order: offs[j] = sum of tiles_touched over positions < j.
+// With bounds (max_parts entries), also the owners of every kSortTile-instance partition p:
+// bounds[p].x owns its first instance p * kSortTile, bounds[p].y its last, min(M, (p + 1) *
+// kSortTile) - 1 -- each position writes the partitions whose first or last instance it owns.
 __global__ void __launch_bounds__(kScanThreads)
 k_splat_offsets(int n, const uint32_t *__restrict__ order, const uint32_t *__restrict__ tiles,
                 const unsigned long long *__restrict__ block_offsets, const uint32_t *__restrict__ num,
-                uint32_t *__restrict__ offs) {
+                uint32_t *__restrict__ offs, uint2 *__restrict__ bounds, uint32_t max_parts) {
     pdl_entry();
     __shared__ uint32_t s_off[kScanTile + 1];
     __shared__ uint32_t s_warp[kScanThreads / 32 + 1];
     const int base = blockIdx.x * kScanTile;
-    cta_offsets(n, base, tiles, order, s_off, nullptr, s_warp);
+    const uint32_t total = cta_offsets(n, base, tiles, order, s_off, nullptr, s_warp);
     const uint32_t gbase = (uint32_t)block_offsets[blockIdx.x];
-    for (int j = threadIdx.x; j < kScanTile; j += kScanThreads)
-        if (base + j < n) offs[base + j] = gbase + s_off[j];
-    if (blockIdx.x == 0 && threadIdx.x == 0) offs[n] = *num;
+    const uint32_t M = *num;
+    constexpr uint32_t T = kSortTile;
+    for (int j = threadIdx.x; j < kScanTile; j += kScanThreads) {
+        if (base + j >= n) continue;
+        const uint32_t o0 = gbase + s_off[j];
+        offs[base + j] = o0;
+        const uint32_t o1 = gbase + (j + 1 < kScanTile ? s_off[j + 1] : total);
+        if (!bounds || o1 <= o0) continue;
+        for (uint32_t p = (o0 + T - 1) / T; p < (o1 + T - 1) / T && p < max_parts; ++p) bounds[p].x = (uint32_t)(base + j);
+        for (uint32_t p = (o0 + 1 + T - 1) / T - 1; p + 1 <= o1 / T && p < max_parts; ++p)
+            bounds[p].y = (uint32_t)(base + j);
+        if (o1 == M && (M - 1) / T < max_parts) bounds[(M - 1) / T].y = (uint32_t)(base + j);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) offs[n] = M;
 }
 
 // Largest s in [0, n) with offs[s] <= target (offs non-decreasing, offs[0] = 0), by warp 0 of
@@ -274,19 +290,15 @@ __device__ __forceinline__ int cta_upper_owner(const uint32_t *__restrict__ offs
 template <int NT>
 __device__ __forceinline__ void partition_runs(int first, int count, uint32_t lo, uint32_t hi,
                                                const uint32_t *__restrict__ offs, const uint32_t *__restrict__ order,
-                                               const int4 *__restrict__ rect, const float2 *__restrict__ mean2d,
-                                               const float4 *__restrict__ conic_o, const SpanCtx &sc, int tiles_x,
-                                               uint32_t *s_base, uint32_t *s_val, uint32_t *mark) {
+                                               const int4 *__restrict__ rect, const uint32_t *__restrict__ runs,
+                                               const float2 *__restrict__ mean2d, const float4 *__restrict__ conic_o,
+                                               const SpanCtx &sc, int tiles_x, uint32_t *s_base, uint32_t *s_val,
+                                               uint32_t *mark) {
     for (int o = threadIdx.x; o < count; o += NT) {
         uint32_t j = offs[first + o];
         const uint32_t id = order[first + o];
-        const float2 mu = __ldg(mean2d + id);
-        const float4 co = __ldg(conic_o + id);
         const int4 r = __ldg(rect + id);
-        const SpanSplat p = span_prepare(mu.x, mu.y, co.x, co.y, co.z, sc.qmax);
-        for (int ty = r.y; ty <= r.w && j < hi; ++ty) {
-            int c0, c1;
-            if (!span_row(p, sc, r, ty, c0, c1)) continue;
+        for_each_run(__ldg(runs + id), mean2d, conic_o, id, r, sc, [&](int ty, int c0, int c1) {
             const uint32_t w = (uint32_t)(c1 - c0 + 1);
             if (j + w > lo) {
                 const uint32_t q = max(j, lo), pos = q - lo;
@@ -295,7 +307,8 @@ __device__ __forceinline__ void partition_runs(int first, int count, uint32_t lo
                 atomicOr(&mark[pos >> 5], 1u << (pos & 31));
             }
             j += w;
-        }
+            return j < hi;
+        });
     }
 }
 
@@ -323,7 +336,7 @@ __device__ __forceinline__ void partition_lookup(uint32_t pos, const uint32_t *s
 // ph[d * n_parts + partition].
 __global__ void __launch_bounds__(kScanThreads)
 k_duplicate_balanced(int n, const uint32_t *__restrict__ order, const uint32_t *__restrict__ offs,
-                     const int4 *__restrict__ rect, const float2 *__restrict__ mean2d,
+                     const int4 *__restrict__ rect, const uint32_t *__restrict__ runs, const float2 *__restrict__ mean2d,
                      const float4 *__restrict__ conic_o, SpanCtx sc, int tiles_x, const uint32_t *__restrict__ num,
                      unsigned long long cap, uint32_t *__restrict__ keys, uint32_t *__restrict__ vals, int bits1,
                      uint32_t n_parts, uint32_t *__restrict__ ph) {
@@ -348,8 +361,8 @@ k_duplicate_balanced(int n, const uint32_t *__restrict__ order, const uint32_t *
     const int first = cta_upper_owner(offs, n, lo, &s_res[0]);
     const int last = cta_upper_owner(offs, n, hi - 1, &s_res[1]);
     const int count = min(last - first + 1, kDupTile);  // every owner has >= 1 instance
-    partition_runs<kScanThreads>(first, count, lo, hi, offs, order, rect, mean2d, conic_o, sc, tiles_x, s_base, s_val,
-                                 s_mark);
+    partition_runs<kScanThreads>(first, count, lo, hi, offs, order, rect, runs, mean2d, conic_o, sc, tiles_x, s_base,
+                                 s_val, s_mark);
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t wbase = lo + (uint32_t)warp * (32 * kDupItems);
@@ -376,8 +389,9 @@ k_duplicate_balanced(int n, const uint32_t *__restrict__ order, const uint32_t *
 template <bool SMEM>
 __global__ void __launch_bounds__(1024)
 k_tile_diff(int n, const uint32_t *__restrict__ order, const uint32_t *__restrict__ n_vis,
-            const int *__restrict__ radius, const int4 *__restrict__ rect, const float2 *__restrict__ mean2d,
-            const float4 *__restrict__ conic_o, SpanCtx sc, int tiles_x, int diff_size, int *__restrict__ diff) {
+            const int *__restrict__ radius, const int4 *__restrict__ rect, const uint32_t *__restrict__ runs,
+            const float2 *__restrict__ mean2d, const float4 *__restrict__ conic_o, SpanCtx sc, int tiles_x,
+            int diff_size, int *__restrict__ diff) {
     pdl_entry();
     extern __shared__ int s_diff[];
     int *d = SMEM ? s_diff : diff;
@@ -391,20 +405,21 @@ k_tile_diff(int n, const uint32_t *__restrict__ order, const uint32_t *__restric
         const int i = order ? (int)order[k] : k;
         if (radius[i] == 0) continue;
         const int4 r = rect[i];
-        const float2 mu = mean2d[i];
-        const float4 co = conic_o[i];
-        const SpanSplat sp = span_prepare(mu.x, mu.y, co.x, co.y, co.z, sc.qmax);
-        for (int ty = r.y; ty <= r.w; ++ty) {  // one run of member tiles per row: +1 at c0, -1 after c1
-            int c0, c1;
-            if (!span_row(sp, sc, r, ty, c0, c1)) continue;
-            atomicAdd(&d[ty * w1 + c0], 1);
+        for_each_run(runs[i], mean2d, conic_o, (uint32_t)i, r, sc, [&](int ty, int c0, int c1) {
+            atomicAdd(&d[ty * w1 + c0], 1);  // one run of member tiles per row: +1 at c0, -1 after c1
             atomicAdd(&d[ty * w1 + c1 + 1], -1);
-        }
+            return true;
+        });
     }
     if (SMEM) {
         __syncthreads();
-        for (int i = threadIdx.x; i < diff_size; i += blockDim.x)
+        // each CTA starts its flush at a different entry, so that concurrent CTAs add to
+        // different addresses rather than queueing on the same ones
+        const int rot = (int)(((long long)blockIdx.x * diff_size) / gridDim.x);
+        for (int k = threadIdx.x; k < diff_size; k += blockDim.x) {
+            const int i = k + rot < diff_size ? k + rot : k + rot - diff_size;
             if (s_diff[i]) atomicAdd(&diff[i], s_diff[i]);
+        }
     }
 }
 
@@ -925,8 +940,9 @@ k_onesweep(const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__res
 // tile digit, so the unsorted instances never go through HBM.
 template <bool WRITE_KEYS>
 __global__ void __launch_bounds__(kSortThreads, kSortCtasPerSm)
-k_dup_sweep(int n, const uint32_t *__restrict__ order, const uint32_t *__restrict__ offs,
-            const int4 *__restrict__ rect, const float2 *__restrict__ mean2d, const float4 *__restrict__ conic_o,
+k_dup_sweep(int n, const uint32_t *__restrict__ order, const uint32_t *__restrict__ offs, const uint2 *__restrict__ bounds,
+            const int4 *__restrict__ rect, const uint32_t *__restrict__ runs, const float2 *__restrict__ mean2d,
+            const float4 *__restrict__ conic_o,
             SpanCtx sc, int tiles_x, const uint32_t *num, unsigned long long cap, int bits,
             const uint32_t *__restrict__ digit_base, uint32_t *lookback, uint32_t *part_counter, uint32_t *status,
             uint32_t *__restrict__ kout, uint32_t *__restrict__ vout) {
@@ -943,11 +959,11 @@ k_dup_sweep(int n, const uint32_t *__restrict__ order, const uint32_t *__restric
     uint32_t *s_val = s_base + kDupTile;
     uint32_t *s_mark = s_val + kDupTile;
     for (int i = threadIdx.x; i < kDupTile / 32; i += kSortThreads) s_mark[i] = 0;
-    const int first = cta_upper_owner(offs, n, lo, &sm.res[0]);
-    const int last = cta_upper_owner(offs, n, hi - 1, &sm.res[1]);
-    const int count = min(last - first + 1, kDupTile);  // every owner has >= 1 instance
-    partition_runs<kSortThreads>(first, count, lo, hi, offs, order, rect, mean2d, conic_o, sc, tiles_x, s_base, s_val,
-                                 s_mark);
+    const uint2 fl = bounds[part];
+    const int first = (int)fl.x, count = min((int)fl.y - (int)fl.x + 1, kDupTile);  // every owner has >= 1 instance
+    __syncthreads();
+    partition_runs<kSortThreads>(first, count, lo, hi, offs, order, rect, runs, mean2d, conic_o, sc, tiles_x, s_base,
+                                 s_val, s_mark);
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t wbase = lo + (uint32_t)warp * (32 * kSortItems);
@@ -1084,7 +1100,8 @@ cudaError_t launch_rts_pass(const K *kin, const uint32_t *vin, K *kout, uint32_t
     const size_t smem = Staging<K, WK>::bytes;
     cudaError_t e = cudaFuncSetAttribute(k_downsweep<K, WK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    launch_k(k_downsweep<K, WK>, n_parts, kSortThreads, smem, st, kin, vin, kout, vout, num, cap, shift, bits, ph, n_parts);
+    launch_k(k_downsweep<K, WK>, n_parts, kSortThreads, smem, st, kin, vin, kout, vout, num, cap, shift, bits, ph,
+             n_parts);
     return cudaGetLastError();
 }
 
@@ -1097,8 +1114,8 @@ cudaError_t launch_pass(const K *kin, const uint32_t *vin, K *kout, uint32_t *vo
     if (e != cudaSuccess) return e;
     const unsigned n_parts = (unsigned)((grid_instances + kSortTile - 1) / kSortTile);
     if (n_parts == 0) return cudaSuccess;
-    launch_k(k_onesweep<K, WK>, n_parts, kSortThreads, smem, st, kin, vin, kout, vout, num, cap, shift, bits, base, lookback,
-                                                           counter, status);
+    launch_k(k_onesweep<K, WK>, n_parts, kSortThreads, smem, st, kin, vin, kout, vout, num, cap, shift, bits, base,
+             lookback, counter, status);
     return cudaGetLastError();
 }
 
@@ -1140,6 +1157,7 @@ Layout layout(int n, uint64_t capacity, int tiles_x, int tiles_y, int strategy, 
         put(17, 0);
         put(18, 0);
         put(19, 0);
+        put(20, 0);
         put(9, (size_t)kMaxPasses * 256 * 4);  // digit bases
         put(10, (size_t)kMaxPasses * 256 * 4); // --- zeroed from here: histograms
         put(11, (size_t)passes * parts_cap * 256 * 4);  // look-back
@@ -1159,6 +1177,7 @@ Layout layout(int n, uint64_t capacity, int tiles_x, int tiles_y, int strategy, 
         put(9, (size_t)kMaxPasses * 256 * 4);  // depth digit bases
         put(15, ((size_t)n + 1) * 4);           // per-position instance offsets in depth order
         put(16, (size_t)n_tiles * 4);           // per-tile instance counts
+        put(20, parts_cap * 8);                 // first and last owner of every tile-pass partition
         put(11, parts_cap * 256 * 4);           // tile-pass partition histograms / offsets
         put(12, parts_n * 256 * 4);             // depth-pass partition histograms / offsets
         put(17, ((std::max(parts_cap, parts_n) * 256 + 4095) / 4096 + 1) * 4);  // table-scan block sums
@@ -1228,9 +1247,8 @@ cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int til
         uint64_t *kb = (passes % 2 == 0) ? reinterpret_cast<uint64_t *>(at(0)) : out.keys;
         uint32_t *vb = (passes % 2 == 0) ? reinterpret_cast<uint32_t *>(at(1)) : out.values;
         if (nb > 0)
-            launch_k(k_duplicate, nb, kScanThreads, 0, st, n, proj.tiles_touched, block_off, proj.tile_rect, proj.mean2d,
-                                                     proj.conic_o, sc, proj.depth,
-                                                     tiles_x, cap, ka, va);
+            launch_k(k_duplicate, nb, kScanThreads, 0, st, n, proj.tiles_touched, block_off, proj.tile_rect,
+                     proj.mean2d, proj.conic_o, sc, proj.depth, tiles_x, cap, ka, va);
         if (grid == 0) return cudaGetLastError();
         PassSpec ps{};
         ps.passes = passes;
@@ -1272,9 +1290,10 @@ cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int til
         if (kPassOnesweep) {
             uint32_t *nv = counters + 2 * kMaxPasses;
             launch_k(k_vis_count, nb, kScanThreads, 0, st, n, proj.radius, block_sums);
-            launch_k(k_scan_block_sums, 1, 1024, 0, st, nb, block_sums, block_off, nv, out.status, (unsigned long long)n);
-            launch_k(k_depth_compact, nb, kScanThreads, 0, st, n, proj.radius, proj.depth, block_off, nv, kbuf[0], vbuf[0],
-                                                          vbuf[1]);
+            launch_k(k_scan_block_sums, 1, 1024, 0, st, nb, block_sums, block_off, nv, out.status,
+                     (unsigned long long)n);
+            launch_k(k_depth_compact, nb, kScanThreads, 0, st, n, proj.radius, proj.depth, block_off, nv, kbuf[0],
+                     vbuf[0], vbuf[1]);
             n_vis = nv;
             n_vis_dev = nv;
             vin = vbuf[0];
@@ -1344,12 +1363,11 @@ cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int til
             TRY(cudaFuncSetAttribute(k_tile_diff<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             const int blocks = std::min((n + 1023) / 1024, 2 * 152);
             launch_k(k_tile_diff<true>, blocks, 1024, smem, st, n, n_vis_dev ? order : nullptr, n_vis_dev, proj.radius,
-                                                          proj.tile_rect, proj.mean2d, proj.conic_o, sc, tiles_x,
-                                                          diff_size, diff);
+                     proj.tile_rect, proj.tile_runs, proj.mean2d, proj.conic_o, sc, tiles_x, diff_size, diff);
         } else {
             launch_k(k_tile_diff<false>, (n + 1023) / 1024, 1024, 0, st, n, n_vis_dev ? order : nullptr, n_vis_dev,
-                                                                    proj.radius, proj.tile_rect, proj.mean2d,
-                                                                    proj.conic_o, sc, tiles_x, diff_size, diff);
+                     proj.radius, proj.tile_rect, proj.tile_runs, proj.mean2d, proj.conic_o, sc, tiles_x, diff_size,
+                     diff);
         }
     }
     {
@@ -1358,10 +1376,10 @@ cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int til
             TRY(cudaFuncSetAttribute(k_tile_setup<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)setup_smem));
             launch_k(k_tile_setup<true>, 1, 1024, setup_smem, st, tiles_x, tiles_y, diff, counts, out.num_instances, cap,
-                                                            tps, out.ranges, tbase);
+                     tps, out.ranges, tbase);
         } else {
             launch_k(k_tile_setup<false>, 1, 1024, 0, st, tiles_x, tiles_y, diff, counts, out.num_instances, cap, tps,
-                                                    out.ranges, tbase);
+                     out.ranges, tbase);
         }
     }
     TRY(cudaGetLastError());
@@ -1369,7 +1387,11 @@ cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int til
     uint32_t *tk_a = reinterpret_cast<uint32_t *>(at(0)), *tv_a = reinterpret_cast<uint32_t *>(at(1));
     uint32_t *tk_b = reinterpret_cast<uint32_t *>(at(2)), *tv_b = reinterpret_cast<uint32_t *>(at(3));
     uint32_t *offs = reinterpret_cast<uint32_t *>(at(15));
-    if (nb > 0) launch_k(k_splat_offsets, nb, kScanThreads, 0, st, n, order, proj.tiles_touched, block_off, out.num_instances, offs);
+    uint2 *bounds = kPassOnesweep ? reinterpret_cast<uint2 *>(at(20)) : nullptr;
+    const uint32_t max_parts = (uint32_t)((capacity + kSortTile - 1) / kSortTile);
+    if (nb > 0)
+        launch_k(k_splat_offsets, nb, kScanThreads, 0, st, n, order, proj.tiles_touched, block_off, out.num_instances,
+                 offs, bounds, max_parts);
     uint32_t *tph = reinterpret_cast<uint32_t *>(at(11));
     const uint32_t n_parts = (uint32_t)((grid + kSortTile - 1) / kSortTile);
     uint32_t *lb = reinterpret_cast<uint32_t *>(at(18));
@@ -1382,16 +1404,14 @@ cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int til
         const size_t smem = last0 ? DupStaging<false>::bytes : DupStaging<true>::bytes;
         if (last0) {
             TRY(cudaFuncSetAttribute(k_dup_sweep<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            launch_k(k_dup_sweep<false>, n_parts, kSortThreads, smem, st, n, order, offs, proj.tile_rect, proj.mean2d,
-                                                                    proj.conic_o, sc, tiles_x,
-                                                                    out.num_instances, cap, tps.bits[0], tbase, lb,
-                                                                    counters, out.status, k0, v0);
+            launch_k(k_dup_sweep<false>, n_parts, kSortThreads, smem, st, n, order, offs, bounds, proj.tile_rect,
+                     proj.tile_runs, proj.mean2d, proj.conic_o, sc, tiles_x, out.num_instances, cap, tps.bits[0],
+                     tbase, lb, counters, out.status, k0, v0);
         } else {
             TRY(cudaFuncSetAttribute(k_dup_sweep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            launch_k(k_dup_sweep<true>, n_parts, kSortThreads, smem, st, n, order, offs, proj.tile_rect, proj.mean2d,
-                                                                   proj.conic_o, sc, tiles_x,
-                                                                   out.num_instances, cap, tps.bits[0], tbase, lb,
-                                                                   counters, out.status, k0, v0);
+            launch_k(k_dup_sweep<true>, n_parts, kSortThreads, smem, st, n, order, offs, bounds, proj.tile_rect,
+                     proj.tile_runs, proj.mean2d, proj.conic_o, sc, tiles_x, out.num_instances, cap, tps.bits[0],
+                     tbase, lb, counters, out.status, k0, v0);
         }
         TRY(cudaGetLastError());
         uint32_t *ka = tk_b, *va = tv_b, *kb = tk_a, *vb = tv_a;
@@ -1411,10 +1431,9 @@ cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int til
     } else if (grid > 0) {
         // reduce-then-scan passes: the duplication also writes the first pass's histograms
         if (n > 0)
-            launch_k(k_duplicate_balanced, n_parts, kScanThreads, 0, st, n, order, offs, proj.tile_rect, proj.mean2d,
-                                                                   proj.conic_o, sc, tiles_x,
-                                                                   out.num_instances, cap, tk_a, tv_a, tps.bits[0],
-                                                                   n_parts, tph);
+            launch_k(k_duplicate_balanced, n_parts, kScanThreads, 0, st, n, order, offs, proj.tile_rect,
+                     proj.tile_runs, proj.mean2d, proj.conic_o, sc, tiles_x, out.num_instances, cap, tk_a, tv_a,
+                     tps.bits[0], n_parts, tph);
         else
             TRY(cudaMemsetAsync(tph, 0, ((size_t)n_parts << tps.bits[0]) * 4, st));
         TRY(cudaGetLastError());

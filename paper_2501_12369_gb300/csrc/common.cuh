@@ -297,6 +297,43 @@ __device__ __forceinline__ bool span_row(const SpanSplat &p, const SpanCtx &sc, 
     return c0 <= c1;
 }
 
+// The runs packed per splat (tile_runs): for a rectangle of at most 4 rows and 15 columns,
+// byte k holds row r.y + k's run as (c1 - r.x) << 4 | (c0 - r.x), 0x0F for a row without
+// member tiles (c0 > c1 once unpacked); kRunsUnpacked otherwise.
+constexpr uint32_t kRunsUnpacked = 0xffffffffu;
+constexpr uint32_t kRunsNone = 0x0f0f0f0fu;  // four empty rows
+
+__device__ __forceinline__ bool runs_packable(const int4 &r) { return r.w - r.y < 4 && r.z - r.x < 15; }
+
+__device__ __forceinline__ uint32_t runs_put(uint32_t pk, const int4 &r, int ty, int c0, int c1) {
+    const int sh = 8 * (ty - r.y);
+    return (pk & ~(0xffu << sh)) | ((uint32_t)((c1 - r.x) << 4 | (c0 - r.x)) << sh);
+}
+
+// Calls f(ty, c0, c1) for the run of every tile row of r that has member tiles, top to bottom,
+// until f returns false: unpacked from pk, or computed from splat id's ellipse when pk is
+// kRunsUnpacked.
+template <typename F>
+__device__ __forceinline__ void for_each_run(uint32_t pk, const float2 *__restrict__ mean2d,
+                                             const float4 *__restrict__ conic_o, uint32_t id, const int4 &r,
+                                             const SpanCtx &sc, F &&f) {
+    if (pk != kRunsUnpacked) {
+        for (int ty = r.y; ty <= r.w; ++ty) {
+            const uint32_t b = (pk >> (8 * (ty - r.y))) & 0xffu;
+            const int c0 = r.x + (int)(b & 15u), c1 = r.x + (int)(b >> 4);
+            if (c0 <= c1 && !f(ty, c0, c1)) return;
+        }
+        return;
+    }
+    const float2 mu = __ldg(mean2d + id);
+    const float4 co = __ldg(conic_o + id);
+    const SpanSplat p = span_prepare(mu.x, mu.y, co.x, co.y, co.z, sc.qmax);
+    for (int ty = r.y; ty <= r.w; ++ty) {
+        int c0, c1;
+        if (span_row(p, sc, r, ty, c0, c1) && !f(ty, c0, c1)) return;
+    }
+}
+
 // Member tiles of a splat in row-major order: the tile of its l-th instance (l below its count).
 __device__ __forceinline__ uint32_t instance_tile_p(const SpanSplat &p, const int4 &r, uint32_t l, int tiles_x,
                                                     const SpanCtx &sc) {

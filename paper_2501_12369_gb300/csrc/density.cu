@@ -255,7 +255,7 @@ cudaError_t launch_densify_stats(const float *grad2d, const int *radius, int n, 
                                  float *count, int *max_radius, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
     launch_k(k_densify_stats, (n + 255) / 256, 256, 0, st, reinterpret_cast<const float4 *>(grad2d), radius, n, 0.5f * W,
-                                                     0.5f * H, accum, count, max_radius);
+             0.5f * H, accum, count, max_radius);
     return cudaGetLastError();
 }
 

@@ -263,18 +263,25 @@ k_preprocess(int n, const float *__restrict__ means, const float *__restrict__ s
     const float4 qr = __ldg(quats + i);
     Geom g;
     uint32_t cnt = 0;  // member tiles: the ellipse's run in every row of the rectangle
+    uint32_t runs = kRunsUnpacked;
     if (project_fixed(m, s, qr, cam, psi, tile, g)) {
         const SpanCtx sc = make_span_ctx(qmax, tile, cam.W, cam.H);
         const int4 r = make_int4(g.rect[0], g.rect[1], g.rect[2], g.rect[3]);
+        const bool pack = runs_packable(r);
+        if (pack) runs = kRunsNone;
         const SpanSplat sp = span_prepare(g.u0, g.u1, g.A, g.B, g.C, qmax);
         for (int ty = r.y; ty <= r.w; ++ty) {
             int c0, c1;
-            if (span_row(sp, sc, r, ty, c0, c1)) cnt += (uint32_t)(c1 - c0 + 1);
+            if (span_row(sp, sc, r, ty, c0, c1)) {
+                cnt += (uint32_t)(c1 - c0 + 1);
+                if (pack) runs = runs_put(runs, r, ty, c0, c1);
+            }
         }
     }
     if (cnt == 0) {  // culled, or an ellipse that reaches no tile
         out.radius[i] = 0;
         out.tiles_touched[i] = 0;
+        out.tile_runs[i] = kRunsUnpacked;
         out.tile_rect[i] = make_int4(0, 0, 0, 0);
         out.depth[i] = 0.0f;
         return;
@@ -283,6 +290,7 @@ k_preprocess(int n, const float *__restrict__ means, const float *__restrict__ s
     out.radius[i] = g.radius;
     out.tile_rect[i] = make_int4(g.rect[0], g.rect[1], g.rect[2], g.rect[3]);
     out.tiles_touched[i] = cnt;
+    out.tile_runs[i] = runs;
     out.mean2d[i] = make_float2(g.u0, g.u1);
     out.conic_o[i] = make_float4(g.A, g.B, g.C, __ldg(opac + i));
 

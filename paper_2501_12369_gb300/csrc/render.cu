@@ -390,8 +390,8 @@ cudaError_t fwd_t(int n_tiles, const uint2 *ranges, const uint32_t *values, cons
                   const KernelSpec &ks, float *image, float *t_final, uint32_t *last, uint32_t *n_contrib,
                   cudaStream_t st) {
     launch_k(k_render_fwd<KIND, TILE>, n_tiles, RenderShape<TILE>::NT, 0, st,
-        ranges, values, mean2d, conic_o, rgb, cam.W, cam.H, tiles_x, qmax, strict, ks,
-        Bg{cam.bg[0], cam.bg[1], cam.bg[2]}, image, t_final, last, n_contrib);
+             ranges, values, mean2d, conic_o, rgb, cam.W, cam.H, tiles_x, qmax, strict, ks,
+             Bg{cam.bg[0], cam.bg[1], cam.bg[2]}, image, t_final, last, n_contrib);
     return cudaGetLastError();
 }
 
@@ -401,8 +401,8 @@ cudaError_t bwd_t(int n_tiles, const uint2 *ranges, const uint32_t *values, cons
                   const KernelSpec &ks, const float *t_final, const uint32_t *last, const float *dL, float *grad2d,
                   cudaStream_t st) {
     launch_k(k_render_bwd<KIND, TILE>, n_tiles, RenderShape<TILE>::NT, 0, st,
-        ranges, values, mean2d, conic_o, rgb, cam.W, cam.H, tiles_x, qmax, strict, ks,
-        Bg{cam.bg[0], cam.bg[1], cam.bg[2]}, t_final, last, dL, reinterpret_cast<float4 *>(grad2d));
+             ranges, values, mean2d, conic_o, rgb, cam.W, cam.H, tiles_x, qmax, strict, ks,
+             Bg{cam.bg[0], cam.bg[1], cam.bg[2]}, t_final, last, dL, reinterpret_cast<float4 *>(grad2d));
     return cudaGetLastError();
 }
 
@@ -467,7 +467,7 @@ cudaError_t fwd_batch_t(const BatchView *views, int n_views, int total_tiles, ui
     e = cudaMemsetAsync(queue, 0, sizeof(uint32_t), st);
     if (e != cudaSuccess) return e;
     launch_k(k_render_fwd_batch<KIND, TILE>, (int)grid, RenderShape<TILE>::NT, 0, st, views, n_views, total_tiles, queue,
-                                                                                 qmax, strict, ks);
+             qmax, strict, ks);
     return cudaGetLastError();
 }
 

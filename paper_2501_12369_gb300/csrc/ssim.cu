@@ -203,7 +203,7 @@ cudaError_t launch_l1_dssim(const float *image, const float *target, int W, int 
     const dim3 grid((W + kSsimTs - 1) / kSsimTs, (H + kSsimTs - 1) / kSsimTs, 3);
     launch_k(k_ssim_fwd, grid, kSsimThreads, 0, st, image, target, W, H, win, maps, maps + n, maps + 2 * n, sums);
     launch_k(k_ssim_bwd, grid, kSsimThreads, 0, st, image, target, W, H, win, maps, maps + n, maps + 2 * n, lam, sums, dL,
-                                              loss);
+             loss);
     return cudaGetLastError();
 }
 

@@ -134,30 +134,30 @@ cudaError_t launch_adam(const darb_train_params &p, const darb_splat_grads &g, c
     const long long K = (long long)(p.sh_degree + 1) * (p.sh_degree + 1);
     auto g4 = [](long long count) { return grid_for((count + 3) / 4); };
     launch_k(k_adam4<0, 0, 0>, g4(3 * n), 256, 0, st, 3 * n, p.means, g.dmeans, s.m_means, s.v_means, c.lr_means,
-                                                 c.lr_means, b1, b2, eps, ibc1, ibc2, nullptr);
+             c.lr_means, b1, b2, eps, ibc1, ibc2, nullptr);
     launch_k(k_adam4<1, 0, 0>, g4(3 * n), 256, 0, st, 3 * n, p.log_scales, g.dscales, s.m_scales, s.v_scales, c.lr_scales,
-                                                 c.lr_scales, b1, b2, eps, ibc1, ibc2, p.scales);
+             c.lr_scales, b1, b2, eps, ibc1, ibc2, p.scales);
     launch_k(k_adam4<0, 0, 0>, g4(4 * n), 256, 0, st, 4 * n, p.quats, g.dquats, s.m_quats, s.v_quats, c.lr_quats,
-                                                 c.lr_quats, b1, b2, eps, ibc1, ibc2, nullptr);
+             c.lr_quats, b1, b2, eps, ibc1, ibc2, nullptr);
     launch_k(k_adam4<2, 0, 0>, g4(n), 256, 0, st, n, p.opacity_logits, g.dopacities, s.m_opac, s.v_opac, c.lr_opacities,
-                                             c.lr_opacities, b1, b2, eps, ibc1, ibc2, p.opacities);
+             c.lr_opacities, b1, b2, eps, ibc1, ibc2, p.opacities);
     const long long cs = 3 * K * n;
     switch (p.sh_degree) {
     case 0:
         launch_k(k_adam_rows<3, 3>, grid_for(cs), 256, 0, st, cs, p.sh, g.dsh, s.m_sh, s.v_sh, c.lr_sh_dc, c.lr_sh_rest, b1,
-                                                         b2, eps, ibc1, ibc2);
+                 b2, eps, ibc1, ibc2);
         break;
     case 1:
         launch_k(k_adam4<0, 12, 3>, g4(cs), 256, 0, st, cs, p.sh, g.dsh, s.m_sh, s.v_sh, c.lr_sh_dc, c.lr_sh_rest, b1, b2,
-                                                  eps, ibc1, ibc2, nullptr);
+                 eps, ibc1, ibc2, nullptr);
         break;
     case 2:
         launch_k(k_adam_rows<27, 3>, grid_for(cs), 256, 0, st, cs, p.sh, g.dsh, s.m_sh, s.v_sh, c.lr_sh_dc, c.lr_sh_rest, b1,
-                                                          b2, eps, ibc1, ibc2);
+                 b2, eps, ibc1, ibc2);
         break;
     default:
         launch_k(k_adam4<0, 48, 3>, g4(cs), 256, 0, st, cs, p.sh, g.dsh, s.m_sh, s.v_sh, c.lr_sh_dc, c.lr_sh_rest, b1, b2,
-                                                  eps, ibc1, ibc2, nullptr);
+                 eps, ibc1, ibc2, nullptr);
         break;
     }
     return cudaGetLastError();

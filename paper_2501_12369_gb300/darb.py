@@ -43,7 +43,7 @@ class darb_splats(ctypes.Structure):
 
 class darb_projected(ctypes.Structure):
     _fields_ = [("depth", c_vp), ("radius", c_vp), ("tile_rect", c_vp), ("mean2d", c_vp), ("conic_o", c_vp),
-                ("rgb", c_vp), ("clamped", c_vp), ("tiles_touched", c_vp)]
+                ("rgb", c_vp), ("clamped", c_vp), ("tiles_touched", c_vp), ("tile_runs", c_vp)]
 
 
 class darb_binning(ctypes.Structure):
@@ -292,6 +292,7 @@ class Projected:
     rgb: torch.Tensor
     clamped: torch.Tensor
     tiles_touched: torch.Tensor
+    tile_runs: torch.Tensor
 
     @staticmethod
     def empty(n, device="cuda"):
@@ -299,7 +300,8 @@ class Projected:
         return Projected(torch.empty(n, dtype=torch.float32, **f), torch.empty(n, dtype=torch.int32, **f),
                          torch.empty(n, 4, dtype=torch.int32, **f), torch.empty(n, 2, dtype=torch.float32, **f),
                          torch.empty(n, 4, dtype=torch.float32, **f), torch.empty(n, 3, dtype=torch.float32, **f),
-                         torch.empty(n, dtype=torch.uint8, **f), torch.empty(n, dtype=torch.int32, **f))
+                         torch.empty(n, dtype=torch.uint8, **f), torch.empty(n, dtype=torch.int32, **f),
+                         torch.empty(n, dtype=torch.int32, **f))
 
     def struct(self) -> darb_projected:
         return darb_projected(*(_p(getattr(self, f.name)) for f in dataclasses.fields(self)))

@@ -47,6 +47,38 @@ def check_preprocess(proj, ref):
     assert not (diff & ~near0).any(), "colour clamp flags differ"
 
 
+def check_tile_runs(proj, ref, ref_lists, tiles_x):
+    """The packed row runs equal, row by row, the oracle's member tiles of every visible splat
+    whose rectangle spans at most 4 rows and 15 columns; 0xFFFFFFFF for the others."""
+    runs = to_np(proj.tile_runs).view(np.uint32)
+    rect = ref["rect"]
+    vis = ~ref["culled"].astype(bool)
+    assert (runs[~vis] == 0xFFFFFFFF).all(), "culled splats must carry 0xFFFFFFFF"
+    tiles = (ref_lists["keys"] >> np.uint64(32)).astype(np.int64)
+    ids = ref_lists["ids"].astype(np.int64)
+    order = np.argsort(ids, kind="stable")
+    ids_s, tiles_s = ids[order], tiles[order]
+    starts = np.searchsorted(ids_s, np.arange(len(rect) + 1))
+    packed = 0
+    for i in np.flatnonzero(vis):
+        x0, y0, x1, y1 = (int(v) for v in rect[i])
+        if y1 - y0 >= 4 or x1 - x0 >= 15:
+            assert runs[i] == 0xFFFFFFFF, f"splat {i}: large rectangle must not be packed"
+            continue
+        packed += 1
+        member = tiles_s[starts[i]:starts[i + 1]]
+        for k in range(y1 - y0 + 1):
+            b = (int(runs[i]) >> (8 * k)) & 0xFF
+            c0, c1 = x0 + (b & 15), x0 + (b >> 4)
+            cols = np.sort(member[member // tiles_x == y0 + k] % tiles_x)
+            if cols.size == 0:
+                assert c0 > c1, f"splat {i} row {y0 + k}: expected no run"
+            else:
+                assert (c0, c1) == (int(cols[0]), int(cols[-1])) and cols.size == c1 - c0 + 1, \
+                    f"splat {i} row {y0 + k}: run ({c0}, {c1}) != {cols.tolist()}"
+    return packed
+
+
 def tile_runs(keys_or_none, values, ranges):
     return [values[a:b] for a, b in ranges]
 

@@ -8,8 +8,8 @@ import torch
 import oracle
 from paper_2501_12369_gb300 import darb, synth
 
-from gpu_helpers import (ambiguity_masked_grad, check_lists, check_preprocess, check_render, gpu_forward,
-                         grad_close, to_np)
+from gpu_helpers import (ambiguity_masked_grad, check_lists, check_preprocess, check_render, check_tile_runs,
+                         gpu_forward, grad_close, to_np)
 
 pytestmark = [pytest.mark.gpu,
               pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
@@ -60,7 +60,9 @@ def test_bin_sort_is_bit_exact(tile, strategy):
     proj, bins, img = r.forward(darb.splats_to_device(s))
     torch.cuda.synchronize()
     ref = oracle.project(s, cam, oracle.kernel_params("half_cosine"), tile, True)
-    check_lists(bins, oracle.build_lists(ref, cam, tile))
+    lists = oracle.build_lists(ref, cam, tile)
+    check_lists(bins, lists)
+    assert check_tile_runs(proj, ref, lists, (cam.width + tile - 1) // tile) > 0
 
 
 def test_bin_sort_strategies_agree_on_a_large_scene():

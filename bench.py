@@ -305,18 +305,23 @@ def algorithmic_bytes(stage, n, M, passes, sh_k, strategy=0, tile_passes=2, n_vi
     sh_b = sh_k * 3 * 4
     if stage == "preprocess":
         # visible: read means, scales, quats, opacity, SH; write depth, radius, rect, mean2d,
-        # conic_o, rgb, clamp bits, tiles.  culled: read means, scales, quats; write depth,
-        # radius, rect, tiles
-        return n_vis * (12 + 12 + 16 + 4 + sh_b + 4 + 4 + 16 + 8 + 16 + 12 + 1 + 4) + (n - n_vis) * (40 + 28)
+        # conic_o, rgb, clamp bits, tiles, packed runs.  culled: read means, scales, quats; write
+        # depth, radius, rect, tiles, packed runs
+        return n_vis * (12 + 12 + 16 + 4 + sh_b + 4 + 4 + 16 + 8 + 16 + 12 + 1 + 4 + 4) + (n - n_vis) * (40 + 32)
     if stage == "bin_sort":
         if strategy == 1:
             return n * (4 + 4 + 16 + 4) + M * (12 + 8 + 24 * passes + 8)
-        # per splat: depth keys (read depth+radius, write key), 4 depth passes (16 B each), tiles
-        # gathered twice in depth order, offsets written and read, rect twice (difference array,
-        # duplication); per instance: the duplication fused with the first tile pass writes
-        # 8 B, every later pass reads 8 B and writes 8 B, the last writes only 4-byte values
+        # per splat: radius read (visible count), radius + depth read (compaction), tiles
+        # gathered in depth order twice (block sums, offsets), offsets written; per culled splat:
+        # its index written to both order buffers; per visible splat: key and index written by
+        # the compaction, the key read by the histogram, 4 depth passes (read 8 B, write 8 B; the
+        # last writes only values), order + radius + rectangle + packed runs read by the
+        # difference array, offset + order + rectangle + packed runs read by the duplication;
+        # per instance: the duplication fused with the first tile pass writes 8 B, every later
+        # pass reads 8 B and writes 8 B, the last writes only 4-byte values
         per_instance = 4 if tile_passes == 1 else 8 + 16 * (tile_passes - 2) + 12
-        return n * (8 + 4 + 4 * 16 + 8 + 8 + 32) + M * per_instance
+        return (n * (4 + 8 + 4 + 4 + 4) + (n - n_vis) * 8 + n_vis * (8 + 4 + 16 * 3 + 12 + 28 + 28)
+                + M * per_instance)
     if stage == "preprocess_bwd":
         # every splat: radius read, all gradients written; visible: parameters, grad2d and clamp
         # bits read
@@ -595,9 +600,10 @@ def launches_per_step(strategy, tile_bits, fused=True):
     """Kernels of libdarb.so launched per training step (memsets excluded)."""
     if strategy == 1:  # 64-bit keys: block sums, scan, duplicate, histogram, hist scan, passes, ranges
         sort = 6 + (32 + tile_bits + 7) // 8
-    else:  # depth keys, histogram, hist scan, 4 depth passes, block sums, scan, tile diff, tile setup,
-        # offsets, duplication fused with the first tile pass, the other tile passes
-        sort = 3 + 4 + 5 + max(1, (tile_bits + 7) // 8)
+    else:  # visible count, its scan, depth compaction, histogram, hist scan, 4 depth passes, block sums,
+        # scan, tile diff, tile setup, offsets, duplication fused with the first tile pass, the other
+        # tile passes
+        sort = 5 + 4 + 5 + max(1, (tile_bits + 7) // 8)
     # preprocess, render_fwd, l1, render_bwd, then preprocess_bwd + 5 Adam groups or one fused kernel
     return 1 + sort + 1 + 1 + 1 + (1 if fused else 1 + 5)
 

@@ -292,7 +292,7 @@ class TrainStep:
 # DRAM bytes (read + write) per splat of k_preprocess_bwd_adam<3>: dram__bytes_read.sum +
 # dram__bytes_write.sum of one launch on 1M clustered splats (1920x1080, tile 32; the
 # train_tail case of paper_2501_12369_gb300.profile_cases), divided by the splat count.
-TRAFFIC_BWD_ADAM_PER_SPLAT = 1437.01
+TRAFFIC_BWD_ADAM_PER_SPLAT = 1436.0
 
 STAGES_FUSED = ["preprocess", "bin_sort", "render_fwd", "l1_loss", "render_bwd", "preprocess_bwd_adam"]
 STAGES_SEPARATE = ["preprocess", "bin_sort", "render_fwd", "l1_loss", "render_bwd", "preprocess_bwd", "adam"]
@@ -314,13 +314,14 @@ def algorithmic_bytes(stage, n, M, passes, sh_k, strategy=0, tile_passes=2, n_vi
         # per splat: radius read (visible count), radius + depth read (compaction), tiles
         # gathered in depth order twice (block sums, offsets), offsets written; per culled splat:
         # its index written to both order buffers; per visible splat: key and index written by
-        # the compaction, the key read by the histogram, 4 depth passes (read 8 B, write 8 B; the
-        # last writes only values), order + radius + rectangle + packed runs read by the
-        # difference array, offset + order + rectangle + packed runs read by the duplication;
+        # the compaction (which also takes the digit histograms), 4 depth passes (read 8 B,
+        # write 8 B; the last writes only values), order + radius + rectangle + packed runs read
+        # by the difference array, offset + order + rectangle + packed runs read by the
+        # duplication;
         # per instance: the duplication fused with the first tile pass writes 8 B, every later
         # pass reads 8 B and writes 8 B, the last writes only 4-byte values
         per_instance = 4 if tile_passes == 1 else 8 + 16 * (tile_passes - 2) + 12
-        return (n * (4 + 8 + 4 + 4 + 4) + (n - n_vis) * 8 + n_vis * (8 + 4 + 16 * 3 + 12 + 28 + 28)
+        return (n * (4 + 8 + 4 + 4 + 4) + (n - n_vis) * 8 + n_vis * (8 + 16 * 3 + 12 + 28 + 28)
                 + M * per_instance)
     if stage == "preprocess_bwd":
         # every splat: radius read, all gradients written; visible: parameters, grad2d and clamp
@@ -413,7 +414,7 @@ def run_ours(args):
     targets = [torch.from_numpy(synth.random_target(1080, 1920, seed=10 + i)).to(device) for i in range(4)]
 
     def step(i, ev=None):
-        ts.target.copy_(targets[i % 4], non_blocking=True) if ev is None else None
+        ts.target = targets[i % 4]
         ts.train(cam_seq[i % len(cam_seq)], ev)
 
     # tile-size autotuning over whole training steps (before anything is timed)
@@ -445,9 +446,8 @@ def run_ours(args):
         step(i)
     torch.cuda.synchronize()
 
-    # timed training steps with per-stage events
-    n_ev = len(STAGES) + 1
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(n_ev)] for _ in range(args.steps)]
+    # timed training steps (no events inside the steps, so that consecutive kernels overlap as
+    # they do in a training loop)
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(local)
     barrier(dist)
@@ -455,8 +455,7 @@ def run_ours(args):
     clocks.start()
     start.record()
     for k in range(args.steps):
-        ts.target = targets[k % 4]
-        step(args.warmup + k, evs[k])
+        step(args.warmup + k)
     end.record()
     torch.cuda.synchronize()
     clk = clocks.stop()
@@ -466,6 +465,14 @@ def run_ours(args):
     status = int(ts.bins.status.item())
     if status != 0:
         raise RuntimeError(f"bin_sort reported status {status} during the timed run")
+
+    # the same steps again with an event between stages, for the per-stage times
+    n_ev = len(STAGES) + 1
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(n_ev)] for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        step(args.warmup + k, evs[k])
+    torch.cuda.synchronize()
     stage_ms = {s: 0.0 for s in STAGES}
     for e in evs:
         for j, s in enumerate(STAGES):
@@ -483,19 +490,39 @@ def run_ours(args):
     fwd_ms = max_over_ranks(dist, fstart.elapsed_time(fend), device)
     fwd_mpix = world * args.steps * 1920 * 1080 / (fwd_ms / 1e3) / 1e6
 
-    # end to end through the C ABI with host buffers: target image H2D from pinned memory,
-    # loss D2H into pinned memory, every step
+    # end to end through the C ABI with host buffers: every step's target image H2D from pinned
+    # memory and its loss D2H into pinned memory.  The copy of step k + 1's target runs on a
+    # copy stream into the other of two device buffers while step k computes (the buffer is
+    # reused only after the step that read it has finished its loss).
     host_targets = [t.cpu().pin_memory() for t in targets]
     loss_host = torch.empty(args.steps, dtype=torch.float32).pin_memory()
-    dev_target = torch.empty_like(targets[0])
-    ts.target = dev_target
+    dev_targets = [torch.empty_like(targets[0]) for _ in range(2)]
+    copy_stream = torch.cuda.Stream(device=device)
+    main_stream = torch.cuda.current_stream(device)
+    copied = [torch.cuda.Event() for _ in range(2)]
+    freed = [torch.cuda.Event() for _ in range(2)]
     estart, eend = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier(dist)
     torch.cuda.synchronize()
     estart.record()
+
+    def prefetch(k):
+        b = k % 2
+        with torch.cuda.stream(copy_stream):
+            if k >= 2:
+                copy_stream.wait_event(freed[b])
+            dev_targets[b].copy_(host_targets[k % 4], non_blocking=True)
+            copied[b].record(copy_stream)
+
+    prefetch(0)
     for k in range(args.steps):
-        dev_target.copy_(host_targets[k % 4], non_blocking=True)
+        if k + 1 < args.steps:
+            prefetch(k + 1)
+        b = k % 2
+        main_stream.wait_event(copied[b])
+        ts.target = dev_targets[b]
         ts.train(cam_seq[args.warmup + k])
+        freed[b].record(main_stream)
         loss_host[k:k + 1].copy_(ts.loss, non_blocking=True)
     eend.record()
     torch.cuda.synchronize()
@@ -600,10 +627,10 @@ def launches_per_step(strategy, tile_bits, fused=True):
     """Kernels of libdarb.so launched per training step (memsets excluded)."""
     if strategy == 1:  # 64-bit keys: block sums, scan, duplicate, histogram, hist scan, passes, ranges
         sort = 6 + (32 + tile_bits + 7) // 8
-    else:  # visible count, its scan, depth compaction, histogram, hist scan, 4 depth passes, block sums,
-        # scan, tile diff, tile setup, offsets, duplication fused with the first tile pass, the other
-        # tile passes
-        sort = 5 + 4 + 5 + max(1, (tile_bits + 7) // 8)
+    else:  # visible count, its scan, depth compaction with the histograms, hist scan, 4 depth passes,
+        # block sums, scan, tile diff, tile setup, offsets, duplication fused with the first tile
+        # pass, the other tile passes
+        sort = 4 + 4 + 5 + max(1, (tile_bits + 7) // 8)
     # preprocess, render_fwd, l1, render_bwd, then preprocess_bwd + 5 Adam groups or one fused kernel
     return 1 + sort + 1 + 1 + 1 + (1 if fused else 1 + 5)
 

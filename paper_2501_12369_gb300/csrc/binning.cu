@@ -8,8 +8,10 @@
 // in ascending splat index.  Two strategies produce it bit for bit:
 //
 // DARB_SORT_DEPTH_THEN_TILE (default)
-//   k_vis_count, k_depth_compact,         sort the visible splats by depth bits (stable, so equal
-//   4 x k_onesweep<u32>                   depths keep index order): N-sized, cheap
+//   k_vis_count, k_depth_compact          the visible splats' depth keys in index order, with
+//                                         their digit histograms
+//   4 x k_onesweep<u32>                   sort them by depth bits (stable, so equal depths keep
+//                                         index order): N-sized, cheap
 //   k_block_sums / k_scan_block_sums      scan of tiles_touched in that depth order
 //   k_tile_diff / k_tile_setup            per-tile instance counts from the row runs (a row-wise
 //                                         difference array, 2 atomics per run) -> the tile
@@ -1021,10 +1023,14 @@ k_vis_count(int n, const int *__restrict__ radius, uint32_t *__restrict__ block_
 __global__ void __launch_bounds__(kScanThreads)
 k_depth_compact(int n, const int *__restrict__ radius, const float *__restrict__ depth,
                 const unsigned long long *__restrict__ block_offsets, const uint32_t *__restrict__ n_vis,
-                uint32_t *__restrict__ keys, uint32_t *__restrict__ ids0, uint32_t *__restrict__ ids1) {
+                uint32_t *__restrict__ keys, uint32_t *__restrict__ ids0, uint32_t *__restrict__ ids1, PassSpec ps,
+                uint32_t *__restrict__ hist) {
     pdl_entry();
     __shared__ uint32_t s_warp[kScanThreads / 32 + 1];
+    __shared__ uint32_t s_h[kMaxPasses * 256];
+    for (int i = threadIdx.x; i < ps.passes * 256; i += kScanThreads) s_h[i] = 0;  // ordered by the scans
     const int base = blockIdx.x * kScanTile;
+    const int lane = threadIdx.x & 31;
     const uint32_t vis0 = (uint32_t)block_offsets[blockIdx.x];
     const uint32_t cul0 = *n_vis + ((uint32_t)base - vis0);  // culled splats before this block
     uint32_t vis = 0, cul = 0;
@@ -1032,19 +1038,30 @@ k_depth_compact(int n, const int *__restrict__ radius, const float *__restrict__
         const int i = base + j * kScanThreads + threadIdx.x;
         const bool valid = i < n;
         const bool v = valid && radius[i] != 0;
-        uint32_t tv, tc;
-        const uint32_t rv = block_exclusive_scan<kScanThreads>(v ? 1u : 0u, s_warp, tv);
-        const uint32_t rc = block_exclusive_scan<kScanThreads>((valid && !v) ? 1u : 0u, s_warp, tc);
+        // visible count in the low half-word, culled count in the high one (at most 256 each)
+        uint32_t t;
+        const uint32_t r = block_exclusive_scan<kScanThreads>(v ? 1u : (valid ? 0x10000u : 0u), s_warp, t);
+        const uint32_t k = v ? __float_as_uint(depth[i]) : 0u;
         if (v) {
-            keys[vis0 + vis + rv] = __float_as_uint(depth[i]);
-            ids0[vis0 + vis + rv] = (uint32_t)i;
+            keys[vis0 + vis + (r & 0xffffu)] = k;
+            ids0[vis0 + vis + (r & 0xffffu)] = (uint32_t)i;
         } else if (valid) {
-            ids0[cul0 + cul + rc] = (uint32_t)i;
-            ids1[cul0 + cul + rc] = (uint32_t)i;
+            ids0[cul0 + cul + (r >> 16)] = (uint32_t)i;
+            ids1[cul0 + cul + (r >> 16)] = (uint32_t)i;
         }
-        vis += tv;
-        cul += tc;
+#pragma unroll
+        for (int p = 0; p < kMaxPasses; ++p) {  // digit histograms of the visible keys
+            if (p >= ps.passes) break;
+            const uint32_t d = v ? (k >> ps.shift[p]) & ((1u << ps.bits[p]) - 1u) : 0xffffffffu;
+            const uint32_t peers = __match_any_sync(0xffffffffu, d);
+            if (v && lane == __ffs(peers) - 1) atomicAdd(&s_h[p * 256 + d], (uint32_t)__popc(peers));
+        }
+        vis += t & 0xffffu;
+        cul += t >> 16;
     }
+    __syncthreads();
+    for (int i = threadIdx.x; i < ps.passes * 256; i += kScanThreads)
+        if (s_h[i]) atomicAdd(&hist[i], s_h[i]);
 }
 
 __global__ void __launch_bounds__(256)
@@ -1292,14 +1309,12 @@ cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int til
             launch_k(k_vis_count, nb, kScanThreads, 0, st, n, proj.radius, block_sums);
             launch_k(k_scan_block_sums, 1, 1024, 0, st, nb, block_sums, block_off, nv, out.status,
                      (unsigned long long)n);
+            uint32_t *dhist = reinterpret_cast<uint32_t *>(at(10)) + kMaxPasses * 256;
             launch_k(k_depth_compact, nb, kScanThreads, 0, st, n, proj.radius, proj.depth, block_off, nv, kbuf[0],
-                     vbuf[0], vbuf[1]);
+                     vbuf[0], vbuf[1], dps, dhist);
             n_vis = nv;
             n_vis_dev = nv;
             vin = vbuf[0];
-            uint32_t *dhist = reinterpret_cast<uint32_t *>(at(10)) + kMaxPasses * 256;
-            const int hb = std::min((n + 255) / 256, 152 * 8);
-            launch_k(k_sort_hist<uint32_t>, hb, 256, 0, st, kbuf[0], n_vis, (unsigned long long)n, dps, dhist);
             launch_k(k_hist_scan, dps.passes, 256, 0, st, dhist, dbase);
         } else {
             launch_k(k_depth_keys, (n + 255) / 256, 256, 0, st, n, proj.radius, proj.depth, kbuf[0]);

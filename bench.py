@@ -307,7 +307,7 @@ def algorithmic_bytes(stage, n, M, passes, sh_k, strategy=0, tile_passes=2, n_vi
         # visible: read means, scales, quats, opacity, SH; write depth, radius, rect, mean2d,
         # conic_o, rgb, clamp bits, tiles, packed runs.  culled: read means, scales, quats; write
         # depth, radius, rect, tiles, packed runs
-        return n_vis * (12 + 12 + 16 + 4 + sh_b + 4 + 4 + 16 + 8 + 16 + 12 + 1 + 4 + 4) + (n - n_vis) * (40 + 32)
+        return n_vis * (12 + 12 + 16 + 4 + sh_b + 4 + 4 + 16 + 8 + 16 + 12 + 1 + 4 + 8) + (n - n_vis) * (40 + 36)
     if stage == "bin_sort":
         if strategy == 1:
             return n * (4 + 4 + 16 + 4) + M * (12 + 8 + 24 * passes + 8)
@@ -315,13 +315,13 @@ def algorithmic_bytes(stage, n, M, passes, sh_k, strategy=0, tile_passes=2, n_vi
         # gathered in depth order twice (block sums, offsets), offsets written; per culled splat:
         # its index written to both order buffers; per visible splat: key and index written by
         # the compaction (which also takes the digit histograms), 4 depth passes (read 8 B,
-        # write 8 B; the last writes only values), order + radius + rectangle + packed runs read
-        # by the difference array, offset + order + rectangle + packed runs read by the
-        # duplication;
+        # write 8 B; the last writes only values), order + radius + rectangle + packed runs
+        # (8 B) read by the difference array, offset + order + rectangle + packed runs read by
+        # the duplication;
         # per instance: the duplication fused with the first tile pass writes 8 B, every later
         # pass reads 8 B and writes 8 B, the last writes only 4-byte values
         per_instance = 4 if tile_passes == 1 else 8 + 16 * (tile_passes - 2) + 12
-        return (n * (4 + 8 + 4 + 4 + 4) + (n - n_vis) * 8 + n_vis * (8 + 16 * 3 + 12 + 28 + 28)
+        return (n * (4 + 8 + 4 + 4 + 4) + (n - n_vis) * 8 + n_vis * (8 + 16 * 3 + 12 + 32 + 32)
                 + M * per_instance)
     if stage == "preprocess_bwd":
         # every splat: radius read, all gradients written; visible: parameters, grad2d and clamp

@@ -127,9 +127,10 @@ typedef struct {
  * tiles_touched [n]: member tiles.  In each tile row of the rectangle they are the run of
  * columns whose pixel centres the ellipse {q <= q_max} reaches over the row's band of
  * pixel-centre heights (the Sec. 3 footprint's support, tested per tile row).
- * tile_runs [n]: the same runs packed, for darb_bin_sort: when the rectangle spans at most 4
- * rows and 15 columns, byte k holds row ty0 + k's run as (c1 - tx0) << 4 | (c0 - tx0), or
- * 0x0F for a row without member tiles; 0xFFFFFFFF for larger rectangles and culled splats. */
+ * tile_runs [n]: the same runs packed, for darb_bin_sort: when the rectangle spans at most 8
+ * rows and 15 columns, byte k (from the least significant) holds row ty0 + k's run as
+ * (c1 - tx0) << 4 | (c0 - tx0), or 0x0F for a row without member tiles (also for the bytes
+ * past the last row); all ones for larger rectangles and culled splats. */
 typedef struct {
     float *depth;
     int32_t *radius;
@@ -139,7 +140,7 @@ typedef struct {
     float *rgb;
     uint8_t *clamped;
     uint32_t *tiles_touched;
-    uint32_t *tile_runs;
+    uint64_t *tile_runs;
 } darb_projected;
 
 /* Outputs of darb_bin_sort, device pointers.

@@ -41,7 +41,7 @@ size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 size_t projected_bytes(int n) {
     const size_t N = (size_t)n;
     return a256(4 * N) + a256(4 * N) + a256(16 * N) + a256(8 * N) + a256(16 * N) + a256(12 * N) + a256(N) +
-           a256(4 * N) + a256(4 * N);
+           a256(4 * N) + a256(8 * N);
 }
 
 struct BatchLayout {
@@ -99,7 +99,7 @@ ProjectedOut view_projected(unsigned char *base, int n) {
     o += a256(N);
     p.tiles_touched = reinterpret_cast<uint32_t *>(base + o);
     o += a256(4 * N);
-    p.tile_runs = reinterpret_cast<uint32_t *>(base + o);
+    p.tile_runs = reinterpret_cast<uint64_t *>(base + o);
     return p;
 }
 

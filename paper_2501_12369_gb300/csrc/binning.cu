@@ -292,7 +292,7 @@ __device__ __forceinline__ int cta_upper_owner(const uint32_t *__restrict__ offs
 template <int NT>
 __device__ __forceinline__ void partition_runs(int first, int count, uint32_t lo, uint32_t hi,
                                                const uint32_t *__restrict__ offs, const uint32_t *__restrict__ order,
-                                               const int4 *__restrict__ rect, const uint32_t *__restrict__ runs,
+                                               const int4 *__restrict__ rect, const uint64_t *__restrict__ runs,
                                                const float2 *__restrict__ mean2d, const float4 *__restrict__ conic_o,
                                                const SpanCtx &sc, int tiles_x, uint32_t *s_base, uint32_t *s_val,
                                                uint32_t *mark) {
@@ -338,7 +338,7 @@ __device__ __forceinline__ void partition_lookup(uint32_t pos, const uint32_t *s
 // ph[d * n_parts + partition].
 __global__ void __launch_bounds__(kScanThreads)
 k_duplicate_balanced(int n, const uint32_t *__restrict__ order, const uint32_t *__restrict__ offs,
-                     const int4 *__restrict__ rect, const uint32_t *__restrict__ runs, const float2 *__restrict__ mean2d,
+                     const int4 *__restrict__ rect, const uint64_t *__restrict__ runs, const float2 *__restrict__ mean2d,
                      const float4 *__restrict__ conic_o, SpanCtx sc, int tiles_x, const uint32_t *__restrict__ num,
                      unsigned long long cap, uint32_t *__restrict__ keys, uint32_t *__restrict__ vals, int bits1,
                      uint32_t n_parts, uint32_t *__restrict__ ph) {
@@ -391,7 +391,7 @@ k_duplicate_balanced(int n, const uint32_t *__restrict__ order, const uint32_t *
 template <bool SMEM>
 __global__ void __launch_bounds__(1024)
 k_tile_diff(int n, const uint32_t *__restrict__ order, const uint32_t *__restrict__ n_vis,
-            const int *__restrict__ radius, const int4 *__restrict__ rect, const uint32_t *__restrict__ runs,
+            const int *__restrict__ radius, const int4 *__restrict__ rect, const uint64_t *__restrict__ runs,
             const float2 *__restrict__ mean2d, const float4 *__restrict__ conic_o, SpanCtx sc, int tiles_x,
             int diff_size, int *__restrict__ diff) {
     pdl_entry();
@@ -403,15 +403,37 @@ k_tile_diff(int n, const uint32_t *__restrict__ order, const uint32_t *__restric
     }
     const int w1 = tiles_x + 1;
     const int m = n_vis ? (int)min(*n_vis, (uint32_t)n) : n;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) {
-        const int i = order ? (int)order[k] : k;
-        if (radius[i] == 0) continue;
-        const int4 r = rect[i];
-        for_each_run(runs[i], mean2d, conic_o, (uint32_t)i, r, sc, [&](int ty, int c0, int c1) {
-            atomicAdd(&d[ty * w1 + c0], 1);  // one run of member tiles per row: +1 at c0, -1 after c1
-            atomicAdd(&d[ty * w1 + c1 + 1], -1);
-            return true;
-        });
+    const int lane = threadIdx.x & 31;
+    auto add = [&](int ty, int c0, int c1) {  // one run of member tiles: +1 at c0, -1 after c1
+        atomicAdd(&d[ty * w1 + c0], 1);
+        atomicAdd(&d[ty * w1 + c1 + 1], -1);
+    };
+    // whole warps iterate together (the rows of a large rectangle are shared by the warp)
+    for (int k0 = blockIdx.x * blockDim.x + (int)(threadIdx.x & ~31u); k0 < m; k0 += gridDim.x * blockDim.x) {
+        const int k = k0 + lane;
+        int i = 0;
+        bool live = false;
+        if (k < m) {
+            i = order ? (int)order[k] : k;
+            live = radius[i] != 0;
+        }
+        int4 r = make_int4(0, 0, 0, 0);
+        uint64_t pk = kRunsUnpacked;
+        if (live) {
+            r = rect[i];
+            pk = runs[i];
+        }
+        if (live && pk != kRunsUnpacked) for_each_packed_run(pk, r, [&](int ty, int c0, int c1) {
+                add(ty, c0, c1);
+                return true;
+            });
+        for (uint32_t bm = __ballot_sync(0xffffffffu, live && pk == kRunsUnpacked); bm; bm &= bm - 1) {
+            const int iL = __shfl_sync(0xffffffffu, i, __ffs(bm) - 1);
+            const float2 mu = mean2d[iL];
+            const float4 co = conic_o[iL];
+            warp_runs(mu.x, mu.y, co.x, co.y, co.z, rect[iL], sc,
+                      [&](int ty, int c0, int c1, uint32_t) { add(ty, c0, c1); });
+        }
     }
     if (SMEM) {
         __syncthreads();
@@ -943,7 +965,7 @@ k_onesweep(const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__res
 template <bool WRITE_KEYS>
 __global__ void __launch_bounds__(kSortThreads, kSortCtasPerSm)
 k_dup_sweep(int n, const uint32_t *__restrict__ order, const uint32_t *__restrict__ offs, const uint2 *__restrict__ bounds,
-            const int4 *__restrict__ rect, const uint32_t *__restrict__ runs, const float2 *__restrict__ mean2d,
+            const int4 *__restrict__ rect, const uint64_t *__restrict__ runs, const float2 *__restrict__ mean2d,
             const float4 *__restrict__ conic_o,
             SpanCtx sc, int tiles_x, const uint32_t *num, unsigned long long cap, int bits,
             const uint32_t *__restrict__ digit_base, uint32_t *lookback, uint32_t *part_counter, uint32_t *status,

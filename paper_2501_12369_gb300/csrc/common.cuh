@@ -297,32 +297,40 @@ __device__ __forceinline__ bool span_row(const SpanSplat &p, const SpanCtx &sc, 
     return c0 <= c1;
 }
 
-// The runs packed per splat (tile_runs): for a rectangle of at most 4 rows and 15 columns,
+// The runs packed per splat (tile_runs): for a rectangle of at most 8 rows and 15 columns,
 // byte k holds row r.y + k's run as (c1 - r.x) << 4 | (c0 - r.x), 0x0F for a row without
 // member tiles (c0 > c1 once unpacked); kRunsUnpacked otherwise.
-constexpr uint32_t kRunsUnpacked = 0xffffffffu;
-constexpr uint32_t kRunsNone = 0x0f0f0f0fu;  // four empty rows
+constexpr uint64_t kRunsUnpacked = ~0ull;
+constexpr uint64_t kRunsNone = 0x0f0f0f0f0f0f0f0full;  // eight empty rows
+constexpr int kRunsRows = 8;
 
-__device__ __forceinline__ bool runs_packable(const int4 &r) { return r.w - r.y < 4 && r.z - r.x < 15; }
+__device__ __forceinline__ bool runs_packable(const int4 &r) { return r.w - r.y < kRunsRows && r.z - r.x < 15; }
 
-__device__ __forceinline__ uint32_t runs_put(uint32_t pk, const int4 &r, int ty, int c0, int c1) {
+__device__ __forceinline__ uint64_t runs_put(uint64_t pk, const int4 &r, int ty, int c0, int c1) {
     const int sh = 8 * (ty - r.y);
-    return (pk & ~(0xffu << sh)) | ((uint32_t)((c1 - r.x) << 4 | (c0 - r.x)) << sh);
+    return (pk & ~(0xffull << sh)) | ((uint64_t)((c1 - r.x) << 4 | (c0 - r.x)) << sh);
+}
+
+// Calls f(ty, c0, c1) for the run of every tile row of r that has member tiles, top to bottom,
+// until f returns false, from the packed word pk (not kRunsUnpacked).
+template <typename F>
+__device__ __forceinline__ void for_each_packed_run(uint64_t pk, const int4 &r, F &&f) {
+    for (int ty = r.y; ty <= r.w; ++ty) {
+        const uint32_t b = (uint32_t)(pk >> (8 * (ty - r.y))) & 0xffu;
+        const int c0 = r.x + (int)(b & 15u), c1 = r.x + (int)(b >> 4);
+        if (c0 <= c1 && !f(ty, c0, c1)) return;
+    }
 }
 
 // Calls f(ty, c0, c1) for the run of every tile row of r that has member tiles, top to bottom,
 // until f returns false: unpacked from pk, or computed from splat id's ellipse when pk is
 // kRunsUnpacked.
 template <typename F>
-__device__ __forceinline__ void for_each_run(uint32_t pk, const float2 *__restrict__ mean2d,
+__device__ __forceinline__ void for_each_run(uint64_t pk, const float2 *__restrict__ mean2d,
                                              const float4 *__restrict__ conic_o, uint32_t id, const int4 &r,
                                              const SpanCtx &sc, F &&f) {
     if (pk != kRunsUnpacked) {
-        for (int ty = r.y; ty <= r.w; ++ty) {
-            const uint32_t b = (pk >> (8 * (ty - r.y))) & 0xffu;
-            const int c0 = r.x + (int)(b & 15u), c1 = r.x + (int)(b >> 4);
-            if (c0 <= c1 && !f(ty, c0, c1)) return;
-        }
+        for_each_packed_run(pk, r, f);
         return;
     }
     const float2 mu = __ldg(mean2d + id);
@@ -332,6 +340,33 @@ __device__ __forceinline__ void for_each_run(uint32_t pk, const float2 *__restri
         int c0, c1;
         if (span_row(p, sc, r, ty, c0, c1) && !f(ty, c0, c1)) return;
     }
+}
+
+// The runs of one splat computed by the whole warp (every lane passes the same splat): lane l
+// takes rows r.y + l, r.y + l + 32, ... and calls f(ty, c0, c1, before) for its row when the
+// row has member tiles, `before` being the member tiles of the splat's rows above it.  Returns
+// the splat's member-tile count to every lane.
+template <typename F>
+__device__ __forceinline__ uint32_t warp_runs(float u0, float u1, float A, float B, float C, const int4 &r,
+                                              const SpanCtx &sc, F &&f) {
+    const int lane = threadIdx.x & 31;
+    const SpanSplat p = span_prepare(u0, u1, A, B, C, sc.qmax);
+    uint32_t carry = 0;
+    for (int ty0 = r.y; ty0 <= r.w; ty0 += 32) {
+        const int ty = ty0 + lane;
+        int c0 = 0, c1 = -1;
+        const bool has = ty <= r.w && span_row(p, sc, r, ty, c0, c1);
+        const uint32_t w = has ? (uint32_t)(c1 - c0 + 1) : 0u;
+        uint32_t x = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (has) f(ty, c0, c1, carry + x - w);
+        carry += __shfl_sync(0xffffffffu, x, 31);
+    }
+    return carry;
 }
 
 // Member tiles of a splat in row-major order: the tile of its l-th instance (l below its count).

@@ -14,7 +14,7 @@ struct ProjectedOut {
     float *rgb;
     uint8_t *clamped;
     uint32_t *tiles_touched;
-    uint32_t *tile_runs;
+    uint64_t *tile_runs;
 };
 
 struct GradOut {
@@ -89,7 +89,7 @@ struct ProjectedIn {
     const uint32_t *tiles_touched;
     const float2 *mean2d;   // with conic_o: the ellipse whose row spans give the member tiles
     const float4 *conic_o;
-    const uint32_t *tile_runs;  // the row spans packed (kRunsUnpacked: recompute them)
+    const uint64_t *tile_runs;  // the row spans packed (kRunsUnpacked: recompute them)
 };
 
 struct BinOut {

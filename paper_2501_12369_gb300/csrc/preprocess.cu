@@ -263,7 +263,7 @@ k_preprocess(int n, const float *__restrict__ means, const float *__restrict__ s
     const float4 qr = __ldg(quats + i);
     Geom g;
     uint32_t cnt = 0;  // member tiles: the ellipse's run in every row of the rectangle
-    uint32_t runs = kRunsUnpacked;
+    uint64_t runs = kRunsUnpacked;
     if (project_fixed(m, s, qr, cam, psi, tile, g)) {
         const SpanCtx sc = make_span_ctx(qmax, tile, cam.W, cam.H);
         const int4 r = make_int4(g.rect[0], g.rect[1], g.rect[2], g.rect[3]);
@@ -668,10 +668,14 @@ cudaError_t launch_preprocess(int n, const darb_splats &sp, const Cam &cam, floa
     const int threads = 256, blocks = (n + threads - 1) / threads;
     const float4 *q = reinterpret_cast<const float4 *>(sp.quats);
     switch (sp.sh_degree) {
-    case 0: launch_k(k_preprocess<0>, blocks, threads, 0, st, n, sp.means, sp.scales, q, sp.opacities, sp.sh, cam, psi, tile, qmax, out); break;
-    case 1: launch_k(k_preprocess<1>, blocks, threads, 0, st, n, sp.means, sp.scales, q, sp.opacities, sp.sh, cam, psi, tile, qmax, out); break;
-    case 2: launch_k(k_preprocess<2>, blocks, threads, 0, st, n, sp.means, sp.scales, q, sp.opacities, sp.sh, cam, psi, tile, qmax, out); break;
-    default: launch_k(k_preprocess<3>, blocks, threads, 0, st, n, sp.means, sp.scales, q, sp.opacities, sp.sh, cam, psi, tile, qmax, out); break;
+    case 0: launch_k(k_preprocess<0>, blocks, threads, 0, st, n, sp.means, sp.scales, q, sp.opacities, sp.sh,
+                     cam, psi, tile, qmax, out); break;
+    case 1: launch_k(k_preprocess<1>, blocks, threads, 0, st, n, sp.means, sp.scales, q, sp.opacities, sp.sh,
+                     cam, psi, tile, qmax, out); break;
+    case 2: launch_k(k_preprocess<2>, blocks, threads, 0, st, n, sp.means, sp.scales, q, sp.opacities, sp.sh,
+                     cam, psi, tile, qmax, out); break;
+    default: launch_k(k_preprocess<3>, blocks, threads, 0, st, n, sp.means, sp.scales, q, sp.opacities, sp.sh,
+                      cam, psi, tile, qmax, out); break;
     }
     return cudaGetLastError();
 }

@@ -301,7 +301,7 @@ class Projected:
                          torch.empty(n, 4, dtype=torch.int32, **f), torch.empty(n, 2, dtype=torch.float32, **f),
                          torch.empty(n, 4, dtype=torch.float32, **f), torch.empty(n, 3, dtype=torch.float32, **f),
                          torch.empty(n, dtype=torch.uint8, **f), torch.empty(n, dtype=torch.int32, **f),
-                         torch.empty(n, dtype=torch.int32, **f))
+                         torch.empty(n, dtype=torch.int64, **f))
 
     def struct(self) -> darb_projected:
         return darb_projected(*(_p(getattr(self, f.name)) for f in dataclasses.fields(self)))

@@ -49,24 +49,29 @@ def check_preprocess(proj, ref):
 
 def check_tile_runs(proj, ref, ref_lists, tiles_x):
     """The packed row runs equal, row by row, the oracle's member tiles of every visible splat
-    whose rectangle spans at most 4 rows and 15 columns; 0xFFFFFFFF for the others."""
-    runs = to_np(proj.tile_runs).view(np.uint32)
+    whose rectangle spans at most 8 rows and 15 columns (the bytes past the last row 0x0F);
+    all ones for the others."""
+    runs = to_np(proj.tile_runs).view(np.uint64)
+    ones = np.uint64(0xFFFFFFFFFFFFFFFF)
     rect = ref["rect"]
     vis = ~ref["culled"].astype(bool)
-    assert (runs[~vis] == 0xFFFFFFFF).all(), "culled splats must carry 0xFFFFFFFF"
+    assert (runs[~vis] == ones).all(), "culled splats must carry all ones"
     tiles = (ref_lists["keys"] >> np.uint64(32)).astype(np.int64)
     ids = ref_lists["ids"].astype(np.int64)
     order = np.argsort(ids, kind="stable")
     ids_s, tiles_s = ids[order], tiles[order]
     starts = np.searchsorted(ids_s, np.arange(len(rect) + 1))
-    packed = 0
+    packed = unpacked = 0
     for i in np.flatnonzero(vis):
         x0, y0, x1, y1 = (int(v) for v in rect[i])
-        if y1 - y0 >= 4 or x1 - x0 >= 15:
-            assert runs[i] == 0xFFFFFFFF, f"splat {i}: large rectangle must not be packed"
+        if y1 - y0 >= 8 or x1 - x0 >= 15:
+            assert runs[i] == ones, f"splat {i}: large rectangle must not be packed"
+            unpacked += 1
             continue
         packed += 1
         member = tiles_s[starts[i]:starts[i + 1]]
+        for k in range(y1 - y0 + 1, 8):
+            assert (int(runs[i]) >> (8 * k)) & 0xFF == 0x0F, f"splat {i}: byte {k} past the last row"
         for k in range(y1 - y0 + 1):
             b = (int(runs[i]) >> (8 * k)) & 0xFF
             c0, c1 = x0 + (b & 15), x0 + (b >> 4)
@@ -76,7 +81,7 @@ def check_tile_runs(proj, ref, ref_lists, tiles_x):
             else:
                 assert (c0, c1) == (int(cols[0]), int(cols[-1])) and cols.size == c1 - c0 + 1, \
                     f"splat {i} row {y0 + k}: run ({c0}, {c1}) != {cols.tolist()}"
-    return packed
+    return packed, unpacked
 
 
 def tile_runs(keys_or_none, values, ranges):

@@ -1048,38 +1048,63 @@ k_depth_compact(int n, const int *__restrict__ radius, const float *__restrict__
                 uint32_t *__restrict__ keys, uint32_t *__restrict__ ids0, uint32_t *__restrict__ ids1, PassSpec ps,
                 uint32_t *__restrict__ hist) {
     pdl_entry();
+    static_assert(kScanItems == 8, "two 16-byte loads per thread");
     __shared__ uint32_t s_warp[kScanThreads / 32 + 1];
     __shared__ uint32_t s_h[kMaxPasses * 256];
-    for (int i = threadIdx.x; i < ps.passes * 256; i += kScanThreads) s_h[i] = 0;  // ordered by the scans
+    for (int i = threadIdx.x; i < ps.passes * 256; i += kScanThreads) s_h[i] = 0;  // ordered by the scan
     const int base = blockIdx.x * kScanTile;
+    const int i0 = base + (int)threadIdx.x * kScanItems;  // this thread's kScanItems consecutive splats
     const int lane = threadIdx.x & 31;
+    int rad[kScanItems];
+    uint32_t key[kScanItems];
+    if (i0 + kScanItems <= n) {  // radius and depth are 16-byte aligned, i0 a multiple of 8
+        const int4 r0 = *reinterpret_cast<const int4 *>(radius + i0), r1 = *reinterpret_cast<const int4 *>(radius + i0 + 4);
+        const uint4 d0 = *reinterpret_cast<const uint4 *>(depth + i0), d1 = *reinterpret_cast<const uint4 *>(depth + i0 + 4);
+        rad[0] = r0.x; rad[1] = r0.y; rad[2] = r0.z; rad[3] = r0.w;
+        rad[4] = r1.x; rad[5] = r1.y; rad[6] = r1.z; rad[7] = r1.w;
+        key[0] = d0.x; key[1] = d0.y; key[2] = d0.z; key[3] = d0.w;
+        key[4] = d1.x; key[5] = d1.y; key[6] = d1.z; key[7] = d1.w;
+    } else {
+#pragma unroll
+        for (int j = 0; j < kScanItems; ++j) {
+            const bool valid = i0 + j < n;
+            rad[j] = valid ? radius[i0 + j] : 0;
+            key[j] = valid ? __float_as_uint(depth[i0 + j]) : 0u;
+        }
+    }
+    uint32_t nv = 0, nc = 0;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        const bool valid = i0 + j < n;
+        nv += (valid && rad[j] != 0) ? 1u : 0u;
+        nc += (valid && rad[j] == 0) ? 1u : 0u;
+    }
+    // visible count in the low half-word, culled count in the high one (at most kScanTile each)
+    uint32_t t;
+    const uint32_t ex = block_exclusive_scan<kScanThreads>(nv | (nc << 16), s_warp, t);
     const uint32_t vis0 = (uint32_t)block_offsets[blockIdx.x];
-    const uint32_t cul0 = *n_vis + ((uint32_t)base - vis0);  // culled splats before this block
-    uint32_t vis = 0, cul = 0;
-    for (int j = 0; j < kScanItems; ++j) {  // kScanThreads consecutive splats per round
-        const int i = base + j * kScanThreads + threadIdx.x;
-        const bool valid = i < n;
-        const bool v = valid && radius[i] != 0;
-        // visible count in the low half-word, culled count in the high one (at most 256 each)
-        uint32_t t;
-        const uint32_t r = block_exclusive_scan<kScanThreads>(v ? 1u : (valid ? 0x10000u : 0u), s_warp, t);
-        const uint32_t k = v ? __float_as_uint(depth[i]) : 0u;
+    uint32_t pv = vis0 + (ex & 0xffffu);
+    uint32_t pc = *n_vis + ((uint32_t)base - vis0) + (ex >> 16);  // culled splats go after all visible ones
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        const int i = i0 + j;
+        const bool valid = i < n, v = valid && rad[j] != 0;
         if (v) {
-            keys[vis0 + vis + (r & 0xffffu)] = k;
-            ids0[vis0 + vis + (r & 0xffffu)] = (uint32_t)i;
+            keys[pv] = key[j];
+            ids0[pv] = (uint32_t)i;
+            ++pv;
         } else if (valid) {
-            ids0[cul0 + cul + (r >> 16)] = (uint32_t)i;
-            ids1[cul0 + cul + (r >> 16)] = (uint32_t)i;
+            ids0[pc] = (uint32_t)i;
+            ids1[pc] = (uint32_t)i;
+            ++pc;
         }
 #pragma unroll
         for (int p = 0; p < kMaxPasses; ++p) {  // digit histograms of the visible keys
             if (p >= ps.passes) break;
-            const uint32_t d = v ? (k >> ps.shift[p]) & ((1u << ps.bits[p]) - 1u) : 0xffffffffu;
+            const uint32_t d = v ? (key[j] >> ps.shift[p]) & ((1u << ps.bits[p]) - 1u) : 0xffffffffu;
             const uint32_t peers = __match_any_sync(0xffffffffu, d);
             if (v && lane == __ffs(peers) - 1) atomicAdd(&s_h[p * 256 + d], (uint32_t)__popc(peers));
         }
-        vis += t & 0xffffu;
-        cul += t >> 16;
     }
     __syncthreads();
     for (int i = threadIdx.x; i < ps.passes * 256; i += kScanThreads)

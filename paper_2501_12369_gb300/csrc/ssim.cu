@@ -2,7 +2,9 @@
 // the 3DGS work it builds on -- per channel, an 11 x 11 Gaussian window (sigma 1.5, normalised)
 // over zero-padded images, C1 = 0.01^2, C2 = 0.03^2 -- averaged over channels and pixels.
 //
-// Two tiled kernels, each CTA one 32 x 32 output tile of one channel with a 5-pixel halo:
+// Two tiled kernels, each CTA one 32 x 32 output tile of one channel with a 5-pixel halo; every
+// separable blur pass gives each thread 4 consecutive outputs, so an input value is read from
+// shared memory once for all the outputs it reaches:
 //   k_ssim_fwd  stages x and y, blurs the five moments (x, y, x^2, y^2, xy) with separable
 //               passes in shared memory, and writes per pixel the partial derivatives of SSIM
 //               w.r.t. the local moments m_x, s_xx, s_xy, plus the block sums of SSIM and |x - y|;
@@ -22,21 +24,24 @@ constexpr int kSsimR = 5;
 constexpr int kSsimTs = 32;
 constexpr int kSsimIn = kSsimTs + 2 * kSsimR;  // 42
 constexpr int kSsimThreads = 256;
+constexpr int kSsimRb = 4;  // outputs per thread along the blur direction (register blocking)
+constexpr int kSsimTaps = 2 * kSsimR + 1;
 constexpr float kSsimC1 = 0.01f * 0.01f;
 constexpr float kSsimC2 = 0.03f * 0.03f;
+static_assert(kSsimTs % kSsimRb == 0 && (kSsimTs / kSsimRb) * kSsimTs == kSsimThreads, "one vertical group per thread");
 
 struct Window {
-    float g[2 * kSsimR + 1];
+    float g[kSsimTaps];
 };
 
 Window make_window() {
     Window w;
-    double sum = 0.0, v[2 * kSsimR + 1];
+    double sum = 0.0, v[kSsimTaps];
     for (int k = -kSsimR; k <= kSsimR; ++k) {
         v[k + kSsimR] = std::exp(-(double)(k * k) / (2.0 * 1.5 * 1.5));
         sum += v[k + kSsimR];
     }
-    for (int k = 0; k <= 2 * kSsimR; ++k) w.g[k] = (float)(v[k] / sum);
+    for (int k = 0; k < kSsimTaps; ++k) w.g[k] = (float)(v[k] / sum);
     return w;
 }
 
@@ -51,6 +56,30 @@ __device__ __forceinline__ float block_sum(float v, float *s_w) {
     return t;  // valid on thread 0
 }
 
+// Blurs along a row: out[i] = sum_k g[k] in[c0 + i + k] for kSsimRb consecutive outputs, each
+// sum taken in tap order (the same order as one output at a time).
+template <int NQ, class In>
+__device__ __forceinline__ void hblur(const Window &win, In in, float (&out)[NQ][kSsimRb]) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+#pragma unroll
+        for (int i = 0; i < kSsimRb; ++i) out[q][i] = 0.0f;
+#pragma unroll
+    for (int t = 0; t < kSsimRb + kSsimTaps - 1; ++t) {  // each input once, into every output it reaches
+        float val[NQ];
+        in(t, val);
+#pragma unroll
+        for (int i = 0; i < kSsimRb; ++i) {
+            const int k = t - i;
+            if (k >= 0 && k < kSsimTaps)
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) out[q][i] = fmaf(win.g[k], val[q], out[q][i]);
+        }
+    }
+}
+
+// Forward: the five local moments by separable blurs (x along rows, then y along columns, each
+// thread kSsimRb consecutive outputs), then the derivative maps and the block sums.
 __global__ void __launch_bounds__(kSsimThreads)
 k_ssim_fwd(const float *__restrict__ x, const float *__restrict__ y, int W, int H, Window win,
            float *__restrict__ d_m, float *__restrict__ d_sxx, float *__restrict__ d_sxy, double *__restrict__ sums) {
@@ -68,49 +97,49 @@ k_ssim_fwd(const float *__restrict__ x, const float *__restrict__ y, int W, int 
         sy[r][c] = in ? y[off + (size_t)gy * W + gx] : 0.0f;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < kSsimIn * kSsimTs; i += kSsimThreads) {  // along x
-        const int r = i / kSsimTs, c = i - r * kSsimTs;
-        float a = 0.f, b = 0.f, aa = 0.f, bb = 0.f, ab = 0.f;
+    // along x: item = (row, group of kSsimRb columns)
+    constexpr int kGroups = kSsimTs / kSsimRb;
+    for (int item = threadIdx.x; item < kSsimIn * kGroups; item += kSsimThreads) {
+        const int r = item / kGroups, c0 = (item - r * kGroups) * kSsimRb;
+        float o[5][kSsimRb];
+        hblur<5>(win, [&](int t, float (&val)[5]) {
+            const float u = sx[r][c0 + t], v = sy[r][c0 + t];
+            val[0] = u;
+            val[1] = v;
+            val[2] = u * u;
+            val[3] = v * v;
+            val[4] = u * v;
+        }, o);
 #pragma unroll
-        for (int k = 0; k <= 2 * kSsimR; ++k) {
-            const float g = win.g[k], u = sx[r][c + k], v = sy[r][c + k];
-            a = fmaf(g, u, a);
-            b = fmaf(g, v, b);
-            aa = fmaf(g, u * u, aa);
-            bb = fmaf(g, v * v, bb);
-            ab = fmaf(g, u * v, ab);
-        }
-        h[0][r][c] = a;
-        h[1][r][c] = b;
-        h[2][r][c] = aa;
-        h[3][r][c] = bb;
-        h[4][r][c] = ab;
+        for (int q = 0; q < 5; ++q)
+#pragma unroll
+            for (int i = 0; i < kSsimRb; ++i) h[q][r][c0 + i] = o[q][i];
     }
     __syncthreads();
+    // along y: thread = (column, group of kSsimRb rows)
+    const int c = threadIdx.x % kSsimTs, r0 = (threadIdx.x / kSsimTs) * kSsimRb;
+    float m[5][kSsimRb];
+    hblur<5>(win, [&](int t, float (&val)[5]) {
+#pragma unroll
+        for (int q = 0; q < 5; ++q) val[q] = h[q][r0 + t][c];
+    }, m);
     float ssim_sum = 0.0f, l1_sum = 0.0f;
-    for (int i = threadIdx.x; i < kSsimTs * kSsimTs; i += kSsimThreads) {  // along y
-        const int r = i / kSsimTs, c = i - r * kSsimTs;
-        const int gy = y0 + r, gx = x0 + c;
+#pragma unroll
+    for (int i = 0; i < kSsimRb; ++i) {
+        const int r = r0 + i, gy = y0 + r, gx = x0 + c;
         if (gx >= W || gy >= H) continue;
-        float m[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-        for (int k = 0; k <= 2 * kSsimR; ++k) {
-            const float g = win.g[k];
-#pragma unroll
-            for (int q = 0; q < 5; ++q) m[q] = fmaf(g, h[q][r + k][c], m[q]);
-        }
-        const float mx = m[0], my = m[1];
+        const float mx = m[0][i], my = m[1][i];
         const float A1 = 2.0f * mx * my + kSsimC1;
-        const float A2 = 2.0f * (m[4] - mx * my) + kSsimC2;
+        const float A2 = 2.0f * (m[4][i] - mx * my) + kSsimC2;
         const float B1 = mx * mx + my * my + kSsimC1;
-        const float B2 = (m[2] - mx * mx) + (m[3] - my * my) + kSsimC2;
+        const float B2 = (m[2][i] - mx * mx) + (m[3][i] - my * my) + kSsimC2;
         const float iB = 1.0f / (B1 * B2);
-        const float s = A1 * A2 * iB;
+        const float sv = A1 * A2 * iB;
         const size_t p = off + (size_t)gy * W + gx;
-        d_m[p] = 2.0f * my * (A2 - A1) * iB - 2.0f * mx * s * (1.0f / B1 - 1.0f / B2);
-        d_sxx[p] = -s / B2;
+        d_m[p] = 2.0f * my * (A2 - A1) * iB - 2.0f * mx * sv * (1.0f / B1 - 1.0f / B2);
+        d_sxx[p] = -sv / B2;
         d_sxy[p] = 2.0f * A1 * iB;
-        ssim_sum += s;
+        ssim_sum += sv;
         l1_sum += fabsf(sx[r + kSsimR][c + kSsimR] - sy[r + kSsimR][c + kSsimR]);
     }
     const float ts = block_sum(ssim_sum, s_w);
@@ -122,6 +151,8 @@ k_ssim_fwd(const float *__restrict__ x, const float *__restrict__ y, int W, int 
     }
 }
 
+// Backward: blurs the three derivative maps (the window is symmetric, so the blur is its own
+// adjoint) with the same blocking, then forms dL/dx.
 __global__ void __launch_bounds__(kSsimThreads)
 k_ssim_bwd(const float *__restrict__ x, const float *__restrict__ y, int W, int H, Window win,
            const float *__restrict__ d_m, const float *__restrict__ d_sxx, const float *__restrict__ d_sxy,
@@ -148,37 +179,34 @@ k_ssim_bwd(const float *__restrict__ x, const float *__restrict__ y, int W, int 
         sa[2][r][c] = in ? d_sxy[p] : 0.0f;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < kSsimIn * kSsimTs; i += kSsimThreads) {
-        const int r = i / kSsimTs, c = i - r * kSsimTs;
-        float a = 0.f, b = 0.f, e = 0.f;
+    constexpr int kGroups = kSsimTs / kSsimRb;
+    for (int item = threadIdx.x; item < kSsimIn * kGroups; item += kSsimThreads) {
+        const int r = item / kGroups, c0 = (item - r * kGroups) * kSsimRb;
+        float o[3][kSsimRb];
+        hblur<3>(win, [&](int t, float (&val)[3]) {
 #pragma unroll
-        for (int k = 0; k <= 2 * kSsimR; ++k) {
-            const float g = win.g[k];
-            a = fmaf(g, sa[0][r][c + k], a);
-            b = fmaf(g, sa[1][r][c + k], b);
-            e = fmaf(g, sa[2][r][c + k], e);
-        }
-        h[0][r][c] = a;
-        h[1][r][c] = b;
-        h[2][r][c] = e;
+            for (int q = 0; q < 3; ++q) val[q] = sa[q][r][c0 + t];
+        }, o);
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+#pragma unroll
+            for (int i = 0; i < kSsimRb; ++i) h[q][r][c0 + i] = o[q][i];
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < kSsimTs * kSsimTs; i += kSsimThreads) {
-        const int r = i / kSsimTs, c = i - r * kSsimTs;
-        const int gy = y0 + r, gx = x0 + c;
-        if (gx >= W || gy >= H) continue;
-        float a = 0.f, b = 0.f, e = 0.f;
+    const int c = threadIdx.x % kSsimTs, r0 = (threadIdx.x / kSsimTs) * kSsimRb;
+    float b[3][kSsimRb];
+    hblur<3>(win, [&](int t, float (&val)[3]) {
 #pragma unroll
-        for (int k = 0; k <= 2 * kSsimR; ++k) {
-            const float g = win.g[k];
-            a = fmaf(g, h[0][r + k][c], a);
-            b = fmaf(g, h[1][r + k][c], b);
-            e = fmaf(g, h[2][r + k][c], e);
-        }
+        for (int q = 0; q < 3; ++q) val[q] = h[q][r0 + t][c];
+    }, b);
+#pragma unroll
+    for (int i = 0; i < kSsimRb; ++i) {
+        const int gy = y0 + r0 + i, gx = x0 + c;
+        if (gx >= W || gy >= H) continue;
         const size_t p = off + (size_t)gy * W + gx;
         const float xv = x[p], yv = y[p], d = xv - yv;
         const float sgn = d > 0.0f ? 1.0f : (d < 0.0f ? -1.0f : 0.0f);
-        const float dssim = (a + 2.0f * xv * b + yv * e) * inv_n;
+        const float dssim = (b[0][i] + 2.0f * xv * b[1][i] + yv * b[2][i]) * inv_n;
         dL[p] = (1.0f - lam) * sgn * inv_n - lam * dssim;
     }
 }

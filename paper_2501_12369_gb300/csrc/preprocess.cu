@@ -250,35 +250,83 @@ __device__ __forceinline__ bool project_fixed(const float m[3], const float s[3]
     return true;
 }
 
+// One CTA takes kPreThreads consecutive splats in two phases.  Phase 1: every thread projects
+// its splat (the decision track) and either writes the culled record or queues the splat, with
+// its projected geometry, in shared memory.  Phase 2: the threads take the queued (visible)
+// splats densely and do the heavy part -- member tiles by row runs, SH colour, the records --
+// so that whole warps, not 38% of each warp's lanes, run it.
+constexpr int kPreThreads = 256;
+
+struct PreGeom {
+    float tz, A, B, C, u0, u1;
+    int rect[4];
+    int radius, idx;
+};
+
 template <int DEG>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kPreThreads)
 k_preprocess(int n, const float *__restrict__ means, const float *__restrict__ scales,
              const float4 *__restrict__ quats, const float *__restrict__ opac,
              const float *__restrict__ sh, Cam cam, float psi, int tile, float qmax, ProjectedOut out) {
     pdl_entry();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const float m[3] = {__ldg(means + 3 * (size_t)i), __ldg(means + 3 * (size_t)i + 1), __ldg(means + 3 * (size_t)i + 2)};
-    const float s[3] = {__ldg(scales + 3 * (size_t)i), __ldg(scales + 3 * (size_t)i + 1), __ldg(scales + 3 * (size_t)i + 2)};
-    const float4 qr = __ldg(quats + i);
-    Geom g;
-    uint32_t cnt = 0;  // member tiles: the ellipse's run in every row of the rectangle
-    uint64_t runs = kRunsUnpacked;
-    if (project_fixed(m, s, qr, cam, psi, tile, g)) {
-        const SpanCtx sc = make_span_ctx(qmax, tile, cam.W, cam.H);
-        const int4 r = make_int4(g.rect[0], g.rect[1], g.rect[2], g.rect[3]);
-        const bool pack = runs_packable(r);
-        if (pack) runs = kRunsNone;
-        const SpanSplat sp = span_prepare(g.u0, g.u1, g.A, g.B, g.C, qmax);
-        for (int ty = r.y; ty <= r.w; ++ty) {
-            int c0, c1;
-            if (span_row(sp, sc, r, ty, c0, c1)) {
-                cnt += (uint32_t)(c1 - c0 + 1);
-                if (pack) runs = runs_put(runs, r, ty, c0, c1);
-            }
+    __shared__ PreGeom s_q[kPreThreads];
+    __shared__ int s_n;
+    if (threadIdx.x == 0) s_n = 0;
+    __syncthreads();
+    {
+        const int i = blockIdx.x * kPreThreads + threadIdx.x;
+        bool vis = false;
+        Geom g;
+        if (i < n) {
+            const float m[3] = {__ldg(means + 3 * (size_t)i), __ldg(means + 3 * (size_t)i + 1),
+                                __ldg(means + 3 * (size_t)i + 2)};
+            const float s[3] = {__ldg(scales + 3 * (size_t)i), __ldg(scales + 3 * (size_t)i + 1),
+                                __ldg(scales + 3 * (size_t)i + 2)};
+            vis = project_fixed(m, s, __ldg(quats + i), cam, psi, tile, g);
+        }
+        const uint32_t vm = __ballot_sync(0xffffffffu, vis);
+        int base = 0;
+        if ((threadIdx.x & 31) == 0 && vm) base = atomicAdd(&s_n, __popc(vm));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (vis) {
+            PreGeom &q = s_q[base + __popc(vm & ((1u << (threadIdx.x & 31)) - 1u))];
+            q.tz = g.t[2];
+            q.A = g.A;
+            q.B = g.B;
+            q.C = g.C;
+            q.u0 = g.u0;
+            q.u1 = g.u1;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) q.rect[k] = g.rect[k];
+            q.radius = g.radius;
+            q.idx = i;
+        } else if (i < n) {
+            out.radius[i] = 0;
+            out.tiles_touched[i] = 0;
+            out.tile_runs[i] = kRunsUnpacked;
+            out.tile_rect[i] = make_int4(0, 0, 0, 0);
+            out.depth[i] = 0.0f;
         }
     }
-    if (cnt == 0) {  // culled, or an ellipse that reaches no tile
+    __syncthreads();
+    const int nq = s_n;
+    if ((int)threadIdx.x >= nq) return;
+    const PreGeom g = s_q[threadIdx.x];
+    const int i = g.idx;
+    const SpanCtx sc = make_span_ctx(qmax, tile, cam.W, cam.H);
+    const int4 r = make_int4(g.rect[0], g.rect[1], g.rect[2], g.rect[3]);
+    uint32_t cnt = 0;  // member tiles: the ellipse's run in every row of the rectangle
+    const bool pack = runs_packable(r);
+    uint64_t runs = pack ? kRunsNone : kRunsUnpacked;
+    const SpanSplat sp = span_prepare(g.u0, g.u1, g.A, g.B, g.C, qmax);
+    for (int ty = r.y; ty <= r.w; ++ty) {
+        int c0, c1;
+        if (span_row(sp, sc, r, ty, c0, c1)) {
+            cnt += (uint32_t)(c1 - c0 + 1);
+            if (pack) runs = runs_put(runs, r, ty, c0, c1);
+        }
+    }
+    if (cnt == 0) {  // an ellipse that reaches no tile: culled
         out.radius[i] = 0;
         out.tiles_touched[i] = 0;
         out.tile_runs[i] = kRunsUnpacked;
@@ -286,9 +334,9 @@ k_preprocess(int n, const float *__restrict__ means, const float *__restrict__ s
         out.depth[i] = 0.0f;
         return;
     }
-    out.depth[i] = g.t[2];
+    out.depth[i] = g.tz;
     out.radius[i] = g.radius;
-    out.tile_rect[i] = make_int4(g.rect[0], g.rect[1], g.rect[2], g.rect[3]);
+    out.tile_rect[i] = r;
     out.tiles_touched[i] = cnt;
     out.tile_runs[i] = runs;
     out.mean2d[i] = make_float2(g.u0, g.u1);
@@ -298,7 +346,8 @@ k_preprocess(int n, const float *__restrict__ means, const float *__restrict__ s
     constexpr int K = (DEG + 1) * (DEG + 1);
     float coef[K][3];
     load_sh<DEG>(sh, i, coef);
-    float d0 = m[0] - cam.campos[0], d1 = m[1] - cam.campos[1], d2 = m[2] - cam.campos[2];
+    float d0 = __ldg(means + 3 * (size_t)i) - cam.campos[0], d1 = __ldg(means + 3 * (size_t)i + 1) - cam.campos[1],
+          d2 = __ldg(means + 3 * (size_t)i + 2) - cam.campos[2];
     const float il = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
     d0 *= il; d1 *= il; d2 *= il;
     float Y[K];
@@ -665,7 +714,7 @@ k_preprocess_bwd_adam(int n, darb_train_params P, darb_adam_state A, AdamConsts 
 cudaError_t launch_preprocess(int n, const darb_splats &sp, const Cam &cam, float psi, int tile, float qmax,
                               const ProjectedOut &out, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
-    const int threads = 256, blocks = (n + threads - 1) / threads;
+    const int threads = kPreThreads, blocks = (n + threads - 1) / threads;
     const float4 *q = reinterpret_cast<const float4 *>(sp.quats);
     switch (sp.sh_degree) {
     case 0: launch_k(k_preprocess<0>, blocks, threads, 0, st, n, sp.means, sp.scales, q, sp.opacities, sp.sh,

@@ -706,12 +706,15 @@ k_downsweep(const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__re
         }
     }
     const uint32_t lt = lanemask_lt();
+    // per-warp counts; each item's stable rank among the warp's items of its digit
 #pragma unroll
     for (int it = 0; it < kSortItems; ++it) {
         const uint32_t d = (uint32_t)(k[it] >> shift) & mask;
         const uint32_t peers = PEERS_BY_MATCH ? __match_any_sync(0xffffffffu, d) : match_digit(d, bits);
-        if (lane == __ffs(peers) - 1) atomicAdd(&s_wh[warp][d], (uint32_t)__popc(peers));
-        rk[it] = peers;
+        const int leader = __ffs(peers) - 1;
+        uint32_t old = 0;
+        if (lane == leader) old = atomicAdd(&s_wh[warp][d], (uint32_t)__popc(peers));
+        rk[it] = __shfl_sync(0xffffffffu, old, leader) + __popc(peers & lt);
     }
     __syncthreads();
     const uint32_t dg = (uint32_t)tid;
@@ -737,12 +740,7 @@ k_downsweep(const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__re
 #pragma unroll
     for (int it = 0; it < kSortItems; ++it) {
         const uint32_t d = (uint32_t)(k[it] >> shift) & mask;
-        const uint32_t peers = rk[it];
-        const uint32_t prev = s_wh[warp][d];
-        const uint32_t pos = prev + __popc(peers & lt);
-        __syncwarp();
-        if (lane == 31 - __clz(peers)) s_wh[warp][d] = prev + __popc(peers);
-        __syncwarp();
+        const uint32_t pos = s_wh[warp][d] + rk[it];
         if (WRITE_KEYS) s_k[pos] = k[it];
         else s_d[pos] = (uint8_t)d;
         s_v[pos] = v[it];
@@ -818,14 +816,17 @@ __device__ __forceinline__ void sweep_partition(SweepSmem &sm, unsigned char *sm
     const uint32_t radix = 1u << bits, mask = radix - 1u;
     uint32_t rk[kSortItems];
     const uint32_t lt = lanemask_lt();
-    // 1) Unordered per-warp digit counts (one shared-memory atomic per group of equal digits);
-    //    rk keeps each item's peer mask for the ordered ranking below.
+    // 1) Per-warp digit counts (one shared-memory atomic per group of equal digits).  The
+    //    atomic's old value, broadcast to the group, plus the lower lanes of the group give each
+    //    item's stable rank among the warp's items of its digit (item-major, lane-minor order).
 #pragma unroll
     for (int it = 0; it < kSortItems; ++it) {
         const uint32_t d = (uint32_t)(k[it] >> shift) & mask;
         const uint32_t peers = PEERS_BY_MATCH ? __match_any_sync(0xffffffffu, d) : match_digit(d, bits);
-        if (lane == __ffs(peers) - 1) atomicAdd(&sm.wh[warp][d], (uint32_t)__popc(peers));
-        rk[it] = peers;
+        const int leader = __ffs(peers) - 1;
+        uint32_t old = 0;
+        if (lane == leader) old = atomicAdd(&sm.wh[warp][d], (uint32_t)__popc(peers));
+        rk[it] = __shfl_sync(0xffffffffu, old, leader) + __popc(peers & lt);
     }
     __syncthreads();
 
@@ -848,17 +849,12 @@ __device__ __forceinline__ void sweep_partition(SweepSmem &sm, unsigned char *sm
     if (dg < radix) sm.cta_excl[dg] = cex;
     __syncthreads();
 
-    // 3) ordered ranking inside each warp (stable: item-major, lane-minor order = input order),
-    //    then staging at the CTA-local sorted position
+    // 3) staging at the CTA-local sorted position: the digit's CTA offset, the warp's offset
+    //    within the digit, the item's rank within the warp (stable: input order)
 #pragma unroll
     for (int it = 0; it < kSortItems; ++it) {
         const uint32_t d = (uint32_t)(k[it] >> shift) & mask;
-        const uint32_t peers = rk[it];
-        const uint32_t prev = sm.wh[warp][d];
-        const uint32_t pos = sm.cta_excl[d] + prev + __popc(peers & lt);
-        __syncwarp();
-        if (lane == 31 - __clz(peers)) sm.wh[warp][d] = prev + __popc(peers);
-        __syncwarp();
+        const uint32_t pos = sm.cta_excl[d] + sm.wh[warp][d] + rk[it];
         if (WRITE_KEYS) s_k[pos] = k[it];
         else s_d[pos] = (uint8_t)d;
         s_v[pos] = v[it];

@@ -66,6 +66,31 @@ def test_bin_sort_is_bit_exact(tile, strategy):
     assert packed > 0 and (tile > 8 or unpacked > 0)  # both the packed and the warp-wide rows
 
 
+@pytest.mark.parametrize("tile", [8, 16, 32])
+def test_large_elongated_and_border_splats(tile):
+    """Rectangles taller than a warp's worth of tile rows (their runs recomputed warp-wide by the
+    tile counts and per thread by the duplication), rectangles too large to pack, and elongated
+    splats around the image border, whose rectangle may reach into the image while their
+    ellipse reaches no tile (culled on both sides)."""
+    cam = synth.pinhole((0.0, 0.0, 3.0), 320, 296, 300.0, bg=(0.1, 0.2, 0.3))
+    big = synth.uniform_cube_scene(24, seed=11, log_scale=(-1.2, -0.6))
+    thin = synth.uniform_cube_scene(600, seed=12, half=1.6, log_scale=(-5.0, -1.5))
+    s = synth.Splats(*(np.concatenate([getattr(big, f), getattr(thin, f)])
+                       for f in ("means", "scales", "quats", "opacities", "sh")), big.sh_degree)
+    r, sd, proj, bins, img = gpu_forward(s, cam, "half_cosine", tile)
+    ref = oracle.project(s, cam, oracle.kernel_params("half_cosine"), tile, True)
+    check_preprocess(proj, ref)
+    lists = oracle.build_lists(ref, cam, tile)
+    check_lists(bins, lists)
+    packed, unpacked = check_tile_runs(proj, ref, lists, (cam.width + tile - 1) // tile)
+    assert packed > 0 and unpacked > 0
+    vis = ref["culled"] == 0
+    rows = ref["rect"][vis, 3] - ref["rect"][vis, 1] + 1
+    if tile == 8:
+        assert rows.max() > 32  # a rectangle taller than one warp of tile rows
+    check_render(img, bins, oracle.forward(s, cam, "half_cosine", tile=tile), cam, tile)
+
+
 def test_bin_sort_strategies_agree_on_a_large_scene():
     s = synth.cluster_scene(300_000, seed=11)
     cam = synth.fibonacci_cameras(10, 6.0, 1280, 720, 1000.0)[4]

@@ -23,6 +23,10 @@ LIB_PATH = os.path.join(OUT_DIR, "libdarb.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-warn-spills",
                      "--expt-relaxed-constexpr", "-I", CSRC, "-I", INCLUDE]
+# Tuning macros (for example -DDARB_SORT_THREADS=256 -DDARB_SORT_CTAS_PER_SM=4), from the
+# environment; a change of them rebuilds every object.
+DEFINES = os.environ.get("DARB_NVCC_DEFINES", "").split()
+STAMP = os.path.join(OUT_DIR, "defines.txt")
 
 
 def nvcc() -> str:
@@ -45,14 +49,14 @@ def _stale(target, deps):
     if not os.path.exists(target):
         return True
     t = os.path.getmtime(target)
-    return any(os.path.getmtime(d) > t for d in deps)
+    return any(os.path.getmtime(d) > t for d in deps + [STAMP])
 
 
 def _compile(src, verbose):
     obj = os.path.join(OUT_DIR, os.path.basename(src) + ".o")
     if not _stale(obj, [src] + _headers()):
         return obj
-    cmd = [nvcc()] + NVCC_FLAGS + (["-Xptxas", "-v"] if verbose else []) + ["-c", src, "-o", obj + ".tmp"]
+    cmd = [nvcc()] + NVCC_FLAGS + DEFINES + (["-Xptxas", "-v"] if verbose else []) + ["-c", src, "-o", obj + ".tmp"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed on {os.path.basename(src)}:\n{r.stderr}")
@@ -64,6 +68,10 @@ def _compile(src, verbose):
 
 def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(OUT_DIR, exist_ok=True)
+    old = open(STAMP).read() if os.path.exists(STAMP) else None
+    if old != " ".join(DEFINES):
+        with open(STAMP, "w") as f:
+            f.write(" ".join(DEFINES))
     srcs = sources()
     if force:
         for o in glob.glob(os.path.join(OUT_DIR, "*.o")):

@@ -77,8 +77,12 @@ cudaError_t launch_reset_opacity(const darb_train_params &p, float max_opacity, 
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
 constexpr int kScanTile = kScanThreads * kScanItems;  // splats per scan/duplicate CTA
-constexpr int kSortThreads = 512;
-constexpr int kSortItems = 8;
+// Shape of the one-pass sort CTAs: threads x items per thread keys per partition (4096).
+#ifndef DARB_SORT_THREADS
+#define DARB_SORT_THREADS 512
+#endif
+constexpr int kSortThreads = DARB_SORT_THREADS;
+constexpr int kSortItems = 4096 / kSortThreads;
 constexpr int kSortTile = kSortThreads * kSortItems;  // keys per onesweep partition
 constexpr int kMaxPasses = 8;
 

@@ -24,11 +24,26 @@ struct Bg {
 
 constexpr int kMaxDevicesRender = 64;
 
+#ifndef DARB_FWD_PIX32
+#define DARB_FWD_PIX32 4
+#endif
 template <int TILE>
 struct RenderShape {
-    static constexpr int PIX = TILE >= 16 ? 2 : 1;   // pixels per thread
+    static constexpr int PIX = TILE == 32 ? DARB_FWD_PIX32 : (TILE >= 16 ? 2 : 1);  // pixels per thread
     static constexpr int NT = TILE * TILE / PIX;      // threads per CTA = records per batch
     static constexpr int ROWS = TILE / PIX;           // row stride between a thread's pixels
+};
+
+// The backward's shape: with 32-pixel tiles each thread may take more pixels, so that every
+// record read from shared memory and every per-warp reduction serves more pixels.
+#ifndef DARB_BWD_PIX32
+#define DARB_BWD_PIX32 4
+#endif
+template <int TILE>
+struct BwdShape {
+    static constexpr int PIX = TILE == 32 ? DARB_BWD_PIX32 : RenderShape<TILE>::PIX;
+    static constexpr int NT = TILE * TILE / PIX;
+    static constexpr int ROWS = TILE / PIX;
 };
 
 template <int TILE>
@@ -159,7 +174,8 @@ k_render_fwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ valu
 // (items numbered view-major; views[v].tile_begin is the first item of view v) until all are
 // done, so small and large views share the GPU without per-view launches or tails.
 template <int KIND, int TILE>
-__global__ void __launch_bounds__(RenderShape<TILE>::NT, 1536 / RenderShape<TILE>::NT)
+__global__ void __launch_bounds__(RenderShape<TILE>::NT,
+                                  (RenderShape<TILE>::PIX >= 4 ? 1024 : 1536) / RenderShape<TILE>::NT)
 k_render_fwd_batch(const BatchView *__restrict__ views, int n_views, int total_tiles, uint32_t *__restrict__ queue,
                    float qmax, int strict, KernelSpec ks) {
     pdl_entry();
@@ -231,14 +247,14 @@ __device__ __forceinline__ float warp_sum8(const float (&v)[9], int lane, float 
 // over the warp by shuffles, then across warps in shared memory, then added to grad2d with one
 // vector atomic per 4 floats.
 template <int KIND, int TILE>
-__global__ void __launch_bounds__(RenderShape<TILE>::NT)
+__global__ void __launch_bounds__(BwdShape<TILE>::NT)
 k_render_bwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ values,
              const float2 *__restrict__ mean2d, const float4 *__restrict__ conic_o,
              const float *__restrict__ rgb, int W, int H, int tiles_x, float qmax, int strict, KernelSpec ks, Bg bg,
              const float *__restrict__ t_final, const uint32_t *__restrict__ last,
              const float *__restrict__ dL_dimage, float4 *__restrict__ grad2d) {
     pdl_entry();
-    using S = RenderShape<TILE>;
+    using S = BwdShape<TILE>;
     constexpr int NT = S::NT, PIX = S::PIX;
     constexpr int NW = NT / 32;
     __shared__ float2 s_xy[NT];
@@ -400,7 +416,7 @@ cudaError_t bwd_t(int n_tiles, const uint2 *ranges, const uint32_t *values, cons
                   const float4 *conic_o, const float *rgb, const Cam &cam, int tiles_x, float qmax, int strict,
                   const KernelSpec &ks, const float *t_final, const uint32_t *last, const float *dL, float *grad2d,
                   cudaStream_t st) {
-    launch_k(k_render_bwd<KIND, TILE>, n_tiles, RenderShape<TILE>::NT, 0, st,
+    launch_k(k_render_bwd<KIND, TILE>, n_tiles, BwdShape<TILE>::NT, 0, st,
              ranges, values, mean2d, conic_o, rgb, cam.W, cam.H, tiles_x, qmax, strict, ks,
              Bg{cam.bg[0], cam.bg[1], cam.bg[2]}, t_final, last, dL, reinterpret_cast<float4 *>(grad2d));
     return cudaGetLastError();

@@ -718,7 +718,7 @@ def run_multiview(device, kernel="half_cosine", reps=10):
     splats, cams = synth.scene_1m_multiview()
     sd = darb.splats_to_device(splats, device)
     pixels = sum(c.width * c.height for c in cams)
-    (tile, depth), table = darb.autotune_batch(sd, cams, kernel, (8, 16, 32), (1, 2, 4), reps=3)
+    (tile, depth), table = darb.autotune_batch(sd, cams, kernel, (8, 16, 32), (1, 2, 4, 8), reps=3)
     br = darb.BatchRenderer(sd, cams, kernel, tile, depth)
     br.capture()
     for _ in range(3):

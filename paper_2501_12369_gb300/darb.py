@@ -731,7 +731,7 @@ class BatchRenderer:
             raise DarbError(int(st[bad]), f"view {bad} of the batch (M = {int(self.num_instances[bad])})")
 
 
-def autotune_batch(splats: SplatTensors, cams, kernel="half_cosine", tiles=(8, 16, 32), depths=(1, 2, 4), reps=5):
+def autotune_batch(splats: SplatTensors, cams, kernel="half_cosine", tiles=(8, 16, 32), depths=(1, 2, 4, 8), reps=5):
     """(tile, depth) with the fastest graph-replayed batch over `cams`, and the ms per batch of
     every pair.  Capacities are sized per tile from counting passes."""
     times = {}

@@ -578,9 +578,10 @@ constexpr bool kPassOnesweep = DARB_PASS_ONESWEEP != 0;
 #endif
 constexpr int kSortCtasPerSm = DARB_SORT_CTAS_PER_SM;
 
-// Peer masks by match.any (one instruction) or by one ballot per digit bit.
+// Peer masks by match.any or by one ballot per digit bit (the default: the ballots measured
+// faster, 0.462 -> 0.436 ms for the sort stage at 3M splats / 1080p).
 #ifndef DARB_PEERS_BY_MATCH
-#define DARB_PEERS_BY_MATCH 1
+#define DARB_PEERS_BY_MATCH 0
 #endif
 constexpr bool PEERS_BY_MATCH = DARB_PEERS_BY_MATCH != 0;
 

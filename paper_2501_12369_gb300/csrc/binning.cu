@@ -415,7 +415,7 @@ k_tile_diff(int n, const uint32_t *__restrict__ order, const uint32_t *__restric
         bool live = false;
         if (k < m) {
             i = order ? (int)order[k] : k;
-            live = radius[i] != 0;
+            live = n_vis != nullptr || radius[i] != 0;  // the compacted order holds visible splats only
         }
         int4 r = make_int4(0, 0, 0, 0);
         uint64_t pk = kRunsUnpacked;
@@ -571,6 +571,12 @@ constexpr int kScanBlock = 4096;  // values per CTA of the table scan (1024 thre
 #define DARB_PASS_ONESWEEP 1
 #endif
 constexpr bool kPassOnesweep = DARB_PASS_ONESWEEP != 0;
+
+// CTAs per SM of the tile difference array (each privatises the array in shared memory and
+// adds it to the global one at the end).
+#ifndef DARB_TILE_DIFF_CTAS_PER_SM
+#define DARB_TILE_DIFF_CTAS_PER_SM 4
+#endif
 
 // Resident CTAs per SM the one-pass sort kernels are compiled for (their register budget).
 #ifndef DARB_SORT_CTAS_PER_SM
@@ -1420,7 +1426,7 @@ cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int til
         const size_t smem = (size_t)diff_size * 4;
         if (smem <= kMaxDiffSmem) {
             TRY(cudaFuncSetAttribute(k_tile_diff<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            const int blocks = std::min((n + 1023) / 1024, 2 * 152);
+            const int blocks = std::min((n + 1023) / 1024, DARB_TILE_DIFF_CTAS_PER_SM * 152);
             launch_k(k_tile_diff<true>, blocks, 1024, smem, st, n, n_vis_dev ? order : nullptr, n_vis_dev, proj.radius,
                      proj.tile_rect, proj.tile_runs, proj.mean2d, proj.conic_o, sc, tiles_x, diff_size, diff);
         } else {

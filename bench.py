@@ -885,7 +885,7 @@ def run_reference(args):
     import oracle
     oracle.build()
     splats, cams = synth.scene_3m_1080p()
-    args.tile = args.tile or 16
+    args.tile = args.tile or 32  # the tile the default run of this bench autotunes to
     vals = []
     for i in range(args.warmup + args.steps):
         r = cpu_baseline(splats, [cams[i % len(cams)]], args.kernel, args.tile, target_seconds=2.0)

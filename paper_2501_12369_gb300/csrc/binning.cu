@@ -388,8 +388,13 @@ k_duplicate_balanced(int n, const uint32_t *__restrict__ order, const uint32_t *
 // have been compacted (order and n_vis given), else all n with the culled ones skipped.  With
 // SMEM each CTA accumulates a private copy in shared memory (grid-stride over splats) and adds
 // its non-zero entries to the global array once.
+#ifdef DARB_TILE_DIFF_MIN_CTAS
+#define DARB_TILE_DIFF_BOUNDS __launch_bounds__(1024, DARB_TILE_DIFF_MIN_CTAS)
+#else
+#define DARB_TILE_DIFF_BOUNDS __launch_bounds__(1024)
+#endif
 template <bool SMEM>
-__global__ void __launch_bounds__(1024)
+__global__ void DARB_TILE_DIFF_BOUNDS
 k_tile_diff(int n, const uint32_t *__restrict__ order, const uint32_t *__restrict__ n_vis,
             const int *__restrict__ radius, const int4 *__restrict__ rect, const uint64_t *__restrict__ runs,
             const float2 *__restrict__ mean2d, const float4 *__restrict__ conic_o, SpanCtx sc, int tiles_x,

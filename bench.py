@@ -634,15 +634,17 @@ def run_ours(args):
 
 
 def launches_per_step(strategy, tile_bits, fused=True):
-    """Kernels of libdarb.so launched per training step (memsets excluded)."""
+    """Kernels of libdarb.so launched per training step."""
     if strategy == 1:  # 64-bit keys: block sums, scan, duplicate, histogram, hist scan, passes, ranges
         sort = 6 + (32 + tile_bits + 7) // 8
     else:  # visible count, its scan, depth compaction with the histograms, hist scan, 4 depth passes,
         # block sums, scan, tile diff, tile setup, offsets, duplication fused with the first tile
         # pass, the other tile passes
         sort = 4 + 4 + 5 + max(1, (tile_bits + 7) // 8)
-    # preprocess, render_fwd, l1, render_bwd, then preprocess_bwd + 5 Adam groups or one fused kernel
-    return 1 + sort + 1 + 1 + 1 + (1 if fused else 1 + 5)
+    sort += 1  # the zeroing of the sort's counters, status and ranges
+    # preprocess, render_fwd, the loss (zeroing + L1), render_bwd (zeroing of grad2d + the
+    # compositing backward), then preprocess_bwd + 5 Adam groups or one fused kernel
+    return 1 + sort + 1 + 2 + 2 + (1 if fused else 1 + 5)
 
 
 def kernel_sweep(ts, step, cam_seq, first, stages, restore_kernel, steps=20):

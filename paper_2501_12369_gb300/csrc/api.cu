@@ -207,7 +207,7 @@ darb_status darb_render_bwd(const darb_projected *proj, int32_t n, const darb_bi
         (n > 0 && (!grad2d || !aligned16(grad2d))))
         return DARB_ERR_INVALID_ARG;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    if (n > 0) DARB_CUDA_TRY(cudaMemsetAsync(grad2d, 0, (size_t)n * 12 * sizeof(float), st));
+    if (n > 0) DARB_CUDA_TRY(launch_zero(st, grad2d, (size_t)n * 12 * sizeof(float)));
     const int tiles_x = tile_count(cam->width, tile), tiles_y = tile_count(cam->height, tile);
     DARB_CUDA_TRY(launch_render_bwd(kparams->kind, tile, tiles_x, tiles_y, bins->ranges, bins->values,
                                     reinterpret_cast<const float2 *>(proj->mean2d),

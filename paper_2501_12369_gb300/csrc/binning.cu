@@ -1290,9 +1290,8 @@ cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int til
         e = (x);                        \
         if (e != cudaSuccess) return e; \
     } while (0)
-    TRY(cudaMemsetAsync(at(10), 0, L.off[14] - L.off[10], st));
-    TRY(cudaMemsetAsync(out.status, 0, sizeof(uint32_t), st));
-    TRY(cudaMemsetAsync(out.ranges, 0, (size_t)n_tiles * 2 * sizeof(uint32_t), st));
+    TRY(launch_zero(st, at(10), L.off[14] - L.off[10], out.status, sizeof(uint32_t), out.ranges,
+                    (size_t)n_tiles * 2 * sizeof(uint32_t)));
     uint32_t *block_sums = reinterpret_cast<uint32_t *>(at(6));
     auto *block_off = reinterpret_cast<unsigned long long *>(at(7));
     uint32_t *counters = reinterpret_cast<uint32_t *>(at(13));

@@ -59,6 +59,11 @@ cudaError_t launch_render_fwd_batch(int kind, int tile, const BatchView *views, 
 cudaError_t launch_psi_moment(const darb_kernel_params &k, double *sums, cudaStream_t st);
 
 // ssim.cu: the L1 + D-SSIM image loss and its gradient.
+// Zeroes up to three device regions (byte counts multiple of 4) in one kernel launch, which,
+// unlike a memset, overlaps its start with the preceding kernel's drain.
+cudaError_t launch_zero(cudaStream_t st, void *p0, size_t b0, void *p1 = nullptr, size_t b1 = 0, void *p2 = nullptr,
+                        size_t b2 = 0);
+
 size_t l1_dssim_workspace_bytes(int W, int H);
 cudaError_t launch_l1_dssim(const float *image, const float *target, int W, int H, float lam, void *workspace,
                             float *dL, float *loss, cudaStream_t st);

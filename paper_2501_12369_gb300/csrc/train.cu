@@ -1,6 +1,8 @@
 // Training-step kernels: the L1 photometric loss term (paper Sec. 4.2) and the Adam update of
 // the 3DGS optimiser (Sec. 5: original 3DGS hyper-parameters, opacity learning rate 0.02).
 // Both are elementwise and HBM-bound; float4 accesses where the layout allows.
+#include <algorithm>
+
 #include "kernels.cuh"
 
 namespace darb {
@@ -115,9 +117,43 @@ int grid_for(long long count) {
 
 }  // namespace
 
+namespace {
+
+struct ZeroRegion {
+    void *p;
+    size_t bytes;
+};
+
+__global__ void __launch_bounds__(256) k_zero(ZeroRegion r0, ZeroRegion r1, ZeroRegion r2) {
+    pdl_entry();
+    const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (size_t)gridDim.x * blockDim.x;
+    const ZeroRegion rs[3] = {r0, r1, r2};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const ZeroRegion r = rs[k];
+        if (!r.p || r.bytes == 0) continue;
+        if ((reinterpret_cast<uintptr_t>(r.p) & 15) == 0 && (r.bytes & 15) == 0) {
+            uint4 *q = reinterpret_cast<uint4 *>(r.p);
+            for (size_t i = tid; i < r.bytes / 16; i += stride) q[i] = make_uint4(0, 0, 0, 0);
+        } else {
+            uint32_t *q = reinterpret_cast<uint32_t *>(r.p);
+            for (size_t i = tid; i < r.bytes / 4; i += stride) q[i] = 0u;
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_zero(cudaStream_t st, void *p0, size_t b0, void *p1, size_t b1, void *p2, size_t b2) {
+    const size_t words = (b0 + b1 + b2) / 16 + 1;
+    const int blocks = (int)std::min<size_t>((words + 255) / 256, 152 * 8);
+    launch_k(k_zero, blocks, 256, 0, st, ZeroRegion{p0, b0}, ZeroRegion{p1, b1}, ZeroRegion{p2, b2});
+    return cudaGetLastError();
+}
+
 cudaError_t launch_l1_loss(const float *image, const float *target, int count, float *dL, float *loss,
                            cudaStream_t st) {
-    cudaError_t e = cudaMemsetAsync(loss, 0, sizeof(float), st);
+    cudaError_t e = launch_zero(st, loss, sizeof(float));
     if (e != cudaSuccess) return e;
     if (count == 0) return cudaSuccess;
     launch_k(k_l1_loss, grid_for(count), 256, 0, st, image, target, count, 1.0f / (float)count, dL, loss);

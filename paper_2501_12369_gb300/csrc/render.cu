@@ -497,7 +497,7 @@ cudaError_t fwd_batch_t(const BatchView *views, int n_views, int total_tiles, ui
     long long grid = (long long)sms * occ;
     if (max_ctas > 0 && grid > max_ctas) grid = max_ctas;
     if (grid > total_tiles) grid = total_tiles;
-    e = cudaMemsetAsync(queue, 0, sizeof(uint32_t), st);
+    e = launch_zero(st, queue, sizeof(uint32_t));
     if (e != cudaSuccess) return e;
     launch_k(k_render_fwd_batch<KIND, TILE>, (int)grid, RenderShape<TILE>::NT, 0, st, views, n_views, total_tiles, queue,
              qmax, strict, ks);

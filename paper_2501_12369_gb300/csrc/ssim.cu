@@ -225,7 +225,7 @@ cudaError_t launch_l1_dssim(const float *image, const float *target, int W, int 
     double *sums = reinterpret_cast<double *>(w);
     float *maps = reinterpret_cast<float *>(w + 256);
     const size_t n = (size_t)3 * W * H;
-    cudaError_t e = cudaMemsetAsync(sums, 0, 2 * sizeof(double), st);
+    cudaError_t e = launch_zero(st, sums, 2 * sizeof(double));
     if (e != cudaSuccess) return e;
     static const Window win = make_window();
     const dim3 grid((W + kSsimTs - 1) / kSsimTs, (H + kSsimTs - 1) / kSsimTs, 3);

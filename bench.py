@@ -13,6 +13,7 @@ Prints one JSON line (rank 0).  --impl reference times the CPU oracle instead.
 from __future__ import annotations
 
 import argparse
+import datetime
 import ctypes
 import json
 import os
@@ -73,9 +74,10 @@ def max_over_ranks(dist, value, device):
 # ----------------------------------------------------------------------------- clocks
 
 class ClockSampler:
-    """nvidia-smi sampled every 200 ms while the timed region runs."""
+    """nvidia-smi sampled every 50 ms; stop(t0, t1) keeps the samples taken between the host
+    times t0 and t1 (the timed region)."""
 
-    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    QUERY = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -89,12 +91,12 @@ class ClockSampler:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
 
-    def stop(self):
+    def stop(self, t0=None, t1=None):
         if self.proc is None:
             return None
         self.proc.terminate()
@@ -105,13 +107,17 @@ class ClockSampler:
         rows = []
         for line in open(self.path):
             f = [x.strip() for x in line.split(",")]
-            if len(f) < 9:
+            if len(f) < 10:
                 continue
             try:
-                rows.append(dict(sm=float(f[1]), max=float(f[2]), hw=f[5], hwt=f[6], swt=f[7], pc=f[8]))
+                ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append(dict(t=ts, sm=float(f[2]), max=float(f[3]), hw=f[6], hwt=f[7], swt=f[8], pc=f[9]))
             except ValueError:
                 continue
         os.unlink(self.path)
+        if t0 is not None and t1 is not None:
+            inside = [r for r in rows if t0 - 0.025 <= r["t"] <= t1 + 0.025]
+            rows = inside or rows
         if not rows:
             return None
         reasons = set()
@@ -451,24 +457,31 @@ def run_ours(args):
     Ms = ts.size_capacity(cam_seq)
     torch.cuda.synchronize()
 
-    # warm-up
+    # warm-up (W steps, then more until the clock sampler has been running for 0.5 s, so that
+    # its samples cover the timed region)
+    clocks = ClockSampler(local)
+    clocks.start()
+    t_sampler = time.time()
     for i in range(args.warmup):
         step(i)
     torch.cuda.synchronize()
+    while time.time() - t_sampler < 0.5:
+        step(args.warmup - 1)
+        torch.cuda.synchronize()
 
     # timed training steps (no events inside the steps, so that consecutive kernels overlap as
     # they do in a training loop)
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    clocks = ClockSampler(local)
     barrier(dist)
     torch.cuda.synchronize()
-    clocks.start()
+    t_region0 = time.time()
     start.record()
     for k in range(args.steps):
         step(args.warmup + k)
     end.record()
     torch.cuda.synchronize()
-    clk = clocks.stop()
+    t_region1 = time.time()
+    clk = clocks.stop(t_region0, t_region1)
     barrier(dist)
     ms_total = start.elapsed_time(end)
     ms_max = max_over_ranks(dist, ms_total, device)

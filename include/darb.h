@@ -438,7 +438,8 @@ typedef struct {
 
 typedef struct {
     int32_t scene_id;   /* from darb_serve_add_scene */
-    int32_t kernel;     /* a darb_kernel, with its darb_kernel_defaults parameters */
+    int32_t kernel;     /* one of the seven fixed darb_kernel kinds, with its darb_kernel_defaults
+                           parameters (a DARB_GENERIC member is not served: DARB_ERR_INVALID_ARG) */
     darb_camera cam;
     float *image;       /* device [3][H][W], caller-owned, written by the server; keep it alive and
                            unread until the ticket completes */

@@ -190,8 +190,9 @@ darb_status darb_tile_grid(const darb_camera *cam, int32_t tile, int32_t *tiles_
  * the "cov *= correctionFactor" lines of the Sec. B listings): view transform, near
  * cull (z <= near_plane), Sigma = R S S^T R^T, Sigma2 = psi (J W Sigma W^T J^T)_2x2
  * + 0.3 I, conic, R = ceil(3 sqrt(lambda_max)) (Sec. 4.1), pixel-exact tile rectangle,
- * SH colour.  Geometry follows a fixed IEEE FP32 operation sequence, so the results
- * are bit-reproducible.  splats, cam, kparams: host structs holding device pointers
+ * member tiles (the row runs of the ellipse q <= kparams->q_max; a splat without member
+ * tiles is culled), SH colour.  Geometry follows a fixed IEEE FP32 operation sequence, so
+ * the results are bit-reproducible.  splats, cam, kparams: host structs holding device pointers
  * (splats) or values.  out: host struct of caller-owned device buffers sized n. */
 darb_status darb_preprocess(const darb_splats *splats, const darb_camera *cam,
                             const darb_kernel_params *kparams, int32_t tile,
@@ -212,9 +213,10 @@ darb_status darb_bin_sort_workspace_size(int32_t n, int32_t tile, const darb_cam
 
 /* Steps 2 and 3: tile/depth key duplication and radix sort (the tile-based
  * rasterization with a bounding box that Sec. A.3 inherits from 3DGS).  Scans
- * tiles_touched, emits one instance per tile of each rectangle and sorts them with LSD
- * onesweep radix passes into the order of key = tile << 32 | bits(depth), ties by splat
- * index, then writes the per-tile ranges.  strategy: a darb_sort_strategy.
+ * tiles_touched, emits one instance per member tile of each splat (the row runs of
+ * darb_projected; kparams->q_max sets the ellipse) and sorts them with LSD onesweep radix
+ * passes into the order of key = tile << 32 | bits(depth), ties by splat index, then writes
+ * the per-tile ranges, [0, 0) for a tile without instances.  strategy: a darb_sort_strategy.
  * proj: darb_preprocess outputs.  workspace: device, at least
  * darb_bin_sort_workspace_size bytes, contents scratch.  capacity: entries of
  * out->keys / out->values (< 2^30).  num_instances_host: if non-NULL the call

@@ -285,6 +285,30 @@ def _tile_pixel_mask(cam, tile, tiles):
     return m
 
 
+def test_4k_view_with_8_pixel_tiles_on_sampled_tiles():
+    """3840 x 2160 with 8-pixel tiles: 129,600 tiles (17 tile bits), so the tile sort takes three
+    passes, and the tile counts and their setup run from global memory.  300k clustered splats;
+    preprocess for every splat, lists and pixels on 32 sampled occupied tiles."""
+    splats = synth.cluster_scene(300_000, seed=4)
+    cam = synth.fibonacci_cameras(16, 6.0, 3840, 2160, 3000.0)[5]
+    tile, kernel = 8, "half_cosine"
+    r, sd, proj, bins, img = gpu_forward(splats, cam, kernel, tile)
+    assert int(bins.status.item()) == 0
+    kp = oracle.kernel_params(kernel)
+    ref_p = oracle.project(splats, cam, kp, tile, True)
+    check_preprocess(proj, ref_p)
+    ranges = to_np(bins.ranges)
+    assert ranges.shape[0] == 480 * 270
+    occupied = np.flatnonzero(ranges[:, 1] > ranges[:, 0])
+    tiles = np.sort(np.random.default_rng(11).choice(occupied, 32, replace=False))
+    mask = np.zeros(ranges.shape[0], np.uint8)
+    mask[tiles] = 1
+    lists = oracle.build_lists(ref_p, cam, tile, mask)
+    check_lists(bins, lists, mask)
+    ref_f = oracle.render(ref_p, cam, kp, tile, "tiled", lists, mask)
+    check_render(img, bins, ref_f, cam, tile, pixel_mask=_tile_pixel_mask(cam, tile, tiles))
+
+
 @pytest.mark.parametrize("tile", [32, 8])
 def test_full_size_training_view_on_sampled_tiles(tile):
     """3M splats, 1920x1080, half-cosine, default sort: with 32-pixel tiles the configuration the

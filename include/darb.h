@@ -327,8 +327,9 @@ darb_status darb_adam_step(const darb_train_params *params, const darb_splat_gra
  * stay in registers and go straight into its Adam update, so no darb_splat_grads buffer is
  * written or read.  Same arguments and results as the two calls in sequence (gradients of
  * culled splats are zero; every splat takes the step).  params: read for the forward values
- * (means, scales, quats, sh) and updated in place; quats, sh and their moments 16-byte
- * aligned.  proj, grad2d: as for darb_preprocess_bwd. */
+ * (means, scales, quats, sh) and updated in place; every parameter and moment array 16-byte
+ * aligned (the Adam pass moves float4 lanes over each group).  proj, grad2d: as for
+ * darb_preprocess_bwd.  DARB_ERR_INVALID_ARG on a missing or misaligned pointer. */
 darb_status darb_preprocess_bwd_adam(const darb_train_params *params, const darb_camera *cam,
                                      const darb_kernel_params *kparams, const darb_projected *proj,
                                      const float *grad2d, const darb_adam_state *state,

@@ -353,10 +353,7 @@ darb_status darb_preprocess_bwd_adam(const darb_train_params *params, const darb
                        state->v_scales, state->m_quats, state->v_quats, state->m_opac, state->v_opac,
                        state->m_sh, state->v_sh};
     for (const void *q : p)
-        if (!q) return DARB_ERR_INVALID_ARG;
-    const void *a16[] = {params->quats, state->m_quats, state->v_quats, params->sh, state->m_sh, state->v_sh};
-    for (const void *q : a16)
-        if (!aligned16(q)) return DARB_ERR_INVALID_ARG;
+        if (!q || !aligned16(q)) return DARB_ERR_INVALID_ARG;  // float4 lanes over every group
     DARB_CUDA_TRY(launch_preprocess_bwd_adam(params->n, params->sh_degree, *params, *state, make_adam_consts(*cfg),
                                              make_cam(*cam), kparams->psi, proj->radius, proj->clamped, grad2d,
                                              reinterpret_cast<cudaStream_t>(stream)));

@@ -213,6 +213,11 @@ def test_fused_backward_adam_argument_checks():
         darb.darb_preprocess_bwd_adam(p, cam, r.kparams, proj, g2.reshape(-1)[1:], st, _cfg(1))  # off 16 B
     with pytest.raises(darb.DarbError):
         darb.darb_preprocess_bwd_adam(p, cam, r.kparams, proj, g2, st, _cfg(0))  # steps count from 1
+    shifted, _ = _clone(p, st)
+    buf = torch.empty(p.means.numel() + 1, device="cuda")
+    shifted.means = buf[1:].view_as(p.means)  # 4 B past a 16-byte boundary: the float4 lanes need it
+    with pytest.raises(darb.DarbError):
+        darb.darb_preprocess_bwd_adam(shifted, cam, r.kparams, proj, g2, st, _cfg(1))
 
 
 # --------------------------------------------------------------------------- L1 + D-SSIM term

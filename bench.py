@@ -570,8 +570,8 @@ def run_ours(args):
     achieved = ab / (stage_ms[rl_stage] / 1e3) / 1e9
     stage_frac = {st: round(ab_of(st) / (stage_ms[st] / 1e3) / 1e9 / peak_gbs, 4)
                   for st in single + ["bin_sort"] if ab_of(st)}
-    # the same stages against the survey's per-unit byte figures (what the standard 3DGS design
-    # moves: 64-bit keys over p = ceil((32 + log2 tiles) / 8) passes, gradients through HBM)
+    # the same stages against the per-unit byte figures of the standard 3DGS design (64-bit keys
+    # over p = ceil((32 + log2 tiles) / 8) passes, gradients through HBM)
     p64 = (32 + tile_bits + 7) // 8
     contract = {"preprocess": ts.n * 288, "bin_sort": ts.n * 24 + M_mean * (12 + 8 + 24 * p64),
                 "preprocess_bwd": ts.n * 500, "adam": ts.n * 28 * (11 + 3 * sh_k),

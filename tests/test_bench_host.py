@@ -70,3 +70,19 @@ def test_algorithmic_bytes_grow_with_the_work():
         bench.algorithmic_bytes("bin_sort", n, M, 6, k, n_vis=10 ** 6)
     # dense Adam: every parameter and both moments read and written, whatever is visible
     assert bench.algorithmic_bytes("adam", n, M, 6, k) == n * ((3 + 3 + 4 + 1 + 3 * k) * 28 + 32)
+
+
+def test_cpu_baseline_window_is_scaled_to_the_frame():
+    # the reference arm's quarter-window step: per-pixel stages scaled by the frame's pixels over
+    # the window's, so the estimate stays close to the full-view one
+    from paper_2501_12369_gb300 import synth
+    import oracle
+    oracle.build()
+    s = synth.cluster_scene(20_000, seed=3)
+    cam = synth.fibonacci_cameras(8, 6.0, 1920, 1080, 1500.0)[2]
+    full = bench.cpu_baseline(s, [cam], "half_cosine", 32, target_seconds=0.2)
+    quarter = bench.cpu_baseline(s, [cam], "half_cosine", 32, target_seconds=0.2, window=(960, 0, 960, 544))
+    assert full["value"] > 0 and quarter["value"] > 0
+    assert "x4" in quarter["sample"] and "960x544 window at (960, 0)" in quarter["sample"]
+    assert "one 1920x1080 view" in full["sample"]
+    assert 0.2 < quarter["value"] / full["value"] < 5.0

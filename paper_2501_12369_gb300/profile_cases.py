@@ -7,6 +7,10 @@ CASE is one of
   sort       two forward passes (the binning and sorting kernels, then compositing)
   train_tail fused preprocess backward + Adam and the separate pair, 3 warm-up iterations
              each, then 20 timed iterations of each (prints ms per iteration)
+  ssim       three L1 + D-SSIM loss evaluations (k_ssim_fwd / k_ssim_bwd) of a seeded image
+             against a seeded target, N pixels wide (16:9; default 3840 when N is not given)
+  batch      two eager batched renders (k_render_fwd_batch) of 16 cameras of the 1M-splat
+             mixed-resolution multi-view scene, 8 streams, TILE-pixel tiles
 on N clustered splats (default 1,000,000, SH degree 3) seen by camera 0 of the 1920x1080
 Fibonacci-sphere cameras (fx = 1500), with TILE-pixel tiles (default 32).  Inputs are seeded.
 Each case launches a fixed sequence, so `ncu -k <kernel> -s <skip> -c <count>` selects the
@@ -93,13 +97,39 @@ def case_train_tail(n, tile):
           f"separate {ev[1].elapsed_time(ev[2]) / 20:.4f} ms per iteration")
 
 
-CASES = {"render": case_render, "sort": case_sort, "train_tail": case_train_tail}
+def case_ssim(n, tile):
+    build.build()
+    W = n if n <= 16384 else 3840
+    H = W * 9 // 16
+    img = torch.from_numpy(synth.random_target(H, W, seed=1)).cuda()
+    tgt = torch.from_numpy(synth.random_target(H, W, seed=2)).cuda()
+    ws = torch.empty(darb.darb_l1_dssim_workspace_size(W, H), dtype=torch.uint8, device="cuda")
+    for _ in range(3):
+        dL, loss = darb.darb_l1_dssim_loss(img, tgt, 0.2, workspace=ws)
+    torch.cuda.synchronize()
+    print(f"{W}x{H}: loss {float(loss[0]):.6f}, mean SSIM {float(loss[1]):.6f}")
+
+
+def case_batch(n, tile):
+    build.build()
+    s, cams = synth.scene_1m_multiview(16)
+    sd = darb.splats_to_device(s)
+    br = darb.BatchRenderer(sd, cams, "half_cosine", tile, 8)
+    for _ in range(2):
+        br.render()
+    torch.cuda.synchronize()
+    br.check()
+    print("views", len(cams), "instances", int(br.num_instances.sum()))
+
+
+CASES = {"render": case_render, "sort": case_sort, "train_tail": case_train_tail, "ssim": case_ssim,
+         "batch": case_batch}
 
 
 def main(argv):
     if not argv or argv[0] not in CASES:
         raise SystemExit(__doc__)
-    n = int(argv[1]) if len(argv) > 1 else 1_000_000
+    n = int(argv[1]) if len(argv) > 1 else (3840 if argv[0] == "ssim" else 1_000_000)
     tile = int(argv[2]) if len(argv) > 2 else 32
     CASES[argv[0]](n, tile)
 

@@ -34,9 +34,10 @@
 //   over the low 32 + ceil(log2 tiles) bits, k_ranges.  About 170 bytes per instance.
 //
 // k_onesweep is one LSD pass: unordered per-warp digit counts published at once (so successors
-// can look back early), stable warp-level ranking with match.any, decoupled look-back across
-// partitions claimed in launch order (spins bounded; on timeout the status word is set and
-// successors are released), and staging in shared memory so the scatter leaves in digit runs.
+// can look back early), stable warp-level ranking (peers by one ballot per digit bit, or by
+// match.any), decoupled look-back across partitions claimed in launch order (spins bounded; on
+// timeout the status word is set and successors are released), and staging in shared memory so
+// the scatter leaves in digit runs.
 #include <algorithm>
 #include <utility>
 
@@ -1110,8 +1111,12 @@ k_depth_compact(int n, const int *__restrict__ radius, const float *__restrict__
         for (int p = 0; p < kMaxPasses; ++p) {  // digit histograms of the visible keys
             if (p >= ps.passes) break;
             const uint32_t d = v ? (key[j] >> ps.shift[p]) & ((1u << ps.bits[p]) - 1u) : 0xffffffffu;
-            const uint32_t peers = __match_any_sync(0xffffffffu, d);
-            if (v && lane == __ffs(peers) - 1) atomicAdd(&s_h[p * 256 + d], (uint32_t)__popc(peers));
+            if (ps.shift[p] < 16) {  // low mantissa bytes: spread digits, rare collisions in a warp
+                if (v) atomicAdd(&s_h[p * 256 + d], 1u);
+            } else {  // exponent bytes: few distinct digits, so a warp's equal digits add once
+                const uint32_t peers = __match_any_sync(0xffffffffu, d);
+                if (v && lane == __ffs(peers) - 1) atomicAdd(&s_h[p * 256 + d], (uint32_t)__popc(peers));
+            }
         }
     }
     __syncthreads();

@@ -1051,6 +1051,11 @@ k_vis_count(int n, const int *__restrict__ radius, uint32_t *__restrict__ block_
     if (threadIdx.x == 0) block_counts[blockIdx.x] = total;
 }
 
+// Depth digits at or above this bit are histogrammed with match.any aggregation, the lower ones
+// with one shared-memory atomic per key.
+#ifndef DARB_DEPTH_HIST_MATCH_SHIFT
+#define DARB_DEPTH_HIST_MATCH_SHIFT 16
+#endif
 __global__ void __launch_bounds__(kScanThreads)
 k_depth_compact(int n, const int *__restrict__ radius, const float *__restrict__ depth,
                 const unsigned long long *__restrict__ block_offsets, const uint32_t *__restrict__ n_vis,
@@ -1111,9 +1116,9 @@ k_depth_compact(int n, const int *__restrict__ radius, const float *__restrict__
         for (int p = 0; p < kMaxPasses; ++p) {  // digit histograms of the visible keys
             if (p >= ps.passes) break;
             const uint32_t d = v ? (key[j] >> ps.shift[p]) & ((1u << ps.bits[p]) - 1u) : 0xffffffffu;
-            if (ps.shift[p] < 16) {  // low mantissa bytes: spread digits, rare collisions in a warp
+            if (ps.shift[p] < DARB_DEPTH_HIST_MATCH_SHIFT) {  // spread digits: rare collisions in a warp
                 if (v) atomicAdd(&s_h[p * 256 + d], 1u);
-            } else {  // exponent bytes: few distinct digits, so a warp's equal digits add once
+            } else {  // exponent side: few distinct digits, so a warp's equal digits add once
                 const uint32_t peers = __match_any_sync(0xffffffffu, d);
                 if (v && lane == __ffs(peers) - 1) atomicAdd(&s_h[p * 256 + d], (uint32_t)__popc(peers));
             }

@@ -15,9 +15,21 @@ k_l1_loss(const float *__restrict__ image, const float *__restrict__ target, int
     pdl_entry();
     __shared__ float s_warp[8];
     float acc = 0.0f;
-    for (int i = blockIdx.x * 256 + threadIdx.x; i < count; i += gridDim.x * 256) {
+    auto sgn = [inv_count](float d) { return d > 0.0f ? inv_count : (d < 0.0f ? -inv_count : 0.0f); };
+    const int tid = blockIdx.x * 256 + threadIdx.x, stride = gridDim.x * 256;
+    // float4 lanes when all three buffers are 16-byte aligned, then the ragged end one by one
+    const bool vec = ((reinterpret_cast<uintptr_t>(image) | reinterpret_cast<uintptr_t>(target) |
+                       reinterpret_cast<uintptr_t>(dL)) & 15) == 0;
+    const int n4 = vec ? count >> 2 : 0;
+    for (int i = tid; i < n4; i += stride) {
+        const float4 a = reinterpret_cast<const float4 *>(image)[i], b = reinterpret_cast<const float4 *>(target)[i];
+        const float d0 = a.x - b.x, d1 = a.y - b.y, d2 = a.z - b.z, d3 = a.w - b.w;
+        reinterpret_cast<float4 *>(dL)[i] = make_float4(sgn(d0), sgn(d1), sgn(d2), sgn(d3));
+        acc += (fabsf(d0) + fabsf(d1)) + (fabsf(d2) + fabsf(d3));
+    }
+    for (int i = 4 * n4 + tid; i < count; i += stride) {
         const float d = image[i] - target[i];
-        dL[i] = d > 0.0f ? inv_count : (d < 0.0f ? -inv_count : 0.0f);
+        dL[i] = sgn(d);
         acc += fabsf(d);
     }
 #pragma unroll
@@ -156,7 +168,7 @@ cudaError_t launch_l1_loss(const float *image, const float *target, int count, f
     cudaError_t e = launch_zero(st, loss, sizeof(float));
     if (e != cudaSuccess) return e;
     if (count == 0) return cudaSuccess;
-    launch_k(k_l1_loss, grid_for(count), 256, 0, st, image, target, count, 1.0f / (float)count, dL, loss);
+    launch_k(k_l1_loss, grid_for((count + 3) / 4), 256, 0, st, image, target, count, 1.0f / (float)count, dL, loss);
     return cudaGetLastError();
 }
 

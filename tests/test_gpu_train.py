@@ -127,6 +127,25 @@ def test_l1_loss_matches_oracle(W, H):
     np.testing.assert_allclose(got, ref_dl, rtol=1e-7)
 
 
+def test_l1_loss_on_buffers_off_a_16_byte_boundary():
+    # the float4 lanes need all three buffers aligned; views 4 bytes in take the one-by-one path
+    W, H = 97, 31
+    rng = np.random.default_rng(5)
+    img = rng.uniform(0, 1, (3, H, W)).astype(np.float32)
+    tgt = rng.uniform(0, 1, (3, H, W)).astype(np.float32)
+    n = img.size
+    bi, bt, bd = (torch.empty(n + 1, device="cuda") for _ in range(3))
+    bi[1:] = torch.from_numpy(img.reshape(-1)).cuda()
+    bt[1:] = torch.from_numpy(tgt.reshape(-1)).cuda()
+    loss = torch.empty(1, device="cuda")
+    dL, loss = darb.darb_l1_loss(bi[1:].view(3, H, W), bt[1:].view(3, H, W), dL_dimage=bd[1:].view(3, H, W),
+                                 loss=loss)
+    torch.cuda.synchronize()
+    ref_loss, ref_dl = oracle.l1_loss(img, tgt)
+    assert abs(float(loss.item()) - ref_loss) <= 1e-5 * ref_loss
+    np.testing.assert_allclose(to_np(dL).astype(np.float64), ref_dl, rtol=1e-7)
+
+
 # --------------------------------------------------------------------------- Adam
 
 @pytest.mark.parametrize("step", [1, 7])

@@ -159,13 +159,25 @@ def check_render(img, bins, ref, cam, tile, pixel_mask=None, tol=COLOUR_TOL):
     return int(uniq.sum()), n_amb, n_unv
 
 
+# Per call of grad_close: (name, elements, elements within rtol alone, elements that pass only
+# through the atol * max floor).  The session summary (conftest.py) prints the totals.
+GRAD_STATS = []
+# Per image-level comparison against the FP64-geometry oracle: dicts printed by the summary.
+GEOM64_STATS = []
+
+
 def grad_close(name, got, ref, rtol=GRAD_RTOL, atol=GRAD_ATOL):
+    """|got - ref| <= rtol |ref| + atol max|ref| per element.  Records how many elements meet the
+    relative bound alone and how many pass only through the absolute floor."""
     got = np.asarray(got, np.float64)
     ref = np.asarray(ref, np.float64)
     scale = np.abs(ref).max(initial=0.0)
     err = np.abs(got - ref)
     bound = rtol * np.abs(ref) + atol * scale
     bad = err > bound
+    rel_ok = err <= rtol * np.abs(ref)
+    nz = ref != 0
+    GRAD_STATS.append((name, int(nz.sum()), int((rel_ok & nz).sum()), int((~rel_ok & ~bad & nz).sum())))
     assert not bad.any(), (f"{name}: {bad.sum()} of {bad.size} elements out of tolerance; worst "
                            f"{(err / np.maximum(bound, 1e-300)).max():.3g}x bound, scale {scale:.3g}")
 

@@ -90,7 +90,7 @@ class darb_densify_cfg(ctypes.Structure):
 class darb_serve_cfg(ctypes.Structure):
     _fields_ = [("scene_bytes", ctypes.c_uint64), ("workspace_bytes", ctypes.c_uint64), ("tile", c_i32),
                 ("max_batch", c_i32), ("depth", c_i32), ("capacity_per_pixel", c_f32),
-                ("capacity_margin", c_f32), ("capacity_min", ctypes.c_uint64)]
+                ("capacity_margin", c_f32), ("capacity_min", ctypes.c_uint64), ("slots", c_i32)]
 
 
 class darb_request(ctypes.Structure):
@@ -99,7 +99,8 @@ class darb_request(ctypes.Structure):
 
 class darb_result(ctypes.Structure):
     _fields_ = [("status", c_i32), ("num_instances", ctypes.c_uint32), ("attempts", ctypes.c_uint32),
-                ("batch_size", ctypes.c_uint32), ("queue_us", ctypes.c_double), ("latency_us", ctypes.c_double)]
+                ("batch_size", ctypes.c_uint32), ("queue_us", ctypes.c_double), ("latency_us", ctypes.c_double),
+                ("batch_id", ctypes.c_uint64), ("gpu_begin_us", ctypes.c_double), ("gpu_end_us", ctypes.c_double)]
 
 
 # Every entry point declared in include/darb.h, with its ctypes signature.
@@ -147,6 +148,7 @@ SIGNATURES = {
     "darb_serve_create": (c_i32, [_P(darb_serve_cfg), _P(c_vp)]),
     "darb_serve_add_scene": (c_i32, [c_vp, _P(darb_splats), _P(c_i32)]),
     "darb_serve_submit": (c_i32, [c_vp, _P(darb_request), _P(ctypes.c_uint64)]),
+    "darb_serve_submit_many": (c_i32, [c_vp, _P(darb_request), c_i32, _P(ctypes.c_uint64), _P(c_i32)]),
     "darb_serve_poll": (c_i32, [c_vp, ctypes.c_uint64, c_i32, _P(darb_result)]),
     "darb_serve_destroy": (None, [c_vp]),
 }
@@ -317,10 +319,12 @@ class Binning:
     M: int | None = None
 
     @staticmethod
-    def empty(capacity, n_tiles, device="cuda"):
+    def empty(capacity, n_tiles, device="cuda", keys=True):
+        """keys=False leaves out the 64-bit keys (only the DARB_SORT_KEYS64 strategy needs them)."""
         f = dict(device=device)
         cap = max(int(capacity), 1)
-        return Binning(torch.empty(cap, dtype=torch.int64, **f), torch.empty(cap, dtype=torch.int32, **f),
+        return Binning(torch.empty(cap, dtype=torch.int64, **f) if keys else None,
+                       torch.empty(cap, dtype=torch.int32, **f),
                        torch.empty(n_tiles, 2, dtype=torch.int32, **f), torch.zeros(1, dtype=torch.int32, **f),
                        torch.zeros(1, dtype=torch.int32, **f))
 
@@ -384,7 +388,10 @@ def darb_bin_sort(proj: Projected, n, tile, cam, workspace: torch.Tensor, capaci
                              workspace.numel() * workspace.element_size(), int(capacity), int(strategy),
                              ctypes.byref(b), ctypes.byref(m) if sync else None, _stream(stream))
     out.M = int(m.value) if sync else None
-    _check(st, "darb_bin_sort")
+    if st != 0:
+        err = DarbError(st, "darb_bin_sort")
+        err.M = out.M  # on DARB_ERR_CAPACITY: the instance count the lists need
+        raise err
     return out
 
 
@@ -527,7 +534,13 @@ def darb_adam_step(params, grads: SplatGrads, state, cfg: darb_adam_config, stre
 # A reusable forward/backward pipeline and its autograd wrapper.
 
 class Rasterizer:
-    """Holds the per-view buffers of one camera configuration and runs the four steps."""
+    """Holds the per-view buffers of one camera configuration and runs the four steps.
+
+    The sort workspace is scratch of a single call and is reused by every forward.  The lists a
+    forward returns are reused too unless `forward(..., owned=True)` is asked for: then they are
+    freshly allocated and belong to the caller, so several forwards can be pending a backward.
+    Calls are ordered on the current stream; forward synchronises once to read the instance count.
+    """
 
     def __init__(self, cam, kernel="half_cosine", tile=16, capacity=None, device="cuda", psi=None,
                  strategy=DARB_SORT_DEPTH_THEN_TILE):
@@ -552,43 +565,60 @@ class Rasterizer:
             self._bins = Binning.empty(self.capacity, self.tiles_x * self.tiles_y, self.device)
             self._n = n
 
-    def forward(self, splats: SplatTensors):
+    def _sort(self, proj, n, owned):
+        tx, ty = darb_tile_grid(self.cam, self.tile)
+        if (tx, ty) != (self.tiles_x, self.tiles_y):  # the camera was changed to another resolution
+            self.tiles_x, self.tiles_y = tx, ty
+            self._ws = None
+        self._ensure(n, self.capacity)
+        out = (Binning.empty(self.capacity, tx * ty, self.device, keys=self.strategy == DARB_SORT_KEYS64)
+               if owned else self._bins)
+        return darb_bin_sort(proj, n, self.tile, self.cam, self._ws, self.capacity, out, strategy=self.strategy)
+
+    def forward(self, splats: SplatTensors, owned=False):
         proj = darb_preprocess(splats, self.cam, self.kparams, self.tile)
         if self.capacity == 0:
             self.capacity = max(1024, 8 * splats.n)
-        self._ensure(splats.n, self.capacity)
         try:
-            bins = darb_bin_sort(proj, splats.n, self.tile, self.cam, self._ws, self.capacity, self._bins,
-                                 strategy=self.strategy)
+            bins = self._sort(proj, splats.n, owned)
         except DarbError as e:
             if e.status != 3:
                 raise
-            self._ensure(splats.n, int(self._bins.M * 1.25) + 1)
-            bins = darb_bin_sort(proj, splats.n, self.tile, self.cam, self._ws, self.capacity, self._bins,
-                                 strategy=self.strategy)
+            self._ensure(splats.n, int(e.M * 1.25) + 1)
+            bins = self._sort(proj, splats.n, owned)
         img = darb_render_fwd(proj, bins, self.cam, self.kparams, self.tile)
         return proj, bins, img
 
-    def backward(self, splats, proj, bins, img, dL_dimage):
-        g2 = darb_render_bwd(proj, splats.n, bins, self.cam, self.kparams, self.tile, img, dL_dimage.contiguous())
-        return darb_preprocess_bwd(splats, self.cam, self.kparams, proj, g2), g2
+    def backward(self, splats, proj, bins, img, dL_dimage, cam=None):
+        cam = self.cam if cam is None else cam
+        g2 = darb_render_bwd(proj, splats.n, bins, cam, self.kparams, self.tile, img, dL_dimage.contiguous())
+        return darb_preprocess_bwd(splats, cam, self.kparams, proj, g2), g2
 
 
 class DarbRasterize(torch.autograd.Function):
-    """image = DarbRasterize.apply(means, scales, quats, opacities, sh, sh_degree, rasterizer)."""
+    """image = DarbRasterize.apply(means, scales, quats, opacities, sh, sh_degree, rasterizer).
+
+    The inputs are the activated splat attributes (scales and opacities after exp / sigmoid,
+    quaternions raw: the library normalises them and differentiates through the normalisation);
+    the output is the [3, H, W] image of `rasterizer.cam`.  Every call keeps its own projected
+    records, lists, image buffers and a snapshot of the camera, so a rasterizer can render several
+    views (or the same view twice) before one backward.  The backward is the hand-written one of
+    Sec. 4.2: compositing replayed back to front, then the chain through the conic, psi, the EWA
+    projection, the quaternion normalisation and the SH basis.
+    """
 
     @staticmethod
     def forward(ctx, means, scales, quats, opacities, sh, sh_degree, rasterizer):
-        s = SplatTensors(means.contiguous(), scales.contiguous(), quats.contiguous(), opacities.contiguous(),
-                         sh.contiguous(), int(sh_degree))
-        proj, bins, img = rasterizer.forward(s)
-        ctx.state = (s, proj, bins, img, rasterizer)
+        s = SplatTensors(means.detach().contiguous(), scales.detach().contiguous(), quats.detach().contiguous(),
+                         opacities.detach().contiguous(), sh.detach().contiguous(), int(sh_degree))
+        proj, bins, img = rasterizer.forward(s, owned=True)
+        ctx.state = (s, proj, bins, img, rasterizer, rasterizer.cam)
         return img.image
 
     @staticmethod
     def backward(ctx, dimage):
-        s, proj, bins, img, r = ctx.state
-        g, _ = r.backward(s, proj, bins, img, dimage.float().contiguous())
+        s, proj, bins, img, r, cam = ctx.state
+        g, _ = r.backward(s, proj, bins, img, dimage.float().contiguous(), cam=cam)
         return g.dmeans, g.dscales, g.dquats, g.dopacities, g.dsh, None, None
 
 
@@ -765,9 +795,9 @@ class Server:
     the library's worker thread).  Images are caller-owned device tensors [3, H, W]."""
 
     def __init__(self, scene_bytes, workspace_bytes, tile=32, max_batch=32, depth=2, capacity_per_pixel=16.0,
-                 capacity_margin=1.15, capacity_min=1 << 16):
+                 capacity_margin=1.15, capacity_min=1 << 16, slots=2):
         self.cfg = darb_serve_cfg(int(scene_bytes), int(workspace_bytes), int(tile), int(max_batch), int(depth),
-                                  float(capacity_per_pixel), float(capacity_margin), int(capacity_min))
+                                  float(capacity_per_pixel), float(capacity_margin), int(capacity_min), int(slots))
         self.handle = c_vp()
         _check(lib().darb_serve_create(ctypes.byref(self.cfg), ctypes.byref(self.handle)), "darb_serve_create")
         self._keep = {}  # ticket -> image tensor, alive until collected
@@ -786,6 +816,23 @@ class Server:
         _check(lib().darb_serve_submit(self.handle, ctypes.byref(req), ctypes.byref(t)), "darb_serve_submit")
         self._keep[int(t.value)] = image
         return int(t.value)
+
+    def submit_many(self, scene_ids, cams, images, kernels="half_cosine"):
+        """Queues several requests at once (the worker sees them together); returns their tickets."""
+        n = len(cams)
+        kernels = [kernels] * n if isinstance(kernels, (str, int)) else list(kernels)
+        for cam, image in zip(cams, images):
+            assert image.is_contiguous() and image.dtype == torch.float32 and \
+                tuple(image.shape) == (3, cam.height, cam.width)
+        reqs = (darb_request * n)(*[darb_request(int(sid), kernel_index(k), camera(c), _p(im))
+                                    for sid, c, im, k in zip(scene_ids, cams, images, kernels)])
+        tickets = (ctypes.c_uint64 * n)()
+        done = c_i32(0)
+        st = lib().darb_serve_submit_many(self.handle, reqs, n, tickets, ctypes.byref(done))
+        for k in range(done.value):
+            self._keep[int(tickets[k])] = images[k]
+        _check(st, "darb_serve_submit_many")
+        return [int(tickets[k]) for k in range(n)]
 
     def poll(self, ticket, timeout_ms=10_000) -> darb_result:
         r = darb_result()

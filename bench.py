@@ -813,7 +813,17 @@ def run_multiview(device, kernel="half_cosine", reps=10):
 
 # ----------------------------------------------------------------------------- serving
 
-def run_serving(device, rates=(200, 500, 1000, 2000), seconds=1.5, kernel="half_cosine", seed=0):
+def _overlapping_batches(results):
+    """Share of batches that began on the device before the previous batch (in device begin
+    order) had ended."""
+    spans = sorted({r.batch_id: (r.gpu_begin_us, r.gpu_end_us) for r in results}.values())
+    if len(spans) < 2:
+        return 0.0
+    return sum(1 for (a0, a1), (b0, b1) in zip(spans, spans[1:]) if b0 < a1) / (len(spans) - 1)
+
+
+def run_serving(device, rates=(200, 500, 1000, 2000, 4000, 8000), seconds=1.5, kernel="half_cosine", seed=0,
+                slots=3):
     """Four resident scenes (200k / 500k / 1M / 3M clustered splats, SH degree 3).  Requests: a
     random scene, a random pose on the radius-5 sphere, a random resolution among 640x360 /
     1280x720 / 1920x1080.  Open loop: Poisson arrivals at each rate for `seconds`, submitted from
@@ -822,7 +832,7 @@ def run_serving(device, rates=(200, 500, 1000, 2000), seconds=1.5, kernel="half_
     import threading
     from paper_2501_12369_gb300 import darb, synth
     sizes = (200_000, 500_000, 1_000_000, 3_000_000)
-    srv = darb.Server(scene_bytes=3 << 30, workspace_bytes=48 << 30, tile=32, max_batch=32, depth=2)
+    srv = darb.Server(scene_bytes=3 << 30, workspace_bytes=48 << 30, tile=32, max_batch=32, depth=2, slots=slots)
     try:
         ids = [srv.add_scene(darb.splats_to_device(synth.cluster_scene(n, seed=seed + i), device))
                for i, n in enumerate(sizes)]
@@ -887,6 +897,7 @@ def run_serving(device, rates=(200, 500, 1000, 2000), seconds=1.5, kernel="half_
         seq_s = time.perf_counter() - t0
         seq_px = sum(c.width * c.height for _, c in seq)
         report = {"workload": "serving_4_scenes_200k_500k_1M_3M_mixed_res", "tile": 32, "max_batch": 32,
+                  "slots": slots,
                   "sequential": {"requests": len(seq), "req_s": len(seq) / seq_s,
                                  "mpix_s": seq_px / seq_s / 1e6, "ms_per_request": 1e3 * seq_s / len(seq)},
                   "rates": []}
@@ -902,6 +913,7 @@ def run_serving(device, rates=(200, 500, 1000, 2000), seconds=1.5, kernel="half_
                                     "mpix_s": px / wall / 1e6, "p50_ms": float(np.percentile(lat, 50)),
                                     "p99_ms": float(np.percentile(lat, 99)),
                                     "mean_batch": float(np.mean([r.batch_size for r in out])),
+                                    "batches_overlapping": _overlapping_batches(out),
                                     "retries": int(sum(r.attempts > 1 for r in out))})
         return report
     finally:
@@ -935,8 +947,14 @@ def run_reference(args):
             "config": {"workload": WORKLOAD, "splats": splats.n, "sh_degree": 3, "width": 1920, "height": 1080,
                        "kernel": args.kernel, "tile": args.tile, "parallelism": "host cores"},
             "impl": "reference",
+            # not a measurement of whole steps: each step times a bounded sample and scales it
+            "estimate": True,
+            "window": [960, 544],
+            "scale": {"per_pixel_stages": "x frame pixels / window pixels (about 4)",
+                      "compositing": "sampled tiles x window tiles / sampled tiles",
+                      "adam": "200k-splat slice x 15"},
             "cpu_baseline": {"value": v, "unit": "it/s", "cores": oracle.num_threads(), "kind": "oracle",
-                             "sample": r["sample"]},
+                             "sample": r["sample"], "estimate": True},
             "e2e": {"value": v, "unit": "it/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

@@ -239,7 +239,8 @@ darb_status darb_bin_sort(const darb_projected *proj, int32_t n, int32_t tile,
  * loads the library until the process exits.  Sizes whose darb_bin_sort_workspace_size exceeds
  * 64 MiB are rejected with DARB_ERR_WORKSPACE.  The first call on a device resolves the array's
  * device address (cudaGetSymbolAddress) with that device current; make it before any stream
- * capture.  The call itself allocates nothing: no cudaMalloc, no cudaFree.  All calls share the
+ * capture; the address is kept for the process, so the device must not be reset
+ * (cudaDeviceReset) after that first call.  The call itself allocates nothing: no cudaMalloc, no cudaFree.  All calls share the
  * one array and each call clears what must start at zero, so calls that overlap on the GPU (two
  * streams, or two host threads) race and must be serialised by the caller.  Other arguments and
  * results are those of darb_bin_sort. */
@@ -416,27 +417,33 @@ darb_status darb_render_batch(const darb_splats *splats, const darb_camera *cams
 /* ---- Serving ----------------------------------------------------------------------------
  * A server renders requests (scene, camera, kernel) against resident splat sets on the device
  * that is current at create time.  darb_serve_create allocates the server's whole device pool
- * once (scene_bytes for splat sets plus workspace_bytes for two batch slots) and starts a
- * worker thread; nothing is allocated afterwards.  The worker batches continuously: whenever a
- * slot is free it takes pending requests in arrival order while their workspace fits the slot
- * (at most max_batch), renders them with darb_render_batch (one call per scene and kernel), and
- * completes their tickets when the batch's work has finished; the next batch is formed while
- * the previous one renders.  A request's instance capacity is capacity_per_pixel x W x H
- * until its scene has been rendered, then the scene's largest instances-per-pixel ratio so far
- * x capacity_margin (at least capacity_min); a view that still overflows is re-queued once,
- * at the head, with the capacity its instance count asks for.  The paper describes no serving
- * system; this is the batched forward path of Sec. 4 behind a request queue. */
+ * once (scene_bytes for splat sets plus workspace_bytes split evenly over `slots` batch slots)
+ * and starts a worker thread; nothing is allocated afterwards.  The worker batches
+ * continuously: whenever a slot is free it takes pending requests in arrival order while their
+ * workspace fits the slot (at most max_batch), renders them with darb_render_batch (one call
+ * per scene and kernel, the calls of a batch on up to four streams of the slot so that they
+ * overlap), and completes their tickets when the batch's work has finished.  Every slot has
+ * its own stream, so a batch formed while others render is enqueued at once and its work
+ * overlaps theirs on the device; batches retire in whatever order they finish.  A request's
+ * instance capacity is capacity_per_pixel x W x H until its scene has been rendered, then the
+ * scene's largest instances-per-pixel ratio so far x capacity_margin (at least capacity_min);
+ * a view that still overflows is re-queued once, at the head, with the capacity its instance
+ * count asks for.  The paper describes no serving system; this is the batched forward path of
+ * Sec. 4 behind a request queue. */
 typedef struct darb_server darb_server;
+
+#define DARB_MAX_SERVE_SLOTS 8
 
 typedef struct {
     uint64_t scene_bytes;      /* device bytes for resident splat sets */
-    uint64_t workspace_bytes;  /* device bytes for the two batch slots (half each) */
+    uint64_t workspace_bytes;  /* device bytes for the batch slots (an equal share each) */
     int32_t tile;              /* 8, 16 or 32 */
     int32_t max_batch;         /* requests per batch, 1 .. DARB_MAX_BATCH_VIEWS */
     int32_t depth;             /* darb_batch_params.depth of each batch, 1 .. 8 */
     float capacity_per_pixel;  /* first capacity guess, instances per pixel (> 0) */
     float capacity_margin;     /* factor on the observed ratio (>= 1) */
     uint64_t capacity_min;     /* lower bound of any capacity (>= 1) */
+    int32_t slots;             /* batches in flight at once, 1 .. DARB_MAX_SERVE_SLOTS (0: 2) */
 } darb_serve_cfg;
 
 typedef struct {
@@ -455,8 +462,10 @@ typedef struct {
     uint32_t batch_size;     /* requests in the batch that rendered it */
     double queue_us;         /* submit -> batch enqueued */
     double latency_us;       /* submit -> image complete, as seen by the worker */
+    uint64_t batch_id;       /* 1, 2, ... in the order batches were enqueued (0: never enqueued) */
+    double gpu_begin_us;     /* device time at which the batch's slot stream began it ... */
+    double gpu_end_us;       /* ... and finished it, both since the server was created */
 } darb_result;
-
 /* DARB_ERR_CUDA if the pool cannot be allocated. */
 darb_status darb_serve_create(const darb_serve_cfg *cfg, darb_server **server);
 
@@ -467,6 +476,13 @@ darb_status darb_serve_add_scene(darb_server *server, const darb_splats *splats,
 /* Queues a request; returns at once with its ticket.  DARB_ERR_NOT_FOUND for an unknown
  * scene, DARB_ERR_ADMISSION if its workspace exceeds a batch slot even alone. */
 darb_status darb_serve_submit(darb_server *server, const darb_request *request, uint64_t *ticket);
+
+/* Queues count requests under one hold of the server's queue, in order, so the worker sees
+ * them together (for instance the views of one camera path): tickets[k] is request k's ticket.
+ * Stops at the first request that fails (same errors as darb_serve_submit) and returns its
+ * status; *submitted is the number queued before it, whose tickets stay valid. */
+darb_status darb_serve_submit_many(darb_server *server, const darb_request *requests, int32_t count,
+                                   uint64_t *tickets, int32_t *submitted);
 
 /* Waits up to timeout_ms for a ticket.  On DARB_OK the result is stored and the ticket is
  * released; DARB_ERR_TIMEOUT leaves it pending; DARB_ERR_NOT_FOUND for an unknown or already

@@ -1,16 +1,19 @@
 // Serving: resident scenes and a continuous-batching render loop on one GPU.
 //
 // The server allocates, once at create time, one device pool split into a scene region (splat
-// sets copied in by darb_serve_add_scene, bump-allocated) and two equal batch slots.  A worker
-// thread owns a CUDA stream and repeats: (1) if a slot is free, take pending requests in FIFO
-// order while their workspace fits the slot (admission by free memory) and at most max_batch,
-// group them by (scene, kernel), and enqueue one darb_render_batch per group plus a copy of the
-// per-view statuses and instance counts to pinned host memory, closed by an event; (2) retire
-// batches whose event has completed: a view that overflowed its capacity goes back to the head
-// of the queue once with the capacity its instance count asks for, every other view completes
-// its ticket.  While one batch renders, the next is formed and enqueued, so the GPU does not
-// idle between batches.  Each request's capacity comes from the largest instances-per-pixel
-// ratio seen so far for its scene (or the configured guess), times a margin.
+// sets copied in by darb_serve_add_scene, bump-allocated) and `slots` equal batch slots.  Every
+// slot owns a stream plus kGroupStreams group streams.  A worker thread repeats: (1) for every
+// free slot, take pending requests in FIFO order while their workspace fits the slot (admission
+// by free memory) and at most max_batch, group them by (scene, kernel), and enqueue one
+// darb_render_batch per group, the groups forked over the slot's group streams so that one
+// group's compositing overlaps the next group's sorts, then joined back into the slot stream,
+// which copies the per-view statuses and instance counts to pinned host memory and records the
+// slot's completion event; (2) retire every batch whose event has completed, in any order: a
+// view that overflowed its capacity goes back to the head of the queue once with the capacity
+// its instance count asks for, every other view completes its ticket.  Because slots have their
+// own streams, a batch formed while others render is on the device at once, and the batches'
+// kernels overlap.  Each request's capacity comes from the largest instances-per-pixel ratio
+// seen so far for its scene (or the configured guess), times a margin.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -28,7 +31,9 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
-constexpr int kSlots = 2;
+constexpr int kMaxSlots = DARB_MAX_SERVE_SLOTS;
+constexpr int kDefaultSlots = 2;
+constexpr int kGroupStreams = 4;
 constexpr uint64_t kPageAlign = 4096;
 
 uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
@@ -56,6 +61,7 @@ struct Batch {
     Clock::time_point launched;
     cudaEvent_t done = nullptr;
     int slot = 0;
+    uint64_t id = 0;
 };
 
 }  // namespace
@@ -64,13 +70,19 @@ struct Batch {
 struct darb_server {
     darb_serve_cfg cfg{};
     int device = 0;
+    int slots = 0;
     unsigned char *pool = nullptr;
     uint64_t scene_bytes = 0, scene_used = 0, slot_bytes = 0;
-    unsigned char *slot_base[darb::kSlots] = {};
-    bool slot_busy[darb::kSlots] = {};
-    uint32_t *host_words[darb::kSlots] = {};  // pinned: [max_batch] statuses then [max_batch] counts
-    cudaStream_t stream = nullptr;
-    cudaEvent_t events[darb::kSlots] = {};
+    unsigned char *slot_base[darb::kMaxSlots] = {};
+    bool slot_busy[darb::kMaxSlots] = {};
+    uint32_t *host_words[darb::kMaxSlots] = {};  // pinned: [max_batch] statuses then [max_batch] counts
+    cudaStream_t stream[darb::kMaxSlots] = {};    // slot streams (stream[0] also copies scenes in)
+    cudaStream_t group_stream[darb::kMaxSlots][darb::kGroupStreams] = {};
+    cudaEvent_t begin[darb::kMaxSlots] = {};      // timed: the slot stream reached the batch ...
+    cudaEvent_t events[darb::kMaxSlots] = {};     // ... and finished it (blocking-sync)
+    cudaEvent_t join[darb::kMaxSlots][darb::kGroupStreams] = {};
+    cudaEvent_t epoch = nullptr;                  // device time zero of gpu_begin_us / gpu_end_us
+    uint64_t next_batch = 1;
 
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -155,8 +167,13 @@ size_t plan_groups(const darb_server *S, const std::vector<Pending> &items, std:
     return total;
 }
 
+struct BatchTimes {
+    uint64_t id = 0;
+    double gpu_begin_us = 0.0, gpu_end_us = 0.0;
+};
+
 void complete(darb_server *S, const Pending &p, int32_t status, uint32_t M, uint32_t batch_size,
-              Clock::time_point launched, Clock::time_point now) {
+              Clock::time_point launched, Clock::time_point now, const BatchTimes &bt = BatchTimes{}) {
     Ticket &t = S->tickets[p.ticket];
     t.done = true;
     t.result.status = status;
@@ -165,6 +182,9 @@ void complete(darb_server *S, const Pending &p, int32_t status, uint32_t M, uint
     t.result.batch_size = batch_size;
     t.result.queue_us = std::chrono::duration<double, std::micro>(launched - p.submitted).count();
     t.result.latency_us = std::chrono::duration<double, std::micro>(now - p.submitted).count();
+    t.result.batch_id = bt.id;
+    t.result.gpu_begin_us = bt.gpu_begin_us;
+    t.result.gpu_end_us = bt.gpu_end_us;
 }
 
 // Forms and enqueues one batch into a free slot (lock held).  Returns false if nothing was launched.
@@ -185,10 +205,17 @@ bool launch_batch(darb_server *S, int slot) {
     uint32_t *d_status = reinterpret_cast<uint32_t *>(base);
     uint32_t *d_count = d_status + S->cfg.max_batch;
     size_t off = slot_header_bytes(S);
+    cudaStream_t ms = S->stream[slot];
     int32_t fail = DARB_OK;
+    // fork: the group streams start after the slot stream reaches this batch
+    if (cudaEventRecord(S->begin[slot], ms) != cudaSuccess) fail = DARB_ERR_CUDA;
+    const int used = std::min<int>((int)groups.size(), kGroupStreams);
+    for (int g = 0; g < used && fail == DARB_OK; ++g)
+        if (cudaStreamWaitEvent(S->group_stream[slot][g], S->begin[slot], 0) != cudaSuccess) fail = DARB_ERR_CUDA;
     int view_no = 0;
     std::vector<int> order;  // item index of each view, in launch order
-    for (const GroupPlan &g : groups) {
+    for (size_t gi = 0; gi < groups.size() && fail == DARB_OK; ++gi) {
+        const GroupPlan &g = groups[gi];
         std::vector<darb_camera> cams;
         std::vector<darb_image> outs;
         for (int i : g.idx) {
@@ -199,28 +226,39 @@ bool launch_batch(darb_server *S, int slot) {
         darb_kernel_params kp{};
         darb_kernel_defaults(g.kernel, &kp);
         const darb_batch_params p = group_params(S, (int)cams.size(), g.capacity);
-        const darb_status st = darb_render_batch(&S->scenes[(size_t)g.scene].splats, cams.data(), &kp, &p, base + off,
-                                                 g.bytes, outs.data(), d_count + view_no, d_status + view_no,
-                                                 reinterpret_cast<darb_stream>(S->stream));
+        const darb_status st =
+            darb_render_batch(&S->scenes[(size_t)g.scene].splats, cams.data(), &kp, &p, base + off, g.bytes, outs.data(),
+                              d_count + view_no, d_status + view_no,
+                              reinterpret_cast<darb_stream>(S->group_stream[slot][gi % kGroupStreams]));
         if (st != DARB_OK) fail = st;
         off += g.bytes;
         view_no += (int)cams.size();
+    }
+    // join: the slot stream continues once every group stream has finished its groups
+    for (int g = 0; g < used; ++g) {
+        if (cudaEventRecord(S->join[slot][g], S->group_stream[slot][g]) != cudaSuccess ||
+            cudaStreamWaitEvent(ms, S->join[slot][g], 0) != cudaSuccess)
+            fail = fail == DARB_OK ? DARB_ERR_CUDA : fail;
     }
     Batch b;
     b.slot = slot;
     b.launched = Clock::now();
     b.done = S->events[slot];
-    // items reordered into launch order, so view v of the slot is b.items[v]
-    for (int i : order) b.items.push_back(items[(size_t)i]);
+    b.id = S->next_batch++;
     if (fail != DARB_OK) {
-        for (const Pending &p : b.items) complete(S, p, fail, 0, (uint32_t)b.items.size(), b.launched, Clock::now());
+        // nothing of this batch may still write into the slot when it is reused
+        for (int g = 0; g < used; ++g) cudaStreamSynchronize(S->group_stream[slot][g]);
+        cudaStreamSynchronize(ms);
+        for (const Pending &p : items) complete(S, p, fail, 0, (uint32_t)items.size(), b.launched, Clock::now());
         S->cv_done.notify_all();
         return true;
     }
+    // items reordered into launch order, so view v of the slot is b.items[v]
+    for (int i : order) b.items.push_back(items[(size_t)i]);
     const size_t words = (size_t)S->cfg.max_batch;
-    cudaMemcpyAsync(S->host_words[slot], d_status, words * 4, cudaMemcpyDeviceToHost, S->stream);
-    cudaMemcpyAsync(S->host_words[slot] + words, d_count, words * 4, cudaMemcpyDeviceToHost, S->stream);
-    if (cudaEventRecord(b.done, S->stream) != cudaSuccess) {
+    cudaMemcpyAsync(S->host_words[slot], d_status, words * 4, cudaMemcpyDeviceToHost, ms);
+    cudaMemcpyAsync(S->host_words[slot] + words, d_count, words * 4, cudaMemcpyDeviceToHost, ms);
+    if (cudaEventRecord(b.done, ms) != cudaSuccess) {
         for (const Pending &p : b.items)
             complete(S, p, DARB_ERR_CUDA, 0, (uint32_t)b.items.size(), b.launched, Clock::now());
         S->cv_done.notify_all();
@@ -231,23 +269,22 @@ bool launch_batch(darb_server *S, int slot) {
     return true;
 }
 
-// Retires the oldest batch if its event completed (lock held).  Returns true if one was retired.
-bool retire_batch(darb_server *S, bool wait) {
-    if (S->inflight.empty()) return false;
-    Batch &b = S->inflight.front();
-    cudaError_t q = cudaEventQuery(b.done);
-    if (q == cudaErrorNotReady && wait) {
-        S->mu.unlock();
-        q = cudaEventSynchronize(b.done);
-        S->mu.lock();
-    }
-    if (q == cudaErrorNotReady) return false;
+// Retires a completed batch (lock held; q is the status of its completion event).
+void retire(darb_server *S, const Batch &b, cudaError_t q) {
     const Clock::time_point now = Clock::now();
+    BatchTimes bt;
+    bt.id = b.id;
+    float ms0 = 0.0f, ms1 = 0.0f;
+    if (q == cudaSuccess && cudaEventElapsedTime(&ms0, S->epoch, S->begin[b.slot]) == cudaSuccess &&
+        cudaEventElapsedTime(&ms1, S->epoch, b.done) == cudaSuccess) {
+        bt.gpu_begin_us = 1e3 * (double)ms0;
+        bt.gpu_end_us = 1e3 * (double)ms1;
+    }
     const uint32_t *hs = S->host_words[b.slot];
     const uint32_t *hc = hs + S->cfg.max_batch;
     std::vector<Pending> retry;
     for (size_t v = 0; v < b.items.size(); ++v) {
-        Pending &p = b.items[v];
+        const Pending &p = b.items[v];
         const int32_t status = q == cudaSuccess ? (int32_t)hs[v] : (int32_t)DARB_ERR_CUDA;
         const uint32_t M = q == cudaSuccess ? hc[v] : 0;
         if (status == DARB_OK || status == DARB_ERR_CAPACITY) {
@@ -260,28 +297,49 @@ bool retire_batch(darb_server *S, bool wait) {
             r.attempts = 2;
             r.capacity = std::min<uint64_t>((uint64_t)((double)M * 1.05) + 1024, kMaxCapacity);
             size_t need = 0;
-            if (single_need(S, r.req, r.capacity, &need) &&
-                need + slot_header_bytes(S) <= S->slot_bytes) {
+            if (single_need(S, r.req, r.capacity, &need) && need + slot_header_bytes(S) <= S->slot_bytes) {
                 retry.push_back(r);
                 continue;
             }
         }
-        complete(S, p, status, M, (uint32_t)b.items.size(), b.launched, now);
+        complete(S, p, status, M, (uint32_t)b.items.size(), b.launched, now, bt);
     }
     for (auto it = retry.rbegin(); it != retry.rend(); ++it) S->pending.push_front(*it);
     S->slot_busy[b.slot] = false;
-    S->inflight.pop_front();
     S->cv_done.notify_all();
-    return true;
+}
+
+// Retires every in-flight batch whose work has completed (lock held).  Returns the number retired.
+int retire_ready(darb_server *S) {
+    int n = 0;
+    for (auto it = S->inflight.begin(); it != S->inflight.end();) {
+        const cudaError_t q = cudaEventQuery(it->done);
+        if (q == cudaErrorNotReady) {
+            ++it;
+            continue;
+        }
+        retire(S, *it, q);
+        it = S->inflight.erase(it);
+        ++n;
+    }
+    return n;
+}
+
+// Blocks (lock released) until the oldest in-flight batch has finished, then retires it.
+void wait_oldest(darb_server *S, std::unique_lock<std::mutex> &lock) {
+    cudaEvent_t ev = S->inflight.front().done;  // only this thread changes `inflight`
+    lock.unlock();
+    cudaEventSynchronize(ev);
+    lock.lock();
+    retire_ready(S);
 }
 
 void worker_loop(darb_server *S) {
     cudaSetDevice(S->device);
     std::unique_lock<std::mutex> lock(S->mu);
     for (;;) {
-        bool progress = false;
-        while (retire_batch(S, false)) progress = true;
-        for (int s = 0; s < kSlots; ++s)
+        bool progress = retire_ready(S) > 0;
+        for (int s = 0; s < S->slots; ++s)
             if (!S->slot_busy[s] && !S->pending.empty()) progress |= launch_batch(S, s);
         if (S->stop && S->pending.empty() && S->inflight.empty()) break;
         if (progress) continue;
@@ -289,7 +347,7 @@ void worker_loop(darb_server *S) {
             if (S->pending.empty())
                 S->cv_work.wait_for(lock, std::chrono::microseconds(50));  // new request or a batch finishing
             else
-                retire_batch(S, true);  // both slots busy: wait for the oldest batch
+                wait_oldest(S, lock);  // every slot busy: wait for the oldest batch
         } else if (!S->pending.empty()) {
             // an empty slot that cannot take the head request (admission is checked at submit,
             // so this is a request whose retry grew past the slot): fail it
@@ -313,25 +371,36 @@ extern "C" {
 
 darb_status darb_serve_create(const darb_serve_cfg *cfg, darb_server **out) {
     if (!cfg || !out || !valid_tile(cfg->tile) || cfg->max_batch < 1 || cfg->max_batch > DARB_MAX_BATCH_VIEWS ||
-        cfg->depth < 1 || cfg->depth > 8 || cfg->scene_bytes == 0 || cfg->workspace_bytes < 2 * kPageAlign ||
+        cfg->depth < 1 || cfg->depth > 8 || cfg->scene_bytes == 0 || cfg->slots < 0 || cfg->slots > kMaxSlots ||
         !(cfg->capacity_per_pixel > 0.0f) || !(cfg->capacity_margin >= 1.0f) || cfg->capacity_min < 1)
         return DARB_ERR_INVALID_ARG;
+    const int slots = cfg->slots == 0 ? kDefaultSlots : cfg->slots;
+    if (cfg->workspace_bytes < (uint64_t)slots * kPageAlign) return DARB_ERR_INVALID_ARG;
     darb_server *S = new darb_server();
     S->cfg = *cfg;
+    S->slots = slots;
     if (cudaGetDevice(&S->device) != cudaSuccess) {
         delete S;
         return DARB_ERR_CUDA;
     }
     S->scene_bytes = align_up(cfg->scene_bytes, kPageAlign);
-    S->slot_bytes = align_up(cfg->workspace_bytes / kSlots, kPageAlign);
-    const uint64_t total = S->scene_bytes + kSlots * S->slot_bytes;
+    S->slot_bytes = cfg->workspace_bytes / (uint64_t)slots / kPageAlign * kPageAlign;
+    const uint64_t total = S->scene_bytes + (uint64_t)slots * S->slot_bytes;
     bool ok = cudaMalloc(&S->pool, total) == cudaSuccess;
-    ok = ok && cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking) == cudaSuccess;
-    for (int s = 0; s < kSlots && ok; ++s) {
+    ok = ok && cudaEventCreate(&S->epoch) == cudaSuccess;
+    for (int s = 0; s < slots && ok; ++s) {
         S->slot_base[s] = S->pool + S->scene_bytes + s * S->slot_bytes;
-        ok = cudaEventCreateWithFlags(&S->events[s], cudaEventDisableTiming | cudaEventBlockingSync) == cudaSuccess;
+        ok = cudaStreamCreateWithFlags(&S->stream[s], cudaStreamNonBlocking) == cudaSuccess;
+        for (int g = 0; g < kGroupStreams && ok; ++g) {
+            ok = cudaStreamCreateWithFlags(&S->group_stream[s][g], cudaStreamNonBlocking) == cudaSuccess;
+            ok = ok && cudaEventCreateWithFlags(&S->join[s][g], cudaEventDisableTiming) == cudaSuccess;
+        }
+        ok = ok && cudaEventCreate(&S->begin[s]) == cudaSuccess;
+        ok = ok && cudaEventCreateWithFlags(&S->events[s], cudaEventBlockingSync) == cudaSuccess;
         ok = ok && cudaMallocHost(&S->host_words[s], 8ull * (uint64_t)cfg->max_batch) == cudaSuccess;
     }
+    ok = ok && cudaEventRecord(S->epoch, S->stream[0]) == cudaSuccess &&
+         cudaEventSynchronize(S->epoch) == cudaSuccess;
     if (!ok) {
         darb_serve_destroy(S);
         cudaGetLastError();
@@ -372,20 +441,20 @@ darb_status darb_serve_add_scene(darb_server *S, const darb_splats *splats, int3
                   {d.opacities, splats->opacities, 4 * N},
                   {d.sh, splats->sh, 12 * K * N}};
     for (const auto &c : copies)
-        if (cudaMemcpyAsync(const_cast<float *>(c.dst), c.src, c.bytes, cudaMemcpyDeviceToDevice, S->stream) !=
+        if (cudaMemcpyAsync(const_cast<float *>(c.dst), c.src, c.bytes, cudaMemcpyDeviceToDevice, S->stream[0]) !=
             cudaSuccess)
             return DARB_ERR_CUDA;
-    if (cudaStreamSynchronize(S->stream) != cudaSuccess) return DARB_ERR_CUDA;
+    if (cudaStreamSynchronize(S->stream[0]) != cudaSuccess) return DARB_ERR_CUDA;
     S->scene_used += align_up(need, 256);
     S->scenes.push_back(Scene{d, 0.0});
     *scene_id = (int32_t)S->scenes.size() - 1;
     return DARB_OK;
 }
 
-darb_status darb_serve_submit(darb_server *S, const darb_request *r, uint64_t *ticket) {
-    if (!S || !r || !ticket || !valid_camera(&r->cam) || !r->image || r->kernel < 0 || r->kernel >= kNumKernels - 1)
+// Validates and queues one request (lock held).
+darb_status enqueue(darb_server *S, const darb_request *r, uint64_t *ticket) {
+    if (!r || !ticket || !valid_camera(&r->cam) || !r->image || r->kernel < 0 || r->kernel >= kNumKernels - 1)
         return DARB_ERR_INVALID_ARG;
-    std::lock_guard<std::mutex> lock(S->mu);
     if (S->stop) return DARB_ERR_INVALID_ARG;
     if (r->scene_id < 0 || r->scene_id >= (int32_t)S->scenes.size()) return DARB_ERR_NOT_FOUND;
     Pending p;
@@ -400,8 +469,30 @@ darb_status darb_serve_submit(darb_server *S, const darb_request *r, uint64_t *t
     S->tickets[p.ticket] = Ticket{};
     S->pending.push_back(p);
     *ticket = p.ticket;
-    S->cv_work.notify_one();
     return DARB_OK;
+}
+
+darb_status darb_serve_submit(darb_server *S, const darb_request *r, uint64_t *ticket) {
+    if (!S) return DARB_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(S->mu);
+    const darb_status st = enqueue(S, r, ticket);
+    if (st == DARB_OK) S->cv_work.notify_one();
+    return st;
+}
+
+darb_status darb_serve_submit_many(darb_server *S, const darb_request *requests, int32_t count, uint64_t *tickets,
+                                   int32_t *submitted) {
+    if (!S || !requests || !tickets || !submitted || count < 0) return DARB_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(S->mu);
+    darb_status st = DARB_OK;
+    int32_t k = 0;
+    for (; k < count; ++k) {
+        st = enqueue(S, &requests[k], &tickets[k]);
+        if (st != DARB_OK) break;
+    }
+    *submitted = k;
+    if (k > 0) S->cv_work.notify_one();
+    return st;
 }
 
 darb_status darb_serve_poll(darb_server *S, uint64_t ticket, int32_t timeout_ms, darb_result *result) {
@@ -432,11 +523,17 @@ void darb_serve_destroy(darb_server *S) {
     }
     S->cv_work.notify_all();
     if (S->worker.joinable()) S->worker.join();
-    for (int s = 0; s < kSlots; ++s) {
+    for (int s = 0; s < kMaxSlots; ++s) {
         if (S->events[s]) cudaEventDestroy(S->events[s]);
+        if (S->begin[s]) cudaEventDestroy(S->begin[s]);
         if (S->host_words[s]) cudaFreeHost(S->host_words[s]);
+        for (int g = 0; g < kGroupStreams; ++g) {
+            if (S->join[s][g]) cudaEventDestroy(S->join[s][g]);
+            if (S->group_stream[s][g]) cudaStreamDestroy(S->group_stream[s][g]);
+        }
+        if (S->stream[s]) cudaStreamDestroy(S->stream[s]);
     }
-    if (S->stream) cudaStreamDestroy(S->stream);
+    if (S->epoch) cudaEventDestroy(S->epoch);
     if (S->pool) cudaFree(S->pool);
     delete S;
 }

@@ -52,10 +52,46 @@ def test_serving_equals_single_views(scenes, max_batch):
         assert all(r.status == 0 for r in results)
         if max_batch == 1:
             assert all(r.batch_size == 1 for r in results)
+        assert all(r.batch_id >= 1 and r.gpu_end_us > r.gpu_begin_us >= 0.0 for r in results)
         for (sid, cam, k), img, r in zip(reqs, imgs, results):
             ref = _single(scenes[sid], cam, k, 16)
             assert torch.equal(img, ref)
             assert r.latency_us >= r.queue_us >= 0.0
+    finally:
+        srv.close()
+
+
+@pytest.mark.parametrize("slots", [2, 3])
+def test_batches_form_and_overlap_under_load(scenes, slots):
+    """48 requests queued at once (one hold of the queue), max_batch 8: the worker must batch
+    them, several batches are on the device together (one begins before another has ended, by
+    the device clock), and every image still equals its single-view render."""
+    big = darb.splats_to_device(synth.cluster_scene(200_000, seed=3))
+    srv = darb.Server(1 << 29, 6 << 30, tile=16, max_batch=8, depth=2, slots=slots)
+    try:
+        ids = [srv.add_scene(s) for s in (big, scenes[0], scenes[2])]
+        # views large enough that a batch's device work outlasts the enqueue of the next one
+        rng = np.random.default_rng(40 + slots)
+        cams = synth.random_pose_cameras(48, 4.0, ((1280, 720), (1920, 1080), (640, 360)), 0.8, seed=40 + slots)
+        reqs = [(int(rng.integers(3)), cams[i], KERNELS[int(rng.integers(len(KERNELS)))]) for i in range(48)]
+        imgs = [torch.full((3, cam.height, cam.width), -1.0, device="cuda") for _, cam, _ in reqs]
+        tickets = srv.submit_many([ids[sid] for sid, _, _ in reqs], [c for _, c, _ in reqs], imgs,
+                                  [k for _, _, k in reqs])
+        results = [srv.poll(t) for t in tickets]
+        assert all(r.status == 0 for r in results)
+        sizes = [r.batch_size for r in results]
+        assert max(sizes) > 1, "no request was batched with another"
+        batches = {}
+        for r in results:
+            batches.setdefault(r.batch_id, (r.gpu_begin_us, r.gpu_end_us))
+        assert len(batches) >= 48 // 8
+        spans = sorted(batches.values())
+        assert all(b > a for a, b in spans), "every batch has a positive device duration"
+        overlapped = sum(1 for (a0, a1), (b0, b1) in zip(spans, spans[1:]) if b0 < a1)
+        assert overlapped >= 1, f"no two batches were on the device together: {spans}"
+        for (sid, cam, k), img in zip(reqs, imgs):
+            ref = _single((big, scenes[0], scenes[2])[sid], cam, k, 16)
+            assert torch.equal(img, ref)
     finally:
         srv.close()
 

@@ -26,7 +26,6 @@ NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-
 # Tuning macros (for example -DDARB_SORT_THREADS=256 -DDARB_SORT_CTAS_PER_SM=4), from the
 # environment; a change of them rebuilds every object.
 DEFINES = os.environ.get("DARB_NVCC_DEFINES", "").split()
-STAMP = os.path.join(OUT_DIR, "defines.txt")
 
 
 def nvcc() -> str:
@@ -45,18 +44,18 @@ def _headers():
             glob.glob(os.path.join(INCLUDE, "*.h")))
 
 
-def _stale(target, deps):
+def _stale(target, deps, stamp):
     if not os.path.exists(target):
         return True
     t = os.path.getmtime(target)
-    return any(os.path.getmtime(d) > t for d in deps + [STAMP])
+    return any(os.path.getmtime(d) > t for d in deps + [stamp])
 
 
-def _compile(src, verbose):
-    obj = os.path.join(OUT_DIR, os.path.basename(src) + ".o")
-    if not _stale(obj, [src] + _headers()):
+def _compile(src, out_dir, defines, stamp, verbose):
+    obj = os.path.join(out_dir, os.path.basename(src) + ".o")
+    if not _stale(obj, [src] + _headers(), stamp):
         return obj
-    cmd = [nvcc()] + NVCC_FLAGS + DEFINES + (["-Xptxas", "-v"] if verbose else []) + ["-c", src, "-o", obj + ".tmp"]
+    cmd = [nvcc()] + NVCC_FLAGS + defines + (["-Xptxas", "-v"] if verbose else []) + ["-c", src, "-o", obj + ".tmp"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed on {os.path.basename(src)}:\n{r.stderr}")
@@ -66,25 +65,38 @@ def _compile(src, verbose):
     return obj
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    os.makedirs(OUT_DIR, exist_ok=True)
-    old = open(STAMP).read() if os.path.exists(STAMP) else None
-    if old != " ".join(DEFINES):
-        with open(STAMP, "w") as f:
-            f.write(" ".join(DEFINES))
+def _build_into(out_dir, lib_path, defines, force, verbose):
+    os.makedirs(out_dir, exist_ok=True)
+    stamp = os.path.join(out_dir, "defines.txt")
+    old = open(stamp).read() if os.path.exists(stamp) else None
+    if old != " ".join(defines):
+        with open(stamp, "w") as f:
+            f.write(" ".join(defines))
     srcs = sources()
     if force:
-        for o in glob.glob(os.path.join(OUT_DIR, "*.o")):
+        for o in glob.glob(os.path.join(out_dir, "*.o")):
             os.remove(o)
     with concurrent.futures.ThreadPoolExecutor(max_workers=len(srcs)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, verbose), srcs))
-    if force or _stale(LIB_PATH, objs):
-        cmd = [nvcc()] + ARCH + ["-shared", "-Xcompiler", "-pthread", "-o", LIB_PATH + ".tmp"] + objs
+        objs = list(ex.map(lambda s: _compile(s, out_dir, defines, stamp, verbose), srcs))
+    if force or _stale(lib_path, objs, stamp):
+        cmd = [nvcc()] + ARCH + ["-shared", "-Xcompiler", "-pthread", "-o", lib_path + ".tmp"] + objs
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc link failed:\n" + r.stderr)
-        os.replace(LIB_PATH + ".tmp", LIB_PATH)
-    return LIB_PATH
+        os.replace(lib_path + ".tmp", lib_path)
+    return lib_path
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """libdarb.so, the library every caller loads."""
+    return _build_into(OUT_DIR, LIB_PATH, DEFINES, force, verbose)
+
+
+def build_variant(name: str, defines, force: bool = False) -> str:
+    """A separately built copy of the library (its own folder under _build/) with extra macros,
+    for tests of build-time paths such as the bounded look-back's timeout."""
+    out_dir = os.path.join(OUT_DIR, name)
+    return _build_into(out_dir, os.path.join(out_dir, "libdarb.so"), DEFINES + list(defines), force, False)
 
 
 if __name__ == "__main__":

@@ -50,7 +50,10 @@ namespace {
 constexpr uint32_t kFlagLocal = 1u << 30;
 constexpr uint32_t kFlagIncl = 2u << 30;
 constexpr uint32_t kCountMask = (1u << 30) - 1;
-constexpr int kSpinLimit = 1 << 22;  // with the 512 ns back-off: about two seconds at most
+#ifndef DARB_SPIN_LIMIT
+#define DARB_SPIN_LIMIT (1 << 22)  // with the 512 ns back-off: about two seconds at most
+#endif
+constexpr int kSpinLimit = DARB_SPIN_LIMIT;
 constexpr int kLookbackWindow = 8;
 constexpr size_t kMaxDiffSmem = 96 * 1024;  // tile difference array privatised per CTA up to this size
 constexpr size_t kMaxSetupSmem = 160 * 1024;  // tile counts + difference array staged in shared memory up to this
@@ -1543,3 +1546,40 @@ cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int til
 }
 
 }  // namespace darb
+
+#ifdef DARB_TEST_HOOKS
+// Test-only entry point, compiled into a separate test build of the library (with a short
+// DARB_SPIN_LIMIT) and declared nowhere else: one onesweep pass whose single CTA finds the
+// partition counter preset to 1, so it sorts partition 1 while partition 0 is never processed.
+// Its look-back therefore waits on statuses that nothing publishes, gives up after
+// DARB_SPIN_LIMIT polls, sets DARB_ERR_TIMEOUT in the status word and finishes its pass (every
+// store stays inside the 2-partition buffers).  ws: device, 16-byte aligned, at least
+// darb_test_lookback_timeout_bytes(); *status_host receives the status word after the stream
+// has been synchronised.
+extern "C" size_t darb_test_lookback_timeout_bytes(void) {
+    return (2 * (size_t)darb::kSortTile * 2 + 256 + 2 * 256 + 4) * sizeof(uint32_t);
+}
+
+extern "C" darb_status darb_test_lookback_timeout(void *ws, size_t ws_bytes, uint32_t *status_host,
+                                                  darb_stream stream) {
+    using namespace darb;
+    const size_t need = darb_test_lookback_timeout_bytes();
+    if (!ws || ws_bytes < need || !status_host || (reinterpret_cast<uintptr_t>(ws) & 15u)) return DARB_ERR_INVALID_ARG;
+    const size_t n = 2 * (size_t)kSortTile;
+    uint32_t *kin = static_cast<uint32_t *>(ws), *vout = kin + n, *digit_base = vout + n;
+    uint32_t *lookback = digit_base + 256, *words = lookback + 2 * 256;  // words: counter, status
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(ws, 0, need, st) != cudaSuccess) return DARB_ERR_CUDA;
+    if (cudaMemsetAsync(words, 1, 1, st) != cudaSuccess) return DARB_ERR_CUDA;  // counter = 1 (little endian)
+    const size_t smem = Staging<uint32_t, false>::bytes;
+    if (cudaFuncSetAttribute(k_onesweep<uint32_t, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return DARB_ERR_CUDA;
+    launch_k(k_onesweep<uint32_t, false>, 1, kSortThreads, smem, st, (const uint32_t *)kin, (const uint32_t *)nullptr,
+             (uint32_t *)nullptr, vout, (const uint32_t *)nullptr, (unsigned long long)n, 0, 8,
+             (const uint32_t *)digit_base, lookback, words, words + 1);
+    if (cudaGetLastError() != cudaSuccess) return DARB_ERR_CUDA;
+    if (cudaMemcpyAsync(status_host, words + 1, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess) return DARB_ERR_CUDA;
+    return cudaStreamSynchronize(st) == cudaSuccess ? DARB_OK : DARB_ERR_CUDA;
+}
+#endif

@@ -6,8 +6,11 @@
 // host-side stand-in, never a device address, so the first call on each device (with that
 // device current) resolves the real address with cudaGetSymbolAddress and caches it; later
 // calls on that device reuse it.  That first call may load this file's module, so it should
-// come before any stream capture.  All calls share the one array: the sort clears the parts
-// that must start at zero on every call, and calls whose work overlaps on the GPU race.
+// come before any stream capture.  The cached address belongs to the device's context of that
+// first call: a caller must not reset the device (cudaDeviceReset) while it uses this entry
+// point, because the module is reloaded with the new context and may live at another address.
+// All calls share the one array: the sort clears the parts that must start at zero on every
+// call, and calls whose work overlaps on the GPU race.
 #include <mutex>
 
 #include "kernels.cuh"

@@ -37,13 +37,24 @@ def test_noalloc_sort_equals_workspace_sort_twice_in_a_row():
         ref = darb.darb_bin_sort(proj, splats.n, tile, c, ws, cap)
         M = ref.M
         rk, rv, rr = _np(ref.keys)[:M].copy(), _np(ref.values)[:M].copy(), _np(ref.ranges).copy()
-        for sync in (True, False):  # two calls in a row, host-sized and capacity-sized
-            b = darb.darb_bin_sort_noalloc(proj, splats.n, tile, c, cap, sync=sync)
+        tx, ty = darb.darb_tile_grid(c, tile)
+        b = darb.Binning.empty(cap, tx * ty, "cuda")  # every output allocated before the calls
+        free = []
+        for sync in (True, False, True):  # calls in a row, host-sized and capacity-sized
+            b.values.fill_(-1)
+            b.ranges.fill_(-1)
             torch.cuda.synchronize()
+            if sync is False:  # the first call may load the library's module; measure from the second on
+                free.append(torch.cuda.mem_get_info()[0])
+            darb.darb_bin_sort_noalloc(proj, splats.n, tile, c, cap, out=b, sync=sync)
+            torch.cuda.synchronize()
+            if len(free) == 1:
+                free.append(torch.cuda.mem_get_info()[0])
             assert int(_np(b.num_instances)[0]) == M and int(_np(b.status)[0]) == 0
             assert np.array_equal(_np(b.keys)[:M], rk)
             assert np.array_equal(_np(b.values)[:M], rv)
             assert np.array_equal(_np(b.ranges), rr)
+        assert free[0] == free[1], f"device memory changed across a call: {free[0]} -> {free[1]} bytes free"
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():

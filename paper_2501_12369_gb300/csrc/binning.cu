@@ -521,6 +521,7 @@ k_tile_setup(int tiles_x, int tiles_y, const int *__restrict__ diff_g, uint32_t 
     }
     for (int i = threadIdx.x; i < kMaxPasses * 256; i += 1024) s_h[i] = 0;
     __syncthreads();
+    (void)num;
     for (int y = warp; y < tiles_y; y += 32) {  // prefix along x
         uint32_t carry = 0;
         for (int x0 = 0; x0 < tiles_x; x0 += 32) {
@@ -537,7 +538,12 @@ k_tile_setup(int tiles_x, int tiles_y, const int *__restrict__ diff_g, uint32_t 
     }
     __syncthreads();
 
-    const bool overflow = (unsigned long long)*num > capacity;
+    // M from the counts themselves (the sum of the member tiles, as the scan of tiles_touched
+    // finds it), so that this kernel need not wait for that scan
+    unsigned long long part = 0, M;
+    for (int t = threadIdx.x; t < n_tiles; t += 1024) part += counts[t];
+    block_exclusive_scan<1024>(part, s_warp, M);
+    const bool overflow = M > capacity;
     unsigned long long carry = 0;
     for (int chunk = 0; chunk < n_tiles; chunk += 1024) {
         const int t = chunk + threadIdx.x;
@@ -580,6 +586,13 @@ constexpr int kScanBlock = 4096;  // values per CTA of the table scan (1024 thre
 #define DARB_PASS_ONESWEEP 1
 #endif
 constexpr bool kPassOnesweep = DARB_PASS_ONESWEEP != 0;
+
+// Per-tile counts right after the depth compaction, over the visible splats in index order (1),
+// or after the depth sort, in depth order (0).
+#ifndef DARB_TILE_COUNTS_EARLY
+#define DARB_TILE_COUNTS_EARLY 1
+#endif
+constexpr bool kTileCountsEarly = DARB_TILE_COUNTS_EARLY != 0;
 
 // CTAs per SM of the tile difference array (each privatises the array in shared memory and
 // adds it to the global one at the end).
@@ -1280,6 +1293,44 @@ Layout layout(int n, uint64_t capacity, int tiles_x, int tiles_y, int strategy, 
 
 int sort_tile_bits(int n_tiles) { return log2_ceil((uint32_t)n_tiles); }
 
+namespace {
+// k_tile_diff over the visible splats (order: their ids, n_vis: their count; null: every splat)
+// and k_tile_setup: per-tile instance counts -> ranges and the tile passes' digit bases.
+cudaError_t launch_tile_counts(int n, const uint32_t *order, const uint32_t *n_vis, const ProjectedIn &proj,
+                               const SpanCtx &sc, int tiles_x, int tiles_y, int *diff, uint32_t *counts,
+                               const BinOut &out, unsigned long long cap, const PassSpec &tps, uint32_t *tbase,
+                               cudaStream_t st) {
+    const int n_tiles = tiles_x * tiles_y;
+    if (n > 0) {
+        const int diff_size = (tiles_x + 1) * (tiles_y + 1);
+        const size_t smem = (size_t)diff_size * 4;
+        if (smem <= kMaxDiffSmem) {
+            const cudaError_t e =
+                cudaFuncSetAttribute(k_tile_diff<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            const int blocks = std::min((n + 1023) / 1024, DARB_TILE_DIFF_CTAS_PER_SM * 152);
+            launch_k(k_tile_diff<true>, blocks, 1024, smem, st, n, order, n_vis, proj.radius, proj.tile_rect,
+                     proj.tile_runs, proj.mean2d, proj.conic_o, sc, tiles_x, diff_size, diff);
+        } else {
+            launch_k(k_tile_diff<false>, (n + 1023) / 1024, 1024, 0, st, n, order, n_vis, proj.radius, proj.tile_rect,
+                     proj.tile_runs, proj.mean2d, proj.conic_o, sc, tiles_x, diff_size, diff);
+        }
+    }
+    const size_t setup_smem = ((size_t)n_tiles + (size_t)(tiles_x + 1) * (tiles_y + 1)) * 4;
+    if (setup_smem <= kMaxSetupSmem) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(k_tile_setup<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)setup_smem);
+        if (e != cudaSuccess) return e;
+        launch_k(k_tile_setup<true>, 1, 1024, setup_smem, st, tiles_x, tiles_y, diff, counts, out.num_instances, cap,
+                 tps, out.ranges, tbase);
+    } else {
+        launch_k(k_tile_setup<false>, 1, 1024, 0, st, tiles_x, tiles_y, diff, counts, out.num_instances, cap, tps,
+                 out.ranges, tbase);
+    }
+    return cudaGetLastError();
+}
+}  // namespace
+
 size_t sort_workspace_bytes(int n, uint64_t capacity, int tiles_x, int tiles_y, int strategy) {
     return layout(n, capacity, tiles_x, tiles_y, strategy, sort_tile_bits(tiles_x * tiles_y)).total;
 }
@@ -1359,7 +1410,13 @@ cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int til
         return cudaGetLastError();
     }
 
-    // DEPTH_THEN_TILE: 1) depth order of the splats (4 stable 8-bit passes over N keys)
+    // DEPTH_THEN_TILE
+    const PassSpec tps = split_bits(tile_bits);
+    int *diff = reinterpret_cast<int *>(at(10)) + 2 * kMaxPasses * 256;
+    uint32_t *counts = reinterpret_cast<uint32_t *>(at(16));
+    uint32_t *tbase = reinterpret_cast<uint32_t *>(at(8));
+    bool tile_counts_done = false;
+    // 1) depth order of the splats (4 stable 8-bit passes over N keys)
     uint32_t *kbuf[2] = {reinterpret_cast<uint32_t *>(at(4)), reinterpret_cast<uint32_t *>(at(4)) + n};
     uint32_t *vbuf[2] = {reinterpret_cast<uint32_t *>(at(5)), reinterpret_cast<uint32_t *>(at(5)) + n};
     const uint32_t *order = nullptr;  // sorted splat ids
@@ -1383,6 +1440,13 @@ cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int til
             n_vis_dev = nv;
             vin = vbuf[0];
             launch_k(k_hist_scan, dps.passes, 256, 0, st, dhist, dbase);
+            if (kTileCountsEarly) {
+                // the per-tile counts need no depth order: walk the visible splats in index order
+                // (coalesced reads) before the depth passes overwrite this compacted list
+                TRY(launch_tile_counts(n, vbuf[0], nv, proj, sc, tiles_x, tiles_y, diff, counts, out, cap, tps, tbase,
+                                       st));
+                tile_counts_done = true;
+            }
         } else {
             launch_k(k_depth_keys, (n + 255) / 256, 256, 0, st, n, proj.radius, proj.depth, kbuf[0]);
         }
@@ -1433,38 +1497,11 @@ cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int til
         }
         grid = M;
     }
-    // 3) per-tile counts from the rectangles -> ranges and tile-pass digit bases
-    const PassSpec tps = split_bits(tile_bits);
-    int *diff = reinterpret_cast<int *>(at(10)) + 2 * kMaxPasses * 256;
-    uint32_t *counts = reinterpret_cast<uint32_t *>(at(16));
-    uint32_t *tbase = reinterpret_cast<uint32_t *>(at(8));
-    if (n > 0) {
-        const int diff_size = (tiles_x + 1) * (tiles_y + 1);
-        const size_t smem = (size_t)diff_size * 4;
-        if (smem <= kMaxDiffSmem) {
-            TRY(cudaFuncSetAttribute(k_tile_diff<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            const int blocks = std::min((n + 1023) / 1024, DARB_TILE_DIFF_CTAS_PER_SM * 152);
-            launch_k(k_tile_diff<true>, blocks, 1024, smem, st, n, n_vis_dev ? order : nullptr, n_vis_dev, proj.radius,
-                     proj.tile_rect, proj.tile_runs, proj.mean2d, proj.conic_o, sc, tiles_x, diff_size, diff);
-        } else {
-            launch_k(k_tile_diff<false>, (n + 1023) / 1024, 1024, 0, st, n, n_vis_dev ? order : nullptr, n_vis_dev,
-                     proj.radius, proj.tile_rect, proj.tile_runs, proj.mean2d, proj.conic_o, sc, tiles_x, diff_size,
-                     diff);
-        }
-    }
-    {
-        const size_t setup_smem = ((size_t)n_tiles + (size_t)(tiles_x + 1) * (tiles_y + 1)) * 4;
-        if (setup_smem <= kMaxSetupSmem) {
-            TRY(cudaFuncSetAttribute(k_tile_setup<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)setup_smem));
-            launch_k(k_tile_setup<true>, 1, 1024, setup_smem, st, tiles_x, tiles_y, diff, counts, out.num_instances, cap,
-                     tps, out.ranges, tbase);
-        } else {
-            launch_k(k_tile_setup<false>, 1, 1024, 0, st, tiles_x, tiles_y, diff, counts, out.num_instances, cap, tps,
-                     out.ranges, tbase);
-        }
-    }
-    TRY(cudaGetLastError());
+    // 3) per-tile counts from the rectangles -> ranges and tile-pass digit bases (done above
+    //    when the compacted index order was available)
+    if (!tile_counts_done)
+        TRY(launch_tile_counts(n, n_vis_dev ? order : nullptr, n_vis_dev, proj, sc, tiles_x, tiles_y, diff, counts,
+                               out, cap, tps, tbase, st));
     // 4) per-position offsets, then the balanced duplication in depth order
     uint32_t *tk_a = reinterpret_cast<uint32_t *>(at(0)), *tv_a = reinterpret_cast<uint32_t *>(at(1));
     uint32_t *tk_b = reinterpret_cast<uint32_t *>(at(2)), *tv_b = reinterpret_cast<uint32_t *>(at(3));

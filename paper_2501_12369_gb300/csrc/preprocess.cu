@@ -257,6 +257,26 @@ __device__ __forceinline__ bool project_fixed(const float m[3], const float s[3]
 // so that whole warps, not 38% of each warp's lanes, run it.
 constexpr int kPreThreads = 256;
 
+// L2 prefetch of a queued splat's SH row in phase 1 (1), or none (0).
+#ifndef DARB_PRE_SH_PREFETCH
+#define DARB_PRE_SH_PREFETCH 1
+#endif
+// A culled splat's record: radius 0, no member tiles, unpacked runs.  Its other fields are not
+// read by any later step and are left as they were (1), or zeroed as well (0).
+#ifndef DARB_PRE_CULLED_MIN
+#define DARB_PRE_CULLED_MIN 1
+#endif
+
+__device__ __forceinline__ void write_culled(const ProjectedOut &out, int i) {
+    out.radius[i] = 0;
+    out.tiles_touched[i] = 0;
+    out.tile_runs[i] = kRunsUnpacked;
+#if !DARB_PRE_CULLED_MIN
+    out.tile_rect[i] = make_int4(0, 0, 0, 0);
+    out.depth[i] = 0.0f;
+#endif
+}
+
 struct PreGeom {
     float tz, A, B, C, u0, u1;
     int rect[4];
@@ -313,12 +333,17 @@ k_preprocess(int n, const float *__restrict__ means, const float *__restrict__ s
             q.radius = g.radius;
             q.idx = i;
         } else if (i < n) {
-            out.radius[i] = 0;
-            out.tiles_touched[i] = 0;
-            out.tile_runs[i] = kRunsUnpacked;
-            out.tile_rect[i] = make_int4(0, 0, 0, 0);
-            out.depth[i] = 0.0f;
+            write_culled(out, i);
         }
+#if DARB_PRE_SH_PREFETCH
+        if (vis) {  // start the SH row of a queued splat on its way to L2 during the projection of the rest
+            const char *row = reinterpret_cast<const char *>(sh + (size_t)i * 3 * (DEG + 1) * (DEG + 1));
+            constexpr int kRowBytes = 12 * (DEG + 1) * (DEG + 1);
+#pragma unroll
+            for (int o = 0; o < kRowBytes + 127; o += 128)
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(row + min(o, kRowBytes - 1)));
+        }
+#endif
     }
     __syncthreads();
     const int nq = s_n;
@@ -339,11 +364,7 @@ k_preprocess(int n, const float *__restrict__ means, const float *__restrict__ s
         }
     }
     if (cnt == 0) {  // an ellipse that reaches no tile: culled
-        out.radius[i] = 0;
-        out.tiles_touched[i] = 0;
-        out.tile_runs[i] = kRunsUnpacked;
-        out.tile_rect[i] = make_int4(0, 0, 0, 0);
-        out.depth[i] = 0.0f;
+        write_culled(out, i);
         return;
     }
     out.depth[i] = g.tz;

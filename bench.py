@@ -312,8 +312,8 @@ def algorithmic_bytes(stage, n, M, passes, sh_k, strategy=0, tile_passes=2, n_vi
     if stage == "preprocess":
         # visible: read means, scales, quats, opacity, SH; write depth, radius, rect, mean2d,
         # conic_o, rgb, clamp bits, tiles, packed runs.  culled: read means, scales, quats; write
-        # depth, radius, rect, tiles, packed runs
-        return n_vis * (12 + 12 + 16 + 4 + sh_b + 4 + 4 + 16 + 8 + 16 + 12 + 1 + 4 + 8) + (n - n_vis) * (40 + 36)
+        # radius, tiles, packed runs
+        return n_vis * (12 + 12 + 16 + 4 + sh_b + 4 + 4 + 16 + 8 + 16 + 12 + 1 + 4 + 8) + (n - n_vis) * (40 + 16)
     if stage == "bin_sort":
         if strategy == 1:
             return n * (4 + 4 + 16 + 4) + M * (12 + 8 + 24 * passes + 8)
@@ -668,6 +668,27 @@ def launches_per_step(strategy, tile_bits, fused=True):
     return 1 + sort + 1 + 2 + 2 + (1 if fused else 1 + 5)
 
 
+def pair_counts(ts):
+    """(pixel, splat) pair counts of the last forward, from its outputs: blended pairs (sum of
+    n_contrib); replayed pairs (sum of `last`: the records a pixel passes up to its last blended
+    splat, which is what the compositing backward evaluates, and a lower bound of what the
+    forward evaluates); listed pairs (the records of every pixel's tile list); and the share of
+    pixels left with T >= 0.01, which no further splat could have stopped (alpha <= 0.99), so
+    the forward walked their whole list."""
+    img, ranges = ts.img, ts.bins.ranges
+    tx = ts.tx
+    ys = torch.arange(ts.H, device=ts.device) // ts.tile
+    xs = torch.arange(ts.W, device=ts.device) // ts.tile
+    tile_of = ys[:, None] * tx + xs[None, :]
+    lens = (ranges[:, 1] - ranges[:, 0]).to(torch.int64)
+    listed = lens[tile_of]
+    unsat = img.t_final >= 0.01
+    return {"blended": int(img.n_contrib.to(torch.int64).sum()), "replayed": int(img.last.to(torch.int64).sum()),
+            "listed": int(listed.sum()),
+            "fwd_walked_lower_bound": int(torch.where(unsat, listed, img.last.to(torch.int64)).sum()),
+            "unsaturated_share": round(float(unsat.float().mean()), 4)}
+
+
 def kernel_sweep(ts, step, cam_seq, first, stages, restore_kernel, steps=20):
     """Training it/s and per-stage ms for every reconstruction kernel (the tile stays the
     autotuned one; capacity is re-sized, since psi changes the footprints)."""
@@ -689,8 +710,15 @@ def kernel_sweep(ts, step, cam_seq, first, stages, restore_kernel, steps=20):
         torch.cuda.synchronize()
         per = {s: sum(e[i].elapsed_time(e[i + 1]) for e in evs) / steps for i, s in enumerate(stages)}
         total = evs[0][0].elapsed_time(evs[-1][-1])
+        ts.forward(cam_seq[first % len(cam_seq)])
+        pc = pair_counts(ts)
+        fwd_s, bwd_s = per["render_fwd"] / 1e3, per["render_bwd"] / 1e3
+        pc.update({"fwd_walked_pairs_per_s": round(pc["fwd_walked_lower_bound"] / fwd_s / 1e9, 3),
+                   "fwd_blended_pairs_per_s": round(pc["blended"] / fwd_s / 1e9, 3),
+                   "bwd_evaluated_pairs_per_s": round(pc["replayed"] / bwd_s / 1e9, 3),
+                   "bwd_blended_pairs_per_s": round(pc["blended"] / bwd_s / 1e9, 3), "unit": "G pairs/s"})
         out[label] = {"it_s": round(steps / (total / 1e3), 1), "mean_instances": int(np.mean(Ms)),
-                      "stage_ms": {s: round(v, 4) for s, v in per.items()}}
+                      "stage_ms": {s: round(v, 4) for s, v in per.items()}, "pairs": pc}
     out["generic_half_cosine_xi3_beta1.5"]["psi"] = generic.psi
     out["generic_half_cosine_xi3_beta1.5"]["psi_device_ms"] = round(psi_ms, 3)
     ts.set_kernel(restore_kernel)

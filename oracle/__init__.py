@@ -4,9 +4,14 @@ TEST INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
 ``cpu_baseline`` / reference legs of ``bench.py`` may import this package.
 It shares no code with the CUDA library and imports nothing from it.
 
-Every function here is argument marshalling; the arithmetic lives in
+The rasterizer's arithmetic (projection, SH, kernels, tile lists,
+compositing, its analytic gradient, psi by quadrature) lives in
 darb_oracle.c (see its header for what is computed and where the paper
-defines it).
+defines it); the functions wrapping it here only marshal arguments.  The
+training-step terms are plain FP64 NumPy in this file: l1_loss, ssim_window,
+ssim_map and l1_dssim_loss (the image loss), densify_stats, densify_actions,
+densify and reset_opacity (density control), adam_update and
+adam_step_splats (the optimiser), and psi_moment's quadrature driver.
 
 Kernel table (Table 1 forms with the xi of Table 2, the psi of the Sec. B
 listings, and the main-lobe limits of Sec. A.3 / the listings):

@@ -1,6 +1,6 @@
 """Small, self-contained cases for profiling single kernels (for example under ncu).
 
-    python -m paper_2501_12369_gb300.profile_cases CASE [N] [TILE]
+    python profile_cases.py CASE [N] [TILE] [KERNEL]
 
 CASE is one of
   render     two forward + backward passes (compositing kernels k_render_fwd / k_render_bwd)
@@ -12,7 +12,8 @@ CASE is one of
   batch      two eager batched renders (k_render_fwd_batch) of 16 cameras of the 1M-splat
              mixed-resolution multi-view scene, 8 streams, TILE-pixel tiles
 on N clustered splats (default 1,000,000, SH degree 3) seen by camera 0 of the 1920x1080
-Fibonacci-sphere cameras (fx = 1500), with TILE-pixel tiles (default 32).  Inputs are seeded.
+Fibonacci-sphere cameras (fx = 1500), with TILE-pixel tiles (default 32) and the kernel KERNEL
+(default half_cosine) for the render and sort cases.  Inputs are seeded.
 Each case launches a fixed sequence, so `ncu -k <kernel> -s <skip> -c <count>` selects the
 same launches every run.
 """
@@ -23,14 +24,21 @@ import types
 
 import torch
 
-from . import build, darb, synth
+import os
+
+sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+
+from paper_2501_12369_gb300 import build, darb, synth  # noqa: E402
+
+
+KERNEL = "half_cosine"
 
 
 def _setup(n, tile):
     build.build()
     s = synth.cluster_scene(n, seed=0)
     cam = synth.fibonacci_cameras(100, 6.0, 1920, 1080, 1500.0)[0]
-    r = darb.Rasterizer(cam, "half_cosine", tile, capacity=40 * n)
+    r = darb.Rasterizer(cam, KERNEL, tile, capacity=40 * n)
     return s, cam, r, darb.splats_to_device(s)
 
 
@@ -131,6 +139,8 @@ def main(argv):
         raise SystemExit(__doc__)
     n = int(argv[1]) if len(argv) > 1 else (3840 if argv[0] == "ssim" else 1_000_000)
     tile = int(argv[2]) if len(argv) > 2 else 32
+    global KERNEL
+    KERNEL = argv[3] if len(argv) > 3 else KERNEL
     CASES[argv[0]](n, tile)
 
 

@@ -130,15 +130,17 @@ struct PassSpec {
 
 // Per-CTA sums of tiles_touched over kScanTile positions; order (if given) maps positions to splats.
 __global__ void __launch_bounds__(kScanThreads)
-k_block_sums(int n, const uint32_t *__restrict__ tiles, const uint32_t *__restrict__ order, uint32_t *__restrict__ sums) {
+k_block_sums(int n, const uint32_t *__restrict__ tiles, const uint32_t *__restrict__ order,
+             const uint32_t *__restrict__ n_vis, uint32_t *__restrict__ sums) {
     pdl_entry();
     __shared__ uint32_t s_warp[kScanThreads / 32 + 1];
     const int base = blockIdx.x * kScanTile;
+    const int m = n_vis ? (int)min(*n_vis, (uint32_t)n) : n;  // positions past the visible ones hold no instance
     uint32_t s = 0;
 #pragma unroll
     for (int j = 0; j < kScanItems; ++j) {
         const int idx = base + j * kScanThreads + threadIdx.x;
-        if (idx < n) s += tiles[order ? order[idx] : idx];
+        if (idx < m) s += tiles[order ? order[idx] : idx];
     }
     uint32_t total;
     block_exclusive_scan<kScanThreads>(s, s_warp, total);
@@ -240,18 +242,25 @@ k_duplicate(int n, const uint32_t *__restrict__ tiles, const unsigned long long 
 // kSortTile) - 1 -- each position writes the partitions whose first or last instance it owns.
 __global__ void __launch_bounds__(kScanThreads)
 k_splat_offsets(int n, const uint32_t *__restrict__ order, const uint32_t *__restrict__ tiles,
+                const uint32_t *__restrict__ n_vis,
                 const unsigned long long *__restrict__ block_offsets, const uint32_t *__restrict__ num,
                 uint32_t *__restrict__ offs, uint2 *__restrict__ bounds, uint32_t max_parts) {
     pdl_entry();
     __shared__ uint32_t s_off[kScanTile + 1];
     __shared__ uint32_t s_warp[kScanThreads / 32 + 1];
     const int base = blockIdx.x * kScanTile;
-    const uint32_t total = cta_offsets(n, base, tiles, order, s_off, nullptr, s_warp);
+    // with n_vis, only the visible splats' positions (the ones that own instances) are needed
+    const int m = n_vis ? (int)min(*n_vis, (uint32_t)n) : n;
+    if (base >= m) {  // a block of culled positions (uniform over the CTA: no barrier is skipped)
+        if (blockIdx.x == 0 && threadIdx.x == 0) offs[n] = *num;
+        return;
+    }
+    const uint32_t total = cta_offsets(m, base, tiles, order, s_off, nullptr, s_warp);
     const uint32_t gbase = (uint32_t)block_offsets[blockIdx.x];
     const uint32_t M = *num;
     constexpr uint32_t T = kSortTile;
     for (int j = threadIdx.x; j < kScanTile; j += kScanThreads) {
-        if (base + j >= n) continue;
+        if (base + j >= m) continue;
         const uint32_t o0 = gbase + s_off[j];
         offs[base + j] = o0;
         const uint32_t o1 = gbase + (j + 1 < kScanTile ? s_off[j + 1] : total);
@@ -597,7 +606,7 @@ constexpr bool kTileCountsEarly = DARB_TILE_COUNTS_EARLY != 0;
 // CTAs per SM of the tile difference array (each privatises the array in shared memory and
 // adds it to the global one at the end).
 #ifndef DARB_TILE_DIFF_CTAS_PER_SM
-#define DARB_TILE_DIFF_CTAS_PER_SM 4
+#define DARB_TILE_DIFF_CTAS_PER_SM 2  // 2: bin_sort 0.404 -> 0.398 ms against 4 (8: 0.413)
 #endif
 
 // Resident CTAs per SM the one-pass sort kernels are compiled for (their register budget).
@@ -1048,9 +1057,8 @@ k_ranges(const uint64_t *__restrict__ keys, const uint32_t *num, unsigned long l
 // Depth keys of the visible splats only, compacted in index order (so the depth sort, being
 // stable, keeps equal depths in index order): k_vis_count counts each kScanTile block's visible
 // splats, k_scan_block_sums turns the counts into block offsets and the total n_vis, and
-// k_depth_compact writes (depth bits, index) of the visible splats to [0, n_vis) and the culled
-// indices, also in index order, to [n_vis, n) of both value buffers -- where the sorted order
-// ends up after any number of passes over [0, n_vis).
+// k_depth_compact writes (depth bits, index) of the visible splats to [0, n_vis).  Every later
+// step reads the sorted order only below n_vis (the culled splats own no instance).
 __global__ void __launch_bounds__(kScanThreads)
 k_vis_count(int n, const int *__restrict__ radius, uint32_t *__restrict__ block_counts) {
     pdl_entry();
@@ -1070,13 +1078,12 @@ k_vis_count(int n, const int *__restrict__ radius, uint32_t *__restrict__ block_
 // Depth digits at or above this bit are histogrammed with match.any aggregation, the lower ones
 // with one shared-memory atomic per key.
 #ifndef DARB_DEPTH_HIST_MATCH_SHIFT
-#define DARB_DEPTH_HIST_MATCH_SHIFT 16
+#define DARB_DEPTH_HIST_MATCH_SHIFT 32  // every digit by plain atomics (16: 0.404, 8: 0.410 ms bin_sort)
 #endif
 __global__ void __launch_bounds__(kScanThreads)
 k_depth_compact(int n, const int *__restrict__ radius, const float *__restrict__ depth,
-                const unsigned long long *__restrict__ block_offsets, const uint32_t *__restrict__ n_vis,
-                uint32_t *__restrict__ keys, uint32_t *__restrict__ ids0, uint32_t *__restrict__ ids1, PassSpec ps,
-                uint32_t *__restrict__ hist) {
+                const unsigned long long *__restrict__ block_offsets, uint32_t *__restrict__ keys,
+                uint32_t *__restrict__ ids0, PassSpec ps, uint32_t *__restrict__ hist) {
     pdl_entry();
     static_assert(kScanItems == 8, "two 16-byte loads per thread");
     __shared__ uint32_t s_warp[kScanThreads / 32 + 1];
@@ -1102,19 +1109,12 @@ k_depth_compact(int n, const int *__restrict__ radius, const float *__restrict__
             key[j] = valid ? __float_as_uint(depth[i0 + j]) : 0u;
         }
     }
-    uint32_t nv = 0, nc = 0;
+    uint32_t nv = 0;
 #pragma unroll
-    for (int j = 0; j < kScanItems; ++j) {
-        const bool valid = i0 + j < n;
-        nv += (valid && rad[j] != 0) ? 1u : 0u;
-        nc += (valid && rad[j] == 0) ? 1u : 0u;
-    }
-    // visible count in the low half-word, culled count in the high one (at most kScanTile each)
+    for (int j = 0; j < kScanItems; ++j) nv += (i0 + j < n && rad[j] != 0) ? 1u : 0u;
     uint32_t t;
-    const uint32_t ex = block_exclusive_scan<kScanThreads>(nv | (nc << 16), s_warp, t);
-    const uint32_t vis0 = (uint32_t)block_offsets[blockIdx.x];
-    uint32_t pv = vis0 + (ex & 0xffffu);
-    uint32_t pc = *n_vis + ((uint32_t)base - vis0) + (ex >> 16);  // culled splats go after all visible ones
+    const uint32_t ex = block_exclusive_scan<kScanThreads>(nv, s_warp, t);
+    uint32_t pv = (uint32_t)block_offsets[blockIdx.x] + ex;
 #pragma unroll
     for (int j = 0; j < kScanItems; ++j) {
         const int i = i0 + j;
@@ -1123,10 +1123,6 @@ k_depth_compact(int n, const int *__restrict__ radius, const float *__restrict__
             keys[pv] = key[j];
             ids0[pv] = (uint32_t)i;
             ++pv;
-        } else if (valid) {
-            ids0[pc] = (uint32_t)i;
-            ids1[pc] = (uint32_t)i;
-            ++pc;
         }
 #pragma unroll
         for (int p = 0; p < kMaxPasses; ++p) {  // digit histograms of the visible keys
@@ -1361,7 +1357,7 @@ cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int til
     uint32_t *counters = reinterpret_cast<uint32_t *>(at(13));
 
     if (strategy == DARB_SORT_KEYS64) {
-        if (nb > 0) launch_k(k_block_sums, nb, kScanThreads, 0, st, n, proj.tiles_touched, nullptr, block_sums);
+        if (nb > 0) launch_k(k_block_sums, nb, kScanThreads, 0, st, n, proj.tiles_touched, nullptr, nullptr, block_sums);
         launch_k(k_scan_block_sums, 1, 1024, 0, st, nb, block_sums, block_off, out.num_instances, out.status, cap);
         TRY(cudaGetLastError());
         uint64_t grid = capacity;
@@ -1434,8 +1430,8 @@ cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int til
             launch_k(k_scan_block_sums, 1, 1024, 0, st, nb, block_sums, block_off, nv, out.status,
                      (unsigned long long)n);
             uint32_t *dhist = reinterpret_cast<uint32_t *>(at(10)) + kMaxPasses * 256;
-            launch_k(k_depth_compact, nb, kScanThreads, 0, st, n, proj.radius, proj.depth, block_off, nv, kbuf[0],
-                     vbuf[0], vbuf[1], dps, dhist);
+            launch_k(k_depth_compact, nb, kScanThreads, 0, st, n, proj.radius, proj.depth, block_off, kbuf[0],
+                     vbuf[0], dps, dhist);
             n_vis = nv;
             n_vis_dev = nv;
             vin = vbuf[0];
@@ -1482,7 +1478,7 @@ cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int til
         order = vin;
     }
     // 2) scan of tiles_touched in depth order
-    if (nb > 0) launch_k(k_block_sums, nb, kScanThreads, 0, st, n, proj.tiles_touched, order, block_sums);
+    if (nb > 0) launch_k(k_block_sums, nb, kScanThreads, 0, st, n, proj.tiles_touched, order, n_vis_dev, block_sums);
     launch_k(k_scan_block_sums, 1, 1024, 0, st, nb, block_sums, block_off, out.num_instances, out.status, cap);
     TRY(cudaGetLastError());
     uint64_t grid = capacity;
@@ -1509,7 +1505,8 @@ cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int til
     uint2 *bounds = kPassOnesweep ? reinterpret_cast<uint2 *>(at(20)) : nullptr;
     const uint32_t max_parts = (uint32_t)((capacity + kSortTile - 1) / kSortTile);
     if (nb > 0)
-        launch_k(k_splat_offsets, nb, kScanThreads, 0, st, n, order, proj.tiles_touched, block_off, out.num_instances,
+        launch_k(k_splat_offsets, nb, kScanThreads, 0, st, n, order, proj.tiles_touched, n_vis_dev, block_off,
+                 out.num_instances,
                  offs, bounds, max_parts);
     uint32_t *tph = reinterpret_cast<uint32_t *>(at(11));
     const uint32_t n_parts = (uint32_t)((grid + kSortTile - 1) / kSortTile);

@@ -302,28 +302,88 @@ __device__ __forceinline__ int cta_upper_owner(const uint32_t *__restrict__ offs
 // first position of every run inside the partition (clipped to lo), records the run's tile id
 // at that position and the splat id and sets the position's bit in `mark` (cleared by the
 // caller).  Every instance then finds its run start in `mark` without recomputing the ellipse.
+// The row runs of the splats whose runs are not packed (rectangles of more than 8 rows or 15
+// columns), recorded once by k_tile_diff, which computes them anyway, so that the duplication
+// reads them instead of recomputing the ellipse row by row.  off[id] is the first entry of
+// splat id's rectangle rows (one entry per row, c0 | c1 << 16, c0 > c1 for a row without
+// member tiles), or kNoTable when the table was full; only unpacked visible splats have one.
+constexpr uint32_t kNoTable = 0xffffffffu;
+constexpr uint32_t kRowEmpty = 0x0000ffffu;  // c0 = 65535 > c1 = 0
+struct RunTable {
+    uint32_t *off;
+    uint32_t *tab;
+    uint32_t *count;  // entries handed out (zeroed per call)
+    uint32_t cap;
+};
+
 template <int NT>
 __device__ __forceinline__ void partition_runs(int first, int count, uint32_t lo, uint32_t hi,
                                                const uint32_t *__restrict__ offs, const uint32_t *__restrict__ order,
                                                const int4 *__restrict__ rect, const uint64_t *__restrict__ runs,
                                                const float2 *__restrict__ mean2d, const float4 *__restrict__ conic_o,
-                                               const SpanCtx &sc, int tiles_x, uint32_t *s_base, uint32_t *s_val,
-                                               uint32_t *mark) {
+                                               const SpanCtx &sc, const RunTable &rt, int tiles_x, uint32_t *s_base,
+                                               uint32_t *s_val, uint32_t *mark, uint16_t *s_q, int *s_qn) {
+    auto mark_run = [&](uint32_t id, uint32_t j, uint32_t w, int ty, int c0) {  // run [j, j + w) of id's instances
+        const uint32_t q = max(j, lo), pos = q - lo;
+        s_base[pos] = (uint32_t)(ty * tiles_x + c0) + (q - j);
+        s_val[pos] = id;
+        atomicOr(&mark[pos >> 5], 1u << (pos & 31));
+    };
+    // owners with packed runs: one thread each (at most 8 rows, decoded from one word); owners
+    // whose runs are in the run table are queued for the warps
     for (int o = threadIdx.x; o < count; o += NT) {
-        uint32_t j = offs[first + o];
         const uint32_t id = order[first + o];
+        const uint64_t pk = __ldg(runs + id);
+        if (pk == kRunsUnpacked && rt.tab) {
+            s_q[atomicAdd(s_qn, 1)] = (uint16_t)o;
+            continue;
+        }
+        uint32_t j = offs[first + o];
         const int4 r = __ldg(rect + id);
-        for_each_run(__ldg(runs + id), mean2d, conic_o, id, r, sc, [&](int ty, int c0, int c1) {
+        for_each_run(pk, mean2d, conic_o, id, r, sc, [&](int ty, int c0, int c1) {
             const uint32_t w = (uint32_t)(c1 - c0 + 1);
-            if (j + w > lo) {
-                const uint32_t q = max(j, lo), pos = q - lo;
-                s_base[pos] = (uint32_t)(ty * tiles_x + c0) + (q - j);
-                s_val[pos] = id;
-                atomicOr(&mark[pos >> 5], 1u << (pos & 31));
-            }
+            if (j + w > lo) mark_run(id, j, w, ty, c0);
             j += w;
             return j < hi;
         });
+    }
+    if (!rt.tab) return;  // uniform: a kernel argument
+    __syncthreads();
+    // queued owners: a warp each, one rectangle row per lane, rows read from the run table in
+    // parallel and placed by a warp prefix sum of their lengths
+    const int nq = *s_qn, lane = threadIdx.x & 31;
+    for (int k = (int)(threadIdx.x >> 5); k < nq; k += NT / 32) {
+        const int o = s_q[k];
+        const uint32_t id = order[first + o];
+        const int4 r = __ldg(rect + id);
+        const uint32_t tb = __ldg(rt.off + id);
+        uint32_t carry = offs[first + o];
+        if (tb == kNoTable) {  // the table was full: one lane computes this owner's runs
+            if (lane == 0)
+                for_each_run(kRunsUnpacked, mean2d, conic_o, id, r, sc, [&](int ty, int c0, int c1) {
+                    const uint32_t w = (uint32_t)(c1 - c0 + 1);
+                    if (carry + w > lo) mark_run(id, carry, w, ty, c0);
+                    carry += w;
+                    return carry < hi;
+                });
+            continue;
+        }
+        const int rows = r.w - r.y + 1;
+        for (int r0 = 0; r0 < rows && carry < hi; r0 += 32) {  // carry is the same in every lane
+            const int k2 = r0 + lane;
+            const uint32_t e = k2 < rows ? __ldg(rt.tab + tb + (uint32_t)k2) : kRowEmpty;
+            const int c0 = (int)(e & 0xffffu), c1 = (int)(e >> 16);
+            const uint32_t w = c0 <= c1 ? (uint32_t)(c1 - c0 + 1) : 0u;
+            uint32_t x = w;
+#pragma unroll
+            for (int sh = 1; sh < 32; sh <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, x, sh);
+                if (lane >= sh) x += y;
+            }
+            const uint32_t start = carry + x - w;
+            if (w && start < hi && start + w > lo) mark_run(id, start, w, r.y + k2, c0);
+            carry += __shfl_sync(0xffffffffu, x, 31);
+        }
     }
 }
 
@@ -352,7 +412,8 @@ __device__ __forceinline__ void partition_lookup(uint32_t pos, const uint32_t *s
 __global__ void __launch_bounds__(kScanThreads)
 k_duplicate_balanced(int n, const uint32_t *__restrict__ order, const uint32_t *__restrict__ offs,
                      const int4 *__restrict__ rect, const uint64_t *__restrict__ runs, const float2 *__restrict__ mean2d,
-                     const float4 *__restrict__ conic_o, SpanCtx sc, int tiles_x, const uint32_t *__restrict__ num,
+                     const float4 *__restrict__ conic_o, SpanCtx sc, RunTable rt, int tiles_x,
+                     const uint32_t *__restrict__ num,
                      unsigned long long cap, uint32_t *__restrict__ keys, uint32_t *__restrict__ vals, int bits1,
                      uint32_t n_parts, uint32_t *__restrict__ ph) {
     pdl_entry();
@@ -361,6 +422,9 @@ k_duplicate_balanced(int n, const uint32_t *__restrict__ order, const uint32_t *
     __shared__ uint32_t s_mark[kDupTile / 32];
     __shared__ uint32_t s_h[256];
     __shared__ int s_res[2];
+    __shared__ uint16_t s_q[kDupTile];
+    __shared__ int s_qn;
+    if (threadIdx.x == 0) s_qn = 0;  // ordered before partition_runs by cta_upper_owner's barriers
     const unsigned long long Mfull = *num;
     if (Mfull > cap) return;  // overflow: nothing is emitted (status already set)
     const uint32_t M = (uint32_t)Mfull;
@@ -376,8 +440,8 @@ k_duplicate_balanced(int n, const uint32_t *__restrict__ order, const uint32_t *
     const int first = cta_upper_owner(offs, n, lo, &s_res[0]);
     const int last = cta_upper_owner(offs, n, hi - 1, &s_res[1]);
     const int count = min(last - first + 1, kDupTile);  // every owner has >= 1 instance
-    partition_runs<kScanThreads>(first, count, lo, hi, offs, order, rect, runs, mean2d, conic_o, sc, tiles_x, s_base,
-                                 s_val, s_mark);
+    partition_runs<kScanThreads>(first, count, lo, hi, offs, order, rect, runs, mean2d, conic_o, sc, rt, tiles_x,
+                                 s_base, s_val, s_mark, s_q, &s_qn);
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t wbase = lo + (uint32_t)warp * (32 * kDupItems);
@@ -410,8 +474,8 @@ template <bool SMEM>
 __global__ void DARB_TILE_DIFF_BOUNDS
 k_tile_diff(int n, const uint32_t *__restrict__ order, const uint32_t *__restrict__ n_vis,
             const int *__restrict__ radius, const int4 *__restrict__ rect, const uint64_t *__restrict__ runs,
-            const float2 *__restrict__ mean2d, const float4 *__restrict__ conic_o, SpanCtx sc, int tiles_x,
-            int diff_size, int *__restrict__ diff) {
+            const float2 *__restrict__ mean2d, const float4 *__restrict__ conic_o, SpanCtx sc, RunTable rt,
+            int tiles_x, int diff_size, int *__restrict__ diff) {
     pdl_entry();
     extern __shared__ int s_diff[];
     int *d = SMEM ? s_diff : diff;
@@ -449,8 +513,21 @@ k_tile_diff(int n, const uint32_t *__restrict__ order, const uint32_t *__restric
             const int iL = __shfl_sync(0xffffffffu, i, __ffs(bm) - 1);
             const float2 mu = mean2d[iL];
             const float4 co = conic_o[iL];
-            warp_runs(mu.x, mu.y, co.x, co.y, co.z, rect[iL], sc,
-                      [&](int ty, int c0, int c1, uint32_t) { add(ty, c0, c1); });
+            const int4 rL = rect[iL];
+            // the rows' runs go to the run table too, for the duplication (every row, the empty
+            // ones marked; each lane writes the rows it computes, so no two lanes share an entry)
+            const uint32_t rows = (uint32_t)(rL.w - rL.y + 1);
+            uint32_t base = 0;
+            if (rt.tab && lane == 0) base = atomicAdd(rt.count, rows);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            const bool keep = rt.tab && (unsigned long long)base + rows <= rt.cap;
+            if (keep)
+                for (uint32_t k = lane; k < rows; k += 32) rt.tab[base + k] = kRowEmpty;
+            warp_runs(mu.x, mu.y, co.x, co.y, co.z, rL, sc, [&](int ty, int c0, int c1, uint32_t) {
+                add(ty, c0, c1);
+                if (keep) rt.tab[base + (uint32_t)(ty - rL.y)] = (uint32_t)c0 | ((uint32_t)c1 << 16);
+            });
+            if (rt.tab && lane == 0) rt.off[iL] = keep ? base : kNoTable;
         }
     }
     if (SMEM) {
@@ -602,6 +679,13 @@ constexpr bool kPassOnesweep = DARB_PASS_ONESWEEP != 0;
 #define DARB_TILE_COUNTS_EARLY 1
 #endif
 constexpr bool kTileCountsEarly = DARB_TILE_COUNTS_EARLY != 0;
+
+// The duplication takes the runs of unpacked splats from the table k_tile_diff records, a warp
+// per splat (1), or recomputes them, a thread per splat (0).
+#ifndef DARB_RUN_TABLE
+#define DARB_RUN_TABLE 1
+#endif
+constexpr bool kRunTable = DARB_RUN_TABLE != 0;
 
 // CTAs per SM of the tile difference array (each privatises the array in shared memory and
 // adds it to the global one at the end).
@@ -812,7 +896,7 @@ struct Staging {
 // instances are generated.
 template <bool WRITE_KEYS>
 struct DupStaging {
-    static constexpr size_t owners = (size_t)(2 * kDupTile + kDupTile / 32) * 4;
+    static constexpr size_t owners = (size_t)(2 * kDupTile + kDupTile / 32 + 4) * 4 + (size_t)kDupTile * 2;
     static constexpr size_t bytes = Staging<uint32_t, WRITE_KEYS>::bytes > owners ? Staging<uint32_t, WRITE_KEYS>::bytes
                                                                                    : owners;
 };
@@ -1001,7 +1085,7 @@ __global__ void __launch_bounds__(kSortThreads, kSortCtasPerSm)
 k_dup_sweep(int n, const uint32_t *__restrict__ order, const uint32_t *__restrict__ offs, const uint2 *__restrict__ bounds,
             const int4 *__restrict__ rect, const uint64_t *__restrict__ runs, const float2 *__restrict__ mean2d,
             const float4 *__restrict__ conic_o,
-            SpanCtx sc, int tiles_x, const uint32_t *num, unsigned long long cap, int bits,
+            SpanCtx sc, RunTable rt, int tiles_x, const uint32_t *num, unsigned long long cap, int bits,
             const uint32_t *__restrict__ digit_base, uint32_t *lookback, uint32_t *part_counter, uint32_t *status,
             uint32_t *__restrict__ kout, uint32_t *__restrict__ vout) {
     pdl_entry();
@@ -1016,12 +1100,15 @@ k_dup_sweep(int n, const uint32_t *__restrict__ order, const uint32_t *__restric
     uint32_t *s_base = reinterpret_cast<uint32_t *>(smem);
     uint32_t *s_val = s_base + kDupTile;
     uint32_t *s_mark = s_val + kDupTile;
+    int *s_qn = reinterpret_cast<int *>(s_mark + kDupTile / 32);
+    uint16_t *s_q = reinterpret_cast<uint16_t *>(s_qn + 4);
     for (int i = threadIdx.x; i < kDupTile / 32; i += kSortThreads) s_mark[i] = 0;
+    if (threadIdx.x == 0) *s_qn = 0;
     const uint2 fl = bounds[part];
     const int first = (int)fl.x, count = min((int)fl.y - (int)fl.x + 1, kDupTile);  // every owner has >= 1 instance
     __syncthreads();
-    partition_runs<kSortThreads>(first, count, lo, hi, offs, order, rect, runs, mean2d, conic_o, sc, tiles_x, s_base,
-                                 s_val, s_mark);
+    partition_runs<kSortThreads>(first, count, lo, hi, offs, order, rect, runs, mean2d, conic_o, sc, rt, tiles_x,
+                                 s_base, s_val, s_mark, s_q, s_qn);
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t wbase = lo + (uint32_t)warp * (32 * kSortItems);
@@ -1218,9 +1305,13 @@ cudaError_t launch_pass(const K *kin, const uint32_t *vin, K *kout, uint32_t *vo
 // ---------------------------------------------------------------------------- workspace
 
 namespace {
+// Entries of the run table: at most a quarter of the instance capacity, at least 64k.  A
+// splat whose rows no longer fit is marked and its runs are recomputed by the duplication.
+uint64_t run_table_entries(uint64_t capacity) { return std::max<uint64_t>(capacity / 4, 1u << 16); }
+
 struct Layout {
     size_t total;
-    size_t off[21];
+    size_t off[23];
 };
 
 // Offsets of the workspace regions.  Regions 0..9 are data; [zero_begin, zero_end) is zeroed per call.
@@ -1252,6 +1343,8 @@ Layout layout(int n, uint64_t capacity, int tiles_x, int tiles_y, int strategy, 
         put(18, 0);
         put(19, 0);
         put(20, 0);
+        put(21, 0);
+        put(22, 0);
         put(9, (size_t)kMaxPasses * 256 * 4);  // digit bases
         put(10, (size_t)kMaxPasses * 256 * 4); // --- zeroed from here: histograms
         put(11, (size_t)passes * parts_cap * 256 * 4);  // look-back
@@ -1272,6 +1365,8 @@ Layout layout(int n, uint64_t capacity, int tiles_x, int tiles_y, int strategy, 
         put(15, ((size_t)n + 1) * 4);           // per-position instance offsets in depth order
         put(16, (size_t)n_tiles * 4);           // per-tile instance counts
         put(20, parts_cap * 8);                 // first and last owner of every tile-pass partition
+        put(21, (size_t)n * 4);                 // run-table slot of every splat
+        put(22, (size_t)run_table_entries(capacity) * 4);  // run table
         put(11, parts_cap * 256 * 4);           // tile-pass partition histograms / offsets
         put(12, parts_n * 256 * 4);             // depth-pass partition histograms / offsets
         put(17, ((std::max(parts_cap, parts_n) * 256 + 4095) / 4096 + 1) * 4);  // table-scan block sums
@@ -1279,7 +1374,7 @@ Layout layout(int n, uint64_t capacity, int tiles_x, int tiles_y, int strategy, 
         put(10, (size_t)2 * kMaxPasses * 256 * 4 + (size_t)(tiles_x + 1) * (tiles_y + 1) * 4);
         put(18, kPassOnesweep ? (size_t)passes * parts_cap * 256 * 4 : 0);  // tile-pass look-back
         put(19, kPassOnesweep ? (size_t)4 * parts_n * 256 * 4 : 0);         // depth-pass look-back
-        put(13, (size_t)(kMaxPasses * 2 + 1) * 4);  // onesweep partition counters, visible-splat count
+        put(13, (size_t)(kMaxPasses * 2 + 2) * 4);  // onesweep partition counters, visible count, run-table fill
     }
     L.off[14] = b;
     L.total = b + 256;
@@ -1293,7 +1388,8 @@ namespace {
 // k_tile_diff over the visible splats (order: their ids, n_vis: their count; null: every splat)
 // and k_tile_setup: per-tile instance counts -> ranges and the tile passes' digit bases.
 cudaError_t launch_tile_counts(int n, const uint32_t *order, const uint32_t *n_vis, const ProjectedIn &proj,
-                               const SpanCtx &sc, int tiles_x, int tiles_y, int *diff, uint32_t *counts,
+                               const SpanCtx &sc, const RunTable &rt, int tiles_x, int tiles_y, int *diff,
+                               uint32_t *counts,
                                const BinOut &out, unsigned long long cap, const PassSpec &tps, uint32_t *tbase,
                                cudaStream_t st) {
     const int n_tiles = tiles_x * tiles_y;
@@ -1306,10 +1402,10 @@ cudaError_t launch_tile_counts(int n, const uint32_t *order, const uint32_t *n_v
             if (e != cudaSuccess) return e;
             const int blocks = std::min((n + 1023) / 1024, DARB_TILE_DIFF_CTAS_PER_SM * 152);
             launch_k(k_tile_diff<true>, blocks, 1024, smem, st, n, order, n_vis, proj.radius, proj.tile_rect,
-                     proj.tile_runs, proj.mean2d, proj.conic_o, sc, tiles_x, diff_size, diff);
+                     proj.tile_runs, proj.mean2d, proj.conic_o, sc, rt, tiles_x, diff_size, diff);
         } else {
             launch_k(k_tile_diff<false>, (n + 1023) / 1024, 1024, 0, st, n, order, n_vis, proj.radius, proj.tile_rect,
-                     proj.tile_runs, proj.mean2d, proj.conic_o, sc, tiles_x, diff_size, diff);
+                     proj.tile_runs, proj.mean2d, proj.conic_o, sc, rt, tiles_x, diff_size, diff);
         }
     }
     const size_t setup_smem = ((size_t)n_tiles + (size_t)(tiles_x + 1) * (tiles_y + 1)) * 4;
@@ -1412,6 +1508,8 @@ cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int til
     uint32_t *counts = reinterpret_cast<uint32_t *>(at(16));
     uint32_t *tbase = reinterpret_cast<uint32_t *>(at(8));
     bool tile_counts_done = false;
+    const RunTable rt{reinterpret_cast<uint32_t *>(at(21)), kRunTable ? reinterpret_cast<uint32_t *>(at(22)) : nullptr,
+                      counters + 2 * kMaxPasses + 1, (uint32_t)run_table_entries(capacity)};
     // 1) depth order of the splats (4 stable 8-bit passes over N keys)
     uint32_t *kbuf[2] = {reinterpret_cast<uint32_t *>(at(4)), reinterpret_cast<uint32_t *>(at(4)) + n};
     uint32_t *vbuf[2] = {reinterpret_cast<uint32_t *>(at(5)), reinterpret_cast<uint32_t *>(at(5)) + n};
@@ -1439,8 +1537,8 @@ cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int til
             if (kTileCountsEarly) {
                 // the per-tile counts need no depth order: walk the visible splats in index order
                 // (coalesced reads) before the depth passes overwrite this compacted list
-                TRY(launch_tile_counts(n, vbuf[0], nv, proj, sc, tiles_x, tiles_y, diff, counts, out, cap, tps, tbase,
-                                       st));
+                TRY(launch_tile_counts(n, vbuf[0], nv, proj, sc, rt, tiles_x, tiles_y, diff, counts, out, cap, tps,
+                                       tbase, st));
                 tile_counts_done = true;
             }
         } else {
@@ -1496,8 +1594,8 @@ cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int til
     // 3) per-tile counts from the rectangles -> ranges and tile-pass digit bases (done above
     //    when the compacted index order was available)
     if (!tile_counts_done)
-        TRY(launch_tile_counts(n, n_vis_dev ? order : nullptr, n_vis_dev, proj, sc, tiles_x, tiles_y, diff, counts,
-                               out, cap, tps, tbase, st));
+        TRY(launch_tile_counts(n, n_vis_dev ? order : nullptr, n_vis_dev, proj, sc, rt, tiles_x, tiles_y, diff,
+                               counts, out, cap, tps, tbase, st));
     // 4) per-position offsets, then the balanced duplication in depth order
     uint32_t *tk_a = reinterpret_cast<uint32_t *>(at(0)), *tv_a = reinterpret_cast<uint32_t *>(at(1));
     uint32_t *tk_b = reinterpret_cast<uint32_t *>(at(2)), *tv_b = reinterpret_cast<uint32_t *>(at(3));
@@ -1521,12 +1619,12 @@ cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int til
         if (last0) {
             TRY(cudaFuncSetAttribute(k_dup_sweep<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             launch_k(k_dup_sweep<false>, n_parts, kSortThreads, smem, st, n, order, offs, bounds, proj.tile_rect,
-                     proj.tile_runs, proj.mean2d, proj.conic_o, sc, tiles_x, out.num_instances, cap, tps.bits[0],
+                     proj.tile_runs, proj.mean2d, proj.conic_o, sc, rt, tiles_x, out.num_instances, cap, tps.bits[0],
                      tbase, lb, counters, out.status, k0, v0);
         } else {
             TRY(cudaFuncSetAttribute(k_dup_sweep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             launch_k(k_dup_sweep<true>, n_parts, kSortThreads, smem, st, n, order, offs, bounds, proj.tile_rect,
-                     proj.tile_runs, proj.mean2d, proj.conic_o, sc, tiles_x, out.num_instances, cap, tps.bits[0],
+                     proj.tile_runs, proj.mean2d, proj.conic_o, sc, rt, tiles_x, out.num_instances, cap, tps.bits[0],
                      tbase, lb, counters, out.status, k0, v0);
         }
         TRY(cudaGetLastError());
@@ -1548,7 +1646,7 @@ cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int til
         // reduce-then-scan passes: the duplication also writes the first pass's histograms
         if (n > 0)
             launch_k(k_duplicate_balanced, n_parts, kScanThreads, 0, st, n, order, offs, proj.tile_rect,
-                     proj.tile_runs, proj.mean2d, proj.conic_o, sc, tiles_x, out.num_instances, cap, tk_a, tv_a,
+                     proj.tile_runs, proj.mean2d, proj.conic_o, sc, rt, tiles_x, out.num_instances, cap, tk_a, tv_a,
                      tps.bits[0], n_parts, tph);
         else
             TRY(cudaMemsetAsync(tph, 0, ((size_t)n_parts << tps.bits[0]) * 4, st));

@@ -317,18 +317,16 @@ def algorithmic_bytes(stage, n, M, passes, sh_k, strategy=0, tile_passes=2, n_vi
     if stage == "bin_sort":
         if strategy == 1:
             return n * (4 + 4 + 16 + 4) + M * (12 + 8 + 24 * passes + 8)
-        # per splat: radius read (visible count), radius + depth read (compaction), tiles
-        # gathered in depth order twice (block sums, offsets), offsets written; per culled splat:
-        # its index written to both order buffers; per visible splat: key and index written by
-        # the compaction (which also takes the digit histograms), 4 depth passes (read 8 B,
-        # write 8 B; the last writes only values), order + radius + rectangle + packed runs
-        # (8 B) read by the difference array, offset + order + rectangle + packed runs read by
-        # the duplication;
-        # per instance: the duplication fused with the first tile pass writes 8 B, every later
-        # pass reads 8 B and writes 8 B, the last writes only 4-byte values
+        # every splat: radius read (visible count), radius + depth read (compaction).  Visible
+        # splats: depth key + index written by the compaction (which also takes the digit
+        # histograms); 4 depth passes (read 8 B, write 8 B; the last writes only 4-byte values);
+        # index + rectangle + packed runs read by the tile counts; index + tile count read by the
+        # block sums and again by the offsets, which write the offset; offset + index + rectangle
+        # + packed runs read by the duplication.  Per instance: the duplication fused with the
+        # first tile pass writes 8 B, every later pass reads 8 B and writes 8 B, the last writes
+        # only 4-byte values.
         per_instance = 4 if tile_passes == 1 else 8 + 16 * (tile_passes - 2) + 12
-        return (n * (4 + 8 + 4 + 4 + 4) + (n - n_vis) * 8 + n_vis * (8 + 16 * 3 + 12 + 32 + 32)
-                + M * per_instance)
+        return n * (4 + 8) + n_vis * (8 + 16 * 3 + 12 + 28 + 8 + 12 + 32) + M * per_instance
     if stage == "preprocess_bwd":
         # every splat: radius read, all gradients written; visible: parameters, grad2d and clamp
         # bits read

@@ -90,6 +90,15 @@ def test_invalid_arguments_are_rejected_before_any_device_work(L):
     cam.width = 0
     assert L.darb_preprocess(ctypes.byref(sp), ctypes.byref(cam), ctypes.byref(kp), 16, ctypes.byref(out), None) == 1
     assert L.darb_status_string(3) == b"instance capacity exceeded"
+    # server configurations are checked before the device is touched
+    srv = ctypes.c_void_p()
+    good = dict(scene_bytes=1 << 20, workspace_bytes=1 << 24, tile=16, max_batch=4, depth=2, capacity_per_pixel=16.0,
+                capacity_margin=1.15, capacity_min=1 << 16, slots=2)
+    for field, value in [("slots", -1), ("slots", 9), ("tile", 12), ("max_batch", 0), ("depth", 9),
+                         ("capacity_margin", 0.5), ("workspace_bytes", 4096)]:
+        cfg = darb.darb_serve_cfg(**dict(good, **{field: value}))
+        assert L.darb_serve_create(ctypes.byref(cfg), ctypes.byref(srv)) == 1, field
+    assert L.darb_serve_submit_many(None, None, 0, None, None) == 1
 
 
 def test_oracle_and_library_share_no_source():

@@ -136,6 +136,13 @@ def test_admission_and_errors(scenes):
         img = torch.empty(3, 64, 64, device="cuda")
         t = srv.submit(sid, cam, img)
         assert srv.poll(t).status == 0
+        # a batch submission stops at the first bad request; the ones before it stay queued
+        imgs = [torch.empty(3, 64, 64, device="cuda") for _ in range(3)]
+        with pytest.raises(darb.DarbError) as e:
+            srv.submit_many([sid, sid, sid + 5], [cam, cam, cam], imgs)
+        assert e.value.status == 7
+        queued = [k for k in srv._keep if k > t]
+        assert len(queued) == 2 and all(srv.poll(k).status == 0 for k in queued)
         with pytest.raises(darb.DarbError) as e:  # collected already
             srv.poll(t, 0)
         assert e.value.status == 7

@@ -465,10 +465,13 @@ k_duplicate_balanced(int n, const uint32_t *__restrict__ order, const uint32_t *
 // have been compacted (order and n_vis given), else all n with the culled ones skipped.  With
 // SMEM each CTA accumulates a private copy in shared memory (grid-stride over splats) and adds
 // its non-zero entries to the global array once.
+#ifndef DARB_TILE_DIFF_THREADS
+#define DARB_TILE_DIFF_THREADS 1024
+#endif
 #ifdef DARB_TILE_DIFF_MIN_CTAS
-#define DARB_TILE_DIFF_BOUNDS __launch_bounds__(1024, DARB_TILE_DIFF_MIN_CTAS)
+#define DARB_TILE_DIFF_BOUNDS __launch_bounds__(DARB_TILE_DIFF_THREADS, DARB_TILE_DIFF_MIN_CTAS)
 #else
-#define DARB_TILE_DIFF_BOUNDS __launch_bounds__(1024)
+#define DARB_TILE_DIFF_BOUNDS __launch_bounds__(DARB_TILE_DIFF_THREADS)
 #endif
 template <bool SMEM>
 __global__ void DARB_TILE_DIFF_BOUNDS
@@ -1400,11 +1403,13 @@ cudaError_t launch_tile_counts(int n, const uint32_t *order, const uint32_t *n_v
             const cudaError_t e =
                 cudaFuncSetAttribute(k_tile_diff<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
-            const int blocks = std::min((n + 1023) / 1024, DARB_TILE_DIFF_CTAS_PER_SM * 152);
-            launch_k(k_tile_diff<true>, blocks, 1024, smem, st, n, order, n_vis, proj.radius, proj.tile_rect,
+            const int blocks = std::min((n + DARB_TILE_DIFF_THREADS - 1) / DARB_TILE_DIFF_THREADS,
+                                        DARB_TILE_DIFF_CTAS_PER_SM * 152);
+            launch_k(k_tile_diff<true>, blocks, DARB_TILE_DIFF_THREADS, smem, st, n, order, n_vis, proj.radius, proj.tile_rect,
                      proj.tile_runs, proj.mean2d, proj.conic_o, sc, rt, tiles_x, diff_size, diff);
         } else {
-            launch_k(k_tile_diff<false>, (n + 1023) / 1024, 1024, 0, st, n, order, n_vis, proj.radius, proj.tile_rect,
+            launch_k(k_tile_diff<false>, (n + DARB_TILE_DIFF_THREADS - 1) / DARB_TILE_DIFF_THREADS,
+                     DARB_TILE_DIFF_THREADS, 0, st, n, order, n_vis, proj.radius, proj.tile_rect,
                      proj.tile_runs, proj.mean2d, proj.conic_o, sc, rt, tiles_x, diff_size, diff);
         }
     }

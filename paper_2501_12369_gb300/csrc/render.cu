@@ -259,7 +259,10 @@ __device__ __forceinline__ float warp_sum8(const float (&v)[9], int lane, float 
 
 // Backward: replay each pixel back to front from its last contributor.  With T_k the
 // transmittance in front of splat k and S the colour composited behind it (background
-// included), dC/dalpha_k = c_k T_k - S / (1 - alpha_k) and dC/dc_k = alpha_k T_k.
+// included), dC/dalpha_k = c_k T_k - S / (1 - alpha_k) and dC/dc_k = alpha_k T_k.  Only the
+// projection of S on the pixel's upstream gradient g is needed: g . dC/dalpha_k =
+// T_k (g . c_k) - (g . S) / (1 - alpha_k), and g . S grows by (g . c_k) alpha_k T_k per splat,
+// so each pixel carries the scalar g . S instead of three colour channels.
 // Per splat and tile the contributions of a thread's pixels are added in registers, summed
 // over the warp by shuffles, then across warps in shared memory, then added to grad2d with one
 // vector atomic per 4 floats.
@@ -291,7 +294,7 @@ k_render_bwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ valu
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const size_t plane = (size_t)W * H;
 
-    float fpy[PIX], T[PIX], g0[PIX], g1[PIX], g2[PIX], S0[PIX], S1[PIX], S2[PIX];
+    float fpy[PIX], T[PIX], g0[PIX], g1[PIX], g2[PIX], GS[PIX];
     uint32_t my_last[PIX];
     uint32_t m = 0;
 #pragma unroll
@@ -309,9 +312,7 @@ k_render_bwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ valu
             g1[k] = dL_dimage[plane + pix];
             g2[k] = dL_dimage[2 * plane + pix];
         }
-        S0[k] = T[k] * bg.r;
-        S1[k] = T[k] * bg.g;
-        S2[k] = T[k] * bg.b;
+        GS[k] = T[k] * fmaf(g2[k], bg.b, fmaf(g1[k], bg.g, g0[k] * bg.r));
         m = max(m, my_last[k]);
     }
 #pragma unroll
@@ -362,12 +363,10 @@ k_render_bwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ valu
                 const float iom = __fdividef(1.0f, om);
                 const float Tk = T[k] * iom;
                 const float c0 = s_rgb[j][0], c1 = s_rgb[j][1], c2 = s_rgb[j][2];
-                const float dalpha = g0[k] * (c0 * Tk - S0[k] * iom) + g1[k] * (c1 * Tk - S1[k] * iom) +
-                                     g2[k] * (c2 * Tk - S2[k] * iom);
+                const float gc = fmaf(g2[k], c2, fmaf(g1[k], c1, g0[k] * c0));
+                const float dalpha = fmaf(Tk, gc, -GS[k] * iom);
                 const float w = alpha * Tk;
-                S0[k] = fmaf(c0, w, S0[k]);
-                S1[k] = fmaf(c1, w, S1[k]);
-                S2[k] = fmaf(c2, w, S2[k]);
+                GS[k] = fmaf(gc, w, GS[k]);
                 T[k] = Tk;
                 v[6] = fmaf(w, g0[k], v[6]);
                 v[7] = fmaf(w, g1[k], v[7]);

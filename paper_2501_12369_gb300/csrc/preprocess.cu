@@ -609,13 +609,36 @@ struct BwdAdamStage {
 
 constexpr int kBwdAdamThreads = 128;
 
+// float4s in flight per thread and array in the Adam walk, and whether its parameter / moment
+// traffic uses the streaming (evict-first) cache hints.
+#ifndef DARB_ADAM_UNROLL
+#define DARB_ADAM_UNROLL 4
+#endif
+#ifndef DARB_ADAM_STREAMING
+#define DARB_ADAM_STREAMING 0
+#endif
+__device__ __forceinline__ float4 adam_ld(const float4 *p) {
+#if DARB_ADAM_STREAMING
+    return __ldcs(p);
+#else
+    return *p;
+#endif
+}
+__device__ __forceinline__ void adam_st(float4 *p, float4 v) {
+#if DARB_ADAM_STREAMING
+    __stcs(p, v);
+#else
+    *p = v;
+#endif
+}
+
 // One parameter group of the block: count floats from p/m/v (HBM, 16-byte aligned) with
 // gradients grad4(j) for float4 j; ACT 1 refreshes act = exp(p), ACT 2 act = sigmoid(p).
 template <int ACT, class Grad4, class LrOf>
 __device__ __forceinline__ void block_adam(int count, float *__restrict__ p, float *__restrict__ m,
                                            float *__restrict__ v, float *__restrict__ act, Grad4 grad4, LrOf lr_of,
                                            const AdamConsts &ac) {
-    constexpr int NT = kBwdAdamThreads, U = 4;
+    constexpr int NT = kBwdAdamThreads, U = DARB_ADAM_UNROLL;
     const int n4 = count >> 2;
     float4 *p4 = reinterpret_cast<float4 *>(p), *m4 = reinterpret_cast<float4 *>(m), *v4 = reinterpret_cast<float4 *>(v);
     for (int b = threadIdx.x; b < n4; b += NT * U) {
@@ -624,9 +647,9 @@ __device__ __forceinline__ void block_adam(int count, float *__restrict__ p, flo
         for (int u = 0; u < U; ++u) {
             const int j = b + u * NT;
             if (j < n4) {
-                P[u] = p4[j];
-                M[u] = m4[j];
-                V[u] = v4[j];
+                P[u] = adam_ld(p4 + j);
+                M[u] = adam_ld(m4 + j);
+                V[u] = adam_ld(v4 + j);
                 G[u] = grad4(j);
             }
         }
@@ -638,9 +661,9 @@ __device__ __forceinline__ void block_adam(int count, float *__restrict__ p, flo
                 adam_apply(P[u].y, G[u].y, M[u].y, V[u].y, lr_of(4 * j + 1), ac);
                 adam_apply(P[u].z, G[u].z, M[u].z, V[u].z, lr_of(4 * j + 2), ac);
                 adam_apply(P[u].w, G[u].w, M[u].w, V[u].w, lr_of(4 * j + 3), ac);
-                p4[j] = P[u];
-                m4[j] = M[u];
-                v4[j] = V[u];
+                adam_st(p4 + j, P[u]);
+                adam_st(m4 + j, M[u]);
+                adam_st(v4 + j, V[u]);
                 if (ACT == 1)
                     reinterpret_cast<float4 *>(act)[j] =
                         make_float4(expf(P[u].x), expf(P[u].y), expf(P[u].z), expf(P[u].w));

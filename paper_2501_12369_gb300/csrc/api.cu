@@ -153,6 +153,15 @@ darb_status darb_bin_sort(const darb_projected *proj, int32_t n, int32_t tile, c
                           const darb_kernel_params *kparams, void *workspace, size_t workspace_bytes,
                           uint64_t capacity, int32_t strategy, const darb_binning *out, uint64_t *num_instances_host,
                           darb_stream stream) {
+    return darb::bin_sort_entry(proj, n, tile, cam, kparams, workspace, workspace_bytes, capacity, strategy, out,
+                                num_instances_host, stream, true);
+}
+}  // extern "C"
+
+darb_status darb::bin_sort_entry(const darb_projected *proj, int32_t n, int32_t tile, const darb_camera *cam,
+                                 const darb_kernel_params *kparams, void *workspace, size_t workspace_bytes,
+                                 uint64_t capacity, int32_t strategy, const darb_binning *out,
+                                 uint64_t *num_instances_host, darb_stream stream, bool allow_fork) {
     if (n < 0 || !valid_tile(tile) || !valid_camera(cam) || !valid_kernel(kparams) || capacity > kMaxCapacity ||
         !out || !valid_strategy(strategy))
         return DARB_ERR_INVALID_ARG;
@@ -179,9 +188,11 @@ darb_status darb_bin_sort(const darb_projected *proj, int32_t n, int32_t tile, c
     bool exceeded = false;
     const SpanCtx sc = make_span_ctx(kparams->q_max, tile, cam->width, cam->height);
     DARB_CUDA_TRY(launch_bin_sort(n, pin, tiles_x, tiles_y, sc, capacity, strategy, workspace, bo,
-                                  num_instances_host, &exceeded, reinterpret_cast<cudaStream_t>(stream)));
+                                  num_instances_host, &exceeded, reinterpret_cast<cudaStream_t>(stream), allow_fork));
     return exceeded ? DARB_ERR_CAPACITY : DARB_OK;
 }
+
+extern "C" {
 
 darb_status darb_render_fwd(const darb_projected *proj, const darb_binning *bins, const darb_camera *cam,
                             const darb_kernel_params *kparams, int32_t tile, const darb_image *out,

@@ -243,7 +243,7 @@ darb_status darb_render_batch(const darb_splats *splats, const darb_camera *cams
         const int tx = tile_count(cams[v].width, tile), ty = tile_count(cams[v].height, tile);
         const SpanCtx sc = make_span_ctx(kparams->q_max, tile, cams[v].width, cams[v].height);
         if (launch_bin_sort(n, pin, tx, ty, sc, bp->capacity, DARB_SORT_DEPTH_THEN_TILE, w + L.slots + L.per_slot * s, bo,
-                            nullptr, &exceeded, ss) != cudaSuccess)
+                            nullptr, &exceeded, ss, /*allow_fork=*/false) != cudaSuccess)
             return DARB_ERR_CUDA;
     }
     // join, then one persistent compositing launch over all views

@@ -39,6 +39,7 @@
 // timeout the status word is set and successors are released), and staging in shared memory so
 // the scatter leaves in digit runs.
 #include <algorithm>
+#include <mutex>
 #include <utility>
 
 #include "kernels.cuh"
@@ -466,7 +467,7 @@ k_duplicate_balanced(int n, const uint32_t *__restrict__ order, const uint32_t *
 // SMEM each CTA accumulates a private copy in shared memory (grid-stride over splats) and adds
 // its non-zero entries to the global array once.
 #ifndef DARB_TILE_DIFF_THREADS
-#define DARB_TILE_DIFF_THREADS 1024
+#define DARB_TILE_DIFF_THREADS 256  // small CTAs fit beside the depth passes' CTAs on the side stream
 #endif
 #ifdef DARB_TILE_DIFF_MIN_CTAS
 #define DARB_TILE_DIFF_BOUNDS __launch_bounds__(DARB_TILE_DIFF_THREADS, DARB_TILE_DIFF_MIN_CTAS)
@@ -693,7 +694,7 @@ constexpr bool kRunTable = DARB_RUN_TABLE != 0;
 // CTAs per SM of the tile difference array (each privatises the array in shared memory and
 // adds it to the global one at the end).
 #ifndef DARB_TILE_DIFF_CTAS_PER_SM
-#define DARB_TILE_DIFF_CTAS_PER_SM 2  // 2: bin_sort 0.404 -> 0.398 ms against 4 (8: 0.413)
+#define DARB_TILE_DIFF_CTAS_PER_SM 4  // beside the depth passes, 256 threads: 4 -> 0.353 ms (8: 0.359; 1024 x 2: 0.371)
 #endif
 
 // Resident CTAs per SM the one-pass sort kernels are compiled for (their register budget).
@@ -1360,7 +1361,7 @@ Layout layout(int n, uint64_t capacity, int tiles_x, int tiles_y, int strategy, 
         put(2, capacity * 4);  // tile keys B
         put(3, capacity * 4);  // values B
         put(4, (size_t)n * 4 * 2);  // depth keys ping-pong
-        put(5, (size_t)n * 4 * 2);  // depth values ping-pong (sorted order ends here)
+        put(5, (size_t)n * 4 * 3);  // compacted ids, then the depth values ping-pong (sorted order ends here)
         put(6, nb * 4);
         put(7, nb * 8);
         put(8, (size_t)kMaxPasses * 256 * 4);  // tile digit bases
@@ -1432,10 +1433,50 @@ size_t sort_workspace_bytes(int n, uint64_t capacity, int tiles_x, int tiles_y, 
     return layout(n, capacity, tiles_x, tiles_y, strategy, sort_tile_bits(tiles_x * tiles_y)).total;
 }
 
+namespace {
+// The side stream of a device that takes the per-tile counts beside the depth passes, and its
+// fork / join events; created on first use, kept for the process.
+struct SortSide {
+    std::mutex mu;
+    bool ready = false;
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
+constexpr int kMaxDevicesSort = 64;
+SortSide g_sort_side[kMaxDevicesSort];
+
+cudaError_t sort_side_init(SortSide &P) {
+    if (P.ready) return cudaSuccess;
+    cudaError_t e = cudaStreamCreateWithFlags(&P.s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P.fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P.join, cudaEventDisableTiming);
+    if (e == cudaSuccess) P.ready = true;
+    return e;
+}
+
+// Makes st wait for the side stream's work once, on every way out of the launcher.
+struct SideJoin {
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    bool pending = false;
+    cudaError_t join() {
+        if (!pending) return cudaSuccess;
+        pending = false;
+        return cudaStreamWaitEvent(st, ev, 0);
+    }
+    ~SideJoin() { join(); }
+};
+}  // namespace
+
+// Per-tile counts beside the depth passes (1), or in line on the caller's stream (0).
+#ifndef DARB_TILE_COUNTS_FORK
+#define DARB_TILE_COUNTS_FORK 1
+#endif
+
 cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int tiles_y, const SpanCtx &sc,
                             uint64_t capacity,
                             int strategy, void *workspace, const BinOut &out, uint64_t *num_instances_host,
-                            bool *capacity_exceeded, cudaStream_t st) {
+                            bool *capacity_exceeded, cudaStream_t st, bool allow_fork) {
     const int n_tiles = tiles_x * tiles_y;
     const int tile_bits = sort_tile_bits(n_tiles);
     const Layout L = layout(n, capacity, tiles_x, tiles_y, strategy, tile_bits);
@@ -1513,11 +1554,28 @@ cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int til
     uint32_t *counts = reinterpret_cast<uint32_t *>(at(16));
     uint32_t *tbase = reinterpret_cast<uint32_t *>(at(8));
     bool tile_counts_done = false;
+    // the side stream of this device, held (with its mutex) until the launcher returns
+    SortSide *side = nullptr;
+    std::unique_lock<std::mutex> side_lock;
+    SideJoin side_join;  // declared after the lock: it joins before the lock is released
+    if (allow_fork && DARB_TILE_COUNTS_FORK && kTileCountsEarly && kPassOnesweep && n > 0) {
+        int dev = 0;
+        TRY(cudaGetDevice(&dev));
+        if (dev >= 0 && dev < kMaxDevicesSort) {
+            side_lock = std::unique_lock<std::mutex>(g_sort_side[dev].mu);
+            TRY(sort_side_init(g_sort_side[dev]));
+            side = &g_sort_side[dev];
+        }
+    }
     const RunTable rt{reinterpret_cast<uint32_t *>(at(21)), kRunTable ? reinterpret_cast<uint32_t *>(at(22)) : nullptr,
                       counters + 2 * kMaxPasses + 1, (uint32_t)run_table_entries(capacity)};
     // 1) depth order of the splats (4 stable 8-bit passes over N keys)
     uint32_t *kbuf[2] = {reinterpret_cast<uint32_t *>(at(4)), reinterpret_cast<uint32_t *>(at(4)) + n};
-    uint32_t *vbuf[2] = {reinterpret_cast<uint32_t *>(at(5)), reinterpret_cast<uint32_t *>(at(5)) + n};
+    // vbuf[0]: the compacted visible ids in index order, which the per-tile counts read on the
+    // side stream while the depth passes run, so the passes' values alternate between vbuf[1]
+    // and vbuf[2] and never overwrite it
+    uint32_t *vbuf[3] = {reinterpret_cast<uint32_t *>(at(5)), reinterpret_cast<uint32_t *>(at(5)) + n,
+                         reinterpret_cast<uint32_t *>(at(5)) + 2 * (size_t)n};
     const uint32_t *order = nullptr;  // sorted splat ids
     const uint32_t *n_vis_dev = nullptr;  // visible count, when order starts with exactly the visible splats
     uint32_t *sums = reinterpret_cast<uint32_t *>(at(17));
@@ -1541,9 +1599,22 @@ cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int til
             launch_k(k_hist_scan, dps.passes, 256, 0, st, dhist, dbase);
             if (kTileCountsEarly) {
                 // the per-tile counts need no depth order: walk the visible splats in index order
-                // (coalesced reads) before the depth passes overwrite this compacted list
+                // (coalesced reads) before the depth passes overwrite this compacted list; on the
+                // side stream they run beside the (latency-bound) depth passes
+                cudaStream_t ts = st;
+                if (side) {
+                    TRY(cudaEventRecord(side->fork, st));
+                    TRY(cudaStreamWaitEvent(side->s, side->fork, 0));
+                    ts = side->s;
+                }
                 TRY(launch_tile_counts(n, vbuf[0], nv, proj, sc, rt, tiles_x, tiles_y, diff, counts, out, cap, tps,
-                                       tbase, st));
+                                       tbase, ts));
+                if (side) {
+                    TRY(cudaEventRecord(side->join, side->s));
+                    side_join.st = st;
+                    side_join.ev = side->join;
+                    side_join.pending = true;
+                }
                 tile_counts_done = true;
             }
         } else {
@@ -1556,26 +1627,27 @@ cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int til
         for (int p = 0; p < dps.passes; ++p) {
             const int nxt = 1 - cur;
             const bool last = p == dps.passes - 1;
+            uint32_t *vout = vbuf[1 + (p & 1)];
             if (kPassOnesweep) {
                 if (last)
-                    TRY((launch_pass<uint32_t, false>(kbuf[cur], vin, nullptr, vbuf[nxt], n_vis, (unsigned long long)n,
+                    TRY((launch_pass<uint32_t, false>(kbuf[cur], vin, nullptr, vout, n_vis, (unsigned long long)n,
                                                       (uint64_t)n, dps.shift[p], dps.bits[p], dbase + p * 256,
                                                       lbd + p * lbd_stride, counters + kMaxPasses + p, out.status, st)));
                 else
-                    TRY((launch_pass<uint32_t, true>(kbuf[cur], vin, kbuf[nxt], vbuf[nxt], n_vis, (unsigned long long)n,
+                    TRY((launch_pass<uint32_t, true>(kbuf[cur], vin, kbuf[nxt], vout, n_vis, (unsigned long long)n,
                                                      (uint64_t)n, dps.shift[p], dps.bits[p], dbase + p * 256,
                                                      lbd + p * lbd_stride, counters + kMaxPasses + p, out.status, st)));
             } else {
                 if (last)
-                    TRY((launch_rts_pass<uint32_t, false>(kbuf[cur], vin, nullptr, vbuf[nxt], nullptr,
+                    TRY((launch_rts_pass<uint32_t, false>(kbuf[cur], vin, nullptr, vout, nullptr,
                                                           (unsigned long long)n, (uint64_t)n, dps.shift[p], dps.bits[p],
                                                           dph, sums, false, st)));
                 else
-                    TRY((launch_rts_pass<uint32_t, true>(kbuf[cur], vin, kbuf[nxt], vbuf[nxt], nullptr,
+                    TRY((launch_rts_pass<uint32_t, true>(kbuf[cur], vin, kbuf[nxt], vout, nullptr,
                                                          (unsigned long long)n, (uint64_t)n, dps.shift[p], dps.bits[p],
                                                          dph, sums, false, st)));
             }
-            vin = vbuf[nxt];
+            vin = vout;
             cur = nxt;
         }
         order = vin;
@@ -1611,6 +1683,7 @@ cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int til
         launch_k(k_splat_offsets, nb, kScanThreads, 0, st, n, order, proj.tiles_touched, n_vis_dev, block_off,
                  out.num_instances,
                  offs, bounds, max_parts);
+    TRY(side_join.join());  // the duplication needs the tile counts' ranges, digit bases and run table
     uint32_t *tph = reinterpret_cast<uint32_t *>(at(11));
     const uint32_t n_parts = (uint32_t)((grid + kSortTile - 1) / kSortTile);
     uint32_t *lb = reinterpret_cast<uint32_t *>(at(18));

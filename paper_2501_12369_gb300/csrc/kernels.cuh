@@ -112,11 +112,14 @@ struct BinOut {
 int sort_tile_bits(int n_tiles);
 size_t sort_workspace_bytes(int n, uint64_t capacity, int tiles_x, int tiles_y, int strategy);
 // Enqueues the whole bin/sort.  With num_instances_host non-null it synchronises once after the
-// scan; if M exceeds the capacity it sets *capacity_exceeded and enqueues nothing more.
+// scan; if M exceeds the capacity it sets *capacity_exceeded and enqueues nothing more.  With
+// allow_fork the per-tile counts run on a library side stream of the device beside the depth
+// passes (forked from and joined back to st with events; concurrent calls of one device are
+// serialised while they enqueue).
 cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int tiles_y, const SpanCtx &sc,
                             uint64_t capacity,
                             int strategy, void *workspace, const BinOut &out, uint64_t *num_instances_host,
-                            bool *capacity_exceeded, cudaStream_t st);
+                            bool *capacity_exceeded, cudaStream_t st, bool allow_fork = true);
 
 // render.cu
 cudaError_t launch_render_fwd(int kind, int tile, int tiles_x, int tiles_y, const uint32_t *ranges,

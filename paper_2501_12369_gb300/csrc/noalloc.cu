@@ -13,7 +13,7 @@
 // call, and calls whose work overlaps on the GPU race.
 #include <mutex>
 
-#include "kernels.cuh"
+#include "validate.h"
 
 namespace {
 
@@ -53,6 +53,7 @@ extern "C" darb_status darb_bin_sort_noalloc(const darb_projected *proj, int32_t
     void *scratch = nullptr;
     const darb_status as = scratch_address(&scratch);
     if (as != DARB_OK) return as;
-    return darb_bin_sort(proj, n, tile, cam, kparams, scratch, kNoAllocScratchBytes, capacity, DARB_SORT_DEPTH_THEN_TILE, out,
-                         num_instances_host, stream);
+    // on the caller's stream only: no library side stream is created for this entry point
+    return darb::bin_sort_entry(proj, n, tile, cam, kparams, scratch, kNoAllocScratchBytes, capacity,
+                                DARB_SORT_DEPTH_THEN_TILE, out, num_instances_host, stream, false);
 }

@@ -43,4 +43,11 @@ inline bool valid_splats(const darb_splats *s) {
 
 constexpr uint64_t kMaxCapacity = (1ull << 30) - 1;
 
+// darb_bin_sort with a switch: allow_fork false keeps every launch on the caller's stream (no
+// library side stream is created or used).
+darb_status bin_sort_entry(const darb_projected *proj, int32_t n, int32_t tile, const darb_camera *cam,
+                           const darb_kernel_params *kparams, void *workspace, size_t workspace_bytes,
+                           uint64_t capacity, int32_t strategy, const darb_binning *out, uint64_t *num_instances_host,
+                           darb_stream stream, bool allow_fork);
+
 }  // namespace darb

@@ -351,6 +351,33 @@ def test_full_size_training_view_on_sampled_tiles(tile):
         grad_close(f"3M/{name}", to_np(got), gp_ref[name])
 
 
+def test_full_size_sort_strategies_agree_on_many_views():
+    """At the benchmark's size the default sort runs its per-tile counts on a side stream beside
+    the depth passes.  Over several views and repeated calls its lists must equal, bit for bit,
+    those of the 64-bit-key strategy, which runs on one stream only: a race between the two
+    streams (for instance over a buffer both read and write) would show as a difference."""
+    splats, cams = synth.scene_3m_1080p(num_cameras=100)
+    sd = darb.splats_to_device(splats)
+    kp = darb.darb_kernel_defaults("half_cosine")
+    tile, cap = 32, 30_000_000
+    tx, ty = darb.darb_tile_grid(cams[0], tile)
+    ws = {st: torch.empty(darb.darb_bin_sort_workspace_size(splats.n, tile, cams[0], cap, st), dtype=torch.uint8,
+                          device="cuda") for st in (darb.DARB_SORT_DEPTH_THEN_TILE, darb.DARB_SORT_KEYS64)}
+    a = darb.Binning.empty(cap, tx * ty, "cuda", keys=False)
+    b = darb.Binning.empty(cap, tx * ty, "cuda")
+    for c in (0, 13, 27, 41, 58, 77, 96):
+        proj = darb.darb_preprocess(sd, cams[c], kp, tile)
+        darb.darb_bin_sort(proj, splats.n, tile, cams[c], ws[darb.DARB_SORT_KEYS64], cap, b,
+                           strategy=darb.DARB_SORT_KEYS64)
+        M = b.M
+        ref_v, ref_r = b.values[:M].clone(), b.ranges.clone()
+        for _ in range(2):
+            darb.darb_bin_sort(proj, splats.n, tile, cams[c], ws[darb.DARB_SORT_DEPTH_THEN_TILE], cap, a)
+            assert a.M == M
+            assert torch.equal(a.values[:M], ref_v), f"camera {c}: values differ"
+            assert torch.equal(a.ranges, ref_r), f"camera {c}: ranges differ"
+
+
 @pytest.mark.parametrize("kernel", ["gaussian", "half_cosine"])
 def test_500k_720p_forward_and_backward_full_frame(kernel):
     s, cam = synth.scene_500k_720p()

@@ -243,11 +243,9 @@ class TrainStep:
         self.visible[cam_idx] = int((self.proj.radius != 0).sum().item())
         return int(m.value)
 
-    def forward(self, cam_idx, ev=None):
+    def _project_and_sort(self, c, rec):
         d, L = self.darb, self.L
         st = d._stream()
-        c = ctypes.byref(self.cam_structs[cam_idx])
-        rec = (lambda i: ev[i].record()) if ev is not None else (lambda i: None)
         rec(0)
         d._check(L.darb_preprocess(ctypes.byref(self.s_splats), c, self.kp_ref, self.tile, ctypes.byref(self.s_proj),
                                    st), "preprocess")
@@ -256,28 +254,40 @@ class TrainStep:
                                  self.ws_bytes,
                                  self.capacity, self.strategy, ctypes.byref(self.s_bins), None, st), "bin_sort")
         rec(2)
+
+    def forward(self, cam_idx, ev=None):
+        """The forward alone: preprocess, sort, compositing."""
+        d, L = self.darb, self.L
+        c = ctypes.byref(self.cam_structs[cam_idx])
+        rec = (lambda i: ev[i].record()) if ev is not None else (lambda i: None)
+        self._project_and_sort(c, rec)
         d._check(L.darb_render_fwd(ctypes.byref(self.s_proj), ctypes.byref(self.s_bins), c, self.kp_ref, self.tile,
-                                   ctypes.byref(self.s_img), st), "render_fwd")
+                                   ctypes.byref(self.s_img), d._stream()), "render_fwd")
         rec(3)
 
     def train(self, cam_idx, ev=None):
+        """One training step.  With the L1 loss the compositing forward takes the loss in its
+        epilogue (darb_render_fwd_l1); with L1 + D-SSIM the loss is its own call."""
         d, L = self.darb, self.L
         st = d._stream()
         c = ctypes.byref(self.cam_structs[cam_idx])
         rec = (lambda i: ev[i].record()) if ev is not None else (lambda i: None)
-        self.forward(cam_idx, ev)
+        self._project_and_sort(c, rec)
         if self.dssim_lambda is None:
-            d._check(L.darb_l1_loss(d._p(self.img.image), d._p(self.target), self.W, self.H, d._p(self.dL),
-                                    d._p(self.loss), st), "l1")
+            d._check(L.darb_render_fwd_l1(ctypes.byref(self.s_proj), ctypes.byref(self.s_bins), c, self.kp_ref,
+                                          self.tile, ctypes.byref(self.s_img), d._p(self.target), d._p(self.dL),
+                                          d._p(self.loss), st), "render_fwd_l1")
         else:
+            d._check(L.darb_render_fwd(ctypes.byref(self.s_proj), ctypes.byref(self.s_bins), c, self.kp_ref,
+                                       self.tile, ctypes.byref(self.s_img), st), "render_fwd")
             d._check(L.darb_l1_dssim_loss(d._p(self.img.image), d._p(self.target), self.W, self.H,
                                           float(self.dssim_lambda), d._p(self.dssim_ws), self.dssim_ws.numel(),
                                           d._p(self.dL), d._p(self.loss2), st), "l1_dssim")
-        rec(4)
+        rec(3)
         d._check(L.darb_render_bwd(ctypes.byref(self.s_proj), self.n, ctypes.byref(self.s_bins), c, self.kp_ref,
                                    self.tile, ctypes.byref(self.s_img), d._p(self.dL), d._p(self.grad2d), st),
                  "render_bwd")
-        rec(5)
+        rec(4)
         self.step_no += 1
         cfg = d.darb_adam_config(LRS["means"], LRS["scales"], LRS["quats"], LRS["opacities"], LRS["sh_dc"],
                                  LRS["sh_rest"], 0.9, 0.999, 1e-15, self.step_no)
@@ -285,14 +295,14 @@ class TrainStep:
             d._check(L.darb_preprocess_bwd_adam(ctypes.byref(self.s_params), c, self.kp_ref, ctypes.byref(self.s_proj),
                                                 d._p(self.grad2d), ctypes.byref(self.s_state), ctypes.byref(cfg), st),
                      "preprocess_bwd_adam")
-            rec(6)
+            rec(5)
             return
         d._check(L.darb_preprocess_bwd(ctypes.byref(self.s_splats), c, self.kp_ref, ctypes.byref(self.s_proj),
                                        d._p(self.grad2d), ctypes.byref(self.s_grads), st), "preprocess_bwd")
-        rec(6)
+        rec(5)
         d._check(L.darb_adam_step(ctypes.byref(self.s_params), ctypes.byref(self.s_grads), ctypes.byref(self.s_state),
                                   ctypes.byref(cfg), st), "adam")
-        rec(7)
+        rec(6)
 
 
 # DRAM bytes (read + write) per splat of k_preprocess_bwd_adam<3>: dram__bytes_read.sum +
@@ -300,8 +310,9 @@ class TrainStep:
 # train_tail case of paper_2501_12369_gb300.profile_cases), divided by the splat count.
 TRAFFIC_BWD_ADAM_PER_SPLAT = 1436.0
 
-STAGES_FUSED = ["preprocess", "bin_sort", "render_fwd", "l1_loss", "render_bwd", "preprocess_bwd_adam"]
-STAGES_SEPARATE = ["preprocess", "bin_sort", "render_fwd", "l1_loss", "render_bwd", "preprocess_bwd", "adam"]
+# the compositing forward takes the L1 loss in its epilogue (darb_render_fwd_l1)
+STAGES_FUSED = ["preprocess", "bin_sort", "render_fwd_l1", "render_bwd", "preprocess_bwd_adam"]
+STAGES_SEPARATE = ["preprocess", "bin_sort", "render_fwd_l1", "render_bwd", "preprocess_bwd", "adam"]
 
 
 def algorithmic_bytes(stage, n, M, passes, sh_k, strategy=0, tile_passes=2, n_vis=None):
@@ -629,7 +640,15 @@ def run_ours(args):
         step(args.warmup + k, dss[k])
     torch.cuda.synchronize()
     d_ms = dss[0][0].elapsed_time(dss[-1][-1]) / dev_steps
-    loss_ms = sum(e[3].elapsed_time(e[4]) for e in dss) / dev_steps
+    # the loss alone (its zeroing, forward and backward kernels), on the last step's image
+    le = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    le[0].record()
+    for _ in range(10):
+        ts.darb.darb_l1_dssim_loss(ts.img.image, ts.target, 0.2, workspace=ts.dssim_ws, dL_dimage=ts.dL,
+                                   loss=ts.loss2)
+    le[1].record()
+    torch.cuda.synchronize()
+    loss_ms = le[0].elapsed_time(le[1]) / 10
     line["l1_dssim_step"] = {"it_s": whole_job_rate(world, 1, d_ms), "ms_per_step": d_ms, "loss_ms": loss_ms,
                              "lambda": 0.2}
     ts.dssim_lambda = None
@@ -661,9 +680,10 @@ def launches_per_step(strategy, tile_bits, fused=True):
         # pass, the other tile passes
         sort = 4 + 4 + 5 + max(1, (tile_bits + 7) // 8)
     sort += 1  # the zeroing of the sort's counters, status and ranges
-    # preprocess, render_fwd, the loss (zeroing + L1), render_bwd (zeroing of grad2d + the
-    # compositing backward), then preprocess_bwd + 5 Adam groups or one fused kernel
-    return 1 + sort + 1 + 2 + 2 + (1 if fused else 1 + 5)
+    # preprocess, the loss zeroing + the compositing forward with the L1 loss in its epilogue,
+    # render_bwd (zeroing of grad2d + the compositing backward), then preprocess_bwd + 5 Adam
+    # groups or one fused kernel
+    return 1 + sort + 2 + 2 + (1 if fused else 1 + 5)
 
 
 def pair_counts(ts):
@@ -710,7 +730,7 @@ def kernel_sweep(ts, step, cam_seq, first, stages, restore_kernel, steps=20):
         total = evs[0][0].elapsed_time(evs[-1][-1])
         ts.forward(cam_seq[first % len(cam_seq)])
         pc = pair_counts(ts)
-        fwd_s, bwd_s = per["render_fwd"] / 1e3, per["render_bwd"] / 1e3
+        fwd_s, bwd_s = per["render_fwd_l1"] / 1e3, per["render_bwd"] / 1e3
         pc.update({"fwd_walked_pairs_per_s": round(pc["fwd_walked_lower_bound"] / fwd_s / 1e9, 3),
                    "fwd_blended_pairs_per_s": round(pc["blended"] / fwd_s / 1e9, 3),
                    "bwd_evaluated_pairs_per_s": round(pc["replayed"] / bwd_s / 1e9, 3),

@@ -210,6 +210,24 @@ darb_status darb_render_fwd(const darb_projected *proj, const darb_binning *bins
     return DARB_OK;
 }
 
+darb_status darb_render_fwd_l1(const darb_projected *proj, const darb_binning *bins, const darb_camera *cam,
+                               const darb_kernel_params *kparams, int32_t tile, const darb_image *out,
+                               const float *target, float *dL_dimage, float *loss, darb_stream stream) {
+    if (!valid_projected_or_empty(proj) || !bins || !bins->ranges || !valid_camera(cam) || !valid_kernel(kparams) ||
+        !valid_tile(tile) || !out || !out->image || !out->t_final || !out->last || !out->n_contrib || !target ||
+        !dL_dimage || !loss)
+        return DARB_ERR_INVALID_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    DARB_CUDA_TRY(launch_zero(st, loss, sizeof(float)));
+    const int tiles_x = tile_count(cam->width, tile), tiles_y = tile_count(cam->height, tile);
+    DARB_CUDA_TRY(launch_render_fwd(kparams->kind, tile, tiles_x, tiles_y, bins->ranges, bins->values,
+                                    reinterpret_cast<const float2 *>(proj->mean2d),
+                                    reinterpret_cast<const float4 *>(proj->conic_o), proj->rgb, make_cam(*cam),
+                                    kparams->q_max, kparams->q_max_strict ? 1 : 0, make_spec(*kparams), out->image,
+                                    out->t_final, out->last, out->n_contrib, st, target, dL_dimage, loss));
+    return DARB_OK;
+}
+
 darb_status darb_render_bwd(const darb_projected *proj, int32_t n, const darb_binning *bins, const darb_camera *cam,
                             const darb_kernel_params *kparams, int32_t tile, const darb_image *fwd,
                             const float *dL_dimage, float *grad2d, darb_stream stream) {

@@ -122,11 +122,14 @@ cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int til
                             bool *capacity_exceeded, cudaStream_t st, bool allow_fork = true);
 
 // render.cu
+// With l1_target non-null the kernel's epilogue also writes the L1 loss gradient to l1_dL and
+// adds the loss to *l1_loss (which the caller zeroes).
 cudaError_t launch_render_fwd(int kind, int tile, int tiles_x, int tiles_y, const uint32_t *ranges,
                               const uint32_t *values, const float2 *mean2d, const float4 *conic_o,
                               const float *rgb, const Cam &cam, float qmax, int strict, const KernelSpec &ks,
                               float *image, float *t_final, uint32_t *last, uint32_t *n_contrib,
-                              cudaStream_t st);
+                              cudaStream_t st, const float *l1_target = nullptr, float *l1_dL = nullptr,
+                              float *l1_loss = nullptr);
 cudaError_t launch_render_bwd(int kind, int tile, int tiles_x, int tiles_y, const uint32_t *ranges,
                               const uint32_t *values, const float2 *mean2d, const float4 *conic_o,
                               const float *rgb, const Cam &cam, float qmax, int strict, const KernelSpec &ks,

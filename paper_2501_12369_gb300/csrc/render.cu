@@ -79,15 +79,27 @@ struct FwdSink {
     Bg bg;
 };
 
+// The L1 image loss (Sec. 4.2) taken in the forward's epilogue, where each pixel's colour is
+// in registers: dL/dC = sign(C - target) / count per channel, and the block's sum of
+// |C - target| / count added to *loss (zeroed by the caller).
+struct L1Out {
+    const float *target;
+    float *dL;
+    float *loss;
+    float inv_count;
+};
+
 // One tile of one view, by the whole CTA.  sink() is called once, after the compositing loop,
-// so the output pointers need not stay live in registers across it.
-template <int KIND, int TILE, class SinkFn>
+// so the output pointers need not stay live in registers across it.  With L1 the epilogue also
+// takes the L1 loss of the tile's pixels (every thread of the CTA reaches it).
+template <int KIND, int TILE, bool L1 = false, class SinkFn>
 __device__ __forceinline__ void render_tile_fwd(int tile, FwdSmem<TILE> &sm, const uint2 *__restrict__ ranges,
                                                 const uint32_t *__restrict__ values,
                                                 const float2 *__restrict__ mean2d,
                                                 const float4 *__restrict__ conic_o, const float *__restrict__ rgb,
                                                 int W, int H, int tiles_x, float qmax, int strict,
-                                                const KernelSpec &ks, SinkFn sink) {
+                                                const KernelSpec &ks, SinkFn sink, const L1Out &l1 = L1Out{},
+                                                float *s_l1 = nullptr) {
     using S = RenderShape<TILE>;
     constexpr int NT = S::NT, PIX = S::PIX;
     const int tx = tile % tiles_x, ty = tile / tiles_x;
@@ -160,31 +172,51 @@ __device__ __forceinline__ void render_tile_fwd(int tile, FwdSmem<TILE> &sm, con
     }
     const size_t plane = (size_t)W * H;
     const FwdSink o = sink();
+    float acc = 0.0f;  // the pixels' |C - target| (with L1)
 #pragma unroll
     for (int k = 0; k < PIX; ++k) {
         const int py = py0 + k * S::ROWS;
         if (!(px < W && py < H)) continue;
         const size_t pix = (size_t)py * W + px;
-        o.image[pix] = fmaf(T[k], o.bg.r, C0[k]);
-        o.image[plane + pix] = fmaf(T[k], o.bg.g, C1[k]);
-        o.image[2 * plane + pix] = fmaf(T[k], o.bg.b, C2[k]);
+        const float c[3] = {fmaf(T[k], o.bg.r, C0[k]), fmaf(T[k], o.bg.g, C1[k]), fmaf(T[k], o.bg.b, C2[k])};
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            o.image[ch * plane + pix] = c[ch];
+            if constexpr (L1) {
+                const float d = c[ch] - l1.target[ch * plane + pix];
+                l1.dL[ch * plane + pix] = d > 0.0f ? l1.inv_count : (d < 0.0f ? -l1.inv_count : 0.0f);
+                acc += fabsf(d);
+            }
+        }
         if (o.t_final) o.t_final[pix] = T[k];
         if (o.last) o.last[pix] = lastp[k];
         if (o.n_contrib) o.n_contrib[pix] = count[k];
     }
+    if constexpr (L1) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        if ((threadIdx.x & 31) == 0) s_l1[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float sum = 0.0f;
+            for (int w = 0; w < S::NT / 32; ++w) sum += s_l1[w];
+            atomicAdd(l1.loss, sum * l1.inv_count);
+        }
+    }
 }
 
-template <int KIND, int TILE>
+template <int KIND, int TILE, bool L1>
 __global__ void DARB_FWD_BOUNDS(RenderShape<TILE>::NT)
 k_render_fwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ values,
              const float2 *__restrict__ mean2d, const float4 *__restrict__ conic_o,
              const float *__restrict__ rgb, int W, int H, int tiles_x, float qmax, int strict, KernelSpec ks, Bg bg,
              float *__restrict__ image, float *__restrict__ t_final, uint32_t *__restrict__ last,
-             uint32_t *__restrict__ n_contrib) {
+             uint32_t *__restrict__ n_contrib, L1Out l1) {
     pdl_entry();
     __shared__ FwdSmem<TILE> sm;
-    render_tile_fwd<KIND, TILE>(blockIdx.x, sm, ranges, values, mean2d, conic_o, rgb, W, H, tiles_x, qmax, strict, ks,
-                                [&] { return FwdSink{image, t_final, last, n_contrib, bg}; });
+    __shared__ float s_l1[L1 ? RenderShape<TILE>::NT / 32 : 1];
+    render_tile_fwd<KIND, TILE, L1>(blockIdx.x, sm, ranges, values, mean2d, conic_o, rgb, W, H, tiles_x, qmax, strict,
+                                    ks, [&] { return FwdSink{image, t_final, last, n_contrib, bg}; }, l1, s_l1);
 }
 
 // Several views in one persistent launch: CTAs take (view, tile) items from a device counter
@@ -420,10 +452,15 @@ template <int KIND, int TILE>
 cudaError_t fwd_t(int n_tiles, const uint2 *ranges, const uint32_t *values, const float2 *mean2d,
                   const float4 *conic_o, const float *rgb, const Cam &cam, int tiles_x, float qmax, int strict,
                   const KernelSpec &ks, float *image, float *t_final, uint32_t *last, uint32_t *n_contrib,
-                  cudaStream_t st) {
-    launch_k(k_render_fwd<KIND, TILE>, n_tiles, RenderShape<TILE>::NT, 0, st,
-             ranges, values, mean2d, conic_o, rgb, cam.W, cam.H, tiles_x, qmax, strict, ks,
-             Bg{cam.bg[0], cam.bg[1], cam.bg[2]}, image, t_final, last, n_contrib);
+                  const L1Out &l1, cudaStream_t st) {
+    if (l1.target)
+        launch_k(k_render_fwd<KIND, TILE, true>, n_tiles, RenderShape<TILE>::NT, 0, st,
+                 ranges, values, mean2d, conic_o, rgb, cam.W, cam.H, tiles_x, qmax, strict, ks,
+                 Bg{cam.bg[0], cam.bg[1], cam.bg[2]}, image, t_final, last, n_contrib, l1);
+    else
+        launch_k(k_render_fwd<KIND, TILE, false>, n_tiles, RenderShape<TILE>::NT, 0, st,
+                 ranges, values, mean2d, conic_o, rgb, cam.W, cam.H, tiles_x, qmax, strict, ks,
+                 Bg{cam.bg[0], cam.bg[1], cam.bg[2]}, image, t_final, last, n_contrib, l1);
     return cudaGetLastError();
 }
 
@@ -444,11 +481,12 @@ cudaError_t launch_render_fwd(int kind, int tile, int tiles_x, int tiles_y, cons
                               const uint32_t *values, const float2 *mean2d, const float4 *conic_o,
                               const float *rgb, const Cam &cam, float qmax, int strict, const KernelSpec &ks,
                               float *image, float *t_final, uint32_t *last, uint32_t *n_contrib,
-                              cudaStream_t st) {
+                              cudaStream_t st, const float *l1_target, float *l1_dL, float *l1_loss) {
     const int n_tiles = tiles_x * tiles_y;
     if (n_tiles == 0) return cudaSuccess;
     const uint2 *rg = reinterpret_cast<const uint2 *>(ranges);
-#define FWD_ARGS (n_tiles, rg, values, mean2d, conic_o, rgb, cam, tiles_x, qmax, strict, ks, image, t_final, last, n_contrib, st)
+    const L1Out l1{l1_target, l1_dL, l1_loss, 1.0f / (3.0f * (float)cam.W * (float)cam.H)};
+#define FWD_ARGS (n_tiles, rg, values, mean2d, conic_o, rgb, cam, tiles_x, qmax, strict, ks, image, t_final, last, n_contrib, l1, st)
 #define FWD_CALL(K, T) fwd_t<K, T> FWD_ARGS
     if (tile == 8) {
         switch (kind) {

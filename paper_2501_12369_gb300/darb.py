@@ -123,6 +123,8 @@ SIGNATURES = {
                                       _P(darb_binning), _P(ctypes.c_uint64), c_vp]),
     "darb_render_fwd": (c_i32, [_P(darb_projected), _P(darb_binning), _P(darb_camera), _P(darb_kernel_params),
                                 c_i32, _P(darb_image), c_vp]),
+    "darb_render_fwd_l1": (c_i32, [_P(darb_projected), _P(darb_binning), _P(darb_camera), _P(darb_kernel_params),
+                                   c_i32, _P(darb_image), c_vp, c_vp, c_vp, c_vp]),
     "darb_render_bwd": (c_i32, [_P(darb_projected), c_i32, _P(darb_binning), _P(darb_camera),
                                 _P(darb_kernel_params), c_i32, _P(darb_image), c_vp, c_vp, c_vp]),
     "darb_preprocess_bwd": (c_i32, [_P(darb_splats), _P(darb_camera), _P(darb_kernel_params), _P(darb_projected),
@@ -417,6 +419,20 @@ def darb_render_fwd(proj: Projected, bins: Binning, cam, kparams, tile=16, out: 
     _check(lib().darb_render_fwd(ctypes.byref(pr), ctypes.byref(b), ctypes.byref(c), ctypes.byref(kparams), int(tile),
                                  ctypes.byref(o), _stream(stream)), "darb_render_fwd")
     return out
+
+
+def darb_render_fwd_l1(proj: Projected, bins: Binning, cam, kparams, tile, target, out: ImageOut | None = None,
+                       dL_dimage=None, loss=None, stream=None):
+    """Forward with the L1 loss in its epilogue; returns (image outputs, dL_dimage, loss[1])."""
+    out = ImageOut.empty(cam.width, cam.height, proj.depth.device) if out is None else out
+    dL_dimage = torch.empty_like(out.image) if dL_dimage is None else dL_dimage
+    loss = torch.empty(1, dtype=torch.float32, device=out.image.device) if loss is None else loss
+    assert target.is_contiguous() and target.dtype == torch.float32 and tuple(target.shape) == tuple(out.image.shape)
+    pr, b, c, o = proj.struct(), bins.struct(), camera(cam), out.struct()
+    _check(lib().darb_render_fwd_l1(ctypes.byref(pr), ctypes.byref(b), ctypes.byref(c), ctypes.byref(kparams),
+                                    int(tile), ctypes.byref(o), _p(target), _p(dL_dimage), _p(loss), _stream(stream)),
+           "darb_render_fwd_l1")
+    return out, dL_dimage, loss
 
 
 def darb_render_bwd(proj: Projected, n, bins: Binning, cam, kparams, tile, fwd: ImageOut, dL_dimage: torch.Tensor,

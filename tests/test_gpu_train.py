@@ -127,6 +127,26 @@ def test_l1_loss_matches_oracle(W, H):
     np.testing.assert_allclose(got, ref_dl, rtol=1e-7)
 
 
+@pytest.mark.parametrize("kernel,tile", [("half_cosine", 32), ("gaussian", 16), ("parabola", 8)])
+def test_forward_with_l1_equals_forward_then_l1(kernel, tile):
+    """darb_render_fwd_l1 (the loss taken in the compositing kernel's epilogue) against
+    darb_render_fwd followed by darb_l1_loss: every image output and the loss gradient bit for
+    bit, the loss up to the order of its FP32 sums; a ragged 333x207 view and a tiny one."""
+    for s, cam in ((synth.cluster_scene(20000, seed=5), synth.fibonacci_cameras(16, 6.0, 333, 207, 260.0)[3]),
+                   (synth.uniform_cube_scene(300, seed=9), synth.pinhole((0.2, 0.1, 3.5), 17, 33, 18.0))):
+        r, sd, proj, bins, img = gpu_forward(s, cam, kernel, tile)
+        target = torch.from_numpy(synth.random_target(cam.height, cam.width, seed=4)).cuda()
+        dL, loss = darb.darb_l1_loss(img.image, target)
+        out, dL2, loss2 = darb.darb_render_fwd_l1(proj, bins, cam, r.kparams, tile, target)
+        torch.cuda.synchronize()
+        for a, b in ((img.image, out.image), (img.t_final, out.t_final), (img.last, out.last),
+                     (img.n_contrib, out.n_contrib), (dL, dL2)):
+            assert torch.equal(a, b)
+        assert abs(float(loss2[0]) - float(loss[0])) <= 1e-5 * abs(float(loss[0]))
+        ref, _ = oracle.l1_loss(to_np(img.image), to_np(target))
+        assert abs(float(loss2[0]) - ref) <= 1e-5 * ref
+
+
 def test_l1_loss_on_buffers_off_a_16_byte_boundary():
     # the float4 lanes need all three buffers aligned; views 4 bytes in take the one-by-one path
     W, H = 97, 31

@@ -224,10 +224,11 @@ darb_status darb_bin_sort_workspace_size(int32_t n, int32_t tile, const darb_cam
  * M > capacity (outputs then undefined); if NULL nothing synchronises, the sort is
  * sized by capacity, and an overflow is reported in out->status with every tile range
  * left empty (so a following darb_render_fwd draws only the background).  The per-tile counts
- * run on a side stream of the library (one per device, created by the first call), forked
- * from and joined back to `stream` with events, beside the depth sort: the call stays ordered
- * on `stream` and is capturable; calls from several host threads on one device are serialised
- * while they enqueue. */
+ * run on a side stream of the library (one per device, created by the first call, so make one
+ * call before capturing the stream), forked from and joined back to `stream` with events,
+ * beside the depth sort: the call stays ordered on `stream` and can be captured in a CUDA graph
+ * (with num_instances_host NULL); calls from several host threads on one device are
+ * serialised while they enqueue. */
 darb_status darb_bin_sort(const darb_projected *proj, int32_t n, int32_t tile,
                           const darb_camera *cam, const darb_kernel_params *kparams,
                           void *workspace, size_t workspace_bytes,

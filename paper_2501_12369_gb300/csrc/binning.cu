@@ -1311,7 +1311,12 @@ cudaError_t launch_pass(const K *kin, const uint32_t *vin, K *kout, uint32_t *vo
 namespace {
 // Entries of the run table: at most a quarter of the instance capacity, at least 64k.  A
 // splat whose rows no longer fit is marked and its runs are recomputed by the duplication.
-uint64_t run_table_entries(uint64_t capacity) { return std::max<uint64_t>(capacity / 4, 1u << 16); }
+#ifndef DARB_RUN_TABLE_MAX
+#define DARB_RUN_TABLE_MAX 0xffffffffu  // a test build caps it to reach the recomputing fallback
+#endif
+uint64_t run_table_entries(uint64_t capacity) {
+    return std::min<uint64_t>(std::max<uint64_t>(capacity / 4, 1u << 16), DARB_RUN_TABLE_MAX);
+}
 
 struct Layout {
     size_t total;

@@ -89,6 +89,50 @@ def test_batch_graph_replay_equals_eager():
         assert torch.equal(br.outs[v].image, eager[v]), f"view {v}"
 
 
+def test_single_view_graph_with_forked_sort_equals_eager():
+    """Preprocess, the default sort (its per-tile counts forked onto the library's side stream
+    and joined back) and compositing captured in one CUDA graph: replays over two cameras
+    (the camera is a kernel argument, so each camera gets its own graph) equal the eager calls."""
+    s = synth.cluster_scene(200_000, seed=6)
+    sd = darb.splats_to_device(s)
+    cams = synth.fibonacci_cameras(8, 6.0, 640, 360, 500.0)[2:4]
+    kp = darb.darb_kernel_defaults("half_cosine")
+    tile, cap = 32, 4_000_000
+    tx, ty = darb.darb_tile_grid(cams[0], tile)
+    ws = torch.empty(darb.darb_bin_sort_workspace_size(s.n, tile, cams[0], cap), dtype=torch.uint8, device="cuda")
+    proj = darb.Projected.empty(s.n)
+    bins = darb.Binning.empty(cap, tx * ty, "cuda", keys=False)
+    img = darb.ImageOut.empty(cams[0].width, cams[0].height)
+
+    def run(cam):
+        darb.darb_preprocess(sd, cam, kp, tile, out=proj)
+        darb.darb_bin_sort(proj, s.n, tile, cam, ws, cap, bins, sync=False)
+        darb.darb_render_fwd(proj, bins, cam, kp, tile, out=img)
+
+    eager = []
+    for cam in cams:  # the first calls also create the sort's side stream
+        run(cam)
+        torch.cuda.synchronize()
+        assert int(bins.status.item()) == 0
+        eager.append([t.clone() for t in (img.image, img.n_contrib, bins.ranges)])
+    graphs = []
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    for cam in cams:
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=side):
+            run(cam)
+        graphs.append(g)
+    torch.cuda.synchronize()
+    for _ in range(2):
+        for g, ref in zip(graphs, eager):
+            img.image.fill_(-1.0)
+            g.replay()
+            torch.cuda.synchronize()
+            for got, want in zip((img.image, img.n_contrib, bins.ranges), ref):
+                assert torch.equal(got, want)
+
+
 def test_batch_capacity_overflow_is_per_view():
     """A capacity below one view's M: that view reports DARB_ERR_CAPACITY and shows background;
     the others render normally."""

@@ -91,6 +91,37 @@ def test_large_elongated_and_border_splats(tile):
     check_render(img, bins, oracle.forward(s, cam, "half_cosine", tile=tile), cam, tile)
 
 
+def test_run_table_overflow_falls_back_to_recomputed_runs():
+    """A copy of the library built with a 64-entry run table: the unpacked splats that no
+    longer fit are marked and their runs recomputed by the duplication.  The lists must still
+    equal the oracle's (the scene and tiles of the elongated-splat test, 8-pixel tiles)."""
+    import ctypes
+    from paper_2501_12369_gb300 import build
+    path = build.build_variant("small_run_table", ["-DDARB_RUN_TABLE_MAX=64"])
+    L = ctypes.CDLL(path)
+    for name, (res, args) in darb.SIGNATURES.items():
+        getattr(L, name).restype, getattr(L, name).argtypes = res, args
+    cam = synth.pinhole((0.0, 0.0, 3.0), 320, 296, 300.0, bg=(0.1, 0.2, 0.3))
+    big = synth.uniform_cube_scene(24, seed=11, log_scale=(-1.2, -0.6))
+    thin = synth.uniform_cube_scene(600, seed=12, half=1.6, log_scale=(-5.0, -1.5))
+    s = synth.Splats(*(np.concatenate([getattr(big, f), getattr(thin, f)])
+                       for f in ("means", "scales", "quats", "opacities", "sh")), big.sh_degree)
+    tile = 8
+    saved = darb._lib
+    try:
+        darb._lib = L
+        r, sd, proj, bins, img = gpu_forward(s, cam, "half_cosine", tile)
+    finally:
+        darb._lib = saved
+    ref = oracle.project(s, cam, oracle.kernel_params("half_cosine"), tile, True)
+    vis = ref["culled"] == 0
+    rows = ref["rect"][vis, 3] - ref["rect"][vis, 1] + 1
+    cols = ref["rect"][vis, 2] - ref["rect"][vis, 0] + 1
+    assert rows[(rows > 8) | (cols > 15)].sum() > 64  # more unpacked rows than the table holds
+    check_lists(bins, oracle.build_lists(ref, cam, tile))
+    check_render(img, bins, oracle.forward(s, cam, "half_cosine", tile=tile), cam, tile)
+
+
 def test_bin_sort_strategies_agree_on_a_large_scene():
     s = synth.cluster_scene(300_000, seed=11)
     cam = synth.fibonacci_cameras(10, 6.0, 1280, 720, 1000.0)[4]

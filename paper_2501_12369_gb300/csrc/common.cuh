@@ -392,6 +392,15 @@ __device__ __forceinline__ bool in_support(float q, float qmax, bool strict) {
     return q >= 0.0f && (strict ? q < qmax : q <= qmax);
 }
 
+// The same test with the strictness folded into the limit once: for floats, q < q_max exactly
+// when q <= the float just below q_max, so in_support(q, qmax, strict) equals
+// in_support_lim(q, support_limit(qmax, strict)) for every q (q_max positive and finite, as
+// the boundary checks).
+__device__ __forceinline__ float support_limit(float qmax, bool strict) {
+    return strict ? __uint_as_float(__float_as_uint(qmax) - 1u) : qmax;
+}
+__device__ __forceinline__ bool in_support_lim(float q, float qlim) { return q >= 0.0f && q <= qlim; }
+
 // q = dx (A dx + 2B dy) + (C dy) dy as a fixed FP32 sequence (no contraction beyond the
 // two explicit fused multiply-adds), shared by forward and backward so both take the
 // same support decision.  B2 = 2B (exact).

@@ -63,6 +63,18 @@ struct BwdShape {
     static constexpr int ROWS = TILE / PIX;
 };
 
+// The forward's per-pair body: branch-free, a pair that does not blend taking weight 0 (1), or
+// one branch per failed test (0).  Both give the same bits: C + rgb * 0 = C and T is kept.
+// Branch-free measured 0.108 -> 0.103 ms (half-cosine) at 3M splats / 1080p.  The backward
+// keeps its branches: there a pair that does not contribute would still pay for F', the
+// reciprocal and the nine products (0.204 -> 0.212 ms half-cosine, 0.669 -> 0.736 Gaussian).
+// Both passes test the support against support_limit(q_max, strict), taken once per thread:
+// with the strictness a kernel argument tested per pair, the forward took 0.103 ms and the
+// backward 0.204 ms (half-cosine), against 0.089 and 0.190 ms.
+#ifndef DARB_FWD_SELECT
+#define DARB_FWD_SELECT 1
+#endif
+
 template <int TILE>
 struct FwdSmem {
     float2 xy[RenderShape<TILE>::NT];
@@ -108,6 +120,7 @@ __device__ __forceinline__ void render_tile_fwd(int tile, FwdSmem<TILE> &sm, con
     const float fpx = (float)px + 0.5f;
     const uint2 r = ranges[tile];
     const int start = (int)r.x, end = (int)r.y;
+    const float qlim = support_limit(qmax, strict);
 
     float fpy[PIX], T[PIX], C0[PIX], C1[PIX], C2[PIX];
     uint32_t count[PIX], lastp[PIX];
@@ -145,13 +158,37 @@ __device__ __forceinline__ void render_tile_fwd(int tile, FwdSmem<TILE> &sm, con
             const float4 co = sm.co[j];
             const float dx = __fsub_rn(xy.x, fpx);
             bool any_live = false;
+#if DARB_FWD_SELECT
+            const float r0 = sm.rgb[j][0], r1 = sm.rgb[j][1], r2 = sm.rgb[j][2];
+            const uint32_t pos = (uint32_t)(b0 - start + j + 1);
 #pragma unroll
             for (int k = 0; k < PIX; ++k) {
                 if (done[k]) continue;
                 any_live = true;
                 const float dy = __fsub_rn(xy.y, fpy[k]);
                 const float q = conic_q(dx, dy, co.x, co.y, co.z);
-                if (!in_support(q, qmax, strict)) continue;
+                const float alpha = fminf(kAlphaMax, __fmul_rn(co.w, kernel_F<KIND>(q, ks)));
+                const float Tn = T[k] * (1.0f - alpha);
+                const bool use = in_support_lim(q, qlim) && alpha >= kAlphaMin;
+                const bool stop = Tn < kTMin;
+                if (use && stop) done[k] = true;
+                const bool blend = use && !stop;
+                const float w = blend ? alpha * T[k] : 0.0f;  // weight 0 leaves C and T exactly as they are
+                C0[k] = fmaf(r0, w, C0[k]);
+                C1[k] = fmaf(r1, w, C1[k]);
+                C2[k] = fmaf(r2, w, C2[k]);
+                T[k] = blend ? Tn : T[k];
+                count[k] += blend ? 1u : 0u;
+                lastp[k] = blend ? pos : lastp[k];
+            }
+#else
+#pragma unroll
+            for (int k = 0; k < PIX; ++k) {
+                if (done[k]) continue;
+                any_live = true;
+                const float dy = __fsub_rn(xy.y, fpy[k]);
+                const float q = conic_q(dx, dy, co.x, co.y, co.z);
+                if (!in_support_lim(q, qlim)) continue;
                 const float alpha = fminf(kAlphaMax, __fmul_rn(co.w, kernel_F<KIND>(q, ks)));
                 if (alpha < kAlphaMin) continue;
                 const float Tn = T[k] * (1.0f - alpha);
@@ -167,6 +204,7 @@ __device__ __forceinline__ void render_tile_fwd(int tile, FwdSmem<TILE> &sm, con
                 ++count[k];
                 lastp[k] = (uint32_t)(b0 - start + j + 1);
             }
+#endif
             if (!any_live) break;
         }
     }
@@ -323,6 +361,7 @@ k_render_bwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ valu
     const float fpx = (float)px + 0.5f;
     const uint2 r = ranges[tile];
     const int start = (int)r.x;
+    const float qlim = support_limit(qmax, strict);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const size_t plane = (size_t)W * H;
 
@@ -385,7 +424,7 @@ k_render_bwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ valu
                 if (pos >= (int)my_last[k]) continue;
                 const float dy = __fsub_rn(xy.y, fpy[k]);
                 const float q = conic_q(dx, dy, co.x, co.y, co.z);
-                if (!in_support(q, qmax, strict)) continue;
+                if (!in_support_lim(q, qlim)) continue;
                 const float F = kernel_F<KIND>(q, ks);
                 const float of = __fmul_rn(co.w, F);
                 const float alpha = fminf(kAlphaMax, of);

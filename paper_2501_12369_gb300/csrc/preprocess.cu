@@ -283,11 +283,13 @@ struct PreGeom {
     int radius, idx;
 };
 
-// Compiled for 8 resident CTAs per SM (32 registers, 2048 threads): the projection is
-// latency-bound, and full occupancy measured 0.172 -> 0.153 ms at 3M splats / 1080p (6 CTAs:
-// 0.157).  DARB_PRE_MIN_CTAS=0 leaves the register count to the compiler.
+// Compiled for 6 resident CTAs per SM (40 registers, 1536 threads): the projection is
+// latency-bound, and a register cap raised occupancy from the compiler's choice (0.172 ->
+// 0.153 ms at 3M splats / 1080p with 8 CTAs, 0.157 with 6).  Since the SH prefetch and the
+// two-phase queue, 6 CTAs measure 0.142 ms against 0.145 at 8 (32 registers, which spill)
+// and 0.150 with no cap.  DARB_PRE_MIN_CTAS=0 leaves the register count to the compiler.
 #ifndef DARB_PRE_MIN_CTAS
-#define DARB_PRE_MIN_CTAS 8
+#define DARB_PRE_MIN_CTAS 6
 #endif
 #if DARB_PRE_MIN_CTAS > 0
 #define DARB_PRE_BOUNDS __launch_bounds__(kPreThreads, DARB_PRE_MIN_CTAS)

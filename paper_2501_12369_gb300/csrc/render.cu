@@ -35,10 +35,11 @@ struct RenderShape {
 };
 
 // Resident CTAs per SM the compositing kernels may be compiled for (a register budget);
-// unset, the compiler chooses.  The backward at 4 (64 registers) measured faster than the
-// compiler's 73 registers at 3 CTAs per SM (0.214 -> 0.208 ms at 3M / 1080p).
+// unset, the compiler chooses.  The backward compiles to 64 registers under a budget of 3 or
+// of 4 CTAs per SM (4 stay resident either way), but the schedule it gets for 3 measured
+// 0.186 ms against 0.190 for the half-cosine at 3M / 1080p (Gaussian 0.604 against 0.612).
 #ifndef DARB_BWD_MIN_CTAS
-#define DARB_BWD_MIN_CTAS 4
+#define DARB_BWD_MIN_CTAS 3
 #endif
 #ifdef DARB_FWD_MIN_CTAS
 #define DARB_FWD_BOUNDS(nt) __launch_bounds__(nt, DARB_FWD_MIN_CTAS)

@@ -675,10 +675,10 @@ def launches_per_step(strategy, tile_bits, fused=True):
     """Kernels of libdarb.so launched per training step."""
     if strategy == 1:  # 64-bit keys: block sums, scan, duplicate, histogram, hist scan, passes, ranges
         sort = 6 + (32 + tile_bits + 7) // 8
-    else:  # visible count, its scan, depth compaction with the histograms, hist scan, 4 depth passes,
-        # block sums, scan, tile diff, tile setup, offsets, duplication fused with the first tile
-        # pass, the other tile passes
-        sort = 4 + 4 + 5 + max(1, (tile_bits + 7) // 8)
+    else:  # depth compaction with the visible count and the digit histograms (one chained pass),
+        # hist scan, 4 depth passes, tile diff, tile setup, offsets with M (one chained pass),
+        # duplication fused with the first tile pass, the other tile passes
+        sort = 2 + 4 + 3 + max(1, (tile_bits + 7) // 8)
     sort += 1  # the zeroing of the sort's counters, status and ranges
     # preprocess, the loss zeroing + the compositing forward with the L1 loss in its epilogue,
     # render_bwd (zeroing of grad2d + the compositing backward), then preprocess_bwd + 5 Adam

@@ -89,6 +89,77 @@ __device__ __forceinline__ void st_relaxed(uint32_t *p, uint32_t v) {
     *reinterpret_cast<volatile uint32_t *>(p) = v;
 }
 
+// ---------------------------------------------------------------------------- chained scans
+//
+// A single-pass exclusive scan over partitions taken in launch order (each CTA claims the next
+// index from a counter, so every predecessor of a partition is already running): a partition
+// publishes its own total, sums its predecessors' published words back to the nearest inclusive
+// prefix, and publishes its own inclusive prefix.  One 64-bit word per partition, zeroed before
+// the launch: bits 62-63 the state (1: the partition's total, 2: the inclusive prefix through
+// it), bits 0-61 the value.
+constexpr unsigned long long kChainOwn = 1ull << 62, kChainIncl = 2ull << 62, kChainVal = (1ull << 62) - 1;
+// The visible count with the compaction, and the instance offsets with M, each as one chained
+// pass (1), or each as block sums, a one-CTA scan of them and the pass itself (0).
+#ifndef DARB_CHAINED_SCANS
+#define DARB_CHAINED_SCANS 1
+#endif
+
+__device__ __forceinline__ unsigned long long ld_relaxed64(const unsigned long long *p) {
+    return *reinterpret_cast<const volatile unsigned long long *>(p);
+}
+__device__ __forceinline__ void st_relaxed64(unsigned long long *p, unsigned long long v) {
+    *reinterpret_cast<volatile unsigned long long *>(p) = v;
+}
+
+// The next partition index from counter, for the whole CTA.
+__device__ __forceinline__ int claim_partition(uint32_t *counter, int *s_part) {
+    if (threadIdx.x == 0) *s_part = (int)atomicAdd(counter, 1u);
+    __syncthreads();
+    return *s_part;
+}
+
+// By the 32 lanes of warp 0: the sum over the partitions before `part` (whose own total is
+// `total`), 32 predecessors per round.  A predecessor not published after kSpinLimit polls sets
+// DARB_ERR_TIMEOUT in *status and ends the wait with the sum found so far.
+__device__ __forceinline__ unsigned long long chain_exclusive(unsigned long long *chain, int part,
+                                                              unsigned long long total, uint32_t *status) {
+    const int lane = threadIdx.x & 31;
+    if (part == 0) {
+        if (lane == 0) st_relaxed64(chain, kChainIncl | (total & kChainVal));
+        return 0ull;
+    }
+    if (lane == 0) st_relaxed64(chain + part, kChainOwn | (total & kChainVal));
+    unsigned long long excl = 0;
+    int p = part - 1, spins = 0, ns = 32;
+    while (p >= 0) {
+        const int idx = p - lane;  // lane l reads predecessor p - l; before partition 0: an inclusive 0
+        const unsigned long long w = idx >= 0 ? ld_relaxed64(chain + idx) : kChainIncl;
+        const uint32_t incl = __ballot_sync(0xffffffffu, (w & ~kChainVal) == kChainIncl);
+        const uint32_t ready = __ballot_sync(0xffffffffu, (w & ~kChainVal) != 0ull);
+        // the lanes up to the nearest inclusive prefix (all 32 when none is in this window)
+        const uint32_t upto = incl ? ((incl & (0u - incl)) << 1) - 1u : 0xffffffffu;
+        if ((ready & upto) != upto) {  // a predecessor has not published yet: poll again
+            if (++spins > kSpinLimit) {
+                if (lane == 0) atomicExch(status, (uint32_t)DARB_ERR_TIMEOUT);
+                break;
+            }
+            if (spins > 16) {
+                __nanosleep(ns);
+                ns = min(ns * 2, 512);
+            }
+            continue;
+        }
+        unsigned long long v = ((upto >> lane) & 1u) ? (w & kChainVal) : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        excl += v;
+        if (incl) break;
+        p -= 32;
+    }
+    if (lane == 0) st_relaxed64(chain + part, kChainIncl | ((excl + total) & kChainVal));
+    return excl;
+}
+
 // Exclusive scan of one value per thread over a CTA of NT threads.  s_warp holds NT/32 + 1
 // entries.  Returns the exclusive prefix; total receives the CTA sum.
 template <int NT, typename T>
@@ -272,6 +343,64 @@ k_splat_offsets(int n, const uint32_t *__restrict__ order, const uint32_t *__res
         if (o1 == M && (M - 1) / T < max_parts) bounds[(M - 1) / T].y = (uint32_t)(base + j);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) offs[n] = M;
+}
+
+// k_block_sums, k_scan_block_sums and k_splat_offsets in one pass: each CTA claims the next
+// kScanTile positions, scans their instance counts, takes their global offset from a chained scan
+// over the blocks before it, and writes the offsets and partition owners as k_splat_offsets
+// does.  Every visible splat owns at least one instance (the preprocessing culls a splat that
+// reaches no tile), so the block holding the last visible position n_vis - 1 holds the last
+// instance: it writes M (num, clamped to 32 bits; DARB_ERR_CAPACITY in status above capacity),
+// offs[n] = M and the owner of M's last partition.
+__global__ void __launch_bounds__(kScanThreads)
+k_splat_offsets_chained(int n, const uint32_t *__restrict__ order, const uint32_t *__restrict__ tiles,
+                        const uint32_t *__restrict__ n_vis, unsigned long long *chain, uint32_t *claim,
+                        uint32_t *__restrict__ num, uint32_t *status, unsigned long long capacity,
+                        uint32_t *__restrict__ offs, uint2 *__restrict__ bounds, uint32_t max_parts) {
+    pdl_entry();
+    __shared__ uint32_t s_off[kScanTile + 1];
+    __shared__ uint32_t s_warp[kScanThreads / 32 + 1];
+    __shared__ int s_part;
+    __shared__ unsigned long long s_g;
+    const int m = (int)min(*n_vis, (uint32_t)n);
+    const int part = claim_partition(claim, &s_part);
+    const int base = part * kScanTile;
+    if (m == 0) {  // no visible splat: no instance
+        if (part == 0 && threadIdx.x == 0) {
+            *num = 0u;
+            offs[n] = 0u;
+        }
+        return;
+    }
+    if (base >= m) return;  // culled positions only (uniform over the CTA; it publishes nothing, and
+                            // no block below m looks back past it)
+    const uint32_t total = cta_offsets(m, base, tiles, order, s_off, nullptr, s_warp);
+    if (threadIdx.x < 32) {
+        const unsigned long long e = chain_exclusive(chain, part, total, status);
+        if (threadIdx.x == 0) s_g = e;
+    }
+    __syncthreads();
+    const unsigned long long g = s_g;
+    const bool last = base + kScanTile >= m;
+    const unsigned long long M = g + total;  // the instance count, in the last block
+    if (last && threadIdx.x == 0) {
+        *num = M > 0xffffffffull ? 0xffffffffu : (uint32_t)M;
+        if (M > capacity) atomicExch(status, (uint32_t)DARB_ERR_CAPACITY);
+        offs[n] = (uint32_t)M;
+    }
+    const uint32_t gbase = (uint32_t)g;
+    constexpr uint32_t T = kSortTile;
+    for (int j = threadIdx.x; j < kScanTile; j += kScanThreads) {
+        if (base + j >= m) continue;
+        const uint32_t o0 = gbase + s_off[j];
+        offs[base + j] = o0;
+        const uint32_t o1 = gbase + (j + 1 < kScanTile ? s_off[j + 1] : total);
+        if (!bounds || o1 <= o0) continue;
+        for (uint32_t p = (o0 + T - 1) / T; p < (o1 + T - 1) / T && p < max_parts; ++p) bounds[p].x = (uint32_t)(base + j);
+        for (uint32_t p = (o0 + 1 + T - 1) / T - 1; p + 1 <= o1 / T && p < max_parts; ++p)
+            bounds[p].y = (uint32_t)(base + j);
+        if (last && base + j == m - 1 && (o1 - 1) / T < max_parts) bounds[(o1 - 1) / T].y = (uint32_t)(base + j);
+    }
 }
 
 // Largest s in [0, n) with offs[s] <= target (offs non-decreasing, offs[0] = 0), by warp 0 of
@@ -1232,6 +1361,83 @@ k_depth_compact(int n, const int *__restrict__ radius, const float *__restrict__
         if (s_h[i]) atomicAdd(&hist[i], s_h[i]);
 }
 
+// k_vis_count, k_scan_block_sums and k_depth_compact in one pass: each CTA claims the next
+// kScanTile block of splats, counts its visible ones, takes their offset from a chained scan over
+// the blocks before it, and writes their (depth bits, index) records and the digit histograms.
+// The block holding splat n - 1 writes the visible count.
+__global__ void __launch_bounds__(kScanThreads)
+k_depth_compact_chained(int n, const int *__restrict__ radius, const float *__restrict__ depth,
+                        unsigned long long *chain, uint32_t *claim, uint32_t *__restrict__ keys,
+                        uint32_t *__restrict__ ids0, PassSpec ps, uint32_t *__restrict__ hist,
+                        uint32_t *__restrict__ n_vis, uint32_t *status) {
+    pdl_entry();
+    static_assert(kScanItems == 8, "two 16-byte loads per thread");
+    __shared__ uint32_t s_warp[kScanThreads / 32 + 1];
+    __shared__ uint32_t s_h[kMaxPasses * 256];
+    __shared__ int s_part;
+    __shared__ unsigned long long s_base;
+    for (int i = threadIdx.x; i < ps.passes * 256; i += kScanThreads) s_h[i] = 0;  // ordered by the claim
+    const int part = claim_partition(claim, &s_part);
+    const int base = part * kScanTile;
+    const int i0 = base + (int)threadIdx.x * kScanItems;  // this thread's kScanItems consecutive splats
+    const int lane = threadIdx.x & 31;
+    int rad[kScanItems];
+    uint32_t key[kScanItems];
+    if (i0 + kScanItems <= n) {  // radius and depth are 16-byte aligned, i0 a multiple of 8
+        const int4 r0 = *reinterpret_cast<const int4 *>(radius + i0), r1 = *reinterpret_cast<const int4 *>(radius + i0 + 4);
+        const uint4 d0 = *reinterpret_cast<const uint4 *>(depth + i0), d1 = *reinterpret_cast<const uint4 *>(depth + i0 + 4);
+        rad[0] = r0.x; rad[1] = r0.y; rad[2] = r0.z; rad[3] = r0.w;
+        rad[4] = r1.x; rad[5] = r1.y; rad[6] = r1.z; rad[7] = r1.w;
+        key[0] = d0.x; key[1] = d0.y; key[2] = d0.z; key[3] = d0.w;
+        key[4] = d1.x; key[5] = d1.y; key[6] = d1.z; key[7] = d1.w;
+    } else {
+#pragma unroll
+        for (int j = 0; j < kScanItems; ++j) {
+            const bool valid = i0 + j < n;
+            rad[j] = valid ? radius[i0 + j] : 0;
+            key[j] = valid ? __float_as_uint(depth[i0 + j]) : 0u;
+        }
+    }
+    uint32_t nv = 0;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) nv += (i0 + j < n && rad[j] != 0) ? 1u : 0u;
+    uint32_t t;
+    const uint32_t ex = block_exclusive_scan<kScanThreads>(nv, s_warp, t);
+    if (threadIdx.x < 32) {
+        const unsigned long long e = chain_exclusive(chain, part, t, status);
+        if (threadIdx.x == 0) {
+            s_base = e;
+            if (base + kScanTile >= n) *n_vis = (uint32_t)(e + t);
+        }
+    }
+    __syncthreads();
+    uint32_t pv = (uint32_t)s_base + ex;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        const int i = i0 + j;
+        const bool valid = i < n, v = valid && rad[j] != 0;
+        if (v) {
+            keys[pv] = key[j];
+            ids0[pv] = (uint32_t)i;
+            ++pv;
+        }
+#pragma unroll
+        for (int p = 0; p < kMaxPasses; ++p) {  // digit histograms of the visible keys
+            if (p >= ps.passes) break;
+            const uint32_t d = v ? (key[j] >> ps.shift[p]) & ((1u << ps.bits[p]) - 1u) : 0xffffffffu;
+            if (ps.shift[p] < DARB_DEPTH_HIST_MATCH_SHIFT) {  // spread digits: rare collisions in a warp
+                if (v) atomicAdd(&s_h[p * 256 + d], 1u);
+            } else {  // exponent side: few distinct digits, so a warp's equal digits add once
+                const uint32_t peers = __match_any_sync(0xffffffffu, d);
+                if (v && lane == __ffs(peers) - 1) atomicAdd(&s_h[p * 256 + d], (uint32_t)__popc(peers));
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < ps.passes * 256; i += kScanThreads)
+        if (s_h[i]) atomicAdd(&hist[i], s_h[i]);
+}
+
 __global__ void __launch_bounds__(256)
 k_depth_keys(int n, const int *__restrict__ radius, const float *__restrict__ depth, uint32_t *__restrict__ keys) {
     pdl_entry();
@@ -1320,7 +1526,7 @@ uint64_t run_table_entries(uint64_t capacity) {
 
 struct Layout {
     size_t total;
-    size_t off[23];
+    size_t off[24];
 };
 
 // Offsets of the workspace regions.  Regions 0..9 are data; [zero_begin, zero_end) is zeroed per call.
@@ -1354,6 +1560,7 @@ Layout layout(int n, uint64_t capacity, int tiles_x, int tiles_y, int strategy, 
         put(20, 0);
         put(21, 0);
         put(22, 0);
+        put(23, 0);
         put(9, (size_t)kMaxPasses * 256 * 4);  // digit bases
         put(10, (size_t)kMaxPasses * 256 * 4); // --- zeroed from here: histograms
         put(11, (size_t)passes * parts_cap * 256 * 4);  // look-back
@@ -1383,7 +1590,9 @@ Layout layout(int n, uint64_t capacity, int tiles_x, int tiles_y, int strategy, 
         put(10, (size_t)2 * kMaxPasses * 256 * 4 + (size_t)(tiles_x + 1) * (tiles_y + 1) * 4);
         put(18, kPassOnesweep ? (size_t)passes * parts_cap * 256 * 4 : 0);  // tile-pass look-back
         put(19, kPassOnesweep ? (size_t)4 * parts_n * 256 * 4 : 0);         // depth-pass look-back
-        put(13, (size_t)(kMaxPasses * 2 + 2) * 4);  // onesweep partition counters, visible count, run-table fill
+        put(23, kPassOnesweep ? nb * 8 * 2 : 0);  // chained-scan words: the compaction's, the offsets'
+        // onesweep partition counters, visible count, run-table fill, the chained scans' claims
+        put(13, (size_t)(kMaxPasses * 2 + 4) * 4);
     }
     L.off[14] = b;
     L.total = b + 256;
@@ -1502,6 +1711,8 @@ cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int til
     uint32_t *block_sums = reinterpret_cast<uint32_t *>(at(6));
     auto *block_off = reinterpret_cast<unsigned long long *>(at(7));
     uint32_t *counters = reinterpret_cast<uint32_t *>(at(13));
+    // chained-scan words (zeroed with the counters): the compaction's nb, then the offsets' nb
+    unsigned long long *chains = reinterpret_cast<unsigned long long *>(at(23));
 
     if (strategy == DARB_SORT_KEYS64) {
         if (nb > 0) launch_k(k_block_sums, nb, kScanThreads, 0, st, n, proj.tiles_touched, nullptr, nullptr, block_sums);
@@ -1592,12 +1803,17 @@ cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int til
         const uint32_t *vin = nullptr;    // first pass: values are the splat indices
         if (kPassOnesweep) {
             uint32_t *nv = counters + 2 * kMaxPasses;
-            launch_k(k_vis_count, nb, kScanThreads, 0, st, n, proj.radius, block_sums);
-            launch_k(k_scan_block_sums, 1, 1024, 0, st, nb, block_sums, block_off, nv, out.status,
-                     (unsigned long long)n);
             uint32_t *dhist = reinterpret_cast<uint32_t *>(at(10)) + kMaxPasses * 256;
-            launch_k(k_depth_compact, nb, kScanThreads, 0, st, n, proj.radius, proj.depth, block_off, kbuf[0],
-                     vbuf[0], dps, dhist);
+            if (DARB_CHAINED_SCANS) {  // visible count, its scan and the compaction in one chained pass
+                launch_k(k_depth_compact_chained, nb, kScanThreads, 0, st, n, proj.radius, proj.depth, chains,
+                         counters + 2 * kMaxPasses + 2, kbuf[0], vbuf[0], dps, dhist, nv, out.status);
+            } else {
+                launch_k(k_vis_count, nb, kScanThreads, 0, st, n, proj.radius, block_sums);
+                launch_k(k_scan_block_sums, 1, 1024, 0, st, nb, block_sums, block_off, nv, out.status,
+                         (unsigned long long)n);
+                launch_k(k_depth_compact, nb, kScanThreads, 0, st, n, proj.radius, proj.depth, block_off, kbuf[0],
+                         vbuf[0], dps, dhist);
+            }
             n_vis = nv;
             n_vis_dev = nv;
             vin = vbuf[0];
@@ -1657,9 +1873,22 @@ cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int til
         }
         order = vin;
     }
-    // 2) scan of tiles_touched in depth order
-    if (nb > 0) launch_k(k_block_sums, nb, kScanThreads, 0, st, n, proj.tiles_touched, order, n_vis_dev, block_sums);
-    launch_k(k_scan_block_sums, 1, 1024, 0, st, nb, block_sums, block_off, out.num_instances, out.status, cap);
+    // 2) scan of tiles_touched in depth order (with the onesweep passes: chained, in step 4)
+    uint32_t *offs = reinterpret_cast<uint32_t *>(at(15));
+    uint2 *bounds = kPassOnesweep ? reinterpret_cast<uint2 *>(at(20)) : nullptr;
+    const uint32_t max_parts = (uint32_t)((capacity + kSortTile - 1) / kSortTile);
+    const bool chained = DARB_CHAINED_SCANS && kPassOnesweep && n_vis_dev;
+    if (chained) {
+        // 4, ahead) per-position offsets and owners, M and the capacity check in one chained pass
+        if (nb > 0)
+            launch_k(k_splat_offsets_chained, nb, kScanThreads, 0, st, n, order, proj.tiles_touched, n_vis_dev,
+                     chains + nb, counters + 2 * kMaxPasses + 3, out.num_instances, out.status, cap, offs, bounds,
+                     max_parts);
+    } else {
+        if (nb > 0)
+            launch_k(k_block_sums, nb, kScanThreads, 0, st, n, proj.tiles_touched, order, n_vis_dev, block_sums);
+        launch_k(k_scan_block_sums, 1, 1024, 0, st, nb, block_sums, block_off, out.num_instances, out.status, cap);
+    }
     TRY(cudaGetLastError());
     uint64_t grid = capacity;
     if (num_instances_host) {
@@ -1681,10 +1910,7 @@ cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int til
     // 4) per-position offsets, then the balanced duplication in depth order
     uint32_t *tk_a = reinterpret_cast<uint32_t *>(at(0)), *tv_a = reinterpret_cast<uint32_t *>(at(1));
     uint32_t *tk_b = reinterpret_cast<uint32_t *>(at(2)), *tv_b = reinterpret_cast<uint32_t *>(at(3));
-    uint32_t *offs = reinterpret_cast<uint32_t *>(at(15));
-    uint2 *bounds = kPassOnesweep ? reinterpret_cast<uint2 *>(at(20)) : nullptr;
-    const uint32_t max_parts = (uint32_t)((capacity + kSortTile - 1) / kSortTile);
-    if (nb > 0)
+    if (nb > 0 && !chained)
         launch_k(k_splat_offsets, nb, kScanThreads, 0, st, n, order, proj.tiles_touched, n_vis_dev, block_off,
                  out.num_instances,
                  offs, bounds, max_parts);

@@ -54,8 +54,8 @@ def test_clock_sampler_reports_throttle_reasons_and_falls_back_to_all_samples():
 
 def test_launch_count_per_training_step():
     # 1080p with 32-pixel tiles: 2040 tiles, 11 tile bits, 2 tile passes
-    assert bench.launches_per_step(0, 11) == 22  # the L1 loss taken in the compositing forward
-    assert bench.launches_per_step(0, 11, fused=False) == 27
+    assert bench.launches_per_step(0, 11) == 18  # the L1 loss taken in the compositing forward
+    assert bench.launches_per_step(0, 11, fused=False) == 23
     assert bench.launches_per_step(0, 17) == bench.launches_per_step(0, 11) + 1  # a third tile pass
     assert bench.launches_per_step(1, 11) == 1 + (1 + 6 + 6) + 2 + 2 + 1  # 64-bit keys: 6 passes
 

@@ -1619,7 +1619,7 @@ cudaError_t launch_tile_counts(int n, const uint32_t *order, const uint32_t *n_v
                 cudaFuncSetAttribute(k_tile_diff<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
             const int blocks = std::min((n + DARB_TILE_DIFF_THREADS - 1) / DARB_TILE_DIFF_THREADS,
-                                        DARB_TILE_DIFF_CTAS_PER_SM * 152);
+                                        DARB_TILE_DIFF_CTAS_PER_SM * kGridSms);
             launch_k(k_tile_diff<true>, blocks, DARB_TILE_DIFF_THREADS, smem, st, n, order, n_vis, proj.radius, proj.tile_rect,
                      proj.tile_runs, proj.mean2d, proj.conic_o, sc, rt, tiles_x, diff_size, diff);
         } else {
@@ -1747,7 +1747,7 @@ cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int til
         }
         uint32_t *hist = reinterpret_cast<uint32_t *>(at(10));
         uint32_t *dbase = reinterpret_cast<uint32_t *>(at(9));
-        const int hb = (int)std::min<uint64_t>((grid + 255) / 256, 152 * 8);
+        const int hb = (int)std::min<uint64_t>((grid + 255) / 256, kGridSms * 8);
         launch_k(k_sort_hist<uint64_t>, hb, 256, 0, st, ka, out.num_instances, cap, ps, hist);
         launch_k(k_hist_scan, passes, 256, 0, st, hist, dbase);
         TRY(cudaGetLastError());
@@ -1759,7 +1759,7 @@ cudaError_t launch_bin_sort(int n, const ProjectedIn &proj, int tiles_x, int til
             std::swap(ka, kb);
             std::swap(va, vb);
         }
-        const int rb = (int)std::min<uint64_t>((grid + 255) / 256, 152 * 16);
+        const int rb = (int)std::min<uint64_t>((grid + 255) / 256, kGridSms * 16);
         launch_k(k_ranges, rb, 256, 0, st, ka, out.num_instances, cap, out.ranges);
         return cudaGetLastError();
     }

@@ -39,6 +39,9 @@ inline void launch_k(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, c
     (void)cudaLaunchKernelEx(&cfg, kernel, static_cast<A &&>(args)...);
 }
 
+// SMs of a GB300 (2 dies x 76): the cap of the grid-stride launches is a multiple of it.
+constexpr int kGridSms = 152;
+
 constexpr float kAlphaMax = 0.99f;          // 3DGS alpha clamp (listings: min(0.99f, ...))
 constexpr float kAlphaMin = 1.0f / 255.0f;  // 3DGS: skip alpha < 1/255
 constexpr float kTMin = 0.0001f;            // 3DGS: stop before T (1 - alpha) < 1e-4

@@ -84,7 +84,7 @@ cudaError_t launch_psi_moment(const darb_kernel_params &kp, double *sums, cudaSt
     cudaError_t e = cudaMemsetAsync(sums, 0, 2 * sizeof(double), st);
     if (e != cudaSuccess) return e;
     const PsiKernel k{kp.kind, kp.base, (double)kp.xi, (double)kp.beta};
-    launch_k(k_psi_moment, 152 * 4, kPsiThreads, 0, st, k, std::sqrt((double)kp.q_max), sums);
+    launch_k(k_psi_moment, kGridSms * 4, kPsiThreads, 0, st, k, std::sqrt((double)kp.q_max), sums);
     return cudaGetLastError();
 }
 

@@ -124,7 +124,7 @@ k_adam_rows(long long count, float *__restrict__ p, const float *__restrict__ g,
 
 int grid_for(long long count) {
     long long b = (count + 255) / 256;
-    return (int)(b < 152 * 16 ? (b > 0 ? b : 1) : 152 * 16);
+    return (int)(b < kGridSms * 16 ? (b > 0 ? b : 1) : kGridSms * 16);
 }
 
 }  // namespace
@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(256) k_zero(ZeroRegion r0, ZeroRegion r1, Zero
 
 cudaError_t launch_zero(cudaStream_t st, void *p0, size_t b0, void *p1, size_t b1, void *p2, size_t b2) {
     const size_t words = (b0 + b1 + b2) / 16 + 1;
-    const int blocks = (int)std::min<size_t>((words + 255) / 256, 152 * 8);
+    const int blocks = (int)std::min<size_t>((words + 255) / 256, kGridSms * 8);
     launch_k(k_zero, blocks, 256, 0, st, ZeroRegion{p0, b0}, ZeroRegion{p1, b1}, ZeroRegion{p2, b2});
     return cudaGetLastError();
 }

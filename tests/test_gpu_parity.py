@@ -285,6 +285,35 @@ def test_empty_and_fully_culled_scenes():
         assert np.all(to_np(img.t_final) == 1.0)
 
 
+@pytest.mark.parametrize("n", [2047, 2048, 2049, 6145])
+@pytest.mark.parametrize("pattern", ["all", "last_block", "first_splat", "odd_blocks"])
+def test_bin_sort_at_scan_block_boundaries(n, pattern):
+    """The sort's scans run over blocks of 2048 splats (visible count and compaction) and of
+    2048 depth-ordered positions (instance offsets), each block taking its offset from the blocks
+    before it.  Lists against the oracle when the visible splats sit only in the last block, only
+    at splat 0, or in every other block (whole blocks contributing nothing), around one and three
+    block boundaries."""
+    cam = synth.pinhole((0.0, 0.0, 4.0), 64, 48, 60.0)
+    s = synth.uniform_cube_scene(n, seed=n % 97)
+    behind = np.ones(n, dtype=bool)
+    if pattern == "all":
+        behind[:] = False
+    elif pattern == "last_block":
+        behind[(n - 1) // 2048 * 2048:] = False
+    elif pattern == "first_splat":
+        behind[0] = False
+    else:
+        for b in range(0, n, 4096):
+            behind[b:b + 2048] = False
+    s.means[behind, 2] += 10.0  # behind the camera
+    r, sd, proj, bins, img = gpu_forward(s, cam, "half_cosine", 16)
+    ref = oracle.project(s, cam, oracle.kernel_params("half_cosine"), 16, True)
+    assert int((ref["culled"] == 0).sum()) == int((to_np(proj.radius) != 0).sum()) > 0
+    lists = oracle.build_lists(ref, cam, 16)
+    assert bins.M == int(ref["tiles"][ref["culled"] == 0].sum())
+    check_lists(bins, lists)
+
+
 def test_single_splat_covering_the_image():
     cam = synth.pinhole((0.0, 0.0, 2.0), 100, 60, 80.0, bg=(0.0, 0.0, 0.0))
     s = synth.uniform_cube_scene(1, seed=2, log_scale=(-0.3, -0.2))

@@ -28,6 +28,16 @@ constexpr int kSsimRb = 4;  // outputs per thread along the blur direction (regi
 constexpr int kSsimTaps = 2 * kSsimR + 1;
 constexpr float kSsimC1 = 0.01f * 0.01f;
 constexpr float kSsimC2 = 0.03f * 0.03f;
+constexpr int kStage = (kSsimIn * kSsimIn + kSsimThreads - 1) / kSsimThreads;  // halo elements per thread
+// Resident CTAs per SM both kernels are compiled for (0: the compiler's register count).
+#ifndef DARB_SSIM_MIN_CTAS
+#define DARB_SSIM_MIN_CTAS 0
+#endif
+#if DARB_SSIM_MIN_CTAS > 0
+#define DARB_SSIM_BOUNDS __launch_bounds__(kSsimThreads, DARB_SSIM_MIN_CTAS)
+#else
+#define DARB_SSIM_BOUNDS __launch_bounds__(kSsimThreads)
+#endif
 static_assert(kSsimTs % kSsimRb == 0 && (kSsimTs / kSsimRb) * kSsimTs == kSsimThreads, "one vertical group per thread");
 
 struct Window {
@@ -80,21 +90,35 @@ __device__ __forceinline__ void hblur(const Window &win, In in, float (&out)[NQ]
 
 // Forward: the five local moments by separable blurs (x along rows, then y along columns, each
 // thread kSsimRb consecutive outputs), then the derivative maps and the block sums.
-__global__ void __launch_bounds__(kSsimThreads)
+__global__ void DARB_SSIM_BOUNDS
 k_ssim_fwd(const float *__restrict__ x, const float *__restrict__ y, int W, int H, Window win,
            float *__restrict__ d_m, float *__restrict__ d_sxx, float *__restrict__ d_sxy, double *__restrict__ sums) {
     pdl_entry();
     __shared__ float sx[kSsimIn][kSsimIn + 1], sy[kSsimIn][kSsimIn + 1];
-    __shared__ float h[5][kSsimIn][kSsimTs];
+    __shared__ float h[5][kSsimIn][kSsimTs + 1];  // padded: a warp's row-pass stores hit 32 banks
     __shared__ float s_w[kSsimThreads / 32];
     const int x0 = blockIdx.x * kSsimTs, y0 = blockIdx.y * kSsimTs;
     const size_t plane = (size_t)W * H, off = (size_t)blockIdx.z * plane;
-    for (int i = threadIdx.x; i < kSsimIn * kSsimIn; i += kSsimThreads) {
-        const int r = i / kSsimIn, c = i - r * kSsimIn;
-        const int gy = y0 - kSsimR + r, gx = x0 - kSsimR + c;
-        const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
-        sx[r][c] = in ? x[off + (size_t)gy * W + gx] : 0.0f;
-        sy[r][c] = in ? y[off + (size_t)gy * W + gx] : 0.0f;
+    {  // every load of the halo tile issued before the first store
+        float vx[kStage], vy[kStage];
+#pragma unroll
+        for (int u = 0; u < kStage; ++u) {
+            const int i = threadIdx.x + u * kSsimThreads;
+            const int r = i / kSsimIn, c = i - r * kSsimIn;
+            const int gy = y0 - kSsimR + r, gx = x0 - kSsimR + c;
+            const bool in = i < kSsimIn * kSsimIn && gx >= 0 && gx < W && gy >= 0 && gy < H;
+            vx[u] = in ? x[off + (size_t)gy * W + gx] : 0.0f;
+            vy[u] = in ? y[off + (size_t)gy * W + gx] : 0.0f;
+        }
+#pragma unroll
+        for (int u = 0; u < kStage; ++u) {
+            const int i = threadIdx.x + u * kSsimThreads;
+            if (i < kSsimIn * kSsimIn) {
+                const int r = i / kSsimIn, c = i - r * kSsimIn;
+                sx[r][c] = vx[u];
+                sy[r][c] = vy[u];
+            }
+        }
     }
     __syncthreads();
     // along x: item = (row, group of kSsimRb columns)
@@ -133,11 +157,12 @@ k_ssim_fwd(const float *__restrict__ x, const float *__restrict__ y, int W, int 
         const float A2 = 2.0f * (m[4][i] - mx * my) + kSsimC2;
         const float B1 = mx * mx + my * my + kSsimC1;
         const float B2 = (m[2][i] - mx * mx) + (m[3][i] - my * my) + kSsimC2;
-        const float iB = 1.0f / (B1 * B2);
+        const float iB1 = __frcp_rn(B1), iB2 = __frcp_rn(B2);  // two reciprocals, no division
+        const float iB = iB1 * iB2;
         const float sv = A1 * A2 * iB;
         const size_t p = off + (size_t)gy * W + gx;
-        d_m[p] = 2.0f * my * (A2 - A1) * iB - 2.0f * mx * sv * (1.0f / B1 - 1.0f / B2);
-        d_sxx[p] = -sv / B2;
+        d_m[p] = 2.0f * my * (A2 - A1) * iB - 2.0f * mx * sv * (iB1 - iB2);
+        d_sxx[p] = -sv * iB2;
         d_sxy[p] = 2.0f * A1 * iB;
         ssim_sum += sv;
         l1_sum += fabsf(sx[r + kSsimR][c + kSsimR] - sy[r + kSsimR][c + kSsimR]);
@@ -153,13 +178,13 @@ k_ssim_fwd(const float *__restrict__ x, const float *__restrict__ y, int W, int 
 
 // Backward: blurs the three derivative maps (the window is symmetric, so the blur is its own
 // adjoint) with the same blocking, then forms dL/dx.
-__global__ void __launch_bounds__(kSsimThreads)
+__global__ void DARB_SSIM_BOUNDS
 k_ssim_bwd(const float *__restrict__ x, const float *__restrict__ y, int W, int H, Window win,
            const float *__restrict__ d_m, const float *__restrict__ d_sxx, const float *__restrict__ d_sxy,
            float lam, const double *__restrict__ sums, float *__restrict__ dL, float *__restrict__ loss) {
     pdl_entry();
     __shared__ float sa[3][kSsimIn][kSsimIn + 1];
-    __shared__ float h[3][kSsimIn][kSsimTs];
+    __shared__ float h[3][kSsimIn][kSsimTs + 1];
     const int x0 = blockIdx.x * kSsimTs, y0 = blockIdx.y * kSsimTs;
     const size_t plane = (size_t)W * H, off = (size_t)blockIdx.z * plane;
     const double n = 3.0 * (double)plane;
@@ -169,14 +194,28 @@ k_ssim_bwd(const float *__restrict__ x, const float *__restrict__ y, int W, int 
         loss[0] = (float)((1.0 - lam) * l1 + lam * (1.0 - ssim));
         loss[1] = (float)ssim;
     }
-    for (int i = threadIdx.x; i < kSsimIn * kSsimIn; i += kSsimThreads) {
-        const int r = i / kSsimIn, c = i - r * kSsimIn;
-        const int gy = y0 - kSsimR + r, gx = x0 - kSsimR + c;
-        const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
-        const size_t p = off + (size_t)gy * W + gx;
-        sa[0][r][c] = in ? d_m[p] : 0.0f;
-        sa[1][r][c] = in ? d_sxx[p] : 0.0f;
-        sa[2][r][c] = in ? d_sxy[p] : 0.0f;
+    {  // every load of the three halo tiles issued before the first store
+        float va[kStage][3];
+#pragma unroll
+        for (int u = 0; u < kStage; ++u) {
+            const int i = threadIdx.x + u * kSsimThreads;
+            const int r = i / kSsimIn, c = i - r * kSsimIn;
+            const int gy = y0 - kSsimR + r, gx = x0 - kSsimR + c;
+            const bool in = i < kSsimIn * kSsimIn && gx >= 0 && gx < W && gy >= 0 && gy < H;
+            const size_t p = off + (size_t)gy * W + gx;
+            va[u][0] = in ? d_m[p] : 0.0f;
+            va[u][1] = in ? d_sxx[p] : 0.0f;
+            va[u][2] = in ? d_sxy[p] : 0.0f;
+        }
+#pragma unroll
+        for (int u = 0; u < kStage; ++u) {
+            const int i = threadIdx.x + u * kSsimThreads;
+            if (i < kSsimIn * kSsimIn) {
+                const int r = i / kSsimIn, c = i - r * kSsimIn;
+#pragma unroll
+                for (int q = 0; q < 3; ++q) sa[q][r][c] = va[u][q];
+            }
+        }
     }
     __syncthreads();
     constexpr int kGroups = kSsimTs / kSsimRb;

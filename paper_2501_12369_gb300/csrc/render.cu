@@ -87,6 +87,12 @@ struct BwdShape {
 #define DARB_FWD_PACK 1
 #endif
 
+// The forward's branch-free body on pairs of a thread's pixels with the packed two-lane FP32
+// instructions of sm_100+ (1), or one pixel at a time (0).
+#ifndef DARB_FWD_PAIR
+#define DARB_FWD_PAIR 1
+#endif
+
 template <int TILE>
 struct FwdSmem {
 #if DARB_FWD_PACK
@@ -152,6 +158,16 @@ __device__ __forceinline__ void render_tile_fwd(int tile, FwdSmem<TILE> &sm, con
         count[k] = lastp[k] = 0;
         done[k] = !(px < W && py < H);
     }
+    // pixels 2p and 2p + 1 as the lanes of one pair (the packed FP32 instructions)
+    constexpr bool kPair = DARB_FWD_PAIR && DARB_FWD_SELECT && PIX % 2 == 0;
+    constexpr int NPP = PIX / 2 > 0 ? PIX / 2 : 1;
+    float2 T2[NPP], C0p[NPP], C1p[NPP], C2p[NPP], nfpy[NPP];
+#pragma unroll
+    for (int pp = 0; pp < NPP; ++pp) {
+        T2[pp] = make_float2(1.0f, 1.0f);
+        C0p[pp] = C1p[pp] = C2p[pp] = make_float2(0.0f, 0.0f);
+        nfpy[pp] = make_float2(-fpy[(2 * pp) % PIX], -fpy[(2 * pp + 1) % PIX]);
+    }
     for (int b0 = start; b0 < end; b0 += NT) {
         bool all_done = true;
 #pragma unroll
@@ -192,6 +208,46 @@ __device__ __forceinline__ void render_tile_fwd(int tile, FwdSmem<TILE> &sm, con
 #endif
             const float dx = __fsub_rn(xy.x, fpx);
             bool any_live = false;
+            if constexpr (kPair) {
+                // the scalar branch-free body below on pairs of pixels: every paired operation
+                // rounds per lane as its scalar form (__fmul_rn, __fmaf_rn, 1 - alpha), so the
+                // support decisions and the sums are the same bits
+                const uint32_t pos = (uint32_t)(b0 - start + j + 1);
+                const float2 dx2 = make_float2(dx, dx), y2 = make_float2(xy.y, xy.y);
+                const float2 A2 = make_float2(co.x, co.x), B2 = make_float2(co.y, co.y);
+                const float2 Cc2 = make_float2(co.z, co.z), o2 = make_float2(co.w, co.w);
+                const float2 one2 = make_float2(1.0f, 1.0f);
+#pragma unroll
+                for (int pp = 0; pp < NPP; ++pp) {
+                    const int k0 = 2 * pp, k1 = 2 * pp + 1;
+                    if (done[k0] && done[k1]) continue;
+                    any_live = true;
+                    const float2 dy = __fadd2_rn(y2, nfpy[pp]);
+                    const float2 g = __ffma2_rn(A2, dx2, __fmul2_rn(B2, dy));
+                    const float2 q = __ffma2_rn(dx2, g, __fmul2_rn(__fmul2_rn(Cc2, dy), dy));
+                    const float2 of = __fmul2_rn(o2, make_float2(kernel_F<KIND>(q.x, ks), kernel_F<KIND>(q.y, ks)));
+                    const float2 alpha = make_float2(fminf(kAlphaMax, of.x), fminf(kAlphaMax, of.y));
+                    const float2 Tn = __fmul2_rn(T2[pp], __fadd2_rn(one2, make_float2(-alpha.x, -alpha.y)));
+                    const bool use0 = !done[k0] && in_support_lim(q.x, qlim) && alpha.x >= kAlphaMin;
+                    const bool use1 = !done[k1] && in_support_lim(q.y, qlim) && alpha.y >= kAlphaMin;
+                    const bool stop0 = Tn.x < kTMin, stop1 = Tn.y < kTMin;
+                    if (use0 && stop0) done[k0] = true;
+                    if (use1 && stop1) done[k1] = true;
+                    const bool blend0 = use0 && !stop0, blend1 = use1 && !stop1;
+                    const float2 wp = __fmul2_rn(alpha, T2[pp]);
+                    const float2 w = make_float2(blend0 ? wp.x : 0.0f, blend1 ? wp.y : 0.0f);
+                    C0p[pp] = __ffma2_rn(make_float2(r0, r0), w, C0p[pp]);
+                    C1p[pp] = __ffma2_rn(make_float2(r1, r1), w, C1p[pp]);
+                    C2p[pp] = __ffma2_rn(make_float2(r2, r2), w, C2p[pp]);
+                    T2[pp] = make_float2(blend0 ? Tn.x : T2[pp].x, blend1 ? Tn.y : T2[pp].y);
+                    count[k0] += blend0 ? 1u : 0u;
+                    count[k1] += blend1 ? 1u : 0u;
+                    lastp[k0] = blend0 ? pos : lastp[k0];
+                    lastp[k1] = blend1 ? pos : lastp[k1];
+                }
+                if (!any_live) break;
+                continue;
+            }
 #if DARB_FWD_SELECT
             const uint32_t pos = (uint32_t)(b0 - start + j + 1);
 #pragma unroll
@@ -239,6 +295,19 @@ __device__ __forceinline__ void render_tile_fwd(int tile, FwdSmem<TILE> &sm, con
             }
 #endif
             if (!any_live) break;
+        }
+    }
+    if constexpr (kPair) {
+#pragma unroll
+        for (int pp = 0; pp < NPP; ++pp) {
+            T[2 * pp] = T2[pp].x;
+            T[2 * pp + 1] = T2[pp].y;
+            C0[2 * pp] = C0p[pp].x;
+            C0[2 * pp + 1] = C0p[pp].y;
+            C1[2 * pp] = C1p[pp].x;
+            C1[2 * pp + 1] = C1p[pp].y;
+            C2[2 * pp] = C2p[pp].x;
+            C2[2 * pp + 1] = C2p[pp].y;
         }
     }
     const size_t plane = (size_t)W * H;

@@ -283,13 +283,19 @@ struct PreGeom {
     int radius, idx;
 };
 
-// Compiled for 6 resident CTAs per SM (40 registers, 1536 threads): the projection is
-// latency-bound, and a register cap raised occupancy from the compiler's choice (0.172 ->
-// 0.153 ms at 3M splats / 1080p with 8 CTAs, 0.157 with 6).  Since the SH prefetch and the
-// two-phase queue, 6 CTAs measure 0.142 ms against 0.145 at 8 (32 registers, which spill)
-// and 0.150 with no cap.  DARB_PRE_MIN_CTAS=0 leaves the register count to the compiler.
+// Compiled for 5 resident CTAs per SM (48 registers, 1280 threads, each with DARB_PRE_SPT = 2
+// splats): the projection is latency-bound, and a register cap raised occupancy from the
+// compiler's choice (0.172 -> 0.153 ms at 3M splats / 1080p with 8 CTAs of one splat per thread).
+// With two splats per thread, 5 CTAs measure 0.136 ms against 0.145 at 6 (40 registers, which
+// spill) and 0.142 at 4; one splat per thread at 6 CTAs: 0.145.  DARB_PRE_MIN_CTAS=0 leaves the
+// register count to the compiler.
 #ifndef DARB_PRE_MIN_CTAS
-#define DARB_PRE_MIN_CTAS 6
+#define DARB_PRE_MIN_CTAS 5
+#endif
+// Splats per thread of k_preprocess: with 2, a thread issues both splats' loads before it
+// projects the first.
+#ifndef DARB_PRE_SPT
+#define DARB_PRE_SPT 2
 #endif
 #if DARB_PRE_MIN_CTAS > 0
 #define DARB_PRE_BOUNDS __launch_bounds__(kPreThreads, DARB_PRE_MIN_CTAS)
@@ -297,60 +303,12 @@ struct PreGeom {
 #define DARB_PRE_BOUNDS __launch_bounds__(kPreThreads)
 #endif
 
+// Phase 2 of k_preprocess for one queued (projected, not culled) splat: member tiles by row
+// runs, the records, the SH colour.
 template <int DEG>
-__global__ void DARB_PRE_BOUNDS
-k_preprocess(int n, const float *__restrict__ means, const float *__restrict__ scales,
-             const float4 *__restrict__ quats, const float *__restrict__ opac,
-             const float *__restrict__ sh, Cam cam, float psi, int tile, float qmax, ProjectedOut out) {
-    pdl_entry();
-    __shared__ PreGeom s_q[kPreThreads];
-    __shared__ int s_n;
-    if (threadIdx.x == 0) s_n = 0;
-    __syncthreads();
-    {
-        const int i = blockIdx.x * kPreThreads + threadIdx.x;
-        bool vis = false;
-        Geom g;
-        if (i < n) {
-            const float m[3] = {__ldg(means + 3 * (size_t)i), __ldg(means + 3 * (size_t)i + 1),
-                                __ldg(means + 3 * (size_t)i + 2)};
-            const float s[3] = {__ldg(scales + 3 * (size_t)i), __ldg(scales + 3 * (size_t)i + 1),
-                                __ldg(scales + 3 * (size_t)i + 2)};
-            vis = project_fixed(m, s, __ldg(quats + i), cam, psi, tile, g);
-        }
-        const uint32_t vm = __ballot_sync(0xffffffffu, vis);
-        int base = 0;
-        if ((threadIdx.x & 31) == 0 && vm) base = atomicAdd(&s_n, __popc(vm));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (vis) {
-            PreGeom &q = s_q[base + __popc(vm & ((1u << (threadIdx.x & 31)) - 1u))];
-            q.tz = g.t[2];
-            q.A = g.A;
-            q.B = g.B;
-            q.C = g.C;
-            q.u0 = g.u0;
-            q.u1 = g.u1;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) q.rect[k] = g.rect[k];
-            q.radius = g.radius;
-            q.idx = i;
-        } else if (i < n) {
-            write_culled(out, i);
-        }
-#if DARB_PRE_SH_PREFETCH
-        if (vis) {  // start the SH row of a queued splat on its way to L2 during the projection of the rest
-            const char *row = reinterpret_cast<const char *>(sh + (size_t)i * 3 * (DEG + 1) * (DEG + 1));
-            constexpr int kRowBytes = 12 * (DEG + 1) * (DEG + 1);
-#pragma unroll
-            for (int o = 0; o < kRowBytes + 127; o += 128)
-                asm volatile("prefetch.global.L2 [%0];" ::"l"(row + min(o, kRowBytes - 1)));
-        }
-#endif
-    }
-    __syncthreads();
-    const int nq = s_n;
-    if ((int)threadIdx.x >= nq) return;
-    const PreGeom g = s_q[threadIdx.x];
+__device__ __forceinline__ void preprocess_queued(const PreGeom &g, const float *__restrict__ means,
+                                                  const float *__restrict__ opac, const float *__restrict__ sh,
+                                                  const Cam &cam, int tile, float qmax, const ProjectedOut &out) {
     const int i = g.idx;
     const SpanCtx sc = make_span_ctx(qmax, tile, cam.W, cam.H);
     const int4 r = make_int4(g.rect[0], g.rect[1], g.rect[2], g.rect[3]);
@@ -401,6 +359,78 @@ k_preprocess(int n, const float *__restrict__ means, const float *__restrict__ s
     }
     out.clamped[i] = cl;
 }
+
+template <int DEG>
+__global__ void DARB_PRE_BOUNDS
+k_preprocess(int n, const float *__restrict__ means, const float *__restrict__ scales,
+             const float4 *__restrict__ quats, const float *__restrict__ opac,
+             const float *__restrict__ sh, Cam cam, float psi, int tile, float qmax, ProjectedOut out) {
+    pdl_entry();
+    constexpr int SPT = DARB_PRE_SPT;
+    __shared__ PreGeom s_q[kPreThreads * SPT];
+    __shared__ int s_n;
+    if (threadIdx.x == 0) s_n = 0;
+    __syncthreads();
+    {
+        // the loads of every splat of the thread first, so that the later splats' loads are in
+        // flight while the first is projected
+        const int i0 = blockIdx.x * kPreThreads * SPT + (int)threadIdx.x;
+        float m[SPT][3], sc3[SPT][3];
+        float4 qr[SPT];
+#pragma unroll
+        for (int u = 0; u < SPT; ++u) {
+            const int i = i0 + u * kPreThreads;
+            if (i < n) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    m[u][c] = __ldg(means + 3 * (size_t)i + c);
+                    sc3[u][c] = __ldg(scales + 3 * (size_t)i + c);
+                }
+                qr[u] = __ldg(quats + i);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < SPT; ++u) {
+            const int i = i0 + u * kPreThreads;
+            bool vis = false;
+            Geom g;
+            if (i < n) vis = project_fixed(m[u], sc3[u], qr[u], cam, psi, tile, g);
+            const uint32_t vm = __ballot_sync(0xffffffffu, vis);
+            int base = 0;
+            if ((threadIdx.x & 31) == 0 && vm) base = atomicAdd(&s_n, __popc(vm));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (vis) {
+                PreGeom &q = s_q[base + __popc(vm & ((1u << (threadIdx.x & 31)) - 1u))];
+                q.tz = g.t[2];
+                q.A = g.A;
+                q.B = g.B;
+                q.C = g.C;
+                q.u0 = g.u0;
+                q.u1 = g.u1;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) q.rect[k] = g.rect[k];
+                q.radius = g.radius;
+                q.idx = i;
+            } else if (i < n) {
+                write_culled(out, i);
+            }
+#if DARB_PRE_SH_PREFETCH
+            if (vis) {  // start the SH row of a queued splat on its way to L2 during the projection of the rest
+                const char *row = reinterpret_cast<const char *>(sh + (size_t)i * 3 * (DEG + 1) * (DEG + 1));
+                constexpr int kRowBytes = 12 * (DEG + 1) * (DEG + 1);
+#pragma unroll
+                for (int o = 0; o < kRowBytes + 127; o += 128)
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(row + min(o, kRowBytes - 1)));
+            }
+#endif
+        }
+    }
+    __syncthreads();
+    const int nq = s_n;
+    for (int e = threadIdx.x; e < nq; e += kPreThreads) preprocess_queued<DEG>(s_q[e], means, opac, sh, cam, tile, qmax,
+                                                                               out);
+}
+
 
 // ---------------------------------------------------------------------------
 // Backward of the preprocessing.  Recomputes the forward quantities in FP32 and
@@ -775,7 +805,7 @@ k_preprocess_bwd_adam(int n, darb_train_params P, darb_adam_state A, AdamConsts 
 cudaError_t launch_preprocess(int n, const darb_splats &sp, const Cam &cam, float psi, int tile, float qmax,
                               const ProjectedOut &out, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
-    const int threads = kPreThreads, blocks = (n + threads - 1) / threads;
+    const int threads = kPreThreads, blocks = (n + threads * DARB_PRE_SPT - 1) / (threads * DARB_PRE_SPT);
     const float4 *q = reinterpret_cast<const float4 *>(sp.quats);
     switch (sp.sh_degree) {
     case 0: launch_k(k_preprocess<0>, blocks, threads, 0, st, n, sp.means, sp.scales, q, sp.opacities, sp.sh,

@@ -59,6 +59,9 @@ struct Cam {
     int W, H;
     float bg[3];
     float campos[3];  // -R^T t, for the SH viewing direction
+    // the Jacobian's guard band, kGuardBand * W / (2 fx) and * H / (2 fy): the same FP32
+    // operations a splat would take, done once per camera
+    float limx, limy;
 };
 
 inline Cam make_cam(const darb_camera &c) {
@@ -72,6 +75,12 @@ inline Cam make_cam(const darb_camera &c) {
         for (int r = 0; r < 3; ++r) s -= (double)c.viewmat[4 * r + j] * (double)c.viewmat[4 * r + 3];
         k.campos[j] = (float)s;
     }
+    // IEEE FP32 on the host as on the device: 2 fx is exact, then one rounded division and one
+    // rounded product (no contraction applies)
+    const float tx2 = 2.0f * c.fx, ty2 = 2.0f * c.fy;
+    const float qx = (float)c.width / tx2, qy = (float)c.height / ty2;
+    k.limx = kGuardBand * qx;
+    k.limy = kGuardBand * qy;
     return k;
 }
 

@@ -195,8 +195,7 @@ __device__ __forceinline__ bool project_fixed(const float m[3], const float s[3]
 
     const float fx = cam.fx, fy = cam.fy;
     const float txtz = __fdiv_rn(t[0], tz), tytz = __fdiv_rn(t[1], tz);
-    const float limx = __fmul_rn(kGuardBand, __fdiv_rn((float)cam.W, __fmul_rn(2.0f, fx)));
-    const float limy = __fmul_rn(kGuardBand, __fdiv_rn((float)cam.H, __fmul_rn(2.0f, fy)));
+    const float limx = cam.limx, limy = cam.limy;
     const float txc = __fmul_rn(fminf(limx, fmaxf(-limx, txtz)), tz);
     const float tyc = __fmul_rn(fminf(limy, fmaxf(-limy, tytz)), tz);
     const float tz2 = __fmul_rn(tz, tz);
@@ -239,10 +238,11 @@ __device__ __forceinline__ bool project_fixed(const float m[3], const float s[3]
     const float y0 = fmaxf(ceilf(__fsub_rn(__fsub_rn(u1, Rf), 0.5f)), 0.0f);
     const float y1 = fminf(floorf(__fsub_rn(__fadd_rn(u1, Rf), 0.5f)), (float)(cam.H - 1));
     if (!(x0 <= x1) || !(y0 <= y1)) return false;
-    g.rect[0] = (int)x0 / tile;
-    g.rect[1] = (int)y0 / tile;
-    g.rect[2] = (int)x1 / tile;
-    g.rect[3] = (int)y1 / tile;
+    const int tsh = __ffs(tile) - 1;  // tile is 8, 16 or 32 and the bounds are >= 0: a shift divides
+    g.rect[0] = (int)x0 >> tsh;
+    g.rect[1] = (int)y0 >> tsh;
+    g.rect[2] = (int)x1 >> tsh;
+    g.rect[3] = (int)y1 >> tsh;
     g.radius = (int)fminf(Rf, 16777216.0f);
     g.u0 = u0;
     g.u1 = u1;
@@ -473,8 +473,7 @@ __device__ __forceinline__ void splat_backward(int i, const float *__restrict__ 
     // Jacobian; the guard-band decision repeats the forward's FP32 sequence
     const float fx = cam.fx, fy = cam.fy;
     const float txtz = __fdiv_rn(tx, tz), tytz = __fdiv_rn(ty, tz);
-    const float limx = __fmul_rn(kGuardBand, __fdiv_rn((float)cam.W, __fmul_rn(2.0f, fx)));
-    const float limy = __fmul_rn(kGuardBand, __fdiv_rn((float)cam.H, __fmul_rn(2.0f, fy)));
+    const float limx = cam.limx, limy = cam.limy;
     const bool clx = (txtz < -limx) || (txtz > limx), cly = (tytz < -limy) || (tytz > limy);
     const float Lx = txtz < 0.f ? -limx : limx, Ly = tytz < 0.f ? -limy : limy;
     const float txc = clx ? Lx * tz : tx, tyc = cly ? Ly * tz : ty;

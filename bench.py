@@ -187,6 +187,9 @@ class TrainStep:
                                       d._p(self.sh), self.n, self.sh_degree)
         self.s_proj = self.proj.struct()
         self.s_img = self.img.struct()
+        # the training step's forward: the loss from the colours in registers, so no image and no
+        # contributor counts are written (the backward reads t_final and last)
+        self.s_img_train = d.darb_image(None, d._p(self.img.t_final), d._p(self.img.last), None)
         self.s_grads = self.grads.struct()
         self.s_params = d.darb_train_params(d._p(self.means), d._p(self.log_scales), d._p(self.quats),
                                             d._p(self.logits), d._p(self.sh), d._p(self.scales), d._p(self.opac),
@@ -275,8 +278,8 @@ class TrainStep:
         self._project_and_sort(c, rec)
         if self.dssim_lambda is None:
             d._check(L.darb_render_fwd_l1(ctypes.byref(self.s_proj), ctypes.byref(self.s_bins), c, self.kp_ref,
-                                          self.tile, ctypes.byref(self.s_img), d._p(self.target), d._p(self.dL),
-                                          d._p(self.loss), st), "render_fwd_l1")
+                                          self.tile, ctypes.byref(self.s_img_train), d._p(self.target),
+                                          d._p(self.dL), d._p(self.loss), st), "render_fwd_l1")
         else:
             d._check(L.darb_render_fwd(ctypes.byref(self.s_proj), ctypes.byref(self.s_bins), c, self.kp_ref,
                                        self.tile, ctypes.byref(self.s_img), st), "render_fwd")

@@ -265,10 +265,11 @@ darb_status darb_render_fwd(const darb_projected *proj, const darb_binning *bins
 
 /* Step 4 with the L1 image loss of Sec. 4.2 taken in the same kernel: darb_render_fwd, then
  * for every pixel and channel dL_dimage = sign(C - target) / (3 W H) and *loss = the mean of
- * |C - target|, while the colour is still in registers (the image is written too).  target,
- * dL_dimage: device [3][H][W]; loss: device [1], zeroed by the call, then accumulated (the
- * order of its FP32 additions varies from run to run; dL_dimage and every image output equal
- * darb_render_fwd + darb_l1_loss bit for bit). */
+ * |C - target|, while the colour is still in registers.  target, dL_dimage: device
+ * [3][H][W]; loss: device [1], zeroed by the call, then accumulated (the order of its FP32
+ * additions varies from run to run; dL_dimage and every image output equal darb_render_fwd +
+ * darb_l1_loss bit for bit).  out->image and out->n_contrib may be NULL (not written): a
+ * training step needs only the loss, its gradient, and t_final and last for the backward. */
 darb_status darb_render_fwd_l1(const darb_projected *proj, const darb_binning *bins,
                                const darb_camera *cam, const darb_kernel_params *kparams,
                                int32_t tile, const darb_image *out, const float *target,

@@ -214,8 +214,7 @@ darb_status darb_render_fwd_l1(const darb_projected *proj, const darb_binning *b
                                const darb_kernel_params *kparams, int32_t tile, const darb_image *out,
                                const float *target, float *dL_dimage, float *loss, darb_stream stream) {
     if (!valid_projected_or_empty(proj) || !bins || !bins->ranges || !valid_camera(cam) || !valid_kernel(kparams) ||
-        !valid_tile(tile) || !out || !out->image || !out->t_final || !out->last || !out->n_contrib || !target ||
-        !dL_dimage || !loss)
+        !valid_tile(tile) || !out || !out->t_final || !out->last || !target || !dL_dimage || !loss)
         return DARB_ERR_INVALID_ARG;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     DARB_CUDA_TRY(launch_zero(st, loss, sizeof(float)));

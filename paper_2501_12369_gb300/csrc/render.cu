@@ -324,7 +324,7 @@ __device__ __forceinline__ void render_tile_fwd(int tile, FwdSmem<TILE> &sm, con
         const float c[3] = {fmaf(T[k], o.bg.r, C0[k]), fmaf(T[k], o.bg.g, C1[k]), fmaf(T[k], o.bg.b, C2[k])};
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) {
-            o.image[ch * plane + pix] = c[ch];
+            if (o.image) o.image[ch * plane + pix] = c[ch];
             if constexpr (L1) {
                 const float d = c[ch] - l1.target[ch * plane + pix];
                 l1.dL[ch * plane + pix] = d > 0.0f ? l1.inv_count : (d < 0.0f ? -l1.inv_count : 0.0f);

@@ -423,11 +423,13 @@ def darb_render_fwd(proj: Projected, bins: Binning, cam, kparams, tile=16, out: 
 
 def darb_render_fwd_l1(proj: Projected, bins: Binning, cam, kparams, tile, target, out: ImageOut | None = None,
                        dL_dimage=None, loss=None, stream=None):
-    """Forward with the L1 loss in its epilogue; returns (image outputs, dL_dimage, loss[1])."""
+    """Forward with the L1 loss in its epilogue; returns (image outputs, dL_dimage, loss[1]).
+    out.image and out.n_contrib may be None (not written)."""
     out = ImageOut.empty(cam.width, cam.height, proj.depth.device) if out is None else out
-    dL_dimage = torch.empty_like(out.image) if dL_dimage is None else dL_dimage
-    loss = torch.empty(1, dtype=torch.float32, device=out.image.device) if loss is None else loss
-    assert target.is_contiguous() and target.dtype == torch.float32 and tuple(target.shape) == tuple(out.image.shape)
+    dL_dimage = torch.empty_like(target) if dL_dimage is None else dL_dimage
+    loss = torch.empty(1, dtype=torch.float32, device=target.device) if loss is None else loss
+    assert target.is_contiguous() and target.dtype == torch.float32
+    assert tuple(target.shape) == (3, cam.height, cam.width)
     pr, b, c, o = proj.struct(), bins.struct(), camera(cam), out.struct()
     _check(lib().darb_render_fwd_l1(ctypes.byref(pr), ctypes.byref(b), ctypes.byref(c), ctypes.byref(kparams),
                                     int(tile), ctypes.byref(o), _p(target), _p(dL_dimage), _p(loss), _stream(stream)),

@@ -147,6 +147,21 @@ def test_forward_with_l1_equals_forward_then_l1(kernel, tile):
         assert abs(float(loss2[0]) - ref) <= 1e-5 * ref
 
 
+def test_forward_with_l1_without_image_and_counts():
+    """darb_render_fwd_l1 with the image and the contributor counts left out (what a training
+    step needs): t_final, last and the loss gradient as with every output, bit for bit."""
+    s, cam = synth.cluster_scene(20000, seed=6), synth.fibonacci_cameras(16, 6.0, 333, 207, 260.0)[5]
+    r, sd, proj, bins, img = gpu_forward(s, cam, "half_cosine", 32)
+    target = torch.from_numpy(synth.random_target(cam.height, cam.width, seed=5)).cuda()
+    full, dL, loss = darb.darb_render_fwd_l1(proj, bins, cam, r.kparams, 32, target)
+    lean = darb.ImageOut(None, torch.empty_like(full.t_final), torch.empty_like(full.last), None)
+    _, dL2, loss2 = darb.darb_render_fwd_l1(proj, bins, cam, r.kparams, 32, target, out=lean)
+    torch.cuda.synchronize()
+    assert torch.equal(full.t_final, lean.t_final) and torch.equal(full.last, lean.last)
+    assert torch.equal(dL, dL2)
+    assert abs(float(loss2[0]) - float(loss[0])) <= 1e-5 * abs(float(loss[0]))
+
+
 def test_l1_loss_on_buffers_off_a_16_byte_boundary():
     # the float4 lanes need all three buffers aligned; views 4 bytes in take the one-by-one path
     W, H = 97, 31

@@ -79,7 +79,7 @@ def _build_into(out_dir, lib_path, defines, force, verbose):
     with concurrent.futures.ThreadPoolExecutor(max_workers=len(srcs)) as ex:
         objs = list(ex.map(lambda s: _compile(s, out_dir, defines, stamp, verbose), srcs))
     if force or _stale(lib_path, objs, stamp):
-        cmd = [nvcc()] + ARCH + ["-shared", "-Xcompiler", "-pthread", "-o", lib_path + ".tmp"] + objs
+        cmd = [nvcc()] + ARCH + ["-shared", "-Xcompiler", "-pthread", "-o", lib_path + ".tmp"] + objs + ["-ldl"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc link failed:\n" + r.stderr)

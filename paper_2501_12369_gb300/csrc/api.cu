@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cstdlib>
 
+#include "trace.h"
 #include "validate.h"
 
 bool darb::pdl_enabled() {
@@ -109,6 +110,7 @@ darb_status darb_kernel_generic(int32_t base, float xi, float beta, int32_t lobe
 }
 
 darb_status darb_kernel_psi(const darb_kernel_params *kparams, double *scratch, double *psi, darb_stream stream) {
+    DARB_TRACE(__func__);
     if (!valid_kernel(kparams) || !scratch || !psi) return DARB_ERR_INVALID_ARG;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     double sums[2] = {0.0, 0.0};
@@ -129,6 +131,7 @@ darb_status darb_tile_grid(const darb_camera *cam, int32_t tile, int32_t *tiles_
 
 darb_status darb_preprocess(const darb_splats *splats, const darb_camera *cam, const darb_kernel_params *kparams,
                             int32_t tile, const darb_projected *out, darb_stream stream) {
+    DARB_TRACE(__func__);
     if (!valid_splats(splats) || !valid_camera(cam) || !valid_kernel(kparams) || !valid_tile(tile))
         return DARB_ERR_INVALID_ARG;
     if (splats->n == 0) return DARB_OK;
@@ -153,6 +156,7 @@ darb_status darb_bin_sort(const darb_projected *proj, int32_t n, int32_t tile, c
                           const darb_kernel_params *kparams, void *workspace, size_t workspace_bytes,
                           uint64_t capacity, int32_t strategy, const darb_binning *out, uint64_t *num_instances_host,
                           darb_stream stream) {
+    DARB_TRACE(__func__);
     return darb::bin_sort_entry(proj, n, tile, cam, kparams, workspace, workspace_bytes, capacity, strategy, out,
                                 num_instances_host, stream, true);
 }
@@ -197,6 +201,7 @@ extern "C" {
 darb_status darb_render_fwd(const darb_projected *proj, const darb_binning *bins, const darb_camera *cam,
                             const darb_kernel_params *kparams, int32_t tile, const darb_image *out,
                             darb_stream stream) {
+    DARB_TRACE(__func__);
     if (!valid_projected_or_empty(proj) || !bins || !bins->ranges || !valid_camera(cam) || !valid_kernel(kparams) ||
         !valid_tile(tile) || !out || !out->image || !out->t_final || !out->last || !out->n_contrib)
         return DARB_ERR_INVALID_ARG;
@@ -213,6 +218,7 @@ darb_status darb_render_fwd(const darb_projected *proj, const darb_binning *bins
 darb_status darb_render_fwd_l1(const darb_projected *proj, const darb_binning *bins, const darb_camera *cam,
                                const darb_kernel_params *kparams, int32_t tile, const darb_image *out,
                                const float *target, float *dL_dimage, float *loss, darb_stream stream) {
+    DARB_TRACE(__func__);
     if (!valid_projected_or_empty(proj) || !bins || !bins->ranges || !valid_camera(cam) || !valid_kernel(kparams) ||
         !valid_tile(tile) || !out || !out->t_final || !out->last || !target || !dL_dimage || !loss)
         return DARB_ERR_INVALID_ARG;
@@ -230,6 +236,7 @@ darb_status darb_render_fwd_l1(const darb_projected *proj, const darb_binning *b
 darb_status darb_render_bwd(const darb_projected *proj, int32_t n, const darb_binning *bins, const darb_camera *cam,
                             const darb_kernel_params *kparams, int32_t tile, const darb_image *fwd,
                             const float *dL_dimage, float *grad2d, darb_stream stream) {
+    DARB_TRACE(__func__);
     if (n < 0 || !valid_projected_or_empty(proj) || !bins || !bins->ranges || !valid_camera(cam) ||
         !valid_kernel(kparams) || !valid_tile(tile) || !fwd || !fwd->t_final || !fwd->last || !dL_dimage ||
         (n > 0 && (!grad2d || !aligned16(grad2d))))
@@ -249,6 +256,7 @@ darb_status darb_render_bwd(const darb_projected *proj, int32_t n, const darb_bi
 darb_status darb_preprocess_bwd(const darb_splats *splats, const darb_camera *cam, const darb_kernel_params *kparams,
                                 const darb_projected *proj, const float *grad2d, const darb_splat_grads *out,
                                 darb_stream stream) {
+    DARB_TRACE(__func__);
     if (!valid_splats(splats) || !valid_camera(cam) || !valid_kernel(kparams)) return DARB_ERR_INVALID_ARG;
     if (splats->n == 0) return DARB_OK;
     if (!valid_projected(proj) || !grad2d || !aligned16(grad2d) || !out || !out->dmeans || !out->dscales ||
@@ -262,6 +270,7 @@ darb_status darb_preprocess_bwd(const darb_splats *splats, const darb_camera *ca
 
 darb_status darb_l1_loss(const float *image, const float *target, int32_t width, int32_t height, float *dL_dimage,
                          float *loss, darb_stream stream) {
+    DARB_TRACE(__func__);
     if (!image || !target || !dL_dimage || !loss || width <= 0 || height <= 0) return DARB_ERR_INVALID_ARG;
     DARB_CUDA_TRY(launch_l1_loss(image, target, 3 * width * height, dL_dimage, loss,
                                  reinterpret_cast<cudaStream_t>(stream)));
@@ -277,6 +286,7 @@ darb_status darb_l1_dssim_workspace_size(int32_t width, int32_t height, size_t *
 darb_status darb_l1_dssim_loss(const float *image, const float *target, int32_t width, int32_t height, float lambda,
                                void *workspace, size_t workspace_bytes, float *dL_dimage, float *loss,
                                darb_stream stream) {
+    DARB_TRACE(__func__);
     if (!image || !target || !dL_dimage || !loss || !workspace || width <= 0 || height <= 0 || width > 65536 ||
         height > 65536 || !(lambda >= 0.0f && lambda <= 1.0f))
         return DARB_ERR_INVALID_ARG;
@@ -310,6 +320,7 @@ bool adam_state_complete(const darb_adam_state *s) {
 
 darb_status darb_densify_stats(const float *grad2d, const int32_t *radius, int32_t n, int32_t width, int32_t height,
                                float *accum, float *count, int32_t *max_radius, darb_stream stream) {
+    DARB_TRACE(__func__);
     if (n < 0 || width <= 0 || height <= 0) return DARB_ERR_INVALID_ARG;
     if (n == 0) return DARB_OK;
     if (!grad2d || !aligned16(grad2d) || !radius || !accum || !count || !max_radius) return DARB_ERR_INVALID_ARG;
@@ -329,6 +340,7 @@ darb_status darb_densify(const darb_train_params *in, const darb_adam_state *in_
                          const darb_densify_cfg *cfg, void *workspace, size_t workspace_bytes, int32_t capacity,
                          const darb_train_params *out, const darb_adam_state *out_state, uint32_t *n_out,
                          darb_stream stream) {
+    DARB_TRACE(__func__);
     if (!train_params_complete(in) || !train_params_complete(out) || !adam_state_complete(in_state) ||
         !adam_state_complete(out_state) || !cfg || !workspace || !n_out || out->sh_degree != in->sh_degree ||
         capacity < 0 || (int64_t)capacity < 2 * (int64_t)in->n || !(cfg->split_scale_div > 0.0f) ||
@@ -343,6 +355,7 @@ darb_status darb_densify(const darb_train_params *in, const darb_adam_state *in_
 }
 
 darb_status darb_reset_opacity(const darb_train_params *params, float max_opacity, darb_stream stream) {
+    DARB_TRACE(__func__);
     if (!train_params_complete(params) || !(max_opacity > 0.0f && max_opacity < 1.0f)) return DARB_ERR_INVALID_ARG;
     DARB_CUDA_TRY(launch_reset_opacity(*params, max_opacity, reinterpret_cast<cudaStream_t>(stream)));
     return DARB_OK;
@@ -350,6 +363,7 @@ darb_status darb_reset_opacity(const darb_train_params *params, float max_opacit
 
 darb_status darb_adam_step(const darb_train_params *params, const darb_splat_grads *grads,
                            const darb_adam_state *state, const darb_adam_config *cfg, darb_stream stream) {
+    DARB_TRACE(__func__);
     if (!params || !grads || !state || !cfg || params->n < 0 || params->sh_degree < 0 || params->sh_degree > 3 ||
         cfg->step < 1 || !(cfg->beta1 >= 0.0f && cfg->beta1 < 1.0f) || !(cfg->beta2 >= 0.0f && cfg->beta2 < 1.0f) ||
         !(cfg->eps > 0.0f))
@@ -370,6 +384,7 @@ darb_status darb_preprocess_bwd_adam(const darb_train_params *params, const darb
                                      const darb_kernel_params *kparams, const darb_projected *proj,
                                      const float *grad2d, const darb_adam_state *state, const darb_adam_config *cfg,
                                      darb_stream stream) {
+    DARB_TRACE(__func__);
     if (!params || !state || !cfg || params->n < 0 || params->sh_degree < 0 || params->sh_degree > 3 ||
         !valid_camera(cam) || !valid_kernel(kparams) || cfg->step < 1 || !(cfg->beta1 >= 0.0f && cfg->beta1 < 1.0f) ||
         !(cfg->beta2 >= 0.0f && cfg->beta2 < 1.0f) || !(cfg->eps > 0.0f))

@@ -15,6 +15,7 @@
 #include <mutex>
 #include <vector>
 
+#include "trace.h"
 #include "validate.h"
 
 namespace darb {
@@ -155,6 +156,7 @@ darb_status darb_render_batch(const darb_splats *splats, const darb_camera *cams
                               const darb_batch_params *bp, void *workspace, size_t workspace_bytes,
                               const darb_image *outs, uint32_t *num_instances, uint32_t *status,
                               darb_stream stream) {
+    DARB_TRACE(__func__);
     if (!valid_splats(splats) || !cams || !valid_kernel(kparams) || !valid_params(bp) || !workspace || !outs)
         return DARB_ERR_INVALID_ARG;
     const int n = splats->n, V = bp->n_views, tile = bp->tile, D = bp->depth;

@@ -13,6 +13,7 @@
 // call, and calls whose work overlaps on the GPU race.
 #include <mutex>
 
+#include "trace.h"
 #include "validate.h"
 
 namespace {
@@ -46,6 +47,7 @@ extern "C" darb_status darb_bin_sort_noalloc(const darb_projected *proj, int32_t
                                              const darb_camera *cam, const darb_kernel_params *kparams,
                                              uint64_t capacity, const darb_binning *out,
                                              uint64_t *num_instances_host, darb_stream stream) {
+    DARB_TRACE(__func__);
     size_t need = 0;
     const darb_status qs = darb_bin_sort_workspace_size(n, tile, cam, capacity, DARB_SORT_DEPTH_THEN_TILE, &need);
     if (qs != DARB_OK) return qs;

@@ -335,3 +335,26 @@ def test_l1_dssim_full_hd_crops():
         sl = (slice(None), slice(y0 - ya, y0 - ya + 96), slice(x0 - xa, x0 - xa + 96))
         got = g[:, y0:y0 + 96, x0:x0 + 96]
         np.testing.assert_allclose(got, ref[sl], rtol=1e-3, atol=1e-4 * np.abs(ref[sl]).max())
+
+
+def test_resume_from_checkpoint_equals_continuing(tmp_path):
+    """One fused step, a checkpoint, then one more step, against the same second step taken
+    from the reloaded checkpoint: parameters, activated copies and moments agree bit for bit
+    (the fused step is a per-splat computation, so equal inputs give equal outputs)."""
+    from paper_2501_12369_gb300 import checkpoint
+    deg = 3
+    s, cam, r, sd, proj, g2, rng = _fused_case("half_cosine", deg, n=2500, seed=21)
+    raw, state = _train_state(s, rng, warm=False)
+    p, st = _to_device(raw, state, deg)
+    darb.darb_preprocess_bwd_adam(p, cam, r.kparams, proj, g2, st, _cfg(1))
+    torch.cuda.synchronize()
+    checkpoint.save_training(tmp_path / "ckpt.npz", p, st, step=1)
+    darb.darb_preprocess_bwd_adam(p, cam, r.kparams, proj, g2, st, _cfg(2))
+    p2, st2, step = checkpoint.load_training(tmp_path / "ckpt.npz", device="cuda")
+    assert step == 1
+    darb.darb_preprocess_bwd_adam(p2, cam, r.kparams, proj, g2, st2, _cfg(step + 1))
+    torch.cuda.synchronize()
+    for f in checkpoint.PARAM_FIELDS:
+        assert torch.equal(getattr(p2, f), getattr(p, f)), f
+    for f in checkpoint.STATE_FIELDS:
+        assert torch.equal(getattr(st2, f), getattr(st, f)), f

@@ -557,12 +557,18 @@ class Rasterizer:
     The sort workspace is scratch of a single call and is reused by every forward.  The lists a
     forward returns are reused too unless `forward(..., owned=True)` is asked for: then they are
     freshly allocated and belong to the caller, so several forwards can be pending a backward.
-    Calls are ordered on the current stream; forward synchronises once to read the instance count.
+    Calls are ordered on the current stream.  With sync=True (the default) forward synchronises
+    once to read the instance count and, if the lists did not fit, grows the capacity and sorts
+    again.  With sync=False nothing synchronises: the sort runs in its asynchronous capacity mode
+    (a view that does not fit renders as background and flags DARB_ERR_CAPACITY on the device),
+    and `check()` later reads every pending forward's status at once and raises on an overflow.
     """
 
     def __init__(self, cam, kernel="half_cosine", tile=16, capacity=None, device="cuda", psi=None,
-                 strategy=DARB_SORT_DEPTH_THEN_TILE):
+                 strategy=DARB_SORT_DEPTH_THEN_TILE, sync=True):
         self.cam = cam
+        self.sync = bool(sync)
+        self._pending = []  # asynchronous mode: (status, M) of every forward since the last check
         self.strategy = int(strategy)
         self.tile = int(tile)
         self.kparams = darb_kernel_defaults(kernel)
@@ -591,12 +597,20 @@ class Rasterizer:
         self._ensure(n, self.capacity)
         out = (Binning.empty(self.capacity, tx * ty, self.device, keys=self.strategy == DARB_SORT_KEYS64)
                if owned else self._bins)
-        return darb_bin_sort(proj, n, self.tile, self.cam, self._ws, self.capacity, out, strategy=self.strategy)
+        return darb_bin_sort(proj, n, self.tile, self.cam, self._ws, self.capacity, out, sync=self.sync,
+                             strategy=self.strategy)
 
     def forward(self, splats: SplatTensors, owned=False):
         proj = darb_preprocess(splats, self.cam, self.kparams, self.tile)
         if self.capacity == 0:
             self.capacity = max(1024, 8 * splats.n)
+        if not self.sync:
+            bins = self._sort(proj, splats.n, owned)
+            # a device-side copy of this call's status word and instance count (the shared
+            # lists of a later forward overwrite bins.status)
+            self._pending.append(torch.cat([bins.status[:1], bins.num_instances[:1]]))
+            img = darb_render_fwd(proj, bins, self.cam, self.kparams, self.tile)
+            return proj, bins, img
         try:
             bins = self._sort(proj, splats.n, owned)
         except DarbError as e:
@@ -606,6 +620,21 @@ class Rasterizer:
             bins = self._sort(proj, splats.n, owned)
         img = darb_render_fwd(proj, bins, self.cam, self.kparams, self.tile)
         return proj, bins, img
+
+    def check(self):
+        """Asynchronous mode: one synchronisation for every forward since the last check.  Raises
+        DarbError (with .M, the largest instance count asked for) if any of them overflowed its
+        capacity; those images are background only.  The pending list is cleared either way."""
+        pending, self._pending = self._pending, []
+        if not pending:
+            return
+        sm = torch.stack(pending).cpu().numpy().astype(np.int64)
+        sm[:, 1] &= 0xFFFFFFFF  # the count is a u32 in an int32 tensor
+        bad = sm[:, 0] != 0
+        if bad.any():
+            err = DarbError(int(sm[bad][0, 0]), "Rasterizer.check")
+            err.M = int(sm[bad][:, 1].max())
+            raise err
 
     def backward(self, splats, proj, bins, img, dL_dimage, cam=None):
         cam = self.cam if cam is None else cam

@@ -161,3 +161,32 @@ def test_finite_difference_spot_check(kernel):
             assert abs(fd - g[idx]) <= 2e-2 * abs(g[idx]) + 2e-3 * scale, \
                 f"{kernel}/{name}[{idx}]: finite difference {fd:.6g} against backward {g[idx]:.6g}"
     assert checked >= 0.8 * (checked + flipped), f"only {checked} of {checked + flipped} samples were smooth"
+
+
+def test_asynchronous_rasterizer_matches_and_reports_overflow():
+    """sync=False: no synchronisation per forward.  With room for the lists, the images, lists and
+    the autograd gradients' forward equal the synchronous rasterizer's bit for bit and check()
+    passes; with too small a capacity check() raises DARB_ERR_CAPACITY with the instance count
+    the view needs, after two forwards (the first one fitting)."""
+    s = synth.cluster_scene(20000, seed=5, sh_degree=3)
+    cam = synth.fibonacci_cameras(16, 6.0, 333, 207, 260.0)[3]
+    sd = darb.splats_to_device(s)
+    r_sync = darb.Rasterizer(cam, "half_cosine", 16)
+    proj_a, bins_a, img_a = r_sync.forward(sd, owned=True)
+    torch.cuda.synchronize()
+    M = bins_a.M
+    r_async = darb.Rasterizer(cam, "half_cosine", 16, capacity=r_sync.capacity, sync=False)
+    proj_b, bins_b, img_b = r_async.forward(sd, owned=True)
+    r_async.check()
+    assert bins_b.M is None and int(bins_b.num_instances[0]) == M
+    assert torch.equal(bins_a.values[:M], bins_b.values[:M]) and torch.equal(bins_a.ranges, bins_b.ranges)
+    assert torch.equal(img_a.image, img_b.image) and torch.equal(img_a.last, img_b.last)
+    # too small for the second view: the deferred check names the overflow and the count needed
+    small = darb.Rasterizer(cam, "half_cosine", 16, capacity=M - 1, sync=False)
+    tiny = darb.splats_to_device(synth.cluster_scene(50, seed=6, sh_degree=3))
+    small.forward(tiny)
+    small.forward(sd)
+    with pytest.raises(darb.DarbError) as e:
+        small.check()
+    assert e.value.status == 3 and e.value.M == M
+    small.check()  # the pending list was cleared

@@ -55,7 +55,10 @@ constexpr uint32_t kCountMask = (1u << 30) - 1;
 #define DARB_SPIN_LIMIT (1 << 22)  // with the 512 ns back-off: about two seconds at most
 #endif
 constexpr int kSpinLimit = DARB_SPIN_LIMIT;
-constexpr int kLookbackWindow = 8;
+#ifndef DARB_LOOKBACK_WINDOW
+#define DARB_LOOKBACK_WINDOW 8  // predecessor statuses a digit's look-back reads per round trip
+#endif
+constexpr int kLookbackWindow = DARB_LOOKBACK_WINDOW;
 constexpr size_t kMaxDiffSmem = 96 * 1024;  // tile difference array privatised per CTA up to this size
 constexpr size_t kMaxSetupSmem = 160 * 1024;  // tile counts + difference array staged in shared memory up to this
 constexpr int kDupItems = 16;

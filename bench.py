@@ -2,11 +2,13 @@
 """Benchmark of the DARB rasterizer on GB300: one 3DGS-style training iteration per step.
 
 Workload: 3,000,000 clustered splats (SH degree 3), 100 cameras on a radius-6 sphere,
-1920x1080, fx = 1500, half-cosine kernel (the paper's headline DARB kernel), 16x16 tiles.
-A step is the whole hot path for one camera: preprocess -> tile/depth key duplication ->
-radix sort + tile ranges -> compositing -> L1 loss -> compositing backward -> preprocess
-backward -> Adam, all in libdarb.so kernels called through the C ABI.  The splat state
-(~2.1 GB with Adam moments) is far larger than L2, so no L2 flush is needed between steps.
+1920x1080, fx = 1500, half-cosine kernel (the paper's headline DARB kernel); the tile size is
+autotuned over 8, 16 and 32 pixels (32 wins).  A step is the whole hot path for one camera:
+preprocess -> per-tile lists (depth sort of the visible splats, their instances in depth
+order, the tile passes, the ranges) -> compositing with the L1 loss in its epilogue ->
+compositing backward -> preprocess backward fused with Adam, all in libdarb.so kernels called
+through the C ABI.  The splat state (~2.1 GB with Adam moments) is far larger than L2, so no
+L2 flush is needed between steps.
 
 Prints one JSON line (rank 0).  --impl reference times the CPU oracle instead.
 """

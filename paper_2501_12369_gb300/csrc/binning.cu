@@ -645,17 +645,30 @@ k_tile_diff(int n, const uint32_t *__restrict__ order, const uint32_t *__restric
                 add(ty, c0, c1);
                 return true;
             });
-        for (uint32_t bm = __ballot_sync(0xffffffffu, live && pk == kRunsUnpacked); bm; bm &= bm - 1) {
-            const int iL = __shfl_sync(0xffffffffu, i, __ffs(bm) - 1);
+        // run-table entries for the warp's unpacked splats: one reservation per warp (a prefix
+        // sum of their row counts), not one atomic on the shared counter per splat
+        const bool big = live && pk == kRunsUnpacked;
+        uint32_t my_rows = big ? (uint32_t)(r.w - r.y + 1) : 0u, my_pre = my_rows;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, my_pre, o);
+            if (lane >= o) my_pre += y;
+        }
+        const uint32_t warp_rows = __shfl_sync(0xffffffffu, my_pre, 31);
+        uint32_t warp_base = 0;
+        if (rt.tab && lane == 0 && warp_rows) warp_base = atomicAdd(rt.count, warp_rows);
+        warp_base = __shfl_sync(0xffffffffu, warp_base, 0);
+        my_pre = warp_base + my_pre - my_rows;  // this lane's first entry
+        for (uint32_t bm = __ballot_sync(0xffffffffu, big); bm; bm &= bm - 1) {
+            const int src = __ffs(bm) - 1;
+            const int iL = __shfl_sync(0xffffffffu, i, src);
             const float2 mu = mean2d[iL];
             const float4 co = conic_o[iL];
             const int4 rL = rect[iL];
             // the rows' runs go to the run table too, for the duplication (every row, the empty
             // ones marked; each lane writes the rows it computes, so no two lanes share an entry)
             const uint32_t rows = (uint32_t)(rL.w - rL.y + 1);
-            uint32_t base = 0;
-            if (rt.tab && lane == 0) base = atomicAdd(rt.count, rows);
-            base = __shfl_sync(0xffffffffu, base, 0);
+            const uint32_t base = __shfl_sync(0xffffffffu, my_pre, src);
             const bool keep = rt.tab && (unsigned long long)base + rows <= rt.cap;
             if (keep)
                 for (uint32_t k = lane; k < rows; k += 32) rt.tab[base + k] = kRowEmpty;

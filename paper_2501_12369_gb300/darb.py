@@ -562,6 +562,8 @@ class Rasterizer:
     again.  With sync=False nothing synchronises: the sort runs in its asynchronous capacity mode
     (a view that does not fit renders as background and flags DARB_ERR_CAPACITY on the device),
     and `check()` later reads every pending forward's status at once and raises on an overflow.
+    Each pending forward keeps an 8-byte device tensor until the next check(), so a long run
+    should call check() now and then (once per step or per batch of views).
     """
 
     def __init__(self, cam, kernel="half_cosine", tile=16, capacity=None, device="cuda", psi=None,
